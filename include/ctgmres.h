@@ -1,0 +1,194 @@
+/*
+ * ctgmres: AB-GMRES and BA-GMRES for 2D parallel-beam CT with an unmatched
+ * back projector B != A^T, on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (paper Sec. 1, eq. (1.1)): A x ~ b with b = A x_bar + e,
+ * A in R^{m x n} the forward projector, B in R^{n x m} the back projector,
+ * n = N^2 pixels, m = n_angles * n_det rays.  The solvers (Sec. 2, algorithm
+ * box) build the Krylov space K_k(BA, B r0) and minimise ||b - A x|| (AB) or
+ * ||B b - B A x|| (BA); the discrepancy principle (Sec. 6.4) stops at the
+ * first k with ||b - A x_k|| <= tau ||e||.
+ *
+ * Discretisation (the paper names ASTRA's interpolation/Joseph model for A
+ * but gives no formulas; this is the library's fixed reading):
+ *   pixel (i, j) (row i, column j) has centre (j - (N-1)/2, i - (N-1)/2),
+ *   pixel size 1; angle a is theta_a = start + a * range / n_angles degrees
+ *   (start and range integers, endpoint excluded); detector d has centre
+ *   s_d = (d - (n_det-1)/2) * det_spacing; ray (a, d) is the line
+ *   x cos(theta_a) + y sin(theta_a) = s_d.
+ *   A (Joseph): rays with theta mod 180 in [0, 45] or [135, 180) step over
+ *   image rows, the others over columns; per step one linear interpolation
+ *   between the two nearest pixels (pixels outside the image are 0), the
+ *   sum scaled by 1/|cos| (rows) or 1/|sin| (columns).
+ *   B (pixel-driven): (B b)[i, j] = sum_a lerp of b[a, .] at detector
+ *   position u = (x_j cos + y_i sin)/det_spacing + (n_det-1)/2; bins outside
+ *   the detector are 0.  B gathers only; it is not the transpose of A.
+ *
+ * Layouts: image x[i * N + j] (row-major float32); sinogram b[a * n_det + d]
+ * (angle-major float32).  All vectors are caller-owned DEVICE memory unless
+ * stated otherwise.
+ *
+ * Errors: every int-returning call returns CTG_OK (0) or a negative status;
+ * ctg_status_string() names it.  Invalid arguments are rejected on the host
+ * before any launch.  Calls enqueue work on `stream` (a cudaStream_t; NULL is
+ * the legacy default stream) and return without waiting, except the two
+ * solvers, which synchronise `stream` before returning to fill ctg_info.
+ */
+#ifndef CTGMRES_H
+#define CTGMRES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CTG_OK = 0,
+    CTG_ERR_INVALID_ARG = -1,  /* bad geometry, null pointer, size or option */
+    CTG_ERR_OOM = -2,          /* device allocation failed                   */
+    CTG_ERR_CUDA = -3,         /* a CUDA runtime call failed                 */
+    CTG_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up         */
+    CTG_ERR_WORKSPACE = -5     /* caller workspace smaller than required     */
+};
+
+enum { CTG_AB = 0, CTG_BA = 1 };                       /* solver variant    */
+enum { CTG_STOP_MAXIT = 0, CTG_STOP_DP = 1, CTG_STOP_BREAKDOWN = 2 };
+enum { CTG_BASIS_FP32 = 0 };                           /* basis storage     */
+
+/* 2D parallel-beam geometry (paper Sec. 6.1, Table 1).  Limits: 1 <= N <=
+ * 16384, 1 <= n_angles, 1 <= n_det <= 65536, start and range integral
+ * degrees with 0 < range <= 360, det_spacing > 0. */
+typedef struct {
+    int32_t N;                /* image side; n = N * N pixels               */
+    int32_t n_angles;         /* N_ang                                      */
+    int32_t n_det;            /* N_det                                      */
+    int32_t reserved;         /* must be 0                                  */
+    double angle_start_deg;   /* theta_0, integer degrees                   */
+    double angle_range_deg;   /* angles span [start, start + range)        */
+    double det_spacing;       /* detector pitch in pixel units (1 = pixel)  */
+} ctg_geom;
+
+/* Solver options. */
+typedef struct {
+    int32_t maxit;            /* iteration cap, >= 1                        */
+    int32_t basis_dtype;      /* CTG_BASIS_FP32                             */
+    double tau;               /* DP safety factor tau >= 1 (Sec. 6.4)       */
+    double noise_norm;        /* ||e||; <= 0 disables the DP stop           */
+} ctg_opts;
+
+/* Solver report, filled on return (host memory). */
+typedef struct {
+    int32_t iters;            /* k of the returned iterate x_k (0 = x0)     */
+    int32_t stop_reason;      /* CTG_STOP_*                                 */
+    double resnorm;           /* ||b - A x_k|| of the returned iterate,
+                                 recomputed from x_k in FP32/FP64           */
+    double rho;               /* GMRES residual: | ||r0|| e1 - H_k y_k |    */
+    double *history;          /* optional caller host array, >= maxit + 1
+                                 entries, or NULL: entry k = ||b - A x_k||
+                                 as used by the DP test (AB: the Hessenberg
+                                 residual, equal in exact arithmetic)      */
+} ctg_info;
+
+/* Where the solver keeps its state inside a caller workspace (byte offsets
+ * from the workspace base).  The basis W holds vectors w_1..w_{k+1}, each of
+ * length L (L = m for AB, n for BA) at stride ld_w floats (ld_w >= L, a
+ * multiple of 64); H is the FP64 (maxit+1) x maxit Hessenberg matrix stored
+ * column by column with leading dimension maxit+1 (h_{i,k} at
+ * H[(k-1) * (maxit+1) + (i-1)]). After a solve these hold the final basis
+ * and Hessenberg matrix, so callers can inspect them. */
+typedef struct {
+    size_t off_w;
+    size_t ld_w;              /* in elements                               */
+    size_t off_h;
+    size_t total_bytes;       /* == ctg_workspace_bytes()                  */
+} ctg_layout;
+
+typedef struct ctg_ctx ctg_ctx;
+
+/* Create / destroy a context on the current CUDA device.  The context caches
+ * per-geometry angle tables and a pinned host staging area; it is not
+ * thread-safe (use one context per host thread). */
+int ctg_create(ctg_ctx **out);
+void ctg_destroy(ctg_ctx *ctx);
+
+/* b = A x: Joseph forward projection (eq. (1.1)).
+ * x: n floats (device, read-only); b: m floats (device, overwritten).
+ * Needs no workspace beyond a context-owned padded image copy (allocated on
+ * first use per geometry; CTG_ERR_OOM if that fails). */
+int ctg_project(ctg_ctx *ctx, const ctg_geom *g, const float *x_dev,
+                float *b_dev, void *stream);
+
+/* x = B b: pixel-driven unmatched back projection (B in eq. (1.2)).
+ * b: m floats (device, read-only); x: n floats (device, overwritten). */
+int ctg_backproject(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev,
+                    float *x_dev, void *stream);
+
+/* Bytes of device workspace a solve of `variant` with these options needs;
+ * 0 if the arguments are invalid.  Dominated by the basis, (maxit + 1)
+ * vectors of length L, which is the paper's storage law k * L (Table 3). */
+size_t ctg_workspace_bytes(const ctg_geom *g, int variant, const ctg_opts *o);
+
+/* Fill *out with the workspace layout for these arguments. */
+int ctg_workspace_layout(const ctg_geom *g, int variant, const ctg_opts *o,
+                         ctg_layout *out);
+
+/* AB-GMRES (Sec. 2, left column): x = x0 + B W_k y_k.
+ * b: m floats; x0: n floats or NULL (x0 = 0); x: n floats (output).
+ * workspace: device memory of >= workspace_bytes bytes, 256-byte aligned, or
+ * NULL, in which case the library allocates and frees it per call.  The
+ * caller owns b, x0, x and the workspace; none may alias another.  Runs on
+ * `stream`, synchronises it before returning and fills *info (info may not
+ * be NULL).  A breakdown (h_{k+1,k} <= 1e-6 ||A B w_k||) is reported in
+ * info->stop_reason, not as an error. */
+int ctg_ab_gmres(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev,
+                 const float *x0_dev, float *x_dev, const ctg_opts *o,
+                 void *workspace_dev, size_t workspace_bytes, ctg_info *info,
+                 void *stream);
+
+/* BA-GMRES (Sec. 2, right column): x = x0 + W_k y_k; same conventions.
+ * The DP test uses the true residual ||b - A x_k||, which costs one extra
+ * forward projection per iteration. */
+int ctg_ba_gmres(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev,
+                 const float *x0_dev, float *x_dev, const ctg_opts *o,
+                 void *workspace_dev, size_t workspace_bytes, ctg_info *info,
+                 void *stream);
+
+/* One classical Gram-Schmidt step with reorthogonalisation (CGS2) of q
+ * against the k orthonormal columns of W, the Arnoldi step of Sec. 2 with
+ * MGS replaced by CGS2 (equal in exact arithmetic):
+ *   h = W^T q; q -= W h; h' = W^T q; q -= W h';  h_out[0..k-1] = h + h',
+ *   h_out[k] = ||q||, and, if h_out[k] > 0, w_out = q / ||q||.
+ * W: k vectors of length L at stride ld_w floats (ld_w >= L, multiple of
+ * 4), device, read-only; q: L floats, device, overwritten by the
+ * orthogonalised vector; w_out: L floats, device (may equal q);
+ * h_out: k + 1 doubles, device; 0 <= k <= 4096.
+ * scratch: device memory of >= ctg_cgs2_scratch_bytes(L, k) bytes (256-byte
+ * aligned), owned by the caller; its contents need no initialisation. */
+size_t ctg_cgs2_scratch_bytes(int64_t L, int32_t k);
+int ctg_cgs2(const float *W_dev, int64_t ld_w, int64_t L, int32_t k,
+             float *q_dev, float *w_out_dev, double *h_out_dev,
+             void *scratch_dev, size_t scratch_bytes, void *stream);
+
+/* Phase tracing (the paper has no counterpart; it reports no timings).
+ * When enabled, the solvers bracket each phase with CUDA events on the
+ * solver's stream and accumulate its device time; kernel launches are
+ * counted whether or not timing is enabled.  Phases: 0 forward projection
+ * (image staging + Joseph A), 1 back projection (B), 2 Arnoldi CGS2 step,
+ * 3 everything else (residual norms, iterate formation). */
+typedef struct {
+    double ms[4];             /* accumulated device milliseconds per phase */
+    int64_t calls[4];         /* phase executions per phase                */
+    int64_t kernels;          /* kernels launched by the library           */
+} ctg_timing;
+int ctg_set_timing(ctg_ctx *ctx, int enable);
+/* Copy the counters into *out; reset them if `reset` is nonzero. */
+int ctg_get_timing(ctg_ctx *ctx, ctg_timing *out, int reset);
+
+const char *ctg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTGMRES_H */

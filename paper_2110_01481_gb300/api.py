@@ -1,0 +1,236 @@
+"""Torch-facing wrappers of the C-ABI (include/ctgmres.h).
+
+Arguments are torch tensors on a CUDA device (float32, contiguous, 16-byte
+aligned); calls are enqueued on torch's current stream of that device.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass, field
+from typing import Optional
+
+import torch
+
+from . import _native as nat
+
+
+@dataclass(frozen=True)
+class Geometry:
+    """2D parallel-beam geometry (paper Sec. 6.1, Table 1)."""
+    N: int
+    n_angles: int
+    n_det: int
+    angle_start_deg: float = 0.0
+    angle_range_deg: float = 180.0
+    det_spacing: float = 1.0
+
+    @property
+    def n(self) -> int:
+        return self.N * self.N
+
+    @property
+    def m(self) -> int:
+        return self.n_angles * self.n_det
+
+    def c(self) -> nat.CtgGeom:
+        return nat.CtgGeom(self.N, self.n_angles, self.n_det, 0,
+                           float(self.angle_start_deg), float(self.angle_range_deg),
+                           float(self.det_spacing))
+
+
+class Context:
+    """One ctg_ctx per CUDA device (cached angle tables, pinned staging)."""
+    _per_device: dict = {}
+
+    def __init__(self, device: int):
+        self.device = device
+        self.handle = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            nat.check(nat.lib().ctg_create(ctypes.byref(self.handle)), "ctg_create")
+
+    @classmethod
+    def get(cls, device) -> "Context":
+        idx = torch.device(device).index
+        if idx is None:
+            idx = torch.cuda.current_device()
+        ctx = cls._per_device.get(idx)
+        if ctx is None:
+            ctx = cls._per_device[idx] = Context(idx)
+        return ctx
+
+    def set_timing(self, enable: bool) -> None:
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().ctg_set_timing(self.handle, int(enable)), "ctg_set_timing")
+
+    def timing(self, reset: bool = False) -> dict:
+        """Per-phase device milliseconds and call counts, and the number of
+        kernels the library launched, since the last reset."""
+        t = nat.CtgTiming()
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().ctg_get_timing(self.handle, ctypes.byref(t), int(reset)),
+                      "ctg_get_timing")
+        out = {p: {"ms": t.ms[i], "calls": int(t.calls[i])} for i, p in enumerate(nat.PHASES)}
+        out["kernels"] = int(t.kernels)
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and nat._lib is not None:
+            try:
+                with torch.cuda.device(self.device):
+                    nat.lib().ctg_destroy(h)
+            except Exception:
+                pass
+
+
+def _dev_ptr(t: torch.Tensor, numel: int, name: str, dtype=torch.float32) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name}: expected a contiguous {dtype} tensor of {numel} elements, "
+                         f"got {t.dtype} {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def project(g: Geometry, x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """b = A x (Joseph forward projection); x: n floats (any shape)."""
+    if out is None:
+        out = torch.empty(g.m, device=x.device, dtype=torch.float32)
+    px, pb = _dev_ptr(x, g.n, "x"), _dev_ptr(out, g.m, "out")
+    ctx = Context.get(x.device)
+    with torch.cuda.device(x.device):
+        nat.check(nat.lib().ctg_project(ctx.handle, ctypes.byref(g.c()), px, pb,
+                                        _stream(x.device)), "ctg_project")
+    return out
+
+
+def backproject(g: Geometry, b: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """x = B b (pixel-driven unmatched back projection); b: m floats."""
+    if out is None:
+        out = torch.empty(g.n, device=b.device, dtype=torch.float32)
+    pb, px = _dev_ptr(b, g.m, "b"), _dev_ptr(out, g.n, "out")
+    ctx = Context.get(b.device)
+    with torch.cuda.device(b.device):
+        nat.check(nat.lib().ctg_backproject(ctx.handle, ctypes.byref(g.c()), pb, px,
+                                            _stream(b.device)), "ctg_backproject")
+    return out
+
+
+def _opts(maxit: int, tau: float, noise_norm: Optional[float]) -> nat.CtgOpts:
+    return nat.CtgOpts(int(maxit), nat.CTG_BASIS_FP32, float(tau),
+                       float(noise_norm) if noise_norm else 0.0)
+
+
+def workspace_bytes(g: Geometry, variant: str, maxit: int) -> int:
+    """Device bytes one solve needs (0 if the arguments are invalid)."""
+    v = nat.CTG_AB if variant == "ab" else nat.CTG_BA
+    return int(nat.lib().ctg_workspace_bytes(ctypes.byref(g.c()), v,
+                                             ctypes.byref(_opts(maxit, 1.0, None))))
+
+
+def workspace_layout(g: Geometry, variant: str, maxit: int) -> nat.CtgLayout:
+    v = nat.CTG_AB if variant == "ab" else nat.CTG_BA
+    out = nat.CtgLayout()
+    nat.check(nat.lib().ctg_workspace_layout(ctypes.byref(g.c()), v,
+                                             ctypes.byref(_opts(maxit, 1.0, None)),
+                                             ctypes.byref(out)), "ctg_workspace_layout")
+    return out
+
+
+@dataclass
+class SolveResult:
+    x: torch.Tensor
+    iters: int
+    stop_reason: int          # 0 maxit, 1 discrepancy principle, 2 breakdown
+    resnorm: float            # ||b - A x_k|| of the returned iterate
+    rho: float                # GMRES residual of the last step
+    history: list = field(default_factory=list)
+    workspace: Optional[torch.Tensor] = None
+
+    def basis(self, g: Geometry, variant: str, maxit: int) -> torch.Tensor:
+        """View of the final Krylov basis W (iters+1 vectors) in the workspace."""
+        ly = workspace_layout(g, variant, maxit)
+        L = g.m if variant == "ab" else g.n
+        f = self.workspace.view(torch.float32)
+        W = f[ly.off_w // 4: ly.off_w // 4 + ly.ld_w * (maxit + 1)].view(maxit + 1, ly.ld_w)
+        return W[: self.iters + 1, :L]
+
+    def hessenberg(self, g: Geometry, variant: str, maxit: int) -> torch.Tensor:
+        """The (iters+1) x iters Hessenberg matrix H_k (FP64) from the workspace."""
+        ly = workspace_layout(g, variant, maxit)
+        d = self.workspace[ly.off_h: ly.off_h + 8 * (maxit + 1) * maxit].view(torch.float64)
+        H = d.view(maxit, maxit + 1).t()          # column-major storage
+        return H[: self.iters + 1, : self.iters]
+
+
+def _solve(fn, variant: str, g: Geometry, b: torch.Tensor, maxit: int,
+           x0: Optional[torch.Tensor], tau: float, noise_norm: Optional[float],
+           out: Optional[torch.Tensor], workspace: Optional[torch.Tensor],
+           keep_workspace: bool) -> SolveResult:
+    dev = b.device
+    pb = _dev_ptr(b, g.m, "b")
+    px0 = _dev_ptr(x0, g.n, "x0") if x0 is not None else None
+    if out is None:
+        out = torch.empty(g.n, device=dev, dtype=torch.float32)
+    px = _dev_ptr(out, g.n, "out")
+    o = _opts(maxit, tau, noise_norm)
+    need = workspace_bytes(g, variant, maxit)
+    if need == 0:
+        raise nat.CtgError(nat.CTG_ERR_INVALID_ARG, f"ctg_{variant}_gmres")
+    if workspace is None and keep_workspace:
+        workspace = torch.empty(need, device=dev, dtype=torch.uint8)
+    pws, nws = (None, 0)
+    if workspace is not None:
+        pws, nws = _dev_ptr(workspace, workspace.numel(), "workspace", torch.uint8), workspace.numel()
+    hist = (ctypes.c_double * (maxit + 1))(*([math.nan] * (maxit + 1)))
+    info = nat.CtgInfo(0, 0, 0.0, 0.0, hist)
+    ctx = Context.get(dev)
+    with torch.cuda.device(dev):
+        nat.check(fn(ctx.handle, ctypes.byref(g.c()), pb, px0, px, ctypes.byref(o), pws, nws,
+                     ctypes.byref(info), _stream(dev)), f"ctg_{variant}_gmres")
+    return SolveResult(out, info.iters, info.stop_reason, info.resnorm, info.rho,
+                       list(hist[: info.iters + 1]), workspace)
+
+
+def ab_gmres(g: Geometry, b: torch.Tensor, maxit: int, x0=None, tau: float = 1.0,
+             noise_norm: Optional[float] = None, out=None, workspace=None,
+             keep_workspace: bool = False) -> SolveResult:
+    """AB-GMRES (paper Sec. 2) with the discrepancy-principle stop when
+    noise_norm is given (Sec. 6.4)."""
+    return _solve(nat.lib().ctg_ab_gmres, "ab", g, b, maxit, x0, tau, noise_norm, out,
+                  workspace, keep_workspace)
+
+
+def ba_gmres(g: Geometry, b: torch.Tensor, maxit: int, x0=None, tau: float = 1.0,
+             noise_norm: Optional[float] = None, out=None, workspace=None,
+             keep_workspace: bool = False) -> SolveResult:
+    """BA-GMRES (paper Sec. 2); same conventions as ``ab_gmres``."""
+    return _solve(nat.lib().ctg_ba_gmres, "ba", g, b, maxit, x0, tau, noise_norm, out,
+                  workspace, keep_workspace)
+
+
+def cgs2(W: torch.Tensor, k: int, q: torch.Tensor, w_out: Optional[torch.Tensor] = None,
+         scratch: Optional[torch.Tensor] = None):
+    """One CGS2 Arnoldi step of q against the first k rows of W (2-D tensor,
+    rows = basis vectors).  Returns (h, w_out), h = k+1 doubles."""
+    L = q.numel()
+    ldw = W.stride(0) if W.dim() == 2 else L
+    if W.dtype != torch.float32 or not W.is_cuda or W.stride(-1) != 1:
+        raise ValueError("W must be a CUDA float32 tensor with unit inner stride")
+    if w_out is None:
+        w_out = torch.empty_like(q)
+    h = torch.empty(k + 1, device=q.device, dtype=torch.float64)
+    need = int(nat.lib().ctg_cgs2_scratch_bytes(L, k))
+    if scratch is None:
+        scratch = torch.empty(need, device=q.device, dtype=torch.uint8)
+    with torch.cuda.device(q.device):
+        nat.check(nat.lib().ctg_cgs2(W.data_ptr(), ldw, L, k, _dev_ptr(q, L, "q"),
+                                     _dev_ptr(w_out, L, "w_out"), h.data_ptr(),
+                                     scratch.data_ptr(), scratch.numel(),
+                                     _stream(q.device)), "ctg_cgs2")
+    return h, w_out

@@ -1,0 +1,742 @@
+// C-ABI of libctgmres (declared in include/ctgmres.h): geometry tables,
+// workspace layout and the host loops of AB-GMRES and BA-GMRES (paper
+// Sec. 2, algorithm box), with the Hessenberg least-squares problem solved
+// by FP64 Givens rotations on the host and the discrepancy-principle stop
+// of Sec. 6.4.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ctg_internal.cuh"
+
+namespace {
+
+constexpr int kMaxIt = 4096;
+constexpr double kBreakdownRtol = 1e-6;   // h_{k+1,k} <= rtol * ||q before CGS2||
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+bool geom_valid(const ctg_geom *g) {
+    if (!g || g->reserved != 0) return false;
+    if (g->N < 1 || g->N > 16384 || g->n_angles < 1 || g->n_angles > (1 << 20)) return false;
+    if (g->n_det < 1 || g->n_det > 65536) return false;
+    if (!(g->det_spacing > 0.0) || !std::isfinite(g->det_spacing)) return false;
+    if ((double)g->n_det * g->det_spacing > (double)(1 << 20)) return false;
+    const double S = g->angle_start_deg, R = g->angle_range_deg;
+    if (!std::isfinite(S) || !std::isfinite(R) || S != std::floor(S) || R != std::floor(R)) return false;
+    if (R <= 0.0 || R > 360.0 || std::fabs(S) > 3600.0) return false;
+    return true;
+}
+
+bool opts_valid(const ctg_opts *o) {
+    if (!o || o->maxit < 1 || o->maxit > kMaxIt) return false;
+    if (o->basis_dtype != CTG_BASIS_FP32) return false;
+    if (!std::isfinite(o->tau) || !std::isfinite(o->noise_norm)) return false;
+    if (o->noise_norm > 0.0 && !(o->tau > 0.0)) return false;
+    return true;
+}
+
+long long to_fx(double v) { return std::llround(std::ldexp(v, CTG_FX_BITS)); }
+
+// theta_a = S + a R / N_a degrees, i.e. theta_a * N_a = num (an integer).
+void angle_of(const ctg_geom *g, int a, double *c, double *s, int *row_driven) {
+    const long long Na = g->n_angles;
+    const long long num = (long long)g->angle_start_deg * Na + (long long)a * (long long)g->angle_range_deg;
+    const long long half_turn = 180 * Na;
+    long long T = num % half_turn;
+    if (T < 0) T += half_turn;
+    // row-driven iff theta mod 180 in [0, 45] or [135, 180)
+    *row_driven = (4 * T <= half_turn) || (4 * T >= 3 * half_turn);
+    const long long quarter = 90 * Na;
+    if (num % quarter == 0) {
+        long long q = (num / quarter) % 4;
+        if (q < 0) q += 4;
+        static const double cq[4] = {1.0, 0.0, -1.0, 0.0}, sq[4] = {0.0, 1.0, 0.0, -1.0};
+        *c = cq[q];
+        *s = sq[q];
+    } else {
+        const double th = (double)num / (double)half_turn * M_PI;
+        *c = std::cos(th);
+        *s = std::sin(th);
+    }
+}
+
+void build_tables(const ctg_geom *g, std::vector<FwdAngle> &fw, std::vector<BackAngle> &bk) {
+    const double h = 0.5 * (g->N - 1), hd = 0.5 * (g->n_det - 1), ds = g->det_spacing;
+    fw.resize(g->n_angles);
+    bk.resize(g->n_angles);
+    for (int a = 0; a < g->n_angles; ++a) {
+        double cs, sn;
+        int rd;
+        angle_of(g, a, &cs, &sn, &rd);
+        const double c = rd ? cs : sn, s = rd ? sn : cs;
+        const double P = ds / c, Q = (h * s - hd * ds) / c + h, D = -s / c;
+        FwdAngle &f = fw[a];
+        f.P = to_fx(P);
+        f.Q = to_fx(Q);
+        f.D = to_fx(D);
+        f.pf = (float)P;
+        f.qf = (float)Q;
+        f.df = (float)D;
+        f.scale = (float)(1.0 / std::fabs(c));
+        f.row_driven = rd;
+        f.pad_ = 0;
+        BackAngle &b = bk[a];
+        b.COS = to_fx(cs / ds);
+        b.SIN = to_fx(sn / ds);
+        b.C = to_fx(hd - h * (cs + sn) / ds);
+        b.cf = (float)(cs / ds);
+        b.sf = (float)(sn / ds);
+    }
+}
+
+bool same_geom(const ctg_geom &a, const ctg_geom &b) {
+    return a.N == b.N && a.n_angles == b.n_angles && a.n_det == b.n_det &&
+           a.angle_start_deg == b.angle_start_deg && a.angle_range_deg == b.angle_range_deg &&
+           a.det_spacing == b.det_spacing;
+}
+
+struct GeomEntry {
+    ctg_geom g;
+    FwdAngle *fwd = nullptr;
+    BackAngle *back = nullptr;
+    float *pad = nullptr;       // context-owned padded image for ctg_project
+    unsigned long long last_use = 0;
+};
+
+struct WsLayout {
+    size_t off_w, ld_w, off_h, off_pad, off_vn0, off_vm0, off_vm1, off_y, off_red, total;
+    int64_t L, n, m;
+    int kmax;
+};
+
+bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) {
+    if (!geom_valid(g) || !opts_valid(o) || (variant != CTG_AB && variant != CTG_BA)) return false;
+    const int64_t n = (int64_t)g->N * g->N, m = (int64_t)g->n_angles * g->n_det;
+    const int64_t L = variant == CTG_AB ? m : n;
+    ly->n = n;
+    ly->m = m;
+    ly->L = L;
+    ly->kmax = o->maxit;
+    ly->ld_w = round_up((size_t)L, 64);
+    size_t off = 0;
+    ly->off_w = off;
+    off = align256(off + sizeof(float) * ly->ld_w * (size_t)(o->maxit + 1));
+    ly->off_h = off;
+    off = align256(off + sizeof(double) * (size_t)(o->maxit + 1) * (size_t)o->maxit);
+    ly->off_pad = off;
+    off = align256(off + sizeof(float) * ctg_pad_floats(g->N));
+    ly->off_vn0 = off;
+    off = align256(off + sizeof(float) * round_up((size_t)n, 64));
+    ly->off_vm0 = off;
+    off = align256(off + sizeof(float) * round_up((size_t)m, 64));
+    ly->off_vm1 = off;
+    off = align256(off + sizeof(float) * round_up((size_t)m, 64));
+    ly->off_y = off;
+    off = align256(off + sizeof(double) * (size_t)(o->maxit + 2));
+    ly->off_red = off;
+    const int64_t Lmax = n > m ? n : m;
+    off = align256(off + ctg_red_scratch_bytes(Lmax, o->maxit + 1));
+    ly->total = off;
+    return true;
+}
+
+}  // namespace
+
+struct ctg_ctx {
+    int device = 0;
+    std::vector<GeomEntry> cache;
+    unsigned long long tick = 0;
+    double *pinned = nullptr;     // host staging for Hessenberg columns and scalars
+    size_t pinned_count = 0;
+    // phase tracing: events bracket each phase on the launching stream and
+    // are resolved into per-phase milliseconds once they have completed
+    struct Mark {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+    std::vector<Mark> marks;
+    double ms[4] = {0, 0, 0, 0};
+    long long calls[4] = {0, 0, 0, 0};
+    long long kernels = 0;
+};
+
+namespace {
+
+int fail_cuda(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) return CTG_ERR_OOM;
+    return CTG_ERR_CUDA;
+}
+
+#define CTG_CK(call)                                  \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return fail_cuda(e_);  \
+    } while (0)
+
+constexpr size_t kMaxCachedGeoms = 4;
+
+int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
+    for (auto &e : ctx->cache)
+        if (same_geom(e.g, *g)) {
+            e.last_use = ++ctx->tick;
+            *out = &e;
+            return CTG_OK;
+        }
+    if (ctx->cache.size() >= kMaxCachedGeoms) {
+        // evict the least recently used geometry; its tables may still be
+        // read by queued work, so wait for the device first
+        size_t victim = 0;
+        for (size_t i = 1; i < ctx->cache.size(); ++i)
+            if (ctx->cache[i].last_use < ctx->cache[victim].last_use) victim = i;
+        CTG_CK(cudaDeviceSynchronize());
+        cudaFree(ctx->cache[victim].fwd);
+        cudaFree(ctx->cache[victim].back);
+        cudaFree(ctx->cache[victim].pad);
+        ctx->cache.erase(ctx->cache.begin() + victim);
+    }
+    std::vector<FwdAngle> fw;
+    std::vector<BackAngle> bk;
+    build_tables(g, fw, bk);
+    GeomEntry e;
+    e.g = *g;
+    e.last_use = ++ctx->tick;
+    cudaError_t err = cudaMalloc(&e.fwd, sizeof(FwdAngle) * fw.size());
+    if (err == cudaSuccess) err = cudaMalloc(&e.back, sizeof(BackAngle) * bk.size());
+    if (err == cudaSuccess)
+        err = cudaMemcpy(e.fwd, fw.data(), sizeof(FwdAngle) * fw.size(), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(e.back, bk.data(), sizeof(BackAngle) * bk.size(), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
+        cudaFree(e.fwd);
+        cudaFree(e.back);
+        return fail_cuda(err);
+    }
+    ctx->cache.push_back(e);
+    *out = &ctx->cache.back();
+    return CTG_OK;
+}
+
+cudaEvent_t next_event(ctg_ctx *ctx) {
+    if (ctx->events_used == ctx->events.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ctx->events.push_back(e);
+    }
+    return ctx->events[ctx->events_used++];
+}
+
+// Runs f() (which enqueues `nkern` kernels on st) as one execution of
+// `phase`, bracketed by events when tracing is on.
+template <typename F>
+cudaError_t traced(ctg_ctx *ctx, int phase, int nkern, cudaStream_t st, F f) {
+    ctx->kernels += nkern;
+    ctx->calls[phase] += 1;
+    if (!ctx->timing) return f();
+    cudaEvent_t a = next_event(ctx), b = next_event(ctx);
+    if (a) cudaEventRecord(a, st);
+    cudaError_t e = f();
+    if (b) cudaEventRecord(b, st);
+    if (a && b) ctx->marks.push_back({phase, a, b});
+    return e;
+}
+
+// Waits for the recorded events and folds them into the phase totals.
+int resolve_marks(ctg_ctx *ctx) {
+    for (const auto &mk : ctx->marks) {
+        float t = 0.f;
+        CTG_CK(cudaEventSynchronize(mk.b));
+        CTG_CK(cudaEventElapsedTime(&t, mk.a, mk.b));
+        ctx->ms[mk.phase] += t;
+    }
+    ctx->marks.clear();
+    ctx->events_used = 0;
+    return CTG_OK;
+}
+
+int ensure_pinned(ctg_ctx *ctx, size_t count) {
+    if (ctx->pinned_count >= count) return CTG_OK;
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    ctx->pinned = nullptr;
+    ctx->pinned_count = 0;
+    CTG_CK(cudaMallocHost(&ctx->pinned, sizeof(double) * count));
+    ctx->pinned_count = count;
+    return CTG_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Host Givens state of the Hessenberg least-squares problem
+// min || beta e1 - H_k y ||: rotations (c, s), the rotated right-hand side g
+// and the triangular factor R (column-major, leading dimension kmax).
+struct Givens {
+    int kmax;
+    std::vector<double> c, s, g, R;
+    explicit Givens(int kmax_, double beta)
+        : kmax(kmax_), c(kmax_), s(kmax_), g(kmax_ + 1, 0.0), R((size_t)kmax_ * kmax_, 0.0) {
+        g[0] = beta;
+    }
+    // Add column k (1-based) h[0..k] of H_k; returns |g_{k+1}| = rho_k.
+    double add_column(int k, const double *hin) {
+        std::vector<double> h(hin, hin + k + 1);
+        for (int i = 0; i < k - 1; ++i) {
+            const double t = c[i] * h[i] + s[i] * h[i + 1];
+            h[i + 1] = -s[i] * h[i] + c[i] * h[i + 1];
+            h[i] = t;
+        }
+        const double a = h[k - 1], b = h[k];
+        const double r = std::hypot(a, b);
+        double ck = 1.0, sk = 0.0;
+        if (b != 0.0) {
+            ck = a / r;
+            sk = b / r;
+        }
+        c[k - 1] = ck;
+        s[k - 1] = sk;
+        h[k - 1] = b != 0.0 ? r : a;
+        g[k] = -sk * g[k - 1];
+        g[k - 1] = ck * g[k - 1];
+        for (int i = 0; i < k; ++i) R[(size_t)(k - 1) * kmax + i] = h[i];
+        return std::fabs(g[k]);
+    }
+    // y = R_k^{-1} g_{1:k} (back substitution).
+    void solve(int k, double *y) const {
+        for (int i = k - 1; i >= 0; --i) {
+            double t = g[i];
+            for (int j = i + 1; j < k; ++j) t -= R[(size_t)j * kmax + i] * y[j];
+            const double d = R[(size_t)i * kmax + i];
+            y[i] = d != 0.0 ? t / d : 0.0;
+        }
+    }
+};
+
+struct SolveCtx {
+    ctg_ctx *ctx;
+    const ctg_geom *g;
+    GeomEntry *ge;
+    WsLayout ly;
+    char *ws;
+    RedScratch rs;
+    cudaStream_t st;
+    float *W() const { return reinterpret_cast<float *>(ws + ly.off_w); }
+    float *Wcol(int j) const { return W() + (size_t)j * ly.ld_w; }
+    double *Hcol(int k) const {   // column k (1-based)
+        return reinterpret_cast<double *>(ws + ly.off_h) + (size_t)(k - 1) * (ly.kmax + 1);
+    }
+    float *pad() const { return reinterpret_cast<float *>(ws + ly.off_pad); }
+    float *vn0() const { return reinterpret_cast<float *>(ws + ly.off_vn0); }
+    float *vm0() const { return reinterpret_cast<float *>(ws + ly.off_vm0); }
+    float *vm1() const { return reinterpret_cast<float *>(ws + ly.off_vm1); }
+    double *ydev() const { return reinterpret_cast<double *>(ws + ly.off_y); }
+
+    cudaError_t forward(const float *x, float *b) const {
+        return traced(ctx, 0, 2, st, [&] {
+            cudaError_t e = ctg_launch_pad(x, pad(), g->N, st);
+            if (e != cudaSuccess) return e;
+            return ctg_launch_forward(pad(), g->N, g->n_angles, g->n_det, ge->fwd, b, st);
+        });
+    }
+    cudaError_t back(const float *b, const float *add, float *x) const {
+        return traced(ctx, 1, 1, st, [&] {
+            return ctg_launch_back(b, g->N, g->n_angles, g->n_det, ge->back, add, x, st);
+        });
+    }
+    cudaError_t cgs2(int64_t L, int k, float *q) const {
+        return traced(ctx, 2, k > 0 ? 4 : 2, st, [&] {
+            return ctg_cgs2_step(W(), ly.ld_w, L, k, q, Wcol(k), Hcol(k), rs, st);
+        });
+    }
+    cudaError_t gemv(int64_t L, int k, const float *base, float *out) const {
+        return traced(ctx, 3, 1, st, [&] {
+            return ctg_gemv(W(), ly.ld_w, L, k, ydev(), base, out, st);
+        });
+    }
+    cudaError_t sub_norm2(const float *a, const float *c, float *out, int64_t L, double *res) const {
+        return traced(ctx, 3, 1, st, [&] { return ctg_sub_norm2(a, c, out, L, res, rs, st); });
+    }
+    cudaError_t scale(const float *v, const double *nrm2, float *out, int64_t L) const {
+        return traced(ctx, 3, 1, st, [&] { return ctg_scale(v, nrm2, out, L, st); });
+    }
+    // copy `count` doubles from the device to the pinned area and wait
+    int fetch(const double *src, size_t count, double **host) const {
+        CTG_CK(cudaMemcpyAsync(ctx->pinned, src, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
+        CTG_CK(cudaStreamSynchronize(st));
+        *host = ctx->pinned;
+        return CTG_OK;
+    }
+    int upload_y(const double *y, int k) const {
+        std::memcpy(ctx->pinned, y, sizeof(double) * k);
+        CTG_CK(cudaMemcpyAsync(ydev(), ctx->pinned, sizeof(double) * k, cudaMemcpyHostToDevice, st));
+        return CTG_OK;
+    }
+    // ||b - A x||, using vm1 as scratch
+    int true_resnorm(const float *b, const float *x, double *out) const {
+        CTG_CK(forward(x, vm1()));
+        CTG_CK(sub_norm2(b, vm1(), nullptr, ly.m, rs.scal + 4));
+        double *h;
+        int rc = fetch(rs.scal + 4, 1, &h);
+        if (rc) return rc;
+        *out = std::sqrt(h[0]);
+        return CTG_OK;
+    }
+};
+
+int solve_setup(ctg_ctx *ctx, const ctg_geom *g, int variant, const ctg_opts *o,
+                const float *b, float *x, void *ws, size_t ws_bytes, ctg_info *info,
+                void *stream, SolveCtx *sc, void **owned) {
+    *owned = nullptr;
+    if (!ctx || !b || !x || !info || !layout_of(g, variant, o, &sc->ly)) return CTG_ERR_INVALID_ARG;
+    if (!aligned16(b) || !aligned16(x)) return CTG_ERR_INVALID_ARG;
+    sc->ctx = ctx;
+    sc->g = g;
+    sc->st = static_cast<cudaStream_t>(stream);
+    int rc = get_geom(ctx, g, &sc->ge);
+    if (rc) return rc;
+    rc = ensure_pinned(ctx, (size_t)o->maxit + 16);
+    if (rc) return rc;
+    if (ws == nullptr) {
+        cudaError_t e = cudaMallocAsync(&ws, sc->ly.total, sc->st);
+        if (e != cudaSuccess) return fail_cuda(e);
+        *owned = ws;
+    } else {
+        if (ws_bytes < sc->ly.total) return CTG_ERR_WORKSPACE;
+        if (((uintptr_t)ws & 255u) != 0) return CTG_ERR_INVALID_ARG;
+    }
+    sc->ws = static_cast<char *>(ws);
+    ctg_red_scratch_carve(sc->ws + sc->ly.off_red, sc->ly.n > sc->ly.m ? sc->ly.n : sc->ly.m,
+                          o->maxit + 1, &sc->rs);
+    CTG_CK(cudaMemsetAsync(sc->rs.counter, 0, 4 * sizeof(unsigned), sc->st));
+    CTG_CK(cudaMemsetAsync(sc->pad(), 0, sizeof(float) * ctg_pad_floats(g->N), sc->st));
+    CTG_CK(cudaMemsetAsync(sc->ws + sc->ly.off_h, 0,
+                           sizeof(double) * (size_t)(o->maxit + 1) * o->maxit, sc->st));
+    info->iters = 0;
+    info->stop_reason = CTG_STOP_MAXIT;
+    info->resnorm = 0.0;
+    info->rho = 0.0;
+    return CTG_OK;
+}
+
+int finish(const SolveCtx &sc, void *owned, int rc) {
+    if (owned) {
+        cudaError_t e = cudaFreeAsync(owned, sc.st);
+        if (rc == CTG_OK && e != cudaSuccess) rc = fail_cuda(e);
+        cudaError_t e2 = cudaStreamSynchronize(sc.st);
+        if (rc == CTG_OK && e2 != cudaSuccess) rc = fail_cuda(e2);
+    }
+    return rc;
+}
+
+int copy_x0(const SolveCtx &sc, const float *x0, float *x) {
+    if (x0) CTG_CK(cudaMemcpyAsync(x, x0, sizeof(float) * sc.ly.n, cudaMemcpyDeviceToDevice, sc.st));
+    else CTG_CK(cudaMemsetAsync(x, 0, sizeof(float) * sc.ly.n, sc.st));
+    return CTG_OK;
+}
+
+// AB-GMRES, Sec. 2 left column.
+int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_opts *o,
+           ctg_info *info) {
+    const int64_t m = sc.ly.m;
+    const bool dp = o->noise_norm > 0.0;
+    const double target = dp ? o->tau * o->noise_norm : 0.0;
+    // r0 = b - A x0, unnormalised into w_1's slot; beta = ||r0||
+    if (x0) {
+        CTG_CK(sc.forward(x0, sc.vm0()));
+        CTG_CK(sc.sub_norm2(b, sc.vm0(), sc.Wcol(0), m, sc.rs.scal + 2));
+    } else {
+        CTG_CK(sc.sub_norm2(b, nullptr, sc.Wcol(0), m, sc.rs.scal + 2));
+    }
+    double *hp;
+    int rc = sc.fetch(sc.rs.scal + 2, 1, &hp);
+    if (rc) return rc;
+    const double beta = std::sqrt(hp[0]);
+    if (info->history) info->history[0] = beta;
+    info->rho = beta;
+    info->resnorm = beta;
+    if ((dp && beta <= target) || beta == 0.0) {
+        info->stop_reason = beta == 0.0 && !(dp && beta <= target) ? CTG_STOP_BREAKDOWN : CTG_STOP_DP;
+        return copy_x0(sc, x0, x);
+    }
+    CTG_CK(sc.scale(sc.Wcol(0), sc.rs.scal + 2, sc.Wcol(0), m));
+    Givens gv(o->maxit, beta);
+    int k = 0;
+    for (k = 1; k <= o->maxit; ++k) {
+        CTG_CK(sc.back(sc.Wcol(k - 1), nullptr, sc.vn0()));        // t = B w_k
+        CTG_CK(sc.forward(sc.vn0(), sc.vm0()));                     // q = A t
+        CTG_CK(sc.cgs2(m, k, sc.vm0()));
+        CTG_CK(cudaMemcpyAsync(sc.ctx->pinned, sc.Hcol(k), sizeof(double) * (k + 1),
+                               cudaMemcpyDeviceToHost, sc.st));
+        CTG_CK(cudaMemcpyAsync(sc.ctx->pinned + k + 1, sc.rs.scal, sizeof(double),
+                               cudaMemcpyDeviceToHost, sc.st));
+        CTG_CK(cudaStreamSynchronize(sc.st));
+        const double *h = sc.ctx->pinned;
+        const bool breakdown = h[k] <= kBreakdownRtol * std::sqrt(h[k + 1]);
+        const double rho = gv.add_column(k, h);
+        info->rho = rho;
+        if (info->history) info->history[k] = rho;
+        if (breakdown) {
+            info->stop_reason = CTG_STOP_BREAKDOWN;
+            break;
+        }
+        if (dp && rho <= target) {
+            info->stop_reason = CTG_STOP_DP;
+            break;
+        }
+    }
+    if (k > o->maxit) k = o->maxit;
+    info->iters = k;
+    // x_k = x0 + B (W_k y_k)
+    std::vector<double> y(k);
+    gv.solve(k, y.data());
+    if ((rc = sc.upload_y(y.data(), k))) return rc;
+    CTG_CK(sc.gemv(m, k, nullptr, sc.vm0()));
+    CTG_CK(sc.back(sc.vm0(), x0, x));
+    return sc.true_resnorm(b, x, &info->resnorm);
+}
+
+// BA-GMRES, Sec. 2 right column.
+int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_opts *o,
+           ctg_info *info) {
+    const int64_t n = sc.ly.n, m = sc.ly.m;
+    const bool dp = o->noise_norm > 0.0;
+    const double target = dp ? o->tau * o->noise_norm : 0.0;
+    // r = b - A x0 (m-vector) and its norm; r0 = B r into w_1's slot
+    if (x0) {
+        CTG_CK(sc.forward(x0, sc.vm0()));
+        CTG_CK(sc.sub_norm2(b, sc.vm0(), sc.vm1(), m, sc.rs.scal + 4));
+    } else {
+        CTG_CK(sc.sub_norm2(b, nullptr, sc.vm1(), m, sc.rs.scal + 4));
+    }
+    CTG_CK(sc.back(sc.vm1(), nullptr, sc.Wcol(0)));
+    CTG_CK(sc.sub_norm2(sc.Wcol(0), nullptr, nullptr, n, sc.rs.scal + 2));
+    double *hp;
+    int rc = sc.fetch(sc.rs.scal + 2, 3, &hp);
+    if (rc) return rc;
+    const double beta = std::sqrt(hp[0]), res0 = std::sqrt(hp[2]);
+    if (info->history) info->history[0] = dp ? res0 : beta;
+    info->rho = beta;
+    info->resnorm = res0;
+    if ((dp && res0 <= target) || beta == 0.0) {
+        info->stop_reason = beta == 0.0 && !(dp && res0 <= target) ? CTG_STOP_BREAKDOWN : CTG_STOP_DP;
+        return copy_x0(sc, x0, x);
+    }
+    CTG_CK(sc.scale(sc.Wcol(0), sc.rs.scal + 2, sc.Wcol(0), n));
+    Givens gv(o->maxit, beta);
+    std::vector<double> y(o->maxit);
+    int k = 0;
+    bool have_x = false;
+    for (k = 1; k <= o->maxit; ++k) {
+        CTG_CK(sc.forward(sc.Wcol(k - 1), sc.vm0()));              // t = A w_k
+        CTG_CK(sc.back(sc.vm0(), nullptr, sc.vn0()));               // q = B t
+        CTG_CK(sc.cgs2(n, k, sc.vn0()));
+        CTG_CK(cudaMemcpyAsync(sc.ctx->pinned, sc.Hcol(k), sizeof(double) * (k + 1),
+                               cudaMemcpyDeviceToHost, sc.st));
+        CTG_CK(cudaMemcpyAsync(sc.ctx->pinned + k + 1, sc.rs.scal, sizeof(double),
+                               cudaMemcpyDeviceToHost, sc.st));
+        CTG_CK(cudaStreamSynchronize(sc.st));
+        const double *h = sc.ctx->pinned;
+        const bool breakdown = h[k] <= kBreakdownRtol * std::sqrt(h[k + 1]);
+        const double rho = gv.add_column(k, h);
+        info->rho = rho;
+        const bool last = breakdown || k == o->maxit;
+        have_x = false;
+        if (dp || last) {
+            // x_k = x0 + W_k y_k and the true residual ||b - A x_k||
+            gv.solve(k, y.data());
+            if ((rc = sc.upload_y(y.data(), k))) return rc;
+            CTG_CK(sc.gemv(n, k, x0, x));
+            if ((rc = sc.true_resnorm(b, x, &info->resnorm))) return rc;
+            have_x = true;
+        }
+        if (info->history) info->history[k] = dp ? info->resnorm : rho;
+        if (breakdown) {
+            info->stop_reason = CTG_STOP_BREAKDOWN;
+            break;
+        }
+        if (dp && info->resnorm <= target) {
+            info->stop_reason = CTG_STOP_DP;
+            break;
+        }
+    }
+    if (k > o->maxit) k = o->maxit;
+    info->iters = k;
+    if (!have_x) {
+        gv.solve(k, y.data());
+        if ((rc = sc.upload_y(y.data(), k))) return rc;
+        CTG_CK(sc.gemv(n, k, x0, x));
+        return sc.true_resnorm(b, x, &info->resnorm);
+    }
+    return CTG_OK;
+}
+
+int solve(int variant, ctg_ctx *ctx, const ctg_geom *g, const float *b, const float *x0,
+          float *x, const ctg_opts *o, void *ws, size_t ws_bytes, ctg_info *info,
+          void *stream) {
+    if (x0 && !aligned16(x0)) return CTG_ERR_INVALID_ARG;
+    SolveCtx sc;
+    void *owned = nullptr;
+    int rc = solve_setup(ctx, g, variant, o, b, x, ws, ws_bytes, info, stream, &sc, &owned);
+    if (rc) {
+        if (owned) cudaFreeAsync(owned, sc.st);
+        return rc;
+    }
+    rc = variant == CTG_AB ? run_ab(sc, b, x0, x, o, info) : run_ba(sc, b, x0, x, o, info);
+    if (rc == CTG_OK) {
+        cudaError_t e = cudaStreamSynchronize(sc.st);
+        if (e != cudaSuccess) rc = fail_cuda(e);
+    }
+    if (rc == CTG_OK) rc = resolve_marks(ctx);
+    return finish(sc, owned, rc);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ctg_create(ctg_ctx **out) {
+    if (!out) return CTG_ERR_INVALID_ARG;
+    ctg_ctx *c = new (std::nothrow) ctg_ctx();
+    if (!c) return CTG_ERR_OOM;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return CTG_ERR_CUDA;
+    }
+    *out = c;
+    return CTG_OK;
+}
+
+void ctg_destroy(ctg_ctx *ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    for (auto ev : ctx->events) cudaEventDestroy(ev);
+    for (auto &e : ctx->cache) {
+        cudaFree(e.fwd);
+        cudaFree(e.back);
+        cudaFree(e.pad);
+    }
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    delete ctx;
+}
+
+int ctg_project(ctg_ctx *ctx, const ctg_geom *g, const float *x_dev, float *b_dev, void *stream) {
+    if (!ctx || !geom_valid(g) || !x_dev || !b_dev) return CTG_ERR_INVALID_ARG;
+    GeomEntry *ge;
+    int rc = get_geom(ctx, g, &ge);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!ge->pad) {
+        const size_t bytes = sizeof(float) * ctg_pad_floats(g->N);
+        CTG_CK(cudaMalloc(&ge->pad, bytes));
+        CTG_CK(cudaMemset(ge->pad, 0, bytes));
+    }
+    CTG_CK(traced(ctx, 0, 2, st, [&] {
+        cudaError_t e = ctg_launch_pad(x_dev, ge->pad, g->N, st);
+        if (e != cudaSuccess) return e;
+        return ctg_launch_forward(ge->pad, g->N, g->n_angles, g->n_det, ge->fwd, b_dev, st);
+    }));
+    return CTG_OK;
+}
+
+int ctg_backproject(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, float *x_dev, void *stream) {
+    if (!ctx || !geom_valid(g) || !b_dev || !x_dev) return CTG_ERR_INVALID_ARG;
+    GeomEntry *ge;
+    int rc = get_geom(ctx, g, &ge);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CTG_CK(traced(ctx, 1, 1, st, [&] {
+        return ctg_launch_back(b_dev, g->N, g->n_angles, g->n_det, ge->back, nullptr, x_dev, st);
+    }));
+    return CTG_OK;
+}
+
+size_t ctg_workspace_bytes(const ctg_geom *g, int variant, const ctg_opts *o) {
+    WsLayout ly;
+    return layout_of(g, variant, o, &ly) ? ly.total : 0;
+}
+
+int ctg_workspace_layout(const ctg_geom *g, int variant, const ctg_opts *o, ctg_layout *out) {
+    WsLayout ly;
+    if (!out || !layout_of(g, variant, o, &ly)) return CTG_ERR_INVALID_ARG;
+    out->off_w = ly.off_w;
+    out->ld_w = ly.ld_w;
+    out->off_h = ly.off_h;
+    out->total_bytes = ly.total;
+    return CTG_OK;
+}
+
+int ctg_ab_gmres(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, const float *x0_dev,
+                 float *x_dev, const ctg_opts *o, void *workspace_dev, size_t workspace_bytes,
+                 ctg_info *info, void *stream) {
+    return solve(CTG_AB, ctx, g, b_dev, x0_dev, x_dev, o, workspace_dev, workspace_bytes, info, stream);
+}
+
+int ctg_ba_gmres(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, const float *x0_dev,
+                 float *x_dev, const ctg_opts *o, void *workspace_dev, size_t workspace_bytes,
+                 ctg_info *info, void *stream) {
+    return solve(CTG_BA, ctx, g, b_dev, x0_dev, x_dev, o, workspace_dev, workspace_bytes, info, stream);
+}
+
+size_t ctg_cgs2_scratch_bytes(int64_t L, int32_t k) {
+    if (L < 1 || k < 0 || k > kMaxIt) return 0;
+    return ctg_red_scratch_bytes(L, k + 1);
+}
+
+int ctg_cgs2(const float *W_dev, int64_t ld_w, int64_t L, int32_t k, float *q_dev,
+             float *w_out_dev, double *h_out_dev, void *scratch_dev, size_t scratch_bytes,
+             void *stream) {
+    if (L < 1 || k < 0 || k > kMaxIt || ld_w < L || (ld_w & 3) != 0) return CTG_ERR_INVALID_ARG;
+    if ((k > 0 && !W_dev) || !q_dev || !w_out_dev || !h_out_dev || !scratch_dev) return CTG_ERR_INVALID_ARG;
+    if ((k > 0 && !aligned16(W_dev)) || !aligned16(q_dev) || !aligned16(w_out_dev)) return CTG_ERR_INVALID_ARG;
+    if (((uintptr_t)scratch_dev & 255u) != 0) return CTG_ERR_INVALID_ARG;
+    if (scratch_bytes < ctg_cgs2_scratch_bytes(L, k)) return CTG_ERR_WORKSPACE;
+    RedScratch rs;
+    ctg_red_scratch_carve(scratch_dev, L, k + 1, &rs);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CTG_CK(cudaMemsetAsync(rs.counter, 0, 4 * sizeof(unsigned), st));
+    CTG_CK(ctg_cgs2_step(W_dev, ld_w, L, k, q_dev, w_out_dev, h_out_dev, rs, st));
+    return CTG_OK;
+}
+
+int ctg_set_timing(ctg_ctx *ctx, int enable) {
+    if (!ctx) return CTG_ERR_INVALID_ARG;
+    int rc = resolve_marks(ctx);
+    ctx->timing = enable != 0;
+    return rc;
+}
+
+int ctg_get_timing(ctg_ctx *ctx, ctg_timing *out, int reset) {
+    if (!ctx || !out) return CTG_ERR_INVALID_ARG;
+    int rc = resolve_marks(ctx);
+    for (int p = 0; p < 4; ++p) {
+        out->ms[p] = ctx->ms[p];
+        out->calls[p] = ctx->calls[p];
+    }
+    out->kernels = ctx->kernels;
+    if (reset) {
+        for (int p = 0; p < 4; ++p) {
+            ctx->ms[p] = 0.0;
+            ctx->calls[p] = 0;
+        }
+        ctx->kernels = 0;
+    }
+    return rc;
+}
+
+const char *ctg_status_string(int status) {
+    switch (status) {
+        case CTG_OK: return "ok";
+        case CTG_ERR_INVALID_ARG: return "invalid argument";
+        case CTG_ERR_OOM: return "out of device memory";
+        case CTG_ERR_CUDA: return "CUDA runtime error";
+        case CTG_ERR_TIMEOUT: return "device-side wait timed out";
+        case CTG_ERR_WORKSPACE: return "workspace too small";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,388 @@
+// Arnoldi orthogonalisation of the Krylov basis (paper Sec. 2, algorithm
+// box: h_{i,k} = q_k^T w_i, q_k -= h_{i,k} w_i, h_{k+1,k} = ||q_k||,
+// w_{k+1} = q_k / h_{k+1,k}), done as classical Gram-Schmidt applied twice
+// (CGS2), which equals the paper's MGS loop in exact arithmetic but needs
+// three sweeps over W instead of k dependent ones:
+//   pass 1  h1 = W^T q,                ||q||^2      (one read of W)
+//   pass 2  q -= W h1,  h2 = W^T q                  (two reads of W)
+//   pass 3  q -= W h2,  ||q||^2                     (one read of W)
+//   scale   w_{k+1} = q / ||q||,  h_{1:k,k} = h1 + h2,  h_{k+1,k} = ||q||
+// Each pass is one launch: every block reduces its slice with warp shuffles
+// into per-block partials, and the last block to finish (atomic ticket, no
+// waiting) sums the partials in a fixed order in FP64, so results are
+// deterministic run to run.
+#include "ctg_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256, kWarps = kThreads / 32;
+constexpr int kTargetGrid = 4 * 152;   // 4 blocks on each of GB300's 152 SMs
+
+__device__ __forceinline__ float4 ld4(const float *p, int64_t g, int64_t L) {
+    const int64_t i = 4 * g;
+    if (i + 3 < L) return __ldg(reinterpret_cast<const float4 *>(p + i));
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < L) v.x = p[i];
+    if (i + 1 < L) v.y = p[i + 1];
+    if (i + 2 < L) v.z = p[i + 2];
+    return v;
+}
+
+__device__ __forceinline__ float4 ld4_rw(const float *p, int64_t g, int64_t L) {
+    const int64_t i = 4 * g;
+    if (i + 3 < L) return *reinterpret_cast<const float4 *>(p + i);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < L) v.x = p[i];
+    if (i + 1 < L) v.y = p[i + 1];
+    if (i + 2 < L) v.z = p[i + 2];
+    return v;
+}
+
+__device__ __forceinline__ void st4(float *p, int64_t g, int64_t L, float4 v) {
+    const int64_t i = 4 * g;
+    if (i + 3 < L) {
+        *reinterpret_cast<float4 *>(p + i) = v;
+        return;
+    }
+    if (i < L) p[i] = v.x;
+    if (i + 1 < L) p[i + 1] = v.y;
+    if (i + 2 < L) p[i + 2] = v.z;
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+
+__device__ __forceinline__ float warp_sum(float s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+__device__ __forceinline__ double warp_sum_d(double s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Writes this block's nred partial sums, then lets the last block sum all
+// blocks' partials (fixed order, FP64) into red_out[0..nred-1].
+__device__ void block_reduce_finish(float *s_w, int nred, float *__restrict__ partials,
+                                    unsigned *__restrict__ counter,
+                                    double *__restrict__ red_out) {
+    __shared__ bool s_last;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = gridDim.x;
+    __syncthreads();
+    for (int j = tid; j < nred; j += kThreads) {
+        float s = 0.f;
+        for (int w = 0; w < kWarps; ++w) s += s_w[w * nred + j];
+        partials[(size_t)j * G + blockIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(counter, 1u) == (unsigned)(G - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int j = warp; j < nred; j += kWarps) {
+        double s = 0.0;
+        for (int bb = lane; bb < G; bb += 32) s += (double)__ldcg(partials + (size_t)j * G + bb);
+        s = warp_sum_d(s);
+        if (lane == 0) red_out[j] = s;
+    }
+    if (tid == 0) *counter = 0u;
+}
+
+// One CGS2 pass over a slice of E float4 groups per thread.
+//   UPDATE: q -= sum_j coef_j W_j (coef: k doubles)
+//   DOTS:   red_out[j] = W_j^T q (after the update)      j < k
+//   NORM:   red_out[DOTS ? k : 0] = q^T q (after the update)
+template <int E, bool UPDATE, bool DOTS, bool NORM>
+__global__ void __launch_bounds__(kThreads)
+cgs_pass_kernel(const float *__restrict__ W, int64_t ldw, int k, float *__restrict__ q,
+                int64_t L, const double *__restrict__ coef, float *__restrict__ partials,
+                unsigned *__restrict__ counter, double *__restrict__ red_out) {
+    extern __shared__ float smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nred = (DOTS ? k : 0) + (NORM ? 1 : 0);
+    float *s_coef = smem;                       // k floats (UPDATE)
+    float *s_w = smem + (UPDATE ? k : 0);       // kWarps * nred floats
+    if (UPDATE)
+        for (int j = tid; j < k; j += kThreads) s_coef[j] = (float)coef[j];
+    const int64_t g0 = (int64_t)blockIdx.x * kThreads * E + tid;
+    float4 qv[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) qv[e] = ld4_rw(q, g0 + (int64_t)e * kThreads, L);
+    if (UPDATE) {
+        __syncthreads();
+#pragma unroll 4
+        for (int j = 0; j < k; ++j) {
+            const float c = s_coef[j];
+            const float *Wj = W + (size_t)j * ldw;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const float4 w = ld4(Wj, g0 + (int64_t)e * kThreads, L);
+                qv[e].x = fmaf(-c, w.x, qv[e].x);
+                qv[e].y = fmaf(-c, w.y, qv[e].y);
+                qv[e].z = fmaf(-c, w.z, qv[e].z);
+                qv[e].w = fmaf(-c, w.w, qv[e].w);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) st4(q, g0 + (int64_t)e * kThreads, L, qv[e]);
+    }
+    if (DOTS) {
+#pragma unroll 4
+        for (int j = 0; j < k; ++j) {
+            const float *Wj = W + (size_t)j * ldw;
+            float s = 0.f;
+#pragma unroll
+            for (int e = 0; e < E; ++e) s += dot4(ld4(Wj, g0 + (int64_t)e * kThreads, L), qv[e]);
+            s = warp_sum(s);
+            if (lane == 0) s_w[warp * nred + j] = s;
+        }
+    }
+    if (NORM) {
+        float s = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) s += dot4(qv[e], qv[e]);
+        s = warp_sum(s);
+        if (lane == 0) s_w[warp * nred + (DOTS ? k : 0)] = s;
+    }
+    block_reduce_finish(s_w, nred, partials, counter, red_out);
+}
+
+// w_out = q / sqrt(nrm2) (0 if nrm2 == 0); block 0 also assembles the
+// Hessenberg column h_out[0..k-1] = h1 + h2, h_out[k] = sqrt(nrm2).
+// q and w_out may be the same vector.
+__global__ void scale_kernel(const float *q, const double *__restrict__ nrm2,
+                             float *w_out, int64_t L, int k,
+                             const double *__restrict__ h1, const double *__restrict__ h2,
+                             double *__restrict__ h_out) {
+    const double nn = *nrm2;
+    const float inv = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.0f;
+    const int64_t L4 = (L + 3) / 4;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L4;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = ld4_rw(q, g, L);
+        v.x *= inv; v.y *= inv; v.z *= inv; v.w *= inv;
+        st4(w_out, g, L, v);
+    }
+    if (h_out != nullptr && blockIdx.x == 0) {
+        for (int j = threadIdx.x; j < k; j += blockDim.x) h_out[j] = h1[j] + h2[j];
+        if (threadIdx.x == 0) h_out[k] = sqrt(nn);
+    }
+}
+
+// out = base + sum_j y_j W_j.
+template <int E>
+__global__ void __launch_bounds__(kThreads)
+gemv_kernel(const float *__restrict__ W, int64_t ldw, int k, const double *__restrict__ y,
+            const float *__restrict__ base, float *__restrict__ out, int64_t L) {
+    extern __shared__ float s_y[];
+    for (int j = threadIdx.x; j < k; j += kThreads) s_y[j] = (float)y[j];
+    __syncthreads();
+    const int64_t g0 = (int64_t)blockIdx.x * kThreads * E + threadIdx.x;
+    float4 acc[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        acc[e] = base ? ld4(base, g0 + (int64_t)e * kThreads, L) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+    for (int j = 0; j < k; ++j) {
+        const float c = s_y[j];
+        const float *Wj = W + (size_t)j * ldw;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float4 w = ld4(Wj, g0 + (int64_t)e * kThreads, L);
+            acc[e].x = fmaf(c, w.x, acc[e].x);
+            acc[e].y = fmaf(c, w.y, acc[e].y);
+            acc[e].z = fmaf(c, w.z, acc[e].z);
+            acc[e].w = fmaf(c, w.w, acc[e].w);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) st4(out, g0 + (int64_t)e * kThreads, L, acc[e]);
+}
+
+// out = a - c (or a), res = ||out||^2; out may be the same vector as a or c.
+template <int E>
+__global__ void __launch_bounds__(kThreads)
+sub_norm2_kernel(const float *a, const float *c, float *out, int64_t L,
+                 float *__restrict__ partials,
+                 unsigned *__restrict__ counter, double *__restrict__ res) {
+    __shared__ float s_w[kWarps];
+    const int tid = threadIdx.x;
+    const int64_t g0 = (int64_t)blockIdx.x * kThreads * E + tid;
+    float s = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int64_t g = g0 + (int64_t)e * kThreads;
+        float4 v = ld4_rw(a, g, L);
+        if (c) {
+            const float4 w = ld4_rw(c, g, L);
+            v.x -= w.x; v.y -= w.y; v.z -= w.z; v.w -= w.w;
+        }
+        if (out) st4(out, g, L, v);
+        s += dot4(v, v);
+    }
+    s = warp_sum(s);
+    if ((tid & 31) == 0) s_w[tid >> 5] = s;
+    block_reduce_finish(s_w, 1, partials, counter, res);
+}
+
+template <typename K>
+cudaError_t ensure_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <bool UPDATE, bool DOTS, bool NORM>
+cudaError_t launch_pass(const float *W, int64_t ldw, int k, float *q, int64_t L,
+                        const double *coef, const RedScratch &rs, double *red_out,
+                        cudaStream_t st) {
+    int E;
+    const int G = ctg_red_grid(L, &E);
+    const int nred = (DOTS ? k : 0) + (NORM ? 1 : 0);
+    const size_t smem = sizeof(float) * ((UPDATE ? k : 0) + (size_t)kWarps * nred);
+    cudaError_t err = cudaSuccess;
+#define CTG_PASS_CASE(EE)                                                            \
+    case EE: {                                                                       \
+        auto kern = cgs_pass_kernel<EE, UPDATE, DOTS, NORM>;                         \
+        if ((err = ensure_smem(kern, smem)) != cudaSuccess) return err;              \
+        kern<<<G, kThreads, smem, st>>>(W, ldw, k, q, L, coef, rs.partials, rs.counter, \
+                                        red_out);                                    \
+        break;                                                                       \
+    }
+    switch (E) {
+        CTG_PASS_CASE(1)
+        CTG_PASS_CASE(2)
+        CTG_PASS_CASE(4)
+        CTG_PASS_CASE(8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CTG_PASS_CASE
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int ctg_red_grid(int64_t L, int *E_out) {
+    const int64_t L4 = (L + 3) / 4;
+    int E = 1;
+    while (E < 8 && (L4 + (int64_t)kThreads * E - 1) / ((int64_t)kThreads * E) > kTargetGrid) E *= 2;
+    int64_t G = (L4 + (int64_t)kThreads * E - 1) / ((int64_t)kThreads * E);
+    if (G < 1) G = 1;
+    *E_out = E;
+    return (int)G;
+}
+
+static int red_grid_max(int64_t L) {
+    int E;
+    const int G = ctg_red_grid(L, &E);
+    return G > kTargetGrid ? G : kTargetGrid;
+}
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t ctg_red_scratch_bytes(int64_t L, int kmax) {
+    const size_t G = (size_t)red_grid_max(L);
+    return align256(sizeof(float) * (size_t)(kmax + 2) * G) +
+           2 * align256(sizeof(double) * (size_t)(kmax + 2)) + align256(sizeof(double) * 8) +
+           align256(sizeof(unsigned) * 4);
+}
+
+void ctg_red_scratch_carve(void *base, int64_t L, int kmax, RedScratch *rs) {
+    char *p = static_cast<char *>(base);
+    const size_t G = (size_t)red_grid_max(L);
+    rs->partials = reinterpret_cast<float *>(p);
+    p += align256(sizeof(float) * (size_t)(kmax + 2) * G);
+    rs->h1 = reinterpret_cast<double *>(p);
+    p += align256(sizeof(double) * (size_t)(kmax + 2));
+    rs->h2 = reinterpret_cast<double *>(p);
+    p += align256(sizeof(double) * (size_t)(kmax + 2));
+    rs->scal = reinterpret_cast<double *>(p);
+    p += align256(sizeof(double) * 8);
+    rs->counter = reinterpret_cast<unsigned *>(p);
+    rs->grid = (int)G;
+    ctg_red_grid(L, &rs->E);
+}
+
+cudaError_t ctg_cgs2_step(const float *W, int64_t ldw, int64_t L, int k, float *q,
+                          float *w_out, double *h_out, const RedScratch &rs,
+                          cudaStream_t st) {
+    cudaError_t err;
+    // pass 1: h1 = W^T q and ||q_pre||^2 (h1[k]); keep the latter in scal[0]
+    if ((err = launch_pass<false, true, true>(W, ldw, k, q, L, nullptr, rs, rs.h1, st)) != cudaSuccess)
+        return err;
+    if ((err = cudaMemcpyAsync(rs.scal, rs.h1 + k, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return err;
+    if (k > 0) {
+        // pass 2: q -= W h1; h2 = W^T q
+        if ((err = launch_pass<true, true, false>(W, ldw, k, q, L, rs.h1, rs, rs.h2, st)) != cudaSuccess)
+            return err;
+        // pass 3: q -= W h2; ||q||^2 -> scal[1]
+        if ((err = launch_pass<true, false, true>(W, ldw, k, q, L, rs.h2, rs, rs.scal + 1, st)) != cudaSuccess)
+            return err;
+    } else {
+        if ((err = cudaMemcpyAsync(rs.scal + 1, rs.scal, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return err;
+    }
+    const int64_t L4 = (L + 3) / 4;
+    int blocks = (int)((L4 + 255) / 256);
+    if (blocks > 4 * kTargetGrid) blocks = 4 * kTargetGrid;
+    if (blocks < 1) blocks = 1;
+    scale_kernel<<<blocks, 256, 0, st>>>(q, rs.scal + 1, w_out, L, k, rs.h1, rs.h2, h_out);
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_gemv(const float *W, int64_t ldw, int64_t L, int k, const double *y,
+                     const float *base, float *out, cudaStream_t st) {
+    int E;
+    const int G = ctg_red_grid(L, &E);
+    const size_t smem = sizeof(float) * (size_t)(k > 0 ? k : 1);
+    cudaError_t err = cudaSuccess;
+    switch (E) {
+#define CTG_GEMV_CASE(EE)                                                          \
+    case EE:                                                                       \
+        if ((err = ensure_smem(gemv_kernel<EE>, smem)) != cudaSuccess) return err; \
+        gemv_kernel<EE><<<G, kThreads, smem, st>>>(W, ldw, k, y, base, out, L);    \
+        break;
+        CTG_GEMV_CASE(1)
+        CTG_GEMV_CASE(2)
+        CTG_GEMV_CASE(4)
+        CTG_GEMV_CASE(8)
+#undef CTG_GEMV_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_sub_norm2(const float *a, const float *c, float *out, int64_t L,
+                          double *res, const RedScratch &rs, cudaStream_t st) {
+    int E;
+    const int G = ctg_red_grid(L, &E);
+    switch (E) {
+#define CTG_SN_CASE(EE)                                                                        \
+    case EE:                                                                                   \
+        sub_norm2_kernel<EE><<<G, kThreads, 0, st>>>(a, c, out, L, rs.partials, rs.counter, res); \
+        break;
+        CTG_SN_CASE(1)
+        CTG_SN_CASE(2)
+        CTG_SN_CASE(4)
+        CTG_SN_CASE(8)
+#undef CTG_SN_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_scale(const float *v, const double *nrm2, float *out, int64_t L,
+                      cudaStream_t st) {
+    const int64_t L4 = (L + 3) / 4;
+    int blocks = (int)((L4 + 255) / 256);
+    if (blocks > 4 * kTargetGrid) blocks = 4 * kTargetGrid;
+    if (blocks < 1) blocks = 1;
+    scale_kernel<<<blocks, 256, 0, st>>>(v, nrm2, out, L, 0, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}

@@ -1,0 +1,80 @@
+// Internal declarations shared by the CUDA translation units of libctgmres.
+//
+// Positions along a ray or across the detector are carried in signed 24.40
+// fixed point (int64): integer steps are exact, so the interpolation index
+// and weight stay accurate to ~1e-7 pixel at every image size without FP64
+// arithmetic on the device (FP32 alone loses ~1e-4 pixel at N = 2048).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ctgmres.h"
+
+#define CTG_FX_BITS 40
+
+// Forward (Joseph) parameters of one angle.  With (c, s) = (cos, sin) for a
+// row-driven ray and (sin, cos) for a column-driven one, the interpolation
+// position of ray d at walk step t (row or column index) is
+//   u(d, t) = Q + d * P + t * D,  P = ds / c,  Q = (h s - hd ds) / c + h,
+//   D = -s / c,  h = (N-1)/2,  hd = (n_det-1)/2,
+// and the ray sum is scaled by 1/|c|.
+struct FwdAngle {
+    long long P, Q, D;     // fixed point
+    float pf, qf, df;      // the same in float, for the walk-range estimate
+    float scale;           // 1 / |c|
+    int row_driven;        // 1: walk rows of x; 0: walk rows of x^T
+    int pad_;
+};
+
+// Back-projection parameters of one angle: the detector position of pixel
+// (i, j) is u(i, j) = C + j * COS + i * SIN with COS = cos/ds, SIN = sin/ds,
+// C = hd - h (cos + sin) / ds.
+struct BackAngle {
+    long long C, COS, SIN; // fixed point
+    float cf, sf;          // COS, SIN in float (tile-local offsets)
+};
+
+// Padded image layout used by the forward projector: two copies of the
+// image, x and x^T, each N rows of stride N + 4 with two zero columns on
+// either side, so that any clamped tap index reads an exact zero.
+__host__ __device__ static inline size_t ctg_pad_stride(int N) { return (size_t)N + 4; }
+__host__ __device__ static inline size_t ctg_pad_floats(int N) { return 2 * (size_t)N * ctg_pad_stride(N); }
+
+// ---- projector launchers (projectors.cu) --------------------------------
+cudaError_t ctg_launch_pad(const float *x, float *pad, int N, cudaStream_t st);
+cudaError_t ctg_launch_forward(const float *pad, int N, int n_angles, int n_det,
+                               const FwdAngle *tab, float *b, cudaStream_t st);
+// x = B b (+ add, if add != NULL)
+cudaError_t ctg_launch_back(const float *b, int N, int n_angles, int n_det,
+                            const BackAngle *tab, const float *add, float *x,
+                            cudaStream_t st);
+
+// ---- Krylov kernels (arnoldi.cu) -----------------------------------------
+// Reduction scratch for one vector length L and up to kmax coefficients.
+struct RedScratch {
+    float *partials;       // (kmax + 2) * grid floats
+    double *h1, *h2;       // kmax + 2 doubles each
+    double *scal;          // 8 doubles: [0] = ||q_pre||^2, [1] = ||q||^2, ...
+    unsigned int *counter; // 4 counters, zero between launches
+    int grid;              // blocks of every reduction pass for this L
+    int E;                 // float4 groups per thread
+};
+int ctg_red_grid(int64_t L, int *E_out);
+size_t ctg_red_scratch_bytes(int64_t L, int kmax);
+void ctg_red_scratch_carve(void *base, int64_t L, int kmax, RedScratch *rs);
+
+// One CGS2 Arnoldi step: orthogonalise q (length L) against k vectors of W
+// (stride ldw), h_out[0..k-1] = h1 + h2, h_out[k] = ||q||, and write
+// w_out = q / ||q|| when ||q|| > 0.  Also leaves ||q_pre||^2 in rs.scal[0].
+cudaError_t ctg_cgs2_step(const float *W, int64_t ldw, int64_t L, int k, float *q,
+                          float *w_out, double *h_out, const RedScratch &rs,
+                          cudaStream_t st);
+// out = base + sum_j y_j W_j (base may be NULL); y: k doubles (device).
+cudaError_t ctg_gemv(const float *W, int64_t ldw, int64_t L, int k, const double *y,
+                     const float *base, float *out, cudaStream_t st);
+// out = a - c (c may be NULL -> out = a) and *res = ||a - c||^2 (double, device).
+cudaError_t ctg_sub_norm2(const float *a, const float *c, float *out, int64_t L,
+                          double *res, const RedScratch &rs, cudaStream_t st);
+// out = v / sqrt(*nrm2) (nrm2 on device; out = 0 when nrm2 == 0).
+cudaError_t ctg_scale(const float *v, const double *nrm2, float *out, int64_t L,
+                      cudaStream_t st);

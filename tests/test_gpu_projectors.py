@@ -1,0 +1,106 @@
+"""Parity of the CUDA projectors with the FP64 oracle (relative 2-norm
+<= 1e-5, the FP32 projection tolerance), on seeded phantoms and random
+vectors, over small ragged geometries and the full workload sizes."""
+import numpy as np
+import pytest
+
+from paper_2110_01481_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+GEOMS = [
+    # N, n_angles, n_det, start, range, det_spacing
+    (64, 90, 91, 0, 180, 1.0),        # 64^2 modified Shepp-Logan workload
+    (33, 17, 50, 0, 180, 1.0),        # ragged tiles, odd N
+    (48, 30, 68, 0, 120, 1.0),        # limited angle [0, 120)
+    (40, 20, 80, 10, 180, 0.75),      # start offset, finer detector pitch
+    (64, 16, 40, 0, 180, 1.0),        # detector narrower than the image
+    (37, 45, 53, 0, 360, 1.3),        # full turn, coarse pitch
+    (1, 1, 1, 0, 180, 1.0),           # degenerate one-pixel, one-ray case
+]
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2110_01481_gb300 as P
+    return P
+
+
+def _pair(P, O, N, Na, Nd, S, R, ds):
+    return (P.Geometry(N, Na, Nd, S, R, ds), O.Geometry(N, Na, Nd, S, R, ds))
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.mark.parametrize("geom", GEOMS)
+def test_forward_parity(P, oracle_mod, geom):
+    import torch
+    g, og = _pair(P, oracle_mod, *geom)
+    N = geom[0]
+    for x in (I.random_ellipses(N, 3), np.random.default_rng(1).uniform(-1, 1, (N, N))):
+        xt = torch.tensor(x.ravel(), dtype=torch.float32, device="cuda")
+        got = P.project(g, xt).double().cpu().numpy()
+        ref = oracle_mod.forward(og, x.astype(np.float32).astype(np.float64))
+        assert _rel(got, ref) <= TOL
+        assert np.abs(got - ref).max() <= TOL * max(np.abs(ref).max(), 1e-30) * 10
+
+
+@pytest.mark.parametrize("geom", GEOMS)
+def test_back_parity(P, oracle_mod, geom):
+    import torch
+    g, og = _pair(P, oracle_mod, *geom)
+    rng = np.random.default_rng(2)
+    for b in (rng.uniform(0, 1, g.m), rng.standard_normal(g.m)):
+        bt = torch.tensor(b, dtype=torch.float32, device="cuda")
+        got = P.backproject(g, bt).double().cpu().numpy()
+        ref = oracle_mod.backproject(og, b.astype(np.float32).astype(np.float64))
+        assert _rel(got, ref) <= TOL
+        assert np.abs(got - ref).max() <= TOL * max(np.abs(ref).max(), 1e-30) * 10
+
+
+def test_back_of_ones_is_angle_count(P):
+    """B 1 = N_a exactly when every pixel centre lies inside the detector."""
+    import torch
+    g = P.Geometry(96, 45, I.detector_count(96))
+    x = P.backproject(g, torch.ones(g.m, device="cuda")).cpu().numpy()
+    np.testing.assert_allclose(x, 45.0, rtol=2e-7)
+
+
+@pytest.mark.parametrize("N,Na", [(512, 720), (2048, 1800)])
+def test_full_size_parity(P, oracle_mod, N, Na):
+    """512^2 x 720 angles x 725 bins and 2048^2 x 1800 x 2897, in the launch
+    configuration the solvers and the benchmark use."""
+    import torch
+    Nd = I.detector_count(N)
+    g, og = P.Geometry(N, Na, Nd), oracle_mod.Geometry(N, Na, Nd)
+    x = I.random_ellipses(N, 2000 + N).astype(np.float32)
+    xt = torch.tensor(x.ravel(), device="cuda")
+    got = P.project(g, xt).double().cpu().numpy()
+    ref = oracle_mod.forward(og, x.astype(np.float64))
+    assert _rel(got, ref) <= TOL
+    bt = torch.tensor(ref, dtype=torch.float32, device="cuda")
+    gotb = P.backproject(g, bt).double().cpu().numpy()
+    refb = oracle_mod.backproject(og, ref.astype(np.float32).astype(np.float64))
+    assert _rel(gotb, refb) <= TOL
+
+
+def test_rejects_bad_arguments(P):
+    import torch
+    from paper_2110_01481_gb300 import _native as nat
+    g = P.Geometry(16, 8, 23)
+    with pytest.raises(ValueError):
+        P.project(g, torch.zeros(10, device="cuda"))
+    with pytest.raises(nat.CtgError):
+        P.project(P.Geometry(16, 8, 23, angle_start_deg=0.5), torch.zeros(256, device="cuda"))
+    with pytest.raises(nat.CtgError):
+        P.backproject(P.Geometry(0, 8, 23), torch.zeros(184, device="cuda"),
+                      out=torch.zeros(0, device="cuda"))
