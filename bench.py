@@ -1,0 +1,347 @@
+"""Benchmark: AB-GMRES + BA-GMRES iterations/s on one GB300 (or N replicas).
+
+One step = one AB-GMRES and one BA-GMRES solve (paper Sec. 2) of the 2D
+parallel-beam workload: a 512 x 512 seeded 20-ellipse phantom, 720 angles
+over [0, 180), 725 detector bins, b = A x_bar + 1% white Gaussian noise, up
+to 150 iterations with the discrepancy-principle stop (tau = 1.02, Sec. 6.4).
+value = Arnoldi iterations completed / device time, inputs resident in HBM;
+e2e = the same through the public API from pinned host buffers, host<->device
+copies included.  Under torchrun (N > 1) every rank solves its own seeded
+instance on its own GPU (replicas, weak scaling).
+
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2110_01481_gb300 import inputs as I  # noqa: E402
+
+N, N_ANG, MAXIT, TAU, ETA = 512, 720, 150, 1.02, 0.01
+N_DET = I.detector_count(N)
+METRIC = "AB/BA-GMRES iterations/s"
+UNIT = "iterations/s"
+WORKLOAD = (f"2D parallel beam, {N}x{N} random-ellipse phantom (20 ellipses), {N_ANG} angles "
+            f"over [0,180), {N_DET} bins, 1% noise; AB-GMRES + BA-GMRES per step, up to "
+            f"{MAXIT} iterations, discrepancy principle tau={TAU}")
+L2_BYTES = 129 * 2 ** 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower() in ("active", "1")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_instance(P, torch, dev, seed):
+    """Seeded phantom, b = A x_bar + e with the library's own A (the oracle is
+    not used on the product path)."""
+    g = P.Geometry(N, N_ANG, N_DET)
+    xbar = I.random_ellipses(N, seed)
+    xt = torch.tensor(xbar.ravel(), dtype=torch.float32, device=dev)
+    bbar = P.project(g, xt).double().cpu().numpy()
+    b, enorm = I.add_noise(bbar, ETA, seed)
+    return g, xbar, torch.tensor(b, dtype=torch.float32, device=dev), enorm
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2110_01481_gb300 as P
+    from paper_2110_01481_gb300 import _native
+
+    seed = 2000 + rank
+    g, xbar, b, enorm = make_instance(P, torch, dev, seed)
+    ws_ab = torch.empty(P.workspace_bytes(g, "ab", MAXIT), dtype=torch.uint8, device=dev)
+    ws_ba = torch.empty(P.workspace_bytes(g, "ba", MAXIT), dtype=torch.uint8, device=dev)
+    x_ab = torch.empty(g.n, dtype=torch.float32, device=dev)
+    x_ba = torch.empty(g.n, dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    ctx = P.Context.get(dev)
+
+    def step(bb):
+        ra = P.ab_gmres(g, bb, MAXIT, tau=TAU, noise_norm=enorm, out=x_ab, workspace=ws_ab)
+        rb = P.ba_gmres(g, bb, MAXIT, tau=TAU, noise_norm=enorm, out=x_ba, workspace=ws_ba)
+        return ra, rb
+
+    for _ in range(args.warmup):
+        step(b)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    ctx.timing(reset=True)
+    ctx.set_timing(True)
+    total_ms, iters, per_solve = 0.0, 0, None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()                            # evict L2 between steps
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ra, rb = step(b)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            iters += ra.iters + rb.iters
+            per_solve = (ra, rb)
+    torch.cuda.synchronize()
+    tm = ctx.timing(reset=True)
+    ctx.set_timing(False)
+    clocks = clk.summary()
+
+    # e2e: b from pinned host memory, x back to host, through the public API
+    b_host = b.cpu().pin_memory()
+    xa_host = torch.empty(g.n, dtype=torch.float32).pin_memory()
+    xb_host = torch.empty(g.n, dtype=torch.float32).pin_memory()
+    b_dev = torch.empty_like(b)
+    e2e_ms, e2e_iters = 0.0, 0
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b_dev.copy_(b_host, non_blocking=True)
+        ra, rb = step(b_dev)
+        xa_host.copy_(x_ab, non_blocking=True)
+        xb_host.copy_(x_ba, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms += 1e3 * (time.perf_counter() - t0)
+            e2e_iters += ra.iters + rb.iters
+
+    if world > 1:
+        t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        it = torch.tensor([iters, e2e_iters], dtype=torch.float64, device=dev)
+        dist.all_reduce(it, op=dist.ReduceOp.SUM)
+        total_ms_max, e2e_ms_max = t.tolist()
+        iters_all, e2e_iters_all = it.tolist()
+    else:
+        total_ms_max, e2e_ms_max, iters_all, e2e_iters_all = total_ms, e2e_ms, iters, e2e_iters
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    ra, rb = per_solve
+    value = iters_all / (total_ms_max / 1e3)
+    hbm, peak_kind = peaks()
+    m, n = g.m, g.n
+    # algorithmic bytes per phase call (FP32): Arnoldi step k reads W_k three
+    # times (3 k L 4) plus ~6 vector passes (24 L); a projector pair reads its
+    # input and writes its output once: 8 (m + n)
+    arn_bytes = 0.0
+    for it_k, L in ((ra.iters, m), (rb.iters, n)):
+        arn_bytes += args.steps * (12.0 * L * it_k * (it_k + 1) / 2 + 24.0 * L * it_k)
+    phases = {p: tm[p] for p in _native.PHASES}
+    roof = {
+        "bound": "hbm", "unit": "GB/s", "kernel": "cgs2 Arnoldi step (4 launches)",
+        "achieved": arn_bytes / (phases["arnoldi"]["ms"] / 1e3) / 1e9 if phases["arnoldi"]["ms"] else None,
+        "peak": hbm, "peak_kind": peak_kind, "traffic": None,
+    }
+    roof["frac"] = roof["achieved"] / hbm if roof["achieved"] else None
+    fwd_calls, back_calls = phases["forward"]["calls"], phases["back"]["calls"]
+    proj_ms = phases["forward"]["ms"] + phases["back"]["ms"]
+    proj_bytes = 4.0 * (m + n) * (fwd_calls + back_calls)   # read input + write output, FP32
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded random-ellipse phantom, 1% Gaussian noise)",
+        "config": {"workload": WORKLOAD, "N": N, "n_angles": N_ANG, "n_det": N_DET,
+                   "maxit": MAXIT, "tau": TAU, "noise": ETA,
+                   "l2": "flushed between timed steps (258 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "iterations_per_step": {"ab": ra.iters, "ba": rb.iters},
+        "stop": {"ab": ra.stop_reason, "ba": rb.stop_reason},
+        "rel_error_vs_truth": {
+            "ab": float(np.linalg.norm(x_ab.double().cpu().numpy() - xbar.ravel()) / np.linalg.norm(xbar)),
+            "ba": float(np.linalg.norm(x_ba.double().cpu().numpy() - xbar.ravel()) / np.linalg.norm(xbar))},
+        "phase_ms_per_step": {p: phases[p]["ms"] / args.steps for p in phases},
+        "phase_calls_per_step": {p: phases[p]["calls"] / args.steps for p in phases},
+        "projector_pair": {"ms_per_step": proj_ms / args.steps,
+                           "algorithmic_GBps": proj_bytes / (proj_ms / 1e3) / 1e9 if proj_ms else None,
+                           "frac_of_hbm": (proj_bytes / (proj_ms / 1e3) / 1e9 / hbm) if proj_ms else None},
+        "clocks": clocks,
+        "e2e": {"value": e2e_iters_all / (e2e_ms_max / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": 4 * m, "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": tm["kernels"],
+        "roofline": roof,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_instance(seed):
+    import oracle as O
+    og = O.Geometry(N, N_ANG, N_DET)
+    xbar = I.random_ellipses(N, seed)
+    b, enorm = I.add_noise(O.forward(og, xbar), ETA, seed)
+    b = b.astype(np.float32).astype(np.float64)
+    return O, og, b, enorm
+
+
+def cpu_baseline(iters_per_solve: int):
+    """The FP64 oracle as it stands, on the host cores: one AB-GMRES and one
+    BA-GMRES solve capped at `iters_per_solve` iterations each."""
+    O, og, b, enorm = _oracle_instance(2000)
+    A = lambda v: O.forward(og, v)
+    B = lambda v: O.backproject(og, v)
+    t0 = time.perf_counter()
+    ra = O.ab_gmres(A, B, b, iters_per_solve, tau=TAU, noise_norm=enorm)
+    rb = O.ba_gmres(A, B, b, iters_per_solve, tau=TAU, noise_norm=enorm)
+    dt = time.perf_counter() - t0
+    its = ra["k"] + rb["k"]
+    return {"value": its / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one AB-GMRES and one BA-GMRES solve of the same workload capped at "
+                      f"{iters_per_solve} iterations each ({its} iterations, {dt:.1f} s; "
+                      f"FP64, matrix-free C projectors with OpenMP, numpy Arnoldi)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    O.build_library()
+    O_, og, b, enorm = _oracle_instance(2000)
+    A = lambda v: O.forward(og, v)
+    B = lambda v: O.backproject(og, v)
+    cap = args.ref_iters
+
+    def step():
+        ra = O.ab_gmres(A, B, b, cap, tau=TAU, noise_norm=enorm)
+        rb = O.ba_gmres(A, B, b, cap, tau=TAU, noise_norm=enorm)
+        return ra["k"] + rb["k"]
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    its = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    value = its / dt
+    sample = (f"each step one AB-GMRES and one BA-GMRES solve of the workload capped at {cap} "
+              f"iterations each (FP64 oracle, matrix-free C projectors with OpenMP)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded random-ellipse phantom, 1% Gaussian noise)",
+        "config": {"workload": WORKLOAD, "N": N, "n_angles": N_ANG, "n_det": N_DET,
+                   "maxit": cap, "tau": TAU, "noise": ETA},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-iters", type=int, default=8)
+    ap.add_argument("--ref-iters", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
