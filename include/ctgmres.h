@@ -171,6 +171,26 @@ int ctg_cgs2(const float *W_dev, int64_t ld_w, int64_t L, int32_t k,
              float *q_dev, float *w_out_dev, double *h_out_dev,
              void *scratch_dev, size_t scratch_bytes, void *stream);
 
+/* ctg_cgs2 without caller scratch and without any allocation.  The paper
+ * has no counterpart: this exists for callers that cannot call cudaMalloc,
+ * for example an application whose memory manager has reserved all device
+ * memory up front and forbids further allocations, or a plugin running
+ * inside a host framework that owns every device allocation.
+ * Same arguments and results as ctg_cgs2, minus the scratch.  The scratch is
+ * a fixed 640 KiB array in device memory that is part of the library (every
+ * GPU that loads the library holds it until the process exits); it serves
+ * k <= 256 and L <= 4,980,736, and larger sizes return CTG_ERR_INVALID_ARG.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any stream
+ * capture.  Every call on a device shares the one array, which keeps the
+ * previous call's contents; each call first clears the part that must start
+ * at zero.  Calls whose work overlaps on the GPU (for example on two streams)
+ * race on the array and give wrong results: serialise them.
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
+int ctg_cgs2_noalloc(const float *W_dev, int64_t ld_w, int64_t L, int32_t k,
+                     float *q_dev, float *w_out_dev, double *h_out_dev,
+                     void *stream);
+
 /* Phase tracing (the paper has no counterpart; it reports no timings).
  * When enabled, the solvers bracket each phase with CUDA events on the
  * solver's stream and accumulate its device time; kernel launches are

@@ -57,7 +57,7 @@ class CtgLayout(ctypes.Structure):
 
 EXPORTS = ("ctg_create", "ctg_destroy", "ctg_project", "ctg_backproject",
            "ctg_workspace_bytes", "ctg_workspace_layout", "ctg_ab_gmres",
-           "ctg_ba_gmres", "ctg_cgs2_scratch_bytes", "ctg_cgs2",
+           "ctg_ba_gmres", "ctg_cgs2_scratch_bytes", "ctg_cgs2", "ctg_cgs2_noalloc",
            "ctg_set_timing", "ctg_get_timing", "ctg_status_string")
 
 
@@ -82,6 +82,8 @@ def _declare(lib):
     lib.ctg_cgs2_scratch_bytes.restype = sz
     lib.ctg_cgs2.argtypes = [vp, i64, i64, i32, vp, vp, vp, vp, sz, vp]
     lib.ctg_cgs2.restype = ctypes.c_int
+    lib.ctg_cgs2_noalloc.argtypes = [vp, i64, i64, i32, vp, vp, vp, vp]
+    lib.ctg_cgs2_noalloc.restype = ctypes.c_int
     lib.ctg_set_timing.argtypes = [vp, ctypes.c_int]
     lib.ctg_set_timing.restype = ctypes.c_int
     lib.ctg_get_timing.argtypes = [vp, ctypes.POINTER(CtgTiming), ctypes.c_int]
