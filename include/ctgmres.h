@@ -148,8 +148,10 @@ int ctg_ab_gmres(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev,
                  void *stream);
 
 /* BA-GMRES (Sec. 2, right column): x = x0 + W_k y_k; same conventions.
- * The DP test uses the true residual ||b - A x_k||, which costs one extra
- * forward projection per iteration. */
+ * The DP test uses the true residual ||b - A x_k||.  Since
+ * A x_k = A x0 + sum_j y_j (A w_j) and every A w_j is already formed by the
+ * Arnoldi step, the workspace keeps those (maxit + 1) vectors of length m
+ * and each test costs one sweep over them instead of a forward projection. */
 int ctg_ba_gmres(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev,
                  const float *x0_dev, float *x_dev, const ctg_opts *o,
                  void *workspace_dev, size_t workspace_bytes, ctg_info *info,

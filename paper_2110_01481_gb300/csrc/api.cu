@@ -16,6 +16,11 @@ namespace {
 constexpr int kMaxIt = 4096;
 constexpr double kBreakdownRtol = 1e-6;   // h_{k+1,k} <= rtol * ||q before CGS2||
 
+// Pinned ring used by the pipelined solver loops: the slot of step k holds
+// its Hessenberg column (k+1 doubles), ||q_pre||^2, a residual norm^2 and y_k.
+constexpr int kRing = 4;
+size_t ring_slot_doubles(int maxit) { return 2 * (size_t)maxit + 8; }
+
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
@@ -40,6 +45,7 @@ bool opts_valid(const ctg_opts *o) {
 }
 
 long long to_fx(double v) { return std::llround(std::ldexp(v, CTG_FX_BITS)); }
+long long to_fxf(double v) { return std::llround(std::ldexp(v, CTG_FXF_BITS)); }
 
 // theta_a = S + a R / N_a degrees, i.e. theta_a * N_a = num (an integer).
 void angle_of(const ctg_geom *g, int a, double *c, double *s, int *row_driven) {
@@ -75,9 +81,9 @@ void build_tables(const ctg_geom *g, std::vector<FwdAngle> &fw, std::vector<Back
         const double c = rd ? cs : sn, s = rd ? sn : cs;
         const double P = ds / c, Q = (h * s - hd * ds) / c + h, D = -s / c;
         FwdAngle &f = fw[a];
-        f.P = to_fx(P);
-        f.Q = to_fx(Q);
-        f.D = to_fx(D);
+        f.P = to_fxf(P);
+        f.Q = to_fxf(Q);
+        f.D = to_fxf(D);
         f.pf = (float)P;
         f.qf = (float)Q;
         f.df = (float)D;
@@ -103,12 +109,15 @@ struct GeomEntry {
     ctg_geom g;
     FwdAngle *fwd = nullptr;
     BackAngle *back = nullptr;
-    float *pad = nullptr;       // context-owned padded image for ctg_project
+    int back_window = 0;        // detector window of the tiled back projector
+    PadLayout pl{};             // staged-image layout of the forward projector
+    float2 *pad = nullptr;      // context-owned staged image for ctg_project
     unsigned long long last_use = 0;
 };
 
 struct WsLayout {
     size_t off_w, ld_w, off_h, off_pad, off_vn0, off_vm0, off_vm1, off_y, off_red, total;
+    size_t off_t, ld_t, off_r0m;   // BA only: T = A W_k and b - A x0
     int64_t L, n, m;
     int kmax;
 };
@@ -128,7 +137,7 @@ bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) 
     ly->off_h = off;
     off = align256(off + sizeof(double) * (size_t)(o->maxit + 1) * (size_t)o->maxit);
     ly->off_pad = off;
-    off = align256(off + sizeof(float) * ctg_pad_floats(g->N));
+    off = align256(off + sizeof(float) * ctg_pad_layout(g->N, g->det_spacing).floats);
     ly->off_vn0 = off;
     off = align256(off + sizeof(float) * round_up((size_t)n, 64));
     ly->off_vm0 = off;
@@ -137,6 +146,11 @@ bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) 
     off = align256(off + sizeof(float) * round_up((size_t)m, 64));
     ly->off_y = off;
     off = align256(off + sizeof(double) * (size_t)(o->maxit + 2));
+    ly->ld_t = round_up((size_t)m, 64);
+    ly->off_t = off;
+    if (variant == CTG_BA) off = align256(off + sizeof(float) * ly->ld_t * (size_t)(o->maxit + 1));
+    ly->off_r0m = off;
+    if (variant == CTG_BA) off = align256(off + sizeof(float) * ly->ld_t);
     ly->off_red = off;
     const int64_t Lmax = n > m ? n : m;
     off = align256(off + ctg_red_scratch_bytes(Lmax, o->maxit + 1));
@@ -165,6 +179,9 @@ struct ctg_ctx {
     double ms[4] = {0, 0, 0, 0};
     long long calls[4] = {0, 0, 0, 0};
     long long kernels = 0;
+    // completion events of the pipelined solver loops (no timing)
+    cudaEvent_t ev_h[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_r[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -207,6 +224,8 @@ int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
     GeomEntry e;
     e.g = *g;
     e.last_use = ++ctx->tick;
+    e.back_window = ctg_back_window(bk.data(), g->n_angles);
+    e.pl = ctg_pad_layout(g->N, g->det_spacing);
     cudaError_t err = cudaMalloc(&e.fwd, sizeof(FwdAngle) * fw.size());
     if (err == cudaSuccess) err = cudaMalloc(&e.back, sizeof(BackAngle) * bk.size());
     if (err == cudaSuccess)
@@ -329,22 +348,24 @@ struct SolveCtx {
     double *Hcol(int k) const {   // column k (1-based)
         return reinterpret_cast<double *>(ws + ly.off_h) + (size_t)(k - 1) * (ly.kmax + 1);
     }
-    float *pad() const { return reinterpret_cast<float *>(ws + ly.off_pad); }
+    float2 *pad() const { return reinterpret_cast<float2 *>(ws + ly.off_pad); }
     float *vn0() const { return reinterpret_cast<float *>(ws + ly.off_vn0); }
     float *vm0() const { return reinterpret_cast<float *>(ws + ly.off_vm0); }
     float *vm1() const { return reinterpret_cast<float *>(ws + ly.off_vm1); }
     double *ydev() const { return reinterpret_cast<double *>(ws + ly.off_y); }
+    float *Tcol(int j) const { return reinterpret_cast<float *>(ws + ly.off_t) + (size_t)j * ly.ld_t; }
+    float *r0m() const { return reinterpret_cast<float *>(ws + ly.off_r0m); }
 
     cudaError_t forward(const float *x, float *b) const {
         return traced(ctx, 0, 2, st, [&] {
-            cudaError_t e = ctg_launch_pad(x, pad(), g->N, st);
+            cudaError_t e = ctg_launch_pad(x, pad(), g->N, ge->pl, st);
             if (e != cudaSuccess) return e;
-            return ctg_launch_forward(pad(), g->N, g->n_angles, g->n_det, ge->fwd, b, st);
+            return ctg_launch_forward(pad(), g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, b, st);
         });
     }
     cudaError_t back(const float *b, const float *add, float *x) const {
         return traced(ctx, 1, 1, st, [&] {
-            return ctg_launch_back(b, g->N, g->n_angles, g->n_det, ge->back, add, x, st);
+            return ctg_launch_back(b, g->N, g->n_angles, g->n_det, ge->back, ge->back_window, add, x, st);
         });
     }
     cudaError_t cgs2(int64_t L, int k, float *q) const {
@@ -357,6 +378,12 @@ struct SolveCtx {
             return ctg_gemv(W(), ly.ld_w, L, k, ydev(), base, out, st);
         });
     }
+    cudaError_t gemv_norm2(const float *V, size_t ldv, int64_t L, int k, const float *base,
+                           double *res) const {
+        return traced(ctx, 3, 1, st, [&] {
+            return ctg_gemv_norm2(V, ldv, L, k, ydev(), base, res, rs, st);
+        });
+    }
     cudaError_t sub_norm2(const float *a, const float *c, float *out, int64_t L, double *res) const {
         return traced(ctx, 3, 1, st, [&] { return ctg_sub_norm2(a, c, out, L, res, rs, st); });
     }
@@ -364,15 +391,20 @@ struct SolveCtx {
         return traced(ctx, 3, 1, st, [&] { return ctg_scale(v, nrm2, out, L, st); });
     }
     // copy `count` doubles from the device to the pinned area and wait
+    // pinned staging outside the pipeline ring (which queued copies of
+    // speculative Arnoldi steps may still be writing)
+    double *pinned_scratch() const { return ctx->pinned + kRing * ring_slot_doubles(ly.kmax); }
     int fetch(const double *src, size_t count, double **host) const {
-        CTG_CK(cudaMemcpyAsync(ctx->pinned, src, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
+        double *hs = pinned_scratch();
+        CTG_CK(cudaMemcpyAsync(hs, src, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
         CTG_CK(cudaStreamSynchronize(st));
-        *host = ctx->pinned;
+        *host = hs;
         return CTG_OK;
     }
     int upload_y(const double *y, int k) const {
-        std::memcpy(ctx->pinned, y, sizeof(double) * k);
-        CTG_CK(cudaMemcpyAsync(ydev(), ctx->pinned, sizeof(double) * k, cudaMemcpyHostToDevice, st));
+        double *hs = pinned_scratch();
+        std::memcpy(hs, y, sizeof(double) * k);
+        CTG_CK(cudaMemcpyAsync(ydev(), hs, sizeof(double) * k, cudaMemcpyHostToDevice, st));
         return CTG_OK;
     }
     // ||b - A x||, using vm1 as scratch
@@ -398,7 +430,7 @@ int solve_setup(ctg_ctx *ctx, const ctg_geom *g, int variant, const ctg_opts *o,
     sc->st = static_cast<cudaStream_t>(stream);
     int rc = get_geom(ctx, g, &sc->ge);
     if (rc) return rc;
-    rc = ensure_pinned(ctx, (size_t)o->maxit + 16);
+    rc = ensure_pinned(ctx, kRing * ring_slot_doubles(o->maxit) + (size_t)o->maxit + 16);
     if (rc) return rc;
     if (ws == nullptr) {
         cudaError_t e = cudaMallocAsync(&ws, sc->ly.total, sc->st);
@@ -412,7 +444,7 @@ int solve_setup(ctg_ctx *ctx, const ctg_geom *g, int variant, const ctg_opts *o,
     ctg_red_scratch_carve(sc->ws + sc->ly.off_red, sc->ly.n > sc->ly.m ? sc->ly.n : sc->ly.m,
                           o->maxit + 1, &sc->rs);
     CTG_CK(cudaMemsetAsync(sc->rs.counter, 0, 4 * sizeof(unsigned), sc->st));
-    CTG_CK(cudaMemsetAsync(sc->pad(), 0, sizeof(float) * ctg_pad_floats(g->N), sc->st));
+    CTG_CK(cudaMemsetAsync(sc->pad(), 0, sizeof(float) * sc->ge->pl.floats, sc->st));
     CTG_CK(cudaMemsetAsync(sc->ws + sc->ly.off_h, 0,
                            sizeof(double) * (size_t)(o->maxit + 1) * o->maxit, sc->st));
     info->iters = 0;
@@ -432,13 +464,59 @@ int finish(const SolveCtx &sc, void *owned, int rc) {
     return rc;
 }
 
+int ensure_events(ctg_ctx *ctx) {
+    for (int i = 0; i < kRing; ++i) {
+        if (!ctx->ev_h[i]) CTG_CK(cudaEventCreateWithFlags(&ctx->ev_h[i], cudaEventDisableTiming));
+        if (!ctx->ev_r[i]) CTG_CK(cudaEventCreateWithFlags(&ctx->ev_r[i], cudaEventDisableTiming));
+    }
+    return CTG_OK;
+}
+
 int copy_x0(const SolveCtx &sc, const float *x0, float *x) {
     if (x0) CTG_CK(cudaMemcpyAsync(x, x0, sizeof(float) * sc.ly.n, cudaMemcpyDeviceToDevice, sc.st));
     else CTG_CK(cudaMemsetAsync(x, 0, sizeof(float) * sc.ly.n, sc.st));
     return CTG_OK;
 }
 
-// AB-GMRES, Sec. 2 left column.
+// Geometric extrapolation of a decreasing residual sequence `steps` values
+// ahead of the last one, from the last two.  Used only to decide whether to
+// enqueue Arnoldi steps before the current one has been checked.
+bool predicts_stop(const std::vector<double> &r, double target, int steps = 1) {
+    const size_t n = r.size();
+    if (n < 2 || target <= 0.0) return false;
+    const double a = r[n - 2], c = r[n - 1];
+    double pred = c;
+    if (a > 0.0)
+        for (int i = 0; i < steps; ++i) pred *= c / a;
+    return pred <= target * 1.05;
+}
+
+struct Pipeline {
+    SolveCtx &sc;
+    int maxit;
+    cudaEvent_t *ev_h, *ev_r;
+    double *slot(int k) const { return sc.ctx->pinned + (size_t)(k % kRing) * ring_slot_doubles(maxit); }
+    // H column k at slot[0..k], ||q_pre||^2 at slot[k+1]
+    int after_step(int k) const {
+        double *sl = slot(k);
+        CTG_CK(cudaMemcpyAsync(sl, sc.Hcol(k), sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, sc.st));
+        CTG_CK(cudaMemcpyAsync(sl + k + 1, sc.rs.scal, sizeof(double), cudaMemcpyDeviceToHost, sc.st));
+        CTG_CK(cudaEventRecord(ev_h[k % kRing], sc.st));
+        return CTG_OK;
+    }
+    int wait_step(int k, const double **h) const {
+        CTG_CK(cudaEventSynchronize(ev_h[k % kRing]));
+        *h = slot(k);
+        return CTG_OK;
+    }
+};
+
+int ensure_events(ctg_ctx *ctx);
+
+// AB-GMRES, Sec. 2 left column.  The Arnoldi recurrence does not depend on
+// the least-squares solve, so step k+1 is enqueued before the host reads
+// step k's Hessenberg column (unless the residual trend predicts a stop at
+// k); the GPU then never waits for the host's Givens update.
 int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_opts *o,
            ctg_info *info) {
     const int64_t m = sc.ly.m;
@@ -463,20 +541,26 @@ int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
         return copy_x0(sc, x0, x);
     }
     CTG_CK(sc.scale(sc.Wcol(0), sc.rs.scal + 2, sc.Wcol(0), m));
+    if ((rc = ensure_events(sc.ctx))) return rc;
+    Pipeline pl{sc, o->maxit, sc.ctx->ev_h, sc.ctx->ev_r};
+    auto enqueue = [&](int kk) -> int {
+        CTG_CK(sc.back(sc.Wcol(kk - 1), nullptr, sc.vn0()));       // t = B w_k
+        CTG_CK(sc.forward(sc.vn0(), sc.vm0()));                    // q = A t
+        CTG_CK(sc.cgs2(m, kk, sc.vm0()));
+        return pl.after_step(kk);
+    };
     Givens gv(o->maxit, beta);
-    int k = 0;
+    std::vector<double> rhos{beta};
+    int next = 1, k = 0;
     for (k = 1; k <= o->maxit; ++k) {
-        CTG_CK(sc.back(sc.Wcol(k - 1), nullptr, sc.vn0()));        // t = B w_k
-        CTG_CK(sc.forward(sc.vn0(), sc.vm0()));                     // q = A t
-        CTG_CK(sc.cgs2(m, k, sc.vm0()));
-        CTG_CK(cudaMemcpyAsync(sc.ctx->pinned, sc.Hcol(k), sizeof(double) * (k + 1),
-                               cudaMemcpyDeviceToHost, sc.st));
-        CTG_CK(cudaMemcpyAsync(sc.ctx->pinned + k + 1, sc.rs.scal, sizeof(double),
-                               cudaMemcpyDeviceToHost, sc.st));
-        CTG_CK(cudaStreamSynchronize(sc.st));
-        const double *h = sc.ctx->pinned;
+        if (next == k && (rc = enqueue(next++))) return rc;
+        if (next == k + 1 && k + 1 <= o->maxit && !(dp && predicts_stop(rhos, target)))
+            if ((rc = enqueue(next++))) return rc;
+        const double *h;
+        if ((rc = pl.wait_step(k, &h))) return rc;
         const bool breakdown = h[k] <= kBreakdownRtol * std::sqrt(h[k + 1]);
         const double rho = gv.add_column(k, h);
+        rhos.push_back(rho);
         info->rho = rho;
         if (info->history) info->history[k] = rho;
         if (breakdown) {
@@ -499,20 +583,23 @@ int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
     return sc.true_resnorm(b, x, &info->resnorm);
 }
 
-// BA-GMRES, Sec. 2 right column.
+// BA-GMRES, Sec. 2 right column.  Pipelined like AB; in addition the DP
+// test needs the true residual of x_k, which is enqueued behind the next
+// Arnoldi step(s) and read back one step later.
 int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_opts *o,
            ctg_info *info) {
     const int64_t n = sc.ly.n, m = sc.ly.m;
     const bool dp = o->noise_norm > 0.0;
     const double target = dp ? o->tau * o->noise_norm : 0.0;
-    // r = b - A x0 (m-vector) and its norm; r0 = B r into w_1's slot
+    // r = b - A x0 (m-vector, kept for the DP residuals) and its norm;
+    // r0 = B r into w_1's slot
     if (x0) {
         CTG_CK(sc.forward(x0, sc.vm0()));
-        CTG_CK(sc.sub_norm2(b, sc.vm0(), sc.vm1(), m, sc.rs.scal + 4));
+        CTG_CK(sc.sub_norm2(b, sc.vm0(), sc.r0m(), m, sc.rs.scal + 4));
     } else {
-        CTG_CK(sc.sub_norm2(b, nullptr, sc.vm1(), m, sc.rs.scal + 4));
+        CTG_CK(sc.sub_norm2(b, nullptr, sc.r0m(), m, sc.rs.scal + 4));
     }
-    CTG_CK(sc.back(sc.vm1(), nullptr, sc.Wcol(0)));
+    CTG_CK(sc.back(sc.r0m(), nullptr, sc.Wcol(0)));
     CTG_CK(sc.sub_norm2(sc.Wcol(0), nullptr, nullptr, n, sc.rs.scal + 2));
     double *hp;
     int rc = sc.fetch(sc.rs.scal + 2, 3, &hp);
@@ -526,32 +613,49 @@ int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
         return copy_x0(sc, x0, x);
     }
     CTG_CK(sc.scale(sc.Wcol(0), sc.rs.scal + 2, sc.Wcol(0), n));
+    if ((rc = ensure_events(sc.ctx))) return rc;
+    Pipeline pl{sc, o->maxit, sc.ctx->ev_h, sc.ctx->ev_r};
+    auto enqueue = [&](int kk) -> int {
+        CTG_CK(sc.forward(sc.Wcol(kk - 1), sc.Tcol(kk - 1)));      // t = A w_k, kept in T
+        CTG_CK(sc.back(sc.Tcol(kk - 1), nullptr, sc.vn0()));       // q = B t
+        CTG_CK(sc.cgs2(n, kk, sc.vn0()));
+        return pl.after_step(kk);
+    };
+    // ||b - A x_k||^2 = ||(b - A x0) - T_k y_k||^2 (A x_k = A x0 + A W_k y_k,
+    // and the columns of A W_k are the t vectors of the Arnoldi steps), read
+    // back through the pinned slot
+    auto enqueue_residual = [&](int kk, const double *y) -> int {
+        double *ys = pl.slot(kk) + o->maxit + 4;
+        for (int i = 0; i < kk; ++i) ys[i] = -y[i];
+        CTG_CK(cudaMemcpyAsync(sc.ydev(), ys, sizeof(double) * kk, cudaMemcpyHostToDevice, sc.st));
+        CTG_CK(sc.gemv_norm2(sc.Tcol(0), sc.ly.ld_t, m, kk, sc.r0m(), sc.rs.scal + 4));
+        CTG_CK(cudaMemcpyAsync(pl.slot(kk) + o->maxit + 2, sc.rs.scal + 4, sizeof(double),
+                               cudaMemcpyDeviceToHost, sc.st));
+        CTG_CK(cudaEventRecord(pl.ev_r[kk % kRing], sc.st));
+        return CTG_OK;
+    };
     Givens gv(o->maxit, beta);
-    std::vector<double> y(o->maxit);
-    int k = 0;
-    bool have_x = false;
+    std::vector<double> y(o->maxit), res{res0};
+    int next = 1, k = 0;
     for (k = 1; k <= o->maxit; ++k) {
-        CTG_CK(sc.forward(sc.Wcol(k - 1), sc.vm0()));              // t = A w_k
-        CTG_CK(sc.back(sc.vm0(), nullptr, sc.vn0()));               // q = B t
-        CTG_CK(sc.cgs2(n, k, sc.vn0()));
-        CTG_CK(cudaMemcpyAsync(sc.ctx->pinned, sc.Hcol(k), sizeof(double) * (k + 1),
-                               cudaMemcpyDeviceToHost, sc.st));
-        CTG_CK(cudaMemcpyAsync(sc.ctx->pinned + k + 1, sc.rs.scal, sizeof(double),
-                               cudaMemcpyDeviceToHost, sc.st));
-        CTG_CK(cudaStreamSynchronize(sc.st));
-        const double *h = sc.ctx->pinned;
+        if (next == k && (rc = enqueue(next++))) return rc;
+        if (next == k + 1 && k + 1 <= o->maxit && !(dp && predicts_stop(res, target)))
+            if ((rc = enqueue(next++))) return rc;
+        const double *h;
+        if ((rc = pl.wait_step(k, &h))) return rc;
         const bool breakdown = h[k] <= kBreakdownRtol * std::sqrt(h[k + 1]);
         const double rho = gv.add_column(k, h);
         info->rho = rho;
         const bool last = breakdown || k == o->maxit;
-        have_x = false;
-        if (dp || last) {
-            // x_k = x0 + W_k y_k and the true residual ||b - A x_k||
+        if (dp) {
             gv.solve(k, y.data());
-            if ((rc = sc.upload_y(y.data(), k))) return rc;
-            CTG_CK(sc.gemv(n, k, x0, x));
-            if ((rc = sc.true_resnorm(b, x, &info->resnorm))) return rc;
-            have_x = true;
+            if ((rc = enqueue_residual(k, y.data()))) return rc;
+            // keep the GPU busy while the residual is read back
+            if (dp && !last && next == k + 2 && k + 2 <= o->maxit && !predicts_stop(res, target, 2))
+                if ((rc = enqueue(next++))) return rc;
+            CTG_CK(cudaEventSynchronize(pl.ev_r[k % kRing]));
+            info->resnorm = std::sqrt(pl.slot(k)[o->maxit + 2]);
+            res.push_back(info->resnorm);
         }
         if (info->history) info->history[k] = dp ? info->resnorm : rho;
         if (breakdown) {
@@ -565,13 +669,11 @@ int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
     }
     if (k > o->maxit) k = o->maxit;
     info->iters = k;
-    if (!have_x) {
-        gv.solve(k, y.data());
-        if ((rc = sc.upload_y(y.data(), k))) return rc;
-        CTG_CK(sc.gemv(n, k, x0, x));
-        return sc.true_resnorm(b, x, &info->resnorm);
-    }
-    return CTG_OK;
+    // x_k = x0 + W_k y_k and its residual, recomputed by a forward projection
+    gv.solve(k, y.data());
+    if ((rc = sc.upload_y(y.data(), k))) return rc;
+    CTG_CK(sc.gemv(n, k, x0, x));
+    return sc.true_resnorm(b, x, &info->resnorm);
 }
 
 int solve(int variant, ctg_ctx *ctx, const ctg_geom *g, const float *b, const float *x0,
@@ -614,6 +716,10 @@ void ctg_destroy(ctg_ctx *ctx) {
     if (!ctx) return;
     cudaDeviceSynchronize();
     for (auto ev : ctx->events) cudaEventDestroy(ev);
+    for (int i = 0; i < 4; ++i) {
+        if (ctx->ev_h[i]) cudaEventDestroy(ctx->ev_h[i]);
+        if (ctx->ev_r[i]) cudaEventDestroy(ctx->ev_r[i]);
+    }
     for (auto &e : ctx->cache) {
         cudaFree(e.fwd);
         cudaFree(e.back);
@@ -630,14 +736,14 @@ int ctg_project(ctg_ctx *ctx, const ctg_geom *g, const float *x_dev, float *b_de
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (!ge->pad) {
-        const size_t bytes = sizeof(float) * ctg_pad_floats(g->N);
+        const size_t bytes = sizeof(float) * ge->pl.floats;
         CTG_CK(cudaMalloc(&ge->pad, bytes));
         CTG_CK(cudaMemset(ge->pad, 0, bytes));
     }
     CTG_CK(traced(ctx, 0, 2, st, [&] {
-        cudaError_t e = ctg_launch_pad(x_dev, ge->pad, g->N, st);
+        cudaError_t e = ctg_launch_pad(x_dev, ge->pad, g->N, ge->pl, st);
         if (e != cudaSuccess) return e;
-        return ctg_launch_forward(ge->pad, g->N, g->n_angles, g->n_det, ge->fwd, b_dev, st);
+        return ctg_launch_forward(ge->pad, g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, b_dev, st);
     }));
     return CTG_OK;
 }
@@ -649,7 +755,8 @@ int ctg_backproject(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, float *
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CTG_CK(traced(ctx, 1, 1, st, [&] {
-        return ctg_launch_back(b_dev, g->N, g->n_angles, g->n_det, ge->back, nullptr, x_dev, st);
+        return ctg_launch_back(b_dev, g->N, g->n_angles, g->n_det, ge->back, ge->back_window,
+                               nullptr, x_dev, st);
     }));
     return CTG_OK;
 }

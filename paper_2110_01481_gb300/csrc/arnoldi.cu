@@ -205,6 +205,41 @@ gemv_kernel(const float *__restrict__ W, int64_t ldw, int k, const double *__res
     for (int e = 0; e < E; ++e) st4(out, g0 + (int64_t)e * kThreads, L, acc[e]);
 }
 
+// res = ||base + sum_j y_j V_j||^2 (the vector itself is not stored).
+template <int E>
+__global__ void __launch_bounds__(kThreads)
+gemv_norm2_kernel(const float *__restrict__ V, int64_t ldv, int k, const double *__restrict__ y,
+                  const float *__restrict__ base, int64_t L, float *__restrict__ partials,
+                  unsigned *__restrict__ counter, double *__restrict__ res) {
+    extern __shared__ float s_y[];
+    __shared__ float s_w[kWarps];
+    for (int j = threadIdx.x; j < k; j += kThreads) s_y[j] = (float)y[j];
+    __syncthreads();
+    const int64_t g0 = (int64_t)blockIdx.x * kThreads * E + threadIdx.x;
+    float4 acc[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[e] = ld4(base, g0 + (int64_t)e * kThreads, L);
+#pragma unroll 4
+    for (int j = 0; j < k; ++j) {
+        const float c = s_y[j];
+        const float *Vj = V + (size_t)j * ldv;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float4 w = ld4(Vj, g0 + (int64_t)e * kThreads, L);
+            acc[e].x = fmaf(c, w.x, acc[e].x);
+            acc[e].y = fmaf(c, w.y, acc[e].y);
+            acc[e].z = fmaf(c, w.z, acc[e].z);
+            acc[e].w = fmaf(c, w.w, acc[e].w);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) s += dot4(acc[e], acc[e]);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
+    block_reduce_finish(s_w, 1, partials, counter, res);
+}
+
 // out = a - c (or a), res = ||out||^2; out may be the same vector as a or c.
 template <int E>
 __global__ void __launch_bounds__(kThreads)
@@ -353,6 +388,30 @@ cudaError_t ctg_gemv(const float *W, int64_t ldw, int64_t L, int k, const double
         CTG_GEMV_CASE(4)
         CTG_GEMV_CASE(8)
 #undef CTG_GEMV_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_gemv_norm2(const float *V, int64_t ldv, int64_t L, int k, const double *y,
+                           const float *base, double *res, const RedScratch &rs,
+                           cudaStream_t st) {
+    int E;
+    const int G = ctg_red_grid(L, &E);
+    const size_t smem = sizeof(float) * (size_t)(k > 0 ? k : 1);
+    cudaError_t err = cudaSuccess;
+    switch (E) {
+#define CTG_GN_CASE(EE)                                                                   \
+    case EE:                                                                              \
+        if ((err = ensure_smem(gemv_norm2_kernel<EE>, smem)) != cudaSuccess) return err;  \
+        gemv_norm2_kernel<EE><<<G, kThreads, smem, st>>>(V, ldv, k, y, base, L, rs.partials, \
+                                                         rs.counter, res);                \
+        break;
+        CTG_GN_CASE(1)
+        CTG_GN_CASE(2)
+        CTG_GN_CASE(4)
+        CTG_GN_CASE(8)
+#undef CTG_GN_CASE
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

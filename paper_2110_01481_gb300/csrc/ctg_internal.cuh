@@ -1,23 +1,26 @@
 // Internal declarations shared by the CUDA translation units of libctgmres.
 //
-// Positions along a ray or across the detector are carried in signed 24.40
-// fixed point (int64): integer steps are exact, so the interpolation index
-// and weight stay accurate to ~1e-7 pixel at every image size without FP64
-// arithmetic on the device (FP32 alone loses ~1e-4 pixel at N = 2048).
+// Positions along a ray or across the detector are carried in fixed point
+// (int64): integer steps are exact, so the interpolation index and weight
+// stay accurate to ~1e-7 pixel at every image size without FP64 arithmetic
+// on the device (FP32 alone loses ~1e-4 pixel at N = 2048).  The forward
+// projector uses 32.32 (the high word is then directly an index), the back
+// projector 24.40.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "../../include/ctgmres.h"
 
-#define CTG_FX_BITS 40
+#define CTG_FX_BITS 40       // back projector
+#define CTG_FXF_BITS 32      // forward projector
 
 // Forward (Joseph) parameters of one angle.  With (c, s) = (cos, sin) for a
 // row-driven ray and (sin, cos) for a column-driven one, the interpolation
 // position of ray d at walk step t (row or column index) is
 //   u(d, t) = Q + d * P + t * D,  P = ds / c,  Q = (h s - hd ds) / c + h,
 //   D = -s / c,  h = (N-1)/2,  hd = (n_det-1)/2,
-// and the ray sum is scaled by 1/|c|.
+// and the ray sum is scaled by 1/|c|.  P, Q, D are 32.32 fixed point.
 struct FwdAngle {
     long long P, Q, D;     // fixed point
     float pf, qf, df;      // the same in float, for the walk-range estimate
@@ -34,19 +37,42 @@ struct BackAngle {
     float cf, sf;          // COS, SIN in float (tile-local offsets)
 };
 
-// Padded image layout used by the forward projector: two copies of the
-// image, x and x^T, each N rows of stride N + 4 with two zero columns on
-// either side, so that any clamped tap index reads an exact zero.
-__host__ __device__ static inline size_t ctg_pad_stride(int N) { return (size_t)N + 4; }
-__host__ __device__ static inline size_t ctg_pad_floats(int N) { return 2 * (size_t)N * ctg_pad_stride(N); }
+// Staged image read by the forward projector: two copies, x and x^T, each N
+// rows of `stride` pairs (v[j] - dv[j], dv[j]) with dv[j] = v[j+1] - v[j]
+// for columns j = -border .. N + border - 1 (zeros outside the image), so
+// that with m = 1 + f in [1, 2): v0 + dv * m = lerp(v, j + f).
+// The border is wide enough that every lane of a warp walking the union of
+// its 32 rays' chords stays inside the buffer (31 |P| + 6 >= the largest
+// distance of such a lane from the image); for very coarse detector pitches
+// the border is 2 and the kernel clamps the tap index instead.
+struct PadLayout {
+    int border;            // zero pairs on each side of a row
+    int stride;            // pairs per row = N + 2 * border
+    bool clamp;            // tap index clamped to [-2, N]
+    size_t floats;         // total floats of the staged image (both copies)
+};
+static inline PadLayout ctg_pad_layout(int N, double det_spacing) {
+    PadLayout p;
+    // |P| = ds / max(|cos|, |sin|) <= sqrt(2) ds
+    const double need = 31.0 * 1.41421356237309515 * det_spacing + 6.0;
+    p.clamp = need > 256.0;
+    p.border = p.clamp ? 2 : (int)need + 1;
+    p.stride = N + 2 * p.border;
+    p.floats = 4 * (size_t)N * (size_t)p.stride;
+    return p;
+}
 
 // ---- projector launchers (projectors.cu) --------------------------------
-cudaError_t ctg_launch_pad(const float *x, float *pad, int N, cudaStream_t st);
-cudaError_t ctg_launch_forward(const float *pad, int N, int n_angles, int n_det,
-                               const FwdAngle *tab, float *b, cudaStream_t st);
-// x = B b (+ add, if add != NULL)
+cudaError_t ctg_launch_pad(const float *x, float2 *pad, int N, const PadLayout &pl,
+                           cudaStream_t st);
+cudaError_t ctg_launch_forward(const float2 *pad, int N, const PadLayout &pl, int n_angles,
+                               int n_det, const FwdAngle *tab, float *b, cudaStream_t st);
+// Detector-window width (in bins) that the tiled back projector stages per
+// angle, from the host copy of the angle table.
+int ctg_back_window(const BackAngle *host_tab, int n_angles);
+// x = B b (+ add, if add != NULL); window from ctg_back_window
 cudaError_t ctg_launch_back(const float *b, int N, int n_angles, int n_det,
-                            const BackAngle *tab, const float *add, float *x,
+                            const BackAngle *tab, int window, const float *add, float *x,
                             cudaStream_t st);
 
 // ---- Krylov kernels (arnoldi.cu) -----------------------------------------
@@ -72,6 +98,10 @@ cudaError_t ctg_cgs2_step(const float *W, int64_t ldw, int64_t L, int k, float *
 // out = base + sum_j y_j W_j (base may be NULL); y: k doubles (device).
 cudaError_t ctg_gemv(const float *W, int64_t ldw, int64_t L, int k, const double *y,
                      const float *base, float *out, cudaStream_t st);
+// *res = ||base + sum_j y_j V_j||^2 (double, device); the vector is not stored.
+cudaError_t ctg_gemv_norm2(const float *V, int64_t ldv, int64_t L, int k, const double *y,
+                           const float *base, double *res, const RedScratch &rs,
+                           cudaStream_t st);
 // out = a - c (c may be NULL -> out = a) and *res = ||a - c||^2 (double, device).
 cudaError_t ctg_sub_norm2(const float *a, const float *c, float *out, int64_t L,
                           double *res, const RedScratch &rs, cudaStream_t st);

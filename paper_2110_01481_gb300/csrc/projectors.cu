@@ -1,87 +1,251 @@
 // Matrix-free projectors of the unmatched pair (A, B) (paper Sec. 1,
 // eq. (1.1)-(1.2)): the Joseph ray-driven forward projector A, one thread
-// per ray, and the pixel-driven back projector B, one thread per pixel,
-// gather-only (no atomics).
+// per ray, and the pixel-driven back projector B, one thread per pixel
+// (four pixels per thread), gather-only (no atomics).
+//
+// Both kernels read their input as (value, forward difference) pairs, so one
+// 8-byte load and one FMA give a linear interpolation:
+//   lerp(v, j + f) = v[j] + f (v[j+1] - v[j]).
+#include <cooperative_groups.h>
+
 #include "ctg_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
 constexpr int kPadTile = 32;
 
-// pad = [x with 2 zero columns on each side | x^T likewise]; the zero
-// border columns are written once when the buffer is allocated.
-__global__ void pad_transpose_kernel(const float *__restrict__ x, float *__restrict__ pad,
-                                     int N) {
-    __shared__ float tile[kPadTile][kPadTile + 1];
-    const size_t P = ctg_pad_stride(N);
-    float *xp = pad, *xtp = pad + (size_t)N * P;
+__device__ __forceinline__ float2 lerp_pair(float v0, float v1) {
+    // (v0 - dv, dv): with m = 1 + f, (v0 - dv) + m dv = v0 + f dv
+    const float dv = v1 - v0;
+    return make_float2(v0 - dv, dv);
+}
+
+// Stage the image for the forward projector (layout in ctg_internal.cuh):
+// entries j = -1 .. N-1 of every row of x and of x^T; the other border
+// entries are zero pairs written once when the buffer is allocated.
+__global__ void pad_pairs_kernel(const float *__restrict__ x, float2 *__restrict__ pad, int N,
+                                 int stride, int border) {
+    __shared__ float tile[kPadTile + 1][kPadTile + 2];
+    float2 *xp = pad + border, *xtp = pad + (size_t)N * stride + border;
     const int j0 = blockIdx.x * kPadTile, i0 = blockIdx.y * kPadTile;
+    // tile[r][c] = x[i0 + r][j0 + c] for r, c in [0, 33) (0 outside)
+    for (int r = threadIdx.y; r <= kPadTile; r += blockDim.y)
+        for (int c = threadIdx.x; c <= kPadTile; c += blockDim.x) {
+            const int i = i0 + r, j = j0 + c;
+            tile[r][c] = (i < N && j < N) ? x[(size_t)i * N + j] : 0.0f;
+        }
+    __syncthreads();
     for (int r = threadIdx.y; r < kPadTile; r += blockDim.y) {
         const int i = i0 + r, j = j0 + threadIdx.x;
         if (i < N && j < N) {
-            const float v = x[(size_t)i * N + j];
-            tile[r][threadIdx.x] = v;
-            xp[(size_t)i * P + 2 + j] = v;
+            const float v = tile[r][threadIdx.x];
+            xp[(size_t)i * stride + j] = lerp_pair(v, tile[r][threadIdx.x + 1]);
+            xtp[(size_t)j * stride + i] = lerp_pair(v, tile[r + 1][threadIdx.x]);
         }
     }
-    __syncthreads();
-    for (int r = threadIdx.y; r < kPadTile; r += blockDim.y) {
-        const int j = j0 + r, i = i0 + threadIdx.x;   // xT[j][i] = x[i][j]
-        if (i < N && j < N) xtp[(size_t)j * P + 2 + i] = tile[threadIdx.x][r];
-    }
+    // entry j = -1 of each row: (0 - x[0], x[0])
+    if (blockIdx.x == 0)
+        for (int r = threadIdx.y * blockDim.x + threadIdx.x; r < kPadTile; r += blockDim.x * blockDim.y) {
+            const int i = i0 + r;
+            if (i < N) xp[(size_t)i * stride - 1] = lerp_pair(0.0f, x[(size_t)i * N]);
+        }
+    if (blockIdx.y == 0)
+        for (int c = threadIdx.y * blockDim.x + threadIdx.x; c < kPadTile; c += blockDim.x * blockDim.y) {
+            const int j = j0 + c;
+            if (j < N) xtp[(size_t)j * stride - 1] = lerp_pair(0.0f, x[j]);
+        }
 }
 
 __device__ __forceinline__ float fx_frac(long long U) {
-    // top 24 bits of the 40-bit fraction, exact in float
+    // top 24 bits of the 40-bit fraction of a 24.40 value, in [0, 1)
     const unsigned f24 = (unsigned)((unsigned long long)U >> (CTG_FX_BITS - 24)) & 0xFFFFFFu;
     return (float)f24 * (1.0f / 16777216.0f);
 }
 
-// b[a * n_det + d] = scale_a * sum_t lerp(img_a[t, .], u(d, t)).
-__global__ void __launch_bounds__(256)
-joseph_forward_kernel(const float *__restrict__ pad, int N, int n_angles, int n_det,
-                      const FwdAngle *__restrict__ tab, float *__restrict__ b) {
-    const long long ray = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ray >= (long long)n_angles * n_det) return;
-    const int a = (int)(ray / n_det);
-    const int d = (int)(ray - (long long)a * n_det);
-    const FwdAngle t = tab[a];
-    const size_t P = ctg_pad_stride(N);
-    const float *img = pad + (t.row_driven ? 0 : (size_t)N * P) + 2;
-
-    // walk range: steps whose taps can touch the image, -1 < u < N, with a
-    // one-step margin; the tap index is clamped below, so the estimate only
-    // skips work and never changes the result
-    const float u0 = fmaf((float)d, t.pf, t.qf);
-    int lo = 0, hi = N - 1;
-    if (fabsf(t.df) > 1e-20f) {
-        float r1 = (-1.0f - u0) / t.df, r2 = ((float)N - u0) / t.df;
-        float tlo = fmaxf(fminf(r1, r2), -2.0f), thi = fminf(fmaxf(r1, r2), (float)N + 1);
-        lo = max(0, (int)floorf(tlo) - 1);
-        hi = min(N - 1, (int)ceilf(thi) + 1);
-    } else if (!(u0 > -2.0f && u0 < (float)N + 1.0f)) {
-        lo = 1;
-        hi = 0;
-    }
-    long long U = t.Q + (long long)d * t.P + (long long)lo * t.D;
-    float acc = 0.0f;
-    for (int s = lo; s <= hi; ++s) {
-        int j0 = (int)(U >> CTG_FX_BITS);
-        j0 = min(max(j0, -2), N);          // clamped taps read the zero border
-        const float f = fx_frac(U);
-        const float *row = img + (size_t)s * P + j0;
-        const float v0 = __ldg(row), v1 = __ldg(row + 1);
-        acc += fmaf(f, v1 - v0, v0);
-        U += t.D;
-    }
-    b[ray] = acc * t.scale;
+__device__ __forceinline__ float one_plus_frac(unsigned lo) {
+    // 1 + (top 23 bits of a 32-bit fraction), exactly, in [1, 2)
+    return __uint_as_float(0x3F800000u | (lo >> 9));
 }
 
+constexpr int kFwdAngles = 8;   // warps per block, one angle each
+
+// b[a * n_det + d] = scale_a * sum_t lerp(img_a[t, .], u(d, t)).
+// A warp holds 32 adjacent rays of one angle and walks the union of their
+// chords' row ranges in lockstep, so each load instruction reads one image
+// row.  The walk position is 32.32 fixed point with the row stride folded
+// into the step, so its high word is the staged-pair index and its low word
+// the interpolation weight.  A lane outside its own chord reads zero pairs
+// in the border (or, with kClamp, a clamped index into the 2-pair border).
+template <bool kClamp>
+__global__ void __launch_bounds__(32 * kFwdAngles)
+joseph_forward_kernel(const float2 *__restrict__ pad, int N, int stride, int border,
+                      int n_angles, int n_det, const FwdAngle *__restrict__ tab,
+                      float *__restrict__ b) {
+    const int lane = threadIdx.x & 31;
+    const int a = blockIdx.y * kFwdAngles + (threadIdx.x >> 5);
+    if (a >= n_angles) return;                        // whole warp
+    const int d = blockIdx.x * 32 + lane;
+    const FwdAngle t = tab[a];
+    const float2 *img = pad + (t.row_driven ? 0 : (size_t)N * stride) + border;
+
+    // this ray's steps whose taps can touch the image (-1 < u < N), with a
+    // one-step margin; rays past the last detector take an empty range
+    int lo = N, hi = -1;
+    if (d < n_det) {
+        const float u0 = fmaf((float)d, t.pf, t.qf);
+        if (fabsf(t.df) > 1e-20f) {
+            const float r1 = (-1.0f - u0) / t.df, r2 = ((float)N - u0) / t.df;
+            const float tlo = fmaxf(fminf(r1, r2), -2.0f), thi = fminf(fmaxf(r1, r2), (float)N + 1);
+            lo = max(0, (int)floorf(tlo) - 1);
+            hi = min(N - 1, (int)ceilf(thi) + 1);
+        } else if (u0 > -2.0f && u0 < (float)N + 1.0f) {
+            lo = 0;
+            hi = N - 1;
+        }
+    }
+    const int wlo = __reduce_min_sync(0xffffffffu, lo);
+    const int whi = __reduce_max_sync(0xffffffffu, hi);
+    float acc0 = 0.0f, acc1 = 0.0f;
+    if (!kClamp) {
+        const long long Ds = t.D + ((long long)stride << CTG_FXF_BITS);
+        long long U = t.Q + (long long)d * t.P + (long long)wlo * Ds;
+        float acc2 = 0.0f, acc3 = 0.0f;
+        int s = wlo;
+        for (; s + 3 <= whi; s += 4) {
+            const float2 pa = __ldg(img + (int)(U >> CTG_FXF_BITS));
+            const float ma = one_plus_frac((unsigned)U);
+            U += Ds;
+            const float2 pb = __ldg(img + (int)(U >> CTG_FXF_BITS));
+            const float mb = one_plus_frac((unsigned)U);
+            U += Ds;
+            const float2 pc = __ldg(img + (int)(U >> CTG_FXF_BITS));
+            const float mc = one_plus_frac((unsigned)U);
+            U += Ds;
+            const float2 pd = __ldg(img + (int)(U >> CTG_FXF_BITS));
+            const float md = one_plus_frac((unsigned)U);
+            U += Ds;
+            acc0 = fmaf(ma, pa.y, acc0 + pa.x);
+            acc1 = fmaf(mb, pb.y, acc1 + pb.x);
+            acc2 = fmaf(mc, pc.y, acc2 + pc.x);
+            acc3 = fmaf(md, pd.y, acc3 + pd.x);
+        }
+        for (; s <= whi; ++s) {
+            const float2 pa = __ldg(img + (int)(U >> CTG_FXF_BITS));
+            acc0 = fmaf(one_plus_frac((unsigned)U), pa.y, acc0 + pa.x);
+            U += Ds;
+        }
+        acc0 += acc2;
+        acc1 += acc3;
+    } else {
+        long long U = t.Q + (long long)d * t.P + (long long)wlo * t.D;
+        for (int s = wlo; s <= whi; ++s) {
+            const int j = min(max((int)(U >> CTG_FXF_BITS), -2), N);
+            const float2 pa = __ldg(img + (size_t)s * stride + j);
+            acc0 = fmaf(one_plus_frac((unsigned)U), pa.y, acc0 + pa.x);
+            U += t.D;
+        }
+    }
+    if (d < n_det) b[(size_t)a * n_det + d] = (acc0 + acc1) * t.scale;
+}
+
+// ---------------------------------------------------------------------------
+// Pixel-driven back projection.  A thread-block cluster of kBSplit CTAs owns
+// a 32 x 32 pixel tile; each CTA (256 threads, four rows each) sums a
+// contiguous quarter of the angles.  For a chunk of angles a CTA stages, per
+// angle, the detector window that the tile projects onto as
+// (b[d], b[d+1] - b[d]) pairs in shared memory (zeros outside the
+// detector), so the inner loop has no bounds test and one 8-byte shared
+// load per interpolation.  The tile origin's detector position is formed
+// exactly in fixed point; each pixel adds a small float offset.  The CTAs'
+// partial sums are then added through distributed shared memory in rank
+// order (deterministic, no atomics), each CTA finishing a quarter of the
+// tile's rows.
+constexpr int kBT = 32;          // tile side
+constexpr int kBRows = 4;        // rows per thread (threads: 32 x 8)
+constexpr int kBThreads = 256;
+constexpr int kBChunk = 32;      // angles staged per pass
+constexpr int kBSplit = 4;       // CTAs per cluster = angle groups per tile
+
+__global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
+pixel_back_tiled_kernel(const float *__restrict__ b, int N, int n_angles, int n_det,
+                        const BackAngle *__restrict__ tab, int W, const float *__restrict__ add,
+                        float *__restrict__ x) {
+    extern __shared__ float2 s_pairs[];               // kBChunk * W pairs
+    __shared__ float4 s_par[kBChunk];                 // cf, sf, u0' (window-relative), origin
+    __shared__ float s_part[kBRows][kBThreads];       // this CTA's partial sums
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();       // == blockIdx.z
+    const int j0 = blockIdx.x * kBT, i0 = blockIdx.y * kBT;
+    const int dj = threadIdx.x & 31, di = threadIdx.x >> 5;   // di in [0, 8)
+    const float fdj = (float)dj, fdi = (float)di;
+    const int per = (n_angles + kBSplit - 1) / kBSplit;
+    const int a_begin = min(n_angles, rank * per), a_end = min(n_angles, a_begin + per);
+    float acc[kBRows] = {0.f, 0.f, 0.f, 0.f};
+    const float kMagic = 12582912.0f;                 // 1.5 * 2^23
+    for (int a0 = a_begin; a0 < a_end; a0 += kBChunk) {
+        const int na = min(kBChunk, a_end - a0);
+        __syncthreads();
+        if (threadIdx.x < na) {
+            const BackAngle t = tab[a0 + threadIdx.x];
+            const long long U0 = t.C + (long long)j0 * t.COS + (long long)i0 * t.SIN;
+            const int dbase = (int)(U0 >> CTG_FX_BITS);
+            const float phi = fx_frac(U0);
+            // lowest detector position over the tile (a corner), minus one
+            const float umin = phi + fminf(0.f, (kBT - 1) * t.cf) + fminf(0.f, (kBT - 1) * t.sf);
+            const int org = dbase + (int)floorf(umin) - 1;
+            s_par[threadIdx.x] = make_float4(t.cf, t.sf, (float)(dbase - org) + phi,
+                                             __int_as_float(org));
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < na * W; e += kBThreads) {
+            const int k = e / W, w = e - k * W;
+            const int dd = __float_as_int(s_par[k].w) + w;
+            const float *brow = b + (size_t)(a0 + k) * n_det;
+            const float v0 = ((unsigned)dd < (unsigned)n_det) ? __ldg(brow + dd) : 0.0f;
+            const float v1 = ((unsigned)(dd + 1) < (unsigned)n_det) ? __ldg(brow + dd + 1) : 0.0f;
+            s_pairs[e] = make_float2(v0, v1 - v0);
+        }
+        __syncthreads();
+        const float2 *pw = s_pairs;
+#pragma unroll 2
+        for (int k = 0; k < na; ++k, pw += W) {
+            const float4 p = s_par[k];
+            float u = fmaf(fdi, p.y, fmaf(fdj, p.x, p.z));
+            const float du = 8.0f * p.y;
+#pragma unroll
+            for (int r = 0; r < kBRows; ++r) {
+                // floor(u) by the round-down magic-number add (0 <= u < 2^22)
+                const float tt = __fadd_rd(u, kMagic);
+                const int idx = __float_as_int(tt) - 0x4B400000;
+                const float f = u - (tt - kMagic);
+                const float2 pr = pw[idx];
+                acc[r] += fmaf(f, pr.y, pr.x);
+                u += du;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kBRows; ++r) s_part[r][threadIdx.x] = acc[r];
+    cluster.sync();
+    // this CTA finishes row group `rank` of every thread: pixel row di + 8 rank
+    float sum = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kBSplit; ++q)
+        sum += cluster.map_shared_rank(&s_part[rank][0], q)[threadIdx.x];
+    const int i = i0 + di + 8 * rank, j = j0 + dj;
+    if (i < N && j < N) {
+        const size_t p = (size_t)i * N + j;
+        x[p] = add ? sum + add[p] : sum;
+    }
+    cluster.sync();   // peers' shared memory must outlive the reads above
+}
+
+// Generic pixel-driven back projection (any detector pitch): 32 x 8 tiles,
+// taps read through L1 with bounds tests.
 constexpr int kBX = 32, kBY = 8, kAChunk = 256;
 
-// x[i, j] = sum_a lerp(b[a, .], u_a(i, j)) (+ add[i, j]).  A block owns a
-// 32 x 8 pixel tile; the tile origin's detector position is formed exactly
-// in fixed point once per angle, and each pixel adds its small float offset.
 __global__ void __launch_bounds__(kBX *kBY)
 pixel_back_kernel(const float *__restrict__ b, int N, int n_angles, int n_det,
                   const BackAngle *__restrict__ tab, const float *__restrict__ add,
@@ -124,25 +288,47 @@ pixel_back_kernel(const float *__restrict__ b, int N, int n_angles, int n_det,
 
 }  // namespace
 
-cudaError_t ctg_launch_pad(const float *x, float *pad, int N, cudaStream_t st) {
+int ctg_back_window(const BackAngle *host_tab, int n_angles) {
+    // detector span of a 32 x 32 tile at any angle, plus the floor/ceil and
+    // second-tap margins
+    double span = 0.0;
+    for (int a = 0; a < n_angles; ++a) {
+        const double s = (kBT - 1) * ((double)fabsf(host_tab[a].cf) + (double)fabsf(host_tab[a].sf));
+        if (s > span) span = s;
+    }
+    return (int)ceil(span) + 4;
+}
+
+cudaError_t ctg_launch_pad(const float *x, float2 *pad, int N, const PadLayout &pl,
+                           cudaStream_t st) {
     dim3 grid((N + kPadTile - 1) / kPadTile, (N + kPadTile - 1) / kPadTile);
-    pad_transpose_kernel<<<grid, dim3(kPadTile, 8), 0, st>>>(x, pad, N);
+    pad_pairs_kernel<<<grid, dim3(kPadTile, 8), 0, st>>>(x, pad, N, pl.stride, pl.border);
     return cudaGetLastError();
 }
 
-cudaError_t ctg_launch_forward(const float *pad, int N, int n_angles, int n_det,
-                               const FwdAngle *tab, float *b, cudaStream_t st) {
-    const long long m = (long long)n_angles * n_det;
-    const int threads = 256;
-    const long long blocks = (m + threads - 1) / threads;
-    joseph_forward_kernel<<<(unsigned)blocks, threads, 0, st>>>(pad, N, n_angles, n_det, tab, b);
+cudaError_t ctg_launch_forward(const float2 *pad, int N, const PadLayout &pl, int n_angles,
+                               int n_det, const FwdAngle *tab, float *b, cudaStream_t st) {
+    dim3 grid((n_det + 31) / 32, (n_angles + kFwdAngles - 1) / kFwdAngles);
+    if (pl.clamp)
+        joseph_forward_kernel<true><<<grid, 32 * kFwdAngles, 0, st>>>(pad, N, pl.stride, pl.border,
+                                                                      n_angles, n_det, tab, b);
+    else
+        joseph_forward_kernel<false><<<grid, 32 * kFwdAngles, 0, st>>>(pad, N, pl.stride, pl.border,
+                                                                       n_angles, n_det, tab, b);
     return cudaGetLastError();
 }
 
 cudaError_t ctg_launch_back(const float *b, int N, int n_angles, int n_det,
-                            const BackAngle *tab, const float *add, float *x,
+                            const BackAngle *tab, int window, const float *add, float *x,
                             cudaStream_t st) {
-    dim3 grid((N + kBX - 1) / kBX, (N + kBY - 1) / kBY);
-    pixel_back_kernel<<<grid, dim3(kBX, kBY), 0, st>>>(b, N, n_angles, n_det, tab, add, x);
+    const size_t smem = sizeof(float2) * (size_t)kBChunk * window;
+    if (window > 0 && smem <= 40 * 1024) {
+        dim3 grid((N + kBT - 1) / kBT, (N + kBT - 1) / kBT, kBSplit);
+        pixel_back_tiled_kernel<<<grid, kBThreads, smem, st>>>(b, N, n_angles, n_det, tab, window,
+                                                               add, x);
+    } else {
+        dim3 grid((N + kBX - 1) / kBX, (N + kBY - 1) / kBY);
+        pixel_back_kernel<<<grid, dim3(kBX, kBY), 0, st>>>(b, N, n_angles, n_det, tab, add, x);
+    }
     return cudaGetLastError();
 }

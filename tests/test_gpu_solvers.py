@@ -148,6 +148,28 @@ def test_nonzero_initial_guess(P, oracle_mod, variant):
 
 
 @pytest.mark.parametrize("variant", ["ab", "ba"])
+def test_nonzero_initial_guess_with_discrepancy_stop(P, oracle_mod, variant):
+    """x0 != 0 together with the DP stop: the residual of x_k is measured
+    from b - A x0 (BA reuses the basis vectors' projections for it)."""
+    O = oracle_mod
+    og, xt, b, enorm = _problem(O, 64, 90, seed=1064)
+    A, B = _ops(O, og)
+    x0 = (0.3 * I.random_ellipses(64, 6).ravel()).astype(np.float32).astype(np.float64)
+    solver = O.ab_gmres if variant == "ab" else O.ba_gmres
+    ref = solver(A, B, b, 60, x0=x0, tau=1.02, noise_norm=enorm)
+    _, r = _solve(P, variant, og, b, 60, x0=x0, tau=1.02, noise_norm=enorm)
+    assert r.stop_reason == 1 and ref["stop_reason"] == 1
+    target = 1.02 * enorm
+    if r.iters == ref["k"]:
+        assert _rel(r.x.double().cpu().numpy(), ref["x"]) <= X_TOL
+    else:
+        assert abs(r.iters - ref["k"]) == 1
+        kk = min(r.iters, ref["k"])
+        assert abs(ref["resnorm"][kk] - target) < 1e-4 * target
+    assert r.resnorm == pytest.approx(np.linalg.norm(b - A(r.x.double().cpu().numpy())), rel=1e-5)
+
+
+@pytest.mark.parametrize("variant", ["ab", "ba"])
 def test_degenerate_starts(P, oracle_mod, variant):
     import torch
     O = oracle_mod
