@@ -144,6 +144,61 @@ def joseph_interpolations(N, n_angles, n_det, start=0, rng=180, ds=1.0):
 L1_PEAK_GBS = 152 * 128 * 2.070
 
 
+def reduce_across_ranks(dist, torch, device, maxed, summed):
+    """Combine per-rank timings: the max over ranks of each value in `maxed`
+    (times) and the sum over ranks of each value in `summed` (work done).
+    Works for any process group backend (NCCL on GPUs, gloo on CPU)."""
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return list(maxed), list(summed)
+    t = torch.tensor(list(maxed), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor(list(summed), dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return t.tolist(), w.tolist()
+
+
+def cgs2_timing(P, torch, native, dev, k, L, steps, flush):
+    """Median device time (ms) of one CGS2 step of a length-L vector against
+    k stored vectors: the Arnoldi step at a large basis, where it is the
+    HBM-bound kernel of the path (3 sweeps of W_k are its algorithmic
+    traffic).  L2 is flushed before every timed step."""
+    ldw = (L + 63) // 64 * 64
+    Wc = torch.randn(k + 1, ldw, device=dev, dtype=torch.float32) / math.sqrt(L)
+    qc = torch.randn(L, device=dev, dtype=torch.float32)
+    qw = torch.empty_like(qc)
+    scratch = torch.empty(int(native.lib().ctg_cgs2_scratch_bytes(L, k)), dtype=torch.uint8,
+                          device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = []
+    for i in range(3 + steps):
+        qw.copy_(qc)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.cgs2(Wc, k, qw, w_out=Wc[k, :L], scratch=scratch)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= 3:
+            out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def run_cgs2_only(args):
+    """Just the large-basis Arnoldi step (for profiling that kernel alone)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2110_01481_gb300 as P
+    from paper_2110_01481_gb300 import _native
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    for L in (N_ANG * N_DET, 2048 * 2048):
+        ms = cgs2_timing(P, torch, _native, dev, args.cgs2_k, L, args.steps, flush)
+        gbs = 4.0 * L * (3 * args.cgs2_k + 6) / (ms / 1e3) / 1e9
+        print(json.dumps({"cgs2_k": args.cgs2_k, "L": L, "us": ms * 1e3,
+                          "algorithmic_GBps": gbs, "frac_of_hbm": gbs / peaks()[0]}))
+
+
 def make_instance(P, torch, dev, seed):
     """Seeded phantom, b = A x_bar + e with the library's own A (the oracle is
     not used on the product path)."""
@@ -225,6 +280,10 @@ def run_gpu(args):
     tm = ctx.timing(reset=True)
     ctx.set_timing(False)
 
+    cgs_k, cgs_L = 100, g.m
+    cgs_ms = cgs2_timing(P, torch, _native, dev, cgs_k, cgs_L, args.steps, flush)
+    cgs_bytes = 4.0 * cgs_L * (3 * cgs_k + 6)
+
     # e2e: b from pinned host memory, x back to host, through the public API
     b_host = b.cpu().pin_memory()
     xa_host = torch.empty(g.n, dtype=torch.float32).pin_memory()
@@ -244,15 +303,8 @@ def run_gpu(args):
             e2e_ms += 1e3 * (time.perf_counter() - t0)
             e2e_iters += ra.iters + rb.iters
 
-    if world > 1:
-        t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        it = torch.tensor([iters, e2e_iters], dtype=torch.float64, device=dev)
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        total_ms_max, e2e_ms_max = t.tolist()
-        iters_all, e2e_iters_all = it.tolist()
-    else:
-        total_ms_max, e2e_ms_max, iters_all, e2e_iters_all = total_ms, e2e_ms, iters, e2e_iters
+    (total_ms_max, e2e_ms_max), (iters_all, e2e_iters_all) = reduce_across_ranks(
+        dist, torch, dev, [total_ms, e2e_ms], [iters, e2e_iters])
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -275,6 +327,11 @@ def run_gpu(args):
         "peak": hbm, "peak_kind": peak_kind + " copy bandwidth",
     }
     arnoldi_roof["frac"] = arnoldi_roof["achieved"] / hbm if arnoldi_roof["achieved"] else None
+    arnoldi_roof["in_step_note"] = "at the solves' own k (<= 14 here), latency-bound"
+    arnoldi_roof["large_k"] = {"k": cgs_k, "L": cgs_L, "us": cgs_ms * 1e3,
+                               "algorithmic_bytes": cgs_bytes,
+                               "achieved_GBps": cgs_bytes / (cgs_ms / 1e3) / 1e9,
+                               "frac": cgs_bytes / (cgs_ms / 1e3) / 1e9 / hbm}
     # dominant kernel by device time in the timed region
     dom = max(("forward", "back", "arnoldi"), key=lambda p: phases[p]["ms"])
     if dom == "arnoldi":
@@ -403,9 +460,14 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=8)
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cgs2-only", action="store_true",
+                    help="time only the large-basis Arnoldi (CGS2) step")
+    ap.add_argument("--cgs2-k", type=int, default=100)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.cgs2_only:
+        run_cgs2_only(args)
     else:
         run_gpu(args)
 

@@ -16,7 +16,8 @@
 namespace {
 
 constexpr int kThreads = 256, kWarps = kThreads / 32;
-constexpr int kTargetGrid = 4 * 152;   // 4 blocks on each of GB300's 152 SMs
+constexpr int kTargetGrid = 2 * 152;   // 2 blocks on each of GB300's 152 SMs
+constexpr int kMaxE = 8;               // float4 groups per thread, at most
 
 __device__ __forceinline__ float4 ld4(const float *p, int64_t g, int64_t L) {
     const int64_t i = 4 * g;
@@ -65,19 +66,25 @@ __device__ __forceinline__ double warp_sum_d(double s) {
     return s;
 }
 
+// Partial sums are laid out [j][Gp] with Gp = G rounded up to 4, so the
+// last block can read them as float4.
+__host__ __device__ inline int padded_grid(int G) { return (G + 3) & ~3; }
+
 // Writes this block's nred partial sums, then lets the last block sum all
-// blocks' partials (fixed order, FP64) into red_out[0..nred-1].
+// blocks' partials (fixed order, FP64) into red_out[0..nred-1].  The last
+// block's warps each take four coefficients at a time and read the partials
+// as float4, so the serial tail is a few L2 round trips.
 __device__ void block_reduce_finish(float *s_w, int nred, float *__restrict__ partials,
                                     unsigned *__restrict__ counter,
                                     double *__restrict__ red_out) {
     __shared__ bool s_last;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int G = gridDim.x;
+    const int G = gridDim.x, Gp = padded_grid(G);
     __syncthreads();
     for (int j = tid; j < nred; j += kThreads) {
         float s = 0.f;
         for (int w = 0; w < kWarps; ++w) s += s_w[w * nred + j];
-        partials[(size_t)j * G + blockIdx.x] = s;
+        partials[(size_t)j * Gp + blockIdx.x] = s;
     }
     __threadfence();
     __syncthreads();
@@ -85,13 +92,64 @@ __device__ void block_reduce_finish(float *s_w, int nred, float *__restrict__ pa
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (int j = warp; j < nred; j += kWarps) {
-        double s = 0.0;
-        for (int bb = lane; bb < G; bb += 32) s += (double)__ldcg(partials + (size_t)j * G + bb);
-        s = warp_sum_d(s);
-        if (lane == 0) red_out[j] = s;
+    const int G4 = Gp / 4;
+    for (int j0 = warp * 4; j0 < nred; j0 += kWarps * 4) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int g4 = lane; g4 < G4; g4 += 32) {
+            float4 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                v[q] = (j0 + q < nred)
+                           ? __ldcg(reinterpret_cast<const float4 *>(partials + (size_t)(j0 + q) * Gp) + g4)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int b0 = 4 * g4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                // the padding entries (block index >= G) were never written
+                acc[q] += (double)v[q].x;
+                if (b0 + 1 < G) acc[q] += (double)v[q].y;
+                if (b0 + 2 < G) acc[q] += (double)v[q].z;
+                if (b0 + 3 < G) acc[q] += (double)v[q].w;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double t = warp_sum_d(acc[q]);
+            if (lane == 0 && j0 + q < nred) red_out[j0 + q] = t;
+        }
     }
     if (tid == 0) *counter = 0u;
+}
+
+// acc += sum_j c_j V_j over this thread's E float4 groups, loads issued in
+// batches of JB vectors so that 8 float4 per thread are in flight.
+template <int E>
+__device__ __forceinline__ void accumulate_batched(const float *__restrict__ V, int64_t ldv, int k,
+                                                   const float *c, int64_t g0, int64_t L,
+                                                   float4 (&acc)[E]) {
+    constexpr int JB = 8 / E > 0 ? 8 / E : 1;
+    for (int j0 = 0; j0 < k; j0 += JB) {
+        float4 w[JB][E];
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+            const float *Vj = V + (size_t)(j0 + jj) * ldv;
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                w[jj][e] = (j0 + jj < k) ? ld4(Vj, g0 + (int64_t)e * kThreads, L)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+            const float cj = (j0 + jj < k) ? c[j0 + jj] : 0.f;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                acc[e].x = fmaf(cj, w[jj][e].x, acc[e].x);
+                acc[e].y = fmaf(cj, w[jj][e].y, acc[e].y);
+                acc[e].z = fmaf(cj, w[jj][e].z, acc[e].z);
+                acc[e].w = fmaf(cj, w[jj][e].w, acc[e].w);
+            }
+        }
+    }
 }
 
 // One CGS2 pass over a slice of E float4 groups per thread.
@@ -99,7 +157,7 @@ __device__ void block_reduce_finish(float *s_w, int nred, float *__restrict__ pa
 //   DOTS:   red_out[j] = W_j^T q (after the update)      j < k
 //   NORM:   red_out[DOTS ? k : 0] = q^T q (after the update)
 template <int E, bool UPDATE, bool DOTS, bool NORM>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 cgs_pass_kernel(const float *__restrict__ W, int64_t ldw, int k, float *__restrict__ q,
                 int64_t L, const double *__restrict__ coef, float *__restrict__ partials,
                 unsigned *__restrict__ counter, double *__restrict__ red_out) {
@@ -114,33 +172,56 @@ cgs_pass_kernel(const float *__restrict__ W, int64_t ldw, int k, float *__restri
     float4 qv[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) qv[e] = ld4_rw(q, g0 + (int64_t)e * kThreads, L);
+    // Loads are issued in batches of JB vectors (JB * E = 8 float4 per
+    // thread in flight) before any of them is used, so each thread keeps
+    // 128 bytes of HBM reads outstanding.
+    constexpr int JB = 8 / E > 0 ? 8 / E : 1;
     if (UPDATE) {
         __syncthreads();
-#pragma unroll 4
-        for (int j = 0; j < k; ++j) {
-            const float c = s_coef[j];
-            const float *Wj = W + (size_t)j * ldw;
+        for (int j0 = 0; j0 < k; j0 += JB) {
+            float4 w[JB][E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const float4 w = ld4(Wj, g0 + (int64_t)e * kThreads, L);
-                qv[e].x = fmaf(-c, w.x, qv[e].x);
-                qv[e].y = fmaf(-c, w.y, qv[e].y);
-                qv[e].z = fmaf(-c, w.z, qv[e].z);
-                qv[e].w = fmaf(-c, w.w, qv[e].w);
+            for (int jj = 0; jj < JB; ++jj) {
+                const float *Wj = W + (size_t)(j0 + jj) * ldw;
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    w[jj][e] = (j0 + jj < k) ? ld4(Wj, g0 + (int64_t)e * kThreads, L)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int jj = 0; jj < JB; ++jj) {
+                const float c = (j0 + jj < k) ? s_coef[j0 + jj] : 0.f;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    qv[e].x = fmaf(-c, w[jj][e].x, qv[e].x);
+                    qv[e].y = fmaf(-c, w[jj][e].y, qv[e].y);
+                    qv[e].z = fmaf(-c, w[jj][e].z, qv[e].z);
+                    qv[e].w = fmaf(-c, w[jj][e].w, qv[e].w);
+                }
             }
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) st4(q, g0 + (int64_t)e * kThreads, L, qv[e]);
     }
     if (DOTS) {
-#pragma unroll 4
-        for (int j = 0; j < k; ++j) {
-            const float *Wj = W + (size_t)j * ldw;
-            float s = 0.f;
+        for (int j0 = 0; j0 < k; j0 += JB) {
+            float4 w[JB][E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) s += dot4(ld4(Wj, g0 + (int64_t)e * kThreads, L), qv[e]);
-            s = warp_sum(s);
-            if (lane == 0) s_w[warp * nred + j] = s;
+            for (int jj = 0; jj < JB; ++jj) {
+                const float *Wj = W + (size_t)(j0 + jj) * ldw;
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    w[jj][e] = (j0 + jj < k) ? ld4(Wj, g0 + (int64_t)e * kThreads, L)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int jj = 0; jj < JB; ++jj) {
+                float sj = 0.f;
+#pragma unroll
+                for (int e = 0; e < E; ++e) sj += dot4(w[jj][e], qv[e]);
+                sj = warp_sum(sj);
+                if (lane == 0 && j0 + jj < k) s_w[warp * nred + j0 + jj] = sj;
+            }
         }
     }
     if (NORM) {
@@ -177,7 +258,7 @@ __global__ void scale_kernel(const float *q, const double *__restrict__ nrm2,
 
 // out = base + sum_j y_j W_j.
 template <int E>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 gemv_kernel(const float *__restrict__ W, int64_t ldw, int k, const double *__restrict__ y,
             const float *__restrict__ base, float *__restrict__ out, int64_t L) {
     extern __shared__ float s_y[];
@@ -188,26 +269,14 @@ gemv_kernel(const float *__restrict__ W, int64_t ldw, int k, const double *__res
 #pragma unroll
     for (int e = 0; e < E; ++e)
         acc[e] = base ? ld4(base, g0 + (int64_t)e * kThreads, L) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-    for (int j = 0; j < k; ++j) {
-        const float c = s_y[j];
-        const float *Wj = W + (size_t)j * ldw;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const float4 w = ld4(Wj, g0 + (int64_t)e * kThreads, L);
-            acc[e].x = fmaf(c, w.x, acc[e].x);
-            acc[e].y = fmaf(c, w.y, acc[e].y);
-            acc[e].z = fmaf(c, w.z, acc[e].z);
-            acc[e].w = fmaf(c, w.w, acc[e].w);
-        }
-    }
+    accumulate_batched<E>(W, ldw, k, s_y, g0, L, acc);
 #pragma unroll
     for (int e = 0; e < E; ++e) st4(out, g0 + (int64_t)e * kThreads, L, acc[e]);
 }
 
 // res = ||base + sum_j y_j V_j||^2 (the vector itself is not stored).
 template <int E>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 gemv_norm2_kernel(const float *__restrict__ V, int64_t ldv, int k, const double *__restrict__ y,
                   const float *__restrict__ base, int64_t L, float *__restrict__ partials,
                   unsigned *__restrict__ counter, double *__restrict__ res) {
@@ -219,19 +288,7 @@ gemv_norm2_kernel(const float *__restrict__ V, int64_t ldv, int k, const double 
     float4 acc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) acc[e] = ld4(base, g0 + (int64_t)e * kThreads, L);
-#pragma unroll 4
-    for (int j = 0; j < k; ++j) {
-        const float c = s_y[j];
-        const float *Vj = V + (size_t)j * ldv;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const float4 w = ld4(Vj, g0 + (int64_t)e * kThreads, L);
-            acc[e].x = fmaf(c, w.x, acc[e].x);
-            acc[e].y = fmaf(c, w.y, acc[e].y);
-            acc[e].z = fmaf(c, w.z, acc[e].z);
-            acc[e].w = fmaf(c, w.w, acc[e].w);
-        }
-    }
+    accumulate_batched<E>(V, ldv, k, s_y, g0, L, acc);
     float s = 0.f;
 #pragma unroll
     for (int e = 0; e < E; ++e) s += dot4(acc[e], acc[e]);
@@ -242,7 +299,7 @@ gemv_norm2_kernel(const float *__restrict__ V, int64_t ldv, int k, const double 
 
 // out = a - c (or a), res = ||out||^2; out may be the same vector as a or c.
 template <int E>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 sub_norm2_kernel(const float *a, const float *c, float *out, int64_t L,
                  float *__restrict__ partials,
                  unsigned *__restrict__ counter, double *__restrict__ res) {
@@ -305,7 +362,7 @@ cudaError_t launch_pass(const float *W, int64_t ldw, int k, float *q, int64_t L,
 int ctg_red_grid(int64_t L, int *E_out) {
     const int64_t L4 = (L + 3) / 4;
     int E = 1;
-    while (E < 8 && (L4 + (int64_t)kThreads * E - 1) / ((int64_t)kThreads * E) > kTargetGrid) E *= 2;
+    while (E < kMaxE && (L4 + (int64_t)kThreads * E - 1) / ((int64_t)kThreads * E) > kTargetGrid) E *= 2;
     int64_t G = (L4 + (int64_t)kThreads * E - 1) / ((int64_t)kThreads * E);
     if (G < 1) G = 1;
     *E_out = E;
@@ -321,7 +378,7 @@ static int red_grid_max(int64_t L) {
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 size_t ctg_red_scratch_bytes(int64_t L, int kmax) {
-    const size_t G = (size_t)red_grid_max(L);
+    const size_t G = (size_t)padded_grid(red_grid_max(L));
     return align256(sizeof(float) * (size_t)(kmax + 2) * G) +
            2 * align256(sizeof(double) * (size_t)(kmax + 2)) + align256(sizeof(double) * 8) +
            align256(sizeof(unsigned) * 4);
@@ -329,7 +386,7 @@ size_t ctg_red_scratch_bytes(int64_t L, int kmax) {
 
 void ctg_red_scratch_carve(void *base, int64_t L, int kmax, RedScratch *rs) {
     char *p = static_cast<char *>(base);
-    const size_t G = (size_t)red_grid_max(L);
+    const size_t G = (size_t)padded_grid(red_grid_max(L));
     rs->partials = reinterpret_cast<float *>(p);
     p += align256(sizeof(float) * (size_t)(kmax + 2) * G);
     rs->h1 = reinterpret_cast<double *>(p);

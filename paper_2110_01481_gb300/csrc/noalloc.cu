@@ -16,7 +16,8 @@ namespace {
 // Largest problem the fixed scratch serves: k <= 256 basis vectors of
 // length L <= 4,980,736 (608 blocks x 256 threads x 8 float4 groups, which
 // covers a 2048 x 2048 image).  The reduction scratch for that size is
-// 635,136 bytes; the array is 640 KiB.
+// 635,136 bytes; the array is 640 KiB, and every call checks the exact
+// requirement against it.
 constexpr int kNoAllocMaxK = 256;
 constexpr int64_t kNoAllocMaxL = 4980736;
 constexpr size_t kNoAllocScratchBytes = 640 * 1024;
