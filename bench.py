@@ -42,6 +42,31 @@ WORKLOAD = (f"2D parallel beam, {N}x{N} random-ellipse phantom (20 ellipses), {N
 L2_BYTES = 129 * 2 ** 20
 
 
+def recorded_traffic(kernel: str, workload: str = "512x720x725"):
+    """DRAM bytes per launch of `kernel` from the ncu record in
+    profiles/traffic.txt, or None if there is none or the kernel's source
+    file has changed since it was captured."""
+    import hashlib
+    try:
+        lines = open(os.path.join(ROOT, "profiles", "traffic.txt")).read().splitlines()
+    except OSError:
+        return None
+    for line in lines:
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(tok.split("=", 1) for tok in line.split())
+        if kv.get("kernel") != kernel or kv.get("workload") != workload:
+            continue
+        try:
+            src = open(os.path.join(ROOT, kv["file"]), "rb").read()
+        except OSError:
+            return None
+        if hashlib.sha256(src).hexdigest()[: len(kv["source_sha256"])] != kv["source_sha256"]:
+            return None
+        return int(kv["dram_bytes"])
+    return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -349,7 +374,7 @@ def run_gpu(args):
                 "achieved": ach, "peak": L1_PEAK_GBS,
                 "peak_kind": "derived: L1/shared data path, 152 SM x 128 B/clk x 2.07 GHz; "
                              "8 B (one value/difference pair) per interpolation",
-                "frac": ach / L1_PEAK_GBS, "traffic": None,
+                "frac": ach / L1_PEAK_GBS, "traffic": recorded_traffic(kname),
                 "interpolations_per_launch": interp,
                 "launch_us": per_launch_s * 1e6}
     fwd_calls, back_calls = phases["forward"]["calls"], phases["back"]["calls"]
