@@ -224,6 +224,69 @@ def run_cgs2_only(args):
                           "algorithmic_GBps": gbs, "frac_of_hbm": gbs / peaks()[0]}))
 
 
+def run_precision(args):
+    """Krylov basis storage study on the 2048^2, 1800-angle, 2897-bin
+    workload (1% noise): BA-GMRES and AB-GMRES with the basis stored in FP32,
+    FP16 and BF16, run to fixed iteration counts; reports the relative error
+    against the ground truth, the relative difference to the FP32-basis
+    iterate, throughput and the workspace footprint."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2110_01481_gb300 as P
+    dev = torch.device("cuda", 0)
+    Np, Nap = 2048, 1800
+    Ndp = I.detector_count(Np)
+    g = P.Geometry(Np, Nap, Ndp)
+    xbar = I.random_ellipses(Np, 4000)
+    bbar = P.project(g, torch.tensor(xbar.ravel(), dtype=torch.float32, device=dev))
+    b_np, enorm = I.add_noise(bbar.double().cpu().numpy(), ETA, 4000)
+    b = torch.tensor(b_np, dtype=torch.float32, device=dev)
+    xn = np.linalg.norm(xbar)
+    ks = [int(k) for k in args.precision_k.split(",")]
+    hbm = peaks()[0]
+    ctx = P.Context.get(dev)
+    rows = []
+    for variant in ("ba", "ab"):
+        ref = {}
+        for basis in ("fp32", "fp16", "bf16"):
+            ws = torch.empty(P.workspace_bytes(g, variant, max(ks), basis), dtype=torch.uint8, device=dev)
+            for k in ks:
+                fn = P.ba_gmres if variant == "ba" else P.ab_gmres
+                fn(g, b, min(k, 2), workspace=ws, basis=basis)       # warm-up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = fn(g, b, k, workspace=ws, basis=basis)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                # the Arnoldi (CGS2) phase of the same solve, traced
+                ctx.timing(reset=True)
+                ctx.set_timing(True)
+                fn(g, b, k, workspace=ws, basis=basis)
+                torch.cuda.synchronize()
+                tm = ctx.timing(reset=True)
+                ctx.set_timing(False)
+                L = g.n if variant == "ba" else g.m
+                es = 4 if basis == "fp32" else 2
+                arn_bytes = sum(3.0 * kk * L * es + 24.0 * L for kk in range(1, r.iters + 1))
+                arn_gbs = arn_bytes / (tm["arnoldi"]["ms"] / 1e3) / 1e9
+                x = r.x.double().cpu().numpy()
+                if basis == "fp32":
+                    ref[k] = x
+                rows.append({"variant": variant, "basis": basis, "k": r.iters,
+                             "rel_err_vs_truth": float(np.linalg.norm(x - xbar.ravel()) / xn),
+                             "rel_diff_vs_fp32_basis": float(np.linalg.norm(x - ref[k]) / np.linalg.norm(ref[k])),
+                             "resnorm_over_noise": r.resnorm / enorm,
+                             "iterations_per_s": r.iters / dt,
+                             "arnoldi_ms": tm["arnoldi"]["ms"],
+                             "arnoldi_algorithmic_GBps": arn_gbs,
+                             "arnoldi_frac_of_hbm": arn_gbs / hbm,
+                             "workspace_GB": ws.numel() / 1e9})
+                print(json.dumps(rows[-1]), flush=True)
+            del ws
+            torch.cuda.empty_cache()
+
+
 def make_instance(P, torch, dev, seed):
     """Seeded phantom, b = A x_bar + e with the library's own A (the oracle is
     not used on the product path)."""
@@ -488,11 +551,16 @@ def main():
     ap.add_argument("--cgs2-only", action="store_true",
                     help="time only the large-basis Arnoldi (CGS2) step")
     ap.add_argument("--cgs2-k", type=int, default=100)
+    ap.add_argument("--precision", action="store_true",
+                    help="basis-storage study (FP32/FP16/BF16) on the 2048^2 workload")
+    ap.add_argument("--precision-k", default="25,50,100,200")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.cgs2_only:
         run_cgs2_only(args)
+    elif args.precision:
+        run_precision(args)
     else:
         run_gpu(args)
 

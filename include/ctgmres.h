@@ -55,7 +55,7 @@ enum {
 
 enum { CTG_AB = 0, CTG_BA = 1 };                       /* solver variant    */
 enum { CTG_STOP_MAXIT = 0, CTG_STOP_DP = 1, CTG_STOP_BREAKDOWN = 2 };
-enum { CTG_BASIS_FP32 = 0 };                           /* basis storage     */
+enum { CTG_BASIS_FP32 = 0, CTG_BASIS_BF16 = 1, CTG_BASIS_FP16 = 2 };  /* basis storage */
 
 /* 2D parallel-beam geometry (paper Sec. 6.1, Table 1).  Limits: 1 <= N <=
  * 16384, 1 <= n_angles, 1 <= n_det <= 65536, start and range integral
@@ -73,7 +73,10 @@ typedef struct {
 /* Solver options. */
 typedef struct {
     int32_t maxit;            /* iteration cap, >= 1                        */
-    int32_t basis_dtype;      /* CTG_BASIS_FP32                             */
+    int32_t basis_dtype;      /* CTG_BASIS_FP32, _BF16 or _FP16: element type
+                                 of the stored Krylov basis W; arithmetic is
+                                 FP32 (FP64 for reductions and the
+                                 Hessenberg problem) in every case         */
     double tau;               /* DP safety factor tau >= 1 (Sec. 6.4)       */
     double noise_norm;        /* ||e||; <= 0 disables the DP stop           */
 } ctg_opts;

@@ -20,7 +20,8 @@ CTG_ERR_TIMEOUT = -4
 CTG_ERR_WORKSPACE = -5
 CTG_AB, CTG_BA = 0, 1
 CTG_STOP_MAXIT, CTG_STOP_DP, CTG_STOP_BREAKDOWN = 0, 1, 2
-CTG_BASIS_FP32 = 0
+CTG_BASIS_FP32, CTG_BASIS_BF16, CTG_BASIS_FP16 = 0, 1, 2
+BASIS = {"fp32": CTG_BASIS_FP32, "bf16": CTG_BASIS_BF16, "fp16": CTG_BASIS_FP16}
 
 
 class CtgGeom(ctypes.Structure):

@@ -121,23 +121,28 @@ def backproject(g: Geometry, b: torch.Tensor, out: Optional[torch.Tensor] = None
     return out
 
 
-def _opts(maxit: int, tau: float, noise_norm: Optional[float]) -> nat.CtgOpts:
-    return nat.CtgOpts(int(maxit), nat.CTG_BASIS_FP32, float(tau),
+_TORCH_BASIS = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}
+
+
+def _opts(maxit: int, tau: float, noise_norm: Optional[float], basis: str = "fp32") -> nat.CtgOpts:
+    if basis not in nat.BASIS:
+        raise ValueError(f"basis must be one of {sorted(nat.BASIS)}")
+    return nat.CtgOpts(int(maxit), nat.BASIS[basis], float(tau),
                        float(noise_norm) if noise_norm else 0.0)
 
 
-def workspace_bytes(g: Geometry, variant: str, maxit: int) -> int:
+def workspace_bytes(g: Geometry, variant: str, maxit: int, basis: str = "fp32") -> int:
     """Device bytes one solve needs (0 if the arguments are invalid)."""
     v = nat.CTG_AB if variant == "ab" else nat.CTG_BA
     return int(nat.lib().ctg_workspace_bytes(ctypes.byref(g.c()), v,
-                                             ctypes.byref(_opts(maxit, 1.0, None))))
+                                             ctypes.byref(_opts(maxit, 1.0, None, basis))))
 
 
-def workspace_layout(g: Geometry, variant: str, maxit: int) -> nat.CtgLayout:
+def workspace_layout(g: Geometry, variant: str, maxit: int, basis: str = "fp32") -> nat.CtgLayout:
     v = nat.CTG_AB if variant == "ab" else nat.CTG_BA
     out = nat.CtgLayout()
     nat.check(nat.lib().ctg_workspace_layout(ctypes.byref(g.c()), v,
-                                             ctypes.byref(_opts(maxit, 1.0, None)),
+                                             ctypes.byref(_opts(maxit, 1.0, None, basis)),
                                              ctypes.byref(out)), "ctg_workspace_layout")
     return out
 
@@ -151,18 +156,22 @@ class SolveResult:
     rho: float                # GMRES residual of the last step
     history: list = field(default_factory=list)
     workspace: Optional[torch.Tensor] = None
+    basis_type: str = "fp32"
 
     def basis(self, g: Geometry, variant: str, maxit: int) -> torch.Tensor:
-        """View of the final Krylov basis W (iters+1 vectors) in the workspace."""
-        ly = workspace_layout(g, variant, maxit)
+        """View of the final Krylov basis W (iters+1 vectors, stored element
+        type) in the workspace."""
+        ly = workspace_layout(g, variant, maxit, self.basis_type)
         L = g.m if variant == "ab" else g.n
-        f = self.workspace.view(torch.float32)
-        W = f[ly.off_w // 4: ly.off_w // 4 + ly.ld_w * (maxit + 1)].view(maxit + 1, ly.ld_w)
+        dt = _TORCH_BASIS[self.basis_type]
+        es = torch.empty(0, dtype=dt).element_size()
+        nbytes = es * ly.ld_w * (maxit + 1)
+        W = self.workspace[ly.off_w: ly.off_w + nbytes].view(dt).view(maxit + 1, ly.ld_w)
         return W[: self.iters + 1, :L]
 
     def hessenberg(self, g: Geometry, variant: str, maxit: int) -> torch.Tensor:
         """The (iters+1) x iters Hessenberg matrix H_k (FP64) from the workspace."""
-        ly = workspace_layout(g, variant, maxit)
+        ly = workspace_layout(g, variant, maxit, self.basis_type)
         d = self.workspace[ly.off_h: ly.off_h + 8 * (maxit + 1) * maxit].view(torch.float64)
         H = d.view(maxit, maxit + 1).t()          # column-major storage
         return H[: self.iters + 1, : self.iters]
@@ -171,15 +180,15 @@ class SolveResult:
 def _solve(fn, variant: str, g: Geometry, b: torch.Tensor, maxit: int,
            x0: Optional[torch.Tensor], tau: float, noise_norm: Optional[float],
            out: Optional[torch.Tensor], workspace: Optional[torch.Tensor],
-           keep_workspace: bool) -> SolveResult:
+           keep_workspace: bool, basis: str = "fp32") -> SolveResult:
     dev = b.device
     pb = _dev_ptr(b, g.m, "b")
     px0 = _dev_ptr(x0, g.n, "x0") if x0 is not None else None
     if out is None:
         out = torch.empty(g.n, device=dev, dtype=torch.float32)
     px = _dev_ptr(out, g.n, "out")
-    o = _opts(maxit, tau, noise_norm)
-    need = workspace_bytes(g, variant, maxit)
+    o = _opts(maxit, tau, noise_norm, basis)
+    need = workspace_bytes(g, variant, maxit, basis)
     if need == 0:
         raise nat.CtgError(nat.CTG_ERR_INVALID_ARG, f"ctg_{variant}_gmres")
     if workspace is None and keep_workspace:
@@ -194,24 +203,25 @@ def _solve(fn, variant: str, g: Geometry, b: torch.Tensor, maxit: int,
         nat.check(fn(ctx.handle, ctypes.byref(g.c()), pb, px0, px, ctypes.byref(o), pws, nws,
                      ctypes.byref(info), _stream(dev)), f"ctg_{variant}_gmres")
     return SolveResult(out, info.iters, info.stop_reason, info.resnorm, info.rho,
-                       list(hist[: info.iters + 1]), workspace)
+                       list(hist[: info.iters + 1]), workspace, basis)
 
 
 def ab_gmres(g: Geometry, b: torch.Tensor, maxit: int, x0=None, tau: float = 1.0,
              noise_norm: Optional[float] = None, out=None, workspace=None,
-             keep_workspace: bool = False) -> SolveResult:
+             keep_workspace: bool = False, basis: str = "fp32") -> SolveResult:
     """AB-GMRES (paper Sec. 2) with the discrepancy-principle stop when
-    noise_norm is given (Sec. 6.4)."""
+    noise_norm is given (Sec. 6.4).  basis: storage type of the Krylov basis
+    ("fp32", "bf16" or "fp16"; arithmetic stays FP32/FP64)."""
     return _solve(nat.lib().ctg_ab_gmres, "ab", g, b, maxit, x0, tau, noise_norm, out,
-                  workspace, keep_workspace)
+                  workspace, keep_workspace, basis)
 
 
 def ba_gmres(g: Geometry, b: torch.Tensor, maxit: int, x0=None, tau: float = 1.0,
              noise_norm: Optional[float] = None, out=None, workspace=None,
-             keep_workspace: bool = False) -> SolveResult:
+             keep_workspace: bool = False, basis: str = "fp32") -> SolveResult:
     """BA-GMRES (paper Sec. 2); same conventions as ``ab_gmres``."""
     return _solve(nat.lib().ctg_ba_gmres, "ba", g, b, maxit, x0, tau, noise_norm, out,
-                  workspace, keep_workspace)
+                  workspace, keep_workspace, basis)
 
 
 def cgs2(W: torch.Tensor, k: int, q: torch.Tensor, w_out: Optional[torch.Tensor] = None,

@@ -38,7 +38,7 @@ bool geom_valid(const ctg_geom *g) {
 
 bool opts_valid(const ctg_opts *o) {
     if (!o || o->maxit < 1 || o->maxit > kMaxIt) return false;
-    if (o->basis_dtype != CTG_BASIS_FP32) return false;
+    if (ctg_basis_bytes(o->basis_dtype) == 0) return false;
     if (!std::isfinite(o->tau) || !std::isfinite(o->noise_norm)) return false;
     if (o->noise_norm > 0.0 && !(o->tau > 0.0)) return false;
     return true;
@@ -120,6 +120,8 @@ struct WsLayout {
     size_t off_t, ld_t, off_r0m;   // BA only: T = A W_k and b - A x0
     int64_t L, n, m;
     int kmax;
+    int dtype;      // basis element type
+    size_t es;      // basis element bytes
 };
 
 bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) {
@@ -130,10 +132,12 @@ bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) 
     ly->m = m;
     ly->L = L;
     ly->kmax = o->maxit;
+    ly->dtype = o->basis_dtype;
+    ly->es = ctg_basis_bytes(o->basis_dtype);
     ly->ld_w = round_up((size_t)L, 64);
     size_t off = 0;
     ly->off_w = off;
-    off = align256(off + sizeof(float) * ly->ld_w * (size_t)(o->maxit + 1));
+    off = align256(off + ly->es * ly->ld_w * (size_t)(o->maxit + 1));
     ly->off_h = off;
     off = align256(off + sizeof(double) * (size_t)(o->maxit + 1) * (size_t)o->maxit);
     ly->off_pad = off;
@@ -343,8 +347,8 @@ struct SolveCtx {
     char *ws;
     RedScratch rs;
     cudaStream_t st;
-    float *W() const { return reinterpret_cast<float *>(ws + ly.off_w); }
-    float *Wcol(int j) const { return W() + (size_t)j * ly.ld_w; }
+    void *W() const { return ws + ly.off_w; }
+    void *Wcol(int j) const { return ws + ly.off_w + (size_t)j * ly.ld_w * ly.es; }
     double *Hcol(int k) const {   // column k (1-based)
         return reinterpret_cast<double *>(ws + ly.off_h) + (size_t)(k - 1) * (ly.kmax + 1);
     }
@@ -356,26 +360,27 @@ struct SolveCtx {
     float *Tcol(int j) const { return reinterpret_cast<float *>(ws + ly.off_t) + (size_t)j * ly.ld_t; }
     float *r0m() const { return reinterpret_cast<float *>(ws + ly.off_r0m); }
 
-    cudaError_t forward(const float *x, float *b) const {
+    cudaError_t forward(const void *x, float *b, int xtype = CTG_BASIS_FP32) const {
         return traced(ctx, 0, 2, st, [&] {
-            cudaError_t e = ctg_launch_pad(x, pad(), g->N, ge->pl, st);
+            cudaError_t e = ctg_launch_pad(x, xtype, pad(), g->N, ge->pl, st);
             if (e != cudaSuccess) return e;
             return ctg_launch_forward(pad(), g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, b, st);
         });
     }
-    cudaError_t back(const float *b, const float *add, float *x) const {
+    cudaError_t back(const void *b, const float *add, float *x, int btype = CTG_BASIS_FP32) const {
         return traced(ctx, 1, 1, st, [&] {
-            return ctg_launch_back(b, g->N, g->n_angles, g->n_det, ge->back, ge->back_window, add, x, st);
+            return ctg_launch_back(b, btype, g->N, g->n_angles, g->n_det, ge->back, ge->back_window,
+                                   add, x, st);
         });
     }
     cudaError_t cgs2(int64_t L, int k, float *q) const {
         return traced(ctx, 2, k > 0 ? 4 : 2, st, [&] {
-            return ctg_cgs2_step(W(), ly.ld_w, L, k, q, Wcol(k), Hcol(k), rs, st);
+            return ctg_cgs2_step(W(), ly.dtype, ly.ld_w, L, k, q, Wcol(k), Hcol(k), rs, st);
         });
     }
     cudaError_t gemv(int64_t L, int k, const float *base, float *out) const {
         return traced(ctx, 3, 1, st, [&] {
-            return ctg_gemv(W(), ly.ld_w, L, k, ydev(), base, out, st);
+            return ctg_gemv(W(), ly.dtype, ly.ld_w, L, k, ydev(), base, out, st);
         });
     }
     cudaError_t gemv_norm2(const float *V, size_t ldv, int64_t L, int k, const float *base,
@@ -387,8 +392,9 @@ struct SolveCtx {
     cudaError_t sub_norm2(const float *a, const float *c, float *out, int64_t L, double *res) const {
         return traced(ctx, 3, 1, st, [&] { return ctg_sub_norm2(a, c, out, L, res, rs, st); });
     }
-    cudaError_t scale(const float *v, const double *nrm2, float *out, int64_t L) const {
-        return traced(ctx, 3, 1, st, [&] { return ctg_scale(v, nrm2, out, L, st); });
+    // out (a basis vector) = v / sqrt(*nrm2), rounded to the basis type
+    cudaError_t scale(const float *v, const double *nrm2, void *out, int64_t L) const {
+        return traced(ctx, 3, 1, st, [&] { return ctg_scale(v, nrm2, out, ly.dtype, L, st); });
     }
     // copy `count` doubles from the device to the pinned area and wait
     // pinned staging outside the pipeline ring (which queued copies of
@@ -522,12 +528,12 @@ int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
     const int64_t m = sc.ly.m;
     const bool dp = o->noise_norm > 0.0;
     const double target = dp ? o->tau * o->noise_norm : 0.0;
-    // r0 = b - A x0, unnormalised into w_1's slot; beta = ||r0||
+    // r0 = b - A x0 (FP32, in vm0); beta = ||r0||
     if (x0) {
         CTG_CK(sc.forward(x0, sc.vm0()));
-        CTG_CK(sc.sub_norm2(b, sc.vm0(), sc.Wcol(0), m, sc.rs.scal + 2));
+        CTG_CK(sc.sub_norm2(b, sc.vm0(), sc.vm0(), m, sc.rs.scal + 2));
     } else {
-        CTG_CK(sc.sub_norm2(b, nullptr, sc.Wcol(0), m, sc.rs.scal + 2));
+        CTG_CK(sc.sub_norm2(b, nullptr, sc.vm0(), m, sc.rs.scal + 2));
     }
     double *hp;
     int rc = sc.fetch(sc.rs.scal + 2, 1, &hp);
@@ -540,11 +546,11 @@ int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
         info->stop_reason = beta == 0.0 && !(dp && beta <= target) ? CTG_STOP_BREAKDOWN : CTG_STOP_DP;
         return copy_x0(sc, x0, x);
     }
-    CTG_CK(sc.scale(sc.Wcol(0), sc.rs.scal + 2, sc.Wcol(0), m));
+    CTG_CK(sc.scale(sc.vm0(), sc.rs.scal + 2, sc.Wcol(0), m));   // w_1 = r0 / beta
     if ((rc = ensure_events(sc.ctx))) return rc;
     Pipeline pl{sc, o->maxit, sc.ctx->ev_h, sc.ctx->ev_r};
     auto enqueue = [&](int kk) -> int {
-        CTG_CK(sc.back(sc.Wcol(kk - 1), nullptr, sc.vn0()));       // t = B w_k
+        CTG_CK(sc.back(sc.Wcol(kk - 1), nullptr, sc.vn0(), sc.ly.dtype));   // t = B w_k
         CTG_CK(sc.forward(sc.vn0(), sc.vm0()));                    // q = A t
         CTG_CK(sc.cgs2(m, kk, sc.vm0()));
         return pl.after_step(kk);
@@ -599,8 +605,8 @@ int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
     } else {
         CTG_CK(sc.sub_norm2(b, nullptr, sc.r0m(), m, sc.rs.scal + 4));
     }
-    CTG_CK(sc.back(sc.r0m(), nullptr, sc.Wcol(0)));
-    CTG_CK(sc.sub_norm2(sc.Wcol(0), nullptr, nullptr, n, sc.rs.scal + 2));
+    CTG_CK(sc.back(sc.r0m(), nullptr, sc.vn0()));
+    CTG_CK(sc.sub_norm2(sc.vn0(), nullptr, nullptr, n, sc.rs.scal + 2));
     double *hp;
     int rc = sc.fetch(sc.rs.scal + 2, 3, &hp);
     if (rc) return rc;
@@ -612,11 +618,11 @@ int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
         info->stop_reason = beta == 0.0 && !(dp && res0 <= target) ? CTG_STOP_BREAKDOWN : CTG_STOP_DP;
         return copy_x0(sc, x0, x);
     }
-    CTG_CK(sc.scale(sc.Wcol(0), sc.rs.scal + 2, sc.Wcol(0), n));
+    CTG_CK(sc.scale(sc.vn0(), sc.rs.scal + 2, sc.Wcol(0), n));   // w_1 = r0 / beta
     if ((rc = ensure_events(sc.ctx))) return rc;
     Pipeline pl{sc, o->maxit, sc.ctx->ev_h, sc.ctx->ev_r};
     auto enqueue = [&](int kk) -> int {
-        CTG_CK(sc.forward(sc.Wcol(kk - 1), sc.Tcol(kk - 1)));      // t = A w_k, kept in T
+        CTG_CK(sc.forward(sc.Wcol(kk - 1), sc.Tcol(kk - 1), sc.ly.dtype));  // t = A w_k, kept in T
         CTG_CK(sc.back(sc.Tcol(kk - 1), nullptr, sc.vn0()));       // q = B t
         CTG_CK(sc.cgs2(n, kk, sc.vn0()));
         return pl.after_step(kk);
@@ -741,7 +747,7 @@ int ctg_project(ctg_ctx *ctx, const ctg_geom *g, const float *x_dev, float *b_de
         CTG_CK(cudaMemset(ge->pad, 0, bytes));
     }
     CTG_CK(traced(ctx, 0, 2, st, [&] {
-        cudaError_t e = ctg_launch_pad(x_dev, ge->pad, g->N, ge->pl, st);
+        cudaError_t e = ctg_launch_pad(x_dev, CTG_BASIS_FP32, ge->pad, g->N, ge->pl, st);
         if (e != cudaSuccess) return e;
         return ctg_launch_forward(ge->pad, g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, b_dev, st);
     }));
@@ -755,7 +761,8 @@ int ctg_backproject(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, float *
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CTG_CK(traced(ctx, 1, 1, st, [&] {
-        return ctg_launch_back(b_dev, g->N, g->n_angles, g->n_det, ge->back, ge->back_window,
+        return ctg_launch_back(b_dev, CTG_BASIS_FP32, g->N, g->n_angles, g->n_det, ge->back,
+                               ge->back_window,
                                nullptr, x_dev, st);
     }));
     return CTG_OK;
@@ -805,7 +812,7 @@ int ctg_cgs2(const float *W_dev, int64_t ld_w, int64_t L, int32_t k, float *q_de
     ctg_red_scratch_carve(scratch_dev, L, k + 1, &rs);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CTG_CK(cudaMemsetAsync(rs.counter, 0, 4 * sizeof(unsigned), st));
-    CTG_CK(ctg_cgs2_step(W_dev, ld_w, L, k, q_dev, w_out_dev, h_out_dev, rs, st));
+    CTG_CK(ctg_cgs2_step(W_dev, CTG_BASIS_FP32, ld_w, L, k, q_dev, w_out_dev, h_out_dev, rs, st));
     return CTG_OK;
 }
 

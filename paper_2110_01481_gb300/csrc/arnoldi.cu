@@ -11,6 +11,9 @@
 // into per-block partials, and the last block to finish (atomic ticket, no
 // waiting) sums the partials in a fixed order in FP64, so results are
 // deterministic run to run.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "ctg_internal.cuh"
 
 namespace {
@@ -49,6 +52,72 @@ __device__ __forceinline__ void st4(float *p, int64_t g, int64_t L, float4 v) {
     if (i + 1 < L) p[i + 1] = v.y;
     if (i + 2 < L) p[i + 2] = v.z;
 }
+
+// Basis vectors may be stored in FP32, BF16 or FP16; every kernel converts
+// them to FP32 on use and accumulates in FP32 (reductions in FP64).  A
+// float4 group of the FP32 work vector pairs with one 8-byte load of a
+// 16-bit basis vector.
+// Raw (unconverted) loads, so that a batch of loads is issued before any
+// conversion consumes one: FP32 groups stay float4, 16-bit groups are
+// loaded as uint2 and converted only when used.
+template <typename T> struct RawOf { using type = uint2; };
+template <> struct RawOf<float> { using type = float4; };
+
+__device__ __forceinline__ float4 ldraw(const float *p, int64_t g, int64_t L) { return ld4(p, g, L); }
+
+template <typename H>
+__device__ __forceinline__ uint2 ldraw16(const H *p, int64_t g, int64_t L) {
+    const int64_t i = 4 * g;
+    if (i + 3 < L) return __ldg(reinterpret_cast<const uint2 *>(p + i));
+    unsigned short h[4] = {0, 0, 0, 0};
+    const unsigned short *ps = reinterpret_cast<const unsigned short *>(p);
+    if (i < L) h[0] = ps[i];
+    if (i + 1 < L) h[1] = ps[i + 1];
+    if (i + 2 < L) h[2] = ps[i + 2];
+    return make_uint2((unsigned)h[0] | ((unsigned)h[1] << 16), (unsigned)h[2] | ((unsigned)h[3] << 16));
+}
+__device__ __forceinline__ uint2 ldraw(const __nv_bfloat16 *p, int64_t g, int64_t L) { return ldraw16(p, g, L); }
+__device__ __forceinline__ uint2 ldraw(const __half *p, int64_t g, int64_t L) { return ldraw16(p, g, L); }
+
+template <typename T> __device__ __forceinline__ float4 cvt4(float4 r) { return r; }
+template <typename T> __device__ __forceinline__ float4 cvt4(uint2 u);
+template <> __device__ __forceinline__ float4 cvt4<__nv_bfloat16>(uint2 u) {
+    // a bf16 is the top half of an FP32
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+}
+template <> __device__ __forceinline__ float4 cvt4<__half>(uint2 u) {
+    __half2 a, b;
+    memcpy(&a, &u.x, 4);
+    memcpy(&b, &u.y, 4);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+__device__ __forceinline__ void stw4(float *p, int64_t g, int64_t L, float4 v) { st4(p, g, L, v); }
+
+template <typename H>
+__device__ __forceinline__ H to16(float x) {
+    if constexpr (std::is_same<H, __nv_bfloat16>::value) return __float2bfloat16_rn(x);
+    else return __float2half_rn(x);
+}
+
+template <typename H>
+__device__ __forceinline__ void stw4_16(H *p, int64_t g, int64_t L, float4 v) {
+    const int64_t i = 4 * g;
+    if (i + 3 < L) {
+        H h[4] = {to16<H>(v.x), to16<H>(v.y), to16<H>(v.z), to16<H>(v.w)};
+        uint2 u;
+        memcpy(&u, h, 8);
+        *reinterpret_cast<uint2 *>(p + i) = u;
+        return;
+    }
+    if (i < L) p[i] = to16<H>(v.x);
+    if (i + 1 < L) p[i + 1] = to16<H>(v.y);
+    if (i + 2 < L) p[i + 2] = to16<H>(v.z);
+}
+__device__ __forceinline__ void stw4(__nv_bfloat16 *p, int64_t g, int64_t L, float4 v) { stw4_16(p, g, L, v); }
+__device__ __forceinline__ void stw4(__half *p, int64_t g, int64_t L, float4 v) { stw4_16(p, g, L, v); }
 
 __device__ __forceinline__ float dot4(float4 a, float4 b) {
     return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
@@ -121,32 +190,37 @@ __device__ void block_reduce_finish(float *s_w, int nred, float *__restrict__ pa
     if (tid == 0) *counter = 0u;
 }
 
+// Vectors per load batch: 128 bytes of basis data in flight per thread.
+template <typename T, int E>
+__host__ __device__ constexpr int batch_vectors() {
+    return (int)(128 / (4 * sizeof(T) * E)) > 0 ? (int)(128 / (4 * sizeof(T) * E)) : 1;
+}
+
 // acc += sum_j c_j V_j over this thread's E float4 groups, loads issued in
-// batches of JB vectors so that 8 float4 per thread are in flight.
-template <int E>
-__device__ __forceinline__ void accumulate_batched(const float *__restrict__ V, int64_t ldv, int k,
+// batches of JB vectors so that 128 bytes per thread are in flight.
+template <typename T, int E>
+__device__ __forceinline__ void accumulate_batched(const T *__restrict__ V, int64_t ldv, int k,
                                                    const float *c, int64_t g0, int64_t L,
                                                    float4 (&acc)[E]) {
-    constexpr int JB = 8 / E > 0 ? 8 / E : 1;
+    constexpr int JB = batch_vectors<T, E>();
     for (int j0 = 0; j0 < k; j0 += JB) {
-        float4 w[JB][E];
+        typename RawOf<T>::type w[JB][E];
 #pragma unroll
         for (int jj = 0; jj < JB; ++jj) {
-            const float *Vj = V + (size_t)(j0 + jj) * ldv;
+            const T *Vj = V + (size_t)min(j0 + jj, k - 1) * ldv;   // see cgs_pass_kernel
 #pragma unroll
-            for (int e = 0; e < E; ++e)
-                w[jj][e] = (j0 + jj < k) ? ld4(Vj, g0 + (int64_t)e * kThreads, L)
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int e = 0; e < E; ++e) w[jj][e] = ldraw(Vj, g0 + (int64_t)e * kThreads, L);
         }
 #pragma unroll
         for (int jj = 0; jj < JB; ++jj) {
             const float cj = (j0 + jj < k) ? c[j0 + jj] : 0.f;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                acc[e].x = fmaf(cj, w[jj][e].x, acc[e].x);
-                acc[e].y = fmaf(cj, w[jj][e].y, acc[e].y);
-                acc[e].z = fmaf(cj, w[jj][e].z, acc[e].z);
-                acc[e].w = fmaf(cj, w[jj][e].w, acc[e].w);
+                const float4 wf = cvt4<T>(w[jj][e]);
+                acc[e].x = fmaf(cj, wf.x, acc[e].x);
+                acc[e].y = fmaf(cj, wf.y, acc[e].y);
+                acc[e].z = fmaf(cj, wf.z, acc[e].z);
+                acc[e].w = fmaf(cj, wf.w, acc[e].w);
             }
         }
     }
@@ -156,9 +230,9 @@ __device__ __forceinline__ void accumulate_batched(const float *__restrict__ V, 
 //   UPDATE: q -= sum_j coef_j W_j (coef: k doubles)
 //   DOTS:   red_out[j] = W_j^T q (after the update)      j < k
 //   NORM:   red_out[DOTS ? k : 0] = q^T q (after the update)
-template <int E, bool UPDATE, bool DOTS, bool NORM>
+template <typename T, int E, bool UPDATE, bool DOTS, bool NORM>
 __global__ void __launch_bounds__(kThreads, 2)
-cgs_pass_kernel(const float *__restrict__ W, int64_t ldw, int k, float *__restrict__ q,
+cgs_pass_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict__ q,
                 int64_t L, const double *__restrict__ coef, float *__restrict__ partials,
                 unsigned *__restrict__ counter, double *__restrict__ red_out) {
     extern __shared__ float smem[];
@@ -172,31 +246,33 @@ cgs_pass_kernel(const float *__restrict__ W, int64_t ldw, int k, float *__restri
     float4 qv[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) qv[e] = ld4_rw(q, g0 + (int64_t)e * kThreads, L);
-    // Loads are issued in batches of JB vectors (JB * E = 8 float4 per
-    // thread in flight) before any of them is used, so each thread keeps
-    // 128 bytes of HBM reads outstanding.
-    constexpr int JB = 8 / E > 0 ? 8 / E : 1;
+    // Loads are issued in batches of JB vectors before any of them is used,
+    // so each thread keeps 128 bytes of HBM reads outstanding (8 float4 of
+    // an FP32 basis, 16 half-width groups of a 16-bit one).
+    constexpr int JB = batch_vectors<T, E>();
     if (UPDATE) {
         __syncthreads();
         for (int j0 = 0; j0 < k; j0 += JB) {
-            float4 w[JB][E];
+            typename RawOf<T>::type w[JB][E];
 #pragma unroll
             for (int jj = 0; jj < JB; ++jj) {
-                const float *Wj = W + (size_t)(j0 + jj) * ldw;
+                // past the last vector the load repeats vector k-1 (a cache
+                // hit) and its coefficient / dot is dropped, so every load of
+                // the batch is unconditional and issued before any use
+                const T *Wj = W + (size_t)min(j0 + jj, k - 1) * ldw;
 #pragma unroll
-                for (int e = 0; e < E; ++e)
-                    w[jj][e] = (j0 + jj < k) ? ld4(Wj, g0 + (int64_t)e * kThreads, L)
-                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int e = 0; e < E; ++e) w[jj][e] = ldraw(Wj, g0 + (int64_t)e * kThreads, L);
             }
 #pragma unroll
             for (int jj = 0; jj < JB; ++jj) {
                 const float c = (j0 + jj < k) ? s_coef[j0 + jj] : 0.f;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    qv[e].x = fmaf(-c, w[jj][e].x, qv[e].x);
-                    qv[e].y = fmaf(-c, w[jj][e].y, qv[e].y);
-                    qv[e].z = fmaf(-c, w[jj][e].z, qv[e].z);
-                    qv[e].w = fmaf(-c, w[jj][e].w, qv[e].w);
+                    const float4 wf = cvt4<T>(w[jj][e]);
+                    qv[e].x = fmaf(-c, wf.x, qv[e].x);
+                    qv[e].y = fmaf(-c, wf.y, qv[e].y);
+                    qv[e].z = fmaf(-c, wf.z, qv[e].z);
+                    qv[e].w = fmaf(-c, wf.w, qv[e].w);
                 }
             }
         }
@@ -205,20 +281,18 @@ cgs_pass_kernel(const float *__restrict__ W, int64_t ldw, int k, float *__restri
     }
     if (DOTS) {
         for (int j0 = 0; j0 < k; j0 += JB) {
-            float4 w[JB][E];
+            typename RawOf<T>::type w[JB][E];
 #pragma unroll
             for (int jj = 0; jj < JB; ++jj) {
-                const float *Wj = W + (size_t)(j0 + jj) * ldw;
+                const T *Wj = W + (size_t)min(j0 + jj, k - 1) * ldw;
 #pragma unroll
-                for (int e = 0; e < E; ++e)
-                    w[jj][e] = (j0 + jj < k) ? ld4(Wj, g0 + (int64_t)e * kThreads, L)
-                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int e = 0; e < E; ++e) w[jj][e] = ldraw(Wj, g0 + (int64_t)e * kThreads, L);
             }
 #pragma unroll
             for (int jj = 0; jj < JB; ++jj) {
                 float sj = 0.f;
 #pragma unroll
-                for (int e = 0; e < E; ++e) sj += dot4(w[jj][e], qv[e]);
+                for (int e = 0; e < E; ++e) sj += dot4(cvt4<T>(w[jj][e]), qv[e]);
                 sj = warp_sum(sj);
                 if (lane == 0 && j0 + jj < k) s_w[warp * nred + j0 + jj] = sj;
             }
@@ -236,9 +310,10 @@ cgs_pass_kernel(const float *__restrict__ W, int64_t ldw, int k, float *__restri
 
 // w_out = q / sqrt(nrm2) (0 if nrm2 == 0); block 0 also assembles the
 // Hessenberg column h_out[0..k-1] = h1 + h2, h_out[k] = sqrt(nrm2).
-// q and w_out may be the same vector.
+// q and w_out may be the same vector (FP32 storage only).
+template <typename T>
 __global__ void scale_kernel(const float *q, const double *__restrict__ nrm2,
-                             float *w_out, int64_t L, int k,
+                             T *w_out, int64_t L, int k,
                              const double *__restrict__ h1, const double *__restrict__ h2,
                              double *__restrict__ h_out) {
     const double nn = *nrm2;
@@ -248,7 +323,7 @@ __global__ void scale_kernel(const float *q, const double *__restrict__ nrm2,
          g += (int64_t)gridDim.x * blockDim.x) {
         float4 v = ld4_rw(q, g, L);
         v.x *= inv; v.y *= inv; v.z *= inv; v.w *= inv;
-        st4(w_out, g, L, v);
+        stw4(w_out, g, L, v);
     }
     if (h_out != nullptr && blockIdx.x == 0) {
         for (int j = threadIdx.x; j < k; j += blockDim.x) h_out[j] = h1[j] + h2[j];
@@ -257,9 +332,9 @@ __global__ void scale_kernel(const float *q, const double *__restrict__ nrm2,
 }
 
 // out = base + sum_j y_j W_j.
-template <int E>
+template <typename T, int E>
 __global__ void __launch_bounds__(kThreads, 2)
-gemv_kernel(const float *__restrict__ W, int64_t ldw, int k, const double *__restrict__ y,
+gemv_kernel(const T *__restrict__ W, int64_t ldw, int k, const double *__restrict__ y,
             const float *__restrict__ base, float *__restrict__ out, int64_t L) {
     extern __shared__ float s_y[];
     for (int j = threadIdx.x; j < k; j += kThreads) s_y[j] = (float)y[j];
@@ -269,7 +344,7 @@ gemv_kernel(const float *__restrict__ W, int64_t ldw, int k, const double *__res
 #pragma unroll
     for (int e = 0; e < E; ++e)
         acc[e] = base ? ld4(base, g0 + (int64_t)e * kThreads, L) : make_float4(0.f, 0.f, 0.f, 0.f);
-    accumulate_batched<E>(W, ldw, k, s_y, g0, L, acc);
+    accumulate_batched<T, E>(W, ldw, k, s_y, g0, L, acc);
 #pragma unroll
     for (int e = 0; e < E; ++e) st4(out, g0 + (int64_t)e * kThreads, L, acc[e]);
 }
@@ -288,7 +363,7 @@ gemv_norm2_kernel(const float *__restrict__ V, int64_t ldv, int k, const double 
     float4 acc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) acc[e] = ld4(base, g0 + (int64_t)e * kThreads, L);
-    accumulate_batched<E>(V, ldv, k, s_y, g0, L, acc);
+    accumulate_batched<float, E>(V, ldv, k, s_y, g0, L, acc);
     float s = 0.f;
 #pragma unroll
     for (int e = 0; e < E; ++e) s += dot4(acc[e], acc[e]);
@@ -329,8 +404,8 @@ cudaError_t ensure_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <bool UPDATE, bool DOTS, bool NORM>
-cudaError_t launch_pass(const float *W, int64_t ldw, int k, float *q, int64_t L,
+template <typename T, bool UPDATE, bool DOTS, bool NORM>
+cudaError_t launch_pass(const T *W, int64_t ldw, int k, float *q, int64_t L,
                         const double *coef, const RedScratch &rs, double *red_out,
                         cudaStream_t st) {
     int E;
@@ -340,7 +415,7 @@ cudaError_t launch_pass(const float *W, int64_t ldw, int k, float *q, int64_t L,
     cudaError_t err = cudaSuccess;
 #define CTG_PASS_CASE(EE)                                                            \
     case EE: {                                                                       \
-        auto kern = cgs_pass_kernel<EE, UPDATE, DOTS, NORM>;                         \
+        auto kern = cgs_pass_kernel<T, EE, UPDATE, DOTS, NORM>;                      \
         if ((err = ensure_smem(kern, smem)) != cudaSuccess) return err;              \
         kern<<<G, kThreads, smem, st>>>(W, ldw, k, q, L, coef, rs.partials, rs.counter, \
                                         red_out);                                    \
@@ -400,45 +475,51 @@ void ctg_red_scratch_carve(void *base, int64_t L, int kmax, RedScratch *rs) {
     ctg_red_grid(L, &rs->E);
 }
 
-cudaError_t ctg_cgs2_step(const float *W, int64_t ldw, int64_t L, int k, float *q,
-                          float *w_out, double *h_out, const RedScratch &rs,
-                          cudaStream_t st) {
+namespace {
+
+int scale_blocks(int64_t L) {
+    const int64_t L4 = (L + 3) / 4;
+    int blocks = (int)((L4 + 255) / 256);
+    if (blocks > 4 * kTargetGrid) blocks = 4 * kTargetGrid;
+    return blocks < 1 ? 1 : blocks;
+}
+
+template <typename T>
+cudaError_t cgs2_step_t(const T *W, int64_t ldw, int64_t L, int k, float *q, T *w_out,
+                        double *h_out, const RedScratch &rs, cudaStream_t st) {
     cudaError_t err;
     // pass 1: h1 = W^T q and ||q_pre||^2 (h1[k]); keep the latter in scal[0]
-    if ((err = launch_pass<false, true, true>(W, ldw, k, q, L, nullptr, rs, rs.h1, st)) != cudaSuccess)
+    if ((err = launch_pass<T, false, true, true>(W, ldw, k, q, L, nullptr, rs, rs.h1, st)) != cudaSuccess)
         return err;
     if ((err = cudaMemcpyAsync(rs.scal, rs.h1 + k, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return err;
     if (k > 0) {
         // pass 2: q -= W h1; h2 = W^T q
-        if ((err = launch_pass<true, true, false>(W, ldw, k, q, L, rs.h1, rs, rs.h2, st)) != cudaSuccess)
+        if ((err = launch_pass<T, true, true, false>(W, ldw, k, q, L, rs.h1, rs, rs.h2, st)) != cudaSuccess)
             return err;
         // pass 3: q -= W h2; ||q||^2 -> scal[1]
-        if ((err = launch_pass<true, false, true>(W, ldw, k, q, L, rs.h2, rs, rs.scal + 1, st)) != cudaSuccess)
+        if ((err = launch_pass<T, true, false, true>(W, ldw, k, q, L, rs.h2, rs, rs.scal + 1, st)) != cudaSuccess)
             return err;
     } else {
         if ((err = cudaMemcpyAsync(rs.scal + 1, rs.scal, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
             return err;
     }
-    const int64_t L4 = (L + 3) / 4;
-    int blocks = (int)((L4 + 255) / 256);
-    if (blocks > 4 * kTargetGrid) blocks = 4 * kTargetGrid;
-    if (blocks < 1) blocks = 1;
-    scale_kernel<<<blocks, 256, 0, st>>>(q, rs.scal + 1, w_out, L, k, rs.h1, rs.h2, h_out);
+    scale_kernel<T><<<scale_blocks(L), 256, 0, st>>>(q, rs.scal + 1, w_out, L, k, rs.h1, rs.h2, h_out);
     return cudaGetLastError();
 }
 
-cudaError_t ctg_gemv(const float *W, int64_t ldw, int64_t L, int k, const double *y,
-                     const float *base, float *out, cudaStream_t st) {
+template <typename T>
+cudaError_t gemv_t(const T *W, int64_t ldw, int64_t L, int k, const double *y,
+                   const float *base, float *out, cudaStream_t st) {
     int E;
     const int G = ctg_red_grid(L, &E);
     const size_t smem = sizeof(float) * (size_t)(k > 0 ? k : 1);
     cudaError_t err = cudaSuccess;
     switch (E) {
-#define CTG_GEMV_CASE(EE)                                                          \
-    case EE:                                                                       \
-        if ((err = ensure_smem(gemv_kernel<EE>, smem)) != cudaSuccess) return err; \
-        gemv_kernel<EE><<<G, kThreads, smem, st>>>(W, ldw, k, y, base, out, L);    \
+#define CTG_GEMV_CASE(EE)                                                             \
+    case EE:                                                                          \
+        if ((err = ensure_smem(gemv_kernel<T, EE>, smem)) != cudaSuccess) return err; \
+        gemv_kernel<T, EE><<<G, kThreads, smem, st>>>(W, ldw, k, y, base, out, L);    \
         break;
         CTG_GEMV_CASE(1)
         CTG_GEMV_CASE(2)
@@ -448,6 +529,35 @@ cudaError_t ctg_gemv(const float *W, int64_t ldw, int64_t L, int k, const double
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t ctg_cgs2_step(const void *W, int dtype, int64_t ldw, int64_t L, int k, float *q,
+                          void *w_out, double *h_out, const RedScratch &rs, cudaStream_t st) {
+    switch (dtype) {
+        case CTG_BASIS_FP32:
+            return cgs2_step_t(static_cast<const float *>(W), ldw, L, k, q,
+                               static_cast<float *>(w_out), h_out, rs, st);
+        case CTG_BASIS_BF16:
+            return cgs2_step_t(static_cast<const __nv_bfloat16 *>(W), ldw, L, k, q,
+                               static_cast<__nv_bfloat16 *>(w_out), h_out, rs, st);
+        case CTG_BASIS_FP16:
+            return cgs2_step_t(static_cast<const __half *>(W), ldw, L, k, q,
+                               static_cast<__half *>(w_out), h_out, rs, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t ctg_gemv(const void *W, int dtype, int64_t ldw, int64_t L, int k, const double *y,
+                     const float *base, float *out, cudaStream_t st) {
+    switch (dtype) {
+        case CTG_BASIS_FP32: return gemv_t(static_cast<const float *>(W), ldw, L, k, y, base, out, st);
+        case CTG_BASIS_BF16:
+            return gemv_t(static_cast<const __nv_bfloat16 *>(W), ldw, L, k, y, base, out, st);
+        case CTG_BASIS_FP16: return gemv_t(static_cast<const __half *>(W), ldw, L, k, y, base, out, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t ctg_gemv_norm2(const float *V, int64_t ldv, int64_t L, int k, const double *y,
@@ -493,12 +603,22 @@ cudaError_t ctg_sub_norm2(const float *a, const float *c, float *out, int64_t L,
     return cudaGetLastError();
 }
 
-cudaError_t ctg_scale(const float *v, const double *nrm2, float *out, int64_t L,
+cudaError_t ctg_scale(const float *v, const double *nrm2, void *out, int dtype, int64_t L,
                       cudaStream_t st) {
-    const int64_t L4 = (L + 3) / 4;
-    int blocks = (int)((L4 + 255) / 256);
-    if (blocks > 4 * kTargetGrid) blocks = 4 * kTargetGrid;
-    if (blocks < 1) blocks = 1;
-    scale_kernel<<<blocks, 256, 0, st>>>(v, nrm2, out, L, 0, nullptr, nullptr, nullptr);
+    switch (dtype) {
+        case CTG_BASIS_FP32:
+            scale_kernel<float><<<scale_blocks(L), 256, 0, st>>>(v, nrm2, static_cast<float *>(out), L,
+                                                                 0, nullptr, nullptr, nullptr);
+            break;
+        case CTG_BASIS_BF16:
+            scale_kernel<__nv_bfloat16><<<scale_blocks(L), 256, 0, st>>>(
+                v, nrm2, static_cast<__nv_bfloat16 *>(out), L, 0, nullptr, nullptr, nullptr);
+            break;
+        case CTG_BASIS_FP16:
+            scale_kernel<__half><<<scale_blocks(L), 256, 0, st>>>(v, nrm2, static_cast<__half *>(out),
+                                                                  L, 0, nullptr, nullptr, nullptr);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }

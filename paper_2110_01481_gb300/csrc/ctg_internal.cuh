@@ -63,15 +63,18 @@ static inline PadLayout ctg_pad_layout(int N, double det_spacing) {
 }
 
 // ---- projector launchers (projectors.cu) --------------------------------
-cudaError_t ctg_launch_pad(const float *x, float2 *pad, int N, const PadLayout &pl,
+// Stage x (n elements of type `dtype`, a CTG_BASIS_* value) for the
+// forward projector.
+cudaError_t ctg_launch_pad(const void *x, int dtype, float2 *pad, int N, const PadLayout &pl,
                            cudaStream_t st);
 cudaError_t ctg_launch_forward(const float2 *pad, int N, const PadLayout &pl, int n_angles,
                                int n_det, const FwdAngle *tab, float *b, cudaStream_t st);
 // Detector-window width (in bins) that the tiled back projector stages per
 // angle, from the host copy of the angle table.
 int ctg_back_window(const BackAngle *host_tab, int n_angles);
-// x = B b (+ add, if add != NULL); window from ctg_back_window
-cudaError_t ctg_launch_back(const float *b, int N, int n_angles, int n_det,
+// x = B b (+ add, if add != NULL); b has element type `dtype`; window from
+// ctg_back_window
+cudaError_t ctg_launch_back(const void *b, int dtype, int N, int n_angles, int n_det,
                             const BackAngle *tab, int window, const float *add, float *x,
                             cudaStream_t st);
 
@@ -89,14 +92,20 @@ int ctg_red_grid(int64_t L, int *E_out);
 size_t ctg_red_scratch_bytes(int64_t L, int kmax);
 void ctg_red_scratch_carve(void *base, int64_t L, int kmax, RedScratch *rs);
 
-// One CGS2 Arnoldi step: orthogonalise q (length L) against k vectors of W
-// (stride ldw), h_out[0..k-1] = h1 + h2, h_out[k] = ||q||, and write
-// w_out = q / ||q|| when ||q|| > 0.  Also leaves ||q_pre||^2 in rs.scal[0].
-cudaError_t ctg_cgs2_step(const float *W, int64_t ldw, int64_t L, int k, float *q,
-                          float *w_out, double *h_out, const RedScratch &rs,
-                          cudaStream_t st);
+// Basis element size in bytes for a CTG_BASIS_* type (0 if unknown).
+static inline size_t ctg_basis_bytes(int dtype) {
+    return dtype == CTG_BASIS_FP32 ? 4 : (dtype == CTG_BASIS_BF16 || dtype == CTG_BASIS_FP16) ? 2 : 0;
+}
+
+// One CGS2 Arnoldi step: orthogonalise the FP32 vector q (length L) against
+// k vectors of W (element type `dtype`, stride ldw elements),
+// h_out[0..k-1] = h1 + h2, h_out[k] = ||q||, and write w_out = q / ||q||
+// (rounded to `dtype`) when ||q|| > 0.  Also leaves ||q_pre||^2 in
+// rs.scal[0].
+cudaError_t ctg_cgs2_step(const void *W, int dtype, int64_t ldw, int64_t L, int k, float *q,
+                          void *w_out, double *h_out, const RedScratch &rs, cudaStream_t st);
 // out = base + sum_j y_j W_j (base may be NULL); y: k doubles (device).
-cudaError_t ctg_gemv(const float *W, int64_t ldw, int64_t L, int k, const double *y,
+cudaError_t ctg_gemv(const void *W, int dtype, int64_t ldw, int64_t L, int k, const double *y,
                      const float *base, float *out, cudaStream_t st);
 // *res = ||base + sum_j y_j V_j||^2 (double, device); the vector is not stored.
 cudaError_t ctg_gemv_norm2(const float *V, int64_t ldv, int64_t L, int k, const double *y,
@@ -105,6 +114,7 @@ cudaError_t ctg_gemv_norm2(const float *V, int64_t ldv, int64_t L, int k, const 
 // out = a - c (c may be NULL -> out = a) and *res = ||a - c||^2 (double, device).
 cudaError_t ctg_sub_norm2(const float *a, const float *c, float *out, int64_t L,
                           double *res, const RedScratch &rs, cudaStream_t st);
-// out = v / sqrt(*nrm2) (nrm2 on device; out = 0 when nrm2 == 0).
-cudaError_t ctg_scale(const float *v, const double *nrm2, float *out, int64_t L,
+// out = v / sqrt(*nrm2) rounded to `dtype` (nrm2 on device; out = 0 when
+// nrm2 == 0).
+cudaError_t ctg_scale(const float *v, const double *nrm2, void *out, int dtype, int64_t L,
                       cudaStream_t st);

@@ -68,7 +68,7 @@ extern "C" int ctg_cgs2_noalloc(const float *W_dev, int64_t ld_w, int64_t L, int
     // the array keeps the previous call's contents: the completion counters
     // must start at zero
     if (cudaMemsetAsync(rs.counter, 0, 4 * sizeof(unsigned), st) != cudaSuccess) return CTG_ERR_CUDA;
-    if (ctg_cgs2_step(W_dev, ld_w, L, k, q_dev, w_out_dev, h_out_dev, rs, st) != cudaSuccess)
+    if (ctg_cgs2_step(W_dev, CTG_BASIS_FP32, ld_w, L, k, q_dev, w_out_dev, h_out_dev, rs, st) != cudaSuccess)
         return CTG_ERR_CUDA;
     return CTG_OK;
 }

@@ -7,6 +7,8 @@
 // 8-byte load and one FMA give a linear interpolation:
 //   lerp(v, j + f) = v[j] + f (v[j+1] - v[j]).
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "ctg_internal.cuh"
 
@@ -15,6 +17,11 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kPadTile = 32;
+
+// Inputs that are Krylov basis vectors may be stored in BF16 or FP16.
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
 __device__ __forceinline__ float2 lerp_pair(float v0, float v1) {
     // (v0 - dv, dv): with m = 1 + f, (v0 - dv) + m dv = v0 + f dv
@@ -25,7 +32,8 @@ __device__ __forceinline__ float2 lerp_pair(float v0, float v1) {
 // Stage the image for the forward projector (layout in ctg_internal.cuh):
 // entries j = -1 .. N-1 of every row of x and of x^T; the other border
 // entries are zero pairs written once when the buffer is allocated.
-__global__ void pad_pairs_kernel(const float *__restrict__ x, float2 *__restrict__ pad, int N,
+template <typename T>
+__global__ void pad_pairs_kernel(const T *__restrict__ x, float2 *__restrict__ pad, int N,
                                  int stride, int border) {
     __shared__ float tile[kPadTile + 1][kPadTile + 2];
     float2 *xp = pad + border, *xtp = pad + (size_t)N * stride + border;
@@ -34,7 +42,7 @@ __global__ void pad_pairs_kernel(const float *__restrict__ x, float2 *__restrict
     for (int r = threadIdx.y; r <= kPadTile; r += blockDim.y)
         for (int c = threadIdx.x; c <= kPadTile; c += blockDim.x) {
             const int i = i0 + r, j = j0 + c;
-            tile[r][c] = (i < N && j < N) ? x[(size_t)i * N + j] : 0.0f;
+            tile[r][c] = (i < N && j < N) ? to_f(x[(size_t)i * N + j]) : 0.0f;
         }
     __syncthreads();
     for (int r = threadIdx.y; r < kPadTile; r += blockDim.y) {
@@ -49,12 +57,12 @@ __global__ void pad_pairs_kernel(const float *__restrict__ x, float2 *__restrict
     if (blockIdx.x == 0)
         for (int r = threadIdx.y * blockDim.x + threadIdx.x; r < kPadTile; r += blockDim.x * blockDim.y) {
             const int i = i0 + r;
-            if (i < N) xp[(size_t)i * stride - 1] = lerp_pair(0.0f, x[(size_t)i * N]);
+            if (i < N) xp[(size_t)i * stride - 1] = lerp_pair(0.0f, to_f(x[(size_t)i * N]));
         }
     if (blockIdx.y == 0)
         for (int c = threadIdx.y * blockDim.x + threadIdx.x; c < kPadTile; c += blockDim.x * blockDim.y) {
             const int j = j0 + c;
-            if (j < N) xtp[(size_t)j * stride - 1] = lerp_pair(0.0f, x[j]);
+            if (j < N) xtp[(size_t)j * stride - 1] = lerp_pair(0.0f, to_f(x[j]));
         }
 }
 
@@ -168,8 +176,9 @@ constexpr int kBThreads = 256;
 constexpr int kBChunk = 32;      // angles staged per pass
 constexpr int kBSplit = 4;       // CTAs per cluster = angle groups per tile
 
+template <typename T>
 __global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
-pixel_back_tiled_kernel(const float *__restrict__ b, int N, int n_angles, int n_det,
+pixel_back_tiled_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
                         const BackAngle *__restrict__ tab, int W, const float *__restrict__ add,
                         float *__restrict__ x) {
     extern __shared__ float2 s_pairs[];               // kBChunk * W pairs
@@ -202,9 +211,9 @@ pixel_back_tiled_kernel(const float *__restrict__ b, int N, int n_angles, int n_
         for (int e = threadIdx.x; e < na * W; e += kBThreads) {
             const int k = e / W, w = e - k * W;
             const int dd = __float_as_int(s_par[k].w) + w;
-            const float *brow = b + (size_t)(a0 + k) * n_det;
-            const float v0 = ((unsigned)dd < (unsigned)n_det) ? __ldg(brow + dd) : 0.0f;
-            const float v1 = ((unsigned)(dd + 1) < (unsigned)n_det) ? __ldg(brow + dd + 1) : 0.0f;
+            const T *brow = b + (size_t)(a0 + k) * n_det;
+            const float v0 = ((unsigned)dd < (unsigned)n_det) ? to_f(__ldg(brow + dd)) : 0.0f;
+            const float v1 = ((unsigned)(dd + 1) < (unsigned)n_det) ? to_f(__ldg(brow + dd + 1)) : 0.0f;
             s_pairs[e] = make_float2(v0, v1 - v0);
         }
         __syncthreads();
@@ -246,8 +255,9 @@ pixel_back_tiled_kernel(const float *__restrict__ b, int N, int n_angles, int n_
 // taps read through L1 with bounds tests.
 constexpr int kBX = 32, kBY = 8, kAChunk = 256;
 
+template <typename T>
 __global__ void __launch_bounds__(kBX *kBY)
-pixel_back_kernel(const float *__restrict__ b, int N, int n_angles, int n_det,
+pixel_back_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
                   const BackAngle *__restrict__ tab, const float *__restrict__ add,
                   float *__restrict__ x) {
     __shared__ float4 sp[kAChunk];
@@ -266,7 +276,7 @@ pixel_back_kernel(const float *__restrict__ b, int N, int n_angles, int n_det,
                                   __int_as_float((int)(U0 >> CTG_FX_BITS)));
         }
         __syncthreads();
-        const float *brow = b + (size_t)a0 * n_det;
+        const T *brow = b + (size_t)a0 * n_det;
 #pragma unroll 4
         for (int k = 0; k < na; ++k, brow += n_det) {
             const float4 p = sp[k];
@@ -274,8 +284,8 @@ pixel_back_kernel(const float *__restrict__ b, int N, int n_angles, int n_det,
             const float fl = floorf(u);
             const int dd = __float_as_int(p.w) + (int)fl;
             const float f = u - fl;
-            const float v0 = ((unsigned)dd < (unsigned)n_det) ? __ldg(brow + dd) : 0.0f;
-            const float v1 = ((unsigned)(dd + 1) < (unsigned)n_det) ? __ldg(brow + dd + 1) : 0.0f;
+            const float v0 = ((unsigned)dd < (unsigned)n_det) ? to_f(__ldg(brow + dd)) : 0.0f;
+            const float v1 = ((unsigned)(dd + 1) < (unsigned)n_det) ? to_f(__ldg(brow + dd + 1)) : 0.0f;
             acc += fmaf(f, v1 - v0, v0);
         }
     }
@@ -299,10 +309,24 @@ int ctg_back_window(const BackAngle *host_tab, int n_angles) {
     return (int)ceil(span) + 4;
 }
 
-cudaError_t ctg_launch_pad(const float *x, float2 *pad, int N, const PadLayout &pl,
+cudaError_t ctg_launch_pad(const void *x, int dtype, float2 *pad, int N, const PadLayout &pl,
                            cudaStream_t st) {
-    dim3 grid((N + kPadTile - 1) / kPadTile, (N + kPadTile - 1) / kPadTile);
-    pad_pairs_kernel<<<grid, dim3(kPadTile, 8), 0, st>>>(x, pad, N, pl.stride, pl.border);
+    dim3 grid((N + kPadTile - 1) / kPadTile, (N + kPadTile - 1) / kPadTile), block(kPadTile, 8);
+    switch (dtype) {
+        case CTG_BASIS_FP32:
+            pad_pairs_kernel<<<grid, block, 0, st>>>(static_cast<const float *>(x), pad, N, pl.stride,
+                                                     pl.border);
+            break;
+        case CTG_BASIS_BF16:
+            pad_pairs_kernel<<<grid, block, 0, st>>>(static_cast<const __nv_bfloat16 *>(x), pad, N,
+                                                     pl.stride, pl.border);
+            break;
+        case CTG_BASIS_FP16:
+            pad_pairs_kernel<<<grid, block, 0, st>>>(static_cast<const __half *>(x), pad, N, pl.stride,
+                                                     pl.border);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -318,17 +342,36 @@ cudaError_t ctg_launch_forward(const float2 *pad, int N, const PadLayout &pl, in
     return cudaGetLastError();
 }
 
-cudaError_t ctg_launch_back(const float *b, int N, int n_angles, int n_det,
-                            const BackAngle *tab, int window, const float *add, float *x,
-                            cudaStream_t st) {
+namespace {
+
+template <typename T>
+cudaError_t launch_back_t(const T *b, int N, int n_angles, int n_det, const BackAngle *tab,
+                          int window, const float *add, float *x, cudaStream_t st) {
     const size_t smem = sizeof(float2) * (size_t)kBChunk * window;
     if (window > 0 && smem <= 40 * 1024) {
         dim3 grid((N + kBT - 1) / kBT, (N + kBT - 1) / kBT, kBSplit);
-        pixel_back_tiled_kernel<<<grid, kBThreads, smem, st>>>(b, N, n_angles, n_det, tab, window,
-                                                               add, x);
+        pixel_back_tiled_kernel<T><<<grid, kBThreads, smem, st>>>(b, N, n_angles, n_det, tab, window,
+                                                                  add, x);
     } else {
         dim3 grid((N + kBX - 1) / kBX, (N + kBY - 1) / kBY);
-        pixel_back_kernel<<<grid, dim3(kBX, kBY), 0, st>>>(b, N, n_angles, n_det, tab, add, x);
+        pixel_back_kernel<T><<<grid, dim3(kBX, kBY), 0, st>>>(b, N, n_angles, n_det, tab, add, x);
     }
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t ctg_launch_back(const void *b, int dtype, int N, int n_angles, int n_det,
+                            const BackAngle *tab, int window, const float *add, float *x,
+                            cudaStream_t st) {
+    switch (dtype) {
+        case CTG_BASIS_FP32:
+            return launch_back_t(static_cast<const float *>(b), N, n_angles, n_det, tab, window, add, x, st);
+        case CTG_BASIS_BF16:
+            return launch_back_t(static_cast<const __nv_bfloat16 *>(b), N, n_angles, n_det, tab, window,
+                                 add, x, st);
+        case CTG_BASIS_FP16:
+            return launch_back_t(static_cast<const __half *>(b), N, n_angles, n_det, tab, window, add, x, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
