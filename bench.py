@@ -287,6 +287,82 @@ def run_precision(args):
             torch.cuda.empty_cache()
 
 
+def batch_problems(P, torch, dev, count, seed0=3000):
+    """The batched workload: `count` seeded random-ellipse instances with
+    N in {128, 256, 512, 1024}, angle counts in {60, 180, 360, 720}, a
+    quarter of them limited-angle scans over [0, 120), N_det = ceil(sqrt2 N),
+    noise 0.5-3%, AB and BA alternating, discrepancy stop tau = 1.02."""
+    rng = np.random.default_rng(seed0)
+    probs, bs, truths = [], [], []
+    for i in range(count):
+        N = int(rng.choice([128, 256, 512, 1024]))
+        Na = int(rng.choice([60, 180, 360, 720]))
+        R = 120 if rng.uniform() < 0.25 else 180
+        eta = float(rng.uniform(0.005, 0.03))
+        g = P.Geometry(N, Na, I.detector_count(N), 0, R)
+        xbar = I.random_ellipses(N, seed0 + i)
+        bbar = P.project(g, torch.tensor(xbar.ravel(), dtype=torch.float32, device=dev))
+        b, enorm = I.add_noise(bbar.double().cpu().numpy(), eta, seed0 + i)
+        probs.append({"geometry": g, "variant": "ab" if i % 2 == 0 else "ba", "maxit": 100,
+                      "tau": TAU, "noise_norm": enorm})
+        bs.append(torch.tensor(b, dtype=torch.float32, device=dev))
+        truths.append(xbar.ravel())
+    return probs, bs, truths
+
+
+def run_batch(args):
+    """Batched engine vs the plain one-at-a-time solves on the same
+    instances: aggregate iterations/s and the reconstruction error of each."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2110_01481_gb300 as P
+    dev = torch.device("cuda", 0)
+    probs, bs, truths = batch_problems(P, torch, dev, args.batch_size)
+    batch = P.Batch(probs)
+    outs = [torch.empty(p["geometry"].n, device=dev) for p in probs]
+    batch.solve(bs, outs=outs)                    # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rb = batch.solve(bs, outs=outs)
+    torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t0) / args.steps
+    err_b = [float(np.linalg.norm(o.double().cpu().numpy() - t) / np.linalg.norm(t))
+             for o, t in zip(outs, truths)]
+    # plain method: the single-solve path, one instance after another
+    wss = [torch.empty(P.workspace_bytes(p["geometry"], p["variant"], p["maxit"]),
+                       dtype=torch.uint8, device=dev) for p in probs]
+    def plain():
+        res = []
+        for p, b, o, ws in zip(probs, bs, outs, wss):
+            fn = P.ab_gmres if p["variant"] == "ab" else P.ba_gmres
+            res.append(fn(p["geometry"], b, p["maxit"], tau=TAU, noise_norm=p["noise_norm"],
+                          out=o, workspace=ws))
+        return res
+    plain()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rp = plain()
+    torch.cuda.synchronize()
+    t_plain = (time.perf_counter() - t0) / args.steps
+    err_p = [float(np.linalg.norm(o.double().cpu().numpy() - t) / np.linalg.norm(t))
+             for o, t in zip(outs, truths)]
+    it_b, it_p = sum(r.iters for r in rb), sum(r.iters for r in rp)
+    print(json.dumps({
+        "workload": f"{len(probs)} instances, N in {{128,256,512,1024}}, angles in {{60,180,360,720}}, "
+                    "25% limited-angle [0,120), noise 0.5-3%, AB/BA alternating, DP tau=1.02, maxit 100",
+        "batched": {"s_per_batch": t_batch, "iterations": it_b, "iterations_per_s": it_b / t_batch},
+        "plain_one_at_a_time": {"s_per_batch": t_plain, "iterations": it_p,
+                                "iterations_per_s": it_p / t_plain},
+        "speedup": t_plain / t_batch,
+        "same_stop_index": sum(int(a.iters == b.iters) for a, b in zip(rb, rp)),
+        "mean_rel_error_vs_truth": {"batched": float(np.mean(err_b)), "plain": float(np.mean(err_p))},
+        "max_abs_error_difference": float(np.max(np.abs(np.array(err_b) - np.array(err_p)))),
+        "workspace_GB": batch.workspace_bytes / 1e9}))
+
+
 def make_instance(P, torch, dev, seed):
     """Seeded phantom, b = A x_bar + e with the library's own A (the oracle is
     not used on the product path)."""
@@ -554,6 +630,9 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="basis-storage study (FP32/FP16/BF16) on the 2048^2 workload")
     ap.add_argument("--precision-k", default="25,50,100,200")
+    ap.add_argument("--batch", action="store_true",
+                    help="batched engine vs one-at-a-time solves on 64 mixed instances")
+    ap.add_argument("--batch-size", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -561,6 +640,8 @@ def main():
         run_cgs2_only(args)
     elif args.precision:
         run_precision(args)
+    elif args.batch:
+        run_batch(args)
     else:
         run_gpu(args)
 

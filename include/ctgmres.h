@@ -160,6 +160,28 @@ int ctg_ba_gmres(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev,
                  void *workspace_dev, size_t workspace_bytes, ctg_info *info,
                  void *stream);
 
+/* Batched AB-/BA-GMRES: n independent solves of possibly different
+ * geometries, variants (CTG_AB / CTG_BA) and options advance together, one
+ * Arnoldi step of every active solve per round (Sec. 2 algorithm box for
+ * each), with the Hessenberg least-squares update (FP64 Givens) and the
+ * discrepancy-principle stop (Sec. 6.4) done on the device.  A round is one
+ * launch per phase for all solves and is replayed as a captured CUDA graph.
+ * ctg_batch_create: geoms, variants, opts are arrays of n (FP32 basis only,
+ * maxit <= 1024, det_spacing >= ~0.25); the batch owns its device workspace
+ * (ctg_batch_workspace_bytes) and a stream of its own.
+ * ctg_batch_solve: b_dev, x_dev: host arrays of n device pointers (m and n
+ * floats of each solve); x0_dev: NULL or an array whose entries may be NULL;
+ * infos: n reports, filled as by ctg_ab_gmres.  Work is ordered after prior
+ * work on `stream`, and `stream` waits for it; the call returns when done.
+ * Each solve's result does not depend on the others in the batch. */
+typedef struct ctg_batch ctg_batch;
+int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms, const int32_t *variants,
+                     const ctg_opts *opts, ctg_batch **out);
+size_t ctg_batch_workspace_bytes(const ctg_batch *batch);
+int ctg_batch_solve(ctg_batch *batch, const float *const *b_dev, const float *const *x0_dev,
+                    float *const *x_dev, ctg_info *infos, void *stream);
+void ctg_batch_destroy(ctg_batch *batch);
+
 /* One classical Gram-Schmidt step with reorthogonalisation (CGS2) of q
  * against the k orthonormal columns of W, the Arnoldi step of Sec. 2 with
  * MGS replaced by CGS2 (equal in exact arithmetic):

@@ -59,7 +59,8 @@ class CtgLayout(ctypes.Structure):
 EXPORTS = ("ctg_create", "ctg_destroy", "ctg_project", "ctg_backproject",
            "ctg_workspace_bytes", "ctg_workspace_layout", "ctg_ab_gmres",
            "ctg_ba_gmres", "ctg_cgs2_scratch_bytes", "ctg_cgs2", "ctg_cgs2_noalloc",
-           "ctg_set_timing", "ctg_get_timing", "ctg_status_string")
+           "ctg_set_timing", "ctg_get_timing", "ctg_status_string",
+           "ctg_batch_create", "ctg_batch_workspace_bytes", "ctg_batch_solve", "ctg_batch_destroy")
 
 
 def _declare(lib):
@@ -89,6 +90,15 @@ def _declare(lib):
     lib.ctg_set_timing.restype = ctypes.c_int
     lib.ctg_get_timing.argtypes = [vp, ctypes.POINTER(CtgTiming), ctypes.c_int]
     lib.ctg_get_timing.restype = ctypes.c_int
+    lib.ctg_batch_create.argtypes = [vp, i32, G, ctypes.POINTER(i32), O, ctypes.POINTER(vp)]
+    lib.ctg_batch_create.restype = ctypes.c_int
+    lib.ctg_batch_workspace_bytes.argtypes = [vp]
+    lib.ctg_batch_workspace_bytes.restype = sz
+    lib.ctg_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    ctypes.POINTER(CtgInfo), vp]
+    lib.ctg_batch_solve.restype = ctypes.c_int
+    lib.ctg_batch_destroy.argtypes = [vp]
+    lib.ctg_batch_destroy.restype = None
     lib.ctg_status_string.argtypes = [ctypes.c_int]
     lib.ctg_status_string.restype = ctypes.c_char_p
     return lib

@@ -244,3 +244,67 @@ def cgs2(W: torch.Tensor, k: int, q: torch.Tensor, w_out: Optional[torch.Tensor]
                                      scratch.data_ptr(), scratch.numel(),
                                      _stream(q.device)), "ctg_cgs2")
     return h, w_out
+
+
+class Batch:
+    """Batched AB-/BA-GMRES (ctg_batch_*): solves of different geometries,
+    variants and options advance together, one Arnoldi step per round, with
+    the Hessenberg update and the stopping rule on the device and each round
+    replayed as a captured CUDA graph.
+
+    problems: list of dicts with keys geometry (Geometry), variant ("ab" or
+    "ba"), maxit, and optionally tau, noise_norm."""
+
+    def __init__(self, problems, device=None):
+        if not problems:
+            raise ValueError("empty batch")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.problems = list(problems)
+        n = len(problems)
+        geoms = (nat.CtgGeom * n)(*[p["geometry"].c() for p in problems])
+        variants = (ctypes.c_int32 * n)(*[nat.CTG_AB if p["variant"] == "ab" else nat.CTG_BA
+                                          for p in problems])
+        opts = (nat.CtgOpts * n)(*[_opts(p["maxit"], p.get("tau", 1.0), p.get("noise_norm"))
+                                   for p in problems])
+        self.ctx = Context.get(self.device)
+        self.handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().ctg_batch_create(self.ctx.handle, n, geoms, variants, opts,
+                                                 ctypes.byref(self.handle)), "ctg_batch_create")
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(nat.lib().ctg_batch_workspace_bytes(self.handle))
+
+    def solve(self, bs, x0s=None, outs=None):
+        """bs: list of CUDA tensors (m floats each); returns a list of
+        SolveResult in the same order."""
+        n = len(self.problems)
+        if len(bs) != n:
+            raise ValueError("one right-hand side per problem")
+        if outs is None:
+            outs = [torch.empty(p["geometry"].n, device=self.device, dtype=torch.float32)
+                    for p in self.problems]
+        pb = (ctypes.c_void_p * n)(*[_dev_ptr(b, p["geometry"].m, "b") for b, p in zip(bs, self.problems)])
+        px = (ctypes.c_void_p * n)(*[_dev_ptr(x, p["geometry"].n, "x") for x, p in zip(outs, self.problems)])
+        px0 = None
+        if x0s is not None:
+            px0 = (ctypes.c_void_p * n)(*[_dev_ptr(x0, p["geometry"].n, "x0") if x0 is not None else None
+                                          for x0, p in zip(x0s, self.problems)])
+        hists = [(ctypes.c_double * (p["maxit"] + 1))(*([math.nan] * (p["maxit"] + 1)))
+                 for p in self.problems]
+        infos = (nat.CtgInfo * n)(*[nat.CtgInfo(0, 0, 0.0, 0.0, h) for h in hists])
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().ctg_batch_solve(self.handle, pb, px0, px, infos,
+                                                _stream(self.device)), "ctg_batch_solve")
+        return [SolveResult(outs[i], infos[i].iters, infos[i].stop_reason, infos[i].resnorm,
+                            infos[i].rho, list(hists[i][: infos[i].iters + 1])) for i in range(n)]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and nat._lib is not None:
+            try:
+                with torch.cuda.device(self.device):
+                    nat.lib().ctg_batch_destroy(h)
+            except Exception:
+                pass

@@ -99,6 +99,16 @@ void build_tables(const ctg_geom *g, std::vector<FwdAngle> &fw, std::vector<Back
     }
 }
 
+}  // namespace
+
+bool ctg_geom_valid(const ctg_geom *g) { return geom_valid(g); }
+bool ctg_opts_valid(const ctg_opts *o) { return opts_valid(o); }
+void ctg_build_tables(const ctg_geom *g, std::vector<FwdAngle> &fw, std::vector<BackAngle> &bk) {
+    build_tables(g, fw, bk);
+}
+
+namespace {
+
 bool same_geom(const ctg_geom &a, const ctg_geom &b) {
     return a.N == b.N && a.n_angles == b.n_angles && a.n_det == b.n_det &&
            a.angle_start_deg == b.angle_start_deg && a.angle_range_deg == b.angle_range_deg &&

@@ -145,15 +145,15 @@ __host__ __device__ inline int padded_grid(int G) { return (G + 3) & ~3; }
 // as float4, so the serial tail is a few L2 round trips.
 __device__ void block_reduce_finish(float *s_w, int nred, float *__restrict__ partials,
                                     unsigned *__restrict__ counter,
-                                    double *__restrict__ red_out) {
+                                    double *__restrict__ red_out, int blk, int G) {
     __shared__ bool s_last;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int G = gridDim.x, Gp = padded_grid(G);
+    const int Gp = padded_grid(G);
     __syncthreads();
     for (int j = tid; j < nred; j += kThreads) {
         float s = 0.f;
         for (int w = 0; w < kWarps; ++w) s += s_w[w * nred + j];
-        partials[(size_t)j * Gp + blockIdx.x] = s;
+        partials[(size_t)j * Gp + blk] = s;
     }
     __threadfence();
     __syncthreads();
@@ -231,10 +231,12 @@ __device__ __forceinline__ void accumulate_batched(const T *__restrict__ V, int6
 //   DOTS:   red_out[j] = W_j^T q (after the update)      j < k
 //   NORM:   red_out[DOTS ? k : 0] = q^T q (after the update)
 template <typename T, int E, bool UPDATE, bool DOTS, bool NORM>
-__global__ void __launch_bounds__(kThreads, 2)
-cgs_pass_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict__ q,
-                int64_t L, const double *__restrict__ coef, float *__restrict__ partials,
-                unsigned *__restrict__ counter, double *__restrict__ red_out) {
+__device__ __forceinline__ void cgs_pass_body(const T *__restrict__ W, int64_t ldw, int k,
+                                              float *__restrict__ q, int64_t L,
+                                              const double *__restrict__ coef,
+                                              float *__restrict__ partials,
+                                              unsigned *__restrict__ counter,
+                                              double *__restrict__ red_out, int blk, int G) {
     extern __shared__ float smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nred = (DOTS ? k : 0) + (NORM ? 1 : 0);
@@ -242,7 +244,7 @@ cgs_pass_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict__
     float *s_w = smem + (UPDATE ? k : 0);       // kWarps * nred floats
     if (UPDATE)
         for (int j = tid; j < k; j += kThreads) s_coef[j] = (float)coef[j];
-    const int64_t g0 = (int64_t)blockIdx.x * kThreads * E + tid;
+    const int64_t g0 = (int64_t)blk * kThreads * E + tid;
     float4 qv[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) qv[e] = ld4_rw(q, g0 + (int64_t)e * kThreads, L);
@@ -305,30 +307,47 @@ cgs_pass_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict__
         s = warp_sum(s);
         if (lane == 0) s_w[warp * nred + (DOTS ? k : 0)] = s;
     }
-    block_reduce_finish(s_w, nred, partials, counter, red_out);
+    block_reduce_finish(s_w, nred, partials, counter, red_out, blk, G);
+}
+
+template <typename T, int E, bool UPDATE, bool DOTS, bool NORM>
+__global__ void __launch_bounds__(kThreads, 2)
+cgs_pass_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict__ q,
+                int64_t L, const double *__restrict__ coef, float *__restrict__ partials,
+                unsigned *__restrict__ counter, double *__restrict__ red_out) {
+    cgs_pass_body<T, E, UPDATE, DOTS, NORM>(W, ldw, k, q, L, coef, partials, counter, red_out,
+                                            blockIdx.x, gridDim.x);
 }
 
 // w_out = q / sqrt(nrm2) (0 if nrm2 == 0); block 0 also assembles the
 // Hessenberg column h_out[0..k-1] = h1 + h2, h_out[k] = sqrt(nrm2).
 // q and w_out may be the same vector (FP32 storage only).
 template <typename T>
-__global__ void scale_kernel(const float *q, const double *__restrict__ nrm2,
-                             T *w_out, int64_t L, int k,
-                             const double *__restrict__ h1, const double *__restrict__ h2,
-                             double *__restrict__ h_out) {
+__device__ __forceinline__ void scale_body(const float *q, const double *__restrict__ nrm2,
+                                           T *w_out, int64_t L, int k,
+                                           const double *__restrict__ h1,
+                                           const double *__restrict__ h2,
+                                           double *__restrict__ h_out, int blk, int nblk) {
     const double nn = *nrm2;
     const float inv = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.0f;
     const int64_t L4 = (L + 3) / 4;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L4;
-         g += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t g = (int64_t)blk * blockDim.x + threadIdx.x; g < L4;
+         g += (int64_t)nblk * blockDim.x) {
         float4 v = ld4_rw(q, g, L);
         v.x *= inv; v.y *= inv; v.z *= inv; v.w *= inv;
         stw4(w_out, g, L, v);
     }
-    if (h_out != nullptr && blockIdx.x == 0) {
+    if (h_out != nullptr && blk == 0) {
         for (int j = threadIdx.x; j < k; j += blockDim.x) h_out[j] = h1[j] + h2[j];
         if (threadIdx.x == 0) h_out[k] = sqrt(nn);
     }
+}
+
+template <typename T>
+__global__ void scale_kernel(const float *q, const double *__restrict__ nrm2, T *w_out, int64_t L,
+                             int k, const double *__restrict__ h1, const double *__restrict__ h2,
+                             double *__restrict__ h_out) {
+    scale_body<T>(q, nrm2, w_out, L, k, h1, h2, h_out, blockIdx.x, gridDim.x);
 }
 
 // out = base + sum_j y_j W_j.
@@ -351,15 +370,17 @@ gemv_kernel(const T *__restrict__ W, int64_t ldw, int k, const double *__restric
 
 // res = ||base + sum_j y_j V_j||^2 (the vector itself is not stored).
 template <int E>
-__global__ void __launch_bounds__(kThreads, 2)
-gemv_norm2_kernel(const float *__restrict__ V, int64_t ldv, int k, const double *__restrict__ y,
-                  const float *__restrict__ base, int64_t L, float *__restrict__ partials,
-                  unsigned *__restrict__ counter, double *__restrict__ res) {
+__device__ __forceinline__ void gemv_norm2_body(const float *__restrict__ V, int64_t ldv, int k,
+                                                const double *__restrict__ y,
+                                                const float *__restrict__ base, int64_t L,
+                                                float *__restrict__ partials,
+                                                unsigned *__restrict__ counter,
+                                                double *__restrict__ res, int blk, int G) {
     extern __shared__ float s_y[];
     __shared__ float s_w[kWarps];
     for (int j = threadIdx.x; j < k; j += kThreads) s_y[j] = (float)y[j];
     __syncthreads();
-    const int64_t g0 = (int64_t)blockIdx.x * kThreads * E + threadIdx.x;
+    const int64_t g0 = (int64_t)blk * kThreads * E + threadIdx.x;
     float4 acc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) acc[e] = ld4(base, g0 + (int64_t)e * kThreads, L);
@@ -369,7 +390,15 @@ gemv_norm2_kernel(const float *__restrict__ V, int64_t ldv, int k, const double 
     for (int e = 0; e < E; ++e) s += dot4(acc[e], acc[e]);
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
-    block_reduce_finish(s_w, 1, partials, counter, res);
+    block_reduce_finish(s_w, 1, partials, counter, res, blk, G);
+}
+
+template <int E>
+__global__ void __launch_bounds__(kThreads, 2)
+gemv_norm2_kernel(const float *__restrict__ V, int64_t ldv, int k, const double *__restrict__ y,
+                  const float *__restrict__ base, int64_t L, float *__restrict__ partials,
+                  unsigned *__restrict__ counter, double *__restrict__ res) {
+    gemv_norm2_body<E>(V, ldv, k, y, base, L, partials, counter, res, blockIdx.x, gridDim.x);
 }
 
 // out = a - c (or a), res = ||out||^2; out may be the same vector as a or c.
@@ -395,7 +424,134 @@ sub_norm2_kernel(const float *a, const float *c, float *out, int64_t L,
     }
     s = warp_sum(s);
     if ((tid & 31) == 0) s_w[tid >> 5] = s;
-    block_reduce_finish(s_w, 1, partials, counter, res);
+    block_reduce_finish(s_w, 1, partials, counter, res, blockIdx.x, gridDim.x);
+}
+
+// ---- batched kernels (one launch for every instance of a batch) ----------
+// E = 1 passes; map[blockIdx.x] = (instance, block of that instance).
+
+__device__ __forceinline__ int vec_blocks_dev(long long L) {
+    return (int)(((L + 3) / 4 + kThreads - 1) / kThreads);
+}
+
+template <bool UPDATE, bool DOTS, bool NORM>
+__global__ void __launch_bounds__(kThreads, 2)
+batch_cgs_pass_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
+    const int2 mp = map[blockIdx.x];
+    BatchInst &I = insts[mp.x];
+    if (!I.active) return;
+    float *q = I.variant == CTG_AB ? I.vm : I.vn;
+    const double *coef = UPDATE ? (DOTS ? I.h1 : I.h2) : nullptr;
+    double *red_out = DOTS ? (UPDATE ? I.h2 : I.h1) : I.scal + 1;
+    cgs_pass_body<float, 1, UPDATE, DOTS, NORM>(I.W, I.ldw, I.k, q, I.L, coef, I.partials,
+                                                I.counter, red_out, mp.y, I.G);
+}
+
+__global__ void batch_scale_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
+    const int2 mp = map[blockIdx.x];
+    BatchInst &I = insts[mp.x];
+    if (!I.active) return;
+    const float *q = I.variant == CTG_AB ? I.vm : I.vn;
+    scale_body<float>(q, I.scal + 1, I.W + (size_t)I.k * I.ldw, I.L, I.k, I.h1, I.h2,
+                      I.H + (size_t)(I.k - 1) * (I.maxit + 1), mp.y, I.G);
+}
+
+// One warp per instance: FP64 Givens update of the Hessenberg least-squares
+// problem with the new column (rotations kept in gc/gs, rotated column in
+// R, rotated right-hand side gg), the breakdown test, and for BA with the
+// discrepancy stop, y_k = R^{-1} gg (stored negated for the residual).
+__global__ void batch_givens_kernel(BatchInst *__restrict__ insts) {
+    BatchInst &I = insts[blockIdx.x];
+    if (!I.active) return;
+    const int k = I.k, lane = threadIdx.x, ldr = I.maxit;
+    const double *h = I.H + (size_t)(k - 1) * (I.maxit + 1);
+    double *Rk = I.R + (size_t)(k - 1) * ldr;         // column k of R
+    if (lane == 0) {
+        double r_prev = h[0];
+        for (int i = 0; i < k - 1; ++i) {
+            const double a = r_prev, b = h[i + 1];
+            Rk[i] = I.gc[i] * a + I.gs[i] * b;
+            r_prev = -I.gs[i] * a + I.gc[i] * b;
+        }
+        const double a = r_prev, b = h[k];
+        const double r = hypot(a, b);
+        double c = 1.0, sn = 0.0;
+        if (b != 0.0) {
+            c = a / r;
+            sn = b / r;
+        }
+        I.gc[k - 1] = c;
+        I.gs[k - 1] = sn;
+        Rk[k - 1] = b != 0.0 ? r : a;
+        I.gg[k] = -sn * I.gg[k - 1];
+        I.gg[k - 1] = c * I.gg[k - 1];
+        I.rho = fabs(I.gg[k]);
+        I.breakdown = h[k] <= 1e-6 * sqrt(I.h1[k]);     // h1[k] = ||q before CGS2||^2
+    }
+    __syncwarp();
+    if (I.variant == CTG_BA && I.target > 0.0) {
+        // back substitution, one row at a time, the row sums shared by the warp
+        for (int i = k - 1; i >= 0; --i) {
+            double t = 0.0;
+            for (int j = i + 1 + lane; j < k; j += 32) t += I.R[(size_t)j * ldr + i] * (-I.y[j]);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) {
+                const double d = I.R[(size_t)i * ldr + i];
+                I.y[i] = -(d != 0.0 ? (I.gg[i] - t) / d : 0.0);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// BA with the discrepancy stop: ||b - A x_k||^2 = ||(b - A x0) - T_k y_k||^2.
+__global__ void __launch_bounds__(kThreads, 2)
+batch_residual_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
+    const int2 mp = map[blockIdx.x];
+    BatchInst &I = insts[mp.x];
+    if (!I.active || I.variant != CTG_BA || !(I.target > 0.0)) return;
+    gemv_norm2_body<1>(I.T, I.ldt, I.k, I.y, I.r0m, I.m, I.partials, I.counter, I.scal + 4, mp.y,
+                       vec_blocks_dev(I.m));
+}
+
+// One thread per instance: the stopping rules (Sec. 6.4), then k -> k + 1.
+__global__ void batch_finish_kernel(BatchInst *__restrict__ insts, int n, int *active_count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    BatchInst &I = insts[i];
+    if (!I.active) return;
+    const int k = I.k;
+    const bool dp = I.target > 0.0;
+    if (I.variant == CTG_BA && dp) I.resnorm = sqrt(I.scal[4]);
+    I.hist[k] = (I.variant == CTG_BA && dp) ? I.resnorm : I.rho;
+    int stop = -1;
+    if (I.breakdown) stop = CTG_STOP_BREAKDOWN;
+    else if (dp && (I.variant == CTG_AB ? I.rho : I.resnorm) <= I.target) stop = CTG_STOP_DP;
+    else if (k == I.maxit) stop = CTG_STOP_MAXIT;
+    if (stop >= 0) {
+        I.active = 0;
+        I.iters = k;
+        I.stop_reason = stop;
+        atomicSub(active_count, 1);
+    } else {
+        I.k = k + 1;
+    }
+}
+
+// Exit: y = R^{-1} gg for each finished instance's k (one warp each).
+__global__ void batch_solve_y_kernel(BatchInst *__restrict__ insts) {
+    BatchInst &I = insts[blockIdx.x];
+    const int k = I.iters, lane = threadIdx.x, ldr = I.maxit;
+    for (int i = k - 1; i >= 0; --i) {
+        double t = 0.0;
+        for (int j = i + 1 + lane; j < k; j += 32) t += I.R[(size_t)j * ldr + i] * I.y[j];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) {
+            const double d = I.R[(size_t)i * ldr + i];
+            I.y[i] = d != 0.0 ? (I.gg[i] - t) / d : 0.0;
+        }
+        __syncwarp();
+    }
 }
 
 template <typename K>
@@ -620,5 +776,56 @@ cudaError_t ctg_scale(const float *v, const double *nrm2, void *out, int dtype, 
             break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+int ctg_vec_blocks(long long L) { return (int)(((L + 3) / 4 + kThreads - 1) / kThreads); }
+
+cudaError_t ctg_batch_cgs2(BatchInst *insts, const int2 *map, int nblocks, int max_k,
+                           cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    const size_t smem = sizeof(float) * ((size_t)max_k + (size_t)kWarps * (max_k + 1));
+    auto k1 = batch_cgs_pass_kernel<false, true, true>;
+    auto k2 = batch_cgs_pass_kernel<true, true, false>;
+    auto k3 = batch_cgs_pass_kernel<true, false, true>;
+    k1<<<nblocks, kThreads, smem, st>>>(insts, map);
+    k2<<<nblocks, kThreads, smem, st>>>(insts, map);
+    k3<<<nblocks, kThreads, smem, st>>>(insts, map);
+    batch_scale_kernel<<<nblocks, kThreads, 0, st>>>(insts, map);
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_batch_prepare(int max_k) {
+    const size_t smem = sizeof(float) * ((size_t)max_k + (size_t)kWarps * (max_k + 1));
+    cudaError_t err;
+    if ((err = ensure_smem(batch_cgs_pass_kernel<false, true, true>, smem)) != cudaSuccess) return err;
+    if ((err = ensure_smem(batch_cgs_pass_kernel<true, true, false>, smem)) != cudaSuccess) return err;
+    if ((err = ensure_smem(batch_cgs_pass_kernel<true, false, true>, smem)) != cudaSuccess) return err;
+    return ensure_smem(batch_residual_kernel, sizeof(float) * (size_t)(max_k > 0 ? max_k : 1));
+}
+
+cudaError_t ctg_batch_givens(BatchInst *insts, int n_inst, cudaStream_t st) {
+    if (n_inst <= 0) return cudaSuccess;
+    batch_givens_kernel<<<n_inst, 32, 0, st>>>(insts);
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_batch_residual(BatchInst *insts, const int2 *map_m, int nblocks, int max_k,
+                               cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    const size_t smem = sizeof(float) * (size_t)(max_k > 0 ? max_k : 1);
+    batch_residual_kernel<<<nblocks, kThreads, smem, st>>>(insts, map_m);
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_batch_finish(BatchInst *insts, int n_inst, int *active_count, cudaStream_t st) {
+    if (n_inst <= 0) return cudaSuccess;
+    batch_finish_kernel<<<(n_inst + 127) / 128, 128, 0, st>>>(insts, n_inst, active_count);
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_batch_solve_y(BatchInst *insts, int n_inst, cudaStream_t st) {
+    if (n_inst <= 0) return cudaSuccess;
+    batch_solve_y_kernel<<<n_inst, 32, 0, st>>>(insts);
     return cudaGetLastError();
 }

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/ctgmres.h"
 
 #define CTG_FX_BITS 40       // back projector
@@ -118,3 +120,75 @@ cudaError_t ctg_sub_norm2(const float *a, const float *c, float *out, int64_t L,
 // nrm2 == 0).
 cudaError_t ctg_scale(const float *v, const double *nrm2, void *out, int dtype, int64_t L,
                       cudaStream_t st);
+
+// ---- batched engine (batch.cu; kernels in projectors.cu and arnoldi.cu) ----
+// Device-resident state of one instance (one solve) of a batch.  A round of
+// the batch advances every active instance by one Arnoldi step (k -> k+1)
+// with one launch per kernel for all instances; kernels read k and the
+// activity flag from here, so one captured CUDA graph serves every round.
+struct BatchInst {
+    // geometry
+    int N, n_angles, n_det, variant;      // variant: CTG_AB / CTG_BA
+    const FwdAngle *fwd;
+    const BackAngle *back;
+    int back_window;
+    int pad_stride, pad_border, pad_clamp;
+    long long n, m, L;
+    // iteration state
+    int k;                // the step to perform: orthogonalise against w_1..w_k
+    int active;           // 1 while iterating
+    int maxit;
+    int stop_reason;
+    int iters;
+    int breakdown;        // set by the Givens kernel for the finish kernel
+    double target;        // tau ||e|| (<= 0: no discrepancy stop)
+    double rho;           // last GMRES residual |g_{k+1}|
+    double resnorm;       // last ||b - A x_k|| (BA with the DP stop)
+    // buffers (FP32 basis)
+    float *W;             // (maxit + 1) x ldw
+    long long ldw;
+    float *T;             // BA: (maxit + 1) x ldt, t_j = A w_j
+    long long ldt;
+    double *H;            // (maxit + 1) x maxit, column-major, unrotated
+    double *R;            // maxit x maxit, column-major: rotated H (upper triangle)
+    double *gc, *gs, *gg; // Givens cosines, sines (maxit), rotated rhs (maxit + 1)
+    double *y;            // maxit: minus the least-squares solution (for r = r0 - T y)
+    double *hist;         // maxit + 1: history as in ctg_info
+    float *vn, *vm;       // work vectors of length n and m
+    float2 *pad;          // staged image for the forward projector
+    float *r0m;           // BA: b - A x0
+    // reduction scratch of this instance (E = 1 passes, grid G)
+    float *partials;
+    double *h1, *h2, *scal;
+    unsigned *counter;
+    int G;                // blocks of this instance's CGS2 / vector passes
+    int pad_;
+};
+
+// Block maps: entry b of a batched launch's map is (instance, local block).
+enum { CTG_PH_BACK_AB = 0, CTG_PH_PAD = 1, CTG_PH_FWD = 2, CTG_PH_BACK_BA = 3 };
+cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int phase,
+                           int max_window, cudaStream_t st);
+cudaError_t ctg_batch_pad(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st);
+cudaError_t ctg_batch_forward(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st);
+// Local block counts of one instance for the maps above.
+int ctg_back_tiles(int N);
+int ctg_pad_tiles(int N);
+int ctg_fwd_blocks(int n_angles, int n_det);
+int ctg_back_window_max();
+cudaError_t ctg_batch_cgs2(BatchInst *insts, const int2 *map, int nblocks, int max_k,
+                           cudaStream_t st);
+// Set the batched kernels' shared-memory attributes (before graph capture).
+cudaError_t ctg_batch_prepare(int max_k);
+cudaError_t ctg_batch_givens(BatchInst *insts, int n_inst, cudaStream_t st);
+cudaError_t ctg_batch_residual(BatchInst *insts, const int2 *map_m, int nblocks, int max_k,
+                               cudaStream_t st);
+cudaError_t ctg_batch_finish(BatchInst *insts, int n_inst, int *active_count, cudaStream_t st);
+// Exit: y = R^{-1} g for the instance's final k (stored with a + sign).
+cudaError_t ctg_batch_solve_y(BatchInst *insts, int n_inst, cudaStream_t st);
+int ctg_vec_blocks(long long L);          // blocks of an E = 1 vector pass over L
+
+// ---- host helpers shared by api.cu and batch.cu --------------------------
+bool ctg_geom_valid(const ctg_geom *g);
+bool ctg_opts_valid(const ctg_opts *o);
+void ctg_build_tables(const ctg_geom *g, std::vector<FwdAngle> &fw, std::vector<BackAngle> &bk);

@@ -33,11 +33,11 @@ __device__ __forceinline__ float2 lerp_pair(float v0, float v1) {
 // entries j = -1 .. N-1 of every row of x and of x^T; the other border
 // entries are zero pairs written once when the buffer is allocated.
 template <typename T>
-__global__ void pad_pairs_kernel(const T *__restrict__ x, float2 *__restrict__ pad, int N,
-                                 int stride, int border) {
+__device__ __forceinline__ void pad_pairs_block(const T *__restrict__ x, float2 *__restrict__ pad,
+                                                int N, int stride, int border, int bx, int by) {
     __shared__ float tile[kPadTile + 1][kPadTile + 2];
     float2 *xp = pad + border, *xtp = pad + (size_t)N * stride + border;
-    const int j0 = blockIdx.x * kPadTile, i0 = blockIdx.y * kPadTile;
+    const int j0 = bx * kPadTile, i0 = by * kPadTile;
     // tile[r][c] = x[i0 + r][j0 + c] for r, c in [0, 33) (0 outside)
     for (int r = threadIdx.y; r <= kPadTile; r += blockDim.y)
         for (int c = threadIdx.x; c <= kPadTile; c += blockDim.x) {
@@ -54,16 +54,22 @@ __global__ void pad_pairs_kernel(const T *__restrict__ x, float2 *__restrict__ p
         }
     }
     // entry j = -1 of each row: (0 - x[0], x[0])
-    if (blockIdx.x == 0)
+    if (bx == 0)
         for (int r = threadIdx.y * blockDim.x + threadIdx.x; r < kPadTile; r += blockDim.x * blockDim.y) {
             const int i = i0 + r;
             if (i < N) xp[(size_t)i * stride - 1] = lerp_pair(0.0f, to_f(x[(size_t)i * N]));
         }
-    if (blockIdx.y == 0)
+    if (by == 0)
         for (int c = threadIdx.y * blockDim.x + threadIdx.x; c < kPadTile; c += blockDim.x * blockDim.y) {
             const int j = j0 + c;
             if (j < N) xtp[(size_t)j * stride - 1] = lerp_pair(0.0f, to_f(x[j]));
         }
+}
+
+template <typename T>
+__global__ void pad_pairs_kernel(const T *__restrict__ x, float2 *__restrict__ pad, int N,
+                                 int stride, int border) {
+    pad_pairs_block(x, pad, N, stride, border, blockIdx.x, blockIdx.y);
 }
 
 __device__ __forceinline__ float fx_frac(long long U) {
@@ -87,14 +93,14 @@ constexpr int kFwdAngles = 8;   // warps per block, one angle each
 // the interpolation weight.  A lane outside its own chord reads zero pairs
 // in the border (or, with kClamp, a clamped index into the 2-pair border).
 template <bool kClamp>
-__global__ void __launch_bounds__(32 * kFwdAngles)
-joseph_forward_kernel(const float2 *__restrict__ pad, int N, int stride, int border,
-                      int n_angles, int n_det, const FwdAngle *__restrict__ tab,
-                      float *__restrict__ b) {
+__device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ pad, int N,
+                                                     int stride, int border, int n_angles,
+                                                     int n_det, const FwdAngle *__restrict__ tab,
+                                                     float *__restrict__ b, int bx, int by) {
     const int lane = threadIdx.x & 31;
-    const int a = blockIdx.y * kFwdAngles + (threadIdx.x >> 5);
+    const int a = by * kFwdAngles + (threadIdx.x >> 5);
     if (a >= n_angles) return;                        // whole warp
-    const int d = blockIdx.x * 32 + lane;
+    const int d = bx * 32 + lane;
     const FwdAngle t = tab[a];
     const float2 *img = pad + (t.row_driven ? 0 : (size_t)N * stride) + border;
 
@@ -158,6 +164,15 @@ joseph_forward_kernel(const float2 *__restrict__ pad, int N, int stride, int bor
     if (d < n_det) b[(size_t)a * n_det + d] = (acc0 + acc1) * t.scale;
 }
 
+template <bool kClamp>
+__global__ void __launch_bounds__(32 * kFwdAngles)
+joseph_forward_kernel(const float2 *__restrict__ pad, int N, int stride, int border,
+                      int n_angles, int n_det, const FwdAngle *__restrict__ tab,
+                      float *__restrict__ b) {
+    joseph_forward_block<kClamp>(pad, N, stride, border, n_angles, n_det, tab, b, blockIdx.x,
+                                 blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // Pixel-driven back projection.  A thread-block cluster of kBSplit CTAs owns
 // a 32 x 32 pixel tile; each CTA (256 threads, four rows each) sums a
@@ -176,17 +191,19 @@ constexpr int kBThreads = 256;
 constexpr int kBChunk = 32;      // angles staged per pass
 constexpr int kBSplit = 4;       // CTAs per cluster = angle groups per tile
 
+// Body of one CTA of the back-projection cluster for tile (bx, by).  Every
+// CTA of a cluster must call it (it synchronises the cluster twice).
 template <typename T>
-__global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
-pixel_back_tiled_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
-                        const BackAngle *__restrict__ tab, int W, const float *__restrict__ add,
-                        float *__restrict__ x) {
+__device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, int n_angles,
+                                                int n_det, const BackAngle *__restrict__ tab,
+                                                int W, const float *__restrict__ add,
+                                                float *__restrict__ x, int bx, int by) {
     extern __shared__ float2 s_pairs[];               // kBChunk * W pairs
     __shared__ float4 s_par[kBChunk];                 // cf, sf, u0' (window-relative), origin
     __shared__ float s_part[kBRows][kBThreads];       // this CTA's partial sums
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();       // == blockIdx.z
-    const int j0 = blockIdx.x * kBT, i0 = blockIdx.y * kBT;
+    const int j0 = bx * kBT, i0 = by * kBT;
     const int dj = threadIdx.x & 31, di = threadIdx.x >> 5;   // di in [0, 8)
     const float fdj = (float)dj, fdi = (float)di;
     const int per = (n_angles + kBSplit - 1) / kBSplit;
@@ -251,6 +268,14 @@ pixel_back_tiled_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
     cluster.sync();   // peers' shared memory must outlive the reads above
 }
 
+template <typename T>
+__global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
+pixel_back_tiled_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
+                        const BackAngle *__restrict__ tab, int W, const float *__restrict__ add,
+                        float *__restrict__ x) {
+    pixel_back_tile(b, N, n_angles, n_det, tab, W, add, x, blockIdx.x, blockIdx.y);
+}
+
 // Generic pixel-driven back projection (any detector pitch): 32 x 8 tiles,
 // taps read through L1 with bounds tests.
 constexpr int kBX = 32, kBY = 8, kAChunk = 256;
@@ -296,7 +321,83 @@ pixel_back_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
     }
 }
 
+// ---- batched kernels: one launch for the same phase of every instance ----
+// map[blockIdx.x] = (instance, local block of that instance's own grid).
+
+__global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
+batch_back_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ map, int phase) {
+    const int2 mp = map[blockIdx.x];
+    const BatchInst &I = insts[mp.x];
+    // the same decision in all CTAs of the cluster (they share blockIdx.x)
+    if (!I.active || ((phase == CTG_PH_BACK_AB) != (I.variant == CTG_AB))) return;
+    const int tx = (I.N + kBT - 1) / kBT;
+    const float *in = phase == CTG_PH_BACK_AB ? I.W + (size_t)(I.k - 1) * I.ldw
+                                              : I.T + (size_t)(I.k - 1) * I.ldt;
+    pixel_back_tile<float>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn,
+                           mp.y % tx, mp.y / tx);
+}
+
+__global__ void batch_pad_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
+    const int2 mp = map[blockIdx.x];
+    const BatchInst &I = insts[mp.x];
+    if (!I.active) return;
+    const int tx = (I.N + kPadTile - 1) / kPadTile;
+    // AB stages t = B w_k; BA stages w_k itself
+    const float *src = I.variant == CTG_AB ? I.vn : I.W + (size_t)(I.k - 1) * I.ldw;
+    pad_pairs_block<float>(src, I.pad, I.N, I.pad_stride, I.pad_border, mp.y % tx, mp.y / tx);
+}
+
+__global__ void __launch_bounds__(32 * kFwdAngles)
+batch_forward_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
+    const int2 mp = map[blockIdx.x];
+    const BatchInst &I = insts[mp.x];
+    if (!I.active) return;
+    const int bxn = (I.n_det + 31) / 32;
+    // AB: q = A t; BA: t_k = A w_k, kept in T
+    float *out = I.variant == CTG_AB ? I.vm : I.T + (size_t)(I.k - 1) * I.ldt;
+    if (I.pad_clamp)
+        joseph_forward_block<true>(I.pad, I.N, I.pad_stride, I.pad_border, I.n_angles, I.n_det,
+                                   I.fwd, out, mp.y % bxn, mp.y / bxn);
+    else
+        joseph_forward_block<false>(I.pad, I.N, I.pad_stride, I.pad_border, I.n_angles, I.n_det,
+                                    I.fwd, out, mp.y % bxn, mp.y / bxn);
+}
+
 }  // namespace
+
+int ctg_back_tiles(int N) {
+    const int t = (N + kBT - 1) / kBT;
+    return t * t;
+}
+int ctg_pad_tiles(int N) {
+    const int t = (N + kPadTile - 1) / kPadTile;
+    return t * t;
+}
+int ctg_fwd_blocks(int n_angles, int n_det) {
+    return ((n_det + 31) / 32) * ((n_angles + kFwdAngles - 1) / kFwdAngles);
+}
+// largest window the tiled back projector can stage in shared memory
+int ctg_back_window_max() { return (40 * 1024) / (int)(sizeof(float2) * kBChunk); }
+
+cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int phase,
+                           int max_window, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    const size_t smem = sizeof(float2) * (size_t)kBChunk * max_window;
+    batch_back_kernel<<<dim3(nblocks, 1, kBSplit), kBThreads, smem, st>>>(insts, map, phase);
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_batch_pad(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    batch_pad_kernel<<<nblocks, dim3(kPadTile, 8), 0, st>>>(insts, map);
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_batch_forward(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    batch_forward_kernel<<<nblocks, 32 * kFwdAngles, 0, st>>>(insts, map);
+    return cudaGetLastError();
+}
 
 int ctg_back_window(const BackAngle *host_tab, int n_angles) {
     // detector span of a 32 x 32 tile at any angle, plus the floor/ceil and

@@ -1,0 +1,128 @@
+"""Batched AB-/BA-GMRES (ctg_batch_*): solves of different sizes, variants,
+angle ranges and budgets advance together, one Arnoldi step per round, with
+the Givens update and the stopping rule on the device.
+
+Checked: every solve of a mixed batch agrees with the single-solve path
+(same stop, iterate within 1e-4 at the discrepancy stop, which falls in the
+well-conditioned range of these problems); a solve's result is the same,
+bit for bit, alone and in the mix; oracle parity at the discrepancy stop;
+the k = 0 stops and b = 0 inside a batch.
+"""
+import numpy as np
+import pytest
+
+from paper_2110_01481_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2110_01481_gb300 as P
+    return P
+
+
+def _case(O, N, Na, rng_deg, eta, seed):
+    og = O.Geometry(N, Na, I.detector_count(N), 0, rng_deg)
+    xt = I.random_ellipses(N, seed)
+    b, enorm = I.add_noise(O.forward(og, xt), eta, seed)
+    return og, xt.ravel(), b.astype(np.float32), enorm
+
+
+MIX = [  # N, angles, range, noise, variant, maxit, use DP
+    (64, 60, 180, 0.01, "ab", 40, True),
+    (128, 180, 180, 0.02, "ba", 40, True),
+    (96, 90, 120, 0.03, "ab", 30, True),
+    (64, 45, 180, 0.01, "ba", 12, False),
+    (160, 90, 180, 0.005, "ab", 25, False),
+    (128, 120, 120, 0.015, "ba", 40, True),
+]
+
+
+def _problems(P, O):
+    cases, probs = [], []
+    for i, (N, Na, R, eta, v, maxit, dp) in enumerate(MIX):
+        og, xt, b, enorm = _case(O, N, Na, R, eta, 3000 + i)
+        cases.append((og, xt, b, enorm))
+        probs.append({"geometry": P.Geometry(N, Na, og.n_det, 0, R), "variant": v,
+                      "maxit": maxit, "tau": 1.02, "noise_norm": enorm if dp else None})
+    return cases, probs
+
+
+def test_batch_matches_single_solves(P, oracle_mod):
+    import torch
+    cases, probs = _problems(P, oracle_mod)
+    bs = [torch.tensor(c[2], device="cuda") for c in cases]
+    batch = P.Batch(probs)
+    res = batch.solve(bs)
+    torch.cuda.synchronize()
+    for (og, xt, b, enorm), p, r, bt in zip(cases, probs, res, bs):
+        fn = P.ab_gmres if p["variant"] == "ab" else P.ba_gmres
+        ref = fn(p["geometry"], bt, p["maxit"], tau=1.02, noise_norm=p["noise_norm"])
+        torch.cuda.synchronize()
+        assert r.stop_reason == ref.stop_reason
+        assert abs(r.iters - ref.iters) <= (1 if p["noise_norm"] else 0)
+        if r.iters == ref.iters:
+            d = (r.x - ref.x).double().norm() / ref.x.double().norm()
+            # no-DP runs to a fixed k are compared where the iterate is well
+            # conditioned (k <= 25 here); DP stops fall there too
+            assert d.item() <= 1e-4, (p, d.item())
+        assert r.resnorm == pytest.approx(ref.resnorm, rel=1e-3)
+        if p["noise_norm"]:
+            assert r.resnorm <= 1.02 * enorm * (1 + 1e-5)
+
+
+def test_batch_result_is_independent_of_the_mix(P, oracle_mod):
+    import torch
+    cases, probs = _problems(P, oracle_mod)
+    bs = [torch.tensor(c[2], device="cuda") for c in cases]
+    mixed = P.Batch(probs).solve(bs)
+    for i in (1, 4):
+        alone = P.Batch([probs[i]]).solve([bs[i]])[0]
+        torch.cuda.synchronize()
+        assert alone.iters == mixed[i].iters
+        assert torch.equal(alone.x, mixed[i].x)
+
+
+def test_batch_discrepancy_stop_matches_oracle(P, oracle_mod):
+    import torch
+    O = oracle_mod
+    cases, probs = _problems(P, O)
+    sel = [0, 1]
+    batch = P.Batch([probs[i] for i in sel])
+    res = batch.solve([torch.tensor(cases[i][2], device="cuda") for i in sel])
+    for i, r in zip(sel, res):
+        og, xt, b, enorm = cases[i]
+        A = lambda v: O.forward(og, v)
+        B = lambda v: O.backproject(og, v)
+        solver = O.ab_gmres if probs[i]["variant"] == "ab" else O.ba_gmres
+        ref = solver(A, B, b.astype(np.float64), probs[i]["maxit"], tau=1.02, noise_norm=enorm)
+        assert r.stop_reason == 1 and ref["stop_reason"] == 1
+        if r.iters == ref["k"]:
+            x = r.x.double().cpu().numpy()
+            assert np.linalg.norm(x - ref["x"]) <= 1e-4 * np.linalg.norm(ref["x"])
+        else:
+            assert abs(r.iters - ref["k"]) == 1
+
+
+def test_batch_zero_iteration_stops(P, oracle_mod):
+    import torch
+    O = oracle_mod
+    og, xt, b, enorm = _case(O, 48, 40, 180, 0.01, 3100)
+    g = P.Geometry(48, 40, og.n_det)
+    x0 = torch.tensor(xt, dtype=torch.float32, device="cuda")
+    bb = P.project(g, x0)
+    probs = [{"geometry": g, "variant": "ab", "maxit": 5, "noise_norm": 1e-3},
+             {"geometry": g, "variant": "ba", "maxit": 5},
+             {"geometry": g, "variant": "ba", "maxit": 60, "tau": 1.02, "noise_norm": enorm}]
+    res = P.Batch(probs).solve([bb, torch.zeros_like(bb), torch.tensor(b, device="cuda")],
+                               x0s=[x0, None, None])
+    torch.cuda.synchronize()
+    assert res[0].iters == 0 and res[0].stop_reason == 1 and torch.equal(res[0].x, x0)
+    assert res[1].iters == 0 and res[1].stop_reason == 2 and torch.count_nonzero(res[1].x) == 0
+    assert res[2].iters > 0 and res[2].stop_reason == 1
