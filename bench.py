@@ -363,6 +363,129 @@ def run_batch(args):
         "workspace_GB": batch.workspace_bytes / 1e9}))
 
 
+def serve_requests(P, torch, dev, count, seed0=5000):
+    """The served workload: `count` seeded requests, each drawing N in
+    {128, 256, 512, 1024}, angle count in {60, 180, 360, 720} (a quarter
+    limited-angle over [0, 120)), noise 0.5-5%, variant AB or BA and maxit
+    in [50, 200], discrepancy stop tau = 1.02; random-ellipse phantoms."""
+    rng = np.random.default_rng(seed0)
+    reqs = []
+    for i in range(count):
+        N = int(rng.choice([128, 256, 512, 1024]))
+        Na = int(rng.choice([60, 180, 360, 720]))
+        R = 120 if rng.uniform() < 0.25 else 180
+        eta = float(rng.uniform(0.005, 0.05))
+        variant = "ab" if rng.uniform() < 0.5 else "ba"
+        maxit = int(rng.integers(50, 201))
+        g = P.Geometry(N, Na, I.detector_count(N), 0, R)
+        xbar = torch.tensor(I.random_ellipses(N, seed0 + i).ravel(), dtype=torch.float32, device=dev)
+        bbar = P.project(g, xbar).double().cpu().numpy()
+        b, enorm = I.add_noise(bbar, eta, seed0 + i)
+        reqs.append({"geometry": g, "variant": variant, "maxit": maxit, "tau": TAU,
+                     "noise_norm": enorm, "b": torch.tensor(b, dtype=torch.float32, device=dev),
+                     "xbar": xbar})
+    return reqs
+
+
+def _latency_stats(arrive, done):
+    lat = np.array([done[i] - arrive[i] for i in range(len(arrive))])
+    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3)}
+
+
+def serve_fifo(P, torch, reqs, arrive):
+    """Plain server: one solve at a time through the single-solve path, in
+    arrival order."""
+    done, iters, outs = [0.0] * len(reqs), 0, []
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if arrive[i] > now:
+            time.sleep(arrive[i] - now)
+        fn = P.ab_gmres if r["variant"] == "ab" else P.ba_gmres
+        res = fn(r["geometry"], r["b"], r["maxit"], tau=r["tau"], noise_norm=r["noise_norm"])
+        torch.cuda.synchronize()
+        done[i] = time.perf_counter() - t0
+        iters += res.iters
+        outs.append(res.x)
+    return done, iters, outs, done[-1]
+
+
+def serve_engine(P, torch, reqs, arrive, slots, budget, rounds):
+    """Continuous batching: arrived requests are admitted while slots and
+    memory allow; every step advances all running solves by `rounds`
+    Arnoldi steps."""
+    eng = P.Engine(slots, budget)
+    done, outs, iters = [0.0] * len(reqs), [None] * len(reqs), 0
+    nxt, queue, finished = 0, [], 0
+    t0 = time.perf_counter()
+    while finished < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and arrive[nxt] <= now:
+            queue.append(nxt)
+            nxt += 1
+        while queue:
+            r = reqs[queue[0]]
+            if eng.submit(r["geometry"], r["b"], r["variant"], r["maxit"], tau=r["tau"],
+                          noise_norm=r["noise_norm"], tag=queue[0]) is None:
+                break
+            queue.pop(0)
+        if eng.in_flight == 0:
+            if nxt < len(reqs):
+                time.sleep(max(0.0, arrive[nxt] - (time.perf_counter() - t0)))
+            continue
+        for t, res in eng.step(rounds):
+            done[t] = time.perf_counter() - t0
+            outs[t] = res.x
+            iters += res.iters
+            finished += 1
+    del eng
+    return done, iters, outs, max(done)
+
+
+def run_serve(args):
+    """Poisson arrivals at fractions of the one-at-a-time capacity; p50/p99
+    latency (completion - arrival) and throughput of the continuous-batching
+    engine against the plain one-at-a-time server on the same requests."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2110_01481_gb300 as P
+    dev = torch.device("cuda", 0)
+    reqs = serve_requests(P, torch, dev, args.serve_requests)
+    xbars = [r.pop("xbar") for r in reqs]
+
+    def err(outs):
+        return float(np.mean([((o - x).norm() / x.norm()).item() for o, x in zip(outs, xbars)]))
+
+    # warm-up of both paths (graph capture, workspaces, module loads)
+    serve_fifo(P, torch, reqs[:8], [0.0] * 8)
+    serve_engine(P, torch, reqs[:8], [0.0] * 8, args.serve_slots, args.serve_budget_gb << 30, 4)
+    # capacity of the plain server: all requests back to back
+    d, it_fifo, outs, span = serve_fifo(P, torch, reqs, [0.0] * len(reqs))
+    capacity = len(reqs) / span
+    base = {"workload": f"{len(reqs)} requests, N in {{128,256,512,1024}}, angles in {{60,180,360,720}}, "
+                        "25% limited-angle [0,120), noise 0.5-5%, AB/BA, maxit 50-200, DP tau=1.02, "
+                        "Poisson arrivals",
+            "one_at_a_time_capacity_req_per_s": capacity,
+            "one_at_a_time_iterations_per_s": it_fifo / span,
+            "slots": args.serve_slots, "budget_GB": args.serve_budget_gb, "rounds_per_step": 4}
+    print(json.dumps(base), flush=True)
+    rng = np.random.default_rng(5999)
+    gaps = rng.exponential(1.0, len(reqs))
+    for frac in [float(f) for f in args.serve_rates.split(",")]:
+        rate = frac * capacity
+        arrive = list(np.cumsum(gaps) / rate)
+        row = {"rate_x_capacity": frac, "offered_req_per_s": rate}
+        for name, fn in (("engine", lambda a: serve_engine(P, torch, reqs, a, args.serve_slots,
+                                                            args.serve_budget_gb << 30, 4)),
+                         ("one_at_a_time", lambda a: serve_fifo(P, torch, reqs, a))):
+            done, iters, outs, span = fn(arrive)
+            row[name] = dict(_latency_stats(arrive, done), served_req_per_s=len(reqs) / span,
+                             iterations_per_s=iters / span, mean_rel_error_vs_truth=err(outs))
+        print(json.dumps(row), flush=True)
+
+
 def make_instance(P, torch, dev, seed):
     """Seeded phantom, b = A x_bar + e with the library's own A (the oracle is
     not used on the product path)."""
@@ -633,6 +756,12 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="batched engine vs one-at-a-time solves on 64 mixed instances")
     ap.add_argument("--batch-size", type=int, default=64)
+    ap.add_argument("--serve", action="store_true",
+                    help="Poisson-arrival serving: continuous batching vs one-at-a-time")
+    ap.add_argument("--serve-requests", type=int, default=500)
+    ap.add_argument("--serve-rates", default="0.25,0.5,0.75,0.9,1.1")
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-budget-gb", type=int, default=96)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -642,6 +771,8 @@ def main():
         run_precision(args)
     elif args.batch:
         run_batch(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_gpu(args)
 

@@ -50,7 +50,10 @@ enum {
     CTG_ERR_OOM = -2,          /* device allocation failed                   */
     CTG_ERR_CUDA = -3,         /* a CUDA runtime call failed                 */
     CTG_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up         */
-    CTG_ERR_WORKSPACE = -5     /* caller workspace smaller than required     */
+    CTG_ERR_WORKSPACE = -5,    /* caller workspace smaller than required     */
+    CTG_ERR_BUSY = -6          /* serving engine: no free slot, or the
+                                  request does not fit the memory budget now;
+                                  retry after a completion                   */
 };
 
 enum { CTG_AB = 0, CTG_BA = 1 };                       /* solver variant    */
@@ -181,6 +184,38 @@ size_t ctg_batch_workspace_bytes(const ctg_batch *batch);
 int ctg_batch_solve(ctg_batch *batch, const float *const *b_dev, const float *const *x0_dev,
                     float *const *x_dev, ctg_info *infos, void *stream);
 void ctg_batch_destroy(ctg_batch *batch);
+
+/* Serving engine: continuous batching of independent solves (the batched
+ * rounds above, with solves joining and leaving between steps).
+ * ctg_engine_create: at most max_slots solves in flight (1..4096), whose
+ *   workspaces (allocated per solve, stream-ordered, from a memory pool of
+ *   the engine that keeps up to hbm_budget_bytes mapped) together stay
+ *   within hbm_budget_bytes.  Uses the current device.
+ * ctg_engine_request_bytes: device bytes one solve occupies while in flight
+ *   (its Krylov basis dominates: the storage law k L of Table 3), or 0 if the
+ *   arguments are invalid (FP32 basis, maxit <= 1024 as for ctg_batch).
+ * ctg_engine_submit: admits one solve, or returns CTG_ERR_BUSY if no slot is
+ *   free or its bytes do not fit the remaining budget, CTG_ERR_OOM if they
+ *   exceed the whole budget.  b_dev must be ready
+ *   on `stream`; b_dev, x0_dev (or NULL), x_dev and history (NULL or maxit + 1
+ *   doubles of host memory) must stay valid until the solve is reported.
+ *   Computes r0 and starts the solve before returning.
+ * ctg_engine_step: runs `rounds` Arnoldi rounds of every running solve, then
+ *   forms the iterate x of up to max_done finished solves and reports their
+ *   tags and ctg_info (x_dev is complete when reported) and releases their
+ *   memory; *n_done is the number reported.  Returns when done.
+ * ctg_engine_in_flight: solves admitted and not yet reported.
+ * A solve's result does not depend on which others share the engine. */
+typedef struct ctg_engine ctg_engine;
+int ctg_engine_create(ctg_ctx *ctx, int32_t max_slots, size_t hbm_budget_bytes, ctg_engine **out);
+size_t ctg_engine_request_bytes(const ctg_geom *g, int32_t variant, const ctg_opts *o);
+int ctg_engine_submit(ctg_engine *engine, const ctg_geom *g, int32_t variant, const ctg_opts *o,
+                      const float *b_dev, const float *x0_dev, float *x_dev, double *history,
+                      int64_t tag, void *stream);
+int ctg_engine_step(ctg_engine *engine, int32_t rounds, int32_t max_done, int64_t *done_tags,
+                    ctg_info *done_infos, int32_t *n_done);
+int32_t ctg_engine_in_flight(const ctg_engine *engine);
+void ctg_engine_destroy(ctg_engine *engine);
 
 /* One classical Gram-Schmidt step with reorthogonalisation (CGS2) of q
  * against the k orthonormal columns of W, the Arnoldi step of Sec. 2 with

@@ -18,6 +18,7 @@ CTG_ERR_OOM = -2
 CTG_ERR_CUDA = -3
 CTG_ERR_TIMEOUT = -4
 CTG_ERR_WORKSPACE = -5
+CTG_ERR_BUSY = -6
 CTG_AB, CTG_BA = 0, 1
 CTG_STOP_MAXIT, CTG_STOP_DP, CTG_STOP_BREAKDOWN = 0, 1, 2
 CTG_BASIS_FP32, CTG_BASIS_BF16, CTG_BASIS_FP16 = 0, 1, 2
@@ -60,7 +61,9 @@ EXPORTS = ("ctg_create", "ctg_destroy", "ctg_project", "ctg_backproject",
            "ctg_workspace_bytes", "ctg_workspace_layout", "ctg_ab_gmres",
            "ctg_ba_gmres", "ctg_cgs2_scratch_bytes", "ctg_cgs2", "ctg_cgs2_noalloc",
            "ctg_set_timing", "ctg_get_timing", "ctg_status_string",
-           "ctg_batch_create", "ctg_batch_workspace_bytes", "ctg_batch_solve", "ctg_batch_destroy")
+           "ctg_batch_create", "ctg_batch_workspace_bytes", "ctg_batch_solve", "ctg_batch_destroy",
+           "ctg_engine_create", "ctg_engine_request_bytes", "ctg_engine_submit",
+           "ctg_engine_step", "ctg_engine_in_flight", "ctg_engine_destroy")
 
 
 def _declare(lib):
@@ -99,6 +102,20 @@ def _declare(lib):
     lib.ctg_batch_solve.restype = ctypes.c_int
     lib.ctg_batch_destroy.argtypes = [vp]
     lib.ctg_batch_destroy.restype = None
+    lib.ctg_engine_create.argtypes = [vp, i32, sz, ctypes.POINTER(vp)]
+    lib.ctg_engine_create.restype = ctypes.c_int
+    lib.ctg_engine_request_bytes.argtypes = [G, i32, O]
+    lib.ctg_engine_request_bytes.restype = sz
+    lib.ctg_engine_submit.argtypes = [vp, G, i32, O, vp, vp, vp, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.c_int64, vp]
+    lib.ctg_engine_submit.restype = ctypes.c_int
+    lib.ctg_engine_step.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(CtgInfo), ctypes.POINTER(i32)]
+    lib.ctg_engine_step.restype = ctypes.c_int
+    lib.ctg_engine_in_flight.argtypes = [vp]
+    lib.ctg_engine_in_flight.restype = i32
+    lib.ctg_engine_destroy.argtypes = [vp]
+    lib.ctg_engine_destroy.restype = None
     lib.ctg_status_string.argtypes = [ctypes.c_int]
     lib.ctg_status_string.restype = ctypes.c_char_p
     return lib

@@ -308,3 +308,96 @@ class Batch:
                     nat.lib().ctg_batch_destroy(h)
             except Exception:
                 pass
+
+
+class Engine:
+    """Serving engine (ctg_engine_*): continuous batching of independent
+    AB-/BA-GMRES solves.  ``submit`` admits a solve while others run, if a
+    slot is free and its workspace fits the device-memory budget; ``step``
+    advances every running solve by ``rounds`` Arnoldi steps and returns the
+    solves that finished, as (tag, SolveResult) pairs.  The tensors of a
+    solve are held here until it is reported."""
+
+    def __init__(self, max_slots, hbm_budget_bytes, device=None):
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.max_slots = int(max_slots)
+        self.ctx = Context.get(self.device)
+        self.handle = ctypes.c_void_p()
+        self._held = {}
+        self._next_tag = 0
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().ctg_engine_create(self.ctx.handle, self.max_slots, int(hbm_budget_bytes),
+                                                  ctypes.byref(self.handle)), "ctg_engine_create")
+
+    @staticmethod
+    def request_bytes(geometry, variant, maxit, tau=1.0, noise_norm=None) -> int:
+        """Device bytes one solve occupies while in flight (0: invalid)."""
+        g = geometry.c()
+        o = _opts(maxit, tau, noise_norm)
+        v = nat.CTG_AB if variant == "ab" else nat.CTG_BA
+        return int(nat.lib().ctg_engine_request_bytes(ctypes.byref(g), v, ctypes.byref(o)))
+
+    @property
+    def in_flight(self) -> int:
+        return int(nat.lib().ctg_engine_in_flight(self.handle))
+
+    def submit(self, geometry, b, variant="ab", maxit=100, tau=1.0, noise_norm=None,
+               x0=None, out=None, tag=None):
+        """Admit one solve; returns its tag, or None if the engine is busy
+        (no free slot, or not enough of the memory budget left)."""
+        if tag is None:
+            tag = self._next_tag
+        self._next_tag = max(self._next_tag, int(tag) + 1)
+        if out is None:
+            out = torch.empty(geometry.n, device=self.device, dtype=torch.float32)
+        g = geometry.c()
+        o = _opts(maxit, tau, noise_norm)
+        hist = (ctypes.c_double * (maxit + 1))(*([math.nan] * (maxit + 1)))
+        pb = _dev_ptr(b, geometry.m, "b")
+        px = _dev_ptr(out, geometry.n, "x")
+        px0 = _dev_ptr(x0, geometry.n, "x0") if x0 is not None else None
+        with torch.cuda.device(self.device):
+            rc = nat.lib().ctg_engine_submit(self.handle, ctypes.byref(g),
+                                             nat.CTG_AB if variant == "ab" else nat.CTG_BA,
+                                             ctypes.byref(o), pb, px0, px, hist, int(tag),
+                                             _stream(self.device))
+        if rc == nat.CTG_ERR_BUSY:
+            return None
+        nat.check(rc, "ctg_engine_submit")
+        self._held[int(tag)] = (b, x0, out, hist)
+        return int(tag)
+
+    def step(self, rounds=4):
+        """Run ``rounds`` rounds; returns [(tag, SolveResult)] of the solves
+        that finished (their x is complete)."""
+        cap = max(self.max_slots, 1)
+        tags = (ctypes.c_int64 * cap)()
+        infos = (nat.CtgInfo * cap)()
+        n = ctypes.c_int32(0)
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().ctg_engine_step(self.handle, int(rounds), cap, tags, infos,
+                                                ctypes.byref(n)), "ctg_engine_step")
+        done = []
+        for i in range(n.value):
+            t = int(tags[i])
+            _, _, out, hist = self._held.pop(t)
+            inf = infos[i]
+            done.append((t, SolveResult(out, inf.iters, inf.stop_reason, inf.resnorm, inf.rho,
+                                        list(hist[: inf.iters + 1]))))
+        return done
+
+    def drain(self, rounds=4):
+        """Step until every admitted solve is reported."""
+        done = []
+        while self.in_flight:
+            done += self.step(rounds)
+        return done
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and nat._lib is not None:
+            try:
+                with torch.cuda.device(self.device):
+                    nat.lib().ctg_engine_destroy(h)
+            except Exception:
+                pass

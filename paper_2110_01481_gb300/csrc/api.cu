@@ -859,6 +859,7 @@ const char *ctg_status_string(int status) {
         case CTG_ERR_CUDA: return "CUDA runtime error";
         case CTG_ERR_TIMEOUT: return "device-side wait timed out";
         case CTG_ERR_WORKSPACE: return "workspace too small";
+        case CTG_ERR_BUSY: return "no free slot or memory budget; retry after a completion";
         default: return "unknown status";
     }
 }

@@ -146,23 +146,59 @@ void release(ctg_batch *b) {
     delete b;
 }
 
-int capture_round(ctg_batch *b) {
+// Everything one captured round needs: the instance array, the block maps
+// (offsets / lengths into one map array) and the launch limits.
+struct RoundSpec {
+    BatchInst *insts;
+    int n_inst;
+    const int2 *maps;
+    int map_back, n_back, map_pad, n_pad, map_fwd, n_fwd, map_cgs, n_cgs, map_m, n_m;
+    int max_window, max_maxit;
+    int *d_active;
+};
+
+// Build the block maps of instances `ids` (indices into the instance array).
+template <typename Plans>
+void build_maps(const Plans &plans, const std::vector<int> &ids, std::vector<int2> &maps, RoundSpec &rs) {
+    maps.clear();
+    auto add = [&](int &off, int &len, auto count) {
+        off = (int)maps.size();
+        for (int i : ids) {
+            const int c = count(plans[i]);
+            for (int j = 0; j < c; ++j) maps.push_back(make_int2(i, j));
+        }
+        len = (int)maps.size() - off;
+    };
+    add(rs.map_back, rs.n_back, [](const InstPlan &p) { return ctg_back_tiles(p.g.N); });
+    add(rs.map_pad, rs.n_pad, [](const InstPlan &p) { return ctg_pad_tiles(p.g.N); });
+    add(rs.map_fwd, rs.n_fwd, [](const InstPlan &p) { return ctg_fwd_blocks(p.g.n_angles, p.g.n_det); });
+    add(rs.map_cgs, rs.n_cgs, [](const InstPlan &p) {
+        return ctg_vec_blocks(p.variant == CTG_BA ? (long long)p.g.N * p.g.N
+                                                  : (long long)p.g.n_angles * p.g.n_det);
+    });
+    add(rs.map_m, rs.n_m, [](const InstPlan &p) {
+        return (p.variant == CTG_BA && p.o.noise_norm > 0.0)
+                   ? ctg_vec_blocks((long long)p.g.n_angles * p.g.n_det) : 0;
+    });
+}
+
+int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out) {
     cudaGraph_t graph = nullptr;
-    B_CK(ctg_batch_prepare(b->max_maxit));   // kernel attributes, set outside the capture
-    B_CK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+    B_CK(ctg_batch_prepare(r.max_maxit));   // kernel attributes, set outside the capture
+    B_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    const int2 *M = b->d_maps;
-    if (e == cudaSuccess) e = ctg_batch_back(b->d_insts, M + b->map_back, b->n_back, CTG_PH_BACK_AB, b->max_window, b->st);
-    if (e == cudaSuccess) e = ctg_batch_pad(b->d_insts, M + b->map_pad, b->n_pad, b->st);
-    if (e == cudaSuccess) e = ctg_batch_forward(b->d_insts, M + b->map_fwd, b->n_fwd, b->st);
-    if (e == cudaSuccess) e = ctg_batch_back(b->d_insts, M + b->map_back, b->n_back, CTG_PH_BACK_BA, b->max_window, b->st);
-    if (e == cudaSuccess) e = ctg_batch_cgs2(b->d_insts, M + b->map_cgs, b->n_cgs, b->max_maxit, b->st);
-    if (e == cudaSuccess) e = ctg_batch_givens(b->d_insts, b->n, b->st);
-    if (e == cudaSuccess) e = ctg_batch_residual(b->d_insts, M + b->map_m, b->n_m, b->max_maxit, b->st);
-    if (e == cudaSuccess) e = ctg_batch_finish(b->d_insts, b->n, b->d_active, b->st);
-    cudaError_t e2 = cudaStreamEndCapture(b->st, &graph);
+    const int2 *M = r.maps;
+    if (e == cudaSuccess) e = ctg_batch_back(r.insts, M + r.map_back, r.n_back, CTG_PH_BACK_AB, r.max_window, st);
+    if (e == cudaSuccess) e = ctg_batch_pad(r.insts, M + r.map_pad, r.n_pad, st);
+    if (e == cudaSuccess) e = ctg_batch_forward(r.insts, M + r.map_fwd, r.n_fwd, st);
+    if (e == cudaSuccess) e = ctg_batch_back(r.insts, M + r.map_back, r.n_back, CTG_PH_BACK_BA, r.max_window, st);
+    if (e == cudaSuccess) e = ctg_batch_cgs2(r.insts, M + r.map_cgs, r.n_cgs, r.max_maxit, st);
+    if (e == cudaSuccess) e = ctg_batch_givens(r.insts, r.n_inst, st);
+    if (e == cudaSuccess) e = ctg_batch_residual(r.insts, M + r.map_m, r.n_m, r.max_maxit, st);
+    if (e == cudaSuccess) e = ctg_batch_finish(r.insts, r.n_inst, r.d_active, st);
+    cudaError_t e2 = cudaStreamEndCapture(st, &graph);
     if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->round, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     return ck(e);
 }
@@ -208,25 +244,15 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
     if (rc == CTG_OK) rc = ck(cudaMemset(b->ws, 0, total));
     // block maps
     std::vector<int2> maps;
-    auto add_map = [&](int &off, int &len, auto count) {
-        off = (int)maps.size();
-        for (int i = 0; i < n; ++i) {
-            const int c = count(b->inst[i]);
-            for (int j = 0; j < c; ++j) maps.push_back(make_int2(i, j));
-        }
-        len = (int)maps.size() - off;
-    };
-    add_map(b->map_back, b->n_back, [](const InstPlan &p) { return ctg_back_tiles(p.g.N); });
-    add_map(b->map_pad, b->n_pad, [](const InstPlan &p) { return ctg_pad_tiles(p.g.N); });
-    add_map(b->map_fwd, b->n_fwd, [](const InstPlan &p) { return ctg_fwd_blocks(p.g.n_angles, p.g.n_det); });
-    add_map(b->map_cgs, b->n_cgs, [](const InstPlan &p) {
-        return ctg_vec_blocks(p.variant == CTG_BA ? (long long)p.g.N * p.g.N
-                                                  : (long long)p.g.n_angles * p.g.n_det);
-    });
-    add_map(b->map_m, b->n_m, [](const InstPlan &p) {
-        return (p.variant == CTG_BA && p.o.noise_norm > 0.0)
-                   ? ctg_vec_blocks((long long)p.g.n_angles * p.g.n_det) : 0;
-    });
+    std::vector<int> ids(n);
+    for (int i = 0; i < n; ++i) ids[i] = i;
+    RoundSpec spec{};
+    build_maps(b->inst, ids, maps, spec);
+    b->map_back = spec.map_back; b->n_back = spec.n_back;
+    b->map_pad = spec.map_pad; b->n_pad = spec.n_pad;
+    b->map_fwd = spec.map_fwd; b->n_fwd = spec.n_fwd;
+    b->map_cgs = spec.map_cgs; b->n_cgs = spec.n_cgs;
+    b->map_m = spec.map_m; b->n_m = spec.n_m;
     if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_maps, sizeof(int2) * (maps.empty() ? 1 : maps.size())));
     if (rc == CTG_OK && !maps.empty())
         rc = ck(cudaMemcpy(b->d_maps, maps.data(), sizeof(int2) * maps.size(), cudaMemcpyHostToDevice));
@@ -245,7 +271,12 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
             rc = ck(cudaMemcpy((void *)p.d.back, bk[i].data(), sizeof(BackAngle) * bk[i].size(), cudaMemcpyHostToDevice));
         p.d.back_window = ctg_back_window(bk[i].data(), p.g.n_angles);
     }
-    if (rc == CTG_OK) rc = capture_round(b);
+    if (rc == CTG_OK) {
+        RoundSpec r{b->d_insts, n, b->d_maps, b->map_back, b->n_back, b->map_pad, b->n_pad,
+                    b->map_fwd, b->n_fwd, b->map_cgs, b->n_cgs, b->map_m, b->n_m,
+                    b->max_window, b->max_maxit, b->d_active};
+        rc = capture_round(r, b->st, &b->round);
+    }
     if (rc != CTG_OK) {
         release(b);
         return rc;
@@ -258,6 +289,106 @@ extern "C" void ctg_batch_destroy(ctg_batch *b) { release(b); }
 
 extern "C" size_t ctg_batch_workspace_bytes(const ctg_batch *b) { return b ? b->ws_bytes : 0; }
 
+namespace {
+
+// Enqueue the start of one solve: r0 (AB: b - A x0 in vm; BA: b - A x0 in
+// r0m and B r0 in vn), ||r0||^2 in scal[2] and (BA) ||b - A x0||^2 in
+// scal[4]; copies scal[0..7] to `stage` (pinned).
+int enqueue_start(InstPlan &p, const float *b, const float *x0, double *stage, cudaStream_t st) {
+    BatchInst &d = p.d;
+    const RedScratch rs = scratch_of(d);
+    const PadLayout pl = ctg_pad_layout(p.g.N, p.g.det_spacing);
+    B_CK(cudaMemsetAsync(d.counter, 0, 4 * sizeof(unsigned), st));
+    B_CK(cudaMemsetAsync(d.gg, 0, sizeof(double) * (p.o.maxit + 1), st));
+    B_CK(cudaMemsetAsync(d.H, 0, sizeof(double) * (size_t)(p.o.maxit + 1) * p.o.maxit, st));
+    B_CK(cudaMemsetAsync(d.hist, 0, sizeof(double) * (p.o.maxit + 1), st));
+    B_CK(cudaMemsetAsync(d.pad, 0, sizeof(float) * pl.floats, st));
+    if (x0) {
+        B_CK(ctg_launch_pad(x0, CTG_BASIS_FP32, d.pad, p.g.N, pl, st));
+        B_CK(ctg_launch_forward(d.pad, p.g.N, pl, p.g.n_angles, p.g.n_det, d.fwd, d.vm, st));
+    }
+    if (p.variant == CTG_AB) {
+        B_CK(ctg_sub_norm2(b, x0 ? d.vm : nullptr, d.vm, d.m, d.scal + 2, rs, st));
+    } else {
+        B_CK(ctg_sub_norm2(b, x0 ? d.vm : nullptr, d.r0m, d.m, d.scal + 4, rs, st));
+        B_CK(ctg_launch_back(d.r0m, CTG_BASIS_FP32, p.g.N, p.g.n_angles, p.g.n_det, d.back,
+                             d.back_window, nullptr, d.vn, st));
+        B_CK(ctg_sub_norm2(d.vn, nullptr, nullptr, d.n, d.scal + 2, rs, st));
+    }
+    B_CK(cudaMemcpyAsync(stage, d.scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+    return CTG_OK;
+}
+
+// After enqueue_start has completed (stage holds scal): either a k = 0 stop
+// (returns 0, the solve is finished with x = x0) or w_1 = r0 / beta and the
+// rotated right-hand side beta e1 are enqueued (returns 1, the solve is
+// active).  stage[6] is used as the upload slot for beta.
+int activate(InstPlan &p, double *stage, ctg_info *info, cudaStream_t st, int *active_out) {
+    BatchInst &d = p.d;
+    const double beta = std::sqrt(stage[2]);
+    const double res0 = p.variant == CTG_AB ? beta : std::sqrt(stage[4]);
+    d.k = 1;
+    d.iters = 0;
+    d.breakdown = 0;
+    d.rho = beta;
+    d.resnorm = res0;
+    d.stop_reason = CTG_STOP_MAXIT;
+    info->iters = 0;
+    info->stop_reason = CTG_STOP_MAXIT;
+    info->rho = beta;
+    info->resnorm = res0;
+    if (info->history) info->history[0] = d.target > 0.0 ? res0 : beta;
+    const bool dp0 = d.target > 0.0 && res0 <= d.target;
+    if (dp0 || beta == 0.0) {
+        d.active = 0;
+        d.stop_reason = dp0 ? CTG_STOP_DP : CTG_STOP_BREAKDOWN;
+        info->stop_reason = d.stop_reason;
+        *active_out = 0;
+        return CTG_OK;
+    }
+    d.active = 1;
+    B_CK(ctg_scale(p.variant == CTG_AB ? d.vm : d.vn, d.scal + 2, d.W, CTG_BASIS_FP32, d.L, st));
+    stage[6] = beta;
+    B_CK(cudaMemcpyAsync(d.gg, &stage[6], sizeof(double), cudaMemcpyHostToDevice, st));
+    *active_out = 1;
+    return CTG_OK;
+}
+
+// Enqueue the end of a finished solve (d: its device state after the
+// rounds, with y = R^{-1} g already solved): x = x0 + B W y (AB) or
+// x0 + W y (BA), ||b - A x||^2 into stage[5], the history into the caller's
+// array.  The caller reads stage[5] after synchronising.
+int enqueue_finish(const InstPlan &p, const BatchInst &d, const float *b, const float *x0, float *x,
+                   ctg_info *info, double *stage, cudaStream_t st) {
+    const RedScratch rs = scratch_of(d);
+    const PadLayout pl = ctg_pad_layout(p.g.N, p.g.det_spacing);
+    const int k = d.iters;
+    info->iters = k;
+    info->stop_reason = d.stop_reason;
+    if (k == 0) {
+        if (x0) B_CK(cudaMemcpyAsync(x, x0, sizeof(float) * d.n, cudaMemcpyDeviceToDevice, st));
+        else B_CK(cudaMemsetAsync(x, 0, sizeof(float) * d.n, st));
+        return CTG_OK;
+    }
+    info->rho = d.rho;
+    if (p.variant == CTG_AB) {
+        B_CK(ctg_gemv(d.W, CTG_BASIS_FP32, d.ldw, d.m, k, d.y, nullptr, d.vm, st));
+        B_CK(ctg_launch_back(d.vm, CTG_BASIS_FP32, p.g.N, p.g.n_angles, p.g.n_det, d.back,
+                             d.back_window, x0, x, st));
+    } else {
+        B_CK(ctg_gemv(d.W, CTG_BASIS_FP32, d.ldw, d.n, k, d.y, x0, x, st));
+    }
+    B_CK(ctg_launch_pad(x, CTG_BASIS_FP32, d.pad, p.g.N, pl, st));
+    B_CK(ctg_launch_forward(d.pad, p.g.N, pl, p.g.n_angles, p.g.n_det, d.fwd, d.vm, st));
+    B_CK(ctg_sub_norm2(b, d.vm, nullptr, d.m, d.scal + 5, rs, st));
+    B_CK(cudaMemcpyAsync(stage + 5, d.scal + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (info->history)
+        B_CK(cudaMemcpyAsync(info->history + 1, d.hist + 1, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    return CTG_OK;
+}
+
+}  // namespace
+
 extern "C" int ctg_batch_solve(ctg_batch *b, const float *const *b_dev, const float *const *x0_dev,
                                float *const *x_dev, ctg_info *infos, void *stream) {
     if (!b || !b_dev || !x_dev || !infos) return CTG_ERR_INVALID_ARG;
@@ -268,61 +399,18 @@ extern "C" int ctg_batch_solve(ctg_batch *b, const float *const *b_dev, const fl
     cudaStream_t st = b->st;
     B_CK(cudaEventRecord(b->ev_in, user));
     B_CK(cudaStreamWaitEvent(st, b->ev_in, 0));
-    // ---- per instance: r0, beta and (BA) ||b - A x0|| ------------------
     for (int i = 0; i < n; ++i) {
-        InstPlan &p = b->inst[i];
-        BatchInst &d = p.d;
-        const float *x0 = x0_dev ? x0_dev[i] : nullptr;
-        const RedScratch rs = scratch_of(d);
-        const PadLayout pl = ctg_pad_layout(p.g.N, p.g.det_spacing);
-        B_CK(cudaMemsetAsync(d.counter, 0, 4 * sizeof(unsigned), st));
-        B_CK(cudaMemsetAsync(d.gg, 0, sizeof(double) * (p.o.maxit + 1), st));
-        B_CK(cudaMemsetAsync(d.H, 0, sizeof(double) * (size_t)(p.o.maxit + 1) * p.o.maxit, st));
-        B_CK(cudaMemsetAsync(d.hist, 0, sizeof(double) * (p.o.maxit + 1), st));
-        B_CK(cudaMemsetAsync(d.pad, 0, sizeof(float) * pl.floats, st));
-        if (x0) {
-            B_CK(ctg_launch_pad(x0, CTG_BASIS_FP32, d.pad, p.g.N, pl, st));
-            B_CK(ctg_launch_forward(d.pad, p.g.N, pl, p.g.n_angles, p.g.n_det, d.fwd, d.vm, st));
-        }
-        if (p.variant == CTG_AB) {
-            B_CK(ctg_sub_norm2(b_dev[i], x0 ? d.vm : nullptr, d.vm, d.m, d.scal + 2, rs, st));
-        } else {
-            B_CK(ctg_sub_norm2(b_dev[i], x0 ? d.vm : nullptr, d.r0m, d.m, d.scal + 4, rs, st));
-            B_CK(ctg_launch_back(d.r0m, CTG_BASIS_FP32, p.g.N, p.g.n_angles, p.g.n_det, d.back,
-                                 d.back_window, nullptr, d.vn, st));
-            B_CK(ctg_sub_norm2(d.vn, nullptr, nullptr, d.n, d.scal + 2, rs, st));
-        }
-        B_CK(cudaMemcpyAsync(b->h_stage + 8 * i, d.scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+        const int rc = enqueue_start(b->inst[i], b_dev[i], x0_dev ? x0_dev[i] : nullptr,
+                                     b->h_stage + 8 * i, st);
+        if (rc) return rc;
     }
     B_CK(cudaStreamSynchronize(st));
     int active = 0;
     for (int i = 0; i < n; ++i) {
-        InstPlan &p = b->inst[i];
-        BatchInst &d = p.d;
-        const double beta = std::sqrt(b->h_stage[8 * i + 2]);
-        const double res0 = p.variant == CTG_AB ? beta : std::sqrt(b->h_stage[8 * i + 4]);
-        d.k = 1;
-        d.iters = 0;
-        d.breakdown = 0;
-        d.rho = beta;
-        d.resnorm = res0;
-        d.stop_reason = CTG_STOP_MAXIT;
-        infos[i].iters = 0;
-        infos[i].rho = beta;
-        infos[i].resnorm = res0;
-        if (infos[i].history) infos[i].history[0] = d.target > 0.0 ? res0 : beta;
-        const bool dp0 = d.target > 0.0 && res0 <= d.target;
-        if (dp0 || beta == 0.0) {                   // k = 0: x = x0
-            d.active = 0;
-            d.stop_reason = dp0 ? CTG_STOP_DP : CTG_STOP_BREAKDOWN;
-            continue;
-        }
-        d.active = 1;
-        ++active;
-        // w_1 = r0 / beta and the rotated right-hand side beta e1
-        B_CK(ctg_scale(p.variant == CTG_AB ? d.vm : d.vn, d.scal + 2, d.W, CTG_BASIS_FP32, d.L, st));
-        b->h_stage[8 * i + 6] = beta;
-        B_CK(cudaMemcpyAsync(d.gg, &b->h_stage[8 * i + 6], sizeof(double), cudaMemcpyHostToDevice, st));
+        int a = 0;
+        const int rc = activate(b->inst[i], b->h_stage + 8 * i, &infos[i], st, &a);
+        if (rc) return rc;
+        active += a;
     }
     std::vector<BatchInst> hi(n);
     for (int i = 0; i < n; ++i) hi[i] = b->inst[i].d;
@@ -344,39 +432,298 @@ extern "C" int ctg_batch_solve(ctg_batch *b, const float *const *b_dev, const fl
     B_CK(cudaMemcpyAsync(hi.data(), b->d_insts, sizeof(BatchInst) * n, cudaMemcpyDeviceToHost, st));
     B_CK(cudaStreamSynchronize(st));
     for (int i = 0; i < n; ++i) {
-        InstPlan &p = b->inst[i];
-        const BatchInst &d = hi[i];
-        const float *x0 = x0_dev ? x0_dev[i] : nullptr;
-        const RedScratch rs = scratch_of(d);
-        const PadLayout pl = ctg_pad_layout(p.g.N, p.g.det_spacing);
-        const int k = d.active ? d.k : d.iters;   // d.active cannot remain set after the rounds
-        infos[i].iters = k;
-        infos[i].stop_reason = d.stop_reason;
-        infos[i].rho = k > 0 ? d.rho : infos[i].rho;
-        if (k == 0) {
-            if (x0) B_CK(cudaMemcpyAsync(x_dev[i], x0, sizeof(float) * d.n, cudaMemcpyDeviceToDevice, st));
-            else B_CK(cudaMemsetAsync(x_dev[i], 0, sizeof(float) * d.n, st));
-            continue;
-        }
-        if (p.variant == CTG_AB) {
-            B_CK(ctg_gemv(d.W, CTG_BASIS_FP32, d.ldw, d.m, k, d.y, nullptr, d.vm, st));
-            B_CK(ctg_launch_back(d.vm, CTG_BASIS_FP32, p.g.N, p.g.n_angles, p.g.n_det, d.back,
-                                 d.back_window, x0, x_dev[i], st));
-        } else {
-            B_CK(ctg_gemv(d.W, CTG_BASIS_FP32, d.ldw, d.n, k, d.y, x0, x_dev[i], st));
-        }
-        B_CK(ctg_launch_pad(x_dev[i], CTG_BASIS_FP32, d.pad, p.g.N, pl, st));
-        B_CK(ctg_launch_forward(d.pad, p.g.N, pl, p.g.n_angles, p.g.n_det, d.fwd, d.vm, st));
-        B_CK(ctg_sub_norm2(b_dev[i], d.vm, nullptr, d.m, d.scal + 5, rs, st));
-        B_CK(cudaMemcpyAsync(b->h_stage + 8 * i + 5, d.scal + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
-        if (infos[i].history)
-            B_CK(cudaMemcpyAsync(infos[i].history + 1, d.hist + 1, sizeof(double) * k,
-                                 cudaMemcpyDeviceToHost, st));
+        const int rc = enqueue_finish(b->inst[i], hi[i], b_dev[i], x0_dev ? x0_dev[i] : nullptr,
+                                      x_dev[i], &infos[i], b->h_stage + 8 * i, st);
+        if (rc) return rc;
     }
     B_CK(cudaStreamSynchronize(st));
     for (int i = 0; i < n; ++i)
         if (infos[i].iters > 0) infos[i].resnorm = std::sqrt(b->h_stage[8 * i + 5]);
     B_CK(cudaEventRecord(b->ev_out, st));
     B_CK(cudaStreamWaitEvent(user, b->ev_out, 0));
+    return CTG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving engine: continuous batching.  Solves are admitted one at a time
+// into free slots while others are running (admission by the device memory
+// their Krylov basis needs against a budget), each keeps its basis,
+// Hessenberg matrix and iterate resident in its own workspace, and every
+// step advances all running solves by a few rounds of the same batched
+// kernels.  The round graph is re-captured only when new solves have joined
+// since the last step; finished solves are formed, reported and their
+// memory released at the end of the step that finished them.
+struct ctg_engine {
+    struct Slot {
+        int state = 0;          // 0 free, 1 running, 2 finished, not yet reported
+        InstPlan plan;
+        char *ws = nullptr;
+        size_t bytes = 0;
+        const float *b = nullptr;
+        const float *x0 = nullptr;
+        float *x = nullptr;
+        ctg_info info{};
+        long long tag = 0;
+        bool formed = false;    // x and the final residual already computed
+    };
+    ctg_ctx *ctx = nullptr;
+    int max_slots = 0;
+    size_t budget = 0, in_use = 0;
+    std::vector<Slot> slots;
+    BatchInst *d_insts = nullptr;
+    std::vector<BatchInst> h_insts;
+    BatchInst *h_pinned = nullptr;   // pinned mirror used for transfers
+    int2 *d_maps = nullptr;
+    size_t maps_cap = 0;
+    RoundSpec spec{};
+    bool dirty = true;
+    int running = 0;
+    int *d_active = nullptr, *h_active = nullptr;
+    double *h_stage = nullptr;       // 8 per slot
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev_in = nullptr;
+    cudaGraphExec_t round = nullptr;
+    cudaMemPool_t pool = nullptr;    // per-solve workspaces, kept mapped up to the budget
+};
+
+namespace {
+
+void release_engine(ctg_engine *e) {
+    if (!e) return;
+    if (e->st) cudaStreamSynchronize(e->st);
+    for (auto &s : e->slots)
+        if (s.ws) cudaFreeAsync(s.ws, e->st);
+    if (e->st) cudaStreamSynchronize(e->st);
+    if (e->pool) cudaMemPoolDestroy(e->pool);
+    if (e->round) cudaGraphExecDestroy(e->round);
+    if (e->ev_in) cudaEventDestroy(e->ev_in);
+    if (e->st) cudaStreamDestroy(e->st);
+    cudaFree(e->d_insts);
+    cudaFree(e->d_maps);
+    cudaFree(e->d_active);
+    if (e->h_active) cudaFreeHost(e->h_active);
+    if (e->h_stage) cudaFreeHost(e->h_stage);
+    if (e->h_pinned) cudaFreeHost(e->h_pinned);
+    delete e;
+}
+
+bool plan_valid(const ctg_geom *g, int variant, const ctg_opts *o) {
+    if (!ctg_geom_valid(g) || !ctg_opts_valid(o) || o->basis_dtype != CTG_BASIS_FP32 ||
+        o->maxit > 1024 || (variant != CTG_AB && variant != CTG_BA))
+        return false;
+    std::vector<FwdAngle> fw;
+    std::vector<BackAngle> bk;
+    ctg_build_tables(g, fw, bk);
+    return ctg_back_window(bk.data(), g->n_angles) <= ctg_back_window_max();
+}
+
+int recapture(ctg_engine *e) {
+    std::vector<int> ids;
+    for (int i = 0; i < e->max_slots; ++i)
+        if (e->slots[i].state == 1) ids.push_back(i);
+    std::vector<InstPlan> plans(e->max_slots);
+    for (int i = 0; i < e->max_slots; ++i) plans[i] = e->slots[i].plan;
+    std::vector<int2> maps;
+    RoundSpec r{};
+    build_maps(plans, ids, maps, r);
+    if (maps.size() > e->maps_cap) {
+        cudaFree(e->d_maps);
+        e->d_maps = nullptr;
+        e->maps_cap = 0;
+        B_CK(cudaMalloc(&e->d_maps, sizeof(int2) * maps.size()));
+        e->maps_cap = maps.size();
+    }
+    if (!maps.empty())
+        B_CK(cudaMemcpyAsync(e->d_maps, maps.data(), sizeof(int2) * maps.size(), cudaMemcpyHostToDevice, e->st));
+    r.insts = e->d_insts;
+    r.n_inst = e->max_slots;
+    r.maps = e->d_maps;
+    r.max_window = 1;
+    r.max_maxit = 1;
+    for (int i : ids) {
+        r.max_window = std::max(r.max_window, e->slots[i].plan.d.back_window);
+        r.max_maxit = std::max(r.max_maxit, e->slots[i].plan.o.maxit);
+    }
+    r.d_active = e->d_active;
+    B_CK(cudaStreamSynchronize(e->st));        // maps uploaded before they are captured
+    if (e->round) {
+        cudaGraphExecDestroy(e->round);
+        e->round = nullptr;
+    }
+    const int rc = capture_round(r, e->st, &e->round);
+    if (rc) return rc;
+    e->spec = r;
+    e->dirty = false;
+    return CTG_OK;
+}
+
+}  // namespace
+
+extern "C" int ctg_engine_create(ctg_ctx *ctx, int32_t max_slots, size_t hbm_budget_bytes,
+                                 ctg_engine **out) {
+    if (!ctx || max_slots < 1 || max_slots > 4096 || !out) return CTG_ERR_INVALID_ARG;
+    *out = nullptr;
+    ctg_engine *e = new (std::nothrow) ctg_engine();
+    if (!e) return CTG_ERR_OOM;
+    e->ctx = ctx;
+    e->max_slots = max_slots;
+    e->budget = hbm_budget_bytes;
+    e->slots.resize(max_slots);
+    e->h_insts.assign(max_slots, BatchInst{});
+    int rc = ck(cudaMalloc(&e->d_insts, sizeof(BatchInst) * max_slots));
+    if (rc == CTG_OK) rc = ck(cudaMemset(e->d_insts, 0, sizeof(BatchInst) * max_slots));   // all inactive
+    if (rc == CTG_OK) rc = ck(cudaMalloc(&e->d_active, sizeof(int)));
+    if (rc == CTG_OK) rc = ck(cudaMallocHost(&e->h_active, sizeof(int)));
+    if (rc == CTG_OK) rc = ck(cudaMallocHost(&e->h_stage, sizeof(double) * 8 * max_slots));
+    if (rc == CTG_OK) rc = ck(cudaMallocHost(&e->h_pinned, sizeof(BatchInst) * max_slots));
+    if (rc == CTG_OK) rc = ck(cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking));
+    if (rc == CTG_OK) rc = ck(cudaEventCreateWithFlags(&e->ev_in, cudaEventDisableTiming));
+    int dev = 0;
+    if (rc == CTG_OK) rc = ck(cudaGetDevice(&dev));
+    if (rc == CTG_OK) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        rc = ck(cudaMemPoolCreate(&e->pool, &props));
+    }
+    if (rc == CTG_OK) {
+        // freed workspaces stay mapped for the next admissions
+        unsigned long long keep = hbm_budget_bytes;
+        rc = ck(cudaMemPoolSetAttribute(e->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    if (rc != CTG_OK) {
+        release_engine(e);
+        return rc;
+    }
+    *out = e;
+    return CTG_OK;
+}
+
+extern "C" void ctg_engine_destroy(ctg_engine *e) { release_engine(e); }
+
+extern "C" size_t ctg_engine_request_bytes(const ctg_geom *g, int32_t variant, const ctg_opts *o) {
+    if (!plan_valid(g, variant, o)) return 0;
+    InstPlan p;
+    p.g = *g;
+    p.o = *o;
+    p.variant = variant;
+    return al256(plan_instance(p, nullptr));
+}
+
+extern "C" int32_t ctg_engine_in_flight(const ctg_engine *e) {
+    if (!e) return 0;
+    int c = 0;
+    for (const auto &s : e->slots) c += s.state != 0;
+    return c;
+}
+
+extern "C" int ctg_engine_submit(ctg_engine *e, const ctg_geom *g, int32_t variant,
+                                 const ctg_opts *o, const float *b_dev, const float *x0_dev,
+                                 float *x_dev, double *history, int64_t tag, void *stream) {
+    if (!e || !b_dev || !x_dev || !plan_valid(g, variant, o)) return CTG_ERR_INVALID_ARG;
+    int slot = -1;
+    for (int i = 0; i < e->max_slots && slot < 0; ++i)
+        if (e->slots[i].state == 0) slot = i;
+    const size_t bytes = ctg_engine_request_bytes(g, variant, o);
+    if (bytes > e->budget) return CTG_ERR_OOM;      // would never fit
+    if (slot < 0 || e->in_use + bytes > e->budget) return CTG_ERR_BUSY;
+    ctg_engine::Slot &s = e->slots[slot];
+    s.plan = InstPlan{};
+    s.plan.g = *g;
+    s.plan.o = *o;
+    s.plan.variant = variant;
+    B_CK(cudaEventRecord(e->ev_in, static_cast<cudaStream_t>(stream)));
+    B_CK(cudaStreamWaitEvent(e->st, e->ev_in, 0));
+    void *ws = nullptr;
+    B_CK(cudaMallocFromPoolAsync(&ws, bytes, e->pool, e->st));
+    s.ws = static_cast<char *>(ws);
+    s.bytes = bytes;
+    plan_instance(s.plan, s.ws);
+    std::vector<FwdAngle> fw;
+    std::vector<BackAngle> bk;
+    ctg_build_tables(g, fw, bk);
+    s.plan.d.back_window = ctg_back_window(bk.data(), g->n_angles);
+    B_CK(cudaMemcpyAsync((void *)s.plan.d.fwd, fw.data(), sizeof(FwdAngle) * fw.size(), cudaMemcpyHostToDevice, e->st));
+    B_CK(cudaMemcpyAsync((void *)s.plan.d.back, bk.data(), sizeof(BackAngle) * bk.size(), cudaMemcpyHostToDevice, e->st));
+    s.b = b_dev;
+    s.x0 = x0_dev;
+    s.x = x_dev;
+    s.tag = tag;
+    s.formed = false;
+    s.info = ctg_info{};
+    s.info.history = history;
+    double *stage = e->h_stage + 8 * slot;
+    int rc = enqueue_start(s.plan, b_dev, x0_dev, stage, e->st);
+    if (rc == CTG_OK) rc = ck(cudaStreamSynchronize(e->st));   // tables copied, start read back
+    int act = 0;
+    if (rc == CTG_OK) rc = activate(s.plan, stage, &s.info, e->st, &act);
+    if (rc != CTG_OK) {
+        cudaFreeAsync(s.ws, e->st);
+        cudaStreamSynchronize(e->st);
+        s = ctg_engine::Slot{};
+        return rc;
+    }
+    e->in_use += bytes;
+    e->h_pinned[slot] = s.plan.d;
+    B_CK(cudaMemcpyAsync(e->d_insts + slot, e->h_pinned + slot, sizeof(BatchInst), cudaMemcpyHostToDevice, e->st));
+    B_CK(cudaStreamSynchronize(e->st));
+    if (act) {
+        s.state = 1;
+        ++e->running;
+        e->dirty = true;
+    } else {
+        s.state = 2;    // finished at k = 0; x = x0 is formed by the next step
+    }
+    return CTG_OK;
+}
+
+extern "C" int ctg_engine_step(ctg_engine *e, int32_t rounds, int32_t max_done, int64_t *done_tags,
+                               ctg_info *done_infos, int32_t *n_done) {
+    if (!e || rounds < 0 || max_done < 0 || !n_done || (max_done > 0 && (!done_tags || !done_infos)))
+        return CTG_ERR_INVALID_ARG;
+    *n_done = 0;
+    cudaStream_t st = e->st;
+    if (e->running > 0 && rounds > 0) {
+        if (e->dirty) {
+            const int rc = recapture(e);
+            if (rc) return rc;
+        }
+        *e->h_active = e->running;
+        B_CK(cudaMemcpyAsync(e->d_active, e->h_active, sizeof(int), cudaMemcpyHostToDevice, st));
+        for (int j = 0; j < rounds; ++j) B_CK(cudaGraphLaunch(e->round, st));
+        B_CK(ctg_batch_solve_y(e->d_insts, e->max_slots, st));   // y of solves that just finished
+        B_CK(cudaMemcpyAsync(e->h_pinned, e->d_insts, sizeof(BatchInst) * e->max_slots,
+                             cudaMemcpyDeviceToHost, st));
+        B_CK(cudaMemcpyAsync(e->h_active, e->d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        B_CK(cudaStreamSynchronize(st));
+        e->running = *e->h_active;
+        for (int i = 0; i < e->max_slots; ++i)
+            if (e->slots[i].state == 1 && !e->h_pinned[i].active) e->slots[i].state = 2;
+    }
+    // form and report finished solves
+    std::vector<int> fin;
+    for (int i = 0; i < e->max_slots && (int)fin.size() < max_done; ++i)
+        if (e->slots[i].state == 2) fin.push_back(i);
+    for (int i : fin) {
+        ctg_engine::Slot &s = e->slots[i];
+        const BatchInst d = e->h_pinned[i];    // state after the last rounds (or at admission)
+        const int rc = enqueue_finish(s.plan, d, s.b, s.x0, s.x, &s.info, e->h_stage + 8 * i, st);
+        if (rc) return rc;
+    }
+    if (!fin.empty()) B_CK(cudaStreamSynchronize(st));
+    for (int i : fin) {
+        ctg_engine::Slot &s = e->slots[i];
+        if (s.info.iters > 0) s.info.resnorm = std::sqrt(e->h_stage[8 * i + 5]);
+        done_tags[*n_done] = s.tag;
+        done_infos[*n_done] = s.info;
+        ++*n_done;
+        B_CK(cudaFreeAsync(s.ws, st));
+        e->in_use -= s.bytes;
+        s = ctg_engine::Slot{};
+        e->h_pinned[i] = BatchInst{};             // inactive
+        B_CK(cudaMemcpyAsync(e->d_insts + i, e->h_pinned + i, sizeof(BatchInst), cudaMemcpyHostToDevice, st));
+    }
+    if (!fin.empty()) B_CK(cudaStreamSynchronize(st));
     return CTG_OK;
 }
