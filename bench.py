@@ -464,11 +464,16 @@ def run_serve(args):
     # capacity of the plain server: all requests back to back
     d, it_fifo, outs, span = serve_fifo(P, torch, reqs, [0.0] * len(reqs))
     capacity = len(reqs) / span
+    d_e, it_eng, outs_e, span_e = serve_engine(P, torch, reqs, [0.0] * len(reqs), args.serve_slots,
+                                               args.serve_budget_gb << 30, 4)
     base = {"workload": f"{len(reqs)} requests, N in {{128,256,512,1024}}, angles in {{60,180,360,720}}, "
                         "25% limited-angle [0,120), noise 0.5-5%, AB/BA, maxit 50-200, DP tau=1.02, "
                         "Poisson arrivals",
             "one_at_a_time_capacity_req_per_s": capacity,
             "one_at_a_time_iterations_per_s": it_fifo / span,
+            "engine_capacity_req_per_s": len(reqs) / span_e,
+            "engine_iterations_per_s": it_eng / span_e,
+            "mean_rel_error_vs_truth": {"engine": err(outs_e), "one_at_a_time": err(outs)},
             "slots": args.serve_slots, "budget_GB": args.serve_budget_gb, "rounds_per_step": 4}
     print(json.dumps(base), flush=True)
     rng = np.random.default_rng(5999)

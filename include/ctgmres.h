@@ -56,21 +56,33 @@ enum {
                                   retry after a completion                   */
 };
 
-enum { CTG_AB = 0, CTG_BA = 1 };                       /* solver variant    */
+enum { CTG_AB = 0, CTG_BA = 1, CTG_LSQR = 2, CTG_LSMR = 3 };                       /* solver variant    */
 enum { CTG_STOP_MAXIT = 0, CTG_STOP_DP = 1, CTG_STOP_BREAKDOWN = 2 };
 enum { CTG_BASIS_FP32 = 0, CTG_BASIS_BF16 = 1, CTG_BASIS_FP16 = 2 };  /* basis storage */
+/* Back projector B of a geometry.
+ * CTG_BACK_PIXEL: the unmatched pixel-driven back projector (linear
+ *   interpolation on the detector at each pixel centre), the paper's B.
+ * CTG_BACK_MATCHED: B = A^T, the exact transpose of the Joseph forward
+ *   projector (the matched case of Sec. 5).
+ * CTG_BACK_THRESHOLD: B_tau of Sec. 6.5, eq. (Btau): (B_tau)_ij = A_ji where
+ *   A_ji >= back_tau * max(A), else 0; max(A) is taken over all entries of A
+ *   (computed once per geometry on the device, in FP32). */
+enum { CTG_BACK_PIXEL = 0, CTG_BACK_MATCHED = 1, CTG_BACK_THRESHOLD = 2 };
 
 /* 2D parallel-beam geometry (paper Sec. 6.1, Table 1).  Limits: 1 <= N <=
  * 16384, 1 <= n_angles, 1 <= n_det <= 65536, start and range integral
- * degrees with 0 < range <= 360, det_spacing > 0. */
+ * degrees with 0 < range <= 360, det_spacing > 0, n_det * det_spacing <=
+ * 2^20, 1.5 N / det_spacing + n_det < 2^22; back_tau in [0, 1] for
+ * CTG_BACK_THRESHOLD and 0 otherwise. */
 typedef struct {
     int32_t N;                /* image side; n = N * N pixels               */
     int32_t n_angles;         /* N_ang                                      */
     int32_t n_det;            /* N_det                                      */
-    int32_t reserved;         /* must be 0                                  */
+    int32_t back_model;       /* CTG_BACK_PIXEL, _MATCHED or _THRESHOLD     */
     double angle_start_deg;   /* theta_0, integer degrees                   */
     double angle_range_deg;   /* angles span [start, start + range)        */
     double det_spacing;       /* detector pitch in pixel units (1 = pixel)  */
+    double back_tau;          /* threshold tau of B_tau                      */
 } ctg_geom;
 
 /* Solver options. */
@@ -126,17 +138,22 @@ void ctg_destroy(ctg_ctx *ctx);
 int ctg_project(ctg_ctx *ctx, const ctg_geom *g, const float *x_dev,
                 float *b_dev, void *stream);
 
-/* x = B b: pixel-driven unmatched back projection (B in eq. (1.2)).
- * b: m floats (device, read-only); x: n floats (device, overwritten). */
+/* x = B b with the geometry's back projector: by default the pixel-driven
+ * unmatched back projection (B in eq. (1.2)); A^T or B_tau (Sec. 6.5) when
+ * g->back_model selects them.  b: m floats (device, read-only); x: n floats
+ * (device, overwritten). */
 int ctg_backproject(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev,
                     float *x_dev, void *stream);
 
-/* Bytes of device workspace a solve of `variant` with these options needs;
- * 0 if the arguments are invalid.  Dominated by the basis, (maxit + 1)
- * vectors of length L, which is the paper's storage law k * L (Table 3). */
+/* Bytes of device workspace a solve of `variant` (CTG_AB, CTG_BA, CTG_LSQR or
+ * CTG_LSMR) with these options needs; 0 if the arguments are invalid.  For
+ * the GMRES variants it is dominated by the basis, (maxit + 1) vectors of
+ * length L, which is the paper's storage law k * L (Table 3); LSQR and LSMR
+ * need O(n + m) whatever maxit. */
 size_t ctg_workspace_bytes(const ctg_geom *g, int variant, const ctg_opts *o);
 
-/* Fill *out with the workspace layout for these arguments. */
+/* Fill *out with the workspace layout for these arguments (for CTG_LSQR and
+ * CTG_LSMR only total_bytes is meaningful: they keep no basis). */
 int ctg_workspace_layout(const ctg_geom *g, int variant, const ctg_opts *o,
                          ctg_layout *out);
 
@@ -162,6 +179,28 @@ int ctg_ba_gmres(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev,
                  const float *x0_dev, float *x_dev, const ctg_opts *o,
                  void *workspace_dev, size_t workspace_bytes, ctg_info *info,
                  void *stream);
+
+/* LSQR (Paige & Saunders) and LSMR (Fong & Saunders), no damping: the
+ * matched-case comparators of Sec. 5, where AB-GMRES with B = A^T equals
+ * LSQR and BA-GMRES with B = A^T equals LSMR in exact arithmetic.  The
+ * geometry's back projector plays the role of A^T (CTG_BACK_MATCHED for the
+ * methods proper; with an unmatched B they solve the unmatched normal
+ * equations, which Sec. 5 notes is not well founded).  Same arguments and
+ * ownership as ctg_ab_gmres; opts->basis_dtype must be CTG_BASIS_FP32 (there
+ * is no basis: the workspace, ctg_workspace_bytes(g, CTG_LSQR or CTG_LSMR,
+ * opts), is O(n + m) whatever maxit).  Short recurrences, no
+ * reorthogonalisation.  Stopping: the discrepancy principle of Sec. 6.4 on
+ * LSQR's residual estimate |phibar_{k+1}| = ||b - A x_k|| (exact in exact
+ * arithmetic), and for LSMR on ||r_k|| tracked in sinogram space through the
+ * recurrences of x_k; else maxit, or CTG_STOP_BREAKDOWN when alpha or beta
+ * vanishes.  info->rho = the last residual estimate, info->resnorm =
+ * ||b - A x|| recomputed, history[k] = the estimates. */
+int ctg_lsqr(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, const float *x0_dev, float *x_dev,
+             const ctg_opts *opts, void *workspace, size_t workspace_bytes, ctg_info *info,
+             void *stream);
+int ctg_lsmr(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, const float *x0_dev, float *x_dev,
+             const ctg_opts *opts, void *workspace, size_t workspace_bytes, ctg_info *info,
+             void *stream);
 
 /* Batched AB-/BA-GMRES: n independent solves of possibly different
  * geometries, variants (CTG_AB / CTG_BA) and options advance together, one

@@ -138,3 +138,13 @@ def matrix_B(g: Geometry) -> sp.csr_matrix:
     """Explicit sparse B (n x m), for small geometries."""
     return _triplets(_load().orc_backproject_triplets, g, 2 * g.n * g.n_angles,
                      (g.n, g.m))
+
+
+def matrix_B_tau(g: Geometry, tau: float) -> sp.csr_matrix:
+    """The thresholded back projector of Sec. 6.5, eq. (Btau):
+    (B_tau)_ij = A_ji if A_ji >= tau * max_ij A_ij, else 0 (all entries of A
+    are >= 0).  tau = 0 gives the matched back projector A^T."""
+    A = matrix_A(g).tocoo()
+    thr = tau * A.data.max()
+    keep = A.data >= thr
+    return sp.csr_matrix((A.data[keep], (A.col[keep], A.row[keep])), shape=(g.n, g.m))

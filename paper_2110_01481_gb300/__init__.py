@@ -6,7 +6,7 @@ of the Krylov solvers runs in the library's kernels.  See ``api`` for the
 calls: ``project``, ``backproject``, ``ab_gmres``, ``ba_gmres``, ``cgs2``.
 """
 __all__ = ["Geometry", "Context", "SolveResult", "Batch", "Engine", "project", "backproject",
-           "ab_gmres", "ba_gmres", "cgs2", "workspace_bytes", "workspace_layout"]
+           "ab_gmres", "ba_gmres", "lsqr", "lsmr", "cgs2", "workspace_bytes", "workspace_layout"]
 
 
 def __getattr__(name):

@@ -19,18 +19,21 @@ CTG_ERR_CUDA = -3
 CTG_ERR_TIMEOUT = -4
 CTG_ERR_WORKSPACE = -5
 CTG_ERR_BUSY = -6
-CTG_AB, CTG_BA = 0, 1
+CTG_AB, CTG_BA, CTG_LSQR, CTG_LSMR = 0, 1, 2, 3
+VARIANTS = {"ab": CTG_AB, "ba": CTG_BA, "lsqr": CTG_LSQR, "lsmr": CTG_LSMR}
 CTG_STOP_MAXIT, CTG_STOP_DP, CTG_STOP_BREAKDOWN = 0, 1, 2
 CTG_BASIS_FP32, CTG_BASIS_BF16, CTG_BASIS_FP16 = 0, 1, 2
+BACK = {"pixel": 0, "matched": 1, "threshold": 2}
 BASIS = {"fp32": CTG_BASIS_FP32, "bf16": CTG_BASIS_BF16, "fp16": CTG_BASIS_FP16}
 
 
 class CtgGeom(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("n_angles", ctypes.c_int32),
-                ("n_det", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_det", ctypes.c_int32), ("back_model", ctypes.c_int32),
                 ("angle_start_deg", ctypes.c_double),
                 ("angle_range_deg", ctypes.c_double),
-                ("det_spacing", ctypes.c_double)]
+                ("det_spacing", ctypes.c_double),
+                ("back_tau", ctypes.c_double)]
 
 
 class CtgOpts(ctypes.Structure):
@@ -59,7 +62,7 @@ class CtgLayout(ctypes.Structure):
 
 EXPORTS = ("ctg_create", "ctg_destroy", "ctg_project", "ctg_backproject",
            "ctg_workspace_bytes", "ctg_workspace_layout", "ctg_ab_gmres",
-           "ctg_ba_gmres", "ctg_cgs2_scratch_bytes", "ctg_cgs2", "ctg_cgs2_noalloc",
+           "ctg_ba_gmres", "ctg_lsqr", "ctg_lsmr", "ctg_cgs2_scratch_bytes", "ctg_cgs2", "ctg_cgs2_noalloc",
            "ctg_set_timing", "ctg_get_timing", "ctg_status_string",
            "ctg_batch_create", "ctg_batch_workspace_bytes", "ctg_batch_solve", "ctg_batch_destroy",
            "ctg_engine_create", "ctg_engine_request_bytes", "ctg_engine_submit",
@@ -80,7 +83,7 @@ def _declare(lib):
     lib.ctg_workspace_bytes.restype = sz
     lib.ctg_workspace_layout.argtypes = [G, ctypes.c_int, O, ctypes.POINTER(CtgLayout)]
     lib.ctg_workspace_layout.restype = ctypes.c_int
-    for f in (lib.ctg_ab_gmres, lib.ctg_ba_gmres):
+    for f in (lib.ctg_ab_gmres, lib.ctg_ba_gmres, lib.ctg_lsqr, lib.ctg_lsmr):
         f.argtypes = [vp, G, vp, vp, vp, O, vp, sz, ctypes.POINTER(CtgInfo), vp]
         f.restype = ctypes.c_int
     lib.ctg_cgs2_scratch_bytes.argtypes = [i64, i32]

@@ -17,13 +17,17 @@ from . import _native as nat
 
 @dataclass(frozen=True)
 class Geometry:
-    """2D parallel-beam geometry (paper Sec. 6.1, Table 1)."""
+    """2D parallel-beam geometry (paper Sec. 6.1, Table 1) and its back
+    projector: "pixel" (the unmatched pixel-driven B), "matched" (A^T) or
+    "threshold" (B_tau of Sec. 6.5 with tau = back_tau)."""
     N: int
     n_angles: int
     n_det: int
     angle_start_deg: float = 0.0
     angle_range_deg: float = 180.0
     det_spacing: float = 1.0
+    back_model: str = "pixel"
+    back_tau: float = 0.0
 
     @property
     def n(self) -> int:
@@ -34,9 +38,11 @@ class Geometry:
         return self.n_angles * self.n_det
 
     def c(self) -> nat.CtgGeom:
-        return nat.CtgGeom(self.N, self.n_angles, self.n_det, 0,
+        if self.back_model not in nat.BACK:
+            raise ValueError(f"back_model must be one of {sorted(nat.BACK)}")
+        return nat.CtgGeom(self.N, self.n_angles, self.n_det, nat.BACK[self.back_model],
                            float(self.angle_start_deg), float(self.angle_range_deg),
-                           float(self.det_spacing))
+                           float(self.det_spacing), float(self.back_tau))
 
 
 class Context:
@@ -132,8 +138,9 @@ def _opts(maxit: int, tau: float, noise_norm: Optional[float], basis: str = "fp3
 
 
 def workspace_bytes(g: Geometry, variant: str, maxit: int, basis: str = "fp32") -> int:
-    """Device bytes one solve needs (0 if the arguments are invalid)."""
-    v = nat.CTG_AB if variant == "ab" else nat.CTG_BA
+    """Device bytes one solve needs (0 if the arguments are invalid);
+    variant: "ab", "ba", "lsqr" or "lsmr"."""
+    v = nat.VARIANTS[variant]
     return int(nat.lib().ctg_workspace_bytes(ctypes.byref(g.c()), v,
                                              ctypes.byref(_opts(maxit, 1.0, None, basis))))
 
@@ -189,8 +196,9 @@ def _solve(fn, variant: str, g: Geometry, b: torch.Tensor, maxit: int,
     px = _dev_ptr(out, g.n, "out")
     o = _opts(maxit, tau, noise_norm, basis)
     need = workspace_bytes(g, variant, maxit, basis)
+    name = f"ctg_{variant}" if variant in ("lsqr", "lsmr") else f"ctg_{variant}_gmres"
     if need == 0:
-        raise nat.CtgError(nat.CTG_ERR_INVALID_ARG, f"ctg_{variant}_gmres")
+        raise nat.CtgError(nat.CTG_ERR_INVALID_ARG, name)
     if workspace is None and keep_workspace:
         workspace = torch.empty(need, device=dev, dtype=torch.uint8)
     pws, nws = (None, 0)
@@ -201,7 +209,7 @@ def _solve(fn, variant: str, g: Geometry, b: torch.Tensor, maxit: int,
     ctx = Context.get(dev)
     with torch.cuda.device(dev):
         nat.check(fn(ctx.handle, ctypes.byref(g.c()), pb, px0, px, ctypes.byref(o), pws, nws,
-                     ctypes.byref(info), _stream(dev)), f"ctg_{variant}_gmres")
+                     ctypes.byref(info), _stream(dev)), name)
     return SolveResult(out, info.iters, info.stop_reason, info.resnorm, info.rho,
                        list(hist[: info.iters + 1]), workspace, basis)
 
@@ -222,6 +230,26 @@ def ba_gmres(g: Geometry, b: torch.Tensor, maxit: int, x0=None, tau: float = 1.0
     """BA-GMRES (paper Sec. 2); same conventions as ``ab_gmres``."""
     return _solve(nat.lib().ctg_ba_gmres, "ba", g, b, maxit, x0, tau, noise_norm, out,
                   workspace, keep_workspace, basis)
+
+
+def lsqr(g: Geometry, b: torch.Tensor, maxit: int, x0=None, tau: float = 1.0,
+         noise_norm: Optional[float] = None, out=None, workspace=None,
+         keep_workspace: bool = False) -> SolveResult:
+    """LSQR (Sec. 5's matched-case comparator) with the geometry's back
+    projector as A^T (use back_model="matched" for LSQR proper); the
+    discrepancy-principle stop on its residual estimate when noise_norm is
+    given.  history[k] = the estimate of ||b - A x_k||."""
+    return _solve(nat.lib().ctg_lsqr, "lsqr", g, b, maxit, x0, tau, noise_norm, out,
+                  workspace, keep_workspace)
+
+
+def lsmr(g: Geometry, b: torch.Tensor, maxit: int, x0=None, tau: float = 1.0,
+         noise_norm: Optional[float] = None, out=None, workspace=None,
+         keep_workspace: bool = False) -> SolveResult:
+    """LSMR (Sec. 5's matched-case comparator); same conventions as ``lsqr``,
+    history[k] = ||b - A x_k|| tracked through the recurrences."""
+    return _solve(nat.lib().ctg_lsmr, "lsmr", g, b, maxit, x0, tau, noise_norm, out,
+                  workspace, keep_workspace)
 
 
 def cgs2(W: torch.Tensor, k: int, q: torch.Tensor, w_out: Optional[torch.Tensor] = None,

@@ -5,6 +5,7 @@
 // of Sec. 6.4.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -25,11 +26,16 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
 bool geom_valid(const ctg_geom *g) {
-    if (!g || g->reserved != 0) return false;
+    if (!g || g->back_model < CTG_BACK_PIXEL || g->back_model > CTG_BACK_THRESHOLD) return false;
+    if (!std::isfinite(g->back_tau) || g->back_tau < 0.0 || g->back_tau > 1.0) return false;
+    if (g->back_model != CTG_BACK_THRESHOLD && g->back_tau != 0.0) return false;
     if (g->N < 1 || g->N > 16384 || g->n_angles < 1 || g->n_angles > (1 << 20)) return false;
     if (g->n_det < 1 || g->n_det > 65536) return false;
     if (!(g->det_spacing > 0.0) || !std::isfinite(g->det_spacing)) return false;
     if ((double)g->n_det * g->det_spacing > (double)(1 << 20)) return false;
+    // detector coordinates of every pixel fit the 24-bit integer part of the
+    // back projectors' 24.40 fixed point
+    if (1.5 * g->N / g->det_spacing + g->n_det >= (double)(1 << 22)) return false;
     const double S = g->angle_start_deg, R = g->angle_range_deg;
     if (!std::isfinite(S) || !std::isfinite(R) || S != std::floor(S) || R != std::floor(R)) return false;
     if (R <= 0.0 || R > 360.0 || std::fabs(S) > 3600.0) return false;
@@ -99,6 +105,23 @@ void build_tables(const ctg_geom *g, std::vector<FwdAngle> &fw, std::vector<Back
     }
 }
 
+// Per-angle weights of the matched back projector; *rm = the extra detector
+// bins on each side that the widest angle needs beyond the two nearest.
+void build_matched(const ctg_geom *g, std::vector<MatchedAngle> &mt, int *rm) {
+    mt.resize(g->n_angles);
+    double wmax = 0.0;
+    for (int a = 0; a < g->n_angles; ++a) {
+        double cs, sn;
+        int rd;
+        angle_of(g, a, &cs, &sn, &rd);
+        const double c = std::fabs(rd ? cs : sn);      // >= 1/sqrt(2)
+        mt[a].scale = (float)(1.0 / c);
+        mt[a].inv_w = (float)(g->det_spacing / c);
+        wmax = std::max(wmax, c / g->det_spacing);
+    }
+    *rm = std::max(0, (int)std::ceil(wmax) - 1);
+}
+
 }  // namespace
 
 bool ctg_geom_valid(const ctg_geom *g) { return geom_valid(g); }
@@ -112,7 +135,8 @@ namespace {
 bool same_geom(const ctg_geom &a, const ctg_geom &b) {
     return a.N == b.N && a.n_angles == b.n_angles && a.n_det == b.n_det &&
            a.angle_start_deg == b.angle_start_deg && a.angle_range_deg == b.angle_range_deg &&
-           a.det_spacing == b.det_spacing;
+           a.det_spacing == b.det_spacing && a.back_model == b.back_model &&
+           a.back_tau == b.back_tau;
 }
 
 struct GeomEntry {
@@ -122,20 +146,74 @@ struct GeomEntry {
     int back_window = 0;        // detector window of the tiled back projector
     PadLayout pl{};             // staged-image layout of the forward projector
     float2 *pad = nullptr;      // context-owned staged image for ctg_project
+    MatchedAngle *mt = nullptr; // matched / thresholded back projector
+    int rm = 0;
+    float thr = 0.0f;           // B_tau threshold tau * max(A) (0: A^T)
     unsigned long long last_use = 0;
 };
+
+// x = B b (+ add) with the geometry's back projector; b of type `btype`.
+cudaError_t back_apply(const GeomEntry *ge, const void *b, int btype, const float *add, float *x,
+                       cudaStream_t st) {
+    const ctg_geom *g = &ge->g;
+    if (g->back_model == CTG_BACK_PIXEL)
+        return ctg_launch_back(b, btype, g->N, g->n_angles, g->n_det, ge->back, ge->back_window, add,
+                               x, st);
+    return ctg_launch_back_matched(b, btype, g->N, g->n_angles, g->n_det, ge->back, ge->mt, ge->rm,
+                                   ge->thr, add, x, st);
+}
 
 struct WsLayout {
     size_t off_w, ld_w, off_h, off_pad, off_vn0, off_vm0, off_vm1, off_y, off_red, total;
     size_t off_t, ld_t, off_r0m;   // BA only: T = A W_k and b - A x0
+    size_t off_n[4], off_m[5], off_state, off_hist;   // LSQR / LSMR only
     int64_t L, n, m;
     int kmax;
     int dtype;      // basis element type
     size_t es;      // basis element bytes
 };
 
+// LSQR / LSMR: no basis; n-vectors v, w or h, hbar, B u; m-vectors u, p = A v
+// and (LSMR) A h, A hbar, r; the staged image, the device state and history.
+bool layout_lsq(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) {
+    if (o->basis_dtype != CTG_BASIS_FP32) return false;
+    *ly = WsLayout{};
+    const int64_t n = (int64_t)g->N * g->N, m = (int64_t)g->n_angles * g->n_det;
+    ly->n = n;
+    ly->m = m;
+    ly->L = n;
+    ly->kmax = o->maxit;
+    ly->dtype = CTG_BASIS_FP32;
+    ly->es = 4;
+    size_t off = 0;
+    ly->off_pad = off;
+    off = align256(off + sizeof(float) * ctg_pad_layout(g->N, g->det_spacing).floats);
+    for (int i = 0; i < 4; ++i) {
+        ly->off_n[i] = off;
+        off = align256(off + sizeof(float) * round_up((size_t)n, 64));
+    }
+    const int nm = variant == CTG_LSMR ? 5 : 2;
+    for (int i = 0; i < 5; ++i) {
+        ly->off_m[i] = off;
+        if (i < nm) off = align256(off + sizeof(float) * round_up((size_t)m, 64));
+    }
+    ly->off_vm0 = ly->off_m[0];
+    ly->off_vm1 = ly->off_m[1];
+    ly->off_vn0 = ly->off_n[3];
+    ly->off_state = off;
+    off = align256(off + sizeof(LsqState));
+    ly->off_hist = off;
+    off = align256(off + sizeof(double) * (size_t)(o->maxit + 1));
+    ly->off_red = off;
+    off = align256(off + ctg_red_scratch_bytes(n > m ? n : m, 2));
+    ly->total = off;
+    return true;
+}
+
 bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) {
-    if (!geom_valid(g) || !opts_valid(o) || (variant != CTG_AB && variant != CTG_BA)) return false;
+    if (!geom_valid(g) || !opts_valid(o)) return false;
+    if (variant == CTG_LSQR || variant == CTG_LSMR) return layout_lsq(g, variant, o, ly);
+    if (variant != CTG_AB && variant != CTG_BA) return false;
     const int64_t n = (int64_t)g->N * g->N, m = (int64_t)g->n_angles * g->n_det;
     const int64_t L = variant == CTG_AB ? m : n;
     ly->n = n;
@@ -230,6 +308,7 @@ int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
         cudaFree(ctx->cache[victim].fwd);
         cudaFree(ctx->cache[victim].back);
         cudaFree(ctx->cache[victim].pad);
+        cudaFree(ctx->cache[victim].mt);
         ctx->cache.erase(ctx->cache.begin() + victim);
     }
     std::vector<FwdAngle> fw;
@@ -246,9 +325,30 @@ int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
         err = cudaMemcpy(e.fwd, fw.data(), sizeof(FwdAngle) * fw.size(), cudaMemcpyHostToDevice);
     if (err == cudaSuccess)
         err = cudaMemcpy(e.back, bk.data(), sizeof(BackAngle) * bk.size(), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess && g->back_model != CTG_BACK_PIXEL) {
+        std::vector<MatchedAngle> mt;
+        build_matched(g, mt, &e.rm);
+        err = cudaMalloc(&e.mt, sizeof(MatchedAngle) * mt.size());
+        if (err == cudaSuccess)
+            err = cudaMemcpy(e.mt, mt.data(), sizeof(MatchedAngle) * mt.size(), cudaMemcpyHostToDevice);
+        if (err == cudaSuccess && g->back_model == CTG_BACK_THRESHOLD) {
+            // tau * max(A), max over every entry of A (one pass, once per geometry)
+            unsigned *bits = nullptr;
+            unsigned host_bits = 0;
+            err = cudaMalloc(&bits, sizeof(unsigned));
+            if (err == cudaSuccess)
+                err = ctg_matched_max(g->N, g->n_angles, g->n_det, e.back, e.mt, e.rm, bits, nullptr);
+            if (err == cudaSuccess) err = cudaMemcpy(&host_bits, bits, sizeof(unsigned), cudaMemcpyDeviceToHost);
+            cudaFree(bits);
+            float amax;
+            std::memcpy(&amax, &host_bits, sizeof(float));
+            e.thr = (float)(g->back_tau * (double)amax);
+        }
+    }
     if (err != cudaSuccess) {
         cudaFree(e.fwd);
         cudaFree(e.back);
+        cudaFree(e.mt);
         return fail_cuda(err);
     }
     ctx->cache.push_back(e);
@@ -378,10 +478,7 @@ struct SolveCtx {
         });
     }
     cudaError_t back(const void *b, const float *add, float *x, int btype = CTG_BASIS_FP32) const {
-        return traced(ctx, 1, 1, st, [&] {
-            return ctg_launch_back(b, btype, g->N, g->n_angles, g->n_det, ge->back, ge->back_window,
-                                   add, x, st);
-        });
+        return traced(ctx, 1, 1, st, [&] { return back_apply(ge, b, btype, add, x, st); });
     }
     cudaError_t cgs2(int64_t L, int k, float *q) const {
         return traced(ctx, 2, k > 0 ? 4 : 2, st, [&] {
@@ -446,7 +543,8 @@ int solve_setup(ctg_ctx *ctx, const ctg_geom *g, int variant, const ctg_opts *o,
     sc->st = static_cast<cudaStream_t>(stream);
     int rc = get_geom(ctx, g, &sc->ge);
     if (rc) return rc;
-    rc = ensure_pinned(ctx, kRing * ring_slot_doubles(o->maxit) + (size_t)o->maxit + 16);
+    // after the ring: y_k (maxit doubles) or a staged LsqState
+    rc = ensure_pinned(ctx, kRing * ring_slot_doubles(o->maxit) + (size_t)o->maxit + 64);
     if (rc) return rc;
     if (ws == nullptr) {
         cudaError_t e = cudaMallocAsync(&ws, sc->ly.total, sc->st);
@@ -457,12 +555,14 @@ int solve_setup(ctg_ctx *ctx, const ctg_geom *g, int variant, const ctg_opts *o,
         if (((uintptr_t)ws & 255u) != 0) return CTG_ERR_INVALID_ARG;
     }
     sc->ws = static_cast<char *>(ws);
+    const bool lsq = variant == CTG_LSQR || variant == CTG_LSMR;
     ctg_red_scratch_carve(sc->ws + sc->ly.off_red, sc->ly.n > sc->ly.m ? sc->ly.n : sc->ly.m,
-                          o->maxit + 1, &sc->rs);
+                          lsq ? 2 : o->maxit + 1, &sc->rs);
     CTG_CK(cudaMemsetAsync(sc->rs.counter, 0, 4 * sizeof(unsigned), sc->st));
     CTG_CK(cudaMemsetAsync(sc->pad(), 0, sizeof(float) * sc->ge->pl.floats, sc->st));
-    CTG_CK(cudaMemsetAsync(sc->ws + sc->ly.off_h, 0,
-                           sizeof(double) * (size_t)(o->maxit + 1) * o->maxit, sc->st));
+    if (!lsq)
+        CTG_CK(cudaMemsetAsync(sc->ws + sc->ly.off_h, 0,
+                               sizeof(double) * (size_t)(o->maxit + 1) * o->maxit, sc->st));
     info->iters = 0;
     info->stop_reason = CTG_STOP_MAXIT;
     info->resnorm = 0.0;
@@ -692,6 +792,125 @@ int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
     return sc.true_resnorm(b, x, &info->resnorm);
 }
 
+// LSQR / LSMR (Sec. 5's comparators) with the geometry's back projector in
+// the role of A^T.  Each iteration is enqueued before the host reads the
+// previous one's `live` flag; the device decides the stop, so an iteration
+// enqueued after it changes nothing.
+int run_lsq(SolveCtx &sc, int method, const float *b, const float *x0, float *x,
+            const ctg_opts *o, ctg_info *info) {
+    const int64_t n = sc.ly.n, m = sc.ly.m;
+    char *ws = sc.ws;
+    auto nv = [&](int i) { return reinterpret_cast<float *>(ws + sc.ly.off_n[i]); };
+    auto mv = [&](int i) { return reinterpret_cast<float *>(ws + sc.ly.off_m[i]); };
+    float *v = nv(0), *a = nv(1), *c = method == CTG_LSMR ? nv(2) : nullptr, *q = nv(3);
+    float *u = mv(0), *p = mv(1);
+    LsqState *S = reinterpret_cast<LsqState *>(ws + sc.ly.off_state);
+    double *hist = reinterpret_cast<double *>(ws + sc.ly.off_hist);
+    const bool dp = o->noise_norm > 0.0;
+    const double target = dp ? o->tau * o->noise_norm : 0.0;
+    // u~_1 = b - A x0, beta_1^2 = ||u~_1||^2 (into S->beta2)
+    if (x0) {
+        CTG_CK(sc.forward(x0, p));
+        CTG_CK(sc.sub_norm2(b, p, u, m, &S->beta2));
+    } else {
+        CTG_CK(sc.sub_norm2(b, nullptr, u, m, &S->beta2));
+    }
+    // v~_1 = B u~_1 / beta_1, alpha_1^2 = ||v~_1||^2
+    CTG_CK(cudaMemsetAsync(v, 0, sizeof(float) * n, sc.st));
+    CTG_CK(sc.back(u, nullptr, q));
+    CTG_CK(traced(sc.ctx, 3, 1, sc.st, [&] { return ctg_lsq_bidiag_v(q, v, n, S, sc.rs, sc.st); }));
+    double *hp;
+    int rc = sc.fetch(&S->alpha2, 2, &hp);   // alpha2, beta2
+    if (rc) return rc;
+    const double alpha = std::sqrt(hp[0]), beta = std::sqrt(hp[1]);
+    info->rho = beta;
+    info->resnorm = beta;
+    if (info->history) info->history[0] = beta;
+    if ((dp && beta <= target) || beta == 0.0 || alpha == 0.0) {
+        info->stop_reason = dp && beta <= target ? CTG_STOP_DP : CTG_STOP_BREAKDOWN;
+        return copy_x0(sc, x0, x);
+    }
+    LsqState h0{};
+    h0.alpha2 = hp[0];
+    h0.beta2 = hp[1];
+    h0.alpha = alpha;
+    h0.beta = beta;
+    h0.rhobar = alpha;
+    h0.phibar = beta;
+    h0.alphabar = alpha;
+    h0.zetabar = alpha * beta;
+    h0.rho_old = 1.0;
+    h0.rhobar_old = 1.0;
+    h0.cbar = 1.0;
+    h0.sbar = 0.0;
+    h0.inv_alpha = 1.0 / alpha;
+    h0.target = target;
+    h0.hist = hist;
+    h0.method = method;
+    h0.k = 1;
+    h0.maxit = o->maxit;
+    h0.live = 1;
+    h0.live_update = 1;
+    h0.stop_reason = CTG_STOP_MAXIT;
+    h0.status[0] = 1.0;
+    h0.status[1] = beta;
+    double *stage = sc.pinned_scratch();
+    static_assert(sizeof(LsqState) % sizeof(double) == 0, "LsqState is staged as doubles");
+    static_assert(sizeof(LsqState) / sizeof(double) + 1 <= 64, "pinned staging area");
+    std::memcpy(stage, &h0, sizeof(LsqState));
+    stage[sizeof(LsqState) / sizeof(double)] = beta;          // history[0] = ||r_0||
+    CTG_CK(cudaMemcpyAsync(S, stage, sizeof(LsqState), cudaMemcpyHostToDevice, sc.st));
+    CTG_CK(cudaMemcpyAsync(hist, stage + sizeof(LsqState) / sizeof(double), sizeof(double),
+                           cudaMemcpyHostToDevice, sc.st));
+    if ((rc = copy_x0(sc, x0, x))) return rc;
+    CTG_CK(ctg_lsq_start(S, v, a, c, n, sc.st));
+    if (method == CTG_LSMR) {
+        CTG_CK(cudaMemcpyAsync(mv(4), u, sizeof(float) * m, cudaMemcpyDeviceToDevice, sc.st));  // r_0
+        CTG_CK(cudaMemsetAsync(mv(2), 0, sizeof(float) * m, sc.st));
+        CTG_CK(cudaMemsetAsync(mv(3), 0, sizeof(float) * m, sc.st));
+    }
+    if ((rc = ensure_events(sc.ctx))) return rc;
+    Pipeline pl{sc, o->maxit, sc.ctx->ev_h, sc.ctx->ev_r};
+    auto enqueue = [&](int kk) -> int {
+        CTG_CK(sc.forward(v, p));                                              // p = A v_k
+        CTG_CK(traced(sc.ctx, 3, 1, sc.st, [&] { return ctg_lsq_bidiag_u(p, u, m, S, sc.rs, sc.st); }));
+        CTG_CK(sc.back(u, nullptr, q));                                        // q = B u~_{k+1}
+        CTG_CK(traced(sc.ctx, 3, 4, sc.st, [&] {
+            cudaError_t e = ctg_lsq_bidiag_v(q, v, n, S, sc.rs, sc.st);
+            if (e == cudaSuccess) e = ctg_lsq_scalars(S, sc.st);
+            if (e == cudaSuccess) e = ctg_lsq_update(S, v, a, c, x, n, sc.st);
+            if (e == cudaSuccess && method == CTG_LSMR)
+                e = ctg_lsq_residual(S, p, mv(2), mv(3), mv(4), m, sc.rs, sc.st);
+            return e;
+        }));
+        double *sl = pl.slot(kk);
+        CTG_CK(cudaMemcpyAsync(sl, S->status, sizeof(double) * 2, cudaMemcpyDeviceToHost, sc.st));
+        CTG_CK(cudaEventRecord(pl.ev_h[kk % kRing], sc.st));
+        return CTG_OK;
+    };
+    int next = 1;
+    for (int k = 1; k <= o->maxit; ++k) {
+        if (next == k && (rc = enqueue(next++))) return rc;
+        if (next == k + 1 && k + 1 <= o->maxit && (rc = enqueue(next++))) return rc;
+        const double *st;
+        if ((rc = pl.wait_step(k, &st))) return rc;
+        if (st[0] == 0.0) break;
+    }
+    // final state, history and the true residual of x
+    double *fin;
+    if ((rc = sc.fetch(reinterpret_cast<const double *>(S), sizeof(LsqState) / sizeof(double), &fin)))
+        return rc;
+    LsqState hs;
+    std::memcpy(&hs, fin, sizeof(LsqState));
+    info->iters = hs.iters;
+    info->stop_reason = hs.stop_reason;
+    info->rho = hs.status[1];
+    if (info->history && hs.iters > 0)
+        CTG_CK(cudaMemcpyAsync(info->history + 1, hist + 1, sizeof(double) * hs.iters,
+                               cudaMemcpyDeviceToHost, sc.st));
+    return sc.true_resnorm(b, x, &info->resnorm);
+}
+
 int solve(int variant, ctg_ctx *ctx, const ctg_geom *g, const float *b, const float *x0,
           float *x, const ctg_opts *o, void *ws, size_t ws_bytes, ctg_info *info,
           void *stream) {
@@ -703,7 +922,9 @@ int solve(int variant, ctg_ctx *ctx, const ctg_geom *g, const float *b, const fl
         if (owned) cudaFreeAsync(owned, sc.st);
         return rc;
     }
-    rc = variant == CTG_AB ? run_ab(sc, b, x0, x, o, info) : run_ba(sc, b, x0, x, o, info);
+    rc = variant == CTG_AB   ? run_ab(sc, b, x0, x, o, info)
+         : variant == CTG_BA ? run_ba(sc, b, x0, x, o, info)
+                             : run_lsq(sc, variant, b, x0, x, o, info);
     if (rc == CTG_OK) {
         cudaError_t e = cudaStreamSynchronize(sc.st);
         if (e != cudaSuccess) rc = fail_cuda(e);
@@ -740,6 +961,7 @@ void ctg_destroy(ctg_ctx *ctx) {
         cudaFree(e.fwd);
         cudaFree(e.back);
         cudaFree(e.pad);
+        cudaFree(e.mt);
     }
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     delete ctx;
@@ -770,11 +992,7 @@ int ctg_backproject(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, float *
     int rc = get_geom(ctx, g, &ge);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CTG_CK(traced(ctx, 1, 1, st, [&] {
-        return ctg_launch_back(b_dev, CTG_BASIS_FP32, g->N, g->n_angles, g->n_det, ge->back,
-                               ge->back_window,
-                               nullptr, x_dev, st);
-    }));
+    CTG_CK(traced(ctx, 1, 1, st, [&] { return back_apply(ge, b_dev, CTG_BASIS_FP32, nullptr, x_dev, st); }));
     return CTG_OK;
 }
 
@@ -797,6 +1015,18 @@ int ctg_ab_gmres(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, const floa
                  float *x_dev, const ctg_opts *o, void *workspace_dev, size_t workspace_bytes,
                  ctg_info *info, void *stream) {
     return solve(CTG_AB, ctx, g, b_dev, x0_dev, x_dev, o, workspace_dev, workspace_bytes, info, stream);
+}
+
+int ctg_lsqr(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, const float *x0_dev, float *x_dev,
+             const ctg_opts *opts, void *workspace, size_t workspace_bytes, ctg_info *info,
+             void *stream) {
+    return solve(CTG_LSQR, ctx, g, b_dev, x0_dev, x_dev, opts, workspace, workspace_bytes, info, stream);
+}
+
+int ctg_lsmr(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, const float *x0_dev, float *x_dev,
+             const ctg_opts *opts, void *workspace, size_t workspace_bytes, ctg_info *info,
+             void *stream) {
+    return solve(CTG_LSMR, ctx, g, b_dev, x0_dev, x_dev, opts, workspace, workspace_bytes, info, stream);
 }
 
 int ctg_ba_gmres(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, const float *x0_dev,

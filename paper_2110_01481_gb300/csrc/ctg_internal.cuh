@@ -39,6 +39,14 @@ struct BackAngle {
     float cf, sf;          // COS, SIN in float (tile-local offsets)
 };
 
+// Matched back projector A^T (and B_tau) of one angle: with c = cos for a
+// row-driven angle and sin for a column-driven one, pixel (i, j) takes bin
+// d with weight scale * max(0, 1 - |d - u(i, j)| * inv_w), u as in
+// BackAngle, scale = 1/|c|, inv_w = ds/|c|.
+struct MatchedAngle {
+    float scale, inv_w;
+};
+
 // Staged image read by the forward projector: two copies, x and x^T, each N
 // rows of `stride` pairs (v[j] - dv[j], dv[j]) with dv[j] = v[j+1] - v[j]
 // for columns j = -border .. N + border - 1 (zeros outside the image), so
@@ -80,6 +88,17 @@ cudaError_t ctg_launch_back(const void *b, int dtype, int N, int n_angles, int n
                             const BackAngle *tab, int window, const float *add, float *x,
                             cudaStream_t st);
 
+// ---- matched back projector (matched.cu) ----------------------------------
+// x = B_thr b (+ add): the transpose of the forward projector, keeping the
+// terms whose weight is >= thr (thr = 0: A^T exactly); rm = extra detector
+// bins on each side beyond the two nearest (0 when ds >= max |c|).
+cudaError_t ctg_launch_back_matched(const void *b, int dtype, int N, int n_angles, int n_det,
+                                    const BackAngle *tab, const MatchedAngle *mt, int rm, float thr,
+                                    const float *add, float *x, cudaStream_t st);
+// *max_bits = bit pattern of max_ij A_ij (a float >= 0), on the device.
+cudaError_t ctg_matched_max(int N, int n_angles, int n_det, const BackAngle *tab,
+                            const MatchedAngle *mt, int rm, unsigned *max_bits, cudaStream_t st);
+
 // ---- Krylov kernels (arnoldi.cu) -----------------------------------------
 // Reduction scratch for one vector length L and up to kmax coefficients.
 struct RedScratch {
@@ -120,6 +139,50 @@ cudaError_t ctg_sub_norm2(const float *a, const float *c, float *out, int64_t L,
 // nrm2 == 0).
 cudaError_t ctg_scale(const float *v, const double *nrm2, void *out, int dtype, int64_t L,
                       cudaStream_t st);
+
+// ---- LSQR / LSMR (lsq.cu) --------------------------------------------------
+// Device state of one LSQR or LSMR solve (Golub-Kahan bidiagonalisation with
+// the scalar recurrences on the device, so the host only watches `live`).
+// The vectors u are kept unnormalised (u~ = beta u).  Written by the host
+// at the start, then only by the kernels.
+struct LsqState {
+    double alpha2, beta2;         // ||v~||^2, ||u~||^2 of the latest bidiagonalisation step
+    double alpha, beta;           // alpha_k, beta_k (normalisers of v_k, u_k)
+    double rhobar, phibar;        // LSQR
+    double alphabar, zetabar, rho_old, rhobar_old, cbar, sbar;   // LSMR
+    double inv_alpha;             // 1 / alpha_{k+1} for the update
+    double cx, cw;                // LSQR: x += cx w, w = v - cw w
+    double chbar, ch, ch_prev;    // LSMR: hbar = h - chbar hbar, x += cx hbar, h = v - ch h
+    double r2;                    // LSMR: ||r_k||^2 of the tracked residual
+    double target;                // tau ||e|| (0: no discrepancy stop)
+    double *hist;                 // residual history (maxit + 1 doubles, device)
+    int method;                   // CTG_LSQR / CTG_LSMR
+    int k, maxit;                 // iteration being performed
+    int live;                     // 1 while iterating
+    int live_update;              // the current iteration's update is applied
+    int iters, stop_reason;
+    double status[2];             // {live, latest residual estimate} for the host
+};
+// u = p - (alpha/beta) u, state->beta2 = ||u||^2
+cudaError_t ctg_lsq_bidiag_u(const float *p, float *u, int64_t m, LsqState *state,
+                             const RedScratch &rs, cudaStream_t st);
+// v = q / beta' - beta' v with beta' = sqrt(state->beta2), state->alpha2 = ||v||^2
+cudaError_t ctg_lsq_bidiag_v(const float *q, float *v, int64_t n, LsqState *state,
+                             const RedScratch &rs, cudaStream_t st);
+// rotations and update coefficients of iteration k, the stopping rules
+cudaError_t ctg_lsq_scalars(LsqState *state, cudaStream_t st);
+// LSQR: v /= alpha, x += cx w, w = v - cw w; LSMR: v /= alpha,
+// hbar = h - chbar hbar, x += cx hbar, h = v - ch h (a = w or h, c = hbar)
+cudaError_t ctg_lsq_update(const LsqState *state, float *v, float *a, float *c, float *x,
+                           int64_t n, cudaStream_t st);
+// LSMR residual r_k = b - A x_k tracked in sinogram space from p = A v_k:
+// Ah = p - ch_prev Ah, Ahbar = Ah - chbar Ahbar, r -= cx Ahbar, r2 = ||r||^2;
+// then the discrepancy test on it
+cudaError_t ctg_lsq_residual(LsqState *state, const float *p, float *Ah, float *Ahbar, float *r,
+                             int64_t m, const RedScratch &rs, cudaStream_t st);
+// start: v = v~ / alpha_1 and w = v (LSQR) or h = v, hbar = 0 (LSMR)
+cudaError_t ctg_lsq_start(const LsqState *state, float *v, float *a, float *c, int64_t n,
+                          cudaStream_t st);
 
 // ---- batched engine (batch.cu; kernels in projectors.cu and arnoldi.cu) ----
 // Device-resident state of one instance (one solve) of a batch.  A round of

@@ -1,0 +1,188 @@
+// Vector helpers shared by the Krylov kernels (arnoldi.cu, lsq.cu): float4
+// loads and stores with a ragged tail, 16-bit basis loads and conversions,
+// warp sums, and the deterministic last-block reduction (every block writes
+// its partial sums, the last block to arrive sums them in a fixed order in
+// FP64; no block waits for another).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
+#include "ctg_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256, kWarps = kThreads / 32;
+constexpr int kTargetGrid = 2 * 152;   // 2 blocks on each of GB300's 152 SMs
+constexpr int kMaxE = 8;               // float4 groups per thread, at most
+
+__device__ __forceinline__ float4 ld4(const float *p, int64_t g, int64_t L) {
+    const int64_t i = 4 * g;
+    if (i + 3 < L) return __ldg(reinterpret_cast<const float4 *>(p + i));
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < L) v.x = p[i];
+    if (i + 1 < L) v.y = p[i + 1];
+    if (i + 2 < L) v.z = p[i + 2];
+    return v;
+}
+
+__device__ __forceinline__ float4 ld4_rw(const float *p, int64_t g, int64_t L) {
+    const int64_t i = 4 * g;
+    if (i + 3 < L) return *reinterpret_cast<const float4 *>(p + i);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < L) v.x = p[i];
+    if (i + 1 < L) v.y = p[i + 1];
+    if (i + 2 < L) v.z = p[i + 2];
+    return v;
+}
+
+__device__ __forceinline__ void st4(float *p, int64_t g, int64_t L, float4 v) {
+    const int64_t i = 4 * g;
+    if (i + 3 < L) {
+        *reinterpret_cast<float4 *>(p + i) = v;
+        return;
+    }
+    if (i < L) p[i] = v.x;
+    if (i + 1 < L) p[i + 1] = v.y;
+    if (i + 2 < L) p[i + 2] = v.z;
+}
+
+// Basis vectors may be stored in FP32, BF16 or FP16; every kernel converts
+// them to FP32 on use and accumulates in FP32 (reductions in FP64).  A
+// float4 group of the FP32 work vector pairs with one 8-byte load of a
+// 16-bit basis vector.
+// Raw (unconverted) loads, so that a batch of loads is issued before any
+// conversion consumes one: FP32 groups stay float4, 16-bit groups are
+// loaded as uint2 and converted only when used.
+template <typename T> struct RawOf { using type = uint2; };
+template <> struct RawOf<float> { using type = float4; };
+
+__device__ __forceinline__ float4 ldraw(const float *p, int64_t g, int64_t L) { return ld4(p, g, L); }
+
+template <typename H>
+__device__ __forceinline__ uint2 ldraw16(const H *p, int64_t g, int64_t L) {
+    const int64_t i = 4 * g;
+    if (i + 3 < L) return __ldg(reinterpret_cast<const uint2 *>(p + i));
+    unsigned short h[4] = {0, 0, 0, 0};
+    const unsigned short *ps = reinterpret_cast<const unsigned short *>(p);
+    if (i < L) h[0] = ps[i];
+    if (i + 1 < L) h[1] = ps[i + 1];
+    if (i + 2 < L) h[2] = ps[i + 2];
+    return make_uint2((unsigned)h[0] | ((unsigned)h[1] << 16), (unsigned)h[2] | ((unsigned)h[3] << 16));
+}
+__device__ __forceinline__ uint2 ldraw(const __nv_bfloat16 *p, int64_t g, int64_t L) { return ldraw16(p, g, L); }
+__device__ __forceinline__ uint2 ldraw(const __half *p, int64_t g, int64_t L) { return ldraw16(p, g, L); }
+
+template <typename T> __device__ __forceinline__ float4 cvt4(float4 r) { return r; }
+template <typename T> __device__ __forceinline__ float4 cvt4(uint2 u);
+template <> __device__ __forceinline__ float4 cvt4<__nv_bfloat16>(uint2 u) {
+    // a bf16 is the top half of an FP32
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+}
+template <> __device__ __forceinline__ float4 cvt4<__half>(uint2 u) {
+    __half2 a, b;
+    memcpy(&a, &u.x, 4);
+    memcpy(&b, &u.y, 4);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+__device__ __forceinline__ void stw4(float *p, int64_t g, int64_t L, float4 v) { st4(p, g, L, v); }
+
+template <typename H>
+__device__ __forceinline__ H to16(float x) {
+    if constexpr (std::is_same<H, __nv_bfloat16>::value) return __float2bfloat16_rn(x);
+    else return __float2half_rn(x);
+}
+
+template <typename H>
+__device__ __forceinline__ void stw4_16(H *p, int64_t g, int64_t L, float4 v) {
+    const int64_t i = 4 * g;
+    if (i + 3 < L) {
+        H h[4] = {to16<H>(v.x), to16<H>(v.y), to16<H>(v.z), to16<H>(v.w)};
+        uint2 u;
+        memcpy(&u, h, 8);
+        *reinterpret_cast<uint2 *>(p + i) = u;
+        return;
+    }
+    if (i < L) p[i] = to16<H>(v.x);
+    if (i + 1 < L) p[i + 1] = to16<H>(v.y);
+    if (i + 2 < L) p[i + 2] = to16<H>(v.z);
+}
+__device__ __forceinline__ void stw4(__nv_bfloat16 *p, int64_t g, int64_t L, float4 v) { stw4_16(p, g, L, v); }
+__device__ __forceinline__ void stw4(__half *p, int64_t g, int64_t L, float4 v) { stw4_16(p, g, L, v); }
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+
+__device__ __forceinline__ float warp_sum(float s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+__device__ __forceinline__ double warp_sum_d(double s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Partial sums are laid out [j][Gp] with Gp = G rounded up to 4, so the
+// last block can read them as float4.
+__host__ __device__ inline int padded_grid(int G) { return (G + 3) & ~3; }
+
+// Writes this block's nred partial sums, then lets the last block sum all
+// blocks' partials (fixed order, FP64) into red_out[0..nred-1].  The last
+// block's warps each take four coefficients at a time and read the partials
+// as float4, so the serial tail is a few L2 round trips.
+__device__ void block_reduce_finish(float *s_w, int nred, float *__restrict__ partials,
+                                    unsigned *__restrict__ counter,
+                                    double *__restrict__ red_out, int blk, int G) {
+    __shared__ bool s_last;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Gp = padded_grid(G);
+    __syncthreads();
+    for (int j = tid; j < nred; j += kThreads) {
+        float s = 0.f;
+        for (int w = 0; w < kWarps; ++w) s += s_w[w * nred + j];
+        partials[(size_t)j * Gp + blk] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(counter, 1u) == (unsigned)(G - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int G4 = Gp / 4;
+    for (int j0 = warp * 4; j0 < nred; j0 += kWarps * 4) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int g4 = lane; g4 < G4; g4 += 32) {
+            float4 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                v[q] = (j0 + q < nred)
+                           ? __ldcg(reinterpret_cast<const float4 *>(partials + (size_t)(j0 + q) * Gp) + g4)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int b0 = 4 * g4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                // the padding entries (block index >= G) were never written
+                acc[q] += (double)v[q].x;
+                if (b0 + 1 < G) acc[q] += (double)v[q].y;
+                if (b0 + 2 < G) acc[q] += (double)v[q].z;
+                if (b0 + 3 < G) acc[q] += (double)v[q].w;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double t = warp_sum_d(acc[q]);
+            if (lane == 0 && j0 + q < nred) red_out[j0 + q] = t;
+        }
+    }
+    if (tid == 0) *counter = 0u;
+}
+
+}  // namespace

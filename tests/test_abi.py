@@ -45,9 +45,9 @@ def test_status_strings(lib):
     assert lib.ctg_status_string(-99) == b"unknown status"
 
 
-def _g(N, Na, Nd, S=0.0, R=180.0, ds=1.0):
+def _g(N, Na, Nd, S=0.0, R=180.0, ds=1.0, model=0, tau=0.0):
     from paper_2110_01481_gb300 import _native as nat
-    return nat.CtgGeom(N, Na, Nd, 0, S, R, ds)
+    return nat.CtgGeom(N, Na, Nd, model, S, R, ds, tau)
 
 
 def _o(maxit):
@@ -65,10 +65,13 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert ws(_g(64, 90, 91, R=0.0), 0, _o(10)) == 0
     assert ws(_g(64, 90, 91, ds=0.0), 0, _o(10)) == 0
     assert ws(_g(64, 90, 91), 0, _o(0)) == 0            # maxit >= 1
-    assert ws(_g(64, 90, 91), 2, _o(10)) == 0            # unknown variant
-    g = _g(64, 90, 91)
-    g.reserved = 1
-    assert ws(g, 0, _o(10)) == 0
+    assert ws(_g(64, 90, 91), 4, _o(10)) == 0            # unknown variant
+    assert ws(_g(64, 90, 91, model=3), 0, _o(10)) == 0   # unknown back projector
+    assert ws(_g(64, 90, 91, model=2, tau=1.5), 0, _o(10)) == 0   # B_tau needs tau in [0, 1]
+    assert ws(_g(64, 90, 91, model=2, tau=-0.1), 0, _o(10)) == 0
+    assert ws(_g(64, 90, 91, model=1, tau=0.3), 0, _o(10)) == 0   # tau only with B_tau
+    assert ws(_g(64, 90, 91, model=2, tau=0.3), 0, _o(10)) > 0
+    assert ws(_g(64, 90, 91, model=1), 1, _o(10)) > 0
     # solvers and projectors refuse null pointers before touching the GPU
     assert lib.ctg_project(None, ctypes.byref(_g(64, 90, 91)), None, None, None) == -1
     assert lib.ctg_ab_gmres(None, ctypes.byref(_g(64, 90, 91)), None, None, None,
@@ -109,3 +112,36 @@ def test_workspace_follows_the_krylov_storage_law(lib):
         staged = 4 * 4 * N * (N + 2 * 51)
         assert 0 < other <= t_bytes + staged + 4 * 2 * (n + 2 * m) + 8 * (k + 1) * (k + 2) \
             + 4 * (k + 4) * 1300 + 16384
+
+
+def test_lsqr_lsmr_workspace_is_independent_of_maxit(lib):
+    """LSQR and LSMR keep no basis (short recurrences): O(n + m) bytes, plus
+    the residual history (one double per iteration)."""
+    from paper_2110_01481_gb300 import _native as nat
+    g = _g(128, 180, 182, model=1)
+    n, m = 128 * 128, 180 * 182
+    ws = lambda v, k: lib.ctg_workspace_bytes(ctypes.byref(g), v, ctypes.byref(_o(k)))
+    for v, nm in ((nat.CTG_LSQR, 2), (nat.CTG_LSMR, 5)):
+        assert 0 < ws(v, 1000) - ws(v, 10) <= 8 * 990 + 256
+        staged = 4 * 4 * 128 * (128 + 2 * 51)
+        assert 4 * (4 * n + nm * m) < ws(v, 10) <= staged + 4 * (4 * n + nm * m) + 8 * 1001 + 65536
+    o = _o(10)
+    o.basis_dtype = nat.CTG_BASIS_BF16      # no basis to store in 16 bits
+    assert lib.ctg_workspace_bytes(ctypes.byref(g), nat.CTG_LSQR, ctypes.byref(o)) == 0
+    # a GMRES workspace grows with maxit (the basis)
+    assert ws(nat.CTG_AB, 100) > ws(nat.CTG_AB, 10)
+
+
+def test_engine_admission_bytes_on_the_host(lib):
+    """The serving engine sizes a request without touching the GPU: about
+    (maxit + 1) basis vectors; batched solves take the pixel-driven B only."""
+    from paper_2110_01481_gb300 import _native as nat
+    g, o = _g(128, 180, 182), _o(40)
+    rb = lambda g, v, o: lib.ctg_engine_request_bytes(ctypes.byref(g), v, ctypes.byref(o))
+    ab, ba = rb(g, nat.CTG_AB, o), rb(g, nat.CTG_BA, o)
+    assert 4 * 41 * 180 * 182 <= ab < 4 * 41 * 180 * 182 + (4 << 20)
+    assert 4 * 41 * (128 * 128 + 180 * 182) <= ba          # W (n) and T = A W (m)
+    assert rb(_g(128, 180, 182, model=1), nat.CTG_AB, o) == 0
+    assert rb(g, nat.CTG_LSQR, o) == 0
+    o.maxit = 1025
+    assert rb(g, nat.CTG_AB, o) == 0

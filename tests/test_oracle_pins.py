@@ -7,6 +7,8 @@ library result or a value printed in the paper.  CPU only.
 import math
 
 import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg  # noqa: F401
 import pytest
 import scipy.sparse.linalg as sla
 
@@ -198,6 +200,37 @@ def _krylov_basis(M, d, k):
         K[:, j] = v
         v = M @ v
     return np.linalg.qr(K)[0]
+
+
+def test_thresholded_back_projector_against_matrix_free_columns(oracle_mod):
+    """Sec. 6.5, eq. (Btau): B_tau keeps the entries of A^T that are at least
+    tau max(A).  The explicit form is checked against the columns of A taken
+    one by one from the matrix-free forward projector (A e_j), thresholded
+    by hand; tau = 0 is A^T itself."""
+    O = oracle_mod
+    for g in (O.Geometry(9, 7, 13, 0, 180), O.Geometry(8, 6, 12, 30, 120, 0.75)):
+        cols = np.stack([O.forward(g, np.eye(g.n)[j]) for j in range(g.n)], axis=1)   # m x n
+        amax = cols.max()
+        for tau in (0.0, 0.1, 0.5, 0.9):
+            ref = np.where(cols >= tau * amax, cols, 0.0).T
+            got = O.matrix_B_tau(g, tau).toarray()
+            assert np.allclose(got, ref, rtol=0, atol=1e-13), (g, tau)
+        assert np.array_equal(O.matrix_B_tau(g, 0.0).toarray(), O.matrix_A(g).toarray().T)
+
+
+def test_unmatchedness_grows_with_tau(oracle_mod):
+    """Table 4's measure ||B_tau - A^T||_F / ||A||_F is 0 at tau = 0 and grows
+    with tau; B_tau at tau = 1 keeps only the largest entries."""
+    O = oracle_mod
+    g = O.Geometry(32, 45, I.detector_count(32), 0, 180)
+    A = O.matrix_A(g)
+    AT = A.T.tocsr()
+    fa = sp.linalg.norm(A)
+    meas = [sp.linalg.norm(O.matrix_B_tau(g, t) - AT) / fa for t in (0.0, 0.01, 0.1, 0.3, 0.5)]
+    assert meas[0] == 0.0
+    assert all(b > a for a, b in zip(meas, meas[1:]))
+    B1 = O.matrix_B_tau(g, 1.0)
+    assert B1.nnz >= 1 and np.all(B1.data == A.data.max())
 
 
 @pytest.mark.parametrize("ortho", ["mgs", "cgs2"])
