@@ -12,10 +12,13 @@ nothing from it.
   krylov      AB-GMRES and BA-GMRES exactly as the algorithm box of Sec. 2
               (MGS Arnoldi; CGS2 as an option), the discrepancy principle of
               Sec. 6.4, and LSQR / LSMR for the matched case of Sec. 5
+  stopping    the NCP criterion of Sec. 6.4 (a reading of its citation)
 """
 from .projectors import (Geometry, angles, forward, backproject, matrix_A,
                          matrix_B, matrix_B_tau, build_library)
 from .krylov import ab_gmres, ba_gmres, lsqr, lsmr
+from .stopping import ncp, ncp_distance, first_local_minimum
 
 __all__ = ["Geometry", "angles", "forward", "backproject", "matrix_A",
-           "matrix_B", "matrix_B_tau", "build_library", "ab_gmres", "ba_gmres", "lsqr", "lsmr"]
+           "matrix_B", "matrix_B_tau", "build_library", "ab_gmres", "ba_gmres", "lsqr", "lsmr",
+           "ncp", "ncp_distance", "first_local_minimum"]

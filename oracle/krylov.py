@@ -18,7 +18,8 @@ Sec. 2 step by step and in its notation:
 ``y_k`` is taken from a library least-squares solve of the (k+1) x k
 Hessenberg problem, i.e. straight from its definition.  The stopping rule is
 the discrepancy principle of Sec. 6.4: stop at the smallest k >= 0 with
-||b - A x_k|| <= tau ||e||; without it (noise_norm None) run to maxit.
+||b - A x_k|| <= tau ||e||; without it (noise_norm None) run to maxit.  With
+``ncp_shape`` the NCP criterion of Sec. 6.4 decides instead (``stopping``).
 
 Readings where the paper is silent: ``ortho='cgs2'`` replaces the MGS inner
 loop by classical Gram-Schmidt applied twice (equal in exact arithmetic); a
@@ -34,7 +35,9 @@ from __future__ import annotations
 
 import numpy as np
 
-STOP_MAXIT, STOP_DP, STOP_BREAKDOWN = 0, 1, 2
+from .stopping import ncp_distance
+
+STOP_MAXIT, STOP_DP, STOP_BREAKDOWN, STOP_NCP = 0, 1, 2, 3
 BREAKDOWN_RTOL = 1e-14
 
 
@@ -57,16 +60,24 @@ def _orthogonalise(q, W, k, ortho):
 
 
 def _gmres(apply_M, r0, form_x, resid_norm, maxit, tau, noise_norm, ortho,
-           keep):
+           keep, resid_vec=None, ncp_shape=None):
     """Shared Arnoldi/GMRES loop of both columns of the algorithm box.
 
     apply_M(w) is A B w (AB) or B A w (BA); form_x(Wk, y) builds x_k;
-    resid_norm(x) returns ||b - A x||."""
+    resid_norm(x) returns ||b - A x||.  With ncp_shape = (N_a, N_d) the stop
+    is the NCP criterion of Sec. 6.4 instead (``stopping``): the NCP
+    distance d_k of b - A x_k (resid_vec) is recorded for every k, and the
+    solve returns x_k at the first k with d_{k+1} > d_k."""
     L = r0.size
     beta = float(np.linalg.norm(r0))
     x = form_x(np.zeros((0, L)), np.zeros(0))
     out = {"iterates": [x] if keep else None, "rho": [beta],
            "resnorm": [resid_norm(x)], "stop_reason": STOP_MAXIT}
+    use_ncp = ncp_shape is not None
+    if use_ncp:
+        out["ncp"] = [ncp_distance(resid_vec(x), *ncp_shape)]
+        noise_norm = None
+    x_prev = x
     target = None if noise_norm is None else tau * noise_norm
     if target is not None and out["resnorm"][0] <= target:
         out.update(x=x, k=0, stop_reason=STOP_DP, W=np.zeros((0, L)),
@@ -103,6 +114,12 @@ def _gmres(apply_M, r0, form_x, resid_norm, maxit, tau, noise_norm, ortho,
         out["resnorm"].append(resid_norm(x))
         if keep:
             out["iterates"].append(x)
+        if use_ncp:
+            out["ncp"].append(ncp_distance(resid_vec(x), *ncp_shape))
+            if out["ncp"][-1] > out["ncp"][-2]:        # d_k > d_{k-1}: stop at k - 1
+                out.update(x=x_prev, k=k - 1, stop_reason=STOP_NCP, W=W[:k], H=H[:k, :k - 1])
+                return out
+            x_prev = x
         if target is not None and out["resnorm"][-1] <= target:
             out["stop_reason"] = STOP_DP
             break
@@ -111,7 +128,7 @@ def _gmres(apply_M, r0, form_x, resid_norm, maxit, tau, noise_norm, ortho,
 
 
 def ab_gmres(A, B, b, maxit, x0=None, tau=1.0, noise_norm=None, ortho="mgs",
-             keep_iterates=False):
+             keep_iterates=False, ncp_shape=None):
     """AB-GMRES (Sec. 2, left column).  A, B: callables (or matrices).
 
     Returns a dict with x (the returned iterate), k, stop_reason, rho
@@ -127,11 +144,12 @@ def ab_gmres(A, B, b, maxit, x0=None, tau=1.0, noise_norm=None, ortho="mgs",
     return _gmres(lambda w: A_(B_(w)), r0,
                   lambda Wk, y: x0 + B_(Wk.T @ y) if y.size else x0.copy(),
                   lambda x: float(np.linalg.norm(b - A_(x))),
-                  maxit, tau, noise_norm, ortho, keep_iterates)
+                  maxit, tau, noise_norm, ortho, keep_iterates,
+                  lambda x: b - A_(x), ncp_shape)
 
 
 def ba_gmres(A, B, b, maxit, x0=None, tau=1.0, noise_norm=None, ortho="mgs",
-             keep_iterates=False):
+             keep_iterates=False, ncp_shape=None):
     """BA-GMRES (Sec. 2, right column); same return convention as
     ``ab_gmres`` with basis vectors of length n."""
     A_ = A if callable(A) else (lambda v, M=A: M @ v)
@@ -143,7 +161,8 @@ def ba_gmres(A, B, b, maxit, x0=None, tau=1.0, noise_norm=None, ortho="mgs",
     return _gmres(lambda w: B_(A_(w)), r0,
                   lambda Wk, y: x0 + Wk.T @ y if y.size else x0.copy(),
                   lambda x: float(np.linalg.norm(b - A_(x))),
-                  maxit, tau, noise_norm, ortho, keep_iterates)
+                  maxit, tau, noise_norm, ortho, keep_iterates,
+                  lambda x: b - A_(x), ncp_shape)
 
 
 def _reorth(v, basis):

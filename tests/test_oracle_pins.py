@@ -233,6 +233,65 @@ def test_unmatchedness_grows_with_tau(oracle_mod):
     assert B1.nnz >= 1 and np.all(B1.data == A.data.max())
 
 
+def test_ncp_closed_forms(oracle_mod):
+    """The NCP reading of Sec. 6.4: an impulse has a flat periodogram, so its
+    NCP is the white-noise line exactly; a sinusoid at frequency f puts all
+    its power at f, so its NCP is the step 1[i >= f]; the periodogram equals
+    the DFT written out as a sum."""
+    O = oracle_mod
+    for n_det in (10, 11, 64):
+        q = n_det // 2
+        line = np.arange(1, q + 1) / q
+        e0 = np.zeros(n_det)
+        e0[3] = 2.5
+        assert np.allclose(O.ncp(e0), line, atol=1e-14)
+        for f in (1, 2, q - 1):
+            r = np.cos(2 * np.pi * f * np.arange(n_det) / n_det + 0.3)
+            step = (np.arange(1, q + 1) >= f).astype(float)
+            assert np.allclose(O.ncp(r), step, atol=1e-12)
+            want = math.sqrt(np.sum((step - line) ** 2))
+            assert O.ncp_distance(np.tile(r, 3), 3, n_det) == pytest.approx(want, rel=1e-12)
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal(11)
+    dft = np.array([abs(sum(r[d] * np.exp(-2j * np.pi * i * d / 11) for d in range(11))) ** 2
+                    for i in range(1, 6)])
+    assert np.allclose(O.ncp(r), np.cumsum(dft) / dft.sum(), atol=1e-13)
+
+
+def test_ncp_of_white_noise_matches_its_distribution(oracle_mod):
+    """For white Gaussian noise the periodogram ordinates are i.i.d.
+    exponential, so c_i ~ Beta(i, q - i) and E ||c - i/q||^2 = (q - 1) / (6 q)."""
+    O = oracle_mod
+    rng = np.random.default_rng(5)
+    n_a, n_det = 3000, 129                         # odd: no real Nyquist ordinate
+    q = n_det // 2
+    R = rng.standard_normal((n_a, n_det))
+    line = np.arange(1, q + 1) / q
+    d2 = np.mean([np.sum((O.ncp(row) - line) ** 2) for row in R])
+    assert d2 == pytest.approx((q - 1) / (6 * q), rel=0.06)
+    assert O.first_local_minimum([5, 4, 3, 3.5, 1]) == 2
+    assert O.first_local_minimum([5, 4, 3]) == 2
+    assert O.first_local_minimum([1, 2]) == 0
+
+
+def test_ncp_stop_of_gmres(oracle_mod, cfg1_problem):
+    """The NCP stop returns the iterate at the first local minimum of the
+    NCP distance; on these problems it stops before the discrepancy
+    principle, as Sec. 6.4 observes."""
+    O = oracle_mod
+    og, A, B, xt, b, enorm = cfg1_problem
+    for fn in (O.ab_gmres, O.ba_gmres):
+        r = fn(A, B, b, 40, ncp_shape=(og.n_angles, og.n_det), keep_iterates=True)
+        k = r["k"]
+        assert r["stop_reason"] == 3 and k == O.first_local_minimum(r["ncp"])
+        assert np.array_equal(r["x"], r["iterates"][k])
+        for j in (0, k, k + 1):
+            assert r["ncp"][j] == pytest.approx(
+                O.ncp_distance(b - A @ r["iterates"][j], og.n_angles, og.n_det), rel=1e-12)
+        dp = fn(A, B, b, 40, noise_norm=enorm)
+        assert k < dp["k"]
+
+
 @pytest.mark.parametrize("ortho", ["mgs", "cgs2"])
 def test_gmres_matches_brute_force_krylov_minimiser(oracle_mod, ortho):
     """Sec. 2: both methods search x0 + K_k(BA, B r0); AB minimises
