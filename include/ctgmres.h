@@ -57,7 +57,13 @@ enum {
 };
 
 enum { CTG_AB = 0, CTG_BA = 1, CTG_LSQR = 2, CTG_LSMR = 3 };                       /* solver variant    */
-enum { CTG_STOP_MAXIT = 0, CTG_STOP_DP = 1, CTG_STOP_BREAKDOWN = 2 };
+enum { CTG_STOP_MAXIT = 0, CTG_STOP_DP = 1, CTG_STOP_BREAKDOWN = 2, CTG_STOP_NCP = 3 };
+/* Stopping rule (Sec. 6.4).  CTG_RULE_DP: the discrepancy principle when
+ * noise_norm > 0, else maxit.  CTG_RULE_NCP: the NCP criterion (see
+ * ctg_ncp_distance): the solve returns x_k at the first k with
+ * d_{k+1} > d_k, d_k the NCP distance of b - A x_k (noise_norm is not
+ * used); needs 2 <= n_det <= 8192. */
+enum { CTG_RULE_DP = 0, CTG_RULE_NCP = 1 };
 enum { CTG_BASIS_FP32 = 0, CTG_BASIS_BF16 = 1, CTG_BASIS_FP16 = 2 };  /* basis storage */
 /* Back projector B of a geometry.
  * CTG_BACK_PIXEL: the unmatched pixel-driven back projector (linear
@@ -94,6 +100,7 @@ typedef struct {
                                  Hessenberg problem) in every case         */
     double tau;               /* DP safety factor tau >= 1 (Sec. 6.4)       */
     double noise_norm;        /* ||e||; <= 0 disables the DP stop           */
+    int32_t stop_rule;        /* CTG_RULE_DP or CTG_RULE_NCP                */
 } ctg_opts;
 
 /* Solver report, filled on return (host memory). */
@@ -107,6 +114,11 @@ typedef struct {
                                  entries, or NULL: entry k = ||b - A x_k||
                                  as used by the DP test (AB: the Hessenberg
                                  residual, equal in exact arithmetic)      */
+    double *ncp_history;      /* optional caller host array, >= maxit + 2
+                                 entries, or NULL: with CTG_RULE_NCP, entry
+                                 k = the NCP distance d_k, for k = 0 .. the
+                                 last step evaluated (iters + 1 at an NCP
+                                 stop)                                      */
 } ctg_info;
 
 /* Where the solver keeps its state inside a caller workspace (byte offsets
@@ -144,6 +156,16 @@ int ctg_project(ctg_ctx *ctx, const ctg_geom *g, const float *x_dev,
  * (device, overwritten). */
 int ctg_backproject(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev,
                     float *x_dev, void *stream);
+
+/* The NCP distance of Sec. 6.4's NCP criterion for a residual sinogram r
+ * (m floats, device): the paper defines the criterion by citation; reading
+ * taken here: each projection (N_d bins of one angle) is a signal; with
+ * q = floor(N_d / 2) and rhat its DFT, p_i = |rhat_i|^2 (i = 1..q, the zero
+ * frequency left out), c_i = (p_1 + ... + p_i) / (p_1 + ... + p_q); the
+ * distance of a projection is ||c - (1..q)/q||_2 (0 when p = 0), and *out
+ * (host) is the mean over the projections.  Needs 2 <= n_det <= 8192;
+ * synchronises `stream`. */
+int ctg_ncp_distance(ctg_ctx *ctx, const ctg_geom *g, const float *r_dev, double *out, void *stream);
 
 /* Bytes of device workspace a solve of `variant` (CTG_AB, CTG_BA, CTG_LSQR or
  * CTG_LSMR) with these options needs; 0 if the arguments are invalid.  For

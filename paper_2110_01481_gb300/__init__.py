@@ -5,7 +5,7 @@ is used for device memory and streams only; every step of the projectors and
 of the Krylov solvers runs in the library's kernels.  See ``api`` for the
 calls: ``project``, ``backproject``, ``ab_gmres``, ``ba_gmres``, ``cgs2``.
 """
-__all__ = ["Geometry", "Context", "SolveResult", "Batch", "Engine", "project", "backproject",
+__all__ = ["Geometry", "Context", "SolveResult", "Batch", "Engine", "project", "backproject", "ncp_distance",
            "ab_gmres", "ba_gmres", "lsqr", "lsmr", "cgs2", "workspace_bytes", "workspace_layout"]
 
 

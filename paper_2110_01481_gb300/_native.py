@@ -24,6 +24,8 @@ VARIANTS = {"ab": CTG_AB, "ba": CTG_BA, "lsqr": CTG_LSQR, "lsmr": CTG_LSMR}
 CTG_STOP_MAXIT, CTG_STOP_DP, CTG_STOP_BREAKDOWN = 0, 1, 2
 CTG_BASIS_FP32, CTG_BASIS_BF16, CTG_BASIS_FP16 = 0, 1, 2
 BACK = {"pixel": 0, "matched": 1, "threshold": 2}
+RULES = {"dp": 0, "ncp": 1}
+CTG_STOP_NCP = 3
 BASIS = {"fp32": CTG_BASIS_FP32, "bf16": CTG_BASIS_BF16, "fp16": CTG_BASIS_FP16}
 
 
@@ -38,13 +40,15 @@ class CtgGeom(ctypes.Structure):
 
 class CtgOpts(ctypes.Structure):
     _fields_ = [("maxit", ctypes.c_int32), ("basis_dtype", ctypes.c_int32),
-                ("tau", ctypes.c_double), ("noise_norm", ctypes.c_double)]
+                ("tau", ctypes.c_double), ("noise_norm", ctypes.c_double),
+                ("stop_rule", ctypes.c_int32)]
 
 
 class CtgInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("stop_reason", ctypes.c_int32),
                 ("resnorm", ctypes.c_double), ("rho", ctypes.c_double),
-                ("history", ctypes.POINTER(ctypes.c_double))]
+                ("history", ctypes.POINTER(ctypes.c_double)),
+                ("ncp_history", ctypes.POINTER(ctypes.c_double))]
 
 
 class CtgTiming(ctypes.Structure):
@@ -60,7 +64,7 @@ class CtgLayout(ctypes.Structure):
                 ("off_h", ctypes.c_size_t), ("total_bytes", ctypes.c_size_t)]
 
 
-EXPORTS = ("ctg_create", "ctg_destroy", "ctg_project", "ctg_backproject",
+EXPORTS = ("ctg_create", "ctg_destroy", "ctg_project", "ctg_backproject", "ctg_ncp_distance",
            "ctg_workspace_bytes", "ctg_workspace_layout", "ctg_ab_gmres",
            "ctg_ba_gmres", "ctg_lsqr", "ctg_lsmr", "ctg_cgs2_scratch_bytes", "ctg_cgs2", "ctg_cgs2_noalloc",
            "ctg_set_timing", "ctg_get_timing", "ctg_status_string",
@@ -119,6 +123,8 @@ def _declare(lib):
     lib.ctg_engine_in_flight.restype = i32
     lib.ctg_engine_destroy.argtypes = [vp]
     lib.ctg_engine_destroy.restype = None
+    lib.ctg_ncp_distance.argtypes = [vp, G, vp, ctypes.POINTER(ctypes.c_double), vp]
+    lib.ctg_ncp_distance.restype = ctypes.c_int
     lib.ctg_status_string.argtypes = [ctypes.c_int]
     lib.ctg_status_string.restype = ctypes.c_char_p
     return lib

@@ -130,19 +130,23 @@ def backproject(g: Geometry, b: torch.Tensor, out: Optional[torch.Tensor] = None
 _TORCH_BASIS = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}
 
 
-def _opts(maxit: int, tau: float, noise_norm: Optional[float], basis: str = "fp32") -> nat.CtgOpts:
+def _opts(maxit: int, tau: float, noise_norm: Optional[float], basis: str = "fp32",
+          stop: str = "dp") -> nat.CtgOpts:
     if basis not in nat.BASIS:
         raise ValueError(f"basis must be one of {sorted(nat.BASIS)}")
+    if stop not in nat.RULES:
+        raise ValueError(f"stop must be one of {sorted(nat.RULES)}")
     return nat.CtgOpts(int(maxit), nat.BASIS[basis], float(tau),
-                       float(noise_norm) if noise_norm else 0.0)
+                       float(noise_norm) if noise_norm else 0.0, nat.RULES[stop])
 
 
-def workspace_bytes(g: Geometry, variant: str, maxit: int, basis: str = "fp32") -> int:
+def workspace_bytes(g: Geometry, variant: str, maxit: int, basis: str = "fp32",
+                    stop: str = "dp") -> int:
     """Device bytes one solve needs (0 if the arguments are invalid);
     variant: "ab", "ba", "lsqr" or "lsmr"."""
     v = nat.VARIANTS[variant]
     return int(nat.lib().ctg_workspace_bytes(ctypes.byref(g.c()), v,
-                                             ctypes.byref(_opts(maxit, 1.0, None, basis))))
+                                             ctypes.byref(_opts(maxit, 1.0, None, basis, stop))))
 
 
 def workspace_layout(g: Geometry, variant: str, maxit: int, basis: str = "fp32") -> nat.CtgLayout:
@@ -164,6 +168,7 @@ class SolveResult:
     history: list = field(default_factory=list)
     workspace: Optional[torch.Tensor] = None
     basis_type: str = "fp32"
+    ncp_history: list = field(default_factory=list)   # NCP distances d_0.. (stop="ncp")
 
     def basis(self, g: Geometry, variant: str, maxit: int) -> torch.Tensor:
         """View of the final Krylov basis W (iters+1 vectors, stored element
@@ -187,15 +192,15 @@ class SolveResult:
 def _solve(fn, variant: str, g: Geometry, b: torch.Tensor, maxit: int,
            x0: Optional[torch.Tensor], tau: float, noise_norm: Optional[float],
            out: Optional[torch.Tensor], workspace: Optional[torch.Tensor],
-           keep_workspace: bool, basis: str = "fp32") -> SolveResult:
+           keep_workspace: bool, basis: str = "fp32", stop: str = "dp") -> SolveResult:
     dev = b.device
     pb = _dev_ptr(b, g.m, "b")
     px0 = _dev_ptr(x0, g.n, "x0") if x0 is not None else None
     if out is None:
         out = torch.empty(g.n, device=dev, dtype=torch.float32)
     px = _dev_ptr(out, g.n, "out")
-    o = _opts(maxit, tau, noise_norm, basis)
-    need = workspace_bytes(g, variant, maxit, basis)
+    o = _opts(maxit, tau, noise_norm, basis, stop)
+    need = workspace_bytes(g, variant, maxit, basis, stop)
     name = f"ctg_{variant}" if variant in ("lsqr", "lsmr") else f"ctg_{variant}_gmres"
     if need == 0:
         raise nat.CtgError(nat.CTG_ERR_INVALID_ARG, name)
@@ -205,31 +210,46 @@ def _solve(fn, variant: str, g: Geometry, b: torch.Tensor, maxit: int,
     if workspace is not None:
         pws, nws = _dev_ptr(workspace, workspace.numel(), "workspace", torch.uint8), workspace.numel()
     hist = (ctypes.c_double * (maxit + 1))(*([math.nan] * (maxit + 1)))
-    info = nat.CtgInfo(0, 0, 0.0, 0.0, hist)
+    dncp = (ctypes.c_double * (maxit + 2))(*([math.nan] * (maxit + 2)))
+    info = nat.CtgInfo(0, 0, 0.0, 0.0, hist, dncp)
     ctx = Context.get(dev)
     with torch.cuda.device(dev):
         nat.check(fn(ctx.handle, ctypes.byref(g.c()), pb, px0, px, ctypes.byref(o), pws, nws,
                      ctypes.byref(info), _stream(dev)), name)
+    nd = info.iters + (2 if info.stop_reason == nat.CTG_STOP_NCP else 1) if stop == "ncp" else 0
     return SolveResult(out, info.iters, info.stop_reason, info.resnorm, info.rho,
-                       list(hist[: info.iters + 1]), workspace, basis)
+                       list(hist[: info.iters + 1]), workspace, basis, list(dncp[:nd]))
 
 
 def ab_gmres(g: Geometry, b: torch.Tensor, maxit: int, x0=None, tau: float = 1.0,
              noise_norm: Optional[float] = None, out=None, workspace=None,
-             keep_workspace: bool = False, basis: str = "fp32") -> SolveResult:
+             keep_workspace: bool = False, basis: str = "fp32", stop: str = "dp") -> SolveResult:
     """AB-GMRES (paper Sec. 2) with the discrepancy-principle stop when
-    noise_norm is given (Sec. 6.4).  basis: storage type of the Krylov basis
-    ("fp32", "bf16" or "fp16"; arithmetic stays FP32/FP64)."""
+    noise_norm is given (Sec. 6.4), or the NCP stop with stop="ncp".  basis:
+    storage type of the Krylov basis ("fp32", "bf16" or "fp16"; arithmetic
+    stays FP32/FP64)."""
     return _solve(nat.lib().ctg_ab_gmres, "ab", g, b, maxit, x0, tau, noise_norm, out,
-                  workspace, keep_workspace, basis)
+                  workspace, keep_workspace, basis, stop)
 
 
 def ba_gmres(g: Geometry, b: torch.Tensor, maxit: int, x0=None, tau: float = 1.0,
              noise_norm: Optional[float] = None, out=None, workspace=None,
-             keep_workspace: bool = False, basis: str = "fp32") -> SolveResult:
+             keep_workspace: bool = False, basis: str = "fp32", stop: str = "dp") -> SolveResult:
     """BA-GMRES (paper Sec. 2); same conventions as ``ab_gmres``."""
     return _solve(nat.lib().ctg_ba_gmres, "ba", g, b, maxit, x0, tau, noise_norm, out,
-                  workspace, keep_workspace, basis)
+                  workspace, keep_workspace, basis, stop)
+
+
+def ncp_distance(g: Geometry, r: torch.Tensor) -> float:
+    """The NCP distance (Sec. 6.4's NCP criterion) of a residual sinogram r:
+    the mean over the projections of the distance of the normalised
+    cumulative periodogram from the white-noise line."""
+    out = ctypes.c_double()
+    ctx = Context.get(r.device)
+    with torch.cuda.device(r.device):
+        nat.check(nat.lib().ctg_ncp_distance(ctx.handle, ctypes.byref(g.c()), _dev_ptr(r, g.m, "r"),
+                                             ctypes.byref(out), _stream(r.device)), "ctg_ncp_distance")
+    return out.value
 
 
 def lsqr(g: Geometry, b: torch.Tensor, maxit: int, x0=None, tau: float = 1.0,

@@ -47,6 +47,7 @@ bool opts_valid(const ctg_opts *o) {
     if (ctg_basis_bytes(o->basis_dtype) == 0) return false;
     if (!std::isfinite(o->tau) || !std::isfinite(o->noise_norm)) return false;
     if (o->noise_norm > 0.0 && !(o->tau > 0.0)) return false;
+    if (o->stop_rule != CTG_RULE_DP && o->stop_rule != CTG_RULE_NCP) return false;
     return true;
 }
 
@@ -146,6 +147,7 @@ struct GeomEntry {
     int back_window = 0;        // detector window of the tiled back projector
     PadLayout pl{};             // staged-image layout of the forward projector
     float2 *pad = nullptr;      // context-owned staged image for ctg_project
+    float2 *tw = nullptr;       // NCP: DFT twiddles of length n_det (on first use)
     MatchedAngle *mt = nullptr; // matched / thresholded back projector
     int rm = 0;
     float thr = 0.0f;           // B_tau threshold tau * max(A) (0: A^T)
@@ -167,6 +169,7 @@ struct WsLayout {
     size_t off_w, ld_w, off_h, off_pad, off_vn0, off_vm0, off_vm1, off_y, off_red, total;
     size_t off_t, ld_t, off_r0m;   // BA only: T = A W_k and b - A x0
     size_t off_n[4], off_m[5], off_state, off_hist;   // LSQR / LSMR only
+    size_t off_ncp;                // NCP distances of the projections (n_angles doubles)
     int64_t L, n, m;
     int kmax;
     int dtype;      // basis element type
@@ -176,7 +179,7 @@ struct WsLayout {
 // LSQR / LSMR: no basis; n-vectors v, w or h, hbar, B u; m-vectors u, p = A v
 // and (LSMR) A h, A hbar, r; the staged image, the device state and history.
 bool layout_lsq(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) {
-    if (o->basis_dtype != CTG_BASIS_FP32) return false;
+    if (o->basis_dtype != CTG_BASIS_FP32 || o->stop_rule != CTG_RULE_DP) return false;
     *ly = WsLayout{};
     const int64_t n = (int64_t)g->N * g->N, m = (int64_t)g->n_angles * g->n_det;
     ly->n = n;
@@ -214,6 +217,7 @@ bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) 
     if (!geom_valid(g) || !opts_valid(o)) return false;
     if (variant == CTG_LSQR || variant == CTG_LSMR) return layout_lsq(g, variant, o, ly);
     if (variant != CTG_AB && variant != CTG_BA) return false;
+    if (o->stop_rule == CTG_RULE_NCP && (g->n_det < 2 || g->n_det > kCtgNcpMaxDet)) return false;
     const int64_t n = (int64_t)g->N * g->N, m = (int64_t)g->n_angles * g->n_det;
     const int64_t L = variant == CTG_AB ? m : n;
     ly->n = n;
@@ -243,6 +247,8 @@ bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) 
     if (variant == CTG_BA) off = align256(off + sizeof(float) * ly->ld_t * (size_t)(o->maxit + 1));
     ly->off_r0m = off;
     if (variant == CTG_BA) off = align256(off + sizeof(float) * ly->ld_t);
+    ly->off_ncp = off;
+    off = align256(off + sizeof(double) * (size_t)g->n_angles);
     ly->off_red = off;
     const int64_t Lmax = n > m ? n : m;
     off = align256(off + ctg_red_scratch_bytes(Lmax, o->maxit + 1));
@@ -309,6 +315,7 @@ int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
         cudaFree(ctx->cache[victim].back);
         cudaFree(ctx->cache[victim].pad);
         cudaFree(ctx->cache[victim].mt);
+        cudaFree(ctx->cache[victim].tw);
         ctx->cache.erase(ctx->cache.begin() + victim);
     }
     std::vector<FwdAngle> fw;
@@ -353,6 +360,20 @@ int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
     }
     ctx->cache.push_back(e);
     *out = &ctx->cache.back();
+    return CTG_OK;
+}
+
+// (cos, -sin)(2 pi j / n_det), j < n_det, for the NCP periodograms
+int ensure_twiddles(GeomEntry *ge) {
+    if (ge->tw) return CTG_OK;
+    const int nd = ge->g.n_det;
+    std::vector<float2> t(nd);
+    for (int j = 0; j < nd; ++j) {
+        const double ph = 2.0 * M_PI * (double)j / (double)nd;
+        t[j] = make_float2((float)std::cos(ph), (float)-std::sin(ph));
+    }
+    CTG_CK(cudaMalloc(&ge->tw, sizeof(float2) * nd));
+    CTG_CK(cudaMemcpy(ge->tw, t.data(), sizeof(float2) * nd, cudaMemcpyHostToDevice));
     return CTG_OK;
 }
 
@@ -469,6 +490,13 @@ struct SolveCtx {
     double *ydev() const { return reinterpret_cast<double *>(ws + ly.off_y); }
     float *Tcol(int j) const { return reinterpret_cast<float *>(ws + ly.off_t) + (size_t)j * ly.ld_t; }
     float *r0m() const { return reinterpret_cast<float *>(ws + ly.off_r0m); }
+    double *ncpd() const { return reinterpret_cast<double *>(ws + ly.off_ncp); }
+    // *out (device) = the NCP distance of the residual sinogram r
+    cudaError_t ncp(const float *r, double *out) const {
+        return traced(ctx, 3, 2, st, [&] {
+            return ctg_ncp(r, g->n_angles, g->n_det, ge->tw, ncpd(), out, st);
+        });
+    }
 
     cudaError_t forward(const void *x, float *b, int xtype = CTG_BASIS_FP32) const {
         return traced(ctx, 0, 2, st, [&] {
@@ -636,7 +664,8 @@ int ensure_events(ctg_ctx *ctx);
 int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_opts *o,
            ctg_info *info) {
     const int64_t m = sc.ly.m;
-    const bool dp = o->noise_norm > 0.0;
+    const bool use_ncp = o->stop_rule == CTG_RULE_NCP;
+    const bool dp = !use_ncp && o->noise_norm > 0.0;
     const double target = dp ? o->tau * o->noise_norm : 0.0;
     // r0 = b - A x0 (FP32, in vm0); beta = ||r0||
     if (x0) {
@@ -656,9 +685,34 @@ int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
         info->stop_reason = beta == 0.0 && !(dp && beta <= target) ? CTG_STOP_BREAKDOWN : CTG_STOP_DP;
         return copy_x0(sc, x0, x);
     }
+    std::vector<double> dncp;        // NCP distances d_0, d_1, ...
+    if (use_ncp) {
+        if ((rc = ensure_twiddles(sc.ge))) return rc;
+        CTG_CK(sc.ncp(sc.vm0(), sc.rs.scal + 6));
+        if ((rc = sc.fetch(sc.rs.scal + 6, 1, &hp))) return rc;
+        dncp.push_back(hp[0]);
+    }
     CTG_CK(sc.scale(sc.vm0(), sc.rs.scal + 2, sc.Wcol(0), m));   // w_1 = r0 / beta
     if ((rc = ensure_events(sc.ctx))) return rc;
     Pipeline pl{sc, o->maxit, sc.ctx->ev_h, sc.ctx->ev_r};
+    // NCP: r_k = r0 - A B W_k y_k = W_{k+1} (beta e1 - H_k y_k), one read of
+    // W, then its NCP distance, read back through the ring slot
+    std::vector<double> Hh(use_ncp ? (size_t)(o->maxit + 1) * o->maxit : 0), yk(o->maxit);
+    auto enqueue_ncp = [&](int kk) -> int {
+        double *cf = pl.slot(kk) + o->maxit + 4;
+        for (int i = 0; i <= kk; ++i) {
+            double t = i == 0 ? beta : 0.0;
+            for (int j = std::max(0, i - 1); j < kk; ++j) t -= Hh[(size_t)j * (o->maxit + 1) + i] * yk[j];
+            cf[i] = t;
+        }
+        CTG_CK(cudaMemcpyAsync(sc.ydev(), cf, sizeof(double) * (kk + 1), cudaMemcpyHostToDevice, sc.st));
+        CTG_CK(sc.gemv(m, kk + 1, nullptr, sc.vm1()));
+        CTG_CK(sc.ncp(sc.vm1(), sc.rs.scal + 6));
+        CTG_CK(cudaMemcpyAsync(pl.slot(kk) + o->maxit + 3, sc.rs.scal + 6, sizeof(double),
+                               cudaMemcpyDeviceToHost, sc.st));
+        CTG_CK(cudaEventRecord(pl.ev_r[kk % kRing], sc.st));
+        return CTG_OK;
+    };
     auto enqueue = [&](int kk) -> int {
         CTG_CK(sc.back(sc.Wcol(kk - 1), nullptr, sc.vn0(), sc.ly.dtype));   // t = B w_k
         CTG_CK(sc.forward(sc.vn0(), sc.vm0()));                    // q = A t
@@ -687,9 +741,30 @@ int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
             info->stop_reason = CTG_STOP_DP;
             break;
         }
+        if (use_ncp) {
+            for (int i = 0; i <= k; ++i) Hh[(size_t)(k - 1) * (o->maxit + 1) + i] = h[i];
+            gv.solve(k, yk.data());
+            if ((rc = enqueue_ncp(k))) return rc;
+            // keep the GPU busy while d_k is read back
+            if (next == k + 2 && k + 2 <= o->maxit && (rc = enqueue(next++))) return rc;
+            CTG_CK(cudaEventSynchronize(pl.ev_r[k % kRing]));
+            dncp.push_back(pl.slot(k)[o->maxit + 3]);
+            if (dncp[k] > dncp[k - 1]) {          // first local minimum: x_{k-1}
+                info->stop_reason = CTG_STOP_NCP;
+                --k;
+                info->rho = rhos[k];
+                break;
+            }
+        }
     }
     if (k > o->maxit) k = o->maxit;
     info->iters = k;
+    if (info->ncp_history)
+        for (size_t i = 0; i < dncp.size(); ++i) info->ncp_history[i] = dncp[i];
+    if (k == 0) {
+        if ((rc = copy_x0(sc, x0, x))) return rc;
+        return sc.true_resnorm(b, x, &info->resnorm);
+    }
     // x_k = x0 + B (W_k y_k)
     std::vector<double> y(k);
     gv.solve(k, y.data());
@@ -705,7 +780,8 @@ int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
 int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_opts *o,
            ctg_info *info) {
     const int64_t n = sc.ly.n, m = sc.ly.m;
-    const bool dp = o->noise_norm > 0.0;
+    const bool use_ncp = o->stop_rule == CTG_RULE_NCP;
+    const bool dp = !use_ncp && o->noise_norm > 0.0;
     const double target = dp ? o->tau * o->noise_norm : 0.0;
     // r = b - A x0 (m-vector, kept for the DP residuals) and its norm;
     // r0 = B r into w_1's slot
@@ -727,6 +803,13 @@ int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
     if ((dp && res0 <= target) || beta == 0.0) {
         info->stop_reason = beta == 0.0 && !(dp && res0 <= target) ? CTG_STOP_BREAKDOWN : CTG_STOP_DP;
         return copy_x0(sc, x0, x);
+    }
+    std::vector<double> dncp;        // NCP distances d_0, d_1, ...
+    if (use_ncp) {
+        if ((rc = ensure_twiddles(sc.ge))) return rc;
+        CTG_CK(sc.ncp(sc.r0m(), sc.rs.scal + 6));
+        if ((rc = sc.fetch(sc.rs.scal + 6, 1, &hp))) return rc;
+        dncp.push_back(hp[0]);
     }
     CTG_CK(sc.scale(sc.vn0(), sc.rs.scal + 2, sc.Wcol(0), n));   // w_1 = r0 / beta
     if ((rc = ensure_events(sc.ctx))) return rc;
@@ -750,8 +833,23 @@ int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
         CTG_CK(cudaEventRecord(pl.ev_r[kk % kRing], sc.st));
         return CTG_OK;
     };
+    // NCP: r_k = (b - A x0) - T_k y_k, then its NCP distance
+    auto enqueue_ncp = [&](int kk, const double *yy) -> int {
+        double *ys = pl.slot(kk) + o->maxit + 4;
+        for (int i = 0; i < kk; ++i) ys[i] = -yy[i];
+        CTG_CK(cudaMemcpyAsync(sc.ydev(), ys, sizeof(double) * kk, cudaMemcpyHostToDevice, sc.st));
+        CTG_CK(traced(sc.ctx, 3, 1, sc.st, [&] {
+            return ctg_gemv(sc.Tcol(0), CTG_BASIS_FP32, sc.ly.ld_t, m, kk, sc.ydev(), sc.r0m(), sc.vm1(),
+                            sc.st);
+        }));
+        CTG_CK(sc.ncp(sc.vm1(), sc.rs.scal + 6));
+        CTG_CK(cudaMemcpyAsync(pl.slot(kk) + o->maxit + 3, sc.rs.scal + 6, sizeof(double),
+                               cudaMemcpyDeviceToHost, sc.st));
+        CTG_CK(cudaEventRecord(pl.ev_r[kk % kRing], sc.st));
+        return CTG_OK;
+    };
     Givens gv(o->maxit, beta);
-    std::vector<double> y(o->maxit), res{res0};
+    std::vector<double> y(o->maxit), res{res0}, rhos{beta};
     int next = 1, k = 0;
     for (k = 1; k <= o->maxit; ++k) {
         if (next == k && (rc = enqueue(next++))) return rc;
@@ -782,9 +880,29 @@ int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
             info->stop_reason = CTG_STOP_DP;
             break;
         }
+        rhos.push_back(rho);
+        if (use_ncp) {
+            gv.solve(k, y.data());
+            if ((rc = enqueue_ncp(k, y.data()))) return rc;
+            if (!last && next == k + 2 && k + 2 <= o->maxit && (rc = enqueue(next++))) return rc;
+            CTG_CK(cudaEventSynchronize(pl.ev_r[k % kRing]));
+            dncp.push_back(pl.slot(k)[o->maxit + 3]);
+            if (dncp[k] > dncp[k - 1]) {          // first local minimum: x_{k-1}
+                info->stop_reason = CTG_STOP_NCP;
+                --k;
+                info->rho = rhos[k];
+                break;
+            }
+        }
     }
     if (k > o->maxit) k = o->maxit;
     info->iters = k;
+    if (info->ncp_history)
+        for (size_t i = 0; i < dncp.size(); ++i) info->ncp_history[i] = dncp[i];
+    if (k == 0) {
+        if ((rc = copy_x0(sc, x0, x))) return rc;
+        return sc.true_resnorm(b, x, &info->resnorm);
+    }
     // x_k = x0 + W_k y_k and its residual, recomputed by a forward projection
     gv.solve(k, y.data());
     if ((rc = sc.upload_y(y.data(), k))) return rc;
@@ -962,6 +1080,7 @@ void ctg_destroy(ctg_ctx *ctx) {
         cudaFree(e.back);
         cudaFree(e.pad);
         cudaFree(e.mt);
+        cudaFree(e.tw);
     }
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     delete ctx;
@@ -994,6 +1113,24 @@ int ctg_backproject(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, float *
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CTG_CK(traced(ctx, 1, 1, st, [&] { return back_apply(ge, b_dev, CTG_BASIS_FP32, nullptr, x_dev, st); }));
     return CTG_OK;
+}
+
+int ctg_ncp_distance(ctg_ctx *ctx, const ctg_geom *g, const float *r_dev, double *out, void *stream) {
+    if (!ctx || !geom_valid(g) || !r_dev || !out || g->n_det < 2 || g->n_det > kCtgNcpMaxDet)
+        return CTG_ERR_INVALID_ARG;
+    GeomEntry *ge;
+    int rc = get_geom(ctx, g, &ge);
+    if (rc) return rc;
+    if ((rc = ensure_twiddles(ge))) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double *scratch = nullptr;
+    CTG_CK(cudaMallocAsync(&scratch, sizeof(double) * ((size_t)g->n_angles + 1), st));
+    cudaError_t e = ctg_ncp(r_dev, g->n_angles, g->n_det, ge->tw, scratch + 1, scratch, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, scratch, sizeof(double), cudaMemcpyDeviceToHost, st);
+    const cudaError_t e2 = cudaFreeAsync(scratch, st);
+    const cudaError_t e3 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+    return e == cudaSuccess ? CTG_OK : fail_cuda(e);
 }
 
 size_t ctg_workspace_bytes(const ctg_geom *g, int variant, const ctg_opts *o) {

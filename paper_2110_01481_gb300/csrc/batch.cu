@@ -223,7 +223,7 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
         p.o = opts[i];
         p.variant = variants[i];
         if (!ctg_geom_valid(&p.g) || p.g.back_model != CTG_BACK_PIXEL || !ctg_opts_valid(&p.o) ||
-            p.o.basis_dtype != CTG_BASIS_FP32 ||
+            p.o.basis_dtype != CTG_BASIS_FP32 || p.o.stop_rule != CTG_RULE_DP ||
             p.o.maxit > 1024 || (p.variant != CTG_AB && p.variant != CTG_BA)) {
             release(b);
             return CTG_ERR_INVALID_ARG;
@@ -510,7 +510,7 @@ void release_engine(ctg_engine *e) {
 
 bool plan_valid(const ctg_geom *g, int variant, const ctg_opts *o) {
     if (!ctg_geom_valid(g) || g->back_model != CTG_BACK_PIXEL || !ctg_opts_valid(o) ||
-        o->basis_dtype != CTG_BASIS_FP32 ||
+        o->basis_dtype != CTG_BASIS_FP32 || o->stop_rule != CTG_RULE_DP ||
         o->maxit > 1024 || (variant != CTG_AB && variant != CTG_BA))
         return false;
     std::vector<FwdAngle> fw;

@@ -99,6 +99,14 @@ cudaError_t ctg_launch_back_matched(const void *b, int dtype, int N, int n_angle
 cudaError_t ctg_matched_max(int N, int n_angles, int n_det, const BackAngle *tab,
                             const MatchedAngle *mt, int rm, unsigned *max_bits, cudaStream_t st);
 
+// ---- NCP stopping criterion (ncp.cu) --------------------------------------
+constexpr int kCtgNcpMaxDet = 8192;
+// *out (device double) = mean over the n_angles projections of the NCP
+// distance of the residual sinogram r (n_angles x n_det); tw[j] =
+// (cos, -sin)(2 pi j / n_det); dist_scratch: n_angles doubles.
+cudaError_t ctg_ncp(const float *r, int n_angles, int n_det, const float2 *tw, double *dist_scratch,
+                    double *out, cudaStream_t st);
+
 // ---- Krylov kernels (arnoldi.cu) -----------------------------------------
 // Reduction scratch for one vector length L and up to kmax coefficients.
 struct RedScratch {

@@ -72,6 +72,13 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert ws(_g(64, 90, 91, model=1, tau=0.3), 0, _o(10)) == 0   # tau only with B_tau
     assert ws(_g(64, 90, 91, model=2, tau=0.3), 0, _o(10)) > 0
     assert ws(_g(64, 90, 91, model=1), 1, _o(10)) > 0
+    o = _o(10)
+    o.stop_rule = 2                                       # unknown stopping rule
+    assert ws(_g(64, 90, 91), 0, o) == 0
+    o.stop_rule = 1                                       # NCP: needs 2 <= n_det <= 8192
+    assert ws(_g(64, 90, 91), 0, o) > 0 and ws(_g(64, 90, 91), 1, o) > 0
+    assert ws(_g(64, 90, 9000, ds=0.5), 0, o) == 0
+    assert ws(_g(64, 90, 91), 2, o) == 0                 # LSQR / LSMR: DP rule only
     # solvers and projectors refuse null pointers before touching the GPU
     assert lib.ctg_project(None, ctypes.byref(_g(64, 90, 91)), None, None, None) == -1
     assert lib.ctg_ab_gmres(None, ctypes.byref(_g(64, 90, 91)), None, None, None,
