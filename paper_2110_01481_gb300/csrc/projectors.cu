@@ -84,6 +84,8 @@ __device__ __forceinline__ float one_plus_frac(unsigned lo) {
 }
 
 constexpr int kFwdAngles = 8;   // warps per block, one angle each
+constexpr int kFwdDepth = 8;    // image loads in flight per lane (a multiple of 4; 8 measured
+                                // 10% faster than 4 at 512^2, 16 no faster than 8)
 
 // b[a * n_det + d] = scale_a * sum_t lerp(img_a[t, .], u(d, t)).
 // A warp holds 32 adjacent rays of one angle and walks the union of their
@@ -125,33 +127,41 @@ __device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ 
     if (!kClamp) {
         const long long Ds = t.D + ((long long)stride << CTG_FXF_BITS);
         long long U = t.Q + (long long)d * t.P + (long long)wlo * Ds;
-        float acc2 = 0.0f, acc3 = 0.0f;
+        // step s adds into acc[(s - wlo) % 4] whatever the load depth, so the
+        // result does not depend on kFwdDepth
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         int s = wlo;
+        for (; s + kFwdDepth - 1 <= whi; s += kFwdDepth) {
+            float2 p[kFwdDepth];
+            float mw[kFwdDepth];
+#pragma unroll
+            for (int i = 0; i < kFwdDepth; ++i) {
+                p[i] = __ldg(img + (int)(U >> CTG_FXF_BITS));
+                mw[i] = one_plus_frac((unsigned)U);
+                U += Ds;
+            }
+#pragma unroll
+            for (int i = 0; i < kFwdDepth; ++i) acc[i & 3] = fmaf(mw[i], p[i].y, acc[i & 3] + p[i].x);
+        }
         for (; s + 3 <= whi; s += 4) {
-            const float2 pa = __ldg(img + (int)(U >> CTG_FXF_BITS));
-            const float ma = one_plus_frac((unsigned)U);
-            U += Ds;
-            const float2 pb = __ldg(img + (int)(U >> CTG_FXF_BITS));
-            const float mb = one_plus_frac((unsigned)U);
-            U += Ds;
-            const float2 pc = __ldg(img + (int)(U >> CTG_FXF_BITS));
-            const float mc = one_plus_frac((unsigned)U);
-            U += Ds;
-            const float2 pd = __ldg(img + (int)(U >> CTG_FXF_BITS));
-            const float md = one_plus_frac((unsigned)U);
-            U += Ds;
-            acc0 = fmaf(ma, pa.y, acc0 + pa.x);
-            acc1 = fmaf(mb, pb.y, acc1 + pb.x);
-            acc2 = fmaf(mc, pc.y, acc2 + pc.x);
-            acc3 = fmaf(md, pd.y, acc3 + pd.x);
+            float2 p[4];
+            float mw[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                p[i] = __ldg(img + (int)(U >> CTG_FXF_BITS));
+                mw[i] = one_plus_frac((unsigned)U);
+                U += Ds;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = fmaf(mw[i], p[i].y, acc[i] + p[i].x);
         }
         for (; s <= whi; ++s) {
             const float2 pa = __ldg(img + (int)(U >> CTG_FXF_BITS));
-            acc0 = fmaf(one_plus_frac((unsigned)U), pa.y, acc0 + pa.x);
+            acc[0] = fmaf(one_plus_frac((unsigned)U), pa.y, acc[0] + pa.x);
             U += Ds;
         }
-        acc0 += acc2;
-        acc1 += acc3;
+        acc0 = acc[0] + acc[2];
+        acc1 = acc[1] + acc[3];
     } else {
         long long U = t.Q + (long long)d * t.P + (long long)wlo * t.D;
         for (int s = wlo; s <= whi; ++s) {
