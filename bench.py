@@ -491,6 +491,68 @@ def run_serve(args):
         print(json.dumps(row), flush=True)
 
 
+def run_methods(args):
+    """The adjacent method parts on the benchmark workload (512^2, 720 angles,
+    725 bins, 1% noise): AB-/BA-GMRES with the unmatched pixel-driven B,
+    with B = A^T and with the thresholded B_tau (Sec. 6.5), LSQR and LSMR
+    (Sec. 5), the NCP stop (Sec. 6.4); iterations, time and error at the
+    stop, and the back projectors' launch times."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2110_01481_gb300 as P
+    dev = torch.device("cuda", 0)
+    g, xbar, b, enorm = make_instance(P, torch, dev, 2000)
+    xt = torch.tensor(xbar.ravel(), dtype=torch.float64, device=dev)
+
+    def run(label, fn, geom, **kw):
+        fn(geom, b, MAXIT, **kw)                        # warm-up (tables, twiddles)
+        torch.cuda.synchronize()
+        ts, r = [], None
+        for _ in range(max(1, args.steps)):
+            t0 = time.perf_counter()
+            r = fn(geom, b, MAXIT, **kw)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        t = statistics.median(ts)
+        err = ((r.x.double() - xt).norm() / xt.norm()).item()
+        row = {"method": label, "iters": r.iters, "stop": r.stop_reason, "ms": t * 1e3,
+               "iterations_per_s": r.iters / t if r.iters else None, "rel_error_vs_truth": err,
+               "resnorm_over_noise": r.resnorm / enorm}
+        print(json.dumps(row), flush=True)
+
+    dpkw = dict(tau=TAU, noise_norm=enorm)
+    t_end = time.perf_counter() + 1.0                   # clocks up before the first timing
+    while time.perf_counter() < t_end:
+        P.ab_gmres(g, b, MAXIT, **dpkw)
+    torch.cuda.synchronize()
+    for model, tau_b in (("pixel", 0.0), ("matched", 0.0), ("threshold", 0.01), ("threshold", 0.1),
+                         ("threshold", 0.3), ("threshold", 0.5)):
+        gm = P.Geometry(N, N_ANG, N_DET, back_model=model, back_tau=tau_b)
+        tag = model if model != "threshold" else f"B_tau {tau_b}"
+        run(f"AB-GMRES, {tag}, DP", P.ab_gmres, gm, **dpkw)
+        run(f"BA-GMRES, {tag}, DP", P.ba_gmres, gm, **dpkw)
+    gA = P.Geometry(N, N_ANG, N_DET, back_model="matched")
+    run("LSQR (A^T), DP", P.lsqr, gA, **dpkw)
+    run("LSMR (A^T), DP", P.lsmr, gA, **dpkw)
+    run("AB-GMRES, pixel, NCP", P.ab_gmres, g, stop="ncp")
+    run("BA-GMRES, pixel, NCP", P.ba_gmres, g, stop="ncp")
+    # back projector launch times (CUDA events, 20 launches each)
+    y = torch.randn(g.m, device=dev)
+    for model, tau_b in (("pixel", 0.0), ("matched", 0.0), ("threshold", 0.3)):
+        gm = P.Geometry(N, N_ANG, N_DET, back_model=model, back_tau=tau_b)
+        out = P.backproject(gm, y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            P.backproject(gm, y, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / 20 * 1e3
+        print(json.dumps({"back_projector": model, "back_tau": tau_b, "us_per_launch": us,
+                          "interpolations_per_s": g.n * N_ANG / (us * 1e-6)}), flush=True)
+
+
 def make_instance(P, torch, dev, seed):
     """Seeded phantom, b = A x_bar + e with the library's own A (the oracle is
     not used on the product path)."""
@@ -761,6 +823,8 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="batched engine vs one-at-a-time solves on 64 mixed instances")
     ap.add_argument("--batch-size", type=int, default=64)
+    ap.add_argument("--methods", action="store_true",
+                    help="B = A^T, B_tau, LSQR/LSMR and the NCP stop on the benchmark workload")
     ap.add_argument("--serve", action="store_true",
                     help="Poisson-arrival serving: continuous batching vs one-at-a-time")
     ap.add_argument("--serve-requests", type=int, default=500)
@@ -778,6 +842,8 @@ def main():
         run_batch(args)
     elif args.serve:
         run_serve(args)
+    elif args.methods:
+        run_methods(args)
     else:
         run_gpu(args)
 

@@ -116,7 +116,8 @@ def project(g: Geometry, x: torch.Tensor, out: Optional[torch.Tensor] = None) ->
 
 
 def backproject(g: Geometry, b: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """x = B b (pixel-driven unmatched back projection); b: m floats."""
+    """x = B b with the geometry's back projector (by default the unmatched
+    pixel-driven B; A^T or B_tau by back_model); b: m floats."""
     if out is None:
         out = torch.empty(g.n, device=b.device, dtype=torch.float32)
     pb, px = _dev_ptr(b, g.m, "b"), _dev_ptr(out, g.n, "out")

@@ -161,6 +161,9 @@ cudaError_t back_apply(const GeomEntry *ge, const void *b, int btype, const floa
     if (g->back_model == CTG_BACK_PIXEL)
         return ctg_launch_back(b, btype, g->N, g->n_angles, g->n_det, ge->back, ge->back_window, add,
                                x, st);
+    if (ge->rm == 0 && ge->back_window <= ctg_back_window_max())
+        return ctg_launch_back_matched_tiled(b, btype, g->N, g->n_angles, g->n_det, ge->back,
+                                             ge->back_window, ge->mt, ge->thr, add, x, st);
     return ctg_launch_back_matched(b, btype, g->N, g->n_angles, g->n_det, ge->back, ge->mt, ge->rm,
                                    ge->thr, add, x, st);
 }

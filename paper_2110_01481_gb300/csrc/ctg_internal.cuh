@@ -95,6 +95,11 @@ cudaError_t ctg_launch_back(const void *b, int dtype, int N, int n_angles, int n
 cudaError_t ctg_launch_back_matched(const void *b, int dtype, int N, int n_angles, int n_det,
                                     const BackAngle *tab, const MatchedAngle *mt, int rm, float thr,
                                     const float *add, float *x, cudaStream_t st);
+// The same with the tiled design of the pixel-driven B (projectors.cu), for
+// rm = 0 and window <= ctg_back_window_max().
+cudaError_t ctg_launch_back_matched_tiled(const void *b, int dtype, int N, int n_angles, int n_det,
+                                          const BackAngle *tab, int window, const MatchedAngle *mt,
+                                          float thr, const float *add, float *x, cudaStream_t st);
 // *max_bits = bit pattern of max_ij A_ij (a float >= 0), on the device.
 cudaError_t ctg_matched_max(int N, int n_angles, int n_det, const BackAngle *tab,
                             const MatchedAngle *mt, int rm, unsigned *max_bits, cudaStream_t st);

@@ -8,8 +8,9 @@
 // residual's distance is the mean over the projections.
 //
 // One block per projection.  The q periodogram ordinates are a direct DFT
-// against a twiddle table (q * N_d multiply-adds per projection, with the
-// projection staged in shared memory); the cumulative sums are a chunked
+// (q * N_d complex multiply-adds per projection, with the projection staged
+// in shared memory, the twiddles advanced by a re-anchored rotating phasor);
+// the cumulative sums are a chunked
 // scan in FP64 in a fixed order, and the mean over projections is a
 // fixed-order reduction, so the result is deterministic.
 #include "ctg_internal.cuh"
@@ -31,15 +32,27 @@ ncp_projection_kernel(const float *__restrict__ r, int n_det, const float2 *__re
     const float *ra = r + (size_t)a * n_det;
     for (int d = tid; d < n_det; d += kNcpThreads) rs[d] = ra[d];
     __syncthreads();
+    // rhat_i = sum_d r_d z^d with z = exp(-2 pi i i / n_det): the phasor z^d
+    // is advanced by complex multiplication and re-anchored from the exact
+    // table every kAnchor bins, so its rounding drift stays ~kAnchor eps;
+    // all lanes read the same r_d (a shared-memory broadcast)
+    constexpr int kAnchor = 32;
     for (int i = tid + 1; i <= q; i += kNcpThreads) {
+        const float2 w = tw[i];
         float re = 0.f, im = 0.f;
-        int idx = 0;                // (i * d) mod n_det
-        for (int d = 0; d < n_det; ++d) {
-            const float2 t = tw[idx];
-            re = fmaf(rs[d], t.x, re);
-            im = fmaf(rs[d], t.y, im);
-            idx += i;
-            if (idx >= n_det) idx -= n_det;
+        int anchor = 0;                       // (i * d0) mod n_det
+        for (int d0 = 0; d0 < n_det; d0 += kAnchor) {
+            float2 z = tw[anchor];
+            const int d1 = min(n_det, d0 + kAnchor);
+            for (int d = d0; d < d1; ++d) {
+                const float v = rs[d];
+                re = fmaf(v, z.x, re);
+                im = fmaf(v, z.y, im);
+                const float zx = fmaf(z.x, w.x, -z.y * w.y);
+                z.y = fmaf(z.x, w.y, z.y * w.x);
+                z.x = zx;
+            }
+            anchor = (int)(((long long)i * d1) % n_det);
         }
         ps[i - 1] = fmaf(re, re, im * im);
     }

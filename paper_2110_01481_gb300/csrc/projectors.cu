@@ -203,13 +203,22 @@ constexpr int kBSplit = 4;       // CTAs per cluster = angle groups per tile
 
 // Body of one CTA of the back-projection cluster for tile (bx, by).  Every
 // CTA of a cluster must call it (it synchronises the cluster twice).
-template <typename T>
+// kModel: 0 the pixel-driven B (linear interpolation on the detector);
+// 1 the matched A^T and 2 the thresholded B_tau, whose weights for the two
+// nearest bins d0, d0 + 1 of a pixel at detector position d0 + f are
+// scale * max(0, 1 - f inv_w) and scale * max(0, 1 - (1 - f) inv_w) (terms
+// below thr dropped for 2).  The staged pairs are (b[d], b[d+1] - b[d]) for
+// the pixel-driven B and (b[d], b[d+1]) for the others.
+template <typename T, int kModel = 0>
 __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, int n_angles,
                                                 int n_det, const BackAngle *__restrict__ tab,
                                                 int W, const float *__restrict__ add,
-                                                float *__restrict__ x, int bx, int by) {
+                                                float *__restrict__ x, int bx, int by,
+                                                const MatchedAngle *__restrict__ mt = nullptr,
+                                                float thr = 0.0f) {
     extern __shared__ float2 s_pairs[];               // kBChunk * W pairs
     __shared__ float4 s_par[kBChunk];                 // cf, sf, u0' (window-relative), origin
+    __shared__ float4 s_wt[kModel ? kBChunk : 1];     // scale, scale inv_w, scale - scale inv_w
     __shared__ float s_part[kBRows][kBThreads];       // this CTA's partial sums
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();       // == blockIdx.z
@@ -233,6 +242,11 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
             const int org = dbase + (int)floorf(umin) - 1;
             s_par[threadIdx.x] = make_float4(t.cf, t.sf, (float)(dbase - org) + phi,
                                              __int_as_float(org));
+            if constexpr (kModel != 0) {
+                const MatchedAngle m = mt[a0 + threadIdx.x];
+                const float sw = m.scale * m.inv_w;
+                s_wt[threadIdx.x] = make_float4(m.scale, sw, m.scale - sw, 0.0f);
+            }
         }
         __syncthreads();
         for (int e = threadIdx.x; e < na * W; e += kBThreads) {
@@ -241,7 +255,7 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
             const T *brow = b + (size_t)(a0 + k) * n_det;
             const float v0 = ((unsigned)dd < (unsigned)n_det) ? to_f(__ldg(brow + dd)) : 0.0f;
             const float v1 = ((unsigned)(dd + 1) < (unsigned)n_det) ? to_f(__ldg(brow + dd + 1)) : 0.0f;
-            s_pairs[e] = make_float2(v0, v1 - v0);
+            s_pairs[e] = kModel == 0 ? make_float2(v0, v1 - v0) : make_float2(v0, v1);
         }
         __syncthreads();
         const float2 *pw = s_pairs;
@@ -250,6 +264,8 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
             const float4 p = s_par[k];
             float u = fmaf(fdi, p.y, fmaf(fdj, p.x, p.z));
             const float du = 8.0f * p.y;
+            float4 wt = make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (kModel != 0) wt = s_wt[k];
 #pragma unroll
             for (int r = 0; r < kBRows; ++r) {
                 // floor(u) by the round-down magic-number add (0 <= u < 2^22)
@@ -257,7 +273,17 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
                 const int idx = __float_as_int(tt) - 0x4B400000;
                 const float f = u - (tt - kMagic);
                 const float2 pr = pw[idx];
-                acc[r] += fmaf(f, pr.y, pr.x);
+                if constexpr (kModel == 0) {
+                    acc[r] += fmaf(f, pr.y, pr.x);
+                } else {
+                    float w0 = fmaxf(0.0f, fmaf(-f, wt.y, wt.x));
+                    float w1 = fmaxf(0.0f, fmaf(f, wt.y, wt.z));
+                    if constexpr (kModel == 2) {
+                        w0 = w0 >= thr ? w0 : 0.0f;
+                        w1 = w1 >= thr ? w1 : 0.0f;
+                    }
+                    acc[r] = fmaf(w0, pr.x, fmaf(w1, pr.y, acc[r]));
+                }
                 u += du;
             }
         }
@@ -284,6 +310,15 @@ pixel_back_tiled_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
                         const BackAngle *__restrict__ tab, int W, const float *__restrict__ add,
                         float *__restrict__ x) {
     pixel_back_tile(b, N, n_angles, n_det, tab, W, add, x, blockIdx.x, blockIdx.y);
+}
+
+// A^T (kModel 1) or B_tau (kModel 2) with the tiled design above.
+template <typename T, int kModel>
+__global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
+matched_back_tiled_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
+                          const BackAngle *__restrict__ tab, int W, const MatchedAngle *__restrict__ mt,
+                          float thr, const float *__restrict__ add, float *__restrict__ x) {
+    pixel_back_tile<T, kModel>(b, N, n_angles, n_det, tab, W, add, x, blockIdx.x, blockIdx.y, mt, thr);
 }
 
 // Generic pixel-driven back projection (any detector pitch): 32 x 8 tiles,
@@ -470,7 +505,40 @@ cudaError_t launch_back_t(const T *b, int N, int n_angles, int n_det, const Back
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_matched_tiled_t(const T *b, int N, int n_angles, int n_det, const BackAngle *tab,
+                                   int window, const MatchedAngle *mt, float thr, const float *add,
+                                   float *x, cudaStream_t st) {
+    const size_t smem = sizeof(float2) * (size_t)kBChunk * window;
+    const dim3 grid((N + kBT - 1) / kBT, (N + kBT - 1) / kBT, kBSplit);
+    if (thr > 0.0f)
+        matched_back_tiled_kernel<T, 2><<<grid, kBThreads, smem, st>>>(b, N, n_angles, n_det, tab, window,
+                                                                       mt, thr, add, x);
+    else
+        matched_back_tiled_kernel<T, 1><<<grid, kBThreads, smem, st>>>(b, N, n_angles, n_det, tab, window,
+                                                                       mt, thr, add, x);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t ctg_launch_back_matched_tiled(const void *b, int dtype, int N, int n_angles, int n_det,
+                                          const BackAngle *tab, int window, const MatchedAngle *mt,
+                                          float thr, const float *add, float *x, cudaStream_t st) {
+    if (window <= 0 || window > ctg_back_window_max()) return cudaErrorInvalidValue;
+    switch (dtype) {
+        case CTG_BASIS_FP32:
+            return launch_matched_tiled_t(static_cast<const float *>(b), N, n_angles, n_det, tab, window, mt,
+                                          thr, add, x, st);
+        case CTG_BASIS_BF16:
+            return launch_matched_tiled_t(static_cast<const __nv_bfloat16 *>(b), N, n_angles, n_det, tab,
+                                          window, mt, thr, add, x, st);
+        case CTG_BASIS_FP16:
+            return launch_matched_tiled_t(static_cast<const __half *>(b), N, n_angles, n_det, tab, window,
+                                          mt, thr, add, x, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t ctg_launch_back(const void *b, int dtype, int N, int n_angles, int n_det,
                             const BackAngle *tab, int window, const float *add, float *x,
