@@ -512,9 +512,12 @@ struct SolveCtx {
         return traced(ctx, 1, 1, st, [&] { return back_apply(ge, b, btype, add, x, st); });
     }
     cudaError_t cgs2(int64_t L, int k, float *q) const {
-        return traced(ctx, 2, k > 0 ? 4 : 2, st, [&] {
-            return ctg_cgs2_step(W(), ly.dtype, ly.ld_w, L, k, q, Wcol(k), Hcol(k), rs, st);
+        int nk = 0;
+        const cudaError_t e = traced(ctx, 2, 0, st, [&] {
+            return ctg_cgs2_step(W(), ly.dtype, ly.ld_w, L, k, q, Wcol(k), Hcol(k), rs, st, &nk);
         });
+        ctx->kernels += nk;
+        return e;
     }
     cudaError_t gemv(int64_t L, int k, const float *base, float *out) const {
         return traced(ctx, 3, 1, st, [&] {

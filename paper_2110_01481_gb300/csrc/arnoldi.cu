@@ -11,6 +11,8 @@
 // into per-block partials, and the last block to finish (atomic ticket, no
 // waiting) sums the partials in a fixed order in FP64, so results are
 // deterministic run to run.
+#include <cooperative_groups.h>
+
 #include "vecops.cuh"
 
 namespace {
@@ -51,6 +53,73 @@ __device__ __forceinline__ void accumulate_batched(const T *__restrict__ V, int6
     }
 }
 
+// qv -= sum_j c_j W_j over this thread's slice.  Loads are issued in batches
+// of JB vectors before any of them is used, so each thread keeps 128 bytes of
+// HBM reads outstanding (8 float4 of an FP32 basis, 16 half-width groups of a
+// 16-bit one).  Past the last vector the load repeats vector k-1 (a cache
+// hit) and its coefficient / dot is dropped, so every load of the batch is
+// unconditional and issued before any use.
+template <typename T, int E>
+__device__ __forceinline__ void update_slice(const T *__restrict__ W, int64_t ldw, int k,
+                                             const float *s_coef, int64_t g0, int64_t L,
+                                             float4 (&qv)[E]) {
+    constexpr int JB = batch_vectors<T, E>();
+    for (int j0 = 0; j0 < k; j0 += JB) {
+        typename RawOf<T>::type w[JB][E];
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+            const T *Wj = W + (size_t)min(j0 + jj, k - 1) * ldw;
+#pragma unroll
+            for (int e = 0; e < E; ++e) w[jj][e] = ldraw(Wj, g0 + (int64_t)e * kThreads, L);
+        }
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+            const float c = (j0 + jj < k) ? s_coef[j0 + jj] : 0.f;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const float4 wf = cvt4<T>(w[jj][e]);
+                qv[e].x = fmaf(-c, wf.x, qv[e].x);
+                qv[e].y = fmaf(-c, wf.y, qv[e].y);
+                qv[e].z = fmaf(-c, wf.z, qv[e].z);
+                qv[e].w = fmaf(-c, wf.w, qv[e].w);
+            }
+        }
+    }
+}
+
+// Warp sums of W_j^T qv (j < k) into s_w[warp * nred + j] and, with NORM,
+// of qv^T qv into s_w[warp * nred + k]; same load batching as update_slice.
+template <typename T, int E, bool NORM>
+__device__ __forceinline__ void dots_slice(const T *__restrict__ W, int64_t ldw, int k, int64_t g0,
+                                           int64_t L, const float4 (&qv)[E], float *s_w, int nred) {
+    constexpr int JB = batch_vectors<T, E>();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j0 = 0; j0 < k; j0 += JB) {
+        typename RawOf<T>::type w[JB][E];
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+            const T *Wj = W + (size_t)min(j0 + jj, k - 1) * ldw;
+#pragma unroll
+            for (int e = 0; e < E; ++e) w[jj][e] = ldraw(Wj, g0 + (int64_t)e * kThreads, L);
+        }
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+            float sj = 0.f;
+#pragma unroll
+            for (int e = 0; e < E; ++e) sj += dot4(cvt4<T>(w[jj][e]), qv[e]);
+            sj = warp_sum(sj);
+            if (lane == 0 && j0 + jj < k) s_w[warp * nred + j0 + jj] = sj;
+        }
+    }
+    if (NORM) {
+        float s = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) s += dot4(qv[e], qv[e]);
+        s = warp_sum(s);
+        if (lane == 0) s_w[warp * nred + k] = s;
+    }
+}
+
 // One CGS2 pass over a slice of E float4 groups per thread.
 //   UPDATE: q -= sum_j coef_j W_j (coef: k doubles)
 //   DOTS:   red_out[j] = W_j^T q (after the update)      j < k
@@ -63,7 +132,7 @@ __device__ __forceinline__ void cgs_pass_body(const T *__restrict__ W, int64_t l
                                               unsigned *__restrict__ counter,
                                               double *__restrict__ red_out, int blk, int G) {
     extern __shared__ float smem[];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int nred = (DOTS ? k : 0) + (NORM ? 1 : 0);
     float *s_coef = smem;                       // k floats (UPDATE)
     float *s_w = smem + (UPDATE ? k : 0);       // kWarps * nred floats
@@ -73,64 +142,20 @@ __device__ __forceinline__ void cgs_pass_body(const T *__restrict__ W, int64_t l
     float4 qv[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) qv[e] = ld4_rw(q, g0 + (int64_t)e * kThreads, L);
-    // Loads are issued in batches of JB vectors before any of them is used,
-    // so each thread keeps 128 bytes of HBM reads outstanding (8 float4 of
-    // an FP32 basis, 16 half-width groups of a 16-bit one).
-    constexpr int JB = batch_vectors<T, E>();
     if (UPDATE) {
         __syncthreads();
-        for (int j0 = 0; j0 < k; j0 += JB) {
-            typename RawOf<T>::type w[JB][E];
-#pragma unroll
-            for (int jj = 0; jj < JB; ++jj) {
-                // past the last vector the load repeats vector k-1 (a cache
-                // hit) and its coefficient / dot is dropped, so every load of
-                // the batch is unconditional and issued before any use
-                const T *Wj = W + (size_t)min(j0 + jj, k - 1) * ldw;
-#pragma unroll
-                for (int e = 0; e < E; ++e) w[jj][e] = ldraw(Wj, g0 + (int64_t)e * kThreads, L);
-            }
-#pragma unroll
-            for (int jj = 0; jj < JB; ++jj) {
-                const float c = (j0 + jj < k) ? s_coef[j0 + jj] : 0.f;
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const float4 wf = cvt4<T>(w[jj][e]);
-                    qv[e].x = fmaf(-c, wf.x, qv[e].x);
-                    qv[e].y = fmaf(-c, wf.y, qv[e].y);
-                    qv[e].z = fmaf(-c, wf.z, qv[e].z);
-                    qv[e].w = fmaf(-c, wf.w, qv[e].w);
-                }
-            }
-        }
+        update_slice<T, E>(W, ldw, k, s_coef, g0, L, qv);
 #pragma unroll
         for (int e = 0; e < E; ++e) st4(q, g0 + (int64_t)e * kThreads, L, qv[e]);
     }
     if (DOTS) {
-        for (int j0 = 0; j0 < k; j0 += JB) {
-            typename RawOf<T>::type w[JB][E];
-#pragma unroll
-            for (int jj = 0; jj < JB; ++jj) {
-                const T *Wj = W + (size_t)min(j0 + jj, k - 1) * ldw;
-#pragma unroll
-                for (int e = 0; e < E; ++e) w[jj][e] = ldraw(Wj, g0 + (int64_t)e * kThreads, L);
-            }
-#pragma unroll
-            for (int jj = 0; jj < JB; ++jj) {
-                float sj = 0.f;
-#pragma unroll
-                for (int e = 0; e < E; ++e) sj += dot4(cvt4<T>(w[jj][e]), qv[e]);
-                sj = warp_sum(sj);
-                if (lane == 0 && j0 + jj < k) s_w[warp * nred + j0 + jj] = sj;
-            }
-        }
-    }
-    if (NORM) {
+        dots_slice<T, E, NORM>(W, ldw, k, g0, L, qv, s_w, nred);
+    } else if (NORM) {
         float s = 0.f;
 #pragma unroll
         for (int e = 0; e < E; ++e) s += dot4(qv[e], qv[e]);
         s = warp_sum(s);
-        if (lane == 0) s_w[warp * nred + (DOTS ? k : 0)] = s;
+        if ((tid & 31) == 0) s_w[(tid >> 5) * nred] = s;
     }
     block_reduce_finish(s_w, nred, partials, counter, red_out, blk, G);
 }
@@ -142,6 +167,116 @@ cgs_pass_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict__
                 unsigned *__restrict__ counter, double *__restrict__ red_out) {
     cgs_pass_body<T, E, UPDATE, DOTS, NORM>(W, ldw, k, q, L, coef, partials, counter, red_out,
                                             blockIdx.x, gridDim.x);
+}
+
+// The three CGS2 passes and the scaling as one cooperative launch, for small
+// k, where four separate launches are bound by their latency rather than by
+// the basis reads.  The slice of q stays in registers across the passes;
+// each pass writes its per-block partial sums to its own rows of the
+// partials ([0, k] pass 1, [k+1, 2k] pass 2, 2k+1 pass 3, so no block
+// overwrites rows another block may still be reading), the grid synchronises
+// (a cooperative launch keeps every block resident), and every block sums
+// the partials of all blocks in the same fixed order in FP64, so all blocks
+// hold identical coefficients and the result is deterministic.
+__device__ __forceinline__ void reduce_rows(const float *__restrict__ partials, int row0, int nrows,
+                                            int G, int Gp, double *out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = warp; j < nrows; j += kWarps) {
+        const float *pr = partials + (size_t)(row0 + j) * Gp;
+        double acc = 0.0;
+        for (int g = lane; g < G; g += 32) acc += (double)__ldcg(pr + g);
+        acc = warp_sum_d(acc);
+        if (lane == 0) out[j] = acc;
+    }
+}
+
+__device__ __forceinline__ void write_rows(const float *s_w, int nred, int row0, float *partials,
+                                           int Gp, int blk) {
+    for (int j = threadIdx.x; j < nred; j += kThreads) {
+        float t = 0.f;
+        for (int w = 0; w < kWarps; ++w) t += s_w[w * nred + j];
+        partials[(size_t)(row0 + j) * Gp + blk] = t;
+    }
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(kThreads, 2)
+cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict__ q, int64_t L,
+                  T *__restrict__ w_out, double *__restrict__ h_out, float *__restrict__ partials,
+                  double *__restrict__ h1g, double *__restrict__ h2g, double *__restrict__ scal) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    extern __shared__ double smem_d[];
+    double *s_h1 = smem_d;                          // k + 1: h1, then ||q_pre||^2
+    double *s_h2 = s_h1 + (k + 1);                  // k + 1: h2, then ||q||^2
+    float *s_c = reinterpret_cast<float *>(s_h2 + (k + 1));   // k coefficients
+    float *s_w = s_c + k;                           // kWarps * (k + 1)
+    const int tid = threadIdx.x, blk = blockIdx.x, G = gridDim.x, Gp = padded_grid(G);
+    const int64_t g0 = (int64_t)blk * kThreads * E + tid;
+    float4 qv[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) qv[e] = ld4_rw(q, g0 + (int64_t)e * kThreads, L);
+    // pass 1: h1 = W^T q, ||q||^2
+    dots_slice<T, E, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
+    __syncthreads();
+    write_rows(s_w, k + 1, 0, partials, Gp, blk);
+    __threadfence();
+    grid.sync();
+    reduce_rows(partials, 0, k + 1, G, Gp, s_h1);
+    __syncthreads();
+    double nrm2 = s_h1[k];
+    if (k > 0) {
+        // pass 2: q -= W h1, h2 = W^T q
+        for (int j = tid; j < k; j += kThreads) s_c[j] = (float)s_h1[j];
+        __syncthreads();
+        update_slice<T, E>(W, ldw, k, s_c, g0, L, qv);
+        dots_slice<T, E, false>(W, ldw, k, g0, L, qv, s_w, k);
+        __syncthreads();
+        write_rows(s_w, k, k + 1, partials, Gp, blk);
+        __threadfence();
+        grid.sync();
+        reduce_rows(partials, k + 1, k, G, Gp, s_h2);
+        __syncthreads();
+        // pass 3: q -= W h2, ||q||^2
+        for (int j = tid; j < k; j += kThreads) s_c[j] = (float)s_h2[j];
+        __syncthreads();
+        update_slice<T, E>(W, ldw, k, s_c, g0, L, qv);
+        {
+            float t = 0.f;
+#pragma unroll
+            for (int e = 0; e < E; ++e) t += dot4(qv[e], qv[e]);
+            t = warp_sum(t);
+            if ((tid & 31) == 0) s_w[tid >> 5] = t;
+        }
+        __syncthreads();
+        write_rows(s_w, 1, 2 * k + 1, partials, Gp, blk);
+        __threadfence();
+        grid.sync();
+        reduce_rows(partials, 2 * k + 1, 1, G, Gp, s_h2 + k);
+        __syncthreads();
+        nrm2 = s_h2[k];
+    }
+    // w_{k+1} = q / ||q||; q keeps the orthogonalised vector
+    const float inv = nrm2 > 0.0 ? (float)(1.0 / sqrt(nrm2)) : 0.0f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int64_t g = g0 + (int64_t)e * kThreads;
+        st4(q, g, L, qv[e]);
+        stw4(w_out, g, L, make_float4(qv[e].x * inv, qv[e].y * inv, qv[e].z * inv, qv[e].w * inv));
+    }
+    if (blk == 0) {
+        for (int j = tid; j < k; j += kThreads) {
+            h_out[j] = s_h1[j] + s_h2[j];
+            h1g[j] = s_h1[j];
+            h2g[j] = s_h2[j];
+        }
+        if (tid == 0) {
+            h_out[k] = sqrt(nrm2);
+            h1g[k] = s_h1[k];
+            scal[0] = s_h1[k];
+            scal[1] = nrm2;
+        }
+    }
 }
 
 // w_out = q / sqrt(nrm2) (0 if nrm2 == 0); block 0 also assembles the
@@ -433,9 +568,16 @@ static int red_grid_max(int64_t L) {
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Partial rows: kmax + 2 for the separate passes; the fused step (k <= 64)
+// needs 2k + 2.
+static size_t partial_rows(int kmax) {
+    const size_t fused = 2 * (size_t)(kmax < 64 ? kmax : 64) + 2;
+    return (size_t)kmax + 2 > fused ? (size_t)kmax + 2 : fused;
+}
+
 size_t ctg_red_scratch_bytes(int64_t L, int kmax) {
     const size_t G = (size_t)padded_grid(red_grid_max(L));
-    return align256(sizeof(float) * (size_t)(kmax + 2) * G) +
+    return align256(sizeof(float) * partial_rows(kmax) * G) +
            2 * align256(sizeof(double) * (size_t)(kmax + 2)) + align256(sizeof(double) * 8) +
            align256(sizeof(unsigned) * 4);
 }
@@ -444,7 +586,8 @@ void ctg_red_scratch_carve(void *base, int64_t L, int kmax, RedScratch *rs) {
     char *p = static_cast<char *>(base);
     const size_t G = (size_t)padded_grid(red_grid_max(L));
     rs->partials = reinterpret_cast<float *>(p);
-    p += align256(sizeof(float) * (size_t)(kmax + 2) * G);
+    rs->rows = (int)partial_rows(kmax);
+    p += align256(sizeof(float) * partial_rows(kmax) * G);
     rs->h1 = reinterpret_cast<double *>(p);
     p += align256(sizeof(double) * (size_t)(kmax + 2));
     rs->h2 = reinterpret_cast<double *>(p);
@@ -458,6 +601,10 @@ void ctg_red_scratch_carve(void *base, int64_t L, int kmax, RedScratch *rs) {
 
 namespace {
 
+size_t fused_smem_bytes(int k) {
+    return sizeof(double) * 2 * (size_t)(k + 1) + sizeof(float) * ((size_t)k + (size_t)kWarps * (k + 1));
+}
+
 int scale_blocks(int64_t L) {
     const int64_t L4 = (L + 3) / 4;
     int blocks = (int)((L4 + 255) / 256);
@@ -465,10 +612,67 @@ int scale_blocks(int64_t L) {
     return blocks < 1 ? 1 : blocks;
 }
 
+// The fused step is used for k <= kFusedMaxK when the reduction scratch has
+// the 2k + 2 partial rows it needs and every block of the grid can be
+// resident at once (checked once per kernel instantiation).
+constexpr int kFusedMaxK = 64;
+
+template <typename T, int E>
+int fused_resident_blocks() {
+    static int blocks = -1;
+    if (blocks < 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        const size_t smem = fused_smem_bytes(kFusedMaxK);
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cgs2_fused_kernel<T, E>, kThreads,
+                                                          smem) != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 0;
+        }
+        blocks = per_sm * sms;
+    }
+    return blocks;
+}
+
+template <typename T, int E>
+cudaError_t launch_fused(const T *W, int64_t ldw, int64_t L, int k, float *q, T *w_out,
+                         double *h_out, const RedScratch &rs, int G, cudaStream_t st, bool *done) {
+    *done = false;
+    if (G > fused_resident_blocks<T, E>()) return cudaSuccess;
+    const size_t smem = fused_smem_bytes(k);
+    float *partials = rs.partials;
+    double *h1 = rs.h1, *h2 = rs.h2, *scal = rs.scal;
+    void *args[] = {(void *)&W, (void *)&ldw, (void *)&k, (void *)&q, (void *)&L, (void *)&w_out,
+                    (void *)&h_out, (void *)&partials, (void *)&h1, (void *)&h2, (void *)&scal};
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void *)cgs2_fused_kernel<T, E>, dim3(G),
+                                                      dim3(kThreads), args, smem, st);
+    *done = e == cudaSuccess;
+    return e;
+}
+
 template <typename T>
 cudaError_t cgs2_step_t(const T *W, int64_t ldw, int64_t L, int k, float *q, T *w_out,
-                        double *h_out, const RedScratch &rs, cudaStream_t st) {
+                        double *h_out, const RedScratch &rs, cudaStream_t st, int *nkern) {
     cudaError_t err;
+    if (nkern) *nkern = k > 0 ? 4 : 2;
+    if (k <= kFusedMaxK && rs.rows >= 2 * k + 2) {
+        int E;
+        const int G = ctg_red_grid(L, &E);
+        bool done = false;
+        switch (E) {
+            case 1: err = launch_fused<T, 1>(W, ldw, L, k, q, w_out, h_out, rs, G, st, &done); break;
+            case 2: err = launch_fused<T, 2>(W, ldw, L, k, q, w_out, h_out, rs, G, st, &done); break;
+            case 4: err = launch_fused<T, 4>(W, ldw, L, k, q, w_out, h_out, rs, G, st, &done); break;
+            case 8: err = launch_fused<T, 8>(W, ldw, L, k, q, w_out, h_out, rs, G, st, &done); break;
+            default: err = cudaSuccess;
+        }
+        if (err != cudaSuccess) return err;
+        if (done) {
+            if (nkern) *nkern = 1;
+            return cudaSuccess;
+        }
+    }
     // pass 1: h1 = W^T q and ||q_pre||^2 (h1[k]); keep the latter in scal[0]
     if ((err = launch_pass<T, false, true, true>(W, ldw, k, q, L, nullptr, rs, rs.h1, st)) != cudaSuccess)
         return err;
@@ -515,17 +719,18 @@ cudaError_t gemv_t(const T *W, int64_t ldw, int64_t L, int k, const double *y,
 }  // namespace
 
 cudaError_t ctg_cgs2_step(const void *W, int dtype, int64_t ldw, int64_t L, int k, float *q,
-                          void *w_out, double *h_out, const RedScratch &rs, cudaStream_t st) {
+                          void *w_out, double *h_out, const RedScratch &rs, cudaStream_t st,
+                          int *nkern) {
     switch (dtype) {
         case CTG_BASIS_FP32:
             return cgs2_step_t(static_cast<const float *>(W), ldw, L, k, q,
-                               static_cast<float *>(w_out), h_out, rs, st);
+                               static_cast<float *>(w_out), h_out, rs, st, nkern);
         case CTG_BASIS_BF16:
             return cgs2_step_t(static_cast<const __nv_bfloat16 *>(W), ldw, L, k, q,
-                               static_cast<__nv_bfloat16 *>(w_out), h_out, rs, st);
+                               static_cast<__nv_bfloat16 *>(w_out), h_out, rs, st, nkern);
         case CTG_BASIS_FP16:
             return cgs2_step_t(static_cast<const __half *>(W), ldw, L, k, q,
-                               static_cast<__half *>(w_out), h_out, rs, st);
+                               static_cast<__half *>(w_out), h_out, rs, st, nkern);
         default: return cudaErrorInvalidValue;
     }
 }

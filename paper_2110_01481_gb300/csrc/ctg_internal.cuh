@@ -121,6 +121,7 @@ struct RedScratch {
     unsigned int *counter; // 4 counters, zero between launches
     int grid;              // blocks of every reduction pass for this L
     int E;                 // float4 groups per thread
+    int rows = 0;          // partial-sum rows available (kmax + 2, or 2k + 2 for a fused step)
 };
 int ctg_red_grid(int64_t L, int *E_out);
 size_t ctg_red_scratch_bytes(int64_t L, int kmax);
@@ -136,8 +137,11 @@ static inline size_t ctg_basis_bytes(int dtype) {
 // h_out[0..k-1] = h1 + h2, h_out[k] = ||q||, and write w_out = q / ||q||
 // (rounded to `dtype`) when ||q|| > 0.  Also leaves ||q_pre||^2 in
 // rs.scal[0].
+// *nkern (if given) = the kernels launched: 1 for the fused cooperative step
+// (small k, scratch and residency permitting), else 4 (2 when k = 0).
 cudaError_t ctg_cgs2_step(const void *W, int dtype, int64_t ldw, int64_t L, int k, float *q,
-                          void *w_out, double *h_out, const RedScratch &rs, cudaStream_t st);
+                          void *w_out, double *h_out, const RedScratch &rs, cudaStream_t st,
+                          int *nkern = nullptr);
 // out = base + sum_j y_j W_j (base may be NULL); y: k doubles (device).
 cudaError_t ctg_gemv(const void *W, int dtype, int64_t ldw, int64_t L, int k, const double *y,
                      const float *base, float *out, cudaStream_t st);
