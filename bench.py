@@ -443,6 +443,30 @@ def serve_engine(P, torch, reqs, arrive, slots, budget, rounds):
     return done, iters, outs, max(done)
 
 
+def serving_summary(P, torch, dev, count):
+    """The served part of the metric, short: `count` requests of the served
+    workload at Poisson arrivals of 0.9x the one-at-a-time capacity; p50/p99
+    latency and throughput of the continuous-batching engine beside the
+    one-at-a-time server (the full sweep is --serve)."""
+    reqs = serve_requests(P, torch, dev, count)
+    for r in reqs:
+        r.pop("xbar")
+    serve_fifo(P, torch, reqs[:8], [0.0] * 8)
+    serve_engine(P, torch, reqs[:8], [0.0] * 8, 64, 96 << 30, 4)
+    _, _, _, span = serve_fifo(P, torch, reqs, [0.0] * len(reqs))
+    capacity = len(reqs) / span
+    gaps = np.random.default_rng(5999).exponential(1.0, len(reqs))
+    arrive = list(np.cumsum(gaps) / (0.9 * capacity))
+    out = {"requests": len(reqs), "offered_req_per_s": 0.9 * capacity,
+           "one_at_a_time_capacity_req_per_s": capacity}
+    for name, fn in (("engine", lambda a: serve_engine(P, torch, reqs, a, 64, 96 << 30, 4)),
+                     ("one_at_a_time", lambda a: serve_fifo(P, torch, reqs, a))):
+        done, iters, _, span = fn(arrive)
+        out[name] = dict(_latency_stats(arrive, done), served_req_per_s=len(reqs) / span,
+                         iterations_per_s=iters / span)
+    return out
+
+
 def run_serve(args):
     """Poisson arrivals at fractions of the one-at-a-time capacity; p50/p99
     latency (completion - arrival) and throughput of the continuous-batching
@@ -732,9 +756,12 @@ def run_gpu(args):
         "e2e": {"value": e2e_iters_all / (e2e_ms_max / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * m, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches,
+        "tiles": ctx.tuning(g),
         "roofline": roof,
         "arnoldi_roofline": arnoldi_roof,
     }
+    if world == 1 and not args.no_serve:
+        line["serving"] = serving_summary(P, torch, dev, args.serve_quick)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
     print(json.dumps(line))
@@ -814,6 +841,10 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=8)
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the short serving measurement of the default run")
+    ap.add_argument("--serve-quick", type=int, default=160,
+                    help="requests of the default run's serving measurement")
     ap.add_argument("--cgs2-only", action="store_true",
                     help="time only the large-basis Arnoldi (CGS2) step")
     ap.add_argument("--cgs2-k", type=int, default=100)

@@ -157,6 +157,25 @@ int ctg_project(ctg_ctx *ctx, const ctg_geom *g, const float *x_dev,
 int ctg_backproject(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev,
                     float *x_dev, void *stream);
 
+/* Projector tile shapes.  By default the context times, at the first use of
+ * a geometry, the forward projector with 8 and 4 angles per block and the
+ * pixel-driven back projector with 16, 32 and 64 angles staged per pass
+ * (CUDA events, 3 launches each on zero inputs, with temporary buffers of
+ * about 5n + m floats), and keeps the fastest.  The candidates sum every ray
+ * and every pixel in the same order, so results do not depend on the choice.
+ * ctg_set_tiles forces shapes instead (0, 0 restores autotuning); it takes
+ * effect at each geometry's next use.  ctg_get_tuning reports the shapes in
+ * use for a geometry (tuning it first if needed) and the measured times. */
+typedef struct {
+    int32_t fwd_angles;       /* 4 or 8                                     */
+    int32_t back_chunk;       /* 16, 32 or 64                               */
+    int32_t tuned;            /* 1 if chosen by timing                      */
+    float fwd_us[2];          /* measured: 8, 4 angles per block            */
+    float back_us[3];         /* measured: 16, 32, 64 angles per pass       */
+} ctg_tuning;
+int ctg_set_tiles(ctg_ctx *ctx, int32_t fwd_angles, int32_t back_chunk);
+int ctg_get_tuning(ctg_ctx *ctx, const ctg_geom *g, ctg_tuning *out);
+
 /* The NCP distance of Sec. 6.4's NCP criterion for a residual sinogram r
  * (m floats, device): the paper defines the criterion by citation; reading
  * taken here: each projection (N_d bins of one angle) is a signal; with

@@ -38,6 +38,12 @@ class CtgGeom(ctypes.Structure):
                 ("back_tau", ctypes.c_double)]
 
 
+class CtgTuning(ctypes.Structure):
+    _fields_ = [("fwd_angles", ctypes.c_int32), ("back_chunk", ctypes.c_int32),
+                ("tuned", ctypes.c_int32), ("fwd_us", ctypes.c_float * 2),
+                ("back_us", ctypes.c_float * 3)]
+
+
 class CtgOpts(ctypes.Structure):
     _fields_ = [("maxit", ctypes.c_int32), ("basis_dtype", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("noise_norm", ctypes.c_double),
@@ -64,7 +70,7 @@ class CtgLayout(ctypes.Structure):
                 ("off_h", ctypes.c_size_t), ("total_bytes", ctypes.c_size_t)]
 
 
-EXPORTS = ("ctg_create", "ctg_destroy", "ctg_project", "ctg_backproject", "ctg_ncp_distance",
+EXPORTS = ("ctg_create", "ctg_destroy", "ctg_project", "ctg_backproject", "ctg_ncp_distance", "ctg_set_tiles", "ctg_get_tuning",
            "ctg_workspace_bytes", "ctg_workspace_layout", "ctg_ab_gmres",
            "ctg_ba_gmres", "ctg_lsqr", "ctg_lsmr", "ctg_cgs2_scratch_bytes", "ctg_cgs2", "ctg_cgs2_noalloc",
            "ctg_set_timing", "ctg_get_timing", "ctg_status_string",
@@ -123,6 +129,10 @@ def _declare(lib):
     lib.ctg_engine_in_flight.restype = i32
     lib.ctg_engine_destroy.argtypes = [vp]
     lib.ctg_engine_destroy.restype = None
+    lib.ctg_set_tiles.argtypes = [vp, i32, i32]
+    lib.ctg_set_tiles.restype = ctypes.c_int
+    lib.ctg_get_tuning.argtypes = [vp, G, ctypes.POINTER(CtgTuning)]
+    lib.ctg_get_tuning.restype = ctypes.c_int
     lib.ctg_ncp_distance.argtypes = [vp, G, vp, ctypes.POINTER(ctypes.c_double), vp]
     lib.ctg_ncp_distance.restype = ctypes.c_int
     lib.ctg_status_string.argtypes = [ctypes.c_int]

@@ -80,6 +80,20 @@ class Context:
         out["kernels"] = int(t.kernels)
         return out
 
+    def set_tiles(self, fwd_angles: int = 0, back_chunk: int = 0) -> None:
+        """Force the projectors' tile shapes (0, 0: autotuned per geometry)."""
+        nat.check(nat.lib().ctg_set_tiles(self.handle, int(fwd_angles), int(back_chunk)), "ctg_set_tiles")
+
+    def tuning(self, g: "Geometry") -> dict:
+        """Tile shapes in use for geometry g and the autotuner's timings (us)."""
+        t = nat.CtgTuning()
+        with torch.cuda.device(self.device):
+            nat.check(nat.lib().ctg_get_tuning(self.handle, ctypes.byref(g.c()), ctypes.byref(t)),
+                      "ctg_get_tuning")
+        return {"fwd_angles": t.fwd_angles, "back_chunk": t.back_chunk, "tuned": bool(t.tuned),
+                "fwd_us": {8: t.fwd_us[0], 4: t.fwd_us[1]},
+                "back_us": {16: t.back_us[0], 32: t.back_us[1], 64: t.back_us[2]}}
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h and nat._lib is not None:

@@ -151,6 +151,10 @@ struct GeomEntry {
     MatchedAngle *mt = nullptr; // matched / thresholded back projector
     int rm = 0;
     float thr = 0.0f;           // B_tau threshold tau * max(A) (0: A^T)
+    int fwd_angles = 8;         // tile shapes (autotuned unless forced)
+    int back_chunk = 32;
+    bool tuned = false;
+    float fwd_us[2] = {0, 0}, back_us[3] = {0, 0, 0};   // measured: fwd 8, 4; back 16, 32, 64
     unsigned long long last_use = 0;
 };
 
@@ -160,7 +164,7 @@ cudaError_t back_apply(const GeomEntry *ge, const void *b, int btype, const floa
     const ctg_geom *g = &ge->g;
     if (g->back_model == CTG_BACK_PIXEL)
         return ctg_launch_back(b, btype, g->N, g->n_angles, g->n_det, ge->back, ge->back_window, add,
-                               x, st);
+                               x, st, ge->back_chunk);
     if (ge->rm == 0 && ge->back_window <= ctg_back_window_max())
         return ctg_launch_back_matched_tiled(b, btype, g->N, g->n_angles, g->n_det, ge->back,
                                              ge->back_window, ge->mt, ge->thr, add, x, st);
@@ -283,6 +287,8 @@ struct ctg_ctx {
     // completion events of the pipelined solver loops (no timing)
     cudaEvent_t ev_h[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev_r[4] = {nullptr, nullptr, nullptr, nullptr};
+    // projector tile shapes: 0 = autotuned per geometry, else forced
+    int force_fwd_angles = 0, force_back_chunk = 0;
 };
 
 namespace {
@@ -300,12 +306,85 @@ int fail_cuda(cudaError_t e) {
 
 constexpr size_t kMaxCachedGeoms = 4;
 
+// Projector tile autotuner.  Candidate shapes leave every sum in the same
+// order (forward: angles per block, each ray still one warp; pixel-driven
+// back projection: angles staged per pass, each pixel's angles still in
+// order), so the choice changes the speed only.  Each candidate is timed
+// with CUDA events over 3 launches (after one untimed) on zero inputs of the
+// geometry's sizes on a private stream; the fastest is kept.
+int tune_geometry(GeomEntry *ge) {
+    const ctg_geom *g = &ge->g;
+    const size_t n = (size_t)g->N * g->N, m = (size_t)g->n_angles * g->n_det;
+    float2 *pad = nullptr;
+    float *bv = nullptr, *xv = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaMalloc(&pad, sizeof(float) * ge->pl.floats);
+    if (err == cudaSuccess) err = cudaMalloc(&bv, sizeof(float) * m);
+    if (err == cudaSuccess) err = cudaMalloc(&xv, sizeof(float) * n);
+    if (err == cudaSuccess) err = cudaMemset(pad, 0, sizeof(float) * ge->pl.floats);
+    if (err == cudaSuccess) err = cudaMemset(bv, 0, sizeof(float) * m);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    auto timed = [&](auto launch, float *us) {
+        if (err != cudaSuccess) return;
+        launch();
+        err = cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && err == cudaSuccess; ++r) launch();
+        if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        *us = ms * 1e3f / 3.0f;
+    };
+    const int fwd_cand[2] = {8, 4};
+    for (int c = 0; c < 2; ++c)
+        timed([&] {
+            if (err == cudaSuccess)
+                err = ctg_launch_forward(pad, g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, bv, st, fwd_cand[c]);
+        }, &ge->fwd_us[c]);
+    const int back_cand[3] = {16, 32, 64};
+    if (g->back_model == CTG_BACK_PIXEL)
+        for (int c = 0; c < 3; ++c)
+            timed([&] {
+                if (err == cudaSuccess)
+                    err = ctg_launch_back(bv, CTG_BASIS_FP32, g->N, g->n_angles, g->n_det, ge->back,
+                                          ge->back_window, nullptr, xv, st, back_cand[c]);
+            }, &ge->back_us[c]);
+    if (err == cudaSuccess) {
+        ge->fwd_angles = ge->fwd_us[1] < ge->fwd_us[0] ? 4 : 8;
+        int best = 1;
+        if (g->back_model == CTG_BACK_PIXEL)
+            for (int c = 0; c < 3; ++c)
+                if (ge->back_us[c] < ge->back_us[best]) best = c;
+        ge->back_chunk = back_cand[best];
+        ge->tuned = true;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(pad);
+    cudaFree(bv);
+    cudaFree(xv);
+    return err == cudaSuccess ? CTG_OK : fail_cuda(err);
+}
+
+int apply_tiles(ctg_ctx *ctx, GeomEntry *ge) {
+    if (ctx->force_fwd_angles || ctx->force_back_chunk) {
+        ge->fwd_angles = ctx->force_fwd_angles ? ctx->force_fwd_angles : 8;
+        ge->back_chunk = ctx->force_back_chunk ? ctx->force_back_chunk : 32;
+        return CTG_OK;
+    }
+    return ge->tuned ? CTG_OK : tune_geometry(ge);
+}
+
 int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
     for (auto &e : ctx->cache)
         if (same_geom(e.g, *g)) {
             e.last_use = ++ctx->tick;
             *out = &e;
-            return CTG_OK;
+            return apply_tiles(ctx, &e);
         }
     if (ctx->cache.size() >= kMaxCachedGeoms) {
         // evict the least recently used geometry; its tables may still be
@@ -363,7 +442,7 @@ int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
     }
     ctx->cache.push_back(e);
     *out = &ctx->cache.back();
-    return CTG_OK;
+    return apply_tiles(ctx, *out);
 }
 
 // (cos, -sin)(2 pi j / n_det), j < n_det, for the NCP periodograms
@@ -505,7 +584,8 @@ struct SolveCtx {
         return traced(ctx, 0, 2, st, [&] {
             cudaError_t e = ctg_launch_pad(x, xtype, pad(), g->N, ge->pl, st);
             if (e != cudaSuccess) return e;
-            return ctg_launch_forward(pad(), g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, b, st);
+            return ctg_launch_forward(pad(), g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, b, st,
+                                      ge->fwd_angles);
         });
     }
     cudaError_t back(const void *b, const float *add, float *x, int btype = CTG_BASIS_FP32) const {
@@ -1106,7 +1186,8 @@ int ctg_project(ctg_ctx *ctx, const ctg_geom *g, const float *x_dev, float *b_de
     CTG_CK(traced(ctx, 0, 2, st, [&] {
         cudaError_t e = ctg_launch_pad(x_dev, CTG_BASIS_FP32, ge->pad, g->N, ge->pl, st);
         if (e != cudaSuccess) return e;
-        return ctg_launch_forward(ge->pad, g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, b_dev, st);
+        return ctg_launch_forward(ge->pad, g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, b_dev, st,
+                                  ge->fwd_angles);
     }));
     return CTG_OK;
 }
@@ -1118,6 +1199,28 @@ int ctg_backproject(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, float *
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CTG_CK(traced(ctx, 1, 1, st, [&] { return back_apply(ge, b_dev, CTG_BASIS_FP32, nullptr, x_dev, st); }));
+    return CTG_OK;
+}
+
+int ctg_set_tiles(ctg_ctx *ctx, int32_t fwd_angles, int32_t back_chunk) {
+    if (!ctx || (fwd_angles != 0 && fwd_angles != 4 && fwd_angles != 8) ||
+        (back_chunk != 0 && back_chunk != 16 && back_chunk != 32 && back_chunk != 64))
+        return CTG_ERR_INVALID_ARG;
+    ctx->force_fwd_angles = fwd_angles;
+    ctx->force_back_chunk = back_chunk;
+    return CTG_OK;    // applied to every geometry at its next use
+}
+
+int ctg_get_tuning(ctg_ctx *ctx, const ctg_geom *g, ctg_tuning *out) {
+    if (!ctx || !geom_valid(g) || !out) return CTG_ERR_INVALID_ARG;
+    GeomEntry *ge;
+    const int rc = get_geom(ctx, g, &ge);
+    if (rc) return rc;
+    out->fwd_angles = ge->fwd_angles;
+    out->back_chunk = ge->back_chunk;
+    out->tuned = ge->tuned ? 1 : 0;
+    for (int c = 0; c < 2; ++c) out->fwd_us[c] = ge->fwd_us[c];
+    for (int c = 0; c < 3; ++c) out->back_us[c] = ge->back_us[c];
     return CTG_OK;
 }
 

@@ -77,16 +77,21 @@ static inline PadLayout ctg_pad_layout(int N, double det_spacing) {
 // forward projector.
 cudaError_t ctg_launch_pad(const void *x, int dtype, float2 *pad, int N, const PadLayout &pl,
                            cudaStream_t st);
+// fwd_angles: angles (warps) per block, 4 or 8 (a tile shape the context's
+// autotuner chooses; the result does not depend on it).
 cudaError_t ctg_launch_forward(const float2 *pad, int N, const PadLayout &pl, int n_angles,
-                               int n_det, const FwdAngle *tab, float *b, cudaStream_t st);
+                               int n_det, const FwdAngle *tab, float *b, cudaStream_t st,
+                               int fwd_angles = 8);
 // Detector-window width (in bins) that the tiled back projector stages per
 // angle, from the host copy of the angle table.
 int ctg_back_window(const BackAngle *host_tab, int n_angles);
 // x = B b (+ add, if add != NULL); b has element type `dtype`; window from
 // ctg_back_window
+// back_chunk: angles staged per pass, 16, 32 or 64 (tuned like fwd_angles;
+// the result does not depend on it).
 cudaError_t ctg_launch_back(const void *b, int dtype, int N, int n_angles, int n_det,
                             const BackAngle *tab, int window, const float *add, float *x,
-                            cudaStream_t st);
+                            cudaStream_t st, int back_chunk = 32);
 
 // ---- matched back projector (matched.cu) ----------------------------------
 // x = B_thr b (+ add): the transpose of the forward projector, keeping the

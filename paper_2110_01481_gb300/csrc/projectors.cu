@@ -94,13 +94,13 @@ constexpr int kFwdDepth = 8;    // image loads in flight per lane (a multiple of
 // into the step, so its high word is the staged-pair index and its low word
 // the interpolation weight.  A lane outside its own chord reads zero pairs
 // in the border (or, with kClamp, a clamped index into the 2-pair border).
-template <bool kClamp>
+template <bool kClamp, int kAngles = kFwdAngles>
 __device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ pad, int N,
                                                      int stride, int border, int n_angles,
                                                      int n_det, const FwdAngle *__restrict__ tab,
                                                      float *__restrict__ b, int bx, int by) {
     const int lane = threadIdx.x & 31;
-    const int a = by * kFwdAngles + (threadIdx.x >> 5);
+    const int a = by * kAngles + (threadIdx.x >> 5);
     if (a >= n_angles) return;                        // whole warp
     const int d = bx * 32 + lane;
     const FwdAngle t = tab[a];
@@ -174,13 +174,13 @@ __device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ 
     if (d < n_det) b[(size_t)a * n_det + d] = (acc0 + acc1) * t.scale;
 }
 
-template <bool kClamp>
-__global__ void __launch_bounds__(32 * kFwdAngles)
+template <bool kClamp, int kAngles>
+__global__ void __launch_bounds__(32 * kAngles)
 joseph_forward_kernel(const float2 *__restrict__ pad, int N, int stride, int border,
                       int n_angles, int n_det, const FwdAngle *__restrict__ tab,
                       float *__restrict__ b) {
-    joseph_forward_block<kClamp>(pad, N, stride, border, n_angles, n_det, tab, b, blockIdx.x,
-                                 blockIdx.y);
+    joseph_forward_block<kClamp, kAngles>(pad, N, stride, border, n_angles, n_det, tab, b, blockIdx.x,
+                                          blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -209,16 +209,16 @@ constexpr int kBSplit = 4;       // CTAs per cluster = angle groups per tile
 // scale * max(0, 1 - f inv_w) and scale * max(0, 1 - (1 - f) inv_w) (terms
 // below thr dropped for 2).  The staged pairs are (b[d], b[d+1] - b[d]) for
 // the pixel-driven B and (b[d], b[d+1]) for the others.
-template <typename T, int kModel = 0>
+template <typename T, int kModel = 0, int kChunk = kBChunk>
 __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, int n_angles,
                                                 int n_det, const BackAngle *__restrict__ tab,
                                                 int W, const float *__restrict__ add,
                                                 float *__restrict__ x, int bx, int by,
                                                 const MatchedAngle *__restrict__ mt = nullptr,
                                                 float thr = 0.0f) {
-    extern __shared__ float2 s_pairs[];               // kBChunk * W pairs
-    __shared__ float4 s_par[kBChunk];                 // cf, sf, u0' (window-relative), origin
-    __shared__ float4 s_wt[kModel ? kBChunk : 1];     // scale, scale inv_w, scale - scale inv_w
+    extern __shared__ float2 s_pairs[];               // kChunk * W pairs
+    __shared__ float4 s_par[kChunk];                  // cf, sf, u0' (window-relative), origin
+    __shared__ float4 s_wt[kModel ? kChunk : 1];      // scale, scale inv_w, scale - scale inv_w
     __shared__ float s_part[kBRows][kBThreads];       // this CTA's partial sums
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();       // == blockIdx.z
@@ -229,8 +229,8 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
     const int a_begin = min(n_angles, rank * per), a_end = min(n_angles, a_begin + per);
     float acc[kBRows] = {0.f, 0.f, 0.f, 0.f};
     const float kMagic = 12582912.0f;                 // 1.5 * 2^23
-    for (int a0 = a_begin; a0 < a_end; a0 += kBChunk) {
-        const int na = min(kBChunk, a_end - a0);
+    for (int a0 = a_begin; a0 < a_end; a0 += kChunk) {
+        const int na = min(kChunk, a_end - a0);
         __syncthreads();
         if (threadIdx.x < na) {
             const BackAngle t = tab[a0 + threadIdx.x];
@@ -304,12 +304,12 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
     cluster.sync();   // peers' shared memory must outlive the reads above
 }
 
-template <typename T>
+template <typename T, int kChunk>
 __global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
 pixel_back_tiled_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
                         const BackAngle *__restrict__ tab, int W, const float *__restrict__ add,
                         float *__restrict__ x) {
-    pixel_back_tile(b, N, n_angles, n_det, tab, W, add, x, blockIdx.x, blockIdx.y);
+    pixel_back_tile<T, 0, kChunk>(b, N, n_angles, n_det, tab, W, add, x, blockIdx.x, blockIdx.y);
 }
 
 // A^T (kModel 1) or B_tau (kModel 2) with the tiled design above.
@@ -476,28 +476,56 @@ cudaError_t ctg_launch_pad(const void *x, int dtype, float2 *pad, int N, const P
     return cudaGetLastError();
 }
 
-cudaError_t ctg_launch_forward(const float2 *pad, int N, const PadLayout &pl, int n_angles,
-                               int n_det, const FwdAngle *tab, float *b, cudaStream_t st) {
-    dim3 grid((n_det + 31) / 32, (n_angles + kFwdAngles - 1) / kFwdAngles);
+namespace {
+
+template <int kAngles>
+void launch_forward_t(const float2 *pad, int N, const PadLayout &pl, int n_angles, int n_det,
+                      const FwdAngle *tab, float *b, cudaStream_t st) {
+    const dim3 grid((n_det + 31) / 32, (n_angles + kAngles - 1) / kAngles);
     if (pl.clamp)
-        joseph_forward_kernel<true><<<grid, 32 * kFwdAngles, 0, st>>>(pad, N, pl.stride, pl.border,
-                                                                      n_angles, n_det, tab, b);
+        joseph_forward_kernel<true, kAngles><<<grid, 32 * kAngles, 0, st>>>(pad, N, pl.stride, pl.border,
+                                                                            n_angles, n_det, tab, b);
     else
-        joseph_forward_kernel<false><<<grid, 32 * kFwdAngles, 0, st>>>(pad, N, pl.stride, pl.border,
-                                                                       n_angles, n_det, tab, b);
+        joseph_forward_kernel<false, kAngles><<<grid, 32 * kAngles, 0, st>>>(pad, N, pl.stride, pl.border,
+                                                                             n_angles, n_det, tab, b);
+}
+
+}  // namespace
+
+cudaError_t ctg_launch_forward(const float2 *pad, int N, const PadLayout &pl, int n_angles,
+                               int n_det, const FwdAngle *tab, float *b, cudaStream_t st,
+                               int fwd_angles) {
+    // every ray is summed by one warp in the same order whatever the block
+    // shape, so the result does not depend on fwd_angles
+    if (fwd_angles == 4) launch_forward_t<4>(pad, N, pl, n_angles, n_det, tab, b, st);
+    else launch_forward_t<8>(pad, N, pl, n_angles, n_det, tab, b, st);
     return cudaGetLastError();
 }
 
 namespace {
 
+template <typename T, int kChunk>
+void launch_back_tiled(const T *b, int N, int n_angles, int n_det, const BackAngle *tab, int window,
+                       const float *add, float *x, cudaStream_t st) {
+    const size_t smem = sizeof(float2) * (size_t)kChunk * window;
+    const dim3 grid((N + kBT - 1) / kBT, (N + kBT - 1) / kBT, kBSplit);
+    pixel_back_tiled_kernel<T, kChunk><<<grid, kBThreads, smem, st>>>(b, N, n_angles, n_det, tab, window,
+                                                                      add, x);
+}
+
+// back_chunk: angles staged per pass (16, 32 or 64).  Each pixel sums its
+// angles in the same order whatever the chunk, so the result does not
+// depend on it.
 template <typename T>
 cudaError_t launch_back_t(const T *b, int N, int n_angles, int n_det, const BackAngle *tab,
-                          int window, const float *add, float *x, cudaStream_t st) {
-    const size_t smem = sizeof(float2) * (size_t)kBChunk * window;
-    if (window > 0 && smem <= 40 * 1024) {
-        dim3 grid((N + kBT - 1) / kBT, (N + kBT - 1) / kBT, kBSplit);
-        pixel_back_tiled_kernel<T><<<grid, kBThreads, smem, st>>>(b, N, n_angles, n_det, tab, window,
-                                                                  add, x);
+                          int window, const float *add, float *x, cudaStream_t st, int back_chunk) {
+    const size_t bytes_per_angle = sizeof(float2) * (size_t)window;
+    if (window > 0 && back_chunk == 64 && 64 * bytes_per_angle <= 40 * 1024) {
+        launch_back_tiled<T, 64>(b, N, n_angles, n_det, tab, window, add, x, st);
+    } else if (window > 0 && back_chunk == 16 && 16 * bytes_per_angle <= 40 * 1024) {
+        launch_back_tiled<T, 16>(b, N, n_angles, n_det, tab, window, add, x, st);
+    } else if (window > 0 && kBChunk * bytes_per_angle <= 40 * 1024) {
+        launch_back_tiled<T, kBChunk>(b, N, n_angles, n_det, tab, window, add, x, st);
     } else {
         dim3 grid((N + kBX - 1) / kBX, (N + kBY - 1) / kBY);
         pixel_back_kernel<T><<<grid, dim3(kBX, kBY), 0, st>>>(b, N, n_angles, n_det, tab, add, x);
@@ -542,15 +570,17 @@ cudaError_t ctg_launch_back_matched_tiled(const void *b, int dtype, int N, int n
 
 cudaError_t ctg_launch_back(const void *b, int dtype, int N, int n_angles, int n_det,
                             const BackAngle *tab, int window, const float *add, float *x,
-                            cudaStream_t st) {
+                            cudaStream_t st, int back_chunk) {
     switch (dtype) {
         case CTG_BASIS_FP32:
-            return launch_back_t(static_cast<const float *>(b), N, n_angles, n_det, tab, window, add, x, st);
+            return launch_back_t(static_cast<const float *>(b), N, n_angles, n_det, tab, window, add, x, st,
+                                 back_chunk);
         case CTG_BASIS_BF16:
             return launch_back_t(static_cast<const __nv_bfloat16 *>(b), N, n_angles, n_det, tab, window,
-                                 add, x, st);
+                                 add, x, st, back_chunk);
         case CTG_BASIS_FP16:
-            return launch_back_t(static_cast<const __half *>(b), N, n_angles, n_det, tab, window, add, x, st);
+            return launch_back_t(static_cast<const __half *>(b), N, n_angles, n_det, tab, window, add, x, st,
+                                 back_chunk);
         default: return cudaErrorInvalidValue;
     }
 }

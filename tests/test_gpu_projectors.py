@@ -104,3 +104,29 @@ def test_rejects_bad_arguments(P):
     with pytest.raises(nat.CtgError):
         P.backproject(P.Geometry(0, 8, 23), torch.zeros(184, device="cuda"),
                       out=torch.zeros(0, device="cuda"))
+
+
+def test_tile_autotuner_is_result_invariant(P):
+    """The autotuned tile shapes (angles per forward block, angles staged per
+    back-projection pass) change the speed only: every shape gives the same
+    projections bit for bit, and the tuner reports the timed candidates."""
+    import torch
+    ctx = P.Context.get(torch.device("cuda", 0))
+    cases = [P.Geometry(200, 90, 283), P.Geometry(96, 37, 150, 0, 120), P.Geometry(64, 45, 91, 10, 360, 1.3)]
+    gen = torch.Generator(device="cuda").manual_seed(21)
+    try:
+        for g in cases:
+            x = torch.rand(g.n, device="cuda", generator=gen)
+            y = torch.randn(g.m, device="cuda", generator=gen)
+            ctx.set_tiles(0, 0)
+            t = ctx.tuning(g)
+            assert t["tuned"] and t["fwd_angles"] in (4, 8) and t["back_chunk"] in (16, 32, 64)
+            assert all(v > 0 for v in t["fwd_us"].values()) and all(v > 0 for v in t["back_us"].values())
+            ref_a, ref_b = P.project(g, x), P.backproject(g, y)
+            for fa, bc in ((8, 32), (4, 16), (4, 64), (8, 64), (8, 16)):
+                ctx.set_tiles(fa, bc)
+                assert ctx.tuning(g)["fwd_angles"] == fa and ctx.tuning(g)["back_chunk"] == bc
+                assert torch.equal(P.project(g, x), ref_a), (g, fa)
+                assert torch.equal(P.backproject(g, y), ref_b), (g, bc)
+    finally:
+        ctx.set_tiles(0, 0)
