@@ -250,8 +250,12 @@ int ctg_lsmr(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, const float *x
  * discrepancy-principle stop (Sec. 6.4) done on the device.  A round is one
  * launch per phase for all solves and is replayed as a captured CUDA graph.
  * ctg_batch_create: geoms, variants, opts are arrays of n (FP32 basis only,
- * maxit <= 1024, det_spacing >= ~0.25); the batch owns its device workspace
- * (ctg_batch_workspace_bytes) and a stream of its own.
+ * the CTG_RULE_DP stopping rule, maxit <= 1024, det_spacing >= ~0.25; any
+ * back projector, A^T and B_tau only where two detector bins per pixel
+ * suffice, i.e. det_spacing >= max |cos|, |sin|, which holds for
+ * det_spacing >= 1); the batch owns its device workspace
+ * (ctg_batch_workspace_bytes) and a stream of its own.  Invalid or
+ * unsupported arguments return CTG_ERR_INVALID_ARG.
  * ctg_batch_solve: b_dev, x_dev: host arrays of n device pointers (m and n
  * floats of each solve); x0_dev: NULL or an array whose entries may be NULL;
  * infos: n reports, filled as by ctg_ab_gmres.  Work is ordered after prior
@@ -273,7 +277,8 @@ void ctg_batch_destroy(ctg_batch *batch);
  *   within hbm_budget_bytes.  Uses the current device.
  * ctg_engine_request_bytes: device bytes one solve occupies while in flight
  *   (its Krylov basis dominates: the storage law k L of Table 3), or 0 if the
- *   arguments are invalid (FP32 basis, maxit <= 1024 as for ctg_batch).
+ *   arguments are invalid or unsupported (the same conditions as for
+ *   ctg_batch_create).
  * ctg_engine_submit: admits one solve, or returns CTG_ERR_BUSY if no slot is
  *   free or its bytes do not fit the remaining budget, CTG_ERR_OOM if they
  *   exceed the whole budget.  b_dev must be ready

@@ -127,6 +127,9 @@ void build_matched(const ctg_geom *g, std::vector<MatchedAngle> &mt, int *rm) {
 
 bool ctg_geom_valid(const ctg_geom *g) { return geom_valid(g); }
 bool ctg_opts_valid(const ctg_opts *o) { return opts_valid(o); }
+void ctg_build_matched(const ctg_geom *g, std::vector<MatchedAngle> &mt, int *rm) {
+    build_matched(g, mt, rm);
+}
 void ctg_build_tables(const ctg_geom *g, std::vector<FwdAngle> &fw, std::vector<BackAngle> &bk) {
     build_tables(g, fw, bk);
 }

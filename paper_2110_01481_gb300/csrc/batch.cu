@@ -87,12 +87,65 @@ size_t plan_instance(InstPlan &p, char *base) {
     d.pad = (float2 *)take(sizeof(float) * pl.floats);
     d.fwd = (const FwdAngle *)take(sizeof(FwdAngle) * g.n_angles);
     d.back = (const BackAngle *)take(sizeof(BackAngle) * g.n_angles);
+    d.back_model = g.back_model;
+    d.mt = g.back_model != CTG_BACK_PIXEL ? (const MatchedAngle *)take(sizeof(MatchedAngle) * g.n_angles)
+                                          : nullptr;
+    d.back_thr = 0.0f;
     d.partials = (float *)take(sizeof(float) * (size_t)(maxit + 3) * Gp);
     d.h1 = (double *)take(sizeof(double) * (maxit + 3));
     d.h2 = (double *)take(sizeof(double) * (maxit + 3));
     d.scal = (double *)take(sizeof(double) * 8);
     d.counter = (unsigned *)take(sizeof(unsigned) * 4);
     return off;
+}
+
+// Batched solves take every back projector the tiled kernels apply: the
+// pixel-driven B, and A^T / B_tau when two bins per pixel suffice (rm = 0).
+bool back_model_batchable(const ctg_geom *g) {
+    if (g->back_model == CTG_BACK_PIXEL) return true;
+    std::vector<MatchedAngle> mt;
+    int rm = 0;
+    ctg_build_matched(g, mt, &rm);
+    return rm == 0;
+}
+
+// Upload the instance's angle tables (its slice must be planned with a base)
+// and, for B_tau, form the threshold tau max(A) (one device pass).
+int upload_tables(InstPlan &p, cudaStream_t st) {
+    std::vector<FwdAngle> fw;
+    std::vector<BackAngle> bk;
+    ctg_build_tables(&p.g, fw, bk);
+    BatchInst &d = p.d;
+    d.back_window = ctg_back_window(bk.data(), p.g.n_angles);
+    B_CK(cudaMemcpyAsync((void *)d.fwd, fw.data(), sizeof(FwdAngle) * fw.size(), cudaMemcpyHostToDevice, st));
+    B_CK(cudaMemcpyAsync((void *)d.back, bk.data(), sizeof(BackAngle) * bk.size(), cudaMemcpyHostToDevice, st));
+    if (d.mt) {
+        std::vector<MatchedAngle> mt;
+        int rm = 0;
+        ctg_build_matched(&p.g, mt, &rm);
+        B_CK(cudaMemcpyAsync((void *)d.mt, mt.data(), sizeof(MatchedAngle) * mt.size(), cudaMemcpyHostToDevice, st));
+        if (p.g.back_model == CTG_BACK_THRESHOLD) {
+            unsigned bits = 0;
+            B_CK(ctg_matched_max(p.g.N, p.g.n_angles, p.g.n_det, d.back, d.mt, rm, d.counter + 3, st));
+            B_CK(cudaMemcpyAsync(&bits, d.counter + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            B_CK(cudaStreamSynchronize(st));
+            float amax;
+            std::memcpy(&amax, &bits, sizeof(float));
+            d.back_thr = (float)(p.g.back_tau * (double)amax);
+        }
+    }
+    B_CK(cudaStreamSynchronize(st));       // the host vectors go out of scope
+    return CTG_OK;
+}
+
+// x = B b (+ add) with the instance's back projector
+cudaError_t back_inst(const InstPlan &p, const float *b, const float *add, float *x, cudaStream_t st) {
+    const BatchInst &d = p.d;
+    if (d.back_model == CTG_BACK_PIXEL)
+        return ctg_launch_back(b, CTG_BASIS_FP32, p.g.N, p.g.n_angles, p.g.n_det, d.back, d.back_window,
+                               add, x, st);
+    return ctg_launch_back_matched_tiled(b, CTG_BASIS_FP32, p.g.N, p.g.n_angles, p.g.n_det, d.back,
+                                         d.back_window, d.mt, d.back_thr, add, x, st);
 }
 
 RedScratch scratch_of(const BatchInst &d) {
@@ -222,7 +275,7 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
         p.g = geoms[i];
         p.o = opts[i];
         p.variant = variants[i];
-        if (!ctg_geom_valid(&p.g) || p.g.back_model != CTG_BACK_PIXEL || !ctg_opts_valid(&p.o) ||
+        if (!ctg_geom_valid(&p.g) || !back_model_batchable(&p.g) || !ctg_opts_valid(&p.o) ||
             p.o.basis_dtype != CTG_BASIS_FP32 || p.o.stop_rule != CTG_RULE_DP ||
             p.o.maxit > 1024 || (p.variant != CTG_AB && p.variant != CTG_BA)) {
             release(b);
@@ -267,10 +320,7 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
     for (int i = 0; rc == CTG_OK && i < n; ++i) {
         InstPlan &p = b->inst[i];
         plan_instance(p, b->ws + p.off);
-        rc = ck(cudaMemcpy((void *)p.d.fwd, fw[i].data(), sizeof(FwdAngle) * fw[i].size(), cudaMemcpyHostToDevice));
-        if (rc == CTG_OK)
-            rc = ck(cudaMemcpy((void *)p.d.back, bk[i].data(), sizeof(BackAngle) * bk[i].size(), cudaMemcpyHostToDevice));
-        p.d.back_window = ctg_back_window(bk[i].data(), p.g.n_angles);
+        rc = upload_tables(p, b->st);
     }
     if (rc == CTG_OK) {
         RoundSpec r{b->d_insts, n, b->d_maps, b->map_back, b->n_back, b->map_pad, b->n_pad,
@@ -312,8 +362,7 @@ int enqueue_start(InstPlan &p, const float *b, const float *x0, double *stage, c
         B_CK(ctg_sub_norm2(b, x0 ? d.vm : nullptr, d.vm, d.m, d.scal + 2, rs, st));
     } else {
         B_CK(ctg_sub_norm2(b, x0 ? d.vm : nullptr, d.r0m, d.m, d.scal + 4, rs, st));
-        B_CK(ctg_launch_back(d.r0m, CTG_BASIS_FP32, p.g.N, p.g.n_angles, p.g.n_det, d.back,
-                             d.back_window, nullptr, d.vn, st));
+        B_CK(back_inst(p, d.r0m, nullptr, d.vn, st));
         B_CK(ctg_sub_norm2(d.vn, nullptr, nullptr, d.n, d.scal + 2, rs, st));
     }
     B_CK(cudaMemcpyAsync(stage, d.scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
@@ -374,8 +423,7 @@ int enqueue_finish(const InstPlan &p, const BatchInst &d, const float *b, const 
     info->rho = d.rho;
     if (p.variant == CTG_AB) {
         B_CK(ctg_gemv(d.W, CTG_BASIS_FP32, d.ldw, d.m, k, d.y, nullptr, d.vm, st));
-        B_CK(ctg_launch_back(d.vm, CTG_BASIS_FP32, p.g.N, p.g.n_angles, p.g.n_det, d.back,
-                             d.back_window, x0, x, st));
+        B_CK(back_inst(p, d.vm, x0, x, st));
     } else {
         B_CK(ctg_gemv(d.W, CTG_BASIS_FP32, d.ldw, d.n, k, d.y, x0, x, st));
     }
@@ -509,7 +557,7 @@ void release_engine(ctg_engine *e) {
 }
 
 bool plan_valid(const ctg_geom *g, int variant, const ctg_opts *o) {
-    if (!ctg_geom_valid(g) || g->back_model != CTG_BACK_PIXEL || !ctg_opts_valid(o) ||
+    if (!ctg_geom_valid(g) || !back_model_batchable(g) || !ctg_opts_valid(o) ||
         o->basis_dtype != CTG_BASIS_FP32 || o->stop_rule != CTG_RULE_DP ||
         o->maxit > 1024 || (variant != CTG_AB && variant != CTG_BA))
         return false;
@@ -642,12 +690,12 @@ extern "C" int ctg_engine_submit(ctg_engine *e, const ctg_geom *g, int32_t varia
     s.ws = static_cast<char *>(ws);
     s.bytes = bytes;
     plan_instance(s.plan, s.ws);
-    std::vector<FwdAngle> fw;
-    std::vector<BackAngle> bk;
-    ctg_build_tables(g, fw, bk);
-    s.plan.d.back_window = ctg_back_window(bk.data(), g->n_angles);
-    B_CK(cudaMemcpyAsync((void *)s.plan.d.fwd, fw.data(), sizeof(FwdAngle) * fw.size(), cudaMemcpyHostToDevice, e->st));
-    B_CK(cudaMemcpyAsync((void *)s.plan.d.back, bk.data(), sizeof(BackAngle) * bk.size(), cudaMemcpyHostToDevice, e->st));
+    if (const int urc = upload_tables(s.plan, e->st)) {
+        cudaFreeAsync(s.ws, e->st);
+        cudaStreamSynchronize(e->st);
+        s = ctg_engine::Slot{};
+        return urc;
+    }
     s.b = b_dev;
     s.x0 = x0_dev;
     s.x = x_dev;

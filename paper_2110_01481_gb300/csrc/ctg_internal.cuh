@@ -247,7 +247,10 @@ struct BatchInst {
     double *h1, *h2, *scal;
     unsigned *counter;
     int G;                // blocks of this instance's CGS2 / vector passes
-    int pad_;
+    int back_model;       // CTG_BACK_*: the tiled pixel-driven B, A^T or B_tau
+    const MatchedAngle *mt;   // A^T / B_tau weights (back_model != CTG_BACK_PIXEL)
+    float back_thr;       // B_tau threshold tau max(A) (0: A^T)
+    int pad2_;
 };
 
 // Block maps: entry b of a batched launch's map is (instance, local block).
@@ -275,5 +278,8 @@ int ctg_vec_blocks(long long L);          // blocks of an E = 1 vector pass over
 
 // ---- host helpers shared by api.cu and batch.cu --------------------------
 bool ctg_geom_valid(const ctg_geom *g);
+// Matched-projector weights of a geometry (api.cu); *rm = extra bins beyond
+// the two nearest that the widest angle needs (0: the tiled kernels apply).
+void ctg_build_matched(const ctg_geom *g, std::vector<MatchedAngle> &mt, int *rm);
 bool ctg_opts_valid(const ctg_opts *o);
 void ctg_build_tables(const ctg_geom *g, std::vector<FwdAngle> &fw, std::vector<BackAngle> &bk);

@@ -378,8 +378,16 @@ batch_back_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ 
     const int tx = (I.N + kBT - 1) / kBT;
     const float *in = phase == CTG_PH_BACK_AB ? I.W + (size_t)(I.k - 1) * I.ldw
                                               : I.T + (size_t)(I.k - 1) * I.ldt;
-    pixel_back_tile<float>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn,
-                           mp.y % tx, mp.y / tx);
+    // the back projector of this instance (uniform over the cluster)
+    if (I.back_model == CTG_BACK_MATCHED)
+        pixel_back_tile<float, 1>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn,
+                                  mp.y % tx, mp.y / tx, I.mt, 0.0f);
+    else if (I.back_model == CTG_BACK_THRESHOLD)
+        pixel_back_tile<float, 2>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn,
+                                  mp.y % tx, mp.y / tx, I.mt, I.back_thr);
+    else
+        pixel_back_tile<float>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn,
+                               mp.y % tx, mp.y / tx);
 }
 
 __global__ void batch_pad_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ map) {

@@ -141,14 +141,20 @@ def test_lsqr_lsmr_workspace_is_independent_of_maxit(lib):
 
 def test_engine_admission_bytes_on_the_host(lib):
     """The serving engine sizes a request without touching the GPU: about
-    (maxit + 1) basis vectors; batched solves take the pixel-driven B only."""
+    (maxit + 1) basis vectors; unsupported options are refused."""
     from paper_2110_01481_gb300 import _native as nat
     g, o = _g(128, 180, 182), _o(40)
     rb = lambda g, v, o: lib.ctg_engine_request_bytes(ctypes.byref(g), v, ctypes.byref(o))
     ab, ba = rb(g, nat.CTG_AB, o), rb(g, nat.CTG_BA, o)
     assert 4 * 41 * 180 * 182 <= ab < 4 * 41 * 180 * 182 + (4 << 20)
     assert 4 * 41 * (128 * 128 + 180 * 182) <= ba          # W (n) and T = A W (m)
-    assert rb(_g(128, 180, 182, model=1), nat.CTG_AB, o) == 0
+    # A^T and B_tau batch when two detector bins per pixel suffice (pitch >= 1)
+    assert rb(_g(128, 180, 182, model=1), nat.CTG_AB, o) >= ab
+    assert rb(_g(128, 180, 182, model=2, tau=0.3), nat.CTG_BA, o) >= ba
+    assert rb(_g(128, 180, 364, ds=0.5, model=1), nat.CTG_AB, o) == 0
     assert rb(g, nat.CTG_LSQR, o) == 0
+    o.stop_rule = 1                                       # NCP: single solves only
+    assert rb(g, nat.CTG_AB, o) == 0
+    o.stop_rule = 0
     o.maxit = 1025
     assert rb(g, nat.CTG_AB, o) == 0

@@ -126,3 +126,41 @@ def test_batch_zero_iteration_stops(P, oracle_mod):
     assert res[0].iters == 0 and res[0].stop_reason == 1 and torch.equal(res[0].x, x0)
     assert res[1].iters == 0 and res[1].stop_reason == 2 and torch.count_nonzero(res[1].x) == 0
     assert res[2].iters > 0 and res[2].stop_reason == 1
+
+
+def test_batch_with_matched_and_thresholded_back_projectors(P, oracle_mod):
+    """Sec. 6.5's sweep as one batch: the same problem with B = A^T and B_tau
+    for several tau, in AB and BA form, each solve equal to its single-solve
+    run (stop and iterate) and, bit for bit, to itself run alone."""
+    import torch
+    O = oracle_mod
+    og, xt, b, enorm = _case(O, 96, 120, 180, 0.01, 3200)
+    bt = torch.tensor(b, device="cuda")
+    probs = []
+    for model, tb in (("pixel", 0.0), ("matched", 0.0), ("threshold", 0.1), ("threshold", 0.5)):
+        g = P.Geometry(96, 120, og.n_det, 0, 180, 1.0, model, tb)
+        for v in ("ab", "ba"):
+            probs.append({"geometry": g, "variant": v, "maxit": 40, "tau": 1.02, "noise_norm": enorm})
+    res = P.Batch(probs).solve([bt] * len(probs))
+    torch.cuda.synchronize()
+    for p, r in zip(probs, res):
+        fn = P.ab_gmres if p["variant"] == "ab" else P.ba_gmres
+        ref = fn(p["geometry"], bt, 40, tau=1.02, noise_norm=enorm)
+        assert r.stop_reason == ref.stop_reason
+        assert abs(r.iters - ref.iters) <= (1 if r.stop_reason == 1 else 0)
+        if r.iters == ref.iters:
+            d = (r.x - ref.x).double().norm() / ref.x.double().norm()
+            assert d.item() <= 1e-4, (p["geometry"].back_model, p["variant"], d.item())
+    for i in (3, 6):
+        alone = P.Batch([probs[i]]).solve([bt])[0]
+        assert alone.iters == res[i].iters and torch.equal(alone.x, res[i].x)
+    # an engine serving the sweep gives the same results as the batch
+    eng = P.Engine(4, 1 << 34)
+    pending, got = list(range(len(probs))), {}
+    while pending or eng.in_flight:
+        while pending and eng.submit(probs[pending[0]]["geometry"], bt, probs[pending[0]]["variant"], 40,
+                                     tau=1.02, noise_norm=enorm, tag=pending[0]) is not None:
+            pending.pop(0)
+        got.update(dict(eng.step(3)))
+    for i, r in enumerate(res):
+        assert got[i].iters == r.iters and torch.equal(got[i].x, r.x)
