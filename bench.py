@@ -789,10 +789,33 @@ def cpu_baseline(iters_per_solve: int):
     rb = O.ba_gmres(A, B, b, iters_per_solve, tau=TAU, noise_norm=enorm)
     dt = time.perf_counter() - t0
     its = ra["k"] + rb["k"]
-    return {"value": its / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"one AB-GMRES and one BA-GMRES solve of the same workload capped at "
-                      f"{iters_per_solve} iterations each ({its} iterations, {dt:.1f} s; "
-                      f"FP64, matrix-free C projectors with OpenMP, numpy Arnoldi)"}
+    out = {"value": its / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"one AB-GMRES and one BA-GMRES solve of the same workload capped at "
+                     f"{iters_per_solve} iterations each ({its} iterations, {dt:.1f} s; "
+                     f"FP64, matrix-free C projectors with OpenMP, numpy Arnoldi)"}
+    out["single_core"] = cpu_baseline_one_core(max(1, iters_per_solve // 8))
+    return out
+
+
+def cpu_baseline_one_core(iters_per_solve: int):
+    """The same oracle sample on one host core (OpenMP and BLAS threads = 1),
+    in a child process so the thread settings take effect."""
+    code = ("import json, sys, time; sys.path.insert(0, %r); import bench; "
+            "O, og, b, enorm = bench._oracle_instance(2000); "
+            "A = lambda v: O.forward(og, v); B = lambda v: O.backproject(og, v); "
+            "t0 = time.perf_counter(); "
+            "ra = O.ab_gmres(A, B, b, %d, tau=bench.TAU, noise_norm=enorm); "
+            "rb = O.ba_gmres(A, B, b, %d, tau=bench.TAU, noise_norm=enorm); "
+            "print(json.dumps([ra['k'] + rb['k'], time.perf_counter() - t0]))"
+            % (ROOT, iters_per_solve, iters_per_solve))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    its, dt = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": its / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{its} iterations ({iters_per_solve} per solve), {dt:.1f} s"}
 
 
 def run_reference(args):
