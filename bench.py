@@ -443,6 +443,31 @@ def serve_engine(P, torch, reqs, arrive, slots, budget, rounds):
     return done, iters, outs, max(done)
 
 
+def batched_pair(P, torch, g, b, enorm, steps):
+    """The same AB + BA step through the batched API (ctg_batch_solve: both
+    solves advance together, one launch per phase, rounds from a CUDA graph,
+    device-side Givens); L2 flushed between steps like the headline."""
+    probs = [{"geometry": g, "variant": v, "maxit": MAXIT, "tau": TAU, "noise_norm": enorm}
+             for v in ("ab", "ba")]
+    batch = P.Batch(probs)
+    outs = [torch.empty(g.n, device=b.device) for _ in probs]
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=b.device)
+    for _ in range(3):
+        batch.solve([b, b], outs=outs)
+    torch.cuda.synchronize()
+    total, its = 0.0, 0
+    for _ in range(steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = batch.solve([b, b], outs=outs)
+        torch.cuda.synchronize()
+        total += time.perf_counter() - t0
+        its += sum(r.iters for r in res)
+    return {"iterations_per_s": its / total, "ms_per_step": total / steps * 1e3,
+            "iterations_per_step": {"ab": res[0].iters, "ba": res[1].iters}}
+
+
 def serving_summary(P, torch, dev, count):
     """The served part of the metric, short: `count` requests of the served
     workload at Poisson arrivals of 0.9x the one-at-a-time capacity; p50/p99
@@ -760,6 +785,7 @@ def run_gpu(args):
         "roofline": roof,
         "arnoldi_roofline": arnoldi_roof,
     }
+    line["batched_pair"] = batched_pair(P, torch, g, b, enorm, args.steps)
     if world == 1 and not args.no_serve:
         line["serving"] = serving_summary(P, torch, dev, args.serve_quick)
     if world == 1 and not args.no_cpu_baseline:

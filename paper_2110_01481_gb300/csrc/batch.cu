@@ -513,7 +513,6 @@ struct ctg_engine {
         float *x = nullptr;
         ctg_info info{};
         long long tag = 0;
-        bool formed = false;    // x and the final residual already computed
     };
     ctg_ctx *ctx = nullptr;
     int max_slots = 0;
@@ -524,7 +523,6 @@ struct ctg_engine {
     BatchInst *h_pinned = nullptr;   // pinned mirror used for transfers
     int2 *d_maps = nullptr;
     size_t maps_cap = 0;
-    RoundSpec spec{};
     bool dirty = true;
     int running = 0;
     int *d_active = nullptr, *h_active = nullptr;
@@ -602,7 +600,6 @@ int recapture(ctg_engine *e) {
     }
     const int rc = capture_round(r, e->st, &e->round);
     if (rc) return rc;
-    e->spec = r;
     e->dirty = false;
     return CTG_OK;
 }
@@ -700,7 +697,6 @@ extern "C" int ctg_engine_submit(ctg_engine *e, const ctg_geom *g, int32_t varia
     s.x0 = x0_dev;
     s.x = x_dev;
     s.tag = tag;
-    s.formed = false;
     s.info = ctg_info{};
     s.info.history = history;
     double *stage = e->h_stage + 8 * slot;
