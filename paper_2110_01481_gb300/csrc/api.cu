@@ -290,6 +290,7 @@ struct ctg_ctx {
     // completion events of the pipelined solver loops (no timing)
     cudaEvent_t ev_h[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev_r[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_init = nullptr;   // a solve's start values are in the pinned scratch
     // projector tile shapes: 0 = autotuned per geometry, else forced
     int force_fwd_angles = 0, force_back_chunk = 0;
 };
@@ -698,6 +699,7 @@ int finish(const SolveCtx &sc, void *owned, int rc) {
 }
 
 int ensure_events(ctg_ctx *ctx) {
+    if (!ctx->ev_init) CTG_CK(cudaEventCreateWithFlags(&ctx->ev_init, cudaEventDisableTiming));
     for (int i = 0; i < kRing; ++i) {
         if (!ctx->ev_h[i]) CTG_CK(cudaEventCreateWithFlags(&ctx->ev_h[i], cudaEventDisableTiming));
         if (!ctx->ev_r[i]) CTG_CK(cudaEventCreateWithFlags(&ctx->ev_r[i], cudaEventDisableTiming));
@@ -756,6 +758,7 @@ int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
     const bool use_ncp = o->stop_rule == CTG_RULE_NCP;
     const bool dp = !use_ncp && o->noise_norm > 0.0;
     const double target = dp ? o->tau * o->noise_norm : 0.0;
+    double beta = 0.0;
     // r0 = b - A x0 (FP32, in vm0); beta = ||r0||
     if (x0) {
         CTG_CK(sc.forward(x0, sc.vm0()));
@@ -763,26 +766,20 @@ int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
     } else {
         CTG_CK(sc.sub_norm2(b, nullptr, sc.vm0(), m, sc.rs.scal + 2));
     }
-    double *hp;
-    int rc = sc.fetch(sc.rs.scal + 2, 1, &hp);
-    if (rc) return rc;
-    const double beta = std::sqrt(hp[0]);
-    if (info->history) info->history[0] = beta;
-    info->rho = beta;
-    info->resnorm = beta;
-    if ((dp && beta <= target) || beta == 0.0) {
-        info->stop_reason = beta == 0.0 && !(dp && beta <= target) ? CTG_STOP_BREAKDOWN : CTG_STOP_DP;
-        return copy_x0(sc, x0, x);
-    }
+    int rc = CTG_OK;
     std::vector<double> dncp;        // NCP distances d_0, d_1, ...
     if (use_ncp) {
         if ((rc = ensure_twiddles(sc.ge))) return rc;
         CTG_CK(sc.ncp(sc.vm0(), sc.rs.scal + 6));
-        if ((rc = sc.fetch(sc.rs.scal + 6, 1, &hp))) return rc;
-        dncp.push_back(hp[0]);
     }
-    CTG_CK(sc.scale(sc.vm0(), sc.rs.scal + 2, sc.Wcol(0), m));   // w_1 = r0 / beta
+    // ||r0||^2 (and d_0) are read back behind the first Arnoldi step, which
+    // needs no host value (w_1 = r0 / ||r0|| on the device; 0 when r0 = 0)
     if ((rc = ensure_events(sc.ctx))) return rc;
+    double *init = sc.pinned_scratch();
+    CTG_CK(cudaMemcpyAsync(init, sc.rs.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, sc.st));
+    if (use_ncp) CTG_CK(cudaMemcpyAsync(init + 1, sc.rs.scal + 6, sizeof(double), cudaMemcpyDeviceToHost, sc.st));
+    CTG_CK(cudaEventRecord(sc.ctx->ev_init, sc.st));
+    CTG_CK(sc.scale(sc.vm0(), sc.rs.scal + 2, sc.Wcol(0), m));   // w_1 = r0 / beta
     Pipeline pl{sc, o->maxit, sc.ctx->ev_h, sc.ctx->ev_r};
     // NCP: r_k = r0 - A B W_k y_k = W_{k+1} (beta e1 - H_k y_k), one read of
     // W, then its NCP distance, read back through the ring slot
@@ -808,9 +805,20 @@ int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
         CTG_CK(sc.cgs2(m, kk, sc.vm0()));
         return pl.after_step(kk);
     };
+    if ((rc = enqueue(1))) return rc;
+    CTG_CK(cudaEventSynchronize(sc.ctx->ev_init));
+    beta = std::sqrt(init[0]);
+    if (use_ncp) dncp.push_back(init[1]);
+    if (info->history) info->history[0] = beta;
+    info->rho = beta;
+    info->resnorm = beta;
+    if ((dp && beta <= target) || beta == 0.0) {       // the enqueued step is discarded
+        info->stop_reason = beta == 0.0 && !(dp && beta <= target) ? CTG_STOP_BREAKDOWN : CTG_STOP_DP;
+        return copy_x0(sc, x0, x);
+    }
     Givens gv(o->maxit, beta);
     std::vector<double> rhos{beta};
-    int next = 1, k = 0;
+    int next = 2, k = 0;
     for (k = 1; k <= o->maxit; ++k) {
         if (next == k && (rc = enqueue(next++))) return rc;
         if (next == k + 1 && k + 1 <= o->maxit && !(dp && predicts_stop(rhos, target)))
@@ -882,26 +890,20 @@ int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
     }
     CTG_CK(sc.back(sc.r0m(), nullptr, sc.vn0()));
     CTG_CK(sc.sub_norm2(sc.vn0(), nullptr, nullptr, n, sc.rs.scal + 2));
-    double *hp;
-    int rc = sc.fetch(sc.rs.scal + 2, 3, &hp);
-    if (rc) return rc;
-    const double beta = std::sqrt(hp[0]), res0 = std::sqrt(hp[2]);
-    if (info->history) info->history[0] = dp ? res0 : beta;
-    info->rho = beta;
-    info->resnorm = res0;
-    if ((dp && res0 <= target) || beta == 0.0) {
-        info->stop_reason = beta == 0.0 && !(dp && res0 <= target) ? CTG_STOP_BREAKDOWN : CTG_STOP_DP;
-        return copy_x0(sc, x0, x);
-    }
+    int rc = CTG_OK;
     std::vector<double> dncp;        // NCP distances d_0, d_1, ...
     if (use_ncp) {
         if ((rc = ensure_twiddles(sc.ge))) return rc;
         CTG_CK(sc.ncp(sc.r0m(), sc.rs.scal + 6));
-        if ((rc = sc.fetch(sc.rs.scal + 6, 1, &hp))) return rc;
-        dncp.push_back(hp[0]);
     }
-    CTG_CK(sc.scale(sc.vn0(), sc.rs.scal + 2, sc.Wcol(0), n));   // w_1 = r0 / beta
+    // ||B r||^2, ||r||^2 (and d_0) are read back behind the first Arnoldi
+    // step, which needs no host value
     if ((rc = ensure_events(sc.ctx))) return rc;
+    double *init = sc.pinned_scratch();
+    CTG_CK(cudaMemcpyAsync(init, sc.rs.scal + 2, sizeof(double) * 3, cudaMemcpyDeviceToHost, sc.st));
+    if (use_ncp) CTG_CK(cudaMemcpyAsync(init + 3, sc.rs.scal + 6, sizeof(double), cudaMemcpyDeviceToHost, sc.st));
+    CTG_CK(cudaEventRecord(sc.ctx->ev_init, sc.st));
+    CTG_CK(sc.scale(sc.vn0(), sc.rs.scal + 2, sc.Wcol(0), n));   // w_1 = r0 / beta
     Pipeline pl{sc, o->maxit, sc.ctx->ev_h, sc.ctx->ev_r};
     auto enqueue = [&](int kk) -> int {
         CTG_CK(sc.forward(sc.Wcol(kk - 1), sc.Tcol(kk - 1), sc.ly.dtype));  // t = A w_k, kept in T
@@ -937,9 +939,20 @@ int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_op
         CTG_CK(cudaEventRecord(pl.ev_r[kk % kRing], sc.st));
         return CTG_OK;
     };
+    if ((rc = enqueue(1))) return rc;
+    CTG_CK(cudaEventSynchronize(sc.ctx->ev_init));
+    const double beta = std::sqrt(init[0]), res0 = std::sqrt(init[2]);
+    if (use_ncp) dncp.push_back(init[3]);
+    if (info->history) info->history[0] = dp ? res0 : beta;
+    info->rho = beta;
+    info->resnorm = res0;
+    if ((dp && res0 <= target) || beta == 0.0) {        // the enqueued step is discarded
+        info->stop_reason = beta == 0.0 && !(dp && res0 <= target) ? CTG_STOP_BREAKDOWN : CTG_STOP_DP;
+        return copy_x0(sc, x0, x);
+    }
     Givens gv(o->maxit, beta);
     std::vector<double> y(o->maxit), res{res0}, rhos{beta};
-    int next = 1, k = 0;
+    int next = 2, k = 0;
     for (k = 1; k <= o->maxit; ++k) {
         if (next == k && (rc = enqueue(next++))) return rc;
         if (next == k + 1 && k + 1 <= o->maxit && !(dp && predicts_stop(res, target)))
