@@ -653,7 +653,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     ctx.set_timing(False)
     ctx.timing(reset=True)
-    total_ms, iters, per_solve = 0.0, 0, None
+    total_ms, iters, per_solve, step_ms = 0.0, 0, None, []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -665,7 +665,8 @@ def run_gpu(args):
             ra, rb = step(b)
             e1.record(stream)
             e1.synchronize()
-            total_ms += e0.elapsed_time(e1)
+            step_ms.append(e0.elapsed_time(e1))
+            total_ms += step_ms[-1]
             iters += ra.iters + rb.iters
             per_solve = (ra, rb)
     torch.cuda.synchronize()
@@ -767,6 +768,7 @@ def run_gpu(args):
                    "maxit": MAXIT, "tau": TAU, "noise": ETA,
                    "l2": "flushed between timed steps (258 MiB write)",
                    "parallelism": f"replicas x{world}"},
+        "step_ms": [round(t, 4) for t in step_ms],
         "iterations_per_step": {"ab": ra.iters, "ba": rb.iters},
         "stop": {"ab": ra.stop_reason, "ba": rb.stop_reason},
         "rel_error_vs_truth": {
