@@ -568,10 +568,15 @@ static int red_grid_max(int64_t L) {
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Partial rows: kmax + 2 for the separate passes; the fused step (k <= 64)
-// needs 2k + 2.
+// The fused step is used for k <= kFusedMaxK: measured at L = 522,000 it
+// takes 30 / 40 / 49 us at k = 4 / 8 / 12 against 47 / 49 / 51 us for the
+// separate passes, and loses from k = 16 on (60 vs 57 us), where streaming
+// the basis dominates and the separate passes stream it faster.
+constexpr int kFusedMaxK = 12;
+
+// Partial rows: kmax + 2 for the separate passes; the fused step needs 2k + 2.
 static size_t partial_rows(int kmax) {
-    const size_t fused = 2 * (size_t)(kmax < 64 ? kmax : 64) + 2;
+    const size_t fused = 2 * (size_t)(kmax < kFusedMaxK ? kmax : kFusedMaxK) + 2;
     return (size_t)kmax + 2 > fused ? (size_t)kmax + 2 : fused;
 }
 
@@ -612,10 +617,9 @@ int scale_blocks(int64_t L) {
     return blocks < 1 ? 1 : blocks;
 }
 
-// The fused step is used for k <= kFusedMaxK when the reduction scratch has
-// the 2k + 2 partial rows it needs and every block of the grid can be
-// resident at once (checked once per kernel instantiation).
-constexpr int kFusedMaxK = 64;
+// The fused step needs the 2k + 2 partial rows in the reduction scratch and
+// every block of its grid resident at once (checked once per kernel
+// instantiation).
 
 template <typename T, int E>
 int fused_resident_blocks() {
