@@ -180,13 +180,33 @@ cgs_pass_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict__
 // hold identical coefficients and the result is deterministic.
 __device__ __forceinline__ void reduce_rows(const float *__restrict__ partials, int row0, int nrows,
                                             int G, int Gp, double *out) {
+    // each warp takes four rows at a time and reads them as float4 (four
+    // blocks per load); the padding entries (block index >= G) are skipped
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int j = warp; j < nrows; j += kWarps) {
-        const float *pr = partials + (size_t)(row0 + j) * Gp;
-        double acc = 0.0;
-        for (int g = lane; g < G; g += 32) acc += (double)__ldcg(pr + g);
-        acc = warp_sum_d(acc);
-        if (lane == 0) out[j] = acc;
+    const int G4 = Gp / 4;
+    for (int j0 = warp * 4; j0 < nrows; j0 += kWarps * 4) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int g4 = lane; g4 < G4; g4 += 32) {
+            float4 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                v[q] = (j0 + q < nrows)
+                           ? __ldcg(reinterpret_cast<const float4 *>(partials + (size_t)(row0 + j0 + q) * Gp) + g4)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int b0 = 4 * g4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc[q] += (double)v[q].x;
+                if (b0 + 1 < G) acc[q] += (double)v[q].y;
+                if (b0 + 2 < G) acc[q] += (double)v[q].z;
+                if (b0 + 3 < G) acc[q] += (double)v[q].w;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double t = warp_sum_d(acc[q]);
+            if (lane == 0 && j0 + q < nrows) out[j0 + q] = t;
+        }
     }
 }
 
@@ -569,10 +589,10 @@ static int red_grid_max(int64_t L) {
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // The fused step is used for k <= kFusedMaxK: measured at L = 522,000 it
-// takes 30 / 40 / 49 us at k = 4 / 8 / 12 against 47 / 49 / 51 us for the
-// separate passes, and loses from k = 16 on (60 vs 57 us), where streaming
-// the basis dominates and the separate passes stream it faster.
-constexpr int kFusedMaxK = 12;
+// takes 29 / 40 / 75 / 151 us at k = 4 / 12 / 32 / 64 against 45 / 51 / 82 /
+// 153 us for the separate passes; the two meet near k = 64, where streaming
+// the basis dominates.
+constexpr int kFusedMaxK = 64;
 
 // Partial rows: kmax + 2 for the separate passes; the fused step needs 2k + 2.
 static size_t partial_rows(int kmax) {
