@@ -249,13 +249,17 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
             }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < na * W; e += kBThreads) {
-            const int k = e / W, w = e - k * W;
-            const int dd = __float_as_int(s_par[k].w) + w;
+        // one warp per staged angle, lanes along its window (no division)
+        for (int k = threadIdx.x >> 5; k < na; k += kBThreads / 32) {
+            const int org = __float_as_int(s_par[k].w);
             const T *brow = b + (size_t)(a0 + k) * n_det;
-            const float v0 = ((unsigned)dd < (unsigned)n_det) ? to_f(__ldg(brow + dd)) : 0.0f;
-            const float v1 = ((unsigned)(dd + 1) < (unsigned)n_det) ? to_f(__ldg(brow + dd + 1)) : 0.0f;
-            s_pairs[e] = kModel == 0 ? make_float2(v0, v1 - v0) : make_float2(v0, v1);
+            float2 *dst = s_pairs + k * W;
+            for (int w = threadIdx.x & 31; w < W; w += 32) {
+                const int dd = org + w;
+                const float v0 = ((unsigned)dd < (unsigned)n_det) ? to_f(__ldg(brow + dd)) : 0.0f;
+                const float v1 = ((unsigned)(dd + 1) < (unsigned)n_det) ? to_f(__ldg(brow + dd + 1)) : 0.0f;
+                dst[w] = kModel == 0 ? make_float2(v0, v1 - v0) : make_float2(v0, v1);
+            }
         }
         __syncthreads();
         const float2 *pw = s_pairs;
