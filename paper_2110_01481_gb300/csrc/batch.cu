@@ -235,6 +235,10 @@ void build_maps(const Plans &plans, const std::vector<int> &ids, std::vector<int
     });
 }
 
+// Capture one round into *out.  If *out already holds an executable graph
+// (an engine whose membership changed), it is updated in place when the
+// kernel sequence is the same, which is much cheaper than instantiating a new
+// one; otherwise it is replaced.
 int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out) {
     cudaGraph_t graph = nullptr;
     B_CK(ctg_batch_prepare(r.max_maxit));   // kernel attributes, set outside the capture
@@ -251,7 +255,15 @@ int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out) {
     if (e == cudaSuccess) e = ctg_batch_finish(r.insts, r.n_inst, r.d_active, st);
     cudaError_t e2 = cudaStreamEndCapture(st, &graph);
     if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+    if (e == cudaSuccess && *out != nullptr) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(*out, graph, &info) != cudaSuccess) {
+            cudaGetLastError();                      // topology changed: instantiate anew
+            cudaGraphExecDestroy(*out);
+            *out = nullptr;
+        }
+    }
+    if (e == cudaSuccess && *out == nullptr) e = cudaGraphInstantiate(out, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     return ck(e);
 }
@@ -594,10 +606,6 @@ int recapture(ctg_engine *e) {
     }
     r.d_active = e->d_active;
     B_CK(cudaStreamSynchronize(e->st));        // maps uploaded before they are captured
-    if (e->round) {
-        cudaGraphExecDestroy(e->round);
-        e->round = nullptr;
-    }
     const int rc = capture_round(r, e->st, &e->round);
     if (rc) return rc;
     e->dirty = false;
