@@ -6,7 +6,6 @@ aligned); calls are enqueued on torch's current stream of that device.
 from __future__ import annotations
 
 import ctypes
-import math
 from dataclasses import dataclass, field
 from typing import Optional
 
@@ -224,8 +223,9 @@ def _solve(fn, variant: str, g: Geometry, b: torch.Tensor, maxit: int,
     pws, nws = (None, 0)
     if workspace is not None:
         pws, nws = _dev_ptr(workspace, workspace.numel(), "workspace", torch.uint8), workspace.numel()
-    hist = (ctypes.c_double * (maxit + 1))(*([math.nan] * (maxit + 1)))
-    dncp = (ctypes.c_double * (maxit + 2))(*([math.nan] * (maxit + 2)))
+    # the library fills entries 0..iters (the arrays start zeroed)
+    hist = (ctypes.c_double * (maxit + 1))()
+    dncp = (ctypes.c_double * (maxit + 2))() if stop == "ncp" else None
     info = nat.CtgInfo(0, 0, 0.0, 0.0, hist, dncp)
     ctx = Context.get(dev)
     with torch.cuda.device(dev):
@@ -233,7 +233,8 @@ def _solve(fn, variant: str, g: Geometry, b: torch.Tensor, maxit: int,
                      ctypes.byref(info), _stream(dev)), name)
     nd = info.iters + (2 if info.stop_reason == nat.CTG_STOP_NCP else 1) if stop == "ncp" else 0
     return SolveResult(out, info.iters, info.stop_reason, info.resnorm, info.rho,
-                       list(hist[: info.iters + 1]), workspace, basis, list(dncp[:nd]))
+                       list(hist[: info.iters + 1]), workspace, basis,
+                       list(dncp[:nd]) if dncp is not None else [])
 
 
 def ab_gmres(g: Geometry, b: torch.Tensor, maxit: int, x0=None, tau: float = 1.0,
@@ -354,7 +355,7 @@ class Batch:
         if x0s is not None:
             px0 = (ctypes.c_void_p * n)(*[_dev_ptr(x0, p["geometry"].n, "x0") if x0 is not None else None
                                           for x0, p in zip(x0s, self.problems)])
-        hists = [(ctypes.c_double * (p["maxit"] + 1))(*([math.nan] * (p["maxit"] + 1)))
+        hists = [(ctypes.c_double * (p["maxit"] + 1))()
                  for p in self.problems]
         infos = (nat.CtgInfo * n)(*[nat.CtgInfo(0, 0, 0.0, 0.0, h) for h in hists])
         with torch.cuda.device(self.device):
@@ -415,7 +416,7 @@ class Engine:
             out = torch.empty(geometry.n, device=self.device, dtype=torch.float32)
         g = geometry.c()
         o = _opts(maxit, tau, noise_norm)
-        hist = (ctypes.c_double * (maxit + 1))(*([math.nan] * (maxit + 1)))
+        hist = (ctypes.c_double * (maxit + 1))()
         pb = _dev_ptr(b, geometry.m, "b")
         px = _dev_ptr(out, geometry.n, "x")
         px0 = _dev_ptr(x0, geometry.n, "x0") if x0 is not None else None
