@@ -249,8 +249,8 @@ int ctg_lsmr(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, const float *x
  * each), with the Hessenberg least-squares update (FP64 Givens) and the
  * discrepancy-principle stop (Sec. 6.4) done on the device.  A round is one
  * launch per phase for all solves and is replayed as a captured CUDA graph.
- * ctg_batch_create: geoms, variants, opts are arrays of n (FP32 basis only,
- * the CTG_RULE_DP stopping rule, maxit <= 1024, det_spacing >= ~0.25; any
+ * ctg_batch_create: geoms, variants, opts are arrays of n (any basis type,
+ * mixed freely across solves; the CTG_RULE_DP stopping rule, maxit <= 1024, det_spacing >= ~0.25; any
  * back projector, A^T and B_tau only where two detector bins per pixel
  * suffice, i.e. det_spacing >= max |cos|, |sin|, which holds for
  * det_spacing >= 1); the batch owns its device workspace

@@ -317,7 +317,8 @@ class Batch:
     replayed as a captured CUDA graph.
 
     problems: list of dicts with keys geometry (Geometry), variant ("ab" or
-    "ba"), maxit, and optionally tau, noise_norm."""
+    "ba"), maxit, and optionally tau, noise_norm, basis ("fp32", "bf16" or
+    "fp16": storage type of that solve's Krylov basis)."""
 
     def __init__(self, problems, device=None):
         if not problems:
@@ -328,7 +329,8 @@ class Batch:
         geoms = (nat.CtgGeom * n)(*[p["geometry"].c() for p in problems])
         variants = (ctypes.c_int32 * n)(*[nat.CTG_AB if p["variant"] == "ab" else nat.CTG_BA
                                           for p in problems])
-        opts = (nat.CtgOpts * n)(*[_opts(p["maxit"], p.get("tau", 1.0), p.get("noise_norm"))
+        opts = (nat.CtgOpts * n)(*[_opts(p["maxit"], p.get("tau", 1.0), p.get("noise_norm"),
+                                         p.get("basis", "fp32"))
                                    for p in problems])
         self.ctx = Context.get(self.device)
         self.handle = ctypes.c_void_p()
@@ -394,10 +396,10 @@ class Engine:
                                                   ctypes.byref(self.handle)), "ctg_engine_create")
 
     @staticmethod
-    def request_bytes(geometry, variant, maxit, tau=1.0, noise_norm=None) -> int:
+    def request_bytes(geometry, variant, maxit, tau=1.0, noise_norm=None, basis="fp32") -> int:
         """Device bytes one solve occupies while in flight (0: invalid)."""
         g = geometry.c()
-        o = _opts(maxit, tau, noise_norm)
+        o = _opts(maxit, tau, noise_norm, basis)
         v = nat.CTG_AB if variant == "ab" else nat.CTG_BA
         return int(nat.lib().ctg_engine_request_bytes(ctypes.byref(g), v, ctypes.byref(o)))
 
@@ -406,16 +408,17 @@ class Engine:
         return int(nat.lib().ctg_engine_in_flight(self.handle))
 
     def submit(self, geometry, b, variant="ab", maxit=100, tau=1.0, noise_norm=None,
-               x0=None, out=None, tag=None):
+               x0=None, out=None, tag=None, basis="fp32"):
         """Admit one solve; returns its tag, or None if the engine is busy
-        (no free slot, or not enough of the memory budget left)."""
+        (no free slot, or not enough of the memory budget left).  basis:
+        storage type of its Krylov basis ("fp32", "bf16" or "fp16")."""
         if tag is None:
             tag = self._next_tag
         self._next_tag = max(self._next_tag, int(tag) + 1)
         if out is None:
             out = torch.empty(geometry.n, device=self.device, dtype=torch.float32)
         g = geometry.c()
-        o = _opts(maxit, tau, noise_norm)
+        o = _opts(maxit, tau, noise_norm, basis)
         hist = (ctypes.c_double * (maxit + 1))()
         pb = _dev_ptr(b, geometry.m, "b")
         px = _dev_ptr(out, geometry.n, "x")

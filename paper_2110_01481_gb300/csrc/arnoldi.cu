@@ -414,7 +414,9 @@ __device__ __forceinline__ int vec_blocks_dev(long long L) {
     return (int)(((L + 3) / 4 + kThreads - 1) / kThreads);
 }
 
-template <bool UPDATE, bool DOTS, bool NORM>
+// T: the basis element type of the instances in this launch's map (one
+// launch per type, so that each kernel keeps the registers of its own type).
+template <typename T, bool UPDATE, bool DOTS, bool NORM>
 __global__ void __launch_bounds__(kThreads, 2)
 batch_cgs_pass_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
     const int2 mp = map[blockIdx.x];
@@ -423,17 +425,19 @@ batch_cgs_pass_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ ma
     float *q = I.variant == CTG_AB ? I.vm : I.vn;
     const double *coef = UPDATE ? (DOTS ? I.h1 : I.h2) : nullptr;
     double *red_out = DOTS ? (UPDATE ? I.h2 : I.h1) : I.scal + 1;
-    cgs_pass_body<float, 1, UPDATE, DOTS, NORM>(I.W, I.ldw, I.k, q, I.L, coef, I.partials,
-                                                I.counter, red_out, mp.y, I.G);
+    cgs_pass_body<T, 1, UPDATE, DOTS, NORM>(static_cast<const T *>(I.W), I.ldw, I.k, q, I.L, coef,
+                                            I.partials, I.counter, red_out, mp.y, I.G);
 }
 
+template <typename T>
 __global__ void batch_scale_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
     const int2 mp = map[blockIdx.x];
     BatchInst &I = insts[mp.x];
     if (!I.active) return;
     const float *q = I.variant == CTG_AB ? I.vm : I.vn;
-    scale_body<float>(q, I.scal + 1, I.W + (size_t)I.k * I.ldw, I.L, I.k, I.h1, I.h2,
-                      I.H + (size_t)(I.k - 1) * (I.maxit + 1), mp.y, I.G);
+    // w_{k+1}, rounded to the basis type
+    scale_body<T>(q, I.scal + 1, static_cast<T *>(I.W) + (size_t)I.k * I.ldw, I.L, I.k, I.h1, I.h2,
+                  I.H + (size_t)(I.k - 1) * (I.maxit + 1), mp.y, I.G);
 }
 
 // One warp per instance: FP64 Givens update of the Hessenberg least-squares
@@ -835,26 +839,42 @@ cudaError_t ctg_scale(const float *v, const double *nrm2, void *out, int dtype, 
 
 int ctg_vec_blocks(long long L) { return (int)(((L + 3) / 4 + kThreads - 1) / kThreads); }
 
+namespace {
+
+template <typename T>
+void launch_batch_cgs2(BatchInst *insts, const int2 *map, int nblocks, size_t smem, cudaStream_t st) {
+    batch_cgs_pass_kernel<T, false, true, true><<<nblocks, kThreads, smem, st>>>(insts, map);
+    batch_cgs_pass_kernel<T, true, true, false><<<nblocks, kThreads, smem, st>>>(insts, map);
+    batch_cgs_pass_kernel<T, true, false, true><<<nblocks, kThreads, smem, st>>>(insts, map);
+    batch_scale_kernel<T><<<nblocks, kThreads, 0, st>>>(insts, map);
+}
+
+template <typename T>
+cudaError_t prepare_batch_cgs2(size_t smem) {
+    cudaError_t err;
+    if ((err = ensure_smem(batch_cgs_pass_kernel<T, false, true, true>, smem)) != cudaSuccess) return err;
+    if ((err = ensure_smem(batch_cgs_pass_kernel<T, true, true, false>, smem)) != cudaSuccess) return err;
+    return ensure_smem(batch_cgs_pass_kernel<T, true, false, true>, smem);
+}
+
+}  // namespace
+
 cudaError_t ctg_batch_cgs2(BatchInst *insts, const int2 *map, int nblocks, int max_k,
-                           cudaStream_t st) {
+                           cudaStream_t st, int wtype) {
     if (nblocks <= 0) return cudaSuccess;
     const size_t smem = sizeof(float) * ((size_t)max_k + (size_t)kWarps * (max_k + 1));
-    auto k1 = batch_cgs_pass_kernel<false, true, true>;
-    auto k2 = batch_cgs_pass_kernel<true, true, false>;
-    auto k3 = batch_cgs_pass_kernel<true, false, true>;
-    k1<<<nblocks, kThreads, smem, st>>>(insts, map);
-    k2<<<nblocks, kThreads, smem, st>>>(insts, map);
-    k3<<<nblocks, kThreads, smem, st>>>(insts, map);
-    batch_scale_kernel<<<nblocks, kThreads, 0, st>>>(insts, map);
+    if (wtype == CTG_BASIS_BF16) launch_batch_cgs2<__nv_bfloat16>(insts, map, nblocks, smem, st);
+    else if (wtype == CTG_BASIS_FP16) launch_batch_cgs2<__half>(insts, map, nblocks, smem, st);
+    else launch_batch_cgs2<float>(insts, map, nblocks, smem, st);
     return cudaGetLastError();
 }
 
 cudaError_t ctg_batch_prepare(int max_k) {
     const size_t smem = sizeof(float) * ((size_t)max_k + (size_t)kWarps * (max_k + 1));
     cudaError_t err;
-    if ((err = ensure_smem(batch_cgs_pass_kernel<false, true, true>, smem)) != cudaSuccess) return err;
-    if ((err = ensure_smem(batch_cgs_pass_kernel<true, true, false>, smem)) != cudaSuccess) return err;
-    if ((err = ensure_smem(batch_cgs_pass_kernel<true, false, true>, smem)) != cudaSuccess) return err;
+    if ((err = prepare_batch_cgs2<float>(smem)) != cudaSuccess) return err;
+    if ((err = prepare_batch_cgs2<__nv_bfloat16>(smem)) != cudaSuccess) return err;
+    if ((err = prepare_batch_cgs2<__half>(smem)) != cudaSuccess) return err;
     return ensure_smem(batch_residual_kernel, sizeof(float) * (size_t)(max_k > 0 ? max_k : 1));
 }
 

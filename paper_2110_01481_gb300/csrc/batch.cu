@@ -72,7 +72,8 @@ size_t plan_instance(InstPlan &p, char *base) {
     d.ldt = (long long)ldt;
     d.G = ctg_vec_blocks(L);
     d.target = p.o.noise_norm > 0.0 ? p.o.tau * p.o.noise_norm : 0.0;
-    d.W = (float *)take(sizeof(float) * ldw * (size_t)(maxit + 1));
+    d.wtype = p.o.basis_dtype;
+    d.W = take(ctg_basis_bytes(p.o.basis_dtype) * ldw * (size_t)(maxit + 1));
     d.T = ba ? (float *)take(sizeof(float) * ldt * (size_t)(maxit + 1)) : nullptr;
     d.H = (double *)take(sizeof(double) * (size_t)(maxit + 1) * maxit);
     d.R = (double *)take(sizeof(double) * (size_t)maxit * maxit);
@@ -172,6 +173,8 @@ struct ctg_batch {
     int2 *d_maps = nullptr;
     int map_back = 0, map_pad = 0, map_fwd = 0, map_cgs = 0, map_m = 0;   // offsets
     int n_back = 0, n_pad = 0, n_fwd = 0, n_cgs = 0, n_m = 0;             // lengths
+    int map_b16 = 0, n_b16 = 0, map_h16 = 0, n_h16 = 0;   // AB instances with a 16-bit basis
+    int map_cgs_b16 = 0, n_cgs_b16 = 0, map_cgs_h16 = 0, n_cgs_h16 = 0;
     int max_window = 0, max_maxit = 0;
     int *d_active = nullptr;
     int *h_active = nullptr;     // pinned
@@ -206,6 +209,8 @@ struct RoundSpec {
     int n_inst;
     const int2 *maps;
     int map_back, n_back, map_pad, n_pad, map_fwd, n_fwd, map_cgs, n_cgs, map_m, n_m;
+    int map_b16, n_b16, map_h16, n_h16;    // AB back phase of instances with a BF16 / FP16 basis
+    int map_cgs_b16, n_cgs_b16, map_cgs_h16, n_cgs_h16;   // CGS2 of instances with a 16-bit basis
     int max_window, max_maxit;
     int *d_active;
 };
@@ -223,12 +228,22 @@ void build_maps(const Plans &plans, const std::vector<int> &ids, std::vector<int
         len = (int)maps.size() - off;
     };
     add(rs.map_back, rs.n_back, [](const InstPlan &p) { return ctg_back_tiles(p.g.N); });
+    add(rs.map_b16, rs.n_b16, [](const InstPlan &p) {
+        return p.variant == CTG_AB && p.o.basis_dtype == CTG_BASIS_BF16 ? ctg_back_tiles(p.g.N) : 0;
+    });
+    add(rs.map_h16, rs.n_h16, [](const InstPlan &p) {
+        return p.variant == CTG_AB && p.o.basis_dtype == CTG_BASIS_FP16 ? ctg_back_tiles(p.g.N) : 0;
+    });
     add(rs.map_pad, rs.n_pad, [](const InstPlan &p) { return ctg_pad_tiles(p.g.N); });
     add(rs.map_fwd, rs.n_fwd, [](const InstPlan &p) { return ctg_fwd_blocks(p.g.n_angles, p.g.n_det); });
-    add(rs.map_cgs, rs.n_cgs, [](const InstPlan &p) {
+    auto cgs_blocks = [](const InstPlan &p, int wtype) {
+        if (p.o.basis_dtype != wtype) return 0;
         return ctg_vec_blocks(p.variant == CTG_BA ? (long long)p.g.N * p.g.N
                                                   : (long long)p.g.n_angles * p.g.n_det);
-    });
+    };
+    add(rs.map_cgs, rs.n_cgs, [&](const InstPlan &p) { return cgs_blocks(p, CTG_BASIS_FP32); });
+    add(rs.map_cgs_b16, rs.n_cgs_b16, [&](const InstPlan &p) { return cgs_blocks(p, CTG_BASIS_BF16); });
+    add(rs.map_cgs_h16, rs.n_cgs_h16, [&](const InstPlan &p) { return cgs_blocks(p, CTG_BASIS_FP16); });
     add(rs.map_m, rs.n_m, [](const InstPlan &p) {
         return (p.variant == CTG_BA && p.o.noise_norm > 0.0)
                    ? ctg_vec_blocks((long long)p.g.n_angles * p.g.n_det) : 0;
@@ -246,10 +261,18 @@ int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out) {
     cudaError_t e = cudaSuccess;
     const int2 *M = r.maps;
     if (e == cudaSuccess) e = ctg_batch_back(r.insts, M + r.map_back, r.n_back, CTG_PH_BACK_AB, r.max_window, st);
+    if (e == cudaSuccess)
+        e = ctg_batch_back(r.insts, M + r.map_b16, r.n_b16, CTG_PH_BACK_AB, r.max_window, st, CTG_BASIS_BF16);
+    if (e == cudaSuccess)
+        e = ctg_batch_back(r.insts, M + r.map_h16, r.n_h16, CTG_PH_BACK_AB, r.max_window, st, CTG_BASIS_FP16);
     if (e == cudaSuccess) e = ctg_batch_pad(r.insts, M + r.map_pad, r.n_pad, st);
     if (e == cudaSuccess) e = ctg_batch_forward(r.insts, M + r.map_fwd, r.n_fwd, st);
     if (e == cudaSuccess) e = ctg_batch_back(r.insts, M + r.map_back, r.n_back, CTG_PH_BACK_BA, r.max_window, st);
     if (e == cudaSuccess) e = ctg_batch_cgs2(r.insts, M + r.map_cgs, r.n_cgs, r.max_maxit, st);
+    if (e == cudaSuccess)
+        e = ctg_batch_cgs2(r.insts, M + r.map_cgs_b16, r.n_cgs_b16, r.max_maxit, st, CTG_BASIS_BF16);
+    if (e == cudaSuccess)
+        e = ctg_batch_cgs2(r.insts, M + r.map_cgs_h16, r.n_cgs_h16, r.max_maxit, st, CTG_BASIS_FP16);
     if (e == cudaSuccess) e = ctg_batch_givens(r.insts, r.n_inst, st);
     if (e == cudaSuccess) e = ctg_batch_residual(r.insts, M + r.map_m, r.n_m, r.max_maxit, st);
     if (e == cudaSuccess) e = ctg_batch_finish(r.insts, r.n_inst, r.d_active, st);
@@ -288,7 +311,7 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
         p.o = opts[i];
         p.variant = variants[i];
         if (!ctg_geom_valid(&p.g) || !back_model_batchable(&p.g) || !ctg_opts_valid(&p.o) ||
-            p.o.basis_dtype != CTG_BASIS_FP32 || p.o.stop_rule != CTG_RULE_DP ||
+            p.o.stop_rule != CTG_RULE_DP ||
             p.o.maxit > 1024 || (p.variant != CTG_AB && p.variant != CTG_BA)) {
             release(b);
             return CTG_ERR_INVALID_ARG;
@@ -319,6 +342,10 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
     b->map_fwd = spec.map_fwd; b->n_fwd = spec.n_fwd;
     b->map_cgs = spec.map_cgs; b->n_cgs = spec.n_cgs;
     b->map_m = spec.map_m; b->n_m = spec.n_m;
+    b->map_b16 = spec.map_b16; b->n_b16 = spec.n_b16;
+    b->map_h16 = spec.map_h16; b->n_h16 = spec.n_h16;
+    b->map_cgs_b16 = spec.map_cgs_b16; b->n_cgs_b16 = spec.n_cgs_b16;
+    b->map_cgs_h16 = spec.map_cgs_h16; b->n_cgs_h16 = spec.n_cgs_h16;
     if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_maps, sizeof(int2) * (maps.empty() ? 1 : maps.size())));
     if (rc == CTG_OK && !maps.empty())
         rc = ck(cudaMemcpy(b->d_maps, maps.data(), sizeof(int2) * maps.size(), cudaMemcpyHostToDevice));
@@ -337,6 +364,8 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
     if (rc == CTG_OK) {
         RoundSpec r{b->d_insts, n, b->d_maps, b->map_back, b->n_back, b->map_pad, b->n_pad,
                     b->map_fwd, b->n_fwd, b->map_cgs, b->n_cgs, b->map_m, b->n_m,
+                    b->map_b16, b->n_b16, b->map_h16, b->n_h16,
+                    b->map_cgs_b16, b->n_cgs_b16, b->map_cgs_h16, b->n_cgs_h16,
                     b->max_window, b->max_maxit, b->d_active};
         rc = capture_round(r, b->st, &b->round);
     }
@@ -409,7 +438,7 @@ int activate(InstPlan &p, double *stage, ctg_info *info, cudaStream_t st, int *a
         return CTG_OK;
     }
     d.active = 1;
-    B_CK(ctg_scale(p.variant == CTG_AB ? d.vm : d.vn, d.scal + 2, d.W, CTG_BASIS_FP32, d.L, st));
+    B_CK(ctg_scale(p.variant == CTG_AB ? d.vm : d.vn, d.scal + 2, d.W, d.wtype, d.L, st));
     stage[6] = beta;
     B_CK(cudaMemcpyAsync(d.gg, &stage[6], sizeof(double), cudaMemcpyHostToDevice, st));
     *active_out = 1;
@@ -434,10 +463,10 @@ int enqueue_finish(const InstPlan &p, const BatchInst &d, const float *b, const 
     }
     info->rho = d.rho;
     if (p.variant == CTG_AB) {
-        B_CK(ctg_gemv(d.W, CTG_BASIS_FP32, d.ldw, d.m, k, d.y, nullptr, d.vm, st));
+        B_CK(ctg_gemv(d.W, d.wtype, d.ldw, d.m, k, d.y, nullptr, d.vm, st));
         B_CK(back_inst(p, d.vm, x0, x, st));
     } else {
-        B_CK(ctg_gemv(d.W, CTG_BASIS_FP32, d.ldw, d.n, k, d.y, x0, x, st));
+        B_CK(ctg_gemv(d.W, d.wtype, d.ldw, d.n, k, d.y, x0, x, st));
     }
     B_CK(ctg_launch_pad(x, CTG_BASIS_FP32, d.pad, p.g.N, pl, st));
     B_CK(ctg_launch_forward(d.pad, p.g.N, pl, p.g.n_angles, p.g.n_det, d.fwd, d.vm, st));
@@ -568,7 +597,7 @@ void release_engine(ctg_engine *e) {
 
 bool plan_valid(const ctg_geom *g, int variant, const ctg_opts *o) {
     if (!ctg_geom_valid(g) || !back_model_batchable(g) || !ctg_opts_valid(o) ||
-        o->basis_dtype != CTG_BASIS_FP32 || o->stop_rule != CTG_RULE_DP ||
+        o->stop_rule != CTG_RULE_DP ||
         o->maxit > 1024 || (variant != CTG_AB && variant != CTG_BA))
         return false;
     std::vector<FwdAngle> fw;

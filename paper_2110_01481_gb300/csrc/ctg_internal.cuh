@@ -229,8 +229,8 @@ struct BatchInst {
     double target;        // tau ||e|| (<= 0: no discrepancy stop)
     double rho;           // last GMRES residual |g_{k+1}|
     double resnorm;       // last ||b - A x_k|| (BA with the DP stop)
-    // buffers (FP32 basis)
-    float *W;             // (maxit + 1) x ldw
+    // buffers (the basis in FP32, BF16 or FP16; everything else FP32 / FP64)
+    void *W;              // (maxit + 1) x ldw elements of type wtype
     long long ldw;
     float *T;             // BA: (maxit + 1) x ldt, t_j = A w_j
     long long ldt;
@@ -250,13 +250,16 @@ struct BatchInst {
     int back_model;       // CTG_BACK_*: the tiled pixel-driven B, A^T or B_tau
     const MatchedAngle *mt;   // A^T / B_tau weights (back_model != CTG_BACK_PIXEL)
     float back_thr;       // B_tau threshold tau max(A) (0: A^T)
-    int pad2_;
+    int wtype;            // CTG_BASIS_*: element type of the stored basis W
 };
 
 // Block maps: entry b of a batched launch's map is (instance, local block).
 enum { CTG_PH_BACK_AB = 0, CTG_PH_PAD = 1, CTG_PH_FWD = 2, CTG_PH_BACK_BA = 3 };
+// wtype: CTG_BASIS_FP32 launches the kernel for AB instances with an FP32
+// basis and all BA instances; BF16 / FP16 launch it for the AB instances
+// whose basis has that type.
 cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int phase,
-                           int max_window, cudaStream_t st);
+                           int max_window, cudaStream_t st, int wtype = CTG_BASIS_FP32);
 cudaError_t ctg_batch_pad(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st);
 cudaError_t ctg_batch_forward(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st);
 // Local block counts of one instance for the maps above.
@@ -264,8 +267,10 @@ int ctg_back_tiles(int N);
 int ctg_pad_tiles(int N);
 int ctg_fwd_blocks(int n_angles, int n_det);
 int ctg_back_window_max();
+// the three CGS2 passes and the scaling for the instances in `map`, whose
+// basis has element type wtype
 cudaError_t ctg_batch_cgs2(BatchInst *insts, const int2 *map, int nblocks, int max_k,
-                           cudaStream_t st);
+                           cudaStream_t st, int wtype = CTG_BASIS_FP32);
 // Set the batched kernels' shared-memory attributes (before graph capture).
 cudaError_t ctg_batch_prepare(int max_k);
 cudaError_t ctg_batch_givens(BatchInst *insts, int n_inst, cudaStream_t st);

@@ -10,6 +10,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "ctg_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -373,25 +375,42 @@ pixel_back_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
 // ---- batched kernels: one launch for the same phase of every instance ----
 // map[blockIdx.x] = (instance, local block of that instance's own grid).
 
+// One instance's tile with its back projector.
+template <typename T>
+__device__ __forceinline__ void batch_back_tile(const BatchInst &I, const T *in, int bx, int by) {
+    if (I.back_model == CTG_BACK_MATCHED)
+        pixel_back_tile<T, 1>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn, bx, by,
+                              I.mt, 0.0f);
+    else if (I.back_model == CTG_BACK_THRESHOLD)
+        pixel_back_tile<T, 2>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn, bx, by,
+                              I.mt, I.back_thr);
+    else
+        pixel_back_tile<T>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn, bx, by);
+}
+
+// T = float: AB instances with an FP32 basis (back-projecting w_k) and all
+// BA instances (back-projecting the FP32 t_k = A w_k); T = BF16 / FP16: AB
+// instances whose basis is stored in that type (their own launch, so that
+// each kernel holds the tile code of one input type only).
+template <typename T>
 __global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
 batch_back_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ map, int phase) {
     const int2 mp = map[blockIdx.x];
     const BatchInst &I = insts[mp.x];
     // the same decision in all CTAs of the cluster (they share blockIdx.x)
     if (!I.active || ((phase == CTG_PH_BACK_AB) != (I.variant == CTG_AB))) return;
+    constexpr int kType = std::is_same<T, __nv_bfloat16>::value ? CTG_BASIS_BF16
+                          : std::is_same<T, __half>::value      ? CTG_BASIS_FP16
+                                                                : CTG_BASIS_FP32;
+    if (phase == CTG_PH_BACK_AB && I.wtype != kType) return;
     const int tx = (I.N + kBT - 1) / kBT;
-    const float *in = phase == CTG_PH_BACK_AB ? I.W + (size_t)(I.k - 1) * I.ldw
-                                              : I.T + (size_t)(I.k - 1) * I.ldt;
-    // the back projector of this instance (uniform over the cluster)
-    if (I.back_model == CTG_BACK_MATCHED)
-        pixel_back_tile<float, 1>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn,
-                                  mp.y % tx, mp.y / tx, I.mt, 0.0f);
-    else if (I.back_model == CTG_BACK_THRESHOLD)
-        pixel_back_tile<float, 2>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn,
-                                  mp.y % tx, mp.y / tx, I.mt, I.back_thr);
+    const T *in;
+    if constexpr (kType == CTG_BASIS_FP32)
+        in = phase == CTG_PH_BACK_AB ? static_cast<const float *>(I.W) + (size_t)(I.k - 1) * I.ldw
+                                     : I.T + (size_t)(I.k - 1) * I.ldt;
     else
-        pixel_back_tile<float>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn,
-                               mp.y % tx, mp.y / tx);
+        in = static_cast<const T *>(I.W) + (size_t)(I.k - 1) * I.ldw;
+    batch_back_tile(I, in, mp.y % tx, mp.y / tx);
 }
 
 __global__ void batch_pad_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
@@ -399,9 +418,19 @@ __global__ void batch_pad_kernel(const BatchInst *__restrict__ insts, const int2
     const BatchInst &I = insts[mp.x];
     if (!I.active) return;
     const int tx = (I.N + kPadTile - 1) / kPadTile;
-    // AB stages t = B w_k; BA stages w_k itself
-    const float *src = I.variant == CTG_AB ? I.vn : I.W + (size_t)(I.k - 1) * I.ldw;
-    pad_pairs_block<float>(src, I.pad, I.N, I.pad_stride, I.pad_border, mp.y % tx, mp.y / tx);
+    // AB stages t = B w_k; BA stages w_k itself, in its stored type
+    const size_t off = (size_t)(I.k - 1) * I.ldw;
+    if (I.variant == CTG_AB)
+        pad_pairs_block<float>(I.vn, I.pad, I.N, I.pad_stride, I.pad_border, mp.y % tx, mp.y / tx);
+    else if (I.wtype == CTG_BASIS_BF16)
+        pad_pairs_block<__nv_bfloat16>(static_cast<const __nv_bfloat16 *>(I.W) + off, I.pad, I.N,
+                                       I.pad_stride, I.pad_border, mp.y % tx, mp.y / tx);
+    else if (I.wtype == CTG_BASIS_FP16)
+        pad_pairs_block<__half>(static_cast<const __half *>(I.W) + off, I.pad, I.N, I.pad_stride,
+                                I.pad_border, mp.y % tx, mp.y / tx);
+    else
+        pad_pairs_block<float>(static_cast<const float *>(I.W) + off, I.pad, I.N, I.pad_stride,
+                               I.pad_border, mp.y % tx, mp.y / tx);
 }
 
 __global__ void __launch_bounds__(32 * kFwdAngles)
@@ -437,10 +466,16 @@ int ctg_fwd_blocks(int n_angles, int n_det) {
 int ctg_back_window_max() { return (40 * 1024) / (int)(sizeof(float2) * kBChunk); }
 
 cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int phase,
-                           int max_window, cudaStream_t st) {
+                           int max_window, cudaStream_t st, int wtype) {
     if (nblocks <= 0) return cudaSuccess;
     const size_t smem = sizeof(float2) * (size_t)kBChunk * max_window;
-    batch_back_kernel<<<dim3(nblocks, 1, kBSplit), kBThreads, smem, st>>>(insts, map, phase);
+    const dim3 grid(nblocks, 1, kBSplit);
+    if (wtype == CTG_BASIS_BF16)
+        batch_back_kernel<__nv_bfloat16><<<grid, kBThreads, smem, st>>>(insts, map, phase);
+    else if (wtype == CTG_BASIS_FP16)
+        batch_back_kernel<__half><<<grid, kBThreads, smem, st>>>(insts, map, phase);
+    else
+        batch_back_kernel<float><<<grid, kBThreads, smem, st>>>(insts, map, phase);
     return cudaGetLastError();
 }
 

@@ -156,5 +156,9 @@ def test_engine_admission_bytes_on_the_host(lib):
     o.stop_rule = 1                                       # NCP: single solves only
     assert rb(g, nat.CTG_AB, o) == 0
     o.stop_rule = 0
+    o.basis_dtype = nat.CTG_BASIS_BF16                    # a 16-bit basis halves the request
+    ab16 = rb(g, nat.CTG_AB, o)
+    assert 2 * 41 * 180 * 182 <= ab16 < ab - 4 * 41 * 180 * 182 // 2 + (1 << 20)
+    o.basis_dtype = nat.CTG_BASIS_FP32
     o.maxit = 1025
     assert rb(g, nat.CTG_AB, o) == 0

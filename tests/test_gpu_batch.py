@@ -164,3 +164,47 @@ def test_batch_with_matched_and_thresholded_back_projectors(P, oracle_mod):
         got.update(dict(eng.step(3)))
     for i, r in enumerate(res):
         assert got[i].iters == r.iters and torch.equal(got[i].x, r.x)
+
+
+def test_batch_with_16bit_bases(P, oracle_mod):
+    """Solves with FP32, BF16 and FP16 bases in one batch (AB and BA).  Each
+    equals itself run alone bit for bit; against the single-solve path with
+    the same basis type (another reduction order, so a 16-bit rounding may
+    fall the other way) the iterate at a fixed early k is within a few
+    storage unit roundoffs and the discrepancy stop within two steps at the
+    same error; a 16-bit basis about halves the batch's memory."""
+    import torch
+    O = oracle_mod
+    og, xt, b, enorm = _case(O, 96, 120, 180, 0.01, 3300)
+    bt = torch.tensor(b, device="cuda")
+    g = P.Geometry(96, 120, og.n_det)
+    unit = {"fp32": 2.0 ** -24, "bf16": 2.0 ** -8, "fp16": 2.0 ** -11}
+    probs = [{"geometry": g, "variant": v, "maxit": 6, "basis": t}
+             for t in ("fp32", "bf16", "fp16") for v in ("ab", "ba")]
+    res = P.Batch(probs).solve([bt] * len(probs))
+    torch.cuda.synchronize()
+    for p, r in zip(probs, res):
+        fn = P.ab_gmres if p["variant"] == "ab" else P.ba_gmres
+        ref = fn(g, bt, 6, basis=p["basis"])
+        assert r.iters == ref.iters == 6
+        d = ((r.x - ref.x).double().norm() / ref.x.double().norm()).item()
+        assert d <= max(1e-4, 10 * unit[p["basis"]]), (p["variant"], p["basis"], d)
+    for i in (2, 5):
+        alone = P.Batch([probs[i]]).solve([bt])[0]
+        assert torch.equal(alone.x, res[i].x)
+    # discrepancy stops (AB with either 16-bit type, BA with FP16: the cases
+    # whose stop the 16-bit basis keeps, see the precision tests)
+    xt_t = torch.tensor(xt, device="cuda", dtype=torch.float64)
+    dp = [{"geometry": g, "variant": v, "maxit": 60, "basis": t, "tau": 1.02, "noise_norm": enorm}
+          for v, t in (("ab", "bf16"), ("ab", "fp16"), ("ba", "fp16"))]
+    got = P.Batch(dp).solve([bt] * len(dp))
+    for p, r in zip(dp, got):
+        fn = P.ab_gmres if p["variant"] == "ab" else P.ba_gmres
+        ref = fn(g, bt, 60, tau=1.02, noise_norm=enorm, basis=p["basis"])
+        assert r.stop_reason == ref.stop_reason == 1 and abs(r.iters - ref.iters) <= 2
+        e_b = ((r.x.double() - xt_t).norm() / xt_t.norm()).item()
+        e_s = ((ref.x.double() - xt_t).norm() / xt_t.norm()).item()
+        assert abs(e_b - e_s) <= 0.08 * e_s
+    w32 = P.Batch([dict(probs[0], maxit=60)]).workspace_bytes
+    w16 = P.Batch([dict(probs[2], maxit=60)]).workspace_bytes
+    assert w16 < 0.6 * w32
