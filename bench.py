@@ -421,10 +421,12 @@ def serve_fifo(P, torch, reqs, arrive):
     return done, iters, outs, done[-1]
 
 
-def serve_engine(P, torch, reqs, arrive, slots, budget, rounds):
+def serve_engine(P, torch, reqs, arrive, slots, budget, rounds, basis="fp32"):
     """Continuous batching: arrived requests are admitted while slots and
     memory allow; every step advances all running solves by `rounds`
-    Arnoldi steps."""
+    Arnoldi steps.  basis "16": AB solves keep a BF16 basis (AB tolerates a
+    16-bit basis; BA does not reliably: an FP16 BA solve that does not reach
+    its discrepancy stop diverges, so BA stays FP32)."""
     eng = P.Engine(slots, budget)
     done, outs, iters = [0.0] * len(reqs), [None] * len(reqs), 0
     nxt, queue, finished = 0, [], 0
@@ -436,8 +438,9 @@ def serve_engine(P, torch, reqs, arrive, slots, budget, rounds):
             nxt += 1
         while queue:
             r = reqs[queue[0]]
+            btype = "bf16" if basis == "16" and r["variant"] == "ab" else "fp32"
             if eng.submit(r["geometry"], r["b"], r["variant"], r["maxit"], tau=r["tau"],
-                          noise_norm=r["noise_norm"], tag=queue[0]) is None:
+                          noise_norm=r["noise_norm"], tag=queue[0], basis=btype) is None:
                 break
             queue.pop(0)
         if eng.in_flight == 0:
@@ -541,9 +544,14 @@ def run_serve(args):
         rate = frac * capacity
         arrive = list(np.cumsum(gaps) / rate)
         row = {"rate_x_capacity": frac, "offered_req_per_s": rate}
-        for name, fn in (("engine", lambda a: serve_engine(P, torch, reqs, a, args.serve_slots,
-                                                            args.serve_budget_gb << 30, 4)),
-                         ("one_at_a_time", lambda a: serve_fifo(P, torch, reqs, a))):
+        servers = [("engine", lambda a: serve_engine(P, torch, reqs, a, args.serve_slots,
+                                                     args.serve_budget_gb << 30, 4))]
+        if args.serve_basis16:
+            servers.append(("engine_16bit_basis",
+                            lambda a: serve_engine(P, torch, reqs, a, args.serve_slots,
+                                                   args.serve_budget_gb << 30, 4, basis="16")))
+        servers.append(("one_at_a_time", lambda a: serve_fifo(P, torch, reqs, a)))
+        for name, fn in servers:
             done, iters, outs, span = fn(arrive)
             row[name] = dict(_latency_stats(arrive, done), served_req_per_s=len(reqs) / span,
                              iterations_per_s=iters / span, mean_rel_error_vs_truth=err(outs))
@@ -930,6 +938,8 @@ def main():
     ap.add_argument("--serve-rates", default="0.25,0.5,0.75,0.9,1.1")
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-budget-gb", type=int, default=96)
+    ap.add_argument("--serve-basis16", action="store_true",
+                    help="also serve with 16-bit Krylov bases for AB solves (BF16)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -250,11 +250,21 @@ void build_maps(const Plans &plans, const std::vector<int> &ids, std::vector<int
     });
 }
 
+// Which launches a round makes (a launcher skips a phase with no blocks):
+// two rounds with the same signature capture the same kernels in the same
+// order.
+unsigned round_signature(const RoundSpec &r) {
+    const int n[] = {r.n_back, r.n_b16, r.n_h16, r.n_pad, r.n_fwd, r.n_cgs, r.n_cgs_b16, r.n_cgs_h16, r.n_m};
+    unsigned sig = 0;
+    for (int i = 0; i < (int)(sizeof(n) / sizeof(n[0])); ++i) sig |= (n[i] > 0 ? 1u : 0u) << i;
+    return sig;
+}
+
 // Capture one round into *out.  If *out already holds an executable graph
-// (an engine whose membership changed), it is updated in place when the
-// kernel sequence is the same, which is much cheaper than instantiating a new
-// one; otherwise it is replaced.
-int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out) {
+// captured with the same kernel sequence (sig_prev == this round's
+// signature), it is updated in place, which is much cheaper than
+// instantiating a new one; otherwise it is replaced.
+int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out, unsigned sig_prev = ~0u) {
     cudaGraph_t graph = nullptr;
     B_CK(ctg_batch_prepare(r.max_maxit));   // kernel attributes, set outside the capture
     B_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -280,8 +290,8 @@ int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out) {
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess && *out != nullptr) {
         cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(*out, graph, &info) != cudaSuccess) {
-            cudaGetLastError();                      // topology changed: instantiate anew
+        if (sig_prev != round_signature(r) || cudaGraphExecUpdate(*out, graph, &info) != cudaSuccess) {
+            cudaGetLastError();                      // another kernel sequence: instantiate anew
             cudaGraphExecDestroy(*out);
             *out = nullptr;
         }
@@ -565,6 +575,7 @@ struct ctg_engine {
     int2 *d_maps = nullptr;
     size_t maps_cap = 0;
     bool dirty = true;
+    unsigned round_sig = ~0u;        // kernel sequence of the captured round
     int running = 0;
     int *d_active = nullptr, *h_active = nullptr;
     double *h_stage = nullptr;       // 8 per slot
@@ -635,7 +646,8 @@ int recapture(ctg_engine *e) {
     }
     r.d_active = e->d_active;
     B_CK(cudaStreamSynchronize(e->st));        // maps uploaded before they are captured
-    const int rc = capture_round(r, e->st, &e->round);
+    const int rc = capture_round(r, e->st, &e->round, e->round_sig);
+    e->round_sig = round_signature(r);
     if (rc) return rc;
     e->dirty = false;
     return CTG_OK;

@@ -151,3 +151,42 @@ def test_engine_zero_iteration_stops(P, oracle_mod):
     got = dict(eng.drain())
     assert got[7].iters == 0 and got[7].stop_reason == 1 and torch.equal(got[7].x, x0)
     assert got[8].iters == 0 and got[8].stop_reason == 2 and torch.count_nonzero(got[8].x) == 0
+
+
+def test_engine_stream_with_mixed_basis_types(P, oracle_mod):
+    """Solves whose Krylov bases are FP32, BF16 or FP16 join the engine at
+    different rounds (the round graph changes its kernel sequence as the
+    basis types present change); each result equals the same solve run
+    alone, bit for bit, and a 16-bit solve's admission costs about half."""
+    import torch
+    reqs = _requests(P, oracle_mod)
+    types = ["fp32", "bf16", "fp16", "bf16", "fp32", "fp16", "fp32", "bf16"]
+    for r, t in zip(reqs, types):
+        r["basis"] = t if r["variant"] == "ab" else ("fp32" if t == "bf16" else t)
+    bs = [torch.tensor(r["b"], device="cuda") for r in reqs]
+
+    def submit(eng, i):
+        r = reqs[i]
+        return eng.submit(r["geometry"], bs[i], r["variant"], r["maxit"], tau=r["tau"],
+                          noise_norm=r["noise_norm"], tag=i, basis=r["basis"])
+
+    alone = {}
+    eng1 = P.Engine(1, 1 << 34)
+    for i in range(len(reqs)):
+        assert submit(eng1, i) == i
+        alone.update(dict(eng1.drain(rounds=2)))
+    eng = P.Engine(3, 1 << 34)
+    mixed, pending, rounds = {}, list(range(len(reqs))), 0
+    while pending or eng.in_flight:
+        while pending and submit(eng, pending[0]) is not None:
+            pending.pop(0)
+        mixed.update(dict(eng.step(rounds=1 + rounds % 2)))
+        rounds += 1
+    for i in range(len(reqs)):
+        assert alone[i].iters == mixed[i].iters, i
+        assert torch.isfinite(mixed[i].x).all(), i
+        assert torch.equal(alone[i].x, mixed[i].x), i
+    g, r = reqs[0]["geometry"], reqs[0]
+    b32 = P.Engine.request_bytes(g, "ab", 40, basis="fp32")
+    b16 = P.Engine.request_bytes(g, "ab", 40, basis="bf16")
+    assert b16 < 0.65 * b32          # fixed-size buffers weigh more at 64^2
