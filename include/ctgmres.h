@@ -158,22 +158,35 @@ int ctg_backproject(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev,
                     float *x_dev, void *stream);
 
 /* Projector tile shapes.  By default the context times, at the first use of
- * a geometry, the forward projector with 8 and 4 angles per block and the
- * pixel-driven back projector with 16, 32 and 64 angles staged per pass
- * (CUDA events, 3 launches each on zero inputs, with temporary buffers of
- * about 5n + m floats), and keeps the fastest.  The candidates sum every ray
- * and every pixel in the same order, so results do not depend on the choice.
- * ctg_set_tiles forces shapes instead (0, 0 restores autotuning); it takes
- * effect at each geometry's next use.  ctg_get_tuning reports the shapes in
- * use for a geometry (tuning it first if needed) and the measured times. */
+ * a geometry, the forward projector with 8 and 4 angles per block (one angle
+ * per warp, 32 adjacent rays) and with 8 and 16 angles per block (4 angles
+ * per warp, 8 adjacent rays of each), and the pixel-driven back projector
+ * with 16, 32 and 64 angles staged per pass (CUDA events, 3 launches each on
+ * zero inputs, with temporary buffers of about 5n + m floats), and keeps the
+ * fastest.  The shapes with 4 angles per warp are candidates only where the
+ * host has checked that every warp's walk stays inside the staged image
+ * (adjacent angles of a fine angular sampling; not widely spaced ones).  The
+ * candidates sum every ray and every pixel in the same order, so results do
+ * not depend on the choice.  ctg_set_tiles forces shapes instead, the
+ * forward one with one angle per warp (0, 0 restores autotuning);
+ * ctg_set_fwd_tiles forces the forward shape as angles per block and per
+ * warp, (4, 1), (8, 1), (8, 4) or (16, 4) ((0, 0): autotuned; a shape with
+ * 4 angles per warp falls back to (8, 1) where the geometry does not allow
+ * it).  Both take effect at each geometry's next use and return
+ * CTG_ERR_INVALID_ARG for other values.  ctg_get_tuning reports the shapes
+ * in use for a geometry (tuning it first if needed) and the measured times
+ * (0 for a shape not timed). */
 typedef struct {
-    int32_t fwd_angles;       /* 4 or 8                                     */
+    int32_t fwd_angles;       /* angles per forward block: 4, 8 or 16       */
     int32_t back_chunk;       /* 16, 32 or 64                               */
     int32_t tuned;            /* 1 if chosen by timing                      */
-    float fwd_us[2];          /* measured: 8, 4 angles per block            */
+    float fwd_us[2];          /* measured: 8, 4 angles per block, 1 per warp */
     float back_us[3];         /* measured: 16, 32, 64 angles per pass       */
+    int32_t fwd_warp_angles;  /* angles per warp of the forward shape: 1, 4 */
+    float fwd_split_us[2];    /* measured: 8, 16 angles per block, 4 per warp */
 } ctg_tuning;
 int ctg_set_tiles(ctg_ctx *ctx, int32_t fwd_angles, int32_t back_chunk);
+int ctg_set_fwd_tiles(ctg_ctx *ctx, int32_t angles_per_block, int32_t angles_per_warp);
 int ctg_get_tuning(ctg_ctx *ctx, const ctg_geom *g, ctg_tuning *out);
 
 /* The NCP distance of Sec. 6.4's NCP criterion for a residual sinogram r
@@ -342,8 +355,9 @@ int ctg_cgs2_noalloc(const float *W_dev, int64_t ld_w, int64_t L, int32_t k,
  * When enabled, the solvers bracket each phase with CUDA events on the
  * solver's stream and accumulate its device time; kernel launches are
  * counted whether or not timing is enabled.  Phases: 0 forward projection
- * (image staging + Joseph A), 1 back projection (B), 2 Arnoldi CGS2 step,
- * 3 everything else (residual norms, iterate formation). */
+ * (the Joseph A kernel), 1 back projection (B), 2 Arnoldi CGS2 step,
+ * 3 everything else (the forward projector's image staging, residual
+ * norms, iterate formation). */
 typedef struct {
     double ms[4];             /* accumulated device milliseconds per phase */
     int64_t calls[4];         /* phase executions per phase                */

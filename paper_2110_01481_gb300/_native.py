@@ -41,7 +41,8 @@ class CtgGeom(ctypes.Structure):
 class CtgTuning(ctypes.Structure):
     _fields_ = [("fwd_angles", ctypes.c_int32), ("back_chunk", ctypes.c_int32),
                 ("tuned", ctypes.c_int32), ("fwd_us", ctypes.c_float * 2),
-                ("back_us", ctypes.c_float * 3)]
+                ("back_us", ctypes.c_float * 3), ("fwd_warp_angles", ctypes.c_int32),
+                ("fwd_split_us", ctypes.c_float * 2)]
 
 
 class CtgOpts(ctypes.Structure):
@@ -70,7 +71,7 @@ class CtgLayout(ctypes.Structure):
                 ("off_h", ctypes.c_size_t), ("total_bytes", ctypes.c_size_t)]
 
 
-EXPORTS = ("ctg_create", "ctg_destroy", "ctg_project", "ctg_backproject", "ctg_ncp_distance", "ctg_set_tiles", "ctg_get_tuning",
+EXPORTS = ("ctg_create", "ctg_destroy", "ctg_project", "ctg_backproject", "ctg_ncp_distance", "ctg_set_tiles", "ctg_set_fwd_tiles", "ctg_get_tuning",
            "ctg_workspace_bytes", "ctg_workspace_layout", "ctg_ab_gmres",
            "ctg_ba_gmres", "ctg_lsqr", "ctg_lsmr", "ctg_cgs2_scratch_bytes", "ctg_cgs2", "ctg_cgs2_noalloc",
            "ctg_set_timing", "ctg_get_timing", "ctg_status_string",
@@ -131,6 +132,8 @@ def _declare(lib):
     lib.ctg_engine_destroy.restype = None
     lib.ctg_set_tiles.argtypes = [vp, i32, i32]
     lib.ctg_set_tiles.restype = ctypes.c_int
+    lib.ctg_set_fwd_tiles.argtypes = [vp, i32, i32]
+    lib.ctg_set_fwd_tiles.restype = ctypes.c_int
     lib.ctg_get_tuning.argtypes = [vp, G, ctypes.POINTER(CtgTuning)]
     lib.ctg_get_tuning.restype = ctypes.c_int
     lib.ctg_ncp_distance.argtypes = [vp, G, vp, ctypes.POINTER(ctypes.c_double), vp]

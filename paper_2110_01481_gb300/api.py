@@ -79,9 +79,17 @@ class Context:
         out["kernels"] = int(t.kernels)
         return out
 
-    def set_tiles(self, fwd_angles: int = 0, back_chunk: int = 0) -> None:
-        """Force the projectors' tile shapes (0, 0: autotuned per geometry)."""
-        nat.check(nat.lib().ctg_set_tiles(self.handle, int(fwd_angles), int(back_chunk)), "ctg_set_tiles")
+    def set_tiles(self, fwd_angles: int = 0, back_chunk: int = 0, fwd_warp_angles: int = 1) -> None:
+        """Force the projectors' tile shapes (0, 0: autotuned per geometry).
+        The forward shape is fwd_angles angles per block with fwd_warp_angles
+        per warp: (4, 1), (8, 1), (8, 4) or (16, 4)."""
+        lib = nat.lib()
+        if fwd_warp_angles == 1:
+            nat.check(lib.ctg_set_tiles(self.handle, int(fwd_angles), int(back_chunk)), "ctg_set_tiles")
+        else:
+            nat.check(lib.ctg_set_tiles(self.handle, 0, int(back_chunk)), "ctg_set_tiles")
+            nat.check(lib.ctg_set_fwd_tiles(self.handle, int(fwd_angles), int(fwd_warp_angles)),
+                      "ctg_set_fwd_tiles")
 
     def tuning(self, g: "Geometry") -> dict:
         """Tile shapes in use for geometry g and the autotuner's timings (us)."""
@@ -89,8 +97,10 @@ class Context:
         with torch.cuda.device(self.device):
             nat.check(nat.lib().ctg_get_tuning(self.handle, ctypes.byref(g.c()), ctypes.byref(t)),
                       "ctg_get_tuning")
-        return {"fwd_angles": t.fwd_angles, "back_chunk": t.back_chunk, "tuned": bool(t.tuned),
-                "fwd_us": {8: t.fwd_us[0], 4: t.fwd_us[1]},
+        return {"fwd_angles": t.fwd_angles, "fwd_warp_angles": t.fwd_warp_angles,
+                "back_chunk": t.back_chunk, "tuned": bool(t.tuned),
+                "fwd_us": {"8x1": t.fwd_us[0], "4x1": t.fwd_us[1], "8x4": t.fwd_split_us[0],
+                           "16x4": t.fwd_split_us[1]},
                 "back_us": {16: t.back_us[0], 32: t.back_us[1], 64: t.back_us[2]}}
 
     def __del__(self):

@@ -154,11 +154,15 @@ struct GeomEntry {
     MatchedAngle *mt = nullptr; // matched / thresholded back projector
     int rm = 0;
     float thr = 0.0f;           // B_tau threshold tau * max(A) (0: A^T)
-    int fwd_angles = 8;         // tile shapes (autotuned unless forced)
+    int *fwd_order = nullptr;   // forward dispatch orders of the shapes, one after another
+    size_t fwd_order_off[kFwdShapes] = {};
+    bool fwd_split_ok = false;  // shapes with several angles per warp are safe here
+    int fwd_shape = 0;          // tile shapes (autotuned unless forced)
     int back_chunk = 32;
     bool tuned = false;
-    float fwd_us[2] = {0, 0}, back_us[3] = {0, 0, 0};   // measured: fwd 8, 4; back 16, 32, 64
+    float fwd_us[kFwdShapes] = {}, back_us[3] = {0, 0, 0};   // measured (0: not timed)
     unsigned long long last_use = 0;
+    const int *order_for(int shape) const { return fwd_order ? fwd_order + fwd_order_off[shape] : nullptr; }
 };
 
 // x = B b (+ add) with the geometry's back projector; b of type `btype`.
@@ -292,7 +296,7 @@ struct ctg_ctx {
     cudaEvent_t ev_r[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev_init = nullptr;   // a solve's start values are in the pinned scratch
     // projector tile shapes: 0 = autotuned per geometry, else forced
-    int force_fwd_angles = 0, force_back_chunk = 0;
+    int force_fwd_angles = 0, force_fwd_split = 1, force_back_chunk = 0;
 };
 
 namespace {
@@ -308,7 +312,9 @@ int fail_cuda(cudaError_t e) {
         if (e_ != cudaSuccess) return fail_cuda(e_);  \
     } while (0)
 
-constexpr size_t kMaxCachedGeoms = 4;
+// geometries a context keeps (tables, dispatch orders, tuned tile shapes);
+// enough for a served mix of request shapes to be tuned once each
+constexpr size_t kMaxCachedGeoms = 64;
 
 // Projector tile autotuner.  Candidate shapes leave every sum in the same
 // order (forward: angles per block, each ray still one warp; pixel-driven
@@ -342,12 +348,15 @@ int tune_geometry(GeomEntry *ge) {
         if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
         *us = ms * 1e3f / 3.0f;
     };
-    const int fwd_cand[2] = {8, 4};
-    for (int c = 0; c < 2; ++c)
+    for (int c = 0; c < kFwdShapes; ++c) {
+        ge->fwd_us[c] = 0.0f;
+        if (kFwdShapeSplit[c] > 1 && !ge->fwd_split_ok) continue;
         timed([&] {
             if (err == cudaSuccess)
-                err = ctg_launch_forward(pad, g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, bv, st, fwd_cand[c]);
+                err = ctg_launch_forward(pad, g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, bv, st, c,
+                                         ge->order_for(c));
         }, &ge->fwd_us[c]);
+    }
     const int back_cand[3] = {16, 32, 64};
     if (g->back_model == CTG_BACK_PIXEL)
         for (int c = 0; c < 3; ++c)
@@ -357,7 +366,10 @@ int tune_geometry(GeomEntry *ge) {
                                           ge->back_window, nullptr, xv, st, back_cand[c]);
             }, &ge->back_us[c]);
     if (err == cudaSuccess) {
-        ge->fwd_angles = ge->fwd_us[1] < ge->fwd_us[0] ? 4 : 8;
+        int fs = 0;
+        for (int c = 1; c < kFwdShapes; ++c)
+            if (ge->fwd_us[c] > 0.0f && ge->fwd_us[c] < ge->fwd_us[fs]) fs = c;
+        ge->fwd_shape = fs;
         int best = 1;
         if (g->back_model == CTG_BACK_PIXEL)
             for (int c = 0; c < 3; ++c)
@@ -376,7 +388,15 @@ int tune_geometry(GeomEntry *ge) {
 
 int apply_tiles(ctg_ctx *ctx, GeomEntry *ge) {
     if (ctx->force_fwd_angles || ctx->force_back_chunk) {
-        ge->fwd_angles = ctx->force_fwd_angles ? ctx->force_fwd_angles : 8;
+        // a forced shape with several angles per warp falls back to one
+        // angle per warp where the geometry does not allow it
+        int split = ctx->force_fwd_angles ? ctx->force_fwd_split : 1;
+        if (split > 1 && !ge->fwd_split_ok) split = 1;
+        int angles = ctx->force_fwd_angles ? ctx->force_fwd_angles : 8;
+        if (split == 1) angles = std::min(angles, 8);
+        ge->fwd_shape = 0;
+        for (int c = 0; c < kFwdShapes; ++c)
+            if (kFwdShapeAngles[c] == angles && kFwdShapeSplit[c] == split) ge->fwd_shape = c;
         ge->back_chunk = ctx->force_back_chunk ? ctx->force_back_chunk : 32;
         return CTG_OK;
     }
@@ -402,6 +422,7 @@ int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
         cudaFree(ctx->cache[victim].pad);
         cudaFree(ctx->cache[victim].mt);
         cudaFree(ctx->cache[victim].tw);
+        cudaFree(ctx->cache[victim].fwd_order);
         ctx->cache.erase(ctx->cache.begin() + victim);
     }
     std::vector<FwdAngle> fw;
@@ -418,6 +439,18 @@ int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
         err = cudaMemcpy(e.fwd, fw.data(), sizeof(FwdAngle) * fw.size(), cudaMemcpyHostToDevice);
     if (err == cudaSuccess)
         err = cudaMemcpy(e.back, bk.data(), sizeof(BackAngle) * bk.size(), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) {
+        e.fwd_split_ok = ctg_forward_split_safe(fw.data(), g->N, g->n_angles, g->n_det, e.pl, 4);
+        std::vector<int> all, o;
+        for (int c = 0; c < kFwdShapes; ++c) {
+            e.fwd_order_off[c] = all.size();
+            ctg_forward_order(fw.data(), g->N, g->n_angles, g->n_det, c, o);
+            all.insert(all.end(), o.begin(), o.end());
+        }
+        err = cudaMalloc(&e.fwd_order, sizeof(int) * all.size());
+        if (err == cudaSuccess)
+            err = cudaMemcpy(e.fwd_order, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice);
+    }
     if (err == cudaSuccess && g->back_model != CTG_BACK_PIXEL) {
         std::vector<MatchedAngle> mt;
         build_matched(g, mt, &e.rm);
@@ -442,6 +475,7 @@ int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
         cudaFree(e.fwd);
         cudaFree(e.back);
         cudaFree(e.mt);
+        cudaFree(e.fwd_order);
         return fail_cuda(err);
     }
     ctx->cache.push_back(e);
@@ -585,11 +619,15 @@ struct SolveCtx {
     }
 
     cudaError_t forward(const void *x, float *b, int xtype = CTG_BASIS_FP32) const {
-        return traced(ctx, 0, 2, st, [&] {
-            cudaError_t e = ctg_launch_pad(x, xtype, pad(), g->N, ge->pl, st);
-            if (e != cudaSuccess) return e;
+        // the image staging is traced as phase 3, so that phase 0 times the
+        // Joseph kernel alone
+        const cudaError_t e = traced(ctx, 3, 1, st, [&] {
+            return ctg_launch_pad(x, xtype, pad(), g->N, ge->pl, st);
+        });
+        if (e != cudaSuccess) return e;
+        return traced(ctx, 0, 1, st, [&] {
             return ctg_launch_forward(pad(), g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, b, st,
-                                      ge->fwd_angles);
+                                      ge->fwd_shape, ge->order_for(ge->fwd_shape));
         });
     }
     cudaError_t back(const void *b, const float *add, float *x, int btype = CTG_BASIS_FP32) const {
@@ -1180,6 +1218,7 @@ void ctg_destroy(ctg_ctx *ctx) {
     for (auto &e : ctx->cache) {
         cudaFree(e.fwd);
         cudaFree(e.back);
+        cudaFree(e.fwd_order);
         cudaFree(e.pad);
         cudaFree(e.mt);
         cudaFree(e.tw);
@@ -1199,11 +1238,12 @@ int ctg_project(ctg_ctx *ctx, const ctg_geom *g, const float *x_dev, float *b_de
         CTG_CK(cudaMalloc(&ge->pad, bytes));
         CTG_CK(cudaMemset(ge->pad, 0, bytes));
     }
-    CTG_CK(traced(ctx, 0, 2, st, [&] {
-        cudaError_t e = ctg_launch_pad(x_dev, CTG_BASIS_FP32, ge->pad, g->N, ge->pl, st);
-        if (e != cudaSuccess) return e;
+    CTG_CK(traced(ctx, 3, 1, st, [&] {
+        return ctg_launch_pad(x_dev, CTG_BASIS_FP32, ge->pad, g->N, ge->pl, st);
+    }));
+    CTG_CK(traced(ctx, 0, 1, st, [&] {
         return ctg_launch_forward(ge->pad, g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, b_dev, st,
-                                  ge->fwd_angles);
+                                  ge->fwd_shape, ge->order_for(ge->fwd_shape));
     }));
     return CTG_OK;
 }
@@ -1223,8 +1263,25 @@ int ctg_set_tiles(ctg_ctx *ctx, int32_t fwd_angles, int32_t back_chunk) {
         (back_chunk != 0 && back_chunk != 16 && back_chunk != 32 && back_chunk != 64))
         return CTG_ERR_INVALID_ARG;
     ctx->force_fwd_angles = fwd_angles;
+    ctx->force_fwd_split = 1;
     ctx->force_back_chunk = back_chunk;
     return CTG_OK;    // applied to every geometry at its next use
+}
+
+int ctg_set_fwd_tiles(ctg_ctx *ctx, int32_t angles_per_block, int32_t angles_per_warp) {
+    if (!ctx) return CTG_ERR_INVALID_ARG;
+    if (angles_per_block == 0 && angles_per_warp == 0) {
+        ctx->force_fwd_angles = 0;
+        ctx->force_fwd_split = 1;
+        return CTG_OK;
+    }
+    for (int c = 0; c < kFwdShapes; ++c)
+        if (kFwdShapeAngles[c] == angles_per_block && kFwdShapeSplit[c] == angles_per_warp) {
+            ctx->force_fwd_angles = angles_per_block;
+            ctx->force_fwd_split = angles_per_warp;
+            return CTG_OK;
+        }
+    return CTG_ERR_INVALID_ARG;
 }
 
 int ctg_get_tuning(ctg_ctx *ctx, const ctg_geom *g, ctg_tuning *out) {
@@ -1232,11 +1289,13 @@ int ctg_get_tuning(ctg_ctx *ctx, const ctg_geom *g, ctg_tuning *out) {
     GeomEntry *ge;
     const int rc = get_geom(ctx, g, &ge);
     if (rc) return rc;
-    out->fwd_angles = ge->fwd_angles;
+    out->fwd_angles = kFwdShapeAngles[ge->fwd_shape];
     out->back_chunk = ge->back_chunk;
     out->tuned = ge->tuned ? 1 : 0;
     for (int c = 0; c < 2; ++c) out->fwd_us[c] = ge->fwd_us[c];
     for (int c = 0; c < 3; ++c) out->back_us[c] = ge->back_us[c];
+    out->fwd_warp_angles = kFwdShapeSplit[ge->fwd_shape];
+    for (int c = 0; c < 2; ++c) out->fwd_split_us[c] = ge->fwd_us[2 + c];
     return CTG_OK;
 }
 

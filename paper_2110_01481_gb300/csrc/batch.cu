@@ -27,6 +27,7 @@ struct InstPlan {
     int variant;
     size_t off, bytes;         // this instance's slice of the batch workspace
     BatchInst d;               // device pointers filled in at create
+    std::vector<int> fwd_order;   // dispatch order of its forward blocks (longest first)
 };
 
 int ck(cudaError_t e) {
@@ -116,6 +117,7 @@ int upload_tables(InstPlan &p, cudaStream_t st) {
     std::vector<FwdAngle> fw;
     std::vector<BackAngle> bk;
     ctg_build_tables(&p.g, fw, bk);
+    ctg_forward_order(fw.data(), p.g.N, p.g.n_angles, p.g.n_det, 0, p.fwd_order);   // 8 angles x 1 per warp
     BatchInst &d = p.d;
     d.back_window = ctg_back_window(bk.data(), p.g.n_angles);
     B_CK(cudaMemcpyAsync((void *)d.fwd, fw.data(), sizeof(FwdAngle) * fw.size(), cudaMemcpyHostToDevice, st));
@@ -236,6 +238,13 @@ void build_maps(const Plans &plans, const std::vector<int> &ids, std::vector<int
     });
     add(rs.map_pad, rs.n_pad, [](const InstPlan &p) { return ctg_pad_tiles(p.g.N); });
     add(rs.map_fwd, rs.n_fwd, [](const InstPlan &p) { return ctg_fwd_blocks(p.g.n_angles, p.g.n_det); });
+    // each instance's forward blocks longest first (the result is the same
+    // in any order; the launch's tail is shorter)
+    for (int t = rs.map_fwd; t < rs.map_fwd + rs.n_fwd; ++t) {
+        const std::vector<int> &o = plans[maps[t].x].fwd_order;
+        if ((int)o.size() == ctg_fwd_blocks(plans[maps[t].x].g.n_angles, plans[maps[t].x].g.n_det))
+            maps[t].y = o[maps[t].y];
+    }
     auto cgs_blocks = [](const InstPlan &p, int wtype) {
         if (p.o.basis_dtype != wtype) return 0;
         return ctg_vec_blocks(p.variant == CTG_BA ? (long long)p.g.N * p.g.N

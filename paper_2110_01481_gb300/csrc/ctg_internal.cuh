@@ -52,9 +52,12 @@ struct MatchedAngle {
 // for columns j = -border .. N + border - 1 (zeros outside the image), so
 // that with m = 1 + f in [1, 2): v0 + dv * m = lerp(v, j + f).
 // The border is wide enough that every lane of a warp walking the union of
-// its 32 rays' chords stays inside the buffer (31 |P| + 6 >= the largest
-// distance of such a lane from the image); for very coarse detector pitches
-// the border is 2 and the kernel clamps the tap index instead.
+// its 32 rays' chords stays inside the buffer: such a lane is at most
+// 31 |P| + 6 from the image (31 rays apart from a lane whose range starts or
+// ends there, a step of margin on each side of that range, up to 3 steps
+// more where the walk starts at a multiple of 4, |D| <= 1), and the border
+// is 31 sqrt(2) ds + 10 or more; for very coarse detector pitches the border
+// is 2 and the kernel clamps the tap index instead.
 struct PadLayout {
     int border;            // zero pairs on each side of a row
     int stride;            // pairs per row = N + 2 * border
@@ -64,7 +67,7 @@ struct PadLayout {
 static inline PadLayout ctg_pad_layout(int N, double det_spacing) {
     PadLayout p;
     // |P| = ds / max(|cos|, |sin|) <= sqrt(2) ds
-    const double need = 31.0 * 1.41421356237309515 * det_spacing + 6.0;
+    const double need = 31.0 * 1.41421356237309515 * det_spacing + 10.0;
     p.clamp = need > 256.0;
     p.border = p.clamp ? 2 : (int)need + 1;
     p.stride = N + 2 * p.border;
@@ -77,17 +80,44 @@ static inline PadLayout ctg_pad_layout(int N, double det_spacing) {
 // forward projector.
 cudaError_t ctg_launch_pad(const void *x, int dtype, float2 *pad, int N, const PadLayout &pl,
                            cudaStream_t st);
-// fwd_angles: angles (warps) per block, 4 or 8 (a tile shape the context's
-// autotuner chooses; the result does not depend on it).
+// Forward projector block shapes, the tile autotuner's candidates: angles
+// per block x angles per warp (a warp holds 32 / angles-per-warp adjacent
+// rays of each of its angles).  Every shape gives the same result bit for
+// bit.  Shapes with several angles per warp are used only where
+// ctg_forward_split_safe holds for the geometry.
+constexpr int kFwdShapes = 4;
+constexpr int kFwdShapeAngles[kFwdShapes] = {8, 4, 8, 16};
+constexpr int kFwdShapeSplit[kFwdShapes] = {1, 1, 4, 4};
+// Angles per block of the batched forward projector (ctg_fwd_blocks): shape
+// 0, one angle per warp.
+constexpr int kBatchFwdAngles = 8;
+// shape: an index into the tables above.  order: NULL, or the device copy
+// of ctg_forward_order's permutation for the same shape.
 cudaError_t ctg_launch_forward(const float2 *pad, int N, const PadLayout &pl, int n_angles,
                                int n_det, const FwdAngle *tab, float *b, cudaStream_t st,
-                               int fwd_angles = 8);
+                               int shape = 0, const int *order = nullptr);
+// Blocks of one forward launch of `shape`.
+int ctg_fwd_shape_blocks(int shape, int n_angles, int n_det);
+// Dispatch order of the forward projector's blocks of `shape` (tile index
+// by * gx + bx, bx the ray group and by the angle group): longest estimated
+// walk first, which shortens the tail of the launch where the chord
+// lengths, and so the blocks' run times, differ.  From the host copy of the
+// angle table.
+void ctg_forward_order(const FwdAngle *host_tab, int N, int n_angles, int n_det, int shape,
+                       std::vector<int> &order);
+// Whether every lane of a warp holding `split` angles stays inside the
+// staged image's border over its warp's whole walk (checked at both ends of
+// a walk a few steps wider than the kernel's, in the kernel's fixed point).
+// Adjacent angles of a fine angular sampling pass; widely spaced ones, whose
+// chords differ, may not.
+bool ctg_forward_split_safe(const FwdAngle *host_tab, int N, int n_angles, int n_det,
+                            const PadLayout &pl, int split);
 // Detector-window width (in bins) that the tiled back projector stages per
 // angle, from the host copy of the angle table.
 int ctg_back_window(const BackAngle *host_tab, int n_angles);
 // x = B b (+ add, if add != NULL); b has element type `dtype`; window from
 // ctg_back_window
-// back_chunk: angles staged per pass, 16, 32 or 64 (tuned like fwd_angles;
+// back_chunk: angles staged per pass, 16, 32 or 64 (tuned like the forward shape;
 // the result does not depend on it).
 cudaError_t ctg_launch_back(const void *b, int dtype, int N, int n_angles, int n_det,
                             const BackAngle *tab, int window, const float *add, float *x,

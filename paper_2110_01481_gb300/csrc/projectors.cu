@@ -10,6 +10,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <cmath>
 #include <type_traits>
 
 #include "ctg_internal.cuh"
@@ -19,6 +21,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kPadTile = 32;
+constexpr int kPadRows = 8;    // staging blocks are kPadTile x kPadRows threads
 
 // Inputs that are Krylov basis vectors may be stored in BF16 or FP16.
 __device__ __forceinline__ float to_f(float v) { return v; }
@@ -37,23 +40,41 @@ __device__ __forceinline__ float2 lerp_pair(float v0, float v1) {
 template <typename T>
 __device__ __forceinline__ void pad_pairs_block(const T *__restrict__ x, float2 *__restrict__ pad,
                                                 int N, int stride, int border, int bx, int by) {
-    __shared__ float tile[kPadTile + 1][kPadTile + 2];
+    // odd pitch: the column reads of the transposed copy hit 32 distinct banks
+    __shared__ float tile[kPadTile + 1][kPadTile + 1];
     float2 *xp = pad + border, *xtp = pad + (size_t)N * stride + border;
     const int j0 = bx * kPadTile, i0 = by * kPadTile;
-    // tile[r][c] = x[i0 + r][j0 + c] for r, c in [0, 33) (0 outside)
-    for (int r = threadIdx.y; r <= kPadTile; r += blockDim.y)
-        for (int c = threadIdx.x; c <= kPadTile; c += blockDim.x) {
-            const int i = i0 + r, j = j0 + c;
-            tile[r][c] = (i < N && j < N) ? to_f(x[(size_t)i * N + j]) : 0.0f;
-        }
+    // tile[r][c] = x[i0 + r][j0 + c] for r, c in [0, 33) (0 outside); every
+    // load is issued before the first shared store
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPadTile + tx;
+    constexpr int kPasses = (kPadTile + kPadRows) / kPadRows;   // rows 0 .. kPadTile
+    float v[kPasses];
+#pragma unroll
+    for (int t = 0; t < kPasses; ++t) {
+        const int r = ty + t * kPadRows, i = i0 + r, j = j0 + tx;
+        v[t] = (r <= kPadTile && i < N && j < N) ? to_f(x[(size_t)i * N + j]) : 0.0f;
+    }
+    float edge = 0.0f;                    // column kPadTile, rows 0 .. kPadTile
+    if (tid <= kPadTile) {
+        const int i = i0 + tid, j = j0 + kPadTile;
+        edge = (i < N && j < N) ? to_f(x[(size_t)i * N + j]) : 0.0f;
+    }
+#pragma unroll
+    for (int t = 0; t < kPasses; ++t)
+        if (ty + t * kPadRows <= kPadTile) tile[ty + t * kPadRows][tx] = v[t];
+    if (tid <= kPadTile) tile[tid][kPadTile] = edge;
     __syncthreads();
-    for (int r = threadIdx.y; r < kPadTile; r += blockDim.y) {
+    // both copies written along their own rows, so each warp store is one
+    // contiguous run of 32 pairs
+    for (int r = threadIdx.y; r < kPadTile; r += kPadRows) {
         const int i = i0 + r, j = j0 + threadIdx.x;
-        if (i < N && j < N) {
-            const float v = tile[r][threadIdx.x];
-            xp[(size_t)i * stride + j] = lerp_pair(v, tile[r][threadIdx.x + 1]);
-            xtp[(size_t)j * stride + i] = lerp_pair(v, tile[r + 1][threadIdx.x]);
-        }
+        if (i < N && j < N)
+            xp[(size_t)i * stride + j] = lerp_pair(tile[r][threadIdx.x], tile[r][threadIdx.x + 1]);
+    }
+    for (int c = threadIdx.y; c < kPadTile; c += kPadRows) {
+        const int j = j0 + c, i = i0 + threadIdx.x;
+        if (i < N && j < N)
+            xtp[(size_t)j * stride + i] = lerp_pair(tile[threadIdx.x][c], tile[threadIdx.x + 1][c]);
     }
     // entry j = -1 of each row: (0 - x[0], x[0])
     if (bx == 0)
@@ -80,38 +101,65 @@ __device__ __forceinline__ float fx_frac(long long U) {
     return (float)f24 * (1.0f / 16777216.0f);
 }
 
+// floor(u) by the round-down magic-number add, for two positions at once in
+// packed FP32 pairs: t = u + M rounded down (M = 1.5 * 2^23, so the low
+// mantissa bits of t hold floor(u) for 0 <= u < 2^22) and f = u - (t - M),
+// exactly the scalar sequence per position, with half the instructions.
+__device__ __forceinline__ void floor_frac2(float u0, float u1, float &t0, float &t1, float &f0,
+                                            float &f1) {
+    asm("{\n\t.reg .b64 u, m, t, f;\n\t"
+        "mov.b64 u, {%4, %5};\n\t"
+        "mov.b64 m, {%6, %6};\n\t"
+        "add.rm.f32x2 t, u, m;\n\t"
+        "sub.rn.f32x2 f, t, m;\n\t"
+        "sub.rn.f32x2 f, u, f;\n\t"
+        "mov.b64 {%0, %1}, t;\n\t"
+        "mov.b64 {%2, %3}, f;\n\t}"
+        : "=f"(t0), "=f"(t1), "=f"(f0), "=f"(f1)
+        : "f"(u0), "f"(u1), "f"(12582912.0f));
+}
+
 __device__ __forceinline__ float one_plus_frac(unsigned lo) {
     // 1 + (top 23 bits of a 32-bit fraction), exactly, in [1, 2)
     return __uint_as_float(0x3F800000u | (lo >> 9));
 }
 
-constexpr int kFwdAngles = 8;   // warps per block, one angle each
+constexpr int kFwdAngles = kBatchFwdAngles;   // angles per batched block, one per warp
 constexpr int kFwdDepth = 8;    // image loads in flight per lane (a multiple of 4; 8 measured
                                 // 10% faster than 4 at 512^2, 16 no faster than 8)
 
 // b[a * n_det + d] = scale_a * sum_t lerp(img_a[t, .], u(d, t)).
-// A warp holds 32 adjacent rays of one angle and walks the union of their
+// A block holds kAngles consecutive angles; each warp holds kSplit of them
+// and 32 / kSplit adjacent rays of each, and walks the union of its rays'
 // chords' row ranges in lockstep, so each load instruction reads one image
-// row.  The walk position is 32.32 fixed point with the row stride folded
-// into the step, so its high word is the staged-pair index and its low word
-// the interpolation weight.  A lane outside its own chord reads zero pairs
-// in the border (or, with kClamp, a clamped index into the 2-pair border).
-template <bool kClamp, int kAngles = kFwdAngles>
+// row per angle.  The walk position is 32.32 fixed point with the row stride
+// folded into the step, so its high word is the staged-pair index and its
+// low word the interpolation weight.  A lane outside its own chord reads
+// zero pairs in the border (or, with kClamp, a clamped index into the
+// 2-pair border).  The walk starts at a multiple of 4 and step s adds into
+// accumulator s % 4, so a ray's sum depends on its own chord only: every
+// block shape, warp layout and load depth gives the same result bit for
+// bit.  kSplit > 1 needs the host's check (ctg_forward_split_safe) that
+// every lane stays inside the border.
+template <bool kClamp, int kAngles = kFwdAngles, int kSplit = 1>
 __device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ pad, int N,
                                                      int stride, int border, int n_angles,
                                                      int n_det, const FwdAngle *__restrict__ tab,
                                                      float *__restrict__ b, int bx, int by) {
+    constexpr int kRays = 32 / kSplit;
     const int lane = threadIdx.x & 31;
-    const int a = by * kAngles + (threadIdx.x >> 5);
-    if (a >= n_angles) return;                        // whole warp
-    const int d = bx * 32 + lane;
-    const FwdAngle t = tab[a];
+    const int a = by * kAngles + (threadIdx.x >> 5) * kSplit + lane / kRays;
+    const bool live = a < n_angles;
+    if (!__any_sync(0xffffffffu, live)) return;      // whole warp past the last angle
+    const int d = bx * kRays + lane % kRays;
+    const FwdAngle t = tab[live ? a : n_angles - 1];
     const float2 *img = pad + (t.row_driven ? 0 : (size_t)N * stride) + border;
 
     // this ray's steps whose taps can touch the image (-1 < u < N), with a
-    // one-step margin; rays past the last detector take an empty range
+    // one-step margin; rays past the last detector or angle take an empty
+    // range
     int lo = N, hi = -1;
-    if (d < n_det) {
+    if (live && d < n_det) {
         const float u0 = fmaf((float)d, t.pf, t.qf);
         if (fabsf(t.df) > 1e-20f) {
             const float r1 = (-1.0f - u0) / t.df, r2 = ((float)N - u0) / t.df;
@@ -123,14 +171,12 @@ __device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ 
             hi = N - 1;
         }
     }
-    const int wlo = __reduce_min_sync(0xffffffffu, lo);
+    const int wlo = __reduce_min_sync(0xffffffffu, lo) & ~3;
     const int whi = __reduce_max_sync(0xffffffffu, hi);
     float acc0 = 0.0f, acc1 = 0.0f;
     if (!kClamp) {
         const long long Ds = t.D + ((long long)stride << CTG_FXF_BITS);
         long long U = t.Q + (long long)d * t.P + (long long)wlo * Ds;
-        // step s adds into acc[(s - wlo) % 4] whatever the load depth, so the
-        // result does not depend on kFwdDepth
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         int s = wlo;
         for (; s + kFwdDepth - 1 <= whi; s += kFwdDepth) {
@@ -157,11 +203,14 @@ __device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ 
 #pragma unroll
             for (int i = 0; i < 4; ++i) acc[i] = fmaf(mw[i], p[i].y, acc[i] + p[i].x);
         }
-        for (; s <= whi; ++s) {
-            const float2 pa = __ldg(img + (int)(U >> CTG_FXF_BITS));
-            acc[0] = fmaf(one_plus_frac((unsigned)U), pa.y, acc[0] + pa.x);
-            U += Ds;
-        }
+        // at most three steps left, s a multiple of 4
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            if (s + i <= whi) {
+                const float2 pa = __ldg(img + (int)(U >> CTG_FXF_BITS));
+                acc[i] = fmaf(one_plus_frac((unsigned)U), pa.y, acc[i] + pa.x);
+                U += Ds;
+            }
         acc0 = acc[0] + acc[2];
         acc1 = acc[1] + acc[3];
     } else {
@@ -173,16 +222,20 @@ __device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ 
             U += t.D;
         }
     }
-    if (d < n_det) b[(size_t)a * n_det + d] = (acc0 + acc1) * t.scale;
+    if (live && d < n_det) b[(size_t)a * n_det + d] = (acc0 + acc1) * t.scale;
 }
 
-template <bool kClamp, int kAngles>
-__global__ void __launch_bounds__(32 * kAngles)
+// One block per (ray group bx, angle group by), on a 1-D grid of gx * gy
+// blocks; block i takes tile order[i] = by * gx + bx (order NULL: tile i),
+// so that the dispatch order can put the longest walks first.
+template <bool kClamp, int kAngles, int kSplit>
+__global__ void __launch_bounds__(32 * kAngles / kSplit)
 joseph_forward_kernel(const float2 *__restrict__ pad, int N, int stride, int border,
                       int n_angles, int n_det, const FwdAngle *__restrict__ tab,
-                      float *__restrict__ b) {
-    joseph_forward_block<kClamp, kAngles>(pad, N, stride, border, n_angles, n_det, tab, b, blockIdx.x,
-                                          blockIdx.y);
+                      float *__restrict__ b, const int *__restrict__ order, int gx) {
+    const int tile = order ? order[blockIdx.x] : (int)blockIdx.x;
+    joseph_forward_block<kClamp, kAngles, kSplit>(pad, N, stride, border, n_angles, n_det, tab, b,
+                                                  tile % gx, tile / gx);
 }
 
 // ---------------------------------------------------------------------------
@@ -230,7 +283,6 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
     const int per = (n_angles + kBSplit - 1) / kBSplit;
     const int a_begin = min(n_angles, rank * per), a_end = min(n_angles, a_begin + per);
     float acc[kBRows] = {0.f, 0.f, 0.f, 0.f};
-    const float kMagic = 12582912.0f;                 // 1.5 * 2^23
     for (int a0 = a_begin; a0 < a_end; a0 += kChunk) {
         const int na = min(kChunk, a_end - a0);
         __syncthreads();
@@ -268,16 +320,20 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
 #pragma unroll 2
         for (int k = 0; k < na; ++k, pw += W) {
             const float4 p = s_par[k];
-            float u = fmaf(fdi, p.y, fmaf(fdj, p.x, p.z));
             const float du = 8.0f * p.y;
+            float u[kBRows];
+            u[0] = fmaf(fdi, p.y, fmaf(fdj, p.x, p.z));
+#pragma unroll
+            for (int r = 1; r < kBRows; ++r) u[r] = u[r - 1] + du;
+            float tt[kBRows], ff[kBRows];
+#pragma unroll
+            for (int r = 0; r < kBRows; r += 2) floor_frac2(u[r], u[r + 1], tt[r], tt[r + 1], ff[r], ff[r + 1]);
             float4 wt = make_float4(0.f, 0.f, 0.f, 0.f);
             if constexpr (kModel != 0) wt = s_wt[k];
 #pragma unroll
             for (int r = 0; r < kBRows; ++r) {
-                // floor(u) by the round-down magic-number add (0 <= u < 2^22)
-                const float tt = __fadd_rd(u, kMagic);
-                const int idx = __float_as_int(tt) - 0x4B400000;
-                const float f = u - (tt - kMagic);
+                const int idx = __float_as_int(tt[r]) - 0x4B400000;
+                const float f = ff[r];
                 const float2 pr = pw[idx];
                 if constexpr (kModel == 0) {
                     acc[r] += fmaf(f, pr.y, pr.x);
@@ -290,7 +346,6 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
                     }
                     acc[r] = fmaf(w0, pr.x, fmaf(w1, pr.y, acc[r]));
                 }
-                u += du;
             }
         }
     }
@@ -460,7 +515,8 @@ int ctg_pad_tiles(int N) {
     return t * t;
 }
 int ctg_fwd_blocks(int n_angles, int n_det) {
-    return ((n_det + 31) / 32) * ((n_angles + kFwdAngles - 1) / kFwdAngles);
+    static_assert(kFwdShapeAngles[0] == kFwdAngles && kFwdShapeSplit[0] == 1, "batched forward shape");
+    return ctg_fwd_shape_blocks(0, n_angles, n_det);
 }
 // largest window the tiled back projector can stage in shared memory
 int ctg_back_window_max() { return (40 * 1024) / (int)(sizeof(float2) * kBChunk); }
@@ -481,7 +537,7 @@ cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int p
 
 cudaError_t ctg_batch_pad(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
-    batch_pad_kernel<<<nblocks, dim3(kPadTile, 8), 0, st>>>(insts, map);
+    batch_pad_kernel<<<nblocks, dim3(kPadTile, kPadRows), 0, st>>>(insts, map);
     return cudaGetLastError();
 }
 
@@ -504,7 +560,7 @@ int ctg_back_window(const BackAngle *host_tab, int n_angles) {
 
 cudaError_t ctg_launch_pad(const void *x, int dtype, float2 *pad, int N, const PadLayout &pl,
                            cudaStream_t st) {
-    dim3 grid((N + kPadTile - 1) / kPadTile, (N + kPadTile - 1) / kPadTile), block(kPadTile, 8);
+    dim3 grid((N + kPadTile - 1) / kPadTile, (N + kPadTile - 1) / kPadTile), block(kPadTile, kPadRows);
     switch (dtype) {
         case CTG_BASIS_FP32:
             pad_pairs_kernel<<<grid, block, 0, st>>>(static_cast<const float *>(x), pad, N, pl.stride,
@@ -525,28 +581,124 @@ cudaError_t ctg_launch_pad(const void *x, int dtype, float2 *pad, int N, const P
 
 namespace {
 
-template <int kAngles>
+template <int kAngles, int kSplit>
 void launch_forward_t(const float2 *pad, int N, const PadLayout &pl, int n_angles, int n_det,
-                      const FwdAngle *tab, float *b, cudaStream_t st) {
-    const dim3 grid((n_det + 31) / 32, (n_angles + kAngles - 1) / kAngles);
+                      const FwdAngle *tab, float *b, cudaStream_t st, const int *order) {
+    constexpr int kRays = 32 / kSplit;
+    const int gx = (n_det + kRays - 1) / kRays, gy = (n_angles + kAngles - 1) / kAngles;
+    const unsigned grid = (unsigned)gx * (unsigned)gy;
     if (pl.clamp)
-        joseph_forward_kernel<true, kAngles><<<grid, 32 * kAngles, 0, st>>>(pad, N, pl.stride, pl.border,
-                                                                            n_angles, n_det, tab, b);
+        joseph_forward_kernel<true, kAngles, kSplit><<<grid, 32 * kAngles / kSplit, 0, st>>>(
+            pad, N, pl.stride, pl.border, n_angles, n_det, tab, b, order, gx);
     else
-        joseph_forward_kernel<false, kAngles><<<grid, 32 * kAngles, 0, st>>>(pad, N, pl.stride, pl.border,
-                                                                             n_angles, n_det, tab, b);
+        joseph_forward_kernel<false, kAngles, kSplit><<<grid, 32 * kAngles / kSplit, 0, st>>>(
+            pad, N, pl.stride, pl.border, n_angles, n_det, tab, b, order, gx);
+}
+
+// walk range [lo, hi] of ray d of angle t, as joseph_forward_block
+// estimates it (host arithmetic; may differ from the device's by a step)
+void ray_range(const FwdAngle &t, int N, int d, int &lo, int &hi) {
+    const float u0 = (float)d * t.pf + t.qf;
+    lo = N;
+    hi = -1;
+    if (std::fabs(t.df) > 1e-20f) {
+        const float r1 = (-1.0f - u0) / t.df, r2 = ((float)N - u0) / t.df;
+        const float tlo = std::max(std::min(r1, r2), -2.0f);
+        const float thi = std::min(std::max(r1, r2), (float)N + 1);
+        lo = std::max(0, (int)std::floor(tlo) - 1);
+        hi = std::min(N - 1, (int)std::ceil(thi) + 1);
+    } else if (u0 > -2.0f && u0 < (float)N + 1.0f) {
+        lo = 0;
+        hi = N - 1;
+    }
+}
+
+// union walk range of rays d0 .. d1 - 1 of angle t: a ray's range ends are
+// clamped linear functions of d, so the first and last ray give it (all
+// rays when the walk is parallel to the detector, D = 0)
+void group_range(const FwdAngle &t, int N, int d0, int d1, int &wlo, int &whi) {
+    const bool all = !(std::fabs(t.df) > 1e-20f);
+    wlo = N;
+    whi = -1;
+    for (int d = d0; d < d1; d += (all || d + 1 == d1) ? 1 : d1 - 1 - d) {
+        int lo, hi;
+        ray_range(t, N, d, lo, hi);
+        wlo = std::min(wlo, lo);
+        whi = std::max(whi, hi);
+    }
 }
 
 }  // namespace
 
 cudaError_t ctg_launch_forward(const float2 *pad, int N, const PadLayout &pl, int n_angles,
                                int n_det, const FwdAngle *tab, float *b, cudaStream_t st,
-                               int fwd_angles) {
-    // every ray is summed by one warp in the same order whatever the block
-    // shape, so the result does not depend on fwd_angles
-    if (fwd_angles == 4) launch_forward_t<4>(pad, N, pl, n_angles, n_det, tab, b, st);
-    else launch_forward_t<8>(pad, N, pl, n_angles, n_det, tab, b, st);
+                               int shape, const int *order) {
+    // every ray's sum depends on its own chord only, so the result depends
+    // on neither the shape nor the dispatch order
+    switch (shape) {
+        case 1: launch_forward_t<4, 1>(pad, N, pl, n_angles, n_det, tab, b, st, order); break;
+        case 2: launch_forward_t<8, 4>(pad, N, pl, n_angles, n_det, tab, b, st, order); break;
+        case 3: launch_forward_t<16, 4>(pad, N, pl, n_angles, n_det, tab, b, st, order); break;
+        default: launch_forward_t<8, 1>(pad, N, pl, n_angles, n_det, tab, b, st, order); break;
+    }
     return cudaGetLastError();
+}
+
+int ctg_fwd_shape_blocks(int shape, int n_angles, int n_det) {
+    const int rays = 32 / kFwdShapeSplit[shape], angles = kFwdShapeAngles[shape];
+    return ((n_det + rays - 1) / rays) * ((n_angles + angles - 1) / angles);
+}
+
+void ctg_forward_order(const FwdAngle *tab, int N, int n_angles, int n_det, int shape,
+                       std::vector<int> &order) {
+    const int A = kFwdShapeAngles[shape], S = kFwdShapeSplit[shape], R = 32 / S;
+    const int gx = (n_det + R - 1) / R, gy = (n_angles + A - 1) / A;
+    // work of a tile: the steps of its warps' lockstep walks plus a fixed
+    // cost per warp
+    std::vector<long long> cost((size_t)gx * gy, 0);
+    for (int a0 = 0; a0 < n_angles; a0 += S)
+        for (int bx = 0; bx < gx; ++bx) {
+            int wlo = N, whi = -1;
+            for (int a = a0; a < std::min(n_angles, a0 + S); ++a) {
+                int lo, hi;
+                group_range(tab[a], N, bx * R, std::min(n_det, bx * R + R), lo, hi);
+                wlo = std::min(wlo, lo);
+                whi = std::max(whi, hi);
+            }
+            cost[(size_t)(a0 / A) * gx + bx] += (whi >= wlo ? whi - (wlo & ~3) + 1 : 0) + 16;
+        }
+    order.resize(cost.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+}
+
+bool ctg_forward_split_safe(const FwdAngle *tab, int N, int n_angles, int n_det, const PadLayout &pl,
+                            int split) {
+    if (pl.clamp) return true;                      // indices are clamped
+    const int R = 32 / split;
+    for (int a0 = 0; a0 < n_angles; a0 += split)
+        for (int d0 = 0; d0 < n_det; d0 += R) {
+            int wlo = N, whi = -1;
+            for (int a = a0; a < std::min(n_angles, a0 + split); ++a) {
+                int lo, hi;
+                group_range(tab[a], N, d0, std::min(n_det, d0 + R), lo, hi);
+                wlo = std::min(wlo, lo);
+                whi = std::max(whi, hi);
+            }
+            if (whi < wlo) continue;
+            // the device's range may differ from this estimate by a step:
+            // check a wider one
+            const int s_lo = std::max(0, (wlo & ~3) - 4), s_hi = std::min(N - 1, whi + 4);
+            for (int l = 0; l < 32; ++l) {
+                const FwdAngle &t = tab[std::min(n_angles - 1, a0 + l / R)];
+                const long long d = d0 + l % R;
+                for (const long long s : {(long long)s_lo, (long long)s_hi}) {
+                    const long long j = (t.Q + d * t.P + s * t.D) >> CTG_FXF_BITS;
+                    if (j < -pl.border || j > N - 1 + pl.border) return false;
+                }
+            }
+        }
+    return true;
 }
 
 namespace {

@@ -107,9 +107,12 @@ def test_rejects_bad_arguments(P):
 
 
 def test_tile_autotuner_is_result_invariant(P):
-    """The autotuned tile shapes (angles per forward block, angles staged per
-    back-projection pass) change the speed only: every shape gives the same
-    projections bit for bit, and the tuner reports the timed candidates."""
+    """The autotuned tile shapes (angles per forward block and per warp,
+    angles staged per back-projection pass) change the speed only: every
+    shape gives the same projections bit for bit, and the tuner reports the
+    timed candidates.  The shapes with 4 angles per warp are timed where the
+    angular sampling is fine enough for them (90 angles over 180 degrees) and
+    fall back to one angle per warp elsewhere (45 angles over 360)."""
     import torch
     ctx = P.Context.get(torch.device("cuda", 0))
     cases = [P.Geometry(200, 90, 283), P.Geometry(96, 37, 150, 0, 120), P.Geometry(64, 45, 91, 10, 360, 1.3)]
@@ -120,13 +123,21 @@ def test_tile_autotuner_is_result_invariant(P):
             y = torch.randn(g.m, device="cuda", generator=gen)
             ctx.set_tiles(0, 0)
             t = ctx.tuning(g)
-            assert t["tuned"] and t["fwd_angles"] in (4, 8) and t["back_chunk"] in (16, 32, 64)
-            assert all(v > 0 for v in t["fwd_us"].values()) and all(v > 0 for v in t["back_us"].values())
+            assert t["tuned"] and t["back_chunk"] in (16, 32, 64)
+            assert (t["fwd_angles"], t["fwd_warp_angles"]) in ((4, 1), (8, 1), (8, 4), (16, 4))
+            assert t["fwd_us"]["8x1"] > 0 and t["fwd_us"]["4x1"] > 0
+            assert all(v > 0 for v in t["back_us"].values())
+            if g.n_angles == 90:
+                assert t["fwd_us"]["8x4"] > 0 and t["fwd_us"]["16x4"] > 0
             ref_a, ref_b = P.project(g, x), P.backproject(g, y)
-            for fa, bc in ((8, 32), (4, 16), (4, 64), (8, 64), (8, 16)):
-                ctx.set_tiles(fa, bc)
-                assert ctx.tuning(g)["fwd_angles"] == fa and ctx.tuning(g)["back_chunk"] == bc
-                assert torch.equal(P.project(g, x), ref_a), (g, fa)
+            for fa, fw, bc in ((8, 1, 32), (4, 1, 16), (4, 1, 64), (8, 1, 64), (8, 1, 16), (8, 4, 32),
+                               (16, 4, 64)):
+                ctx.set_tiles(fa, bc, fw)
+                tt = ctx.tuning(g)
+                split_ok = tt["fwd_us"]["8x4"] > 0
+                want = (fa, fw) if fw == 1 or split_ok else (8, 1)
+                assert (tt["fwd_angles"], tt["fwd_warp_angles"]) == want and tt["back_chunk"] == bc
+                assert torch.equal(P.project(g, x), ref_a), (g, fa, fw)
                 assert torch.equal(P.backproject(g, y), ref_b), (g, bc)
     finally:
         ctx.set_tiles(0, 0)
