@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <memory>
 #include <vector>
 
 #include "ctg_internal.cuh"
@@ -21,14 +22,40 @@ size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 size_t rup(size_t v, size_t m) { return (v + m - 1) / m * m; }
 int padded4(int G) { return (G + 3) & ~3; }
 
+// Forward projector plan of a geometry: whether warps of several angles
+// are safe for it, and the dispatch orders (longest walk first) of its
+// blocks in the batched shapes 0 and kBatchFwdSplitShape.
+struct FwdPlan {
+    bool split_ok = false;
+    std::vector<int> order[2];
+};
+
 struct InstPlan {
     ctg_geom g;
     ctg_opts o;
     int variant;
     size_t off, bytes;         // this instance's slice of the batch workspace
     BatchInst d;               // device pointers filled in at create
-    std::vector<int> fwd_order;   // dispatch order of its forward blocks (longest first)
+    std::shared_ptr<const FwdPlan> fwd;   // forward projector plan (shared per geometry)
 };
+
+// Geometries with the same forward projector (its tables do not depend on
+// the back projector model).
+bool same_fwd_geom(const ctg_geom &a, const ctg_geom &b) {
+    return a.N == b.N && a.n_angles == b.n_angles && a.n_det == b.n_det &&
+           a.angle_start_deg == b.angle_start_deg && a.angle_range_deg == b.angle_range_deg &&
+           a.det_spacing == b.det_spacing;
+}
+
+// Forward projector plan of a geometry, from its host angle table.
+std::shared_ptr<const FwdPlan> plan_forward(const ctg_geom &g, const std::vector<FwdAngle> &fw) {
+    auto f = std::make_shared<FwdPlan>();
+    const PadLayout pl = ctg_pad_layout(g.N, g.det_spacing);
+    f->split_ok = ctg_forward_split_safe(fw.data(), g.N, g.n_angles, g.n_det, pl, 4);
+    ctg_forward_order(fw.data(), g.N, g.n_angles, g.n_det, 0, f->order[0]);
+    ctg_forward_order(fw.data(), g.N, g.n_angles, g.n_det, kBatchFwdSplitShape, f->order[1]);
+    return f;
+}
 
 int ck(cudaError_t e) {
     return e == cudaSuccess ? CTG_OK : (e == cudaErrorMemoryAllocation ? CTG_ERR_OOM : CTG_ERR_CUDA);
@@ -117,7 +144,7 @@ int upload_tables(InstPlan &p, cudaStream_t st) {
     std::vector<FwdAngle> fw;
     std::vector<BackAngle> bk;
     ctg_build_tables(&p.g, fw, bk);
-    ctg_forward_order(fw.data(), p.g.N, p.g.n_angles, p.g.n_det, 0, p.fwd_order);   // 8 angles x 1 per warp
+    if (!p.fwd) p.fwd = plan_forward(p.g, fw);
     BatchInst &d = p.d;
     d.back_window = ctg_back_window(bk.data(), p.g.n_angles);
     B_CK(cudaMemcpyAsync((void *)d.fwd, fw.data(), sizeof(FwdAngle) * fw.size(), cudaMemcpyHostToDevice, st));
@@ -178,6 +205,7 @@ struct ctg_batch {
     int map_b16 = 0, n_b16 = 0, map_h16 = 0, n_h16 = 0;   // AB instances with a 16-bit basis
     int map_cgs_b16 = 0, n_cgs_b16 = 0, map_cgs_h16 = 0, n_cgs_h16 = 0;
     int max_window = 0, max_maxit = 0;
+    int fwd_shape = 0;
     int *d_active = nullptr;
     int *h_active = nullptr;     // pinned
     double *h_stage = nullptr;   // pinned: per instance scal[0..7]
@@ -215,6 +243,7 @@ struct RoundSpec {
     int map_cgs_b16, n_cgs_b16, map_cgs_h16, n_cgs_h16;   // CGS2 of instances with a 16-bit basis
     int max_window, max_maxit;
     int *d_active;
+    int fwd_shape;    // forward shape of the round (ctg_batch_forward)
 };
 
 // Build the block maps of instances `ids` (indices into the instance array).
@@ -237,13 +266,20 @@ void build_maps(const Plans &plans, const std::vector<int> &ids, std::vector<int
         return p.variant == CTG_AB && p.o.basis_dtype == CTG_BASIS_FP16 ? ctg_back_tiles(p.g.N) : 0;
     });
     add(rs.map_pad, rs.n_pad, [](const InstPlan &p) { return ctg_pad_tiles(p.g.N); });
-    add(rs.map_fwd, rs.n_fwd, [](const InstPlan &p) { return ctg_fwd_blocks(p.g.n_angles, p.g.n_det); });
+    // one forward shape for the round: several angles per warp when every
+    // instance allows it
+    bool split = !ids.empty();
+    for (int i : ids) split = split && plans[i].fwd && plans[i].fwd->split_ok;
+    rs.fwd_shape = split ? kBatchFwdSplitShape : 0;
+    const int fs = rs.fwd_shape;
+    add(rs.map_fwd, rs.n_fwd, [fs](const InstPlan &p) { return ctg_fwd_shape_blocks(fs, p.g.n_angles, p.g.n_det); });
     // each instance's forward blocks longest first (the result is the same
     // in any order; the launch's tail is shorter)
     for (int t = rs.map_fwd; t < rs.map_fwd + rs.n_fwd; ++t) {
-        const std::vector<int> &o = plans[maps[t].x].fwd_order;
-        if ((int)o.size() == ctg_fwd_blocks(plans[maps[t].x].g.n_angles, plans[maps[t].x].g.n_det))
-            maps[t].y = o[maps[t].y];
+        const InstPlan &p = plans[maps[t].x];
+        if (!p.fwd) continue;
+        const std::vector<int> &o = p.fwd->order[split ? 1 : 0];
+        if ((int)o.size() == ctg_fwd_shape_blocks(fs, p.g.n_angles, p.g.n_det)) maps[t].y = o[maps[t].y];
     }
     auto cgs_blocks = [](const InstPlan &p, int wtype) {
         if (p.o.basis_dtype != wtype) return 0;
@@ -266,7 +302,7 @@ unsigned round_signature(const RoundSpec &r) {
     const int n[] = {r.n_back, r.n_b16, r.n_h16, r.n_pad, r.n_fwd, r.n_cgs, r.n_cgs_b16, r.n_cgs_h16, r.n_m};
     unsigned sig = 0;
     for (int i = 0; i < (int)(sizeof(n) / sizeof(n[0])); ++i) sig |= (n[i] > 0 ? 1u : 0u) << i;
-    return sig;
+    return sig | (unsigned)r.fwd_shape << 16;
 }
 
 // Capture one round into *out.  If *out already holds an executable graph
@@ -285,7 +321,7 @@ int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out, uns
     if (e == cudaSuccess)
         e = ctg_batch_back(r.insts, M + r.map_h16, r.n_h16, CTG_PH_BACK_AB, r.max_window, st, CTG_BASIS_FP16);
     if (e == cudaSuccess) e = ctg_batch_pad(r.insts, M + r.map_pad, r.n_pad, st);
-    if (e == cudaSuccess) e = ctg_batch_forward(r.insts, M + r.map_fwd, r.n_fwd, st);
+    if (e == cudaSuccess) e = ctg_batch_forward(r.insts, M + r.map_fwd, r.n_fwd, st, r.fwd_shape);
     if (e == cudaSuccess) e = ctg_batch_back(r.insts, M + r.map_back, r.n_back, CTG_PH_BACK_BA, r.max_window, st);
     if (e == cudaSuccess) e = ctg_batch_cgs2(r.insts, M + r.map_cgs, r.n_cgs, r.max_maxit, st);
     if (e == cudaSuccess)
@@ -336,6 +372,7 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
             return CTG_ERR_INVALID_ARG;
         }
         ctg_build_tables(&p.g, fw[i], bk[i]);
+        p.fwd = plan_forward(p.g, fw[i]);
         const int win = ctg_back_window(bk[i].data(), p.g.n_angles);
         if (win > ctg_back_window_max()) {   // detector pitch too fine for the batched tiles
             release(b);
@@ -365,6 +402,7 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
     b->map_h16 = spec.map_h16; b->n_h16 = spec.n_h16;
     b->map_cgs_b16 = spec.map_cgs_b16; b->n_cgs_b16 = spec.n_cgs_b16;
     b->map_cgs_h16 = spec.map_cgs_h16; b->n_cgs_h16 = spec.n_cgs_h16;
+    b->fwd_shape = spec.fwd_shape;
     if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_maps, sizeof(int2) * (maps.empty() ? 1 : maps.size())));
     if (rc == CTG_OK && !maps.empty())
         rc = ck(cudaMemcpy(b->d_maps, maps.data(), sizeof(int2) * maps.size(), cudaMemcpyHostToDevice));
@@ -385,7 +423,7 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
                     b->map_fwd, b->n_fwd, b->map_cgs, b->n_cgs, b->map_m, b->n_m,
                     b->map_b16, b->n_b16, b->map_h16, b->n_h16,
                     b->map_cgs_b16, b->n_cgs_b16, b->map_cgs_h16, b->n_cgs_h16,
-                    b->max_window, b->max_maxit, b->d_active};
+                    b->max_window, b->max_maxit, b->d_active, b->fwd_shape};
         rc = capture_round(r, b->st, &b->round);
     }
     if (rc != CTG_OK) {
@@ -592,6 +630,9 @@ struct ctg_engine {
     cudaEvent_t ev_in = nullptr;
     cudaGraphExec_t round = nullptr;
     cudaMemPool_t pool = nullptr;    // per-solve workspaces, kept mapped up to the budget
+    // forward plans of the geometries served so far (a few ms of host work
+    // each, so made once per geometry)
+    std::vector<std::pair<ctg_geom, std::shared_ptr<const FwdPlan>>> fwd_plans;
 };
 
 namespace {
@@ -626,12 +667,17 @@ bool plan_valid(const ctg_geom *g, int variant, const ctg_opts *o) {
     return ctg_back_window(bk.data(), g->n_angles) <= ctg_back_window_max();
 }
 
+// The slots' plans indexed by slot, as build_maps reads them (no copies).
+struct SlotPlans {
+    const ctg_engine *e;
+    const InstPlan &operator[](size_t i) const { return e->slots[i].plan; }
+};
+
 int recapture(ctg_engine *e) {
     std::vector<int> ids;
     for (int i = 0; i < e->max_slots; ++i)
         if (e->slots[i].state == 1) ids.push_back(i);
-    std::vector<InstPlan> plans(e->max_slots);
-    for (int i = 0; i < e->max_slots; ++i) plans[i] = e->slots[i].plan;
+    SlotPlans plans{e};
     std::vector<int2> maps;
     RoundSpec r{};
     build_maps(plans, ids, maps, r);
@@ -738,6 +784,8 @@ extern "C" int ctg_engine_submit(ctg_engine *e, const ctg_geom *g, int32_t varia
     s.plan.g = *g;
     s.plan.o = *o;
     s.plan.variant = variant;
+    for (const auto &fp : e->fwd_plans)
+        if (same_fwd_geom(fp.first, *g)) s.plan.fwd = fp.second;
     B_CK(cudaEventRecord(e->ev_in, static_cast<cudaStream_t>(stream)));
     B_CK(cudaStreamWaitEvent(e->st, e->ev_in, 0));
     void *ws = nullptr;
@@ -745,11 +793,16 @@ extern "C" int ctg_engine_submit(ctg_engine *e, const ctg_geom *g, int32_t varia
     s.ws = static_cast<char *>(ws);
     s.bytes = bytes;
     plan_instance(s.plan, s.ws);
+    const bool new_plan = !s.plan.fwd;
     if (const int urc = upload_tables(s.plan, e->st)) {
         cudaFreeAsync(s.ws, e->st);
         cudaStreamSynchronize(e->st);
         s = ctg_engine::Slot{};
         return urc;
+    }
+    if (new_plan) {
+        if (e->fwd_plans.size() >= 256) e->fwd_plans.clear();
+        e->fwd_plans.emplace_back(*g, s.plan.fwd);
     }
     s.b = b_dev;
     s.x0 = x0_dev;

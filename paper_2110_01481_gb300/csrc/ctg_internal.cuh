@@ -88,9 +88,11 @@ cudaError_t ctg_launch_pad(const void *x, int dtype, float2 *pad, int N, const P
 constexpr int kFwdShapes = 4;
 constexpr int kFwdShapeAngles[kFwdShapes] = {8, 4, 8, 16};
 constexpr int kFwdShapeSplit[kFwdShapes] = {1, 1, 4, 4};
-// Angles per block of the batched forward projector (ctg_fwd_blocks): shape
-// 0, one angle per warp.
+// Forward shapes of batched launches: shape 0 (kBatchFwdAngles angles per
+// block, one per warp), or kBatchFwdSplitShape when every instance of the
+// round allows several angles per warp.
 constexpr int kBatchFwdAngles = 8;
+constexpr int kBatchFwdSplitShape = 3;
 // shape: an index into the tables above.  order: NULL, or the device copy
 // of ctg_forward_order's permutation for the same shape.
 cudaError_t ctg_launch_forward(const float2 *pad, int N, const PadLayout &pl, int n_angles,
@@ -291,7 +293,10 @@ enum { CTG_PH_BACK_AB = 0, CTG_PH_PAD = 1, CTG_PH_FWD = 2, CTG_PH_BACK_BA = 3 };
 cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int phase,
                            int max_window, cudaStream_t st, int wtype = CTG_BASIS_FP32);
 cudaError_t ctg_batch_pad(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st);
-cudaError_t ctg_batch_forward(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st);
+// shape: 0, or kBatchFwdSplitShape when every instance of the round allows
+// it (ctg_forward_split_safe); the map's local blocks are that shape's.
+cudaError_t ctg_batch_forward(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st,
+                              int shape = 0);
 // Local block counts of one instance for the maps above.
 int ctg_back_tiles(int N);
 int ctg_pad_tiles(int N);

@@ -488,20 +488,22 @@ __global__ void batch_pad_kernel(const BatchInst *__restrict__ insts, const int2
                                I.pad_border, mp.y % tx, mp.y / tx);
 }
 
-__global__ void __launch_bounds__(32 * kFwdAngles)
+// kAngles, kSplit: the forward shape of the round (one for all instances).
+template <int kAngles, int kSplit>
+__global__ void __launch_bounds__(32 * kAngles / kSplit)
 batch_forward_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
     const int2 mp = map[blockIdx.x];
     const BatchInst &I = insts[mp.x];
     if (!I.active) return;
-    const int bxn = (I.n_det + 31) / 32;
+    const int bxn = (I.n_det + 32 / kSplit - 1) / (32 / kSplit);
     // AB: q = A t; BA: t_k = A w_k, kept in T
     float *out = I.variant == CTG_AB ? I.vm : I.T + (size_t)(I.k - 1) * I.ldt;
     if (I.pad_clamp)
-        joseph_forward_block<true>(I.pad, I.N, I.pad_stride, I.pad_border, I.n_angles, I.n_det,
-                                   I.fwd, out, mp.y % bxn, mp.y / bxn);
+        joseph_forward_block<true, kAngles, kSplit>(I.pad, I.N, I.pad_stride, I.pad_border, I.n_angles,
+                                                    I.n_det, I.fwd, out, mp.y % bxn, mp.y / bxn);
     else
-        joseph_forward_block<false>(I.pad, I.N, I.pad_stride, I.pad_border, I.n_angles, I.n_det,
-                                    I.fwd, out, mp.y % bxn, mp.y / bxn);
+        joseph_forward_block<false, kAngles, kSplit>(I.pad, I.N, I.pad_stride, I.pad_border, I.n_angles,
+                                                     I.n_det, I.fwd, out, mp.y % bxn, mp.y / bxn);
 }
 
 }  // namespace
@@ -516,6 +518,7 @@ int ctg_pad_tiles(int N) {
 }
 int ctg_fwd_blocks(int n_angles, int n_det) {
     static_assert(kFwdShapeAngles[0] == kFwdAngles && kFwdShapeSplit[0] == 1, "batched forward shape");
+    static_assert(kFwdShapeSplit[kBatchFwdSplitShape] > 1, "batched split shape");
     return ctg_fwd_shape_blocks(0, n_angles, n_det);
 }
 // largest window the tiled back projector can stage in shared memory
@@ -541,9 +544,14 @@ cudaError_t ctg_batch_pad(BatchInst *insts, const int2 *map, int nblocks, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t ctg_batch_forward(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st) {
+cudaError_t ctg_batch_forward(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st, int shape) {
     if (nblocks <= 0) return cudaSuccess;
-    batch_forward_kernel<<<nblocks, 32 * kFwdAngles, 0, st>>>(insts, map);
+    if (shape == kBatchFwdSplitShape)
+        batch_forward_kernel<kFwdShapeAngles[kBatchFwdSplitShape], kFwdShapeSplit[kBatchFwdSplitShape]>
+            <<<nblocks, 32 * kFwdShapeAngles[kBatchFwdSplitShape] / kFwdShapeSplit[kBatchFwdSplitShape], 0, st>>>(
+                insts, map);
+    else
+        batch_forward_kernel<kFwdAngles, 1><<<nblocks, 32 * kFwdAngles, 0, st>>>(insts, map);
     return cudaGetLastError();
 }
 
@@ -689,13 +697,16 @@ bool ctg_forward_split_safe(const FwdAngle *tab, int N, int n_angles, int n_det,
             // the device's range may differ from this estimate by a step:
             // check a wider one
             const int s_lo = std::max(0, (wlo & ~3) - 4), s_hi = std::min(N - 1, whi + 4);
-            for (int l = 0; l < 32; ++l) {
-                const FwdAngle &t = tab[std::min(n_angles - 1, a0 + l / R)];
-                const long long d = d0 + l % R;
-                for (const long long s : {(long long)s_lo, (long long)s_hi}) {
-                    const long long j = (t.Q + d * t.P + s * t.D) >> CTG_FXF_BITS;
-                    if (j < -pl.border || j > N - 1 + pl.border) return false;
-                }
+            // a lane's column is affine in its ray d, so the warp's first and
+            // last ray of each angle are its extremes (lanes past the last
+            // angle walk with the last angle's table)
+            for (int a = a0; a < a0 + split; ++a) {
+                const FwdAngle &t = tab[std::min(n_angles - 1, a)];
+                for (const long long d : {(long long)d0, (long long)(d0 + R - 1)})
+                    for (const long long s : {(long long)s_lo, (long long)s_hi}) {
+                        const long long j = (t.Q + d * t.P + s * t.D) >> CTG_FXF_BITS;
+                        if (j < -pl.border || j > N - 1 + pl.border) return false;
+                    }
             }
         }
     return true;
