@@ -120,8 +120,9 @@ __device__ __forceinline__ void floor_frac2(float u0, float u1, float &t0, float
 }
 
 __device__ __forceinline__ float one_plus_frac(unsigned lo) {
-    // 1 + (top 23 bits of a 32-bit fraction), exactly, in [1, 2)
-    return __uint_as_float(0x3F800000u | (lo >> 9));
+    // 1 + (top 23 bits of a 32-bit fraction), exactly, in [1, 2): the low
+    // word of (0x7F : lo) >> 9 is 0x3F800000 | (lo >> 9), one funnel shift
+    return __uint_as_float(__funnelshift_r(lo, 0x7Fu, 9));
 }
 
 constexpr int kFwdAngles = kBatchFwdAngles;   // angles per batched block, one per warp
