@@ -4,9 +4,11 @@
 // (CGS2), which equals the paper's MGS loop in exact arithmetic but needs
 // three sweeps over W instead of k dependent ones:
 //   pass 1  h1 = W^T q,                ||q||^2      (one read of W)
-//   pass 2  q -= W h1,  h2 = W^T q                  (two reads of W)
-//   pass 3  q -= W h2,  ||q||^2                     (one read of W)
-//   scale   w_{k+1} = q / ||q||,  h_{1:k,k} = h1 + h2,  h_{k+1,k} = ||q||
+//   pass 2  q -= W h1,  h2 = W^T q,    ||q1||^2     (two reads of W)
+//   pass 3  q -= W h2,  w_{k+1} = q / ||q||         (one read of W)
+// with ||q||^2 = ||q1||^2 - ||h2||^2 after pass 3 (exact for orthonormal W;
+// h2 is at the rounding level of ||q1|| after the first pass, so nothing
+// cancels), h_{1:k,k} = h1 + h2, h_{k+1,k} = ||q||.
 // Each pass is one launch: every block reduces its slice with warp shuffles
 // into per-block partials, and the last block to finish (atomic ticket, no
 // waiting) sums the partials in a fixed order in FP64, so results are
@@ -246,35 +248,27 @@ cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict
     __syncthreads();
     double nrm2 = s_h1[k];
     if (k > 0) {
-        // pass 2: q -= W h1, h2 = W^T q
+        // pass 2: q1 = q - W h1; h2 = W^T q1, ||q1||^2
         for (int j = tid; j < k; j += kThreads) s_c[j] = (float)s_h1[j];
         __syncthreads();
         update_slice<T, E>(W, ldw, k, s_c, g0, L, qv);
-        dots_slice<T, E, false>(W, ldw, k, g0, L, qv, s_w, k);
+        dots_slice<T, E, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
         __syncthreads();
-        write_rows(s_w, k, k + 1, partials, Gp, blk);
+        write_rows(s_w, k + 1, k + 1, partials, Gp, blk);
         __threadfence();
         grid.sync();
-        reduce_rows(partials, k + 1, k, G, Gp, s_h2);
+        reduce_rows(partials, k + 1, k + 1, G, Gp, s_h2);
         __syncthreads();
-        // pass 3: q -= W h2, ||q||^2
+        // pass 3: q2 = q1 - W h2.  With W orthonormal, ||q2||^2 = ||q1||^2 -
+        // ||h2||^2 exactly; h2 is at the rounding level of ||q1|| after the
+        // first pass, so the difference loses nothing, and the step needs no
+        // third grid-wide reduction.  Every block forms it in the same order.
         for (int j = tid; j < k; j += kThreads) s_c[j] = (float)s_h2[j];
         __syncthreads();
         update_slice<T, E>(W, ldw, k, s_c, g0, L, qv);
-        {
-            float t = 0.f;
-#pragma unroll
-            for (int e = 0; e < E; ++e) t += dot4(qv[e], qv[e]);
-            t = warp_sum(t);
-            if ((tid & 31) == 0) s_w[tid >> 5] = t;
-        }
-        __syncthreads();
-        write_rows(s_w, 1, 2 * k + 1, partials, Gp, blk);
-        __threadfence();
-        grid.sync();
-        reduce_rows(partials, 2 * k + 1, 1, G, Gp, s_h2 + k);
-        __syncthreads();
-        nrm2 = s_h2[k];
+        double h2sq = 0.0;
+        for (int j = 0; j < k; ++j) h2sq = fma(s_h2[j], s_h2[j], h2sq);
+        nrm2 = fmax(0.0, s_h2[k] - h2sq);
     }
     // w_{k+1} = q / ||q||; q keeps the orthogonalised vector
     const float inv = nrm2 > 0.0 ? (float)(1.0 / sqrt(nrm2)) : 0.0f;
@@ -321,6 +315,61 @@ __device__ __forceinline__ void scale_body(const float *q, const double *__restr
         for (int j = threadIdx.x; j < k; j += blockDim.x) h_out[j] = h1[j] + h2[j];
         if (threadIdx.x == 0) h_out[k] = sqrt(nn);
     }
+}
+
+// The last CGS2 pass and the scaling in one sweep: q -= sum_j h2_j W_j, then
+// w_out = q / ||q||, with ||q||^2 = h2[k] - ||h2[0..k-1]||^2 (h2[k] =
+// ||q1||^2 from the second pass; exact for orthonormal W, and h2 is at the
+// rounding level of ||q1||, so nothing cancels).  Block 0 writes the
+// Hessenberg column h_out[0..k] and *nrm2_out.
+template <typename T, int E>
+__device__ __forceinline__ void update_scale_body(const T *__restrict__ W, int64_t ldw, int k,
+                                                  float *__restrict__ q, int64_t L,
+                                                  const double *__restrict__ h1,
+                                                  const double *__restrict__ h2, T *w_out,
+                                                  double *__restrict__ h_out,
+                                                  double *__restrict__ nrm2_out, int blk) {
+    extern __shared__ float smem[];
+    float *s_coef = smem;                                   // k floats
+    __shared__ double s_nn;
+    const int tid = threadIdx.x;
+    for (int j = tid; j < k; j += kThreads) s_coef[j] = (float)h2[j];
+    if (tid < 32) {
+        // ||h2||^2 in a fixed order: lane-strided sums, then a fixed tree
+        double t = 0.0;
+        for (int j = tid; j < k; j += 32) t = fma(h2[j], h2[j], t);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (tid == 0) s_nn = fmax(0.0, h2[k] - t);
+    }
+    __syncthreads();
+    const double nn = s_nn;
+    const float inv = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.0f;
+    const int64_t g0 = (int64_t)blk * kThreads * E + tid;
+    float4 qv[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) qv[e] = ld4_rw(q, g0 + (int64_t)e * kThreads, L);
+    update_slice<T, E>(W, ldw, k, s_coef, g0, L, qv);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int64_t g = g0 + (int64_t)e * kThreads;
+        st4(q, g, L, qv[e]);
+        stw4(w_out, g, L, make_float4(qv[e].x * inv, qv[e].y * inv, qv[e].z * inv, qv[e].w * inv));
+    }
+    if (blk == 0) {
+        if (h_out != nullptr) {
+            for (int j = tid; j < k; j += kThreads) h_out[j] = h1[j] + h2[j];
+            if (tid == 0) h_out[k] = sqrt(nn);
+        }
+        if (tid == 0) *nrm2_out = nn;
+    }
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(kThreads, 2)
+update_scale_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict__ q, int64_t L,
+                    const double *__restrict__ h1, const double *__restrict__ h2, T *w_out,
+                    double *__restrict__ h_out, double *__restrict__ nrm2_out) {
+    update_scale_body<T, E>(W, ldw, k, q, L, h1, h2, w_out, h_out, nrm2_out, blockIdx.x);
 }
 
 template <typename T>
@@ -429,15 +478,18 @@ batch_cgs_pass_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ ma
                                             I.partials, I.counter, red_out, mp.y, I.G);
 }
 
+// Last CGS2 pass and scaling of every instance (update_scale_body): the new
+// basis vector w_{k+1}, rounded to the basis type, and Hessenberg column k.
 template <typename T>
-__global__ void batch_scale_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
+__global__ void __launch_bounds__(kThreads, 2)
+batch_update_scale_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
     const int2 mp = map[blockIdx.x];
     BatchInst &I = insts[mp.x];
     if (!I.active) return;
-    const float *q = I.variant == CTG_AB ? I.vm : I.vn;
-    // w_{k+1}, rounded to the basis type
-    scale_body<T>(q, I.scal + 1, static_cast<T *>(I.W) + (size_t)I.k * I.ldw, I.L, I.k, I.h1, I.h2,
-                  I.H + (size_t)(I.k - 1) * (I.maxit + 1), mp.y, I.G);
+    float *q = I.variant == CTG_AB ? I.vm : I.vn;
+    update_scale_body<T, 1>(static_cast<const T *>(I.W), I.ldw, I.k, q, I.L, I.h1, I.h2,
+                            static_cast<T *>(I.W) + (size_t)I.k * I.ldw,
+                            I.H + (size_t)(I.k - 1) * (I.maxit + 1), I.scal + 1, mp.y);
 }
 
 // One warp per instance: FP64 Givens update of the Hessenberg least-squares
@@ -572,6 +624,31 @@ cudaError_t launch_pass(const T *W, int64_t ldw, int k, float *q, int64_t L,
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_update_scale(const T *W, int64_t ldw, int k, float *q, int64_t L, const RedScratch &rs,
+                                T *w_out, double *h_out, cudaStream_t st) {
+    int E;
+    const int G = ctg_red_grid(L, &E);
+    const size_t smem = sizeof(float) * (size_t)k;
+    cudaError_t err = cudaSuccess;
+#define CTG_US_CASE(EE)                                                                          \
+    case EE: {                                                                                   \
+        auto kern = update_scale_kernel<T, EE>;                                                  \
+        if ((err = ensure_smem(kern, smem)) != cudaSuccess) return err;                          \
+        kern<<<G, kThreads, smem, st>>>(W, ldw, k, q, L, rs.h1, rs.h2, w_out, h_out, rs.scal + 1); \
+        break;                                                                                   \
+    }
+    switch (E) {
+        CTG_US_CASE(1)
+        CTG_US_CASE(2)
+        CTG_US_CASE(4)
+        CTG_US_CASE(8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CTG_US_CASE
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int ctg_red_grid(int64_t L, int *E_out) {
@@ -683,7 +760,7 @@ template <typename T>
 cudaError_t cgs2_step_t(const T *W, int64_t ldw, int64_t L, int k, float *q, T *w_out,
                         double *h_out, const RedScratch &rs, cudaStream_t st, int *nkern) {
     cudaError_t err;
-    if (nkern) *nkern = k > 0 ? 4 : 2;
+    if (nkern) *nkern = k > 0 ? 3 : 2;
     if (k <= kFusedMaxK && rs.rows >= 2 * k + 2) {
         int E;
         const int G = ctg_red_grid(L, &E);
@@ -707,16 +784,14 @@ cudaError_t cgs2_step_t(const T *W, int64_t ldw, int64_t L, int k, float *q, T *
     if ((err = cudaMemcpyAsync(rs.scal, rs.h1 + k, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return err;
     if (k > 0) {
-        // pass 2: q -= W h1; h2 = W^T q
-        if ((err = launch_pass<T, true, true, false>(W, ldw, k, q, L, rs.h1, rs, rs.h2, st)) != cudaSuccess)
+        // pass 2: q -= W h1; h2 = W^T q, ||q||^2 (h2[k])
+        if ((err = launch_pass<T, true, true, true>(W, ldw, k, q, L, rs.h1, rs, rs.h2, st)) != cudaSuccess)
             return err;
-        // pass 3: q -= W h2; ||q||^2 -> scal[1]
-        if ((err = launch_pass<T, true, false, true>(W, ldw, k, q, L, rs.h2, rs, rs.scal + 1, st)) != cudaSuccess)
-            return err;
-    } else {
-        if ((err = cudaMemcpyAsync(rs.scal + 1, rs.scal, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-            return err;
+        // q -= W h2 and w_out = q / ||q|| in one sweep; ||q||^2 -> scal[1]
+        return launch_update_scale<T>(W, ldw, k, q, L, rs, w_out, h_out, st);
     }
+    if ((err = cudaMemcpyAsync(rs.scal + 1, rs.scal, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return err;
     scale_kernel<T><<<scale_blocks(L), 256, 0, st>>>(q, rs.scal + 1, w_out, L, k, rs.h1, rs.h2, h_out);
     return cudaGetLastError();
 }
@@ -843,18 +918,19 @@ namespace {
 
 template <typename T>
 void launch_batch_cgs2(BatchInst *insts, const int2 *map, int nblocks, size_t smem, cudaStream_t st) {
+    // pass 1: h1, ||q||^2; pass 2: q -= W h1, h2, ||q1||^2; then the last
+    // update and the scaling in one sweep
     batch_cgs_pass_kernel<T, false, true, true><<<nblocks, kThreads, smem, st>>>(insts, map);
-    batch_cgs_pass_kernel<T, true, true, false><<<nblocks, kThreads, smem, st>>>(insts, map);
-    batch_cgs_pass_kernel<T, true, false, true><<<nblocks, kThreads, smem, st>>>(insts, map);
-    batch_scale_kernel<T><<<nblocks, kThreads, 0, st>>>(insts, map);
+    batch_cgs_pass_kernel<T, true, true, true><<<nblocks, kThreads, smem, st>>>(insts, map);
+    batch_update_scale_kernel<T><<<nblocks, kThreads, smem, st>>>(insts, map);
 }
 
 template <typename T>
 cudaError_t prepare_batch_cgs2(size_t smem) {
     cudaError_t err;
     if ((err = ensure_smem(batch_cgs_pass_kernel<T, false, true, true>, smem)) != cudaSuccess) return err;
-    if ((err = ensure_smem(batch_cgs_pass_kernel<T, true, true, false>, smem)) != cudaSuccess) return err;
-    return ensure_smem(batch_cgs_pass_kernel<T, true, false, true>, smem);
+    if ((err = ensure_smem(batch_cgs_pass_kernel<T, true, true, true>, smem)) != cudaSuccess) return err;
+    return ensure_smem(batch_update_scale_kernel<T>, smem);
 }
 
 }  // namespace
