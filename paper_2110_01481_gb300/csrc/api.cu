@@ -317,9 +317,11 @@ int fail_cuda(cudaError_t e) {
 constexpr size_t kMaxCachedGeoms = 64;
 
 // Projector tile autotuner.  Candidate shapes leave every sum in the same
-// order (forward: angles per block, each ray still one warp; pixel-driven
+// order (forward: angles per block and per warp, each ray still summed by
+// one lane over its own chord in a fixed accumulator order; pixel-driven
 // back projection: angles staged per pass, each pixel's angles still in
-// order), so the choice changes the speed only.  Each candidate is timed
+// order), so the choice changes the speed only.  Shapes with several angles
+// per warp are timed only where the geometry allows them (fwd_split_ok).  Each candidate is timed
 // with CUDA events over 3 launches (after one untimed) on zero inputs of the
 // geometry's sizes on a private stream; the fastest is kept.
 int tune_geometry(GeomEntry *ge) {
