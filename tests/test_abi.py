@@ -84,6 +84,8 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.ctg_ab_gmres(None, ctypes.byref(_g(64, 90, 91)), None, None, None,
                             ctypes.byref(_o(10)), None, 0, None, None) == -1
     assert lib.ctg_cgs2(None, 8, 8, 1, None, None, None, None, 0, None) == -1
+    assert lib.ctg_set_tiles(None, 8, 32) == -1
+    assert lib.ctg_set_fwd_tiles(None, 8, 4) == -1
     assert lib.ctg_cgs2_scratch_bytes(0, 1) == 0
 
 
