@@ -157,9 +157,10 @@ struct GeomEntry {
     int *fwd_order = nullptr;   // forward dispatch orders of the shapes, one after another
     size_t fwd_order_off[kFwdShapes] = {};
     bool fwd_split_ok = false;  // shapes with several angles per warp are safe here
-    int fwd_shape = 0;          // tile shapes (autotuned unless forced)
+    int fwd_shape = 0;          // tile shapes in use (autotuned unless forced)
     int back_chunk = 32;
     bool tuned = false;
+    int tuned_fwd_shape = 0, tuned_back_chunk = 32;   // the autotuner's choice, kept while forced
     float fwd_us[kFwdShapes] = {}, back_us[3] = {0, 0, 0};   // measured (0: not timed)
     unsigned long long last_use = 0;
     const int *order_for(int shape) const { return fwd_order ? fwd_order + fwd_order_off[shape] : nullptr; }
@@ -371,12 +372,12 @@ int tune_geometry(GeomEntry *ge) {
         int fs = 0;
         for (int c = 1; c < kFwdShapes; ++c)
             if (ge->fwd_us[c] > 0.0f && ge->fwd_us[c] < ge->fwd_us[fs]) fs = c;
-        ge->fwd_shape = fs;
+        ge->fwd_shape = ge->tuned_fwd_shape = fs;
         int best = 1;
         if (g->back_model == CTG_BACK_PIXEL)
             for (int c = 0; c < 3; ++c)
                 if (ge->back_us[c] < ge->back_us[best]) best = c;
-        ge->back_chunk = back_cand[best];
+        ge->back_chunk = ge->tuned_back_chunk = back_cand[best];
         ge->tuned = true;
     }
     if (e0) cudaEventDestroy(e0);
@@ -402,7 +403,10 @@ int apply_tiles(ctg_ctx *ctx, GeomEntry *ge) {
         ge->back_chunk = ctx->force_back_chunk ? ctx->force_back_chunk : 32;
         return CTG_OK;
     }
-    return ge->tuned ? CTG_OK : tune_geometry(ge);
+    if (!ge->tuned) return tune_geometry(ge);
+    ge->fwd_shape = ge->tuned_fwd_shape;     // back from forced shapes
+    ge->back_chunk = ge->tuned_back_chunk;
+    return CTG_OK;
 }
 
 int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {

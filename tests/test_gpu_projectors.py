@@ -139,5 +139,10 @@ def test_tile_autotuner_is_result_invariant(P):
                 assert (tt["fwd_angles"], tt["fwd_warp_angles"]) == want and tt["back_chunk"] == bc
                 assert torch.equal(P.project(g, x), ref_a), (g, fa, fw)
                 assert torch.equal(P.backproject(g, y), ref_b), (g, bc)
+            # clearing the forced shapes restores the autotuner's choice
+            ctx.set_tiles(0, 0)
+            tt = ctx.tuning(g)
+            assert (tt["fwd_angles"], tt["fwd_warp_angles"], tt["back_chunk"]) == \
+                (t["fwd_angles"], t["fwd_warp_angles"], t["back_chunk"])
     finally:
         ctx.set_tiles(0, 0)
