@@ -173,10 +173,14 @@ def joseph_interpolations(N, n_angles, n_det, start=0, rng=180, ds=1.0):
     return total
 
 
-# SM-side bound of the projectors: every interpolation moves one 8-byte
-# (value, difference) pair through the SM's L1/shared data path, 128 B/clk
-# per SM on 152 SMs at the 2070 MHz maximum SM clock.
-L1_PEAK_GBS = 152 * 128 * 2.070
+def l1_peak(torch, dev, sm_max_mhz):
+    """SM-side bound of the projectors: every interpolation moves one 8-byte
+    (value, difference) pair through the SM's L1/shared data path, 128 B/clk
+    per SM, on the device's SM count (queried: 152 on a GB300) at its maximum
+    SM clock (sampled by nvidia-smi; 2070 MHz on a GB300).  GB/s."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_max_mhz if sm_max_mhz else 2070.0
+    return sms * 128 * mhz / 1e3, sms, mhz
 
 
 def reduce_across_ranks(dist, torch, device, maxed, summed):
@@ -631,6 +635,14 @@ def make_instance(P, torch, dev, seed):
     return g, xbar, torch.tensor(b, dtype=torch.float32, device=dev), enorm
 
 
+def bench_config(world):
+    """The workload's config, the same for both arms."""
+    return {"workload": WORKLOAD, "N": N, "n_angles": N_ANG, "n_det": N_DET,
+            "maxit": MAXIT, "tau": TAU, "noise": ETA,
+            "l2": "flushed between timed steps (258 MiB write)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -773,11 +785,13 @@ def run_gpu(args):
             kname = "pixel_back_tiled_kernel"
         per_launch_s = phases[dom]["ms"] / 1e3 / phases[dom]["calls"]
         ach = 8.0 * interp / per_launch_s / 1e9
+        l1, sms, mhz = l1_peak(torch, dev, clocks.get("sm_max_mhz"))
         roof = {"bound": "alu", "unit": "GB/s", "kernel": kname,
-                "achieved": ach, "peak": L1_PEAK_GBS,
-                "peak_kind": "derived: L1/shared data path, 152 SM x 128 B/clk x 2.07 GHz; "
-                             "8 B (one value/difference pair) per interpolation",
-                "frac": ach / L1_PEAK_GBS, "traffic": recorded_traffic(kname),
+                "achieved": ach, "peak": l1,
+                "peak_kind": f"derived: L1/shared data path, {sms} SM (queried) x 128 B/clk x "
+                             f"{mhz / 1e3:.3f} GHz (max SM clock); 8 B (one value/difference pair) "
+                             "per interpolation",
+                "frac": ach / l1, "traffic": recorded_traffic(kname),
                 "interpolations_per_launch": interp,
                 "launch_us": per_launch_s * 1e6}
     fwd_calls, back_calls = phases["forward"]["calls"], phases["back"]["calls"]
@@ -788,10 +802,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded random-ellipse phantom, 1% Gaussian noise)",
-        "config": {"workload": WORKLOAD, "N": N, "n_angles": N_ANG, "n_det": N_DET,
-                   "maxit": MAXIT, "tau": TAU, "noise": ETA,
-                   "l2": "flushed between timed steps (258 MiB write)",
-                   "parallelism": f"replicas x{world}"},
+        "config": bench_config(world),
         "step_ms": [round(t, 4) for t in step_ms],
         "iterations_per_step": {"ab": ra.iters, "ba": rb.iters},
         "stop": {"ab": ra.stop_reason, "ba": rb.stop_reason},
@@ -815,7 +826,7 @@ def run_gpu(args):
     if world == 1 and not args.no_serve:
         line["serving"] = serving_summary(P, torch, dev, args.serve_quick)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_iters_single_core)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -830,22 +841,24 @@ def _oracle_instance(seed):
     return O, og, b, enorm
 
 
-def cpu_baseline(iters_per_solve: int):
+def cpu_baseline(iters_single_core: int):
     """The FP64 oracle as it stands, on the host cores: one AB-GMRES and one
-    BA-GMRES solve capped at `iters_per_solve` iterations each."""
+    BA-GMRES solve of the workload, each run to its discrepancy-principle
+    stop (up to MAXIT), i.e. one full step of the benchmark."""
     O, og, b, enorm = _oracle_instance(2000)
     A = lambda v: O.forward(og, v)
     B = lambda v: O.backproject(og, v)
     t0 = time.perf_counter()
-    ra = O.ab_gmres(A, B, b, iters_per_solve, tau=TAU, noise_norm=enorm)
-    rb = O.ba_gmres(A, B, b, iters_per_solve, tau=TAU, noise_norm=enorm)
+    ra = O.ab_gmres(A, B, b, MAXIT, tau=TAU, noise_norm=enorm)
+    rb = O.ba_gmres(A, B, b, MAXIT, tau=TAU, noise_norm=enorm)
     dt = time.perf_counter() - t0
     its = ra["k"] + rb["k"]
     out = {"value": its / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-           "sample": f"one AB-GMRES and one BA-GMRES solve of the same workload capped at "
-                     f"{iters_per_solve} iterations each ({its} iterations, {dt:.1f} s; "
-                     f"FP64, matrix-free C projectors with OpenMP, numpy Arnoldi)"}
-    out["single_core"] = cpu_baseline_one_core(max(1, iters_per_solve // 8))
+           "sample": f"one full step: one AB-GMRES and one BA-GMRES solve of the workload to "
+                     f"their discrepancy-principle stops (k = {ra['k']} and {rb['k']}; {its} "
+                     f"iterations, {dt:.1f} s; FP64, matrix-free C projectors with OpenMP, numpy "
+                     f"Arnoldi)"}
+    out["single_core"] = cpu_baseline_one_core(iters_single_core)
     return out
 
 
@@ -871,6 +884,12 @@ def cpu_baseline_one_core(iters_per_solve: int):
 
 
 def run_reference(args):
+    """The oracle as the reference arm: every timed step is one full step of
+    the workload, one AB-GMRES and one BA-GMRES solve to their discrepancy
+    stops (the same solves as the GPU arm); warm-up steps run the same
+    solves capped at 2 iterations each (only the code paths need warming).
+    A 258 MiB host buffer is rewritten between timed steps, as the GPU arm
+    flushes its L2."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -879,29 +898,33 @@ def run_reference(args):
     O_, og, b, enorm = _oracle_instance(2000)
     A = lambda v: O.forward(og, v)
     B = lambda v: O.backproject(og, v)
-    cap = args.ref_iters
+    flush = np.empty(2 * L2_BYTES, dtype=np.uint8)
 
-    def step():
+    def step(cap):
         ra = O.ab_gmres(A, B, b, cap, tau=TAU, noise_norm=enorm)
         rb = O.ba_gmres(A, B, b, cap, tau=TAU, noise_norm=enorm)
-        return ra["k"] + rb["k"]
+        return ra["k"], rb["k"]
 
     for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    its = sum(step() for _ in range(args.steps))
-    dt = time.perf_counter() - t0
+        step(2)
+    dt, its, ks = 0.0, 0, None
+    for _ in range(args.steps):
+        flush.fill(0)
+        t0 = time.perf_counter()
+        ks = step(MAXIT)
+        dt += time.perf_counter() - t0
+        its += sum(ks)
     value = its / dt
-    sample = (f"each step one AB-GMRES and one BA-GMRES solve of the workload capped at {cap} "
-              f"iterations each (a bounded sample: the full solves stop at k = 13 and 14; FP64 "
-              f"oracle, matrix-free C projectors with OpenMP)")
+    sample = (f"every timed step one AB-GMRES and one BA-GMRES solve of the workload to their "
+              f"discrepancy stops (k = {ks[0]} and {ks[1]}), FP64 oracle, matrix-free C "
+              f"projectors with OpenMP; warm-up steps capped at 2 iterations per solve")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded random-ellipse phantom, 1% Gaussian noise)",
-        "config": {"workload": WORKLOAD, "N": N, "n_angles": N_ANG, "n_det": N_DET,
-                   "maxit": MAXIT, "tau": TAU, "noise": ETA},
+        "config": bench_config(args.gpus),
+        "iterations_per_step": {"ab": ks[0], "ba": ks[1]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -914,8 +937,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-iters", type=int, default=8)
-    ap.add_argument("--ref-iters", type=int, default=2)
+    ap.add_argument("--cpu-iters-single-core", type=int, default=1,
+                    help="iterations per solve of the one-core oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the short serving measurement of the default run")

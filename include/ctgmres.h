@@ -345,11 +345,13 @@ int ctg_cgs2(const float *W_dev, int64_t ld_w, int64_t L, int32_t k,
  * a fixed 640 KiB array in device memory that is part of the library (every
  * GPU that loads the library holds it until the process exits); it serves
  * k <= 256 and L <= 4,980,736, and larger sizes return CTG_ERR_INVALID_ARG.
- * The first call on each device looks up the array's device address (with
- * that device current) and caches it; make that first call before any stream
- * capture.  Every call on a device shares the one array, which keeps the
- * previous call's contents; each call first clears the part that must start
- * at zero.  Calls whose work overlaps on the GPU (for example on two streams)
+ * Each call looks up the array's device address on the current device
+ * (so an address from a torn-down context is never reused); a call whose
+ * stream is being captured uses the address that an earlier call on the
+ * device found, so make the first call before any stream capture (a first
+ * call under capture returns CTG_ERR_CUDA).  Every call on a device shares
+ * the one array, which keeps the previous call's contents; each call first
+ * clears the part that must start at zero.  Calls whose work overlaps on the GPU (for example on two streams)
  * race on the array and give wrong results: serialise them.
  * Calls no cudaMalloc, cudaFree or allocating library routine. */
 int ctg_cgs2_noalloc(const float *W_dev, int64_t ld_w, int64_t L, int32_t k,

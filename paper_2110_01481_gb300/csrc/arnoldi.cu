@@ -15,6 +15,8 @@
 // deterministic run to run.
 #include <cooperative_groups.h>
 
+#include <atomic>
+
 #include "vecops.cuh"
 
 namespace {
@@ -651,10 +653,48 @@ cudaError_t launch_update_scale(const T *W, int64_t ldw, int k, float *q, int64_
 
 }  // namespace
 
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+// Per-device cache of an int computed once (0 = not yet known, so the
+// static zero-initialisation needs no constructor); thread-safe: a race
+// computes the value twice and stores the same result.
+template <typename F>
+int per_device_cached(std::atomic<int> (&cache)[kMaxDevices], F compute) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return compute(-1);
+    }
+    const int v = cache[dev].load(std::memory_order_acquire);
+    if (v != 0) return v - 1;
+    const int c = compute(dev);
+    cache[dev].store(c + 1, std::memory_order_release);
+    return c;
+}
+
+std::atomic<int> g_target_grid[kMaxDevices];
+
+}  // namespace
+
+int ctg_target_grid() {
+    return per_device_cached(g_target_grid, [](int dev) {
+        int sms = 0;
+        if (dev < 0 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms < 1) {
+            cudaGetLastError();
+            sms = 152;                      // no device: size for a GB300 (152 SMs)
+        }
+        return 2 * sms;
+    });
+}
+
 int ctg_red_grid(int64_t L, int *E_out) {
     const int64_t L4 = (L + 3) / 4;
+    const int target = ctg_target_grid();
     int E = 1;
-    while (E < kMaxE && (L4 + (int64_t)kThreads * E - 1) / ((int64_t)kThreads * E) > kTargetGrid) E *= 2;
+    while (E < kMaxE && (L4 + (int64_t)kThreads * E - 1) / ((int64_t)kThreads * E) > target) E *= 2;
     int64_t G = (L4 + (int64_t)kThreads * E - 1) / ((int64_t)kThreads * E);
     if (G < 1) G = 1;
     *E_out = E;
@@ -664,7 +704,7 @@ int ctg_red_grid(int64_t L, int *E_out) {
 static int red_grid_max(int64_t L) {
     int E;
     const int G = ctg_red_grid(L, &E);
-    return G > kTargetGrid ? G : kTargetGrid;
+    return G > ctg_target_grid() ? G : ctg_target_grid();
 }
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -714,7 +754,7 @@ size_t fused_smem_bytes(int k) {
 int scale_blocks(int64_t L) {
     const int64_t L4 = (L + 3) / 4;
     int blocks = (int)((L4 + 255) / 256);
-    if (blocks > 4 * kTargetGrid) blocks = 4 * kTargetGrid;
+    if (blocks > 4 * ctg_target_grid()) blocks = 4 * ctg_target_grid();
     return blocks < 1 ? 1 : blocks;
 }
 
@@ -724,20 +764,18 @@ int scale_blocks(int64_t L) {
 
 template <typename T, int E>
 int fused_resident_blocks() {
-    static int blocks = -1;
-    if (blocks < 0) {
-        int per_sm = 0, dev = 0, sms = 0;
+    static std::atomic<int> cache[kMaxDevices];
+    return per_device_cached(cache, [](int dev) {
+        int per_sm = 0, sms = 0;
         const size_t smem = fused_smem_bytes(kFusedMaxK);
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        if (dev < 0 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cgs2_fused_kernel<T, E>, kThreads,
                                                           smem) != cudaSuccess) {
             cudaGetLastError();
             per_sm = 0;
         }
-        blocks = per_sm * sms;
-    }
-    return blocks;
+        return per_sm * sms;
+    });
 }
 
 template <typename T, int E>

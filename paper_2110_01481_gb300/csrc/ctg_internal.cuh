@@ -160,6 +160,9 @@ struct RedScratch {
     int E;                 // float4 groups per thread
     int rows = 0;          // partial-sum rows available (kmax + 2, or 2k + 2 for a fused step)
 };
+// Blocks a reduction pass aims for: 2 on every SM of the current device
+// (queried once per device; 2 x 152 when no device can be queried).
+int ctg_target_grid();
 int ctg_red_grid(int64_t L, int *E_out);
 size_t ctg_red_scratch_bytes(int64_t L, int kmax);
 void ctg_red_scratch_carve(void *base, int64_t L, int kmax, RedScratch *rs);

@@ -29,18 +29,25 @@ std::mutex g_setup_mutex;
 void *g_scratch_addr[kMaxDevices] = {};   // device address of the array, per device
 
 // Host code may not use g_noalloc_scratch's name as a device pointer (it is a
-// host-side stand-in); ask the runtime for its address on the current device
-// once and keep it.
-int scratch_address(void **out) {
+// host-side stand-in); ask the runtime for its address on the current device.
+// The lookup is repeated on every call whose stream is not being captured,
+// so an address from a context that has since been torn down (after
+// cudaDeviceReset, say) is never used; during a capture the address found by
+// an earlier call on this device is used.
+int scratch_address(cudaStream_t st, void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CTG_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return CTG_ERR_INVALID_ARG;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return CTG_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (g_scratch_addr[dev] == nullptr) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) return CTG_ERR_CUDA;
         g_scratch_addr[dev] = p;
+    } else if (g_scratch_addr[dev] == nullptr) {
+        return CTG_ERR_CUDA;                 // first call made under capture
     }
     *out = g_scratch_addr[dev];
     return CTG_OK;
@@ -59,12 +66,12 @@ extern "C" int ctg_cgs2_noalloc(const float *W_dev, int64_t ld_w, int64_t L, int
     if ((k > 0 && !aligned16(W_dev)) || !aligned16(q_dev) || !aligned16(w_out_dev))
         return CTG_ERR_INVALID_ARG;
     if (ctg_red_scratch_bytes(L, k + 1) > kNoAllocScratchBytes) return CTG_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     void *scratch = nullptr;
-    const int rc = scratch_address(&scratch);
+    const int rc = scratch_address(st, &scratch);
     if (rc != CTG_OK) return rc;
     RedScratch rs;
     ctg_red_scratch_carve(scratch, L, k + 1, &rs);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the array keeps the previous call's contents: the completion counters
     // must start at zero
     if (cudaMemsetAsync(rs.counter, 0, 4 * sizeof(unsigned), st) != cudaSuccess) return CTG_ERR_CUDA;

@@ -14,7 +14,6 @@
 namespace {
 
 constexpr int kThreads = 256, kWarps = kThreads / 32;
-constexpr int kTargetGrid = 2 * 152;   // 2 blocks on each of GB300's 152 SMs
 constexpr int kMaxE = 8;               // float4 groups per thread, at most
 
 __device__ __forceinline__ float4 ld4(const float *p, int64_t g, int64_t L) {
