@@ -74,7 +74,7 @@ class CtgLayout(ctypes.Structure):
 EXPORTS = ("ctg_create", "ctg_destroy", "ctg_project", "ctg_backproject", "ctg_ncp_distance", "ctg_set_tiles", "ctg_set_fwd_tiles", "ctg_get_tuning",
            "ctg_workspace_bytes", "ctg_workspace_layout", "ctg_ab_gmres",
            "ctg_ba_gmres", "ctg_lsqr", "ctg_lsmr", "ctg_cgs2_scratch_bytes", "ctg_cgs2", "ctg_cgs2_noalloc",
-           "ctg_set_timing", "ctg_get_timing", "ctg_status_string",
+           "ctg_set_timing", "ctg_get_timing", "ctg_set_wait_limit", "ctg_status_string",
            "ctg_batch_create", "ctg_batch_workspace_bytes", "ctg_batch_solve", "ctg_batch_destroy",
            "ctg_engine_create", "ctg_engine_request_bytes", "ctg_engine_submit",
            "ctg_engine_step", "ctg_engine_in_flight", "ctg_engine_destroy")
@@ -105,6 +105,8 @@ def _declare(lib):
     lib.ctg_cgs2_noalloc.restype = ctypes.c_int
     lib.ctg_set_timing.argtypes = [vp, ctypes.c_int]
     lib.ctg_set_timing.restype = ctypes.c_int
+    lib.ctg_set_wait_limit.argtypes = [vp, i64]
+    lib.ctg_set_wait_limit.restype = ctypes.c_int
     lib.ctg_get_timing.argtypes = [vp, ctypes.POINTER(CtgTiming), ctypes.c_int]
     lib.ctg_get_timing.restype = ctypes.c_int
     lib.ctg_batch_create.argtypes = [vp, i32, G, ctypes.POINTER(i32), O, ctypes.POINTER(vp)]

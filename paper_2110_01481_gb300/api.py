@@ -79,6 +79,11 @@ class Context:
         out["kernels"] = int(t.kernels)
         return out
 
+    def set_wait_limit(self, polls: int = 0) -> None:
+        """Polls of a bounded device-side wait before it gives up (the solve
+        then raises CtgError with CTG_ERR_TIMEOUT); 0 restores the default."""
+        nat.check(nat.lib().ctg_set_wait_limit(self.handle, int(polls)), "ctg_set_wait_limit")
+
     def set_tiles(self, fwd_angles: int = 0, back_chunk: int = 0, fwd_warp_angles: int = 1) -> None:
         """Force the projectors' tile shapes (0, 0: autotuned per geometry).
         The forward shape is fwd_angles angles per block with fwd_warp_angles

@@ -15,10 +15,9 @@
 namespace {
 
 constexpr int kMaxIt = 4096;
-constexpr double kBreakdownRtol = 1e-6;   // h_{k+1,k} <= rtol * ||q before CGS2||
 
-// Pinned ring used by the pipelined solver loops: the slot of step k holds
-// its Hessenberg column (k+1 doubles), ||q_pre||^2, a residual norm^2 and y_k.
+// Pinned ring of the LSQR / LSMR loop: the slot of step k holds its status
+// words (live flag, residual estimate).
 constexpr int kRing = 4;
 size_t ring_slot_doubles(int maxit) { return 2 * (size_t)maxit + 8; }
 
@@ -163,28 +162,34 @@ struct GeomEntry {
     int tuned_fwd_shape = 0, tuned_back_chunk = 32;   // the autotuner's choice, kept while forced
     float fwd_us[kFwdShapes] = {}, back_us[3] = {0, 0, 0};   // measured (0: not timed)
     unsigned long long last_use = 0;
+    unsigned long long serial = 0;   // identifies the entry's device tables (graphs captured with them)
     const int *order_for(int shape) const { return fwd_order ? fwd_order + fwd_order_off[shape] : nullptr; }
 };
 
-// x = B b (+ add) with the geometry's back projector; b of type `btype`.
+// x = B b (+ add) with the geometry's back projector; b of type `btype`
+// (column bc of a basis at b when bc.k is set).
 cudaError_t back_apply(const GeomEntry *ge, const void *b, int btype, const float *add, float *x,
-                       cudaStream_t st) {
+                       cudaStream_t st, ColRef bc = col_none()) {
     const ctg_geom *g = &ge->g;
     if (g->back_model == CTG_BACK_PIXEL)
         return ctg_launch_back(b, btype, g->N, g->n_angles, g->n_det, ge->back, ge->back_window, add,
-                               x, st, ge->back_chunk);
+                               x, st, ge->back_chunk, bc);
     if (ge->rm == 0 && ge->back_window <= ctg_back_window_max())
         return ctg_launch_back_matched_tiled(b, btype, g->N, g->n_angles, g->n_det, ge->back,
-                                             ge->back_window, ge->mt, ge->thr, add, x, st);
+                                             ge->back_window, ge->mt, ge->thr, add, x, st, bc);
     return ctg_launch_back_matched(b, btype, g->N, g->n_angles, g->n_det, ge->back, ge->mt, ge->rm,
-                                   ge->thr, add, x, st);
+                                   ge->thr, add, x, st, bc);
 }
 
 struct WsLayout {
     size_t off_w, ld_w, off_h, off_pad, off_vn0, off_vm0, off_vm1, off_y, off_red, total;
-    size_t off_t, ld_t, off_r0m;   // BA only: T = A W_k and b - A x0
-    size_t off_n[4], off_m[5], off_state, off_hist;   // LSQR / LSMR only
+    size_t off_n[4], off_m[5], off_state, off_hist;   // LSQR / LSMR; off_state, off_hist also GMRES
     size_t off_ncp;                // NCP distances of the projections (n_angles doubles)
+    // GMRES loop state: Givens rotations, rotated right-hand side, rotated
+    // columns R, y of the last three steps, NCP residual coefficients,
+    // rho and NCP histories
+    size_t off_gc, off_gs, off_gg, off_R, off_yring, off_z, off_rhoh, off_ncph;
+    bool pad2;                     // the staged image holds two interleaved images
     int64_t L, n, m;
     int kmax;
     int dtype;      // basis element type
@@ -228,13 +233,24 @@ bool layout_lsq(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly)
     return true;
 }
 
+int rule_of(const ctg_opts *o) {
+    return o->stop_rule == CTG_RULE_NCP ? kRuleNCP : (o->noise_norm > 0.0 ? kRuleDP : kRuleMaxit);
+}
+
+// AB / BA: the basis W ((maxit + 1) vectors of length L, the storage law k L
+// of Table 3), the Hessenberg matrix, the staged image (two interleaved
+// images for BA with a residual-based stopping rule), one n-vector, two
+// m-vectors, the iterate coefficients, the loop state (O(maxit^2) doubles
+// for the rotated Hessenberg columns) and the reduction scratch.
 bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) {
     if (!geom_valid(g) || !opts_valid(o)) return false;
     if (variant == CTG_LSQR || variant == CTG_LSMR) return layout_lsq(g, variant, o, ly);
     if (variant != CTG_AB && variant != CTG_BA) return false;
     if (o->stop_rule == CTG_RULE_NCP && (g->n_det < 2 || g->n_det > kCtgNcpMaxDet)) return false;
+    *ly = WsLayout{};
     const int64_t n = (int64_t)g->N * g->N, m = (int64_t)g->n_angles * g->n_det;
     const int64_t L = variant == CTG_AB ? m : n;
+    const size_t K = (size_t)o->maxit;
     ly->n = n;
     ly->m = m;
     ly->L = L;
@@ -242,31 +258,33 @@ bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) 
     ly->dtype = o->basis_dtype;
     ly->es = ctg_basis_bytes(o->basis_dtype);
     ly->ld_w = round_up((size_t)L, 64);
+    ly->pad2 = variant == CTG_BA && rule_of(o) != kRuleMaxit;
     size_t off = 0;
-    ly->off_w = off;
-    off = align256(off + ly->es * ly->ld_w * (size_t)(o->maxit + 1));
-    ly->off_h = off;
-    off = align256(off + sizeof(double) * (size_t)(o->maxit + 1) * (size_t)o->maxit);
-    ly->off_pad = off;
-    off = align256(off + sizeof(float) * ctg_pad_layout(g->N, g->det_spacing).floats);
-    ly->off_vn0 = off;
-    off = align256(off + sizeof(float) * round_up((size_t)n, 64));
-    ly->off_vm0 = off;
-    off = align256(off + sizeof(float) * round_up((size_t)m, 64));
-    ly->off_vm1 = off;
-    off = align256(off + sizeof(float) * round_up((size_t)m, 64));
-    ly->off_y = off;
-    off = align256(off + sizeof(double) * (size_t)(o->maxit + 2));
-    ly->ld_t = round_up((size_t)m, 64);
-    ly->off_t = off;
-    if (variant == CTG_BA) off = align256(off + sizeof(float) * ly->ld_t * (size_t)(o->maxit + 1));
-    ly->off_r0m = off;
-    if (variant == CTG_BA) off = align256(off + sizeof(float) * ly->ld_t);
-    ly->off_ncp = off;
-    off = align256(off + sizeof(double) * (size_t)g->n_angles);
-    ly->off_red = off;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align256(off + bytes);
+        return at;
+    };
+    ly->off_w = take(ly->es * ly->ld_w * (K + 1));
+    ly->off_h = take(sizeof(double) * (K + 1) * K);
+    ly->off_pad = take(sizeof(float) * ctg_pad_layout(g->N, g->det_spacing).floats * (ly->pad2 ? 2 : 1));
+    ly->off_vn0 = take(sizeof(float) * round_up((size_t)n, 64));
+    ly->off_vm0 = take(sizeof(float) * round_up((size_t)m, 64));
+    ly->off_vm1 = take(sizeof(float) * round_up((size_t)m, 64));
+    ly->off_y = take(sizeof(double) * (K + 2));
+    ly->off_state = take(sizeof(GmresState));
+    ly->off_gc = take(sizeof(double) * K);
+    ly->off_gs = take(sizeof(double) * K);
+    ly->off_gg = take(sizeof(double) * (K + 1));
+    ly->off_R = take(sizeof(double) * K * K);
+    ly->off_yring = take(sizeof(double) * 3 * K);
+    ly->off_z = take(sizeof(double) * (K + 1));
+    ly->off_hist = take(sizeof(double) * (K + 1));
+    ly->off_rhoh = take(sizeof(double) * (K + 1));
+    ly->off_ncph = take(sizeof(double) * (K + 2));
+    ly->off_ncp = take(sizeof(double) * (size_t)g->n_angles);
     const int64_t Lmax = n > m ? n : m;
-    off = align256(off + ctg_red_scratch_bytes(Lmax, o->maxit + 1));
+    ly->off_red = take(ctg_red_scratch_bytes(Lmax, o->maxit + 1));
     ly->total = off;
     return true;
 }
@@ -298,6 +316,22 @@ struct ctg_ctx {
     cudaEvent_t ev_init = nullptr;   // a solve's start values are in the pinned scratch
     // projector tile shapes: 0 = autotuned per geometry, else forced
     int force_fwd_angles = 0, force_fwd_split = 1, force_back_chunk = 0;
+    // bounded device-side waits: polls before a wait gives up
+    long long spin_limit = kCtgDefaultSpinLimit;
+    // captured solver loops (CUDA graphs with while-loop nodes), each for
+    // one set of solve arguments, most recently used last
+    struct LoopGraph {
+        std::vector<long long> key;
+        unsigned long long geom_serial;
+        cudaGraphExec_t exec;
+        int n_init, n_fused, n_pass, n_exit;   // kernels per launch of each part
+        int fused_max;
+    };
+    std::vector<LoopGraph> graphs;
+    cudaStream_t cap_st[2] = {nullptr, nullptr};   // capture streams
+    bool capturing = false;     // launches are being captured (not counted as run)
+    long long captured_kernels = 0;
+    int graph_mode = 0;        // 0 untried, 1 cooperative fused step, 2 plain fused step, -1 no graphs
 };
 
 namespace {
@@ -389,6 +423,19 @@ int tune_geometry(GeomEntry *ge) {
     return err == cudaSuccess ? CTG_OK : fail_cuda(err);
 }
 
+// Destroys the captured loops that use a geometry's tables (serial), or all
+// of them (serial 0).
+void drop_graphs(ctg_ctx *ctx, unsigned long long serial) {
+    for (size_t i = 0; i < ctx->graphs.size();) {
+        if (serial == 0 || ctx->graphs[i].geom_serial == serial) {
+            cudaGraphExecDestroy(ctx->graphs[i].exec);
+            ctx->graphs.erase(ctx->graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
 int apply_tiles(ctg_ctx *ctx, GeomEntry *ge) {
     if (ctx->force_fwd_angles || ctx->force_back_chunk) {
         // a forced shape with several angles per warp falls back to one
@@ -423,6 +470,7 @@ int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
         for (size_t i = 1; i < ctx->cache.size(); ++i)
             if (ctx->cache[i].last_use < ctx->cache[victim].last_use) victim = i;
         CTG_CK(cudaDeviceSynchronize());
+        drop_graphs(ctx, ctx->cache[victim].serial);
         cudaFree(ctx->cache[victim].fwd);
         cudaFree(ctx->cache[victim].back);
         cudaFree(ctx->cache[victim].pad);
@@ -437,6 +485,7 @@ int get_geom(ctg_ctx *ctx, const ctg_geom *g, GeomEntry **out) {
     GeomEntry e;
     e.g = *g;
     e.last_use = ++ctx->tick;
+    e.serial = e.last_use;
     e.back_window = ctg_back_window(bk.data(), g->n_angles);
     e.pl = ctg_pad_layout(g->N, g->det_spacing);
     cudaError_t err = cudaMalloc(&e.fwd, sizeof(FwdAngle) * fw.size());
@@ -516,6 +565,10 @@ cudaEvent_t next_event(ctg_ctx *ctx) {
 // `phase`, bracketed by events when tracing is on.
 template <typename F>
 cudaError_t traced(ctg_ctx *ctx, int phase, int nkern, cudaStream_t st, F f) {
+    if (ctx->capturing) {            // counted per launch of the captured graph
+        ctx->captured_kernels += nkern;
+        return f();
+    }
     ctx->kernels += nkern;
     ctx->calls[phase] += 1;
     if (!ctx->timing) return f();
@@ -552,50 +605,6 @@ int ensure_pinned(ctg_ctx *ctx, size_t count) {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Host Givens state of the Hessenberg least-squares problem
-// min || beta e1 - H_k y ||: rotations (c, s), the rotated right-hand side g
-// and the triangular factor R (column-major, leading dimension kmax).
-struct Givens {
-    int kmax;
-    std::vector<double> c, s, g, R;
-    explicit Givens(int kmax_, double beta)
-        : kmax(kmax_), c(kmax_), s(kmax_), g(kmax_ + 1, 0.0), R((size_t)kmax_ * kmax_, 0.0) {
-        g[0] = beta;
-    }
-    // Add column k (1-based) h[0..k] of H_k; returns |g_{k+1}| = rho_k.
-    double add_column(int k, const double *hin) {
-        std::vector<double> h(hin, hin + k + 1);
-        for (int i = 0; i < k - 1; ++i) {
-            const double t = c[i] * h[i] + s[i] * h[i + 1];
-            h[i + 1] = -s[i] * h[i] + c[i] * h[i + 1];
-            h[i] = t;
-        }
-        const double a = h[k - 1], b = h[k];
-        const double r = std::hypot(a, b);
-        double ck = 1.0, sk = 0.0;
-        if (b != 0.0) {
-            ck = a / r;
-            sk = b / r;
-        }
-        c[k - 1] = ck;
-        s[k - 1] = sk;
-        h[k - 1] = b != 0.0 ? r : a;
-        g[k] = -sk * g[k - 1];
-        g[k - 1] = ck * g[k - 1];
-        for (int i = 0; i < k; ++i) R[(size_t)(k - 1) * kmax + i] = h[i];
-        return std::fabs(g[k]);
-    }
-    // y = R_k^{-1} g_{1:k} (back substitution).
-    void solve(int k, double *y) const {
-        for (int i = k - 1; i >= 0; --i) {
-            double t = g[i];
-            for (int j = i + 1; j < k; ++j) t -= R[(size_t)j * kmax + i] * y[j];
-            const double d = R[(size_t)i * kmax + i];
-            y[i] = d != 0.0 ? t / d : 0.0;
-        }
-    }
-};
-
 struct SolveCtx {
     ctg_ctx *ctx;
     const ctg_geom *g;
@@ -614,9 +623,31 @@ struct SolveCtx {
     float *vm0() const { return reinterpret_cast<float *>(ws + ly.off_vm0); }
     float *vm1() const { return reinterpret_cast<float *>(ws + ly.off_vm1); }
     double *ydev() const { return reinterpret_cast<double *>(ws + ly.off_y); }
-    float *Tcol(int j) const { return reinterpret_cast<float *>(ws + ly.off_t) + (size_t)j * ly.ld_t; }
-    float *r0m() const { return reinterpret_cast<float *>(ws + ly.off_r0m); }
     double *ncpd() const { return reinterpret_cast<double *>(ws + ly.off_ncp); }
+    template <typename TT> TT *at(size_t off) const { return reinterpret_cast<TT *>(ws + off); }
+    GmresState *state() const { return at<GmresState>(ly.off_state); }
+    // device pointers of the loop state for the loop kernels
+    LoopBufs loop_bufs() const {
+        LoopBufs B{};
+        B.S = state();
+        B.H = at<double>(ly.off_h);
+        B.ldh = ly.kmax + 1;
+        B.gc = at<double>(ly.off_gc);
+        B.gs = at<double>(ly.off_gs);
+        B.gg = at<double>(ly.off_gg);
+        B.R = at<double>(ly.off_R);
+        B.ldr = ly.kmax;
+        B.y = ydev();
+        B.yring = at<double>(ly.off_yring);
+        B.z = at<double>(ly.off_z);
+        B.hist = at<double>(ly.off_hist);
+        B.rhoh = at<double>(ly.off_rhoh);
+        B.ncph = at<double>(ly.off_ncph);
+        B.scal = rs.scal;
+        B.h1 = rs.h1;
+        B.counter = rs.counter;
+        return B;
+    }
     // *out (device) = the NCP distance of the residual sinogram r
     cudaError_t ncp(const float *r, double *out) const {
         return traced(ctx, 3, 2, st, [&] {
@@ -624,11 +655,12 @@ struct SolveCtx {
         });
     }
 
-    cudaError_t forward(const void *x, float *b, int xtype = CTG_BASIS_FP32) const {
+    // b = A x; x of type xtype, column xc of a basis when xc.k is set
+    cudaError_t forward(const void *x, float *b, int xtype = CTG_BASIS_FP32, ColRef xc = col_none()) const {
         // the image staging is traced as phase 3, so that phase 0 times the
         // Joseph kernel alone
         const cudaError_t e = traced(ctx, 3, 1, st, [&] {
-            return ctg_launch_pad(x, xtype, pad(), g->N, ge->pl, st);
+            return ctg_launch_pad(x, xtype, pad(), g->N, ge->pl, st, xc);
         });
         if (e != cudaSuccess) return e;
         return traced(ctx, 0, 1, st, [&] {
@@ -636,26 +668,38 @@ struct SolveCtx {
                                       ge->fwd_shape, ge->order_for(ge->fwd_shape));
         });
     }
-    cudaError_t back(const void *b, const float *add, float *x, int btype = CTG_BASIS_FP32) const {
-        return traced(ctx, 1, 1, st, [&] { return back_apply(ge, b, btype, add, x, st); });
-    }
-    cudaError_t cgs2(int64_t L, int k, float *q) const {
-        int nk = 0;
-        const cudaError_t e = traced(ctx, 2, 0, st, [&] {
-            return ctg_cgs2_step(W(), ly.dtype, ly.ld_w, L, k, q, Wcol(k), Hcol(k), rs, st, &nk);
+    // b = A x and b2 = A x2 in one walk (x: column xc of the basis)
+    cudaError_t forward2(ColRef xc, const float *x2, float *b, float *b2) const {
+        float4 *p4 = reinterpret_cast<float4 *>(pad());
+        const cudaError_t e = traced(ctx, 3, 1, st, [&] {
+            return ctg_launch_pad2(W(), ly.dtype, xc, x2, p4, g->N, ge->pl, st);
         });
-        ctx->kernels += nk;
+        if (e != cudaSuccess) return e;
+        return traced(ctx, 0, 1, st, [&] {
+            return ctg_launch_forward2(p4, g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, b, b2, st,
+                                       ge->fwd_shape, ge->order_for(ge->fwd_shape));
+        });
+    }
+    cudaError_t back(const void *b, const float *add, float *x, int btype = CTG_BASIS_FP32,
+                     ColRef bc = col_none()) const {
+        return traced(ctx, 1, 1, st, [&] { return back_apply(ge, b, btype, add, x, st, bc); });
+    }
+    // one CGS2 step of the loop (k on the device)
+    cudaError_t cgs2_loop(int64_t L, float *q, int kmax, bool fused, bool cooperative) const {
+        int nk = 0;
+        const LoopStep ls{&state()->k, at<double>(ly.off_h), ly.kmax + 1, kmax, fused};
+        const cudaError_t e = traced(ctx, 2, 0, st, [&] {
+            return ctg_cgs2_step_loop(W(), ly.dtype, ly.ld_w, L, q, ls, rs, ctx->spin_limit, cooperative, st, &nk);
+        });
+        if (ctx->capturing) ctx->captured_kernels += nk;
+        else ctx->kernels += nk;
         return e;
     }
-    cudaError_t gemv(int64_t L, int k, const float *base, float *out) const {
+    // out = base + W y with k = *kdev + koff columns (kmax bounds it)
+    cudaError_t gemv_dev(int64_t L, const int *kdev, int koff, int kmax, const double *y, const float *base,
+                         float *out) const {
         return traced(ctx, 3, 1, st, [&] {
-            return ctg_gemv(W(), ly.dtype, ly.ld_w, L, k, ydev(), base, out, st);
-        });
-    }
-    cudaError_t gemv_norm2(const float *V, size_t ldv, int64_t L, int k, const float *base,
-                           double *res) const {
-        return traced(ctx, 3, 1, st, [&] {
-            return ctg_gemv_norm2(V, ldv, L, k, ydev(), base, res, rs, st);
+            return ctg_gemv(W(), ly.dtype, ly.ld_w, L, kmax, y, base, out, st, kdev, koff);
         });
     }
     cudaError_t sub_norm2(const float *a, const float *c, float *out, int64_t L, double *res) const {
@@ -674,12 +718,6 @@ struct SolveCtx {
         CTG_CK(cudaMemcpyAsync(hs, src, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
         CTG_CK(cudaStreamSynchronize(st));
         *host = hs;
-        return CTG_OK;
-    }
-    int upload_y(const double *y, int k) const {
-        double *hs = pinned_scratch();
-        std::memcpy(hs, y, sizeof(double) * k);
-        CTG_CK(cudaMemcpyAsync(ydev(), hs, sizeof(double) * k, cudaMemcpyHostToDevice, st));
         return CTG_OK;
     }
     // ||b - A x||, using vm1 as scratch
@@ -705,8 +743,8 @@ int solve_setup(ctg_ctx *ctx, const ctg_geom *g, int variant, const ctg_opts *o,
     sc->st = static_cast<cudaStream_t>(stream);
     int rc = get_geom(ctx, g, &sc->ge);
     if (rc) return rc;
-    // after the ring: y_k (maxit doubles) or a staged LsqState
-    rc = ensure_pinned(ctx, kRing * ring_slot_doubles(o->maxit) + (size_t)o->maxit + 64);
+    // after the ring: a GMRES solve's state and histories, or a staged LsqState
+    rc = ensure_pinned(ctx, kRing * ring_slot_doubles(o->maxit) + 3 * (size_t)o->maxit + 64);
     if (rc) return rc;
     if (ws == nullptr) {
         cudaError_t e = cudaMallocAsync(&ws, sc->ly.total, sc->st);
@@ -721,7 +759,7 @@ int solve_setup(ctg_ctx *ctx, const ctg_geom *g, int variant, const ctg_opts *o,
     ctg_red_scratch_carve(sc->ws + sc->ly.off_red, sc->ly.n > sc->ly.m ? sc->ly.n : sc->ly.m,
                           lsq ? 2 : o->maxit + 1, &sc->rs);
     CTG_CK(cudaMemsetAsync(sc->rs.counter, 0, 4 * sizeof(unsigned), sc->st));
-    CTG_CK(cudaMemsetAsync(sc->pad(), 0, sizeof(float) * sc->ge->pl.floats, sc->st));
+    CTG_CK(cudaMemsetAsync(sc->pad(), 0, sizeof(float) * sc->ge->pl.floats * (sc->ly.pad2 ? 2 : 1), sc->st));
     if (!lsq)
         CTG_CK(cudaMemsetAsync(sc->ws + sc->ly.off_h, 0,
                                sizeof(double) * (size_t)(o->maxit + 1) * o->maxit, sc->st));
@@ -757,32 +795,11 @@ int copy_x0(const SolveCtx &sc, const float *x0, float *x) {
     return CTG_OK;
 }
 
-// Geometric extrapolation of a decreasing residual sequence `steps` values
-// ahead of the last one, from the last two.  Used only to decide whether to
-// enqueue Arnoldi steps before the current one has been checked.
-bool predicts_stop(const std::vector<double> &r, double target, int steps = 1) {
-    const size_t n = r.size();
-    if (n < 2 || target <= 0.0) return false;
-    const double a = r[n - 2], c = r[n - 1];
-    double pred = c;
-    if (a > 0.0)
-        for (int i = 0; i < steps; ++i) pred *= c / a;
-    return pred <= target * 1.05;
-}
-
 struct Pipeline {
     SolveCtx &sc;
     int maxit;
     cudaEvent_t *ev_h, *ev_r;
     double *slot(int k) const { return sc.ctx->pinned + (size_t)(k % kRing) * ring_slot_doubles(maxit); }
-    // H column k at slot[0..k], ||q_pre||^2 at slot[k+1]
-    int after_step(int k) const {
-        double *sl = slot(k);
-        CTG_CK(cudaMemcpyAsync(sl, sc.Hcol(k), sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, sc.st));
-        CTG_CK(cudaMemcpyAsync(sl + k + 1, sc.rs.scal, sizeof(double), cudaMemcpyDeviceToHost, sc.st));
-        CTG_CK(cudaEventRecord(ev_h[k % kRing], sc.st));
-        return CTG_OK;
-    }
     int wait_step(int k, const double **h) const {
         CTG_CK(cudaEventSynchronize(ev_h[k % kRing]));
         *h = slot(k);
@@ -792,268 +809,352 @@ struct Pipeline {
 
 int ensure_events(ctg_ctx *ctx);
 
-// AB-GMRES, Sec. 2 left column.  The Arnoldi recurrence does not depend on
-// the least-squares solve, so step k+1 is enqueued before the host reads
-// step k's Hessenberg column (unless the residual trend predicts a stop at
-// k); the GPU then never waits for the host's Givens update.
-int run_ab(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_opts *o,
-           ctg_info *info) {
-    const int64_t m = sc.ly.m;
-    const bool use_ncp = o->stop_rule == CTG_RULE_NCP;
-    const bool dp = !use_ncp && o->noise_norm > 0.0;
-    const double target = dp ? o->tau * o->noise_norm : 0.0;
-    double beta = 0.0;
-    // r0 = b - A x0 (FP32, in vm0); beta = ||r0||
-    if (x0) {
-        CTG_CK(sc.forward(x0, sc.vm0()));
-        CTG_CK(sc.sub_norm2(b, sc.vm0(), sc.vm0(), m, sc.rs.scal + 2));
+// ---------------------------------------------------------------------------
+// AB-GMRES and BA-GMRES (Sec. 2 algorithm box) as a loop that runs on the
+// device.  The kernels of a step read k from the solve's device state
+// (GmresState); the FP64 Givens update, y_k and the stopping rule of Sec.
+// 6.4 are device kernels too (gmres_loop.cu), and the kernel that ends a
+// step advances k or stops the solve.  So the whole solve is one CUDA graph:
+// the start (r0, beta, w_1), two while-loop nodes over the steps (the first
+// with the one-launch CGS2 step for k <= 64, the second with its separate
+// passes) and the exit (y_k, x_k and its true residual), launched once and
+// read back once.  With phase tracing on (or where such a graph cannot be
+// built) the host enqueues the same kernels step by step instead and reads
+// the activity flag after each step.
+//
+// A step, AB (basis length m):  t = B w_k;  q = A t;  CGS2;  Givens and
+//   the stop (DP on rho_k = ||b - A x_k||, equal in exact arithmetic).
+//   With NCP: y_k, r_k = W_{k+1} z_k, its NCP distance, the stop.
+// A step, BA (basis length n), with t_k = A w_k from the step before:
+//   q = B t_k;  CGS2;  Givens;  with DP / NCP x_k = x0 + W_k y_k, then
+//   t_{k+1} = A w_{k+1} and A x_k in one two-image walk, ||b - A x_k||
+//   (and its NCP distance) and the stop.  No A W_k is stored: the basis is
+//   the only O(k L) storage, the storage law of Table 3.
+
+struct LoopPlan {
+    int variant, rule, maxit;
+    double target;
+    bool fused;        // the one-launch CGS2 step serves k <= fused_max
+    int fused_max;
+    bool cooperative;  // launch it cooperatively
+};
+
+int enqueue_init(SolveCtx &sc, const LoopPlan &lp, const float *b, const float *x0, const LoopBufs &B) {
+    const int64_t n = sc.ly.n, m = sc.ly.m;
+    double *scal = sc.rs.scal;
+    if (lp.variant == CTG_AB) {
+        // r0 = b - A x0 in vm0, ||r0||^2 -> scal[2]
+        if (x0) {
+            CTG_CK(sc.forward(x0, sc.vm0()));
+            CTG_CK(sc.sub_norm2(b, sc.vm0(), sc.vm0(), m, scal + 2));
+        } else {
+            CTG_CK(sc.sub_norm2(b, nullptr, sc.vm0(), m, scal + 2));
+        }
+        if (lp.rule == kRuleNCP) CTG_CK(sc.ncp(sc.vm0(), scal + 6));
+        CTG_CK(sc.scale(sc.vm0(), scal + 2, sc.Wcol(0), m));              // w_1 = r0 / beta
     } else {
-        CTG_CK(sc.sub_norm2(b, nullptr, sc.vm0(), m, sc.rs.scal + 2));
-    }
-    int rc = CTG_OK;
-    std::vector<double> dncp;        // NCP distances d_0, d_1, ...
-    if (use_ncp) {
-        if ((rc = ensure_twiddles(sc.ge))) return rc;
-        CTG_CK(sc.ncp(sc.vm0(), sc.rs.scal + 6));
-    }
-    // ||r0||^2 (and d_0) are read back behind the first Arnoldi step, which
-    // needs no host value (w_1 = r0 / ||r0|| on the device; 0 when r0 = 0)
-    if ((rc = ensure_events(sc.ctx))) return rc;
-    double *init = sc.pinned_scratch();
-    CTG_CK(cudaMemcpyAsync(init, sc.rs.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, sc.st));
-    if (use_ncp) CTG_CK(cudaMemcpyAsync(init + 1, sc.rs.scal + 6, sizeof(double), cudaMemcpyDeviceToHost, sc.st));
-    CTG_CK(cudaEventRecord(sc.ctx->ev_init, sc.st));
-    CTG_CK(sc.scale(sc.vm0(), sc.rs.scal + 2, sc.Wcol(0), m));   // w_1 = r0 / beta
-    Pipeline pl{sc, o->maxit, sc.ctx->ev_h, sc.ctx->ev_r};
-    // NCP: r_k = r0 - A B W_k y_k = W_{k+1} (beta e1 - H_k y_k), one read of
-    // W, then its NCP distance, read back through the ring slot
-    std::vector<double> Hh(use_ncp ? (size_t)(o->maxit + 1) * o->maxit : 0), yk(o->maxit);
-    auto enqueue_ncp = [&](int kk) -> int {
-        double *cf = pl.slot(kk) + o->maxit + 4;
-        for (int i = 0; i <= kk; ++i) {
-            double t = i == 0 ? beta : 0.0;
-            for (int j = std::max(0, i - 1); j < kk; ++j) t -= Hh[(size_t)j * (o->maxit + 1) + i] * yk[j];
-            cf[i] = t;
+        // r = b - A x0 in vm1 (||r||^2 -> scal[4]); r0 = B r, ||r0||^2 -> scal[2]
+        if (x0) {
+            CTG_CK(sc.forward(x0, sc.vm0()));
+            CTG_CK(sc.sub_norm2(b, sc.vm0(), sc.vm1(), m, scal + 4));
+        } else {
+            CTG_CK(sc.sub_norm2(b, nullptr, sc.vm1(), m, scal + 4));
         }
-        CTG_CK(cudaMemcpyAsync(sc.ydev(), cf, sizeof(double) * (kk + 1), cudaMemcpyHostToDevice, sc.st));
-        CTG_CK(sc.gemv(m, kk + 1, nullptr, sc.vm1()));
-        CTG_CK(sc.ncp(sc.vm1(), sc.rs.scal + 6));
-        CTG_CK(cudaMemcpyAsync(pl.slot(kk) + o->maxit + 3, sc.rs.scal + 6, sizeof(double),
-                               cudaMemcpyDeviceToHost, sc.st));
-        CTG_CK(cudaEventRecord(pl.ev_r[kk % kRing], sc.st));
-        return CTG_OK;
-    };
-    auto enqueue = [&](int kk) -> int {
-        CTG_CK(sc.back(sc.Wcol(kk - 1), nullptr, sc.vn0(), sc.ly.dtype));   // t = B w_k
-        CTG_CK(sc.forward(sc.vn0(), sc.vm0()));                    // q = A t
-        CTG_CK(sc.cgs2(m, kk, sc.vm0()));
-        return pl.after_step(kk);
-    };
-    if ((rc = enqueue(1))) return rc;
-    CTG_CK(cudaEventSynchronize(sc.ctx->ev_init));
-    beta = std::sqrt(init[0]);
-    if (use_ncp) dncp.push_back(init[1]);
-    if (info->history) info->history[0] = beta;
-    info->rho = beta;
-    info->resnorm = beta;
-    if ((dp && beta <= target) || beta == 0.0) {       // the enqueued step is discarded
-        info->stop_reason = beta == 0.0 && !(dp && beta <= target) ? CTG_STOP_BREAKDOWN : CTG_STOP_DP;
-        return copy_x0(sc, x0, x);
+        if (lp.rule == kRuleNCP) CTG_CK(sc.ncp(sc.vm1(), scal + 6));
+        CTG_CK(sc.back(sc.vm1(), nullptr, sc.vn0()));
+        CTG_CK(sc.sub_norm2(sc.vn0(), nullptr, nullptr, n, scal + 2));
+        CTG_CK(sc.scale(sc.vn0(), scal + 2, sc.Wcol(0), n));              // w_1 = r0 / beta
+        CTG_CK(sc.forward(sc.Wcol(0), sc.vm0(), sc.ly.dtype));            // t_1 = A w_1
     }
-    Givens gv(o->maxit, beta);
-    std::vector<double> rhos{beta};
-    int next = 2, k = 0;
-    for (k = 1; k <= o->maxit; ++k) {
-        if (next == k && (rc = enqueue(next++))) return rc;
-        if (next == k + 1 && k + 1 <= o->maxit && !(dp && predicts_stop(rhos, target)))
-            if ((rc = enqueue(next++))) return rc;
-        const double *h;
-        if ((rc = pl.wait_step(k, &h))) return rc;
-        const bool breakdown = h[k] <= kBreakdownRtol * std::sqrt(h[k + 1]);
-        const double rho = gv.add_column(k, h);
-        rhos.push_back(rho);
-        info->rho = rho;
-        if (info->history) info->history[k] = rho;
-        if (breakdown) {
-            info->stop_reason = CTG_STOP_BREAKDOWN;
-            break;
-        }
-        if (dp && rho <= target) {
-            info->stop_reason = CTG_STOP_DP;
-            break;
-        }
-        if (use_ncp) {
-            for (int i = 0; i <= k; ++i) Hh[(size_t)(k - 1) * (o->maxit + 1) + i] = h[i];
-            gv.solve(k, yk.data());
-            if ((rc = enqueue_ncp(k))) return rc;
-            // keep the GPU busy while d_k is read back
-            if (next == k + 2 && k + 2 <= o->maxit && (rc = enqueue(next++))) return rc;
-            CTG_CK(cudaEventSynchronize(pl.ev_r[k % kRing]));
-            dncp.push_back(pl.slot(k)[o->maxit + 3]);
-            if (dncp[k] > dncp[k - 1]) {          // first local minimum: x_{k-1}
-                info->stop_reason = CTG_STOP_NCP;
-                --k;
-                info->rho = rhos[k];
-                break;
-            }
-        }
-    }
-    if (k > o->maxit) k = o->maxit;
-    info->iters = k;
-    if (info->ncp_history)
-        for (size_t i = 0; i < dncp.size(); ++i) info->ncp_history[i] = dncp[i];
-    if (k == 0) {
-        if ((rc = copy_x0(sc, x0, x))) return rc;
-        return sc.true_resnorm(b, x, &info->resnorm);
-    }
-    // x_k = x0 + B (W_k y_k)
-    std::vector<double> y(k);
-    gv.solve(k, y.data());
-    if ((rc = sc.upload_y(y.data(), k))) return rc;
-    CTG_CK(sc.gemv(m, k, nullptr, sc.vm0()));
-    CTG_CK(sc.back(sc.vm0(), x0, x));
-    return sc.true_resnorm(b, x, &info->resnorm);
+    CTG_CK(traced(sc.ctx, 3, 1, sc.st, [&] {
+        return ctg_loop_init(B, lp.variant, lp.rule, lp.maxit, lp.target, sc.st);
+    }));
+    return CTG_OK;
 }
 
-// BA-GMRES, Sec. 2 right column.  Pipelined like AB; in addition the DP
-// test needs the true residual of x_k, which is enqueued behind the next
-// Arnoldi step(s) and read back one step later.
-int run_ba(SolveCtx &sc, const float *b, const float *x0, float *x, const ctg_opts *o,
-           ctg_info *info) {
+int enqueue_step(SolveCtx &sc, const LoopPlan &lp, const float *b, const float *x0, float *x,
+                 const LoopBufs &B, bool fused) {
     const int64_t n = sc.ly.n, m = sc.ly.m;
-    const bool use_ncp = o->stop_rule == CTG_RULE_NCP;
-    const bool dp = !use_ncp && o->noise_norm > 0.0;
-    const double target = dp ? o->tau * o->noise_norm : 0.0;
-    // r = b - A x0 (m-vector, kept for the DP residuals) and its norm;
-    // r0 = B r into w_1's slot
-    if (x0) {
-        CTG_CK(sc.forward(x0, sc.vm0()));
-        CTG_CK(sc.sub_norm2(b, sc.vm0(), sc.r0m(), m, sc.rs.scal + 4));
-    } else {
-        CTG_CK(sc.sub_norm2(b, nullptr, sc.r0m(), m, sc.rs.scal + 4));
-    }
-    CTG_CK(sc.back(sc.r0m(), nullptr, sc.vn0()));
-    CTG_CK(sc.sub_norm2(sc.vn0(), nullptr, nullptr, n, sc.rs.scal + 2));
-    int rc = CTG_OK;
-    std::vector<double> dncp;        // NCP distances d_0, d_1, ...
-    if (use_ncp) {
-        if ((rc = ensure_twiddles(sc.ge))) return rc;
-        CTG_CK(sc.ncp(sc.r0m(), sc.rs.scal + 6));
-    }
-    // ||B r||^2, ||r||^2 (and d_0) are read back behind the first Arnoldi
-    // step, which needs no host value
-    if ((rc = ensure_events(sc.ctx))) return rc;
-    double *init = sc.pinned_scratch();
-    CTG_CK(cudaMemcpyAsync(init, sc.rs.scal + 2, sizeof(double) * 3, cudaMemcpyDeviceToHost, sc.st));
-    if (use_ncp) CTG_CK(cudaMemcpyAsync(init + 3, sc.rs.scal + 6, sizeof(double), cudaMemcpyDeviceToHost, sc.st));
-    CTG_CK(cudaEventRecord(sc.ctx->ev_init, sc.st));
-    CTG_CK(sc.scale(sc.vn0(), sc.rs.scal + 2, sc.Wcol(0), n));   // w_1 = r0 / beta
-    Pipeline pl{sc, o->maxit, sc.ctx->ev_h, sc.ctx->ev_r};
-    auto enqueue = [&](int kk) -> int {
-        CTG_CK(sc.forward(sc.Wcol(kk - 1), sc.Tcol(kk - 1), sc.ly.dtype));  // t = A w_k, kept in T
-        CTG_CK(sc.back(sc.Tcol(kk - 1), nullptr, sc.vn0()));       // q = B t
-        CTG_CK(sc.cgs2(n, kk, sc.vn0()));
-        return pl.after_step(kk);
+    const int *kdev = &sc.state()->k;
+    const int kmax = fused ? lp.fused_max : lp.maxit;
+    auto givens = [&](bool need_y, bool need_z, bool end) {
+        return traced(sc.ctx, 3, 1, sc.st, [&] {
+            return ctg_loop_givens(B, need_y, need_z, end, lp.maxit, sc.st);
+        });
     };
-    // ||b - A x_k||^2 = ||(b - A x0) - T_k y_k||^2 (A x_k = A x0 + A W_k y_k,
-    // and the columns of A W_k are the t vectors of the Arnoldi steps), read
-    // back through the pinned slot
-    auto enqueue_residual = [&](int kk, const double *y) -> int {
-        double *ys = pl.slot(kk) + o->maxit + 4;
-        for (int i = 0; i < kk; ++i) ys[i] = -y[i];
-        CTG_CK(cudaMemcpyAsync(sc.ydev(), ys, sizeof(double) * kk, cudaMemcpyHostToDevice, sc.st));
-        CTG_CK(sc.gemv_norm2(sc.Tcol(0), sc.ly.ld_t, m, kk, sc.r0m(), sc.rs.scal + 4));
-        CTG_CK(cudaMemcpyAsync(pl.slot(kk) + o->maxit + 2, sc.rs.scal + 4, sizeof(double),
-                               cudaMemcpyDeviceToHost, sc.st));
-        CTG_CK(cudaEventRecord(pl.ev_r[kk % kRing], sc.st));
+    if (lp.variant == CTG_AB) {
+        CTG_CK(sc.back(sc.W(), nullptr, sc.vn0(), sc.ly.dtype, col_at(kdev, -1, (long long)sc.ly.ld_w)));
+        CTG_CK(sc.forward(sc.vn0(), sc.vm0()));                           // q = A B w_k
+        CTG_CK(sc.cgs2_loop(m, sc.vm0(), kmax, fused, lp.cooperative));
+        const bool ncp = lp.rule == kRuleNCP;
+        CTG_CK(givens(ncp, ncp, !ncp));
+        if (ncp) {
+            // r_k = W_{k+1} z_k, its NCP distance, the stop
+            CTG_CK(sc.gemv_dev(m, kdev, 1, kmax + 1, B.z, nullptr, sc.vm1()));
+            CTG_CK(sc.ncp(sc.vm1(), sc.rs.scal + 6));
+            CTG_CK(traced(sc.ctx, 3, 1, sc.st, [&] { return ctg_loop_ncp_decide(B, sc.st); }));
+        }
         return CTG_OK;
-    };
-    // NCP: r_k = (b - A x0) - T_k y_k, then its NCP distance
-    auto enqueue_ncp = [&](int kk, const double *yy) -> int {
-        double *ys = pl.slot(kk) + o->maxit + 4;
-        for (int i = 0; i < kk; ++i) ys[i] = -yy[i];
-        CTG_CK(cudaMemcpyAsync(sc.ydev(), ys, sizeof(double) * kk, cudaMemcpyHostToDevice, sc.st));
+    }
+    CTG_CK(sc.back(sc.vm0(), nullptr, sc.vn0()));                         // q = B t_k
+    CTG_CK(sc.cgs2_loop(n, sc.vn0(), kmax, fused, lp.cooperative));
+    const bool resid = lp.rule != kRuleMaxit;
+    CTG_CK(givens(resid, false, false));
+    const ColRef wnext = col_at(kdev, 0, (long long)sc.ly.ld_w);         // w_{k+1}
+    if (!resid) {
+        CTG_CK(sc.forward(sc.W(), sc.vm0(), sc.ly.dtype, wnext));         // t_{k+1}
+        CTG_CK(traced(sc.ctx, 3, 1, sc.st, [&] { return ctg_loop_advance(B, sc.st); }));
+        return CTG_OK;
+    }
+    CTG_CK(sc.gemv_dev(n, kdev, 0, kmax, B.y, x0, x));                   // x_k = x0 + W_k y_k
+    CTG_CK(sc.forward2(wnext, x, sc.vm0(), sc.vm1()));                    // t_{k+1}, A x_k
+    if (lp.rule == kRuleDP) {
         CTG_CK(traced(sc.ctx, 3, 1, sc.st, [&] {
-            return ctg_gemv(sc.Tcol(0), CTG_BASIS_FP32, sc.ly.ld_t, m, kk, sc.ydev(), sc.r0m(), sc.vm1(),
-                            sc.st);
+            return ctg_loop_resid(B, b, sc.vm1(), nullptr, m, sc.rs, true, sc.st);
+        }));
+    } else {
+        CTG_CK(traced(sc.ctx, 3, 1, sc.st, [&] {
+            return ctg_loop_resid(B, b, sc.vm1(), sc.vm1(), m, sc.rs, false, sc.st);
         }));
         CTG_CK(sc.ncp(sc.vm1(), sc.rs.scal + 6));
-        CTG_CK(cudaMemcpyAsync(pl.slot(kk) + o->maxit + 3, sc.rs.scal + 6, sizeof(double),
-                               cudaMemcpyDeviceToHost, sc.st));
-        CTG_CK(cudaEventRecord(pl.ev_r[kk % kRing], sc.st));
-        return CTG_OK;
-    };
-    if ((rc = enqueue(1))) return rc;
-    CTG_CK(cudaEventSynchronize(sc.ctx->ev_init));
-    const double beta = std::sqrt(init[0]), res0 = std::sqrt(init[2]);
-    if (use_ncp) dncp.push_back(init[3]);
-    if (info->history) info->history[0] = dp ? res0 : beta;
-    info->rho = beta;
-    info->resnorm = res0;
-    if ((dp && res0 <= target) || beta == 0.0) {        // the enqueued step is discarded
-        info->stop_reason = beta == 0.0 && !(dp && res0 <= target) ? CTG_STOP_BREAKDOWN : CTG_STOP_DP;
-        return copy_x0(sc, x0, x);
+        CTG_CK(traced(sc.ctx, 3, 1, sc.st, [&] { return ctg_loop_ncp_decide(B, sc.st); }));
     }
-    Givens gv(o->maxit, beta);
-    std::vector<double> y(o->maxit), res{res0}, rhos{beta};
-    int next = 2, k = 0;
-    for (k = 1; k <= o->maxit; ++k) {
-        if (next == k && (rc = enqueue(next++))) return rc;
-        if (next == k + 1 && k + 1 <= o->maxit && !(dp && predicts_stop(res, target)))
-            if ((rc = enqueue(next++))) return rc;
-        const double *h;
-        if ((rc = pl.wait_step(k, &h))) return rc;
-        const bool breakdown = h[k] <= kBreakdownRtol * std::sqrt(h[k + 1]);
-        const double rho = gv.add_column(k, h);
-        info->rho = rho;
-        const bool last = breakdown || k == o->maxit;
-        if (dp) {
-            gv.solve(k, y.data());
-            if ((rc = enqueue_residual(k, y.data()))) return rc;
-            // keep the GPU busy while the residual is read back
-            if (dp && !last && next == k + 2 && k + 2 <= o->maxit && !predicts_stop(res, target, 2))
-                if ((rc = enqueue(next++))) return rc;
-            CTG_CK(cudaEventSynchronize(pl.ev_r[k % kRing]));
-            info->resnorm = std::sqrt(pl.slot(k)[o->maxit + 2]);
-            res.push_back(info->resnorm);
-        }
-        if (info->history) info->history[k] = dp ? info->resnorm : rho;
-        if (breakdown) {
-            info->stop_reason = CTG_STOP_BREAKDOWN;
-            break;
-        }
-        if (dp && info->resnorm <= target) {
-            info->stop_reason = CTG_STOP_DP;
-            break;
-        }
-        rhos.push_back(rho);
-        if (use_ncp) {
-            gv.solve(k, y.data());
-            if ((rc = enqueue_ncp(k, y.data()))) return rc;
-            if (!last && next == k + 2 && k + 2 <= o->maxit && (rc = enqueue(next++))) return rc;
-            CTG_CK(cudaEventSynchronize(pl.ev_r[k % kRing]));
-            dncp.push_back(pl.slot(k)[o->maxit + 3]);
-            if (dncp[k] > dncp[k - 1]) {          // first local minimum: x_{k-1}
-                info->stop_reason = CTG_STOP_NCP;
-                --k;
-                info->rho = rhos[k];
-                break;
+    return CTG_OK;
+}
+
+// y of the returned iterate, x = x0 + B W y (AB) or x0 + W y (BA), and
+// ||b - A x||.
+int enqueue_exit(SolveCtx &sc, const LoopPlan &lp, const float *b, const float *x0, float *x,
+                 const LoopBufs &B) {
+    const int *idev = &sc.state()->iters;
+    CTG_CK(traced(sc.ctx, 3, 1, sc.st, [&] { return ctg_loop_exit_y(B, lp.maxit, sc.st); }));
+    if (lp.variant == CTG_AB) {
+        CTG_CK(sc.gemv_dev(sc.ly.m, idev, 0, lp.maxit, B.y, nullptr, sc.vm0()));
+        CTG_CK(sc.back(sc.vm0(), x0, x));
+    } else {
+        CTG_CK(sc.gemv_dev(sc.ly.n, idev, 0, lp.maxit, B.y, x0, x));
+    }
+    CTG_CK(sc.forward(x, sc.vm1()));
+    CTG_CK(sc.sub_norm2(b, sc.vm1(), nullptr, sc.ly.m, sc.rs.scal + 5));
+    CTG_CK(traced(sc.ctx, 3, 1, sc.st, [&] { return ctg_loop_final(B, sc.st); }));
+    return CTG_OK;
+}
+
+int ensure_capture_streams(ctg_ctx *ctx) {
+    for (int i = 0; i < 2; ++i)
+        if (!ctx->cap_st[i]) CTG_CK(cudaStreamCreateWithFlags(&ctx->cap_st[i], cudaStreamNonBlocking));
+    return CTG_OK;
+}
+
+// Captures the whole solve into an executable graph (see above).
+int build_loop_graph(SolveCtx &sc, const LoopPlan &lp, const float *b, const float *x0, float *x,
+                     ctg_ctx::LoopGraph *out) {
+    ctg_ctx *ctx = sc.ctx;
+    int rc = ensure_capture_streams(ctx);
+    if (rc) return rc;
+    cudaStream_t user = sc.st;
+    cudaStream_t cs = ctx->cap_st[0], bs = ctx->cap_st[1];
+    const bool use_fused = lp.fused, use_pass = !lp.fused || lp.maxit > lp.fused_max;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ctx->capturing = true;
+    auto fail = [&](cudaError_t e) {
+        ctx->capturing = false;
+        sc.st = user;
+        cudaStreamCaptureStatus st_ = cudaStreamCaptureStatusNone;
+        for (cudaStream_t q : {cs, bs})
+            if (cudaStreamIsCapturing(q, &st_) == cudaSuccess && st_ != cudaStreamCaptureStatusNone) {
+                cudaGraph_t g2 = nullptr;
+                cudaStreamEndCapture(q, &g2);
+                if (g2) cudaGraphDestroy(g2);
             }
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail_cuda(e == cudaSuccess ? cudaErrorUnknown : e);
+    };
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return fail(e);
+    LoopBufs B = sc.loop_bufs();
+    B.in_graph = 1;
+    B.fused_max = lp.fused ? lp.fused_max : 0;
+    // the handles belong to the graph being captured
+    cudaStreamCaptureStatus cstat;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    if ((e = cudaStreamGetCaptureInfo(cs, &cstat, nullptr, &cg, &deps, nullptr, &ndeps)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaGraphConditionalHandleCreate(&B.c_fused, cg, use_fused ? 1u : 0u, cudaGraphCondAssignDefault)) !=
+        cudaSuccess)
+        return fail(e);
+    if ((e = cudaGraphConditionalHandleCreate(&B.c_pass, cg, 1u, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return fail(e);
+    const long long k0 = ctx->captured_kernels;
+    sc.st = cs;
+    if ((rc = enqueue_init(sc, lp, b, x0, B))) return fail(cudaErrorUnknown);
+    out->n_init = (int)(ctx->captured_kernels - k0);
+    // while-loop nodes: their bodies are captured on the second stream
+    auto add_loop = [&](cudaGraphConditionalHandle h, bool fused, int *nkern) -> cudaError_t {
+        cudaError_t e2 = cudaStreamGetCaptureInfo(cs, &cstat, nullptr, &cg, &deps, nullptr, &ndeps);
+        if (e2 != cudaSuccess) return e2;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        if ((e2 = cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp)) != cudaSuccess) return e2;
+        if ((e2 = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+            cudaSuccess)
+            return e2;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if ((e2 = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+            cudaSuccess)
+            return e2;
+        sc.st = bs;
+        const long long kb = ctx->captured_kernels;
+        const int rc2 = enqueue_step(sc, lp, b, x0, x, B, fused);
+        *nkern = (int)(ctx->captured_kernels - kb);
+        sc.st = cs;
+        cudaGraph_t body_out = nullptr;
+        const cudaError_t e3 = cudaStreamEndCapture(bs, &body_out);
+        if (rc2) return cudaErrorUnknown;
+        return e3;
+    };
+    out->n_fused = out->n_pass = 0;
+    if (use_fused && (e = add_loop(B.c_fused, true, &out->n_fused)) != cudaSuccess) return fail(e);
+    if (use_pass && (e = add_loop(B.c_pass, false, &out->n_pass)) != cudaSuccess) return fail(e);
+    const long long ke = ctx->captured_kernels;
+    if ((rc = enqueue_exit(sc, lp, b, x0, x, B))) return fail(cudaErrorUnknown);
+    out->n_exit = (int)(ctx->captured_kernels - ke);
+    if ((e = cudaStreamEndCapture(cs, &graph)) != cudaSuccess) return fail(e);
+    ctx->capturing = false;
+    sc.st = user;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    graph = nullptr;
+    if (e != cudaSuccess) return fail(e);
+    out->exec = exec;
+    out->fused_max = B.fused_max;
+    return CTG_OK;
+}
+
+// Reads the solve's outcome back and fills *info.
+int read_outcome(SolveCtx &sc, const LoopPlan &lp, ctg_info *info, GmresState *hs) {
+    double *pin = sc.pinned_scratch();
+    const size_t sd = (sizeof(GmresState) + sizeof(double) - 1) / sizeof(double);
+    CTG_CK(cudaMemcpyAsync(pin, sc.state(), sizeof(GmresState), cudaMemcpyDeviceToHost, sc.st));
+    CTG_CK(cudaMemcpyAsync(pin + sd, sc.at<double>(sc.ly.off_hist), sizeof(double) * (lp.maxit + 1),
+                           cudaMemcpyDeviceToHost, sc.st));
+    if (lp.rule == kRuleNCP)
+        CTG_CK(cudaMemcpyAsync(pin + sd + lp.maxit + 1, sc.at<double>(sc.ly.off_ncph),
+                               sizeof(double) * (lp.maxit + 2), cudaMemcpyDeviceToHost, sc.st));
+    CTG_CK(cudaStreamSynchronize(sc.st));
+    std::memcpy(hs, pin, sizeof(GmresState));
+    info->iters = hs->iters;
+    info->stop_reason = hs->stop_reason;
+    info->rho = hs->rho;
+    info->resnorm = hs->resnorm;
+    if (info->history)
+        for (int k = 0; k <= hs->iters; ++k) info->history[k] = pin[sd + k];
+    if (info->ncp_history && lp.rule == kRuleNCP) {
+        // d_0 .. d_{iters+1} at an NCP stop, else the distances evaluated
+        const int last = hs->stop_reason == CTG_STOP_NCP ? hs->iters + 1 : hs->iters;
+        for (int k = 0; k <= last; ++k) info->ncp_history[k] = pin[sd + lp.maxit + 1 + k];
+    }
+    return hs->timed_out ? CTG_ERR_TIMEOUT : CTG_OK;
+}
+
+int run_gmres(SolveCtx &sc, int variant, const float *b, const float *x0, float *x, const ctg_opts *o,
+              ctg_info *info) {
+    ctg_ctx *ctx = sc.ctx;
+    LoopPlan lp{};
+    lp.variant = variant;
+    lp.rule = rule_of(o);
+    lp.maxit = o->maxit;
+    lp.target = lp.rule == kRuleDP ? o->tau * o->noise_norm : 0.0;
+    lp.fused_max = std::min(o->maxit, ctg_cgs2_fused_max());
+    lp.fused = ctg_cgs2_fused_ok(sc.ly.dtype, sc.ly.L, lp.fused_max, sc.rs);
+    if (!lp.fused) lp.fused_max = 0;
+    int rc = CTG_OK;
+    if (lp.rule == kRuleNCP && (rc = ensure_twiddles(sc.ge))) return rc;
+    GmresState hs{};
+    if (!ctx->timing && ctx->graph_mode >= 0) {
+        lp.cooperative = ctx->graph_mode != 2;
+        // the captured graph bakes in every pointer and option of the solve
+        long long target_bits = 0;
+        std::memcpy(&target_bits, &lp.target, sizeof(double));
+        const std::vector<long long> key = {
+            (long long)sc.ge->serial, sc.ge->fwd_shape, sc.ge->back_chunk, variant, o->maxit,
+            o->basis_dtype, lp.rule, target_bits, (long long)(uintptr_t)sc.ws,
+            (long long)(uintptr_t)b, (long long)(uintptr_t)x0, (long long)(uintptr_t)x, ctx->spin_limit,
+            lp.cooperative ? 1 : 0, lp.fused ? 1 : 0};
+        size_t gi = ctx->graphs.size();
+        for (size_t i = 0; i < ctx->graphs.size(); ++i)
+            if (ctx->graphs[i].key == key) gi = i;
+        if (gi == ctx->graphs.size()) {
+            ctg_ctx::LoopGraph lg{};
+            lg.key = key;
+            lg.geom_serial = sc.ge->serial;
+            rc = build_loop_graph(sc, lp, b, x0, x, &lg);
+            if (rc != CTG_OK && lp.cooperative) {
+                // a cooperative launch may not be capturable inside a loop
+                // body: fall back to the occupancy-checked plain launch
+                lp.cooperative = false;
+                lg.key[13] = 0;
+                rc = build_loop_graph(sc, lp, b, x0, x, &lg);
+                if (rc == CTG_OK) ctx->graph_mode = 2;
+            }
+            if (rc != CTG_OK) {
+                ctx->graph_mode = -1;                  // no graphs here: the host drives the loop
+            } else {
+                if (ctx->graph_mode == 0) ctx->graph_mode = 1;
+                if (ctx->graphs.size() >= 16) {
+                    cudaGraphExecDestroy(ctx->graphs.front().exec);
+                    ctx->graphs.erase(ctx->graphs.begin());
+                }
+                ctx->graphs.push_back(lg);
+                gi = ctx->graphs.size() - 1;
+            }
+        } else {
+            // most recently used last
+            std::rotate(ctx->graphs.begin() + gi, ctx->graphs.begin() + gi + 1, ctx->graphs.end());
+            gi = ctx->graphs.size() - 1;
+        }
+        if (ctx->graph_mode > 0) {
+            const ctg_ctx::LoopGraph &lg = ctx->graphs[gi];
+            CTG_CK(cudaGraphLaunch(lg.exec, sc.st));
+            rc = read_outcome(sc, lp, info, &hs);
+            const long long steps = hs.steps;
+            const long long sf = lg.n_fused ? std::min<long long>(steps, lg.fused_max) : 0;
+            ctx->kernels += lg.n_init + lg.n_exit + sf * lg.n_fused + (steps - sf) * lg.n_pass;
+            return rc;
         }
     }
-    if (k > o->maxit) k = o->maxit;
-    info->iters = k;
-    if (info->ncp_history)
-        for (size_t i = 0; i < dncp.size(); ++i) info->ncp_history[i] = dncp[i];
-    if (k == 0) {
-        if ((rc = copy_x0(sc, x0, x))) return rc;
-        return sc.true_resnorm(b, x, &info->resnorm);
+    // host-driven: the same kernels, one step at a time
+    lp.cooperative = true;
+    LoopBufs B = sc.loop_bufs();
+    B.in_graph = 0;
+    B.fused_max = lp.fused ? lp.fused_max : 0;
+    if ((rc = enqueue_init(sc, lp, b, x0, B))) return rc;
+    int *flag = reinterpret_cast<int *>(sc.pinned_scratch());
+    if ((rc = ensure_events(ctx))) return rc;
+    for (int k = 1; k <= lp.maxit; ++k) {
+        // the step is skipped when the start already stopped the solve
+        if (k == 1) {
+            CTG_CK(cudaMemcpyAsync(flag, &sc.state()->active, sizeof(int), cudaMemcpyDeviceToHost, sc.st));
+            CTG_CK(cudaEventRecord(ctx->ev_init, sc.st));
+            CTG_CK(cudaEventSynchronize(ctx->ev_init));
+            if (!*flag) break;
+        }
+        if ((rc = enqueue_step(sc, lp, b, x0, x, B, lp.fused && k <= lp.fused_max))) return rc;
+        CTG_CK(cudaMemcpyAsync(flag, &sc.state()->active, sizeof(int), cudaMemcpyDeviceToHost, sc.st));
+        CTG_CK(cudaEventRecord(ctx->ev_init, sc.st));
+        CTG_CK(cudaEventSynchronize(ctx->ev_init));
+        if (!*flag) break;
     }
-    // x_k = x0 + W_k y_k and its residual, recomputed by a forward projection
-    gv.solve(k, y.data());
-    if ((rc = sc.upload_y(y.data(), k))) return rc;
-    CTG_CK(sc.gemv(n, k, x0, x));
-    return sc.true_resnorm(b, x, &info->resnorm);
+    if ((rc = enqueue_exit(sc, lp, b, x0, x, B))) return rc;
+    return read_outcome(sc, lp, info, &hs);
 }
 
 // LSQR / LSMR (Sec. 5's comparators) with the geometry's back projector in
@@ -1186,9 +1287,8 @@ int solve(int variant, ctg_ctx *ctx, const ctg_geom *g, const float *b, const fl
         if (owned) cudaFreeAsync(owned, sc.st);
         return rc;
     }
-    rc = variant == CTG_AB   ? run_ab(sc, b, x0, x, o, info)
-         : variant == CTG_BA ? run_ba(sc, b, x0, x, o, info)
-                             : run_lsq(sc, variant, b, x0, x, o, info);
+    rc = (variant == CTG_AB || variant == CTG_BA) ? run_gmres(sc, variant, b, x0, x, o, info)
+                                                  : run_lsq(sc, variant, b, x0, x, o, info);
     if (rc == CTG_OK) {
         cudaError_t e = cudaStreamSynchronize(sc.st);
         if (e != cudaSuccess) rc = fail_cuda(e);
@@ -1229,8 +1329,18 @@ void ctg_destroy(ctg_ctx *ctx) {
         cudaFree(e.mt);
         cudaFree(e.tw);
     }
+    drop_graphs(ctx, 0);
+    for (cudaStream_t q : ctx->cap_st)
+        if (q) cudaStreamDestroy(q);
+    if (ctx->ev_init) cudaEventDestroy(ctx->ev_init);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     delete ctx;
+}
+
+int ctg_set_wait_limit(ctg_ctx *ctx, int64_t polls) {
+    if (!ctx || polls < 0) return CTG_ERR_INVALID_ARG;
+    ctx->spin_limit = polls == 0 ? kCtgDefaultSpinLimit : (long long)polls;
+    return CTG_OK;
 }
 
 int ctg_project(ctg_ctx *ctx, const ctg_geom *g, const float *x_dev, float *b_dev, void *stream) {

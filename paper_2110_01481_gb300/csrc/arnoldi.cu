@@ -13,8 +13,6 @@
 // into per-block partials, and the last block to finish (atomic ticket, no
 // waiting) sums the partials in a fixed order in FP64, so results are
 // deterministic run to run.
-#include <cooperative_groups.h>
-
 #include <atomic>
 
 #include "vecops.cuh"
@@ -164,24 +162,20 @@ __device__ __forceinline__ void cgs_pass_body(const T *__restrict__ W, int64_t l
     block_reduce_finish(s_w, nred, partials, counter, red_out, blk, G);
 }
 
+// kdev: k read on the device (a step of a captured solver loop), or NULL.
 template <typename T, int E, bool UPDATE, bool DOTS, bool NORM>
 __global__ void __launch_bounds__(kThreads, 2)
-cgs_pass_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict__ q,
-                int64_t L, const double *__restrict__ coef, float *__restrict__ partials,
-                unsigned *__restrict__ counter, double *__restrict__ red_out) {
+cgs_pass_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__restrict__ kdev,
+                float *__restrict__ q, int64_t L, const double *__restrict__ coef,
+                float *__restrict__ partials, unsigned *__restrict__ counter,
+                double *__restrict__ red_out) {
+    if (kdev) k = *kdev;
     cgs_pass_body<T, E, UPDATE, DOTS, NORM>(W, ldw, k, q, L, coef, partials, counter, red_out,
                                             blockIdx.x, gridDim.x);
 }
 
-// The three CGS2 passes and the scaling as one cooperative launch, for small
-// k, where four separate launches are bound by their latency rather than by
-// the basis reads.  The slice of q stays in registers across the passes;
-// each pass writes its per-block partial sums to its own rows of the
-// partials ([0, k] pass 1, [k+1, 2k] pass 2, 2k+1 pass 3, so no block
-// overwrites rows another block may still be reading), the grid synchronises
-// (a cooperative launch keeps every block resident), and every block sums
-// the partials of all blocks in the same fixed order in FP64, so all blocks
-// hold identical coefficients and the result is deterministic.
+// Every block sums the partial rows [row0, row0 + nrows) of all blocks in
+// one fixed order in FP64.
 __device__ __forceinline__ void reduce_rows(const float *__restrict__ partials, int row0, int nrows,
                                             int G, int Gp, double *out) {
     // each warp takes four rows at a time and reads them as float4 (four
@@ -223,19 +217,78 @@ __device__ __forceinline__ void write_rows(const float *s_w, int nred, int row0,
     }
 }
 
+// Grid-wide barrier for a launch whose blocks are all resident at once,
+// with a bounded wait: thread 0 of each block adds one arrival to *count
+// and waits until `target` arrivals are in (target = barrier index x grid
+// size, so one counter serves successive barriers).  After spin_limit polls
+// (about 100 ns apart) it gives up: it sets *err and returns false, as does
+// every block that finds *err set while it waits, so no block waits for
+// ever.  Returns true when the barrier completed.
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, long long spin_limit,
+                                             int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        int ok = 1;
+        long long spins = 0;
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if (v >= target) break;
+            int e;
+            asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(err) : "memory");
+            if (e != 0 || ++spins > spin_limit) {
+                atomicOr(err, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The three CGS2 passes and the scaling as one launch, for small k, where
+// four separate launches are bound by their latency rather than by the
+// basis reads.  The launch must keep every block resident (the host checks
+// the occupancy and launches it cooperatively); the passes are separated by
+// bounded grid barriers (grid_barrier), so a block that is not scheduled
+// makes the others give up with *err set instead of waiting for ever.  The
+// slice of q stays in registers across the passes; each pass writes its
+// per-block partial sums to its own rows of the partials ([0, k] pass 1,
+// [k+1, 2k] pass 2, so no block overwrites rows another block may still be
+// reading), and after the barrier every block sums the partials of all
+// blocks in the same fixed order in FP64, so all blocks hold identical
+// coefficients and the result is deterministic.
+// Step: k, w_out and h_out as given, or (kdev set, a step of a captured
+// solver loop) k = *kdev, w_out = column k of W and h_out = column k of H
+// (leading dimension ldh).  bar[0] counts barrier arrivals (zero at launch;
+// the last block to leave sets it back to zero); on a timeout h_out[0..k]
+// is set to NaN.
 template <typename T, int E>
 __global__ void __launch_bounds__(kThreads, 2)
-cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict__ q, int64_t L,
-                  T *__restrict__ w_out, double *__restrict__ h_out, float *__restrict__ partials,
-                  double *__restrict__ h1g, double *__restrict__ h2g, double *__restrict__ scal) {
-    namespace cg = cooperative_groups;
-    cg::grid_group grid = cg::this_grid();
+cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__restrict__ kdev,
+                  float *__restrict__ q, int64_t L, T *__restrict__ w_out, double *__restrict__ h_out,
+                  double *__restrict__ H, int64_t ldh, float *__restrict__ partials,
+                  double *__restrict__ h1g, double *__restrict__ h2g, double *__restrict__ scal,
+                  unsigned *__restrict__ bar, int *__restrict__ err, long long spin_limit) {
+    if (kdev) {
+        k = *kdev;
+        w_out = const_cast<T *>(W) + (size_t)k * ldw;
+        h_out = H + (size_t)(k - 1) * ldh;
+    }
     extern __shared__ double smem_d[];
     double *s_h1 = smem_d;                          // k + 1: h1, then ||q_pre||^2
     double *s_h2 = s_h1 + (k + 1);                  // k + 1: h2, then ||q||^2
     float *s_c = reinterpret_cast<float *>(s_h2 + (k + 1));   // k coefficients
     float *s_w = s_c + k;                           // kWarps * (k + 1)
     const int tid = threadIdx.x, blk = blockIdx.x, G = gridDim.x, Gp = padded_grid(G);
+    const unsigned nbar = k > 0 ? 2u : 1u;
     const int64_t g0 = (int64_t)blk * kThreads * E + tid;
     float4 qv[E];
 #pragma unroll
@@ -244,12 +297,14 @@ cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict
     dots_slice<T, E, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
     __syncthreads();
     write_rows(s_w, k + 1, 0, partials, Gp, blk);
-    __threadfence();
-    grid.sync();
-    reduce_rows(partials, 0, k + 1, G, Gp, s_h1);
-    __syncthreads();
-    double nrm2 = s_h1[k];
-    if (k > 0) {
+    bool ok = grid_barrier(bar, (unsigned)G, spin_limit, err);
+    double nrm2 = 0.0;
+    if (ok) {
+        reduce_rows(partials, 0, k + 1, G, Gp, s_h1);
+        __syncthreads();
+        nrm2 = s_h1[k];
+    }
+    if (ok && k > 0) {
         // pass 2: q1 = q - W h1; h2 = W^T q1, ||q1||^2
         for (int j = tid; j < k; j += kThreads) s_c[j] = (float)s_h1[j];
         __syncthreads();
@@ -257,20 +312,26 @@ cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict
         dots_slice<T, E, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
         __syncthreads();
         write_rows(s_w, k + 1, k + 1, partials, Gp, blk);
-        __threadfence();
-        grid.sync();
-        reduce_rows(partials, k + 1, k + 1, G, Gp, s_h2);
-        __syncthreads();
-        // pass 3: q2 = q1 - W h2.  With W orthonormal, ||q2||^2 = ||q1||^2 -
-        // ||h2||^2 exactly; h2 is at the rounding level of ||q1|| after the
-        // first pass, so the difference loses nothing, and the step needs no
-        // third grid-wide reduction.  Every block forms it in the same order.
-        for (int j = tid; j < k; j += kThreads) s_c[j] = (float)s_h2[j];
-        __syncthreads();
-        update_slice<T, E>(W, ldw, k, s_c, g0, L, qv);
-        double h2sq = 0.0;
-        for (int j = 0; j < k; ++j) h2sq = fma(s_h2[j], s_h2[j], h2sq);
-        nrm2 = fmax(0.0, s_h2[k] - h2sq);
+        ok = grid_barrier(bar, 2u * (unsigned)G, spin_limit, err);
+        if (ok) {
+            reduce_rows(partials, k + 1, k + 1, G, Gp, s_h2);
+            __syncthreads();
+            // pass 3: q2 = q1 - W h2.  With W orthonormal, ||q2||^2 = ||q1||^2 -
+            // ||h2||^2 exactly; h2 is at the rounding level of ||q1|| after the
+            // first pass, so the difference loses nothing, and the step needs no
+            // third grid-wide reduction.  Every block forms it in the same order.
+            for (int j = tid; j < k; j += kThreads) s_c[j] = (float)s_h2[j];
+            __syncthreads();
+            update_slice<T, E>(W, ldw, k, s_c, g0, L, qv);
+            double h2sq = 0.0;
+            for (int j = 0; j < k; ++j) h2sq = fma(s_h2[j], s_h2[j], h2sq);
+            nrm2 = fmax(0.0, s_h2[k] - h2sq);
+        }
+    }
+    if (!ok) {
+        // gave up at a barrier: leave q and W alone and mark the column
+        for (int j = tid; j <= k; j += kThreads) h_out[j] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
     }
     // w_{k+1} = q / ||q||; q keeps the orthogonalised vector
     const float inv = nrm2 > 0.0 ? (float)(1.0 / sqrt(nrm2)) : 0.0f;
@@ -293,6 +354,8 @@ cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict
             scal[1] = nrm2;
         }
     }
+    // the last block out resets the barrier counter for the next launch
+    if (tid == 0 && atomicAdd(bar, 1u) == (nbar + 1u) * (unsigned)G - 1u) atomicExch(bar, 0u);
 }
 
 // w_out = q / sqrt(nrm2) (0 if nrm2 == 0); block 0 also assembles the
@@ -366,11 +429,18 @@ __device__ __forceinline__ void update_scale_body(const T *__restrict__ W, int64
     }
 }
 
+// kdev set: k = *kdev, w_out = column k of W, h_out = column k of H.
 template <typename T, int E>
 __global__ void __launch_bounds__(kThreads, 2)
-update_scale_kernel(const T *__restrict__ W, int64_t ldw, int k, float *__restrict__ q, int64_t L,
-                    const double *__restrict__ h1, const double *__restrict__ h2, T *w_out,
-                    double *__restrict__ h_out, double *__restrict__ nrm2_out) {
+update_scale_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__restrict__ kdev,
+                    float *__restrict__ q, int64_t L, const double *__restrict__ h1,
+                    const double *__restrict__ h2, T *w_out, double *__restrict__ h_out,
+                    double *__restrict__ H, int64_t ldh, double *__restrict__ nrm2_out) {
+    if (kdev) {
+        k = *kdev;
+        w_out = const_cast<T *>(W) + (size_t)k * ldw;
+        h_out = H + (size_t)(k - 1) * ldh;
+    }
     update_scale_body<T, E>(W, ldw, k, q, L, h1, h2, w_out, h_out, nrm2_out, blockIdx.x);
 }
 
@@ -381,12 +451,14 @@ __global__ void scale_kernel(const float *q, const double *__restrict__ nrm2, T 
     scale_body<T>(q, nrm2, w_out, L, k, h1, h2, h_out, blockIdx.x, gridDim.x);
 }
 
-// out = base + sum_j y_j W_j.
+// out = base + sum_j y_j W_j (j < k; k = *kdev + koff when kdev is set).
 template <typename T, int E>
 __global__ void __launch_bounds__(kThreads, 2)
-gemv_kernel(const T *__restrict__ W, int64_t ldw, int k, const double *__restrict__ y,
-            const float *__restrict__ base, float *__restrict__ out, int64_t L) {
+gemv_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__restrict__ kdev, int koff,
+            const double *__restrict__ y, const float *__restrict__ base, float *__restrict__ out,
+            int64_t L) {
     extern __shared__ float s_y[];
+    if (kdev) k = *kdev + koff;
     for (int j = threadIdx.x; j < k; j += kThreads) s_y[j] = (float)y[j];
     __syncthreads();
     const int64_t g0 = (int64_t)blockIdx.x * kThreads * E + threadIdx.x;
@@ -598,8 +670,10 @@ cudaError_t ensure_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// k: the step's k, or (kdev set) the largest k the launch may see, which
+// sizes its shared memory.
 template <typename T, bool UPDATE, bool DOTS, bool NORM>
-cudaError_t launch_pass(const T *W, int64_t ldw, int k, float *q, int64_t L,
+cudaError_t launch_pass(const T *W, int64_t ldw, int k, const int *kdev, float *q, int64_t L,
                         const double *coef, const RedScratch &rs, double *red_out,
                         cudaStream_t st) {
     int E;
@@ -611,8 +685,8 @@ cudaError_t launch_pass(const T *W, int64_t ldw, int k, float *q, int64_t L,
     case EE: {                                                                       \
         auto kern = cgs_pass_kernel<T, EE, UPDATE, DOTS, NORM>;                      \
         if ((err = ensure_smem(kern, smem)) != cudaSuccess) return err;              \
-        kern<<<G, kThreads, smem, st>>>(W, ldw, k, q, L, coef, rs.partials, rs.counter, \
-                                        red_out);                                    \
+        kern<<<G, kThreads, smem, st>>>(W, ldw, k, kdev, q, L, coef, rs.partials,     \
+                                        rs.counter, red_out);                        \
         break;                                                                       \
     }
     switch (E) {
@@ -627,8 +701,9 @@ cudaError_t launch_pass(const T *W, int64_t ldw, int k, float *q, int64_t L,
 }
 
 template <typename T>
-cudaError_t launch_update_scale(const T *W, int64_t ldw, int k, float *q, int64_t L, const RedScratch &rs,
-                                T *w_out, double *h_out, cudaStream_t st) {
+cudaError_t launch_update_scale(const T *W, int64_t ldw, int k, const int *kdev, double *H, int64_t ldh,
+                                float *q, int64_t L, const RedScratch &rs, T *w_out, double *h_out,
+                                cudaStream_t st) {
     int E;
     const int G = ctg_red_grid(L, &E);
     const size_t smem = sizeof(float) * (size_t)k;
@@ -637,7 +712,8 @@ cudaError_t launch_update_scale(const T *W, int64_t ldw, int k, float *q, int64_
     case EE: {                                                                                   \
         auto kern = update_scale_kernel<T, EE>;                                                  \
         if ((err = ensure_smem(kern, smem)) != cudaSuccess) return err;                          \
-        kern<<<G, kThreads, smem, st>>>(W, ldw, k, q, L, rs.h1, rs.h2, w_out, h_out, rs.scal + 1); \
+        kern<<<G, kThreads, smem, st>>>(W, ldw, k, kdev, q, L, rs.h1, rs.h2, w_out, h_out, H, ldh, \
+                                        rs.scal + 1);                                            \
         break;                                                                                   \
     }
     switch (E) {
@@ -778,38 +854,65 @@ int fused_resident_blocks() {
     });
 }
 
+// Launches the fused step (k, w_out, h_out fixed; or from the loop step
+// `ls` when ls is non-null).  *done = false when the grid cannot be
+// resident at once (the caller then takes the separate passes).  With
+// `cooperative` the launch asks the runtime to guarantee residency (it
+// fails rather than runs otherwise); without it the occupancy check alone
+// stands behind the bounded barriers.
 template <typename T, int E>
 cudaError_t launch_fused(const T *W, int64_t ldw, int64_t L, int k, float *q, T *w_out,
-                         double *h_out, const RedScratch &rs, int G, cudaStream_t st, bool *done) {
+                         double *h_out, const LoopStep *ls, const RedScratch &rs, int G,
+                         long long spin_limit, bool cooperative, cudaStream_t st, bool *done) {
     *done = false;
     if (G > fused_resident_blocks<T, E>()) return cudaSuccess;
-    const size_t smem = fused_smem_bytes(k);
-    float *partials = rs.partials;
-    double *h1 = rs.h1, *h2 = rs.h2, *scal = rs.scal;
-    void *args[] = {(void *)&W, (void *)&ldw, (void *)&k, (void *)&q, (void *)&L, (void *)&w_out,
-                    (void *)&h_out, (void *)&partials, (void *)&h1, (void *)&h2, (void *)&scal};
-    const cudaError_t e = cudaLaunchCooperativeKernel((const void *)cgs2_fused_kernel<T, E>, dim3(G),
-                                                      dim3(kThreads), args, smem, st);
+    const int kcap = ls ? ls->kmax : k;
+    const size_t smem = fused_smem_bytes(kcap);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = cooperative ? 1 : 0;
+    const int *kdev = ls ? ls->k : nullptr;
+    double *H = ls ? ls->H : nullptr;
+    const int64_t ldh = ls ? ls->ldh : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, cgs2_fused_kernel<T, E>, W, ldw, k, kdev, q, L, w_out,
+                                             h_out, H, ldh, rs.partials, rs.h1, rs.h2, rs.scal,
+                                             rs.counter + 1, reinterpret_cast<int *>(rs.counter + 2),
+                                             spin_limit);
     *done = e == cudaSuccess;
     return e;
 }
 
 template <typename T>
+cudaError_t fused_dispatch(const T *W, int64_t ldw, int64_t L, int k, float *q, T *w_out, double *h_out,
+                           const LoopStep *ls, const RedScratch &rs, long long spin_limit,
+                           bool cooperative, cudaStream_t st, bool *done) {
+    int E;
+    const int G = ctg_red_grid(L, &E);
+    switch (E) {
+        case 1: return launch_fused<T, 1>(W, ldw, L, k, q, w_out, h_out, ls, rs, G, spin_limit, cooperative, st, done);
+        case 2: return launch_fused<T, 2>(W, ldw, L, k, q, w_out, h_out, ls, rs, G, spin_limit, cooperative, st, done);
+        case 4: return launch_fused<T, 4>(W, ldw, L, k, q, w_out, h_out, ls, rs, G, spin_limit, cooperative, st, done);
+        case 8: return launch_fused<T, 8>(W, ldw, L, k, q, w_out, h_out, ls, rs, G, spin_limit, cooperative, st, done);
+        default: *done = false; return cudaSuccess;
+    }
+}
+
+template <typename T>
 cudaError_t cgs2_step_t(const T *W, int64_t ldw, int64_t L, int k, float *q, T *w_out,
-                        double *h_out, const RedScratch &rs, cudaStream_t st, int *nkern) {
+                        double *h_out, const RedScratch &rs, long long spin_limit, cudaStream_t st,
+                        int *nkern) {
     cudaError_t err;
     if (nkern) *nkern = k > 0 ? 3 : 2;
     if (k <= kFusedMaxK && rs.rows >= 2 * k + 2) {
-        int E;
-        const int G = ctg_red_grid(L, &E);
         bool done = false;
-        switch (E) {
-            case 1: err = launch_fused<T, 1>(W, ldw, L, k, q, w_out, h_out, rs, G, st, &done); break;
-            case 2: err = launch_fused<T, 2>(W, ldw, L, k, q, w_out, h_out, rs, G, st, &done); break;
-            case 4: err = launch_fused<T, 4>(W, ldw, L, k, q, w_out, h_out, rs, G, st, &done); break;
-            case 8: err = launch_fused<T, 8>(W, ldw, L, k, q, w_out, h_out, rs, G, st, &done); break;
-            default: err = cudaSuccess;
-        }
+        err = fused_dispatch<T>(W, ldw, L, k, q, w_out, h_out, nullptr, rs, spin_limit, true, st, &done);
         if (err != cudaSuccess) return err;
         if (done) {
             if (nkern) *nkern = 1;
@@ -817,16 +920,16 @@ cudaError_t cgs2_step_t(const T *W, int64_t ldw, int64_t L, int k, float *q, T *
         }
     }
     // pass 1: h1 = W^T q and ||q_pre||^2 (h1[k]); keep the latter in scal[0]
-    if ((err = launch_pass<T, false, true, true>(W, ldw, k, q, L, nullptr, rs, rs.h1, st)) != cudaSuccess)
+    if ((err = launch_pass<T, false, true, true>(W, ldw, k, nullptr, q, L, nullptr, rs, rs.h1, st)) != cudaSuccess)
         return err;
     if ((err = cudaMemcpyAsync(rs.scal, rs.h1 + k, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return err;
     if (k > 0) {
         // pass 2: q -= W h1; h2 = W^T q, ||q||^2 (h2[k])
-        if ((err = launch_pass<T, true, true, true>(W, ldw, k, q, L, rs.h1, rs, rs.h2, st)) != cudaSuccess)
+        if ((err = launch_pass<T, true, true, true>(W, ldw, k, nullptr, q, L, rs.h1, rs, rs.h2, st)) != cudaSuccess)
             return err;
         // q -= W h2 and w_out = q / ||q|| in one sweep; ||q||^2 -> scal[1]
-        return launch_update_scale<T>(W, ldw, k, q, L, rs, w_out, h_out, st);
+        return launch_update_scale<T>(W, ldw, k, nullptr, nullptr, 0, q, L, rs, w_out, h_out, st);
     }
     if ((err = cudaMemcpyAsync(rs.scal + 1, rs.scal, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return err;
@@ -834,8 +937,31 @@ cudaError_t cgs2_step_t(const T *W, int64_t ldw, int64_t L, int k, float *q, T *
     return cudaGetLastError();
 }
 
+// A step of a captured solver loop (k >= 1 read on the device): the fused
+// launch or the three separate passes, as ls.fused says.  ||q_pre||^2 is
+// left in rs.h1[k] (not copied to scal[0], whose source would depend on k).
 template <typename T>
-cudaError_t gemv_t(const T *W, int64_t ldw, int64_t L, int k, const double *y,
+cudaError_t cgs2_loop_t(const T *W, int64_t ldw, int64_t L, float *q, const LoopStep &ls,
+                        const RedScratch &rs, long long spin_limit, bool cooperative, cudaStream_t st,
+                        int *nkern) {
+    cudaError_t err;
+    if (ls.fused) {
+        bool done = false;
+        err = fused_dispatch<T>(W, ldw, L, 0, q, nullptr, nullptr, &ls, rs, spin_limit, cooperative, st, &done);
+        if (nkern) *nkern = 1;
+        if (err != cudaSuccess) return err;
+        return done ? cudaSuccess : cudaErrorInvalidConfiguration;
+    }
+    if (nkern) *nkern = 3;
+    if ((err = launch_pass<T, false, true, true>(W, ldw, ls.kmax, ls.k, q, L, nullptr, rs, rs.h1, st)) != cudaSuccess)
+        return err;
+    if ((err = launch_pass<T, true, true, true>(W, ldw, ls.kmax, ls.k, q, L, rs.h1, rs, rs.h2, st)) != cudaSuccess)
+        return err;
+    return launch_update_scale<T>(W, ldw, ls.kmax, ls.k, ls.H, ls.ldh, q, L, rs, nullptr, nullptr, st);
+}
+
+template <typename T>
+cudaError_t gemv_t(const T *W, int64_t ldw, int64_t L, int k, const int *kdev, int koff, const double *y,
                    const float *base, float *out, cudaStream_t st) {
     int E;
     const int G = ctg_red_grid(L, &E);
@@ -845,7 +971,7 @@ cudaError_t gemv_t(const T *W, int64_t ldw, int64_t L, int k, const double *y,
 #define CTG_GEMV_CASE(EE)                                                             \
     case EE:                                                                          \
         if ((err = ensure_smem(gemv_kernel<T, EE>, smem)) != cudaSuccess) return err; \
-        gemv_kernel<T, EE><<<G, kThreads, smem, st>>>(W, ldw, k, y, base, out, L);    \
+        gemv_kernel<T, EE><<<G, kThreads, smem, st>>>(W, ldw, k, kdev, koff, y, base, out, L); \
         break;
         CTG_GEMV_CASE(1)
         CTG_GEMV_CASE(2)
@@ -861,28 +987,67 @@ cudaError_t gemv_t(const T *W, int64_t ldw, int64_t L, int k, const double *y,
 
 cudaError_t ctg_cgs2_step(const void *W, int dtype, int64_t ldw, int64_t L, int k, float *q,
                           void *w_out, double *h_out, const RedScratch &rs, cudaStream_t st,
-                          int *nkern) {
+                          int *nkern, long long spin_limit) {
     switch (dtype) {
         case CTG_BASIS_FP32:
             return cgs2_step_t(static_cast<const float *>(W), ldw, L, k, q,
-                               static_cast<float *>(w_out), h_out, rs, st, nkern);
+                               static_cast<float *>(w_out), h_out, rs, spin_limit, st, nkern);
         case CTG_BASIS_BF16:
             return cgs2_step_t(static_cast<const __nv_bfloat16 *>(W), ldw, L, k, q,
-                               static_cast<__nv_bfloat16 *>(w_out), h_out, rs, st, nkern);
+                               static_cast<__nv_bfloat16 *>(w_out), h_out, rs, spin_limit, st, nkern);
         case CTG_BASIS_FP16:
             return cgs2_step_t(static_cast<const __half *>(W), ldw, L, k, q,
-                               static_cast<__half *>(w_out), h_out, rs, st, nkern);
+                               static_cast<__half *>(w_out), h_out, rs, spin_limit, st, nkern);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t ctg_gemv(const void *W, int dtype, int64_t ldw, int64_t L, int k, const double *y,
-                     const float *base, float *out, cudaStream_t st) {
+cudaError_t ctg_cgs2_step_loop(const void *W, int dtype, int64_t ldw, int64_t L, float *q, const LoopStep &ls,
+                               const RedScratch &rs, long long spin_limit, bool cooperative, cudaStream_t st,
+                               int *nkern) {
     switch (dtype) {
-        case CTG_BASIS_FP32: return gemv_t(static_cast<const float *>(W), ldw, L, k, y, base, out, st);
+        case CTG_BASIS_FP32:
+            return cgs2_loop_t(static_cast<const float *>(W), ldw, L, q, ls, rs, spin_limit, cooperative, st, nkern);
         case CTG_BASIS_BF16:
-            return gemv_t(static_cast<const __nv_bfloat16 *>(W), ldw, L, k, y, base, out, st);
-        case CTG_BASIS_FP16: return gemv_t(static_cast<const __half *>(W), ldw, L, k, y, base, out, st);
+            return cgs2_loop_t(static_cast<const __nv_bfloat16 *>(W), ldw, L, q, ls, rs, spin_limit, cooperative,
+                               st, nkern);
+        case CTG_BASIS_FP16:
+            return cgs2_loop_t(static_cast<const __half *>(W), ldw, L, q, ls, rs, spin_limit, cooperative, st,
+                               nkern);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool ctg_cgs2_fused_ok(int dtype, int64_t L, int kmax, const RedScratch &rs) {
+    if (kmax > kFusedMaxK || rs.rows < 2 * kmax + 2) return false;
+    int E;
+    const int G = ctg_red_grid(L, &E);
+    int cap = 0;
+    switch (dtype * 16 + E) {
+#define CTG_FOK(DT, T)                                                  \
+    case DT * 16 + 1: cap = fused_resident_blocks<T, 1>(); break;       \
+    case DT * 16 + 2: cap = fused_resident_blocks<T, 2>(); break;       \
+    case DT * 16 + 4: cap = fused_resident_blocks<T, 4>(); break;       \
+    case DT * 16 + 8: cap = fused_resident_blocks<T, 8>(); break;
+        CTG_FOK(CTG_BASIS_FP32, float)
+        CTG_FOK(CTG_BASIS_BF16, __nv_bfloat16)
+        CTG_FOK(CTG_BASIS_FP16, __half)
+#undef CTG_FOK
+        default: return false;
+    }
+    return G <= cap;
+}
+
+int ctg_cgs2_fused_max() { return kFusedMaxK; }
+
+cudaError_t ctg_gemv(const void *W, int dtype, int64_t ldw, int64_t L, int k, const double *y,
+                     const float *base, float *out, cudaStream_t st, const int *kdev, int koff) {
+    switch (dtype) {
+        case CTG_BASIS_FP32: return gemv_t(static_cast<const float *>(W), ldw, L, k, kdev, koff, y, base, out, st);
+        case CTG_BASIS_BF16:
+            return gemv_t(static_cast<const __nv_bfloat16 *>(W), ldw, L, k, kdev, koff, y, base, out, st);
+        case CTG_BASIS_FP16:
+            return gemv_t(static_cast<const __half *>(W), ldw, L, k, kdev, koff, y, base, out, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -75,11 +75,33 @@ static inline PadLayout ctg_pad_layout(int N, double det_spacing) {
     return p;
 }
 
+// A vector that is column (*k + off) of a basis with a stride of ld
+// elements, the step index k being read on the device when the kernel runs
+// (so that one captured launch serves every step of a solver loop); with
+// k == nullptr, the vector is the given pointer itself.
+struct ColRef {
+    const int *k;
+    int off;
+    long long ld;
+};
+static inline ColRef col_none() { return ColRef{nullptr, 0, 0}; }
+static inline ColRef col_at(const int *k, int off, long long ld) { return ColRef{k, off, ld}; }
+#ifdef __CUDACC__
+__device__ __forceinline__ size_t col_offset(const ColRef &c) {
+    return c.k ? (size_t)(*c.k + c.off) * (size_t)c.ld : 0;
+}
+#endif
+
 // ---- projector launchers (projectors.cu) --------------------------------
-// Stage x (n elements of type `dtype`, a CTG_BASIS_* value) for the
-// forward projector.
+// Stage x (n elements of type `dtype`, a CTG_BASIS_* value; column xc of a
+// basis at x when xc.k is set) for the forward projector.
 cudaError_t ctg_launch_pad(const void *x, int dtype, float2 *pad, int N, const PadLayout &pl,
-                           cudaStream_t st);
+                           cudaStream_t st, ColRef xc = col_none());
+// Stage two images for ctg_launch_forward2, interleaved: x (type `dtype`,
+// column xc of a basis when xc.k is set) and x2 (FP32).  pad2 holds twice
+// the floats of pl (PadLayout::floats * 2).
+cudaError_t ctg_launch_pad2(const void *x, int dtype, ColRef xc, const float *x2, float4 *pad2, int N,
+                            const PadLayout &pl, cudaStream_t st);
 // Forward projector block shapes, the tile autotuner's candidates: angles
 // per block x angles per warp (a warp holds 32 / angles-per-warp adjacent
 // rays of each of its angles).  Every shape gives the same result bit for
@@ -98,6 +120,11 @@ constexpr int kBatchFwdSplitShape = 3;
 cudaError_t ctg_launch_forward(const float2 *pad, int N, const PadLayout &pl, int n_angles,
                                int n_det, const FwdAngle *tab, float *b, cudaStream_t st,
                                int shape = 0, const int *order = nullptr);
+// b = A x and b2 = A x2 in one walk, from the interleaved staging of
+// ctg_launch_pad2; each ray's sums equal ctg_launch_forward's bit for bit.
+cudaError_t ctg_launch_forward2(const float4 *pad2, int N, const PadLayout &pl, int n_angles, int n_det,
+                                const FwdAngle *tab, float *b, float *b2, cudaStream_t st, int shape = 0,
+                                const int *order = nullptr);
 // Blocks of one forward launch of `shape`.
 int ctg_fwd_shape_blocks(int shape, int n_angles, int n_det);
 // Dispatch order of the forward projector's blocks of `shape` (tile index
@@ -121,9 +148,10 @@ int ctg_back_window(const BackAngle *host_tab, int n_angles);
 // ctg_back_window
 // back_chunk: angles staged per pass, 16, 32 or 64 (tuned like the forward shape;
 // the result does not depend on it).
+// bc: the input is column bc of a basis at b (bc.k set), or b itself.
 cudaError_t ctg_launch_back(const void *b, int dtype, int N, int n_angles, int n_det,
                             const BackAngle *tab, int window, const float *add, float *x,
-                            cudaStream_t st, int back_chunk = 32);
+                            cudaStream_t st, int back_chunk = 32, ColRef bc = col_none());
 
 // ---- matched back projector (matched.cu) ----------------------------------
 // x = B_thr b (+ add): the transpose of the forward projector, keeping the
@@ -131,12 +159,13 @@ cudaError_t ctg_launch_back(const void *b, int dtype, int N, int n_angles, int n
 // bins on each side beyond the two nearest (0 when ds >= max |c|).
 cudaError_t ctg_launch_back_matched(const void *b, int dtype, int N, int n_angles, int n_det,
                                     const BackAngle *tab, const MatchedAngle *mt, int rm, float thr,
-                                    const float *add, float *x, cudaStream_t st);
+                                    const float *add, float *x, cudaStream_t st, ColRef bc = col_none());
 // The same with the tiled design of the pixel-driven B (projectors.cu), for
 // rm = 0 and window <= ctg_back_window_max().
 cudaError_t ctg_launch_back_matched_tiled(const void *b, int dtype, int N, int n_angles, int n_det,
                                           const BackAngle *tab, int window, const MatchedAngle *mt,
-                                          float thr, const float *add, float *x, cudaStream_t st);
+                                          float thr, const float *add, float *x, cudaStream_t st,
+                                          ColRef bc = col_none());
 // *max_bits = bit pattern of max_ij A_ij (a float >= 0), on the device.
 cudaError_t ctg_matched_max(int N, int n_angles, int n_det, const BackAngle *tab,
                             const MatchedAngle *mt, int rm, unsigned *max_bits, cudaStream_t st);
@@ -155,7 +184,9 @@ struct RedScratch {
     float *partials;       // (kmax + 2) * grid floats
     double *h1, *h2;       // kmax + 2 doubles each
     double *scal;          // 8 doubles: [0] = ||q_pre||^2, [1] = ||q||^2, ...
-    unsigned int *counter; // 4 counters, zero between launches
+    unsigned int *counter; // 4 words, zero between solves: [0] the last-block
+                           // ticket of a reduction, [1] the fused step's
+                           // grid-barrier arrivals, [2] its timeout flag
     int grid;              // blocks of every reduction pass for this L
     int E;                 // float4 groups per thread
     int rows = 0;          // partial-sum rows available (kmax + 2, or 2k + 2 for a fused step)
@@ -172,19 +203,47 @@ static inline size_t ctg_basis_bytes(int dtype) {
     return dtype == CTG_BASIS_FP32 ? 4 : (dtype == CTG_BASIS_BF16 || dtype == CTG_BASIS_FP16) ? 2 : 0;
 }
 
+// Polls of a bounded device-side wait (about 100 ns apart) before it gives
+// up: about half a second.
+constexpr long long kCtgDefaultSpinLimit = 1LL << 22;
+
 // One CGS2 Arnoldi step: orthogonalise the FP32 vector q (length L) against
 // k vectors of W (element type `dtype`, stride ldw elements),
 // h_out[0..k-1] = h1 + h2, h_out[k] = ||q||, and write w_out = q / ||q||
 // (rounded to `dtype`) when ||q|| > 0.  Also leaves ||q_pre||^2 in
 // rs.scal[0].
-// *nkern (if given) = the kernels launched: 1 for the fused cooperative step
-// (small k, scratch and residency permitting), else 4 (2 when k = 0).
+// *nkern (if given) = the kernels launched: 1 for the fused step (small k,
+// scratch and residency permitting), else 3 (2 when k = 0).  The fused
+// step's grid barriers give up after spin_limit polls, setting
+// rs.counter[2] and h_out[0..k] to NaN.
 cudaError_t ctg_cgs2_step(const void *W, int dtype, int64_t ldw, int64_t L, int k, float *q,
                           void *w_out, double *h_out, const RedScratch &rs, cudaStream_t st,
-                          int *nkern = nullptr);
-// out = base + sum_j y_j W_j (base may be NULL); y: k doubles (device).
+                          int *nkern = nullptr, long long spin_limit = kCtgDefaultSpinLimit);
+// A CGS2 step inside a captured solver loop: k >= 1 is read on the device
+// (*k), the new vector goes to column k of W and the Hessenberg column to
+// H + (k - 1) ldh; kmax bounds k (it sizes shared memory); fused selects
+// the one-launch step (needs ctg_cgs2_fused_ok) or the three passes.
+// ||q_pre||^2 is left in rs.h1[k].
+struct LoopStep {
+    const int *k;
+    double *H;
+    long long ldh;
+    int kmax;
+    bool fused;
+};
+cudaError_t ctg_cgs2_step_loop(const void *W, int dtype, int64_t ldw, int64_t L, float *q, const LoopStep &ls,
+                               const RedScratch &rs, long long spin_limit, bool cooperative, cudaStream_t st,
+                               int *nkern = nullptr);
+// Whether the fused step serves k <= kmax at length L with this scratch
+// (every block of its grid resident at once).
+bool ctg_cgs2_fused_ok(int dtype, int64_t L, int kmax, const RedScratch &rs);
+int ctg_cgs2_fused_max();
+// out = base + sum_j y_j W_j (base may be NULL); y: k doubles (device); with
+// kdev set, k = *kdev + koff read on the device (k is then only the bound
+// that sizes the launch's shared memory).
 cudaError_t ctg_gemv(const void *W, int dtype, int64_t ldw, int64_t L, int k, const double *y,
-                     const float *base, float *out, cudaStream_t st);
+                     const float *base, float *out, cudaStream_t st, const int *kdev = nullptr,
+                     int koff = 0);
 // *res = ||base + sum_j y_j V_j||^2 (double, device); the vector is not stored.
 cudaError_t ctg_gemv_norm2(const float *V, int64_t ldv, int64_t L, int k, const double *y,
                            const float *base, double *res, const RedScratch &rs,
@@ -196,6 +255,60 @@ cudaError_t ctg_sub_norm2(const float *a, const float *c, float *out, int64_t L,
 // nrm2 == 0).
 cudaError_t ctg_scale(const float *v, const double *nrm2, void *out, int dtype, int64_t L,
                       cudaStream_t st);
+
+// ---- the device-driven GMRES loop (gmres_loop.cu) ---------------------------
+// Stopping rules of a solve: maxit only, the discrepancy principle, NCP.
+enum { kRuleMaxit = 0, kRuleDP = 1, kRuleNCP = 2 };
+// Device state of one AB-/BA-GMRES solve.  The kernels of a step read k
+// here; the step's last kernel advances it or stops the solve.
+struct GmresState {
+    int k;                // the step being performed (1-based)
+    int active;           // 1 while iterating
+    int iters;            // k of the iterate to return
+    int stop_reason;      // CTG_STOP_*
+    int pending;          // breakdown / maxit seen by the Givens kernel (CTG_STOP_* + 1), for the step's end
+    int steps;            // steps executed
+    int timed_out;        // a CGS2 grid barrier gave up
+    int variant, rule, maxit;
+    double target;        // tau ||e||
+    double beta;          // ||r0||
+    double rho;           // |g_{k+1}| of the latest step (at exit: of the returned iterate)
+    double resnorm;       // latest ||b - A x_k|| (BA with DP / NCP; at exit: of the returned iterate)
+    double res0;          // ||b - A x0||
+    double dprev;         // NCP: the previous step's distance
+};
+// Where the loop kernels find a solve's state (device pointers).
+struct LoopBufs {
+    GmresState *S;
+    double *H;            // Hessenberg matrix, column-major, leading dimension ldh
+    long long ldh;
+    double *gc, *gs, *gg; // Givens cosines, sines (maxit) and rotated right-hand side (maxit + 1)
+    double *R;            // rotated columns (upper triangle), column-major, leading dimension ldr
+    int ldr;              // = maxit
+    double *y;            // y of the latest step / of the returned iterate (maxit)
+    double *yring;        // y_j at yring + (j % 3) ldr (NCP returns x_{k-1})
+    double *z;            // AB NCP: coefficients of r_k in W_{k+1} (maxit + 1)
+    double *hist;         // ctg_info history (maxit + 1)
+    double *rhoh;         // rho_k (maxit + 1)
+    double *ncph;         // NCP distances (maxit + 2)
+    double *scal;         // the reduction scratch's scalars
+    double *h1;           // the reduction scratch's h1 (h1[k] = ||q_pre||^2)
+    unsigned *counter;    // the reduction scratch's counters ([2]: barrier timeout)
+    cudaGraphConditionalHandle c_fused, c_pass;   // while-loop conditions (in_graph)
+    int in_graph;
+    int fused_max;        // last k of the fused-CGS2 loop
+};
+cudaError_t ctg_loop_init(const LoopBufs &B, int variant, int rule, int maxit, double target, cudaStream_t st);
+// need_y: y_k every step; need_z: AB NCP residual coefficients; end: the
+// Givens kernel ends the step (AB with DP or maxit)
+cudaError_t ctg_loop_givens(const LoopBufs &B, bool need_y, bool need_z, bool end, int maxit, cudaStream_t st);
+// ||b - Ax||^2 (r_out: NULL or where b - Ax goes); decide: end the step (BA, DP)
+cudaError_t ctg_loop_resid(const LoopBufs &B, const float *b, const float *Ax, float *r_out, int64_t L,
+                           const RedScratch &rs, bool decide, cudaStream_t st);
+cudaError_t ctg_loop_ncp_decide(const LoopBufs &B, cudaStream_t st);
+cudaError_t ctg_loop_advance(const LoopBufs &B, cudaStream_t st);
+cudaError_t ctg_loop_exit_y(const LoopBufs &B, int maxit, cudaStream_t st);
+cudaError_t ctg_loop_final(const LoopBufs &B, cudaStream_t st);
 
 // ---- LSQR / LSMR (lsq.cu) --------------------------------------------------
 // Device state of one LSQR or LSMR solve (Golub-Kahan bidiagonalisation with

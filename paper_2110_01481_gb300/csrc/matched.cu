@@ -55,10 +55,11 @@ __device__ __forceinline__ void stage_chunk(ChunkAngle *sp, const BackAngle *tab
 // nearest (0 when every angle has ds >= |c|).
 template <typename T, bool MAX>
 __global__ void __launch_bounds__(kBX *kBY)
-matched_back_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
+matched_back_kernel(const T *__restrict__ b, ColRef bc, int N, int n_angles, int n_det,
                     const BackAngle *__restrict__ tab, const MatchedAngle *__restrict__ mt, int rm,
                     float thr, const float *__restrict__ add, float *__restrict__ x,
                     unsigned *__restrict__ max_bits) {
+    if (!MAX) b += col_offset(bc);
     __shared__ ChunkAngle sp[kAChunk];
     __shared__ float s_max[kBX * kBY / 32];
     const int j0 = blockIdx.x * kBX, i0 = blockIdx.y * kBY;
@@ -109,11 +110,11 @@ matched_back_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
 }
 
 template <typename T>
-cudaError_t launch_t(const T *b, int N, int n_angles, int n_det, const BackAngle *tab,
+cudaError_t launch_t(const T *b, ColRef bc, int N, int n_angles, int n_det, const BackAngle *tab,
                      const MatchedAngle *mt, int rm, float thr, const float *add, float *x,
                      cudaStream_t st) {
     const dim3 grid((N + kBX - 1) / kBX, (N + kBY - 1) / kBY);
-    matched_back_kernel<T, false><<<grid, dim3(kBX, kBY), 0, st>>>(b, N, n_angles, n_det, tab, mt, rm,
+    matched_back_kernel<T, false><<<grid, dim3(kBX, kBY), 0, st>>>(b, bc, N, n_angles, n_det, tab, mt, rm,
                                                                    thr, add, x, nullptr);
     return cudaGetLastError();
 }
@@ -122,15 +123,17 @@ cudaError_t launch_t(const T *b, int N, int n_angles, int n_det, const BackAngle
 
 cudaError_t ctg_launch_back_matched(const void *b, int dtype, int N, int n_angles, int n_det,
                                     const BackAngle *tab, const MatchedAngle *mt, int rm, float thr,
-                                    const float *add, float *x, cudaStream_t st) {
+                                    const float *add, float *x, cudaStream_t st, ColRef bc) {
     switch (dtype) {
         case CTG_BASIS_FP32:
-            return launch_t(static_cast<const float *>(b), N, n_angles, n_det, tab, mt, rm, thr, add, x, st);
+            return launch_t(static_cast<const float *>(b), bc, N, n_angles, n_det, tab, mt, rm, thr, add, x,
+                            st);
         case CTG_BASIS_BF16:
-            return launch_t(static_cast<const __nv_bfloat16 *>(b), N, n_angles, n_det, tab, mt, rm, thr,
+            return launch_t(static_cast<const __nv_bfloat16 *>(b), bc, N, n_angles, n_det, tab, mt, rm, thr,
                             add, x, st);
         case CTG_BASIS_FP16:
-            return launch_t(static_cast<const __half *>(b), N, n_angles, n_det, tab, mt, rm, thr, add, x, st);
+            return launch_t(static_cast<const __half *>(b), bc, N, n_angles, n_det, tab, mt, rm, thr, add, x,
+                            st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -141,6 +144,6 @@ cudaError_t ctg_matched_max(int N, int n_angles, int n_det, const BackAngle *tab
     if (e != cudaSuccess) return e;
     const dim3 grid((N + kBX - 1) / kBX, (N + kBY - 1) / kBY);
     matched_back_kernel<float, true><<<grid, dim3(kBX, kBY), 0, st>>>(
-        nullptr, N, n_angles, n_det, tab, mt, rm, 0.0f, nullptr, nullptr, max_bits);
+        nullptr, col_none(), N, n_angles, n_det, tab, mt, rm, 0.0f, nullptr, nullptr, max_bits);
     return cudaGetLastError();
 }

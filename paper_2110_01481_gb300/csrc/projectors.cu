@@ -36,63 +36,94 @@ __device__ __forceinline__ float2 lerp_pair(float v0, float v1) {
 
 // Stage the image for the forward projector (layout in ctg_internal.cuh):
 // entries j = -1 .. N-1 of every row of x and of x^T; the other border
-// entries are zero pairs written once when the buffer is allocated.
-template <typename T>
-__device__ __forceinline__ void pad_pairs_block(const T *__restrict__ x, float2 *__restrict__ pad,
-                                                int N, int stride, int border, int bx, int by) {
+// entries are zero pairs written once when the buffer is allocated.  With
+// kImgs = 2 two images x (type T) and x2 (FP32) are staged interleaved, each
+// entry a float4 (pair of x, pair of x2), so that the forward projector
+// reads both with one load.
+template <int kImgs, typename T>
+__device__ __forceinline__ void pad_pairs_block(const T *__restrict__ x, const float *__restrict__ x2,
+                                                void *__restrict__ pad_out, int N, int stride, int border,
+                                                int bx, int by) {
+    using E = typename std::conditional<kImgs == 2, float4, float2>::type;
     // odd pitch: the column reads of the transposed copy hit 32 distinct banks
-    __shared__ float tile[kPadTile + 1][kPadTile + 1];
-    float2 *xp = pad + border, *xtp = pad + (size_t)N * stride + border;
+    __shared__ float tile[kImgs][kPadTile + 1][kPadTile + 1];
+    E *pad = static_cast<E *>(pad_out);
+    E *xp = pad + border, *xtp = pad + (size_t)N * stride + border;
     const int j0 = bx * kPadTile, i0 = by * kPadTile;
-    // tile[r][c] = x[i0 + r][j0 + c] for r, c in [0, 33) (0 outside); every
-    // load is issued before the first shared store
+    // tile[q][r][c] = image q at (i0 + r, j0 + c) for r, c in [0, 33) (0
+    // outside); every load is issued before the first shared store
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPadTile + tx;
     constexpr int kPasses = (kPadTile + kPadRows) / kPadRows;   // rows 0 .. kPadTile
-    float v[kPasses];
+    float v[kImgs][kPasses];
 #pragma unroll
     for (int t = 0; t < kPasses; ++t) {
         const int r = ty + t * kPadRows, i = i0 + r, j = j0 + tx;
-        v[t] = (r <= kPadTile && i < N && j < N) ? to_f(x[(size_t)i * N + j]) : 0.0f;
+        const bool in = r <= kPadTile && i < N && j < N;
+        v[0][t] = in ? to_f(x[(size_t)i * N + j]) : 0.0f;
+        if (kImgs == 2) v[kImgs - 1][t] = in ? x2[(size_t)i * N + j] : 0.0f;
     }
-    float edge = 0.0f;                    // column kPadTile, rows 0 .. kPadTile
+    float edge[kImgs];                    // column kPadTile, rows 0 .. kPadTile
+#pragma unroll
+    for (int q = 0; q < kImgs; ++q) edge[q] = 0.0f;
     if (tid <= kPadTile) {
         const int i = i0 + tid, j = j0 + kPadTile;
-        edge = (i < N && j < N) ? to_f(x[(size_t)i * N + j]) : 0.0f;
+        const bool in = i < N && j < N;
+        edge[0] = in ? to_f(x[(size_t)i * N + j]) : 0.0f;
+        if (kImgs == 2) edge[kImgs - 1] = in ? x2[(size_t)i * N + j] : 0.0f;
     }
 #pragma unroll
-    for (int t = 0; t < kPasses; ++t)
-        if (ty + t * kPadRows <= kPadTile) tile[ty + t * kPadRows][tx] = v[t];
-    if (tid <= kPadTile) tile[tid][kPadTile] = edge;
+    for (int q = 0; q < kImgs; ++q) {
+#pragma unroll
+        for (int t = 0; t < kPasses; ++t)
+            if (ty + t * kPadRows <= kPadTile) tile[q][ty + t * kPadRows][tx] = v[q][t];
+        if (tid <= kPadTile) tile[q][tid][kPadTile] = edge[q];
+    }
     __syncthreads();
+    auto entry = [&](int r0, int c0, int r1, int c1) -> E {
+        if constexpr (kImgs == 2) {
+            const float2 a = lerp_pair(tile[0][r0][c0], tile[0][r1][c1]);
+            const float2 b = lerp_pair(tile[1][r0][c0], tile[1][r1][c1]);
+            return make_float4(a.x, a.y, b.x, b.y);
+        } else {
+            return lerp_pair(tile[0][r0][c0], tile[0][r1][c1]);
+        }
+    };
     // both copies written along their own rows, so each warp store is one
-    // contiguous run of 32 pairs
+    // contiguous run of 32 entries
     for (int r = threadIdx.y; r < kPadTile; r += kPadRows) {
         const int i = i0 + r, j = j0 + threadIdx.x;
-        if (i < N && j < N)
-            xp[(size_t)i * stride + j] = lerp_pair(tile[r][threadIdx.x], tile[r][threadIdx.x + 1]);
+        if (i < N && j < N) xp[(size_t)i * stride + j] = entry(r, threadIdx.x, r, threadIdx.x + 1);
     }
     for (int c = threadIdx.y; c < kPadTile; c += kPadRows) {
         const int j = j0 + c, i = i0 + threadIdx.x;
-        if (i < N && j < N)
-            xtp[(size_t)j * stride + i] = lerp_pair(tile[threadIdx.x][c], tile[threadIdx.x + 1][c]);
+        if (i < N && j < N) xtp[(size_t)j * stride + i] = entry(threadIdx.x, c, threadIdx.x + 1, c);
     }
     // entry j = -1 of each row: (0 - x[0], x[0])
+    auto first = [&](size_t p) -> E {
+        if constexpr (kImgs == 2) {
+            const float2 a = lerp_pair(0.0f, to_f(x[p])), b = lerp_pair(0.0f, x2[p]);
+            return make_float4(a.x, a.y, b.x, b.y);
+        } else {
+            return lerp_pair(0.0f, to_f(x[p]));
+        }
+    };
     if (bx == 0)
         for (int r = threadIdx.y * blockDim.x + threadIdx.x; r < kPadTile; r += blockDim.x * blockDim.y) {
             const int i = i0 + r;
-            if (i < N) xp[(size_t)i * stride - 1] = lerp_pair(0.0f, to_f(x[(size_t)i * N]));
+            if (i < N) xp[(size_t)i * stride - 1] = first((size_t)i * N);
         }
     if (by == 0)
         for (int c = threadIdx.y * blockDim.x + threadIdx.x; c < kPadTile; c += blockDim.x * blockDim.y) {
             const int j = j0 + c;
-            if (j < N) xtp[(size_t)j * stride - 1] = lerp_pair(0.0f, to_f(x[j]));
+            if (j < N) xtp[(size_t)j * stride - 1] = first((size_t)j);
         }
 }
 
-template <typename T>
-__global__ void pad_pairs_kernel(const T *__restrict__ x, float2 *__restrict__ pad, int N,
-                                 int stride, int border) {
-    pad_pairs_block(x, pad, N, stride, border, blockIdx.x, blockIdx.y);
+// xc: the image is column xc of a basis (x + col_offset(xc)), or x itself.
+template <int kImgs, typename T>
+__global__ void pad_pairs_kernel(const T *__restrict__ x, ColRef xc, const float *__restrict__ x2,
+                                 void *__restrict__ pad, int N, int stride, int border) {
+    pad_pairs_block<kImgs, T>(x + col_offset(xc), x2, pad, N, stride, border, blockIdx.x, blockIdx.y);
 }
 
 __device__ __forceinline__ float fx_frac(long long U) {
@@ -130,6 +161,7 @@ constexpr int kFwdDepth = 12;   // image loads in flight per lane (a multiple of
                                 // 4 angles, 12 measured 7% faster than 8 and 3% faster than 16 at
                                 // 512^2 (with one angle per warp, 8 was 10% faster than 4)
 constexpr int kBatchFwdDepth = 8;   // the batched kernel holds both clamp variants: 8 needs no spills
+constexpr int kFwdDepth2 = 8;       // two images: 8 interleaved loads (16 B each) in flight per lane
 
 // b[a * n_det + d] = scale_a * sum_t lerp(img_a[t, .], u(d, t)).
 // A block holds kAngles consecutive angles; each warp holds kSplit of them
@@ -144,11 +176,16 @@ constexpr int kBatchFwdDepth = 8;   // the batched kernel holds both clamp varia
 // block shape, warp layout and load depth gives the same result bit for
 // bit.  kSplit > 1 needs the host's check (ctg_forward_split_safe) that
 // every lane stays inside the border.
-template <bool kClamp, int kAngles = kFwdAngles, int kSplit = 1, int kDepth = kFwdDepth>
-__device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ pad, int N,
+// kImgs = 2 projects two images staged interleaved (pad_pairs_block<2>) in
+// the same walk, b from the first and b2 from the second: each ray's two
+// sums are the ones the one-image kernel gives for each image alone.
+template <bool kClamp, int kAngles = kFwdAngles, int kSplit = 1, int kDepth = kFwdDepth, int kImgs = 1>
+__device__ __forceinline__ void joseph_forward_block(const void *__restrict__ pad_in, int N,
                                                      int stride, int border, int n_angles,
                                                      int n_det, const FwdAngle *__restrict__ tab,
-                                                     float *__restrict__ b, int bx, int by) {
+                                                     float *__restrict__ b, float *__restrict__ b2,
+                                                     int bx, int by) {
+    using E = typename std::conditional<kImgs == 2, float4, float2>::type;
     constexpr int kRays = 32 / kSplit;
     const int lane = threadIdx.x & 31;
     const int a = by * kAngles + (threadIdx.x >> 5) * kSplit + lane / kRays;
@@ -156,7 +193,7 @@ __device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ 
     if (!__any_sync(0xffffffffu, live)) return;      // whole warp past the last angle
     const int d = bx * kRays + lane % kRays;
     const FwdAngle t = tab[live ? a : n_angles - 1];
-    const float2 *img = pad + (t.row_driven ? 0 : (size_t)N * stride) + border;
+    const E *img = static_cast<const E *>(pad_in) + (t.row_driven ? 0 : (size_t)N * stride) + border;
 
     // this ray's steps whose taps can touch the image (-1 < u < N), with a
     // one-step margin; rays past the last detector or angle take an empty
@@ -176,14 +213,24 @@ __device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ 
     }
     const int wlo = __reduce_min_sync(0xffffffffu, lo) & ~3;
     const int whi = __reduce_max_sync(0xffffffffu, hi);
-    float acc0 = 0.0f, acc1 = 0.0f;
+    // acc[i] for image 1, acc[4 + i] for image 2, i = step mod 4
+    float acc[4 * kImgs];
+#pragma unroll
+    for (int i = 0; i < 4 * kImgs; ++i) acc[i] = 0.0f;
+    auto add = [&](float *ac, float mw, const E &p) {
+        if constexpr (kImgs == 2) {
+            ac[0] = fmaf(mw, p.y, ac[0] + p.x);
+            ac[4] = fmaf(mw, p.w, ac[4] + p.z);
+        } else {
+            ac[0] = fmaf(mw, p.y, ac[0] + p.x);
+        }
+    };
     if (!kClamp) {
         const long long Ds = t.D + ((long long)stride << CTG_FXF_BITS);
         long long U = t.Q + (long long)d * t.P + (long long)wlo * Ds;
-        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         int s = wlo;
         for (; s + kDepth - 1 <= whi; s += kDepth) {
-            float2 p[kDepth];
+            E p[kDepth];
             float mw[kDepth];
 #pragma unroll
             for (int i = 0; i < kDepth; ++i) {
@@ -192,10 +239,10 @@ __device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ 
                 U += Ds;
             }
 #pragma unroll
-            for (int i = 0; i < kDepth; ++i) acc[i & 3] = fmaf(mw[i], p[i].y, acc[i & 3] + p[i].x);
+            for (int i = 0; i < kDepth; ++i) add(acc + (i & 3), mw[i], p[i]);
         }
         for (; s + 3 <= whi; s += 4) {
-            float2 p[4];
+            E p[4];
             float mw[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -204,41 +251,43 @@ __device__ __forceinline__ void joseph_forward_block(const float2 *__restrict__ 
                 U += Ds;
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] = fmaf(mw[i], p[i].y, acc[i] + p[i].x);
+            for (int i = 0; i < 4; ++i) add(acc + i, mw[i], p[i]);
         }
         // at most three steps left, s a multiple of 4
 #pragma unroll
         for (int i = 0; i < 3; ++i)
             if (s + i <= whi) {
-                const float2 pa = __ldg(img + (int)(U >> CTG_FXF_BITS));
-                acc[i] = fmaf(one_plus_frac((unsigned)U), pa.y, acc[i] + pa.x);
+                const E pa = __ldg(img + (int)(U >> CTG_FXF_BITS));
+                add(acc + i, one_plus_frac((unsigned)U), pa);
                 U += Ds;
             }
-        acc0 = acc[0] + acc[2];
-        acc1 = acc[1] + acc[3];
     } else {
         long long U = t.Q + (long long)d * t.P + (long long)wlo * t.D;
         for (int s = wlo; s <= whi; ++s) {
             const int j = min(max((int)(U >> CTG_FXF_BITS), -2), N);
-            const float2 pa = __ldg(img + (size_t)s * stride + j);
-            acc0 = fmaf(one_plus_frac((unsigned)U), pa.y, acc0 + pa.x);
+            const E pa = __ldg(img + (size_t)s * stride + j);
+            add(acc, one_plus_frac((unsigned)U), pa);
             U += t.D;
         }
     }
-    if (live && d < n_det) b[(size_t)a * n_det + d] = (acc0 + acc1) * t.scale;
+    if (live && d < n_det) {
+        b[(size_t)a * n_det + d] = ((acc[0] + acc[2]) + (acc[1] + acc[3])) * t.scale;
+        if constexpr (kImgs == 2) b2[(size_t)a * n_det + d] = ((acc[4] + acc[6]) + (acc[5] + acc[7])) * t.scale;
+    }
 }
 
 // One block per (ray group bx, angle group by), on a 1-D grid of gx * gy
 // blocks; block i takes tile order[i] = by * gx + bx (order NULL: tile i),
 // so that the dispatch order can put the longest walks first.
-template <bool kClamp, int kAngles, int kSplit>
+template <bool kClamp, int kAngles, int kSplit, int kImgs>
 __global__ void __launch_bounds__(32 * kAngles / kSplit)
-joseph_forward_kernel(const float2 *__restrict__ pad, int N, int stride, int border,
+joseph_forward_kernel(const void *__restrict__ pad, int N, int stride, int border,
                       int n_angles, int n_det, const FwdAngle *__restrict__ tab,
-                      float *__restrict__ b, const int *__restrict__ order, int gx) {
+                      float *__restrict__ b, float *__restrict__ b2, const int *__restrict__ order,
+                      int gx) {
     const int tile = order ? order[blockIdx.x] : (int)blockIdx.x;
-    joseph_forward_block<kClamp, kAngles, kSplit>(pad, N, stride, border, n_angles, n_det, tab, b,
-                                                  tile % gx, tile / gx);
+    joseph_forward_block<kClamp, kAngles, kSplit, kImgs == 2 ? kFwdDepth2 : kFwdDepth, kImgs>(
+        pad, N, stride, border, n_angles, n_det, tab, b, b2, tile % gx, tile / gx);
 }
 
 // ---------------------------------------------------------------------------
@@ -368,21 +417,24 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
     cluster.sync();   // peers' shared memory must outlive the reads above
 }
 
+// bc: the input is column bc of a basis (b + col_offset(bc)), or b itself.
 template <typename T, int kChunk>
 __global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
-pixel_back_tiled_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
+pixel_back_tiled_kernel(const T *__restrict__ b, ColRef bc, int N, int n_angles, int n_det,
                         const BackAngle *__restrict__ tab, int W, const float *__restrict__ add,
                         float *__restrict__ x) {
-    pixel_back_tile<T, 0, kChunk>(b, N, n_angles, n_det, tab, W, add, x, blockIdx.x, blockIdx.y);
+    pixel_back_tile<T, 0, kChunk>(b + col_offset(bc), N, n_angles, n_det, tab, W, add, x, blockIdx.x,
+                                  blockIdx.y);
 }
 
 // A^T (kModel 1) or B_tau (kModel 2) with the tiled design above.
 template <typename T, int kModel>
 __global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
-matched_back_tiled_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
+matched_back_tiled_kernel(const T *__restrict__ b, ColRef bc, int N, int n_angles, int n_det,
                           const BackAngle *__restrict__ tab, int W, const MatchedAngle *__restrict__ mt,
                           float thr, const float *__restrict__ add, float *__restrict__ x) {
-    pixel_back_tile<T, kModel>(b, N, n_angles, n_det, tab, W, add, x, blockIdx.x, blockIdx.y, mt, thr);
+    pixel_back_tile<T, kModel>(b + col_offset(bc), N, n_angles, n_det, tab, W, add, x, blockIdx.x, blockIdx.y,
+                               mt, thr);
 }
 
 // Generic pixel-driven back projection (any detector pitch): 32 x 8 tiles,
@@ -391,10 +443,11 @@ constexpr int kBX = 32, kBY = 8, kAChunk = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kBX *kBY)
-pixel_back_kernel(const T *__restrict__ b, int N, int n_angles, int n_det,
+pixel_back_kernel(const T *__restrict__ b, ColRef bc, int N, int n_angles, int n_det,
                   const BackAngle *__restrict__ tab, const float *__restrict__ add,
                   float *__restrict__ x) {
     __shared__ float4 sp[kAChunk];
+    b += col_offset(bc);
     const int j0 = blockIdx.x * kBX, i0 = blockIdx.y * kBY;
     const int dj = threadIdx.x, di = threadIdx.y;
     const int tid = di * kBX + dj;
@@ -479,16 +532,16 @@ __global__ void batch_pad_kernel(const BatchInst *__restrict__ insts, const int2
     // AB stages t = B w_k; BA stages w_k itself, in its stored type
     const size_t off = (size_t)(I.k - 1) * I.ldw;
     if (I.variant == CTG_AB)
-        pad_pairs_block<float>(I.vn, I.pad, I.N, I.pad_stride, I.pad_border, mp.y % tx, mp.y / tx);
+        pad_pairs_block<1, float>(I.vn, nullptr, I.pad, I.N, I.pad_stride, I.pad_border, mp.y % tx, mp.y / tx);
     else if (I.wtype == CTG_BASIS_BF16)
-        pad_pairs_block<__nv_bfloat16>(static_cast<const __nv_bfloat16 *>(I.W) + off, I.pad, I.N,
-                                       I.pad_stride, I.pad_border, mp.y % tx, mp.y / tx);
+        pad_pairs_block<1, __nv_bfloat16>(static_cast<const __nv_bfloat16 *>(I.W) + off, nullptr, I.pad, I.N,
+                                          I.pad_stride, I.pad_border, mp.y % tx, mp.y / tx);
     else if (I.wtype == CTG_BASIS_FP16)
-        pad_pairs_block<__half>(static_cast<const __half *>(I.W) + off, I.pad, I.N, I.pad_stride,
-                                I.pad_border, mp.y % tx, mp.y / tx);
+        pad_pairs_block<1, __half>(static_cast<const __half *>(I.W) + off, nullptr, I.pad, I.N, I.pad_stride,
+                                   I.pad_border, mp.y % tx, mp.y / tx);
     else
-        pad_pairs_block<float>(static_cast<const float *>(I.W) + off, I.pad, I.N, I.pad_stride,
-                               I.pad_border, mp.y % tx, mp.y / tx);
+        pad_pairs_block<1, float>(static_cast<const float *>(I.W) + off, nullptr, I.pad, I.N, I.pad_stride,
+                                  I.pad_border, mp.y % tx, mp.y / tx);
 }
 
 // kAngles, kSplit: the forward shape of the round (one for all instances).
@@ -503,12 +556,12 @@ batch_forward_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict
     float *out = I.variant == CTG_AB ? I.vm : I.T + (size_t)(I.k - 1) * I.ldt;
     if (I.pad_clamp)
         joseph_forward_block<true, kAngles, kSplit, kBatchFwdDepth>(I.pad, I.N, I.pad_stride, I.pad_border,
-                                                                    I.n_angles, I.n_det, I.fwd, out, mp.y % bxn,
-                                                                    mp.y / bxn);
+                                                                    I.n_angles, I.n_det, I.fwd, out, nullptr,
+                                                                    mp.y % bxn, mp.y / bxn);
     else
         joseph_forward_block<false, kAngles, kSplit, kBatchFwdDepth>(I.pad, I.N, I.pad_stride, I.pad_border,
-                                                                     I.n_angles, I.n_det, I.fwd, out, mp.y % bxn,
-                                                                     mp.y / bxn);
+                                                                     I.n_angles, I.n_det, I.fwd, out, nullptr,
+                                                                     mp.y % bxn, mp.y / bxn);
 }
 
 }  // namespace
@@ -572,20 +625,41 @@ int ctg_back_window(const BackAngle *host_tab, int n_angles) {
 }
 
 cudaError_t ctg_launch_pad(const void *x, int dtype, float2 *pad, int N, const PadLayout &pl,
-                           cudaStream_t st) {
+                           cudaStream_t st, ColRef xc) {
     dim3 grid((N + kPadTile - 1) / kPadTile, (N + kPadTile - 1) / kPadTile), block(kPadTile, kPadRows);
     switch (dtype) {
         case CTG_BASIS_FP32:
-            pad_pairs_kernel<<<grid, block, 0, st>>>(static_cast<const float *>(x), pad, N, pl.stride,
-                                                     pl.border);
+            pad_pairs_kernel<1><<<grid, block, 0, st>>>(static_cast<const float *>(x), xc, nullptr, pad, N,
+                                                        pl.stride, pl.border);
             break;
         case CTG_BASIS_BF16:
-            pad_pairs_kernel<<<grid, block, 0, st>>>(static_cast<const __nv_bfloat16 *>(x), pad, N,
-                                                     pl.stride, pl.border);
+            pad_pairs_kernel<1><<<grid, block, 0, st>>>(static_cast<const __nv_bfloat16 *>(x), xc, nullptr,
+                                                        pad, N, pl.stride, pl.border);
             break;
         case CTG_BASIS_FP16:
-            pad_pairs_kernel<<<grid, block, 0, st>>>(static_cast<const __half *>(x), pad, N, pl.stride,
-                                                     pl.border);
+            pad_pairs_kernel<1><<<grid, block, 0, st>>>(static_cast<const __half *>(x), xc, nullptr, pad, N,
+                                                        pl.stride, pl.border);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_launch_pad2(const void *x, int dtype, ColRef xc, const float *x2, float4 *pad2, int N,
+                            const PadLayout &pl, cudaStream_t st) {
+    dim3 grid((N + kPadTile - 1) / kPadTile, (N + kPadTile - 1) / kPadTile), block(kPadTile, kPadRows);
+    switch (dtype) {
+        case CTG_BASIS_FP32:
+            pad_pairs_kernel<2><<<grid, block, 0, st>>>(static_cast<const float *>(x), xc, x2, pad2, N,
+                                                        pl.stride, pl.border);
+            break;
+        case CTG_BASIS_BF16:
+            pad_pairs_kernel<2><<<grid, block, 0, st>>>(static_cast<const __nv_bfloat16 *>(x), xc, x2, pad2,
+                                                        N, pl.stride, pl.border);
+            break;
+        case CTG_BASIS_FP16:
+            pad_pairs_kernel<2><<<grid, block, 0, st>>>(static_cast<const __half *>(x), xc, x2, pad2, N,
+                                                        pl.stride, pl.border);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -594,18 +668,29 @@ cudaError_t ctg_launch_pad(const void *x, int dtype, float2 *pad, int N, const P
 
 namespace {
 
-template <int kAngles, int kSplit>
-void launch_forward_t(const float2 *pad, int N, const PadLayout &pl, int n_angles, int n_det,
-                      const FwdAngle *tab, float *b, cudaStream_t st, const int *order) {
+template <int kAngles, int kSplit, int kImgs>
+void launch_forward_t(const void *pad, int N, const PadLayout &pl, int n_angles, int n_det,
+                      const FwdAngle *tab, float *b, float *b2, cudaStream_t st, const int *order) {
     constexpr int kRays = 32 / kSplit;
     const int gx = (n_det + kRays - 1) / kRays, gy = (n_angles + kAngles - 1) / kAngles;
     const unsigned grid = (unsigned)gx * (unsigned)gy;
     if (pl.clamp)
-        joseph_forward_kernel<true, kAngles, kSplit><<<grid, 32 * kAngles / kSplit, 0, st>>>(
-            pad, N, pl.stride, pl.border, n_angles, n_det, tab, b, order, gx);
+        joseph_forward_kernel<true, kAngles, kSplit, kImgs><<<grid, 32 * kAngles / kSplit, 0, st>>>(
+            pad, N, pl.stride, pl.border, n_angles, n_det, tab, b, b2, order, gx);
     else
-        joseph_forward_kernel<false, kAngles, kSplit><<<grid, 32 * kAngles / kSplit, 0, st>>>(
-            pad, N, pl.stride, pl.border, n_angles, n_det, tab, b, order, gx);
+        joseph_forward_kernel<false, kAngles, kSplit, kImgs><<<grid, 32 * kAngles / kSplit, 0, st>>>(
+            pad, N, pl.stride, pl.border, n_angles, n_det, tab, b, b2, order, gx);
+}
+
+template <int kImgs>
+void launch_forward_shape(int shape, const void *pad, int N, const PadLayout &pl, int n_angles, int n_det,
+                          const FwdAngle *tab, float *b, float *b2, cudaStream_t st, const int *order) {
+    switch (shape) {
+        case 1: launch_forward_t<4, 1, kImgs>(pad, N, pl, n_angles, n_det, tab, b, b2, st, order); break;
+        case 2: launch_forward_t<8, 4, kImgs>(pad, N, pl, n_angles, n_det, tab, b, b2, st, order); break;
+        case 3: launch_forward_t<16, 4, kImgs>(pad, N, pl, n_angles, n_det, tab, b, b2, st, order); break;
+        default: launch_forward_t<8, 1, kImgs>(pad, N, pl, n_angles, n_det, tab, b, b2, st, order); break;
+    }
 }
 
 // walk range [lo, hi] of ray d of angle t, as joseph_forward_block
@@ -648,12 +733,14 @@ cudaError_t ctg_launch_forward(const float2 *pad, int N, const PadLayout &pl, in
                                int shape, const int *order) {
     // every ray's sum depends on its own chord only, so the result depends
     // on neither the shape nor the dispatch order
-    switch (shape) {
-        case 1: launch_forward_t<4, 1>(pad, N, pl, n_angles, n_det, tab, b, st, order); break;
-        case 2: launch_forward_t<8, 4>(pad, N, pl, n_angles, n_det, tab, b, st, order); break;
-        case 3: launch_forward_t<16, 4>(pad, N, pl, n_angles, n_det, tab, b, st, order); break;
-        default: launch_forward_t<8, 1>(pad, N, pl, n_angles, n_det, tab, b, st, order); break;
-    }
+    launch_forward_shape<1>(shape, pad, N, pl, n_angles, n_det, tab, b, nullptr, st, order);
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_launch_forward2(const float4 *pad2, int N, const PadLayout &pl, int n_angles, int n_det,
+                                const FwdAngle *tab, float *b, float *b2, cudaStream_t st, int shape,
+                                const int *order) {
+    launch_forward_shape<2>(shape, pad2, N, pl, n_angles, n_det, tab, b, b2, st, order);
     return cudaGetLastError();
 }
 
@@ -720,46 +807,46 @@ bool ctg_forward_split_safe(const FwdAngle *tab, int N, int n_angles, int n_det,
 namespace {
 
 template <typename T, int kChunk>
-void launch_back_tiled(const T *b, int N, int n_angles, int n_det, const BackAngle *tab, int window,
-                       const float *add, float *x, cudaStream_t st) {
+void launch_back_tiled(const T *b, ColRef bc, int N, int n_angles, int n_det, const BackAngle *tab,
+                       int window, const float *add, float *x, cudaStream_t st) {
     const size_t smem = sizeof(float2) * (size_t)kChunk * window;
     const dim3 grid((N + kBT - 1) / kBT, (N + kBT - 1) / kBT, kBSplit);
-    pixel_back_tiled_kernel<T, kChunk><<<grid, kBThreads, smem, st>>>(b, N, n_angles, n_det, tab, window,
-                                                                      add, x);
+    pixel_back_tiled_kernel<T, kChunk><<<grid, kBThreads, smem, st>>>(b, bc, N, n_angles, n_det, tab,
+                                                                      window, add, x);
 }
 
 // back_chunk: angles staged per pass (16, 32 or 64).  Each pixel sums its
 // angles in the same order whatever the chunk, so the result does not
 // depend on it.
 template <typename T>
-cudaError_t launch_back_t(const T *b, int N, int n_angles, int n_det, const BackAngle *tab,
+cudaError_t launch_back_t(const T *b, ColRef bc, int N, int n_angles, int n_det, const BackAngle *tab,
                           int window, const float *add, float *x, cudaStream_t st, int back_chunk) {
     const size_t bytes_per_angle = sizeof(float2) * (size_t)window;
     if (window > 0 && back_chunk == 64 && 64 * bytes_per_angle <= 40 * 1024) {
-        launch_back_tiled<T, 64>(b, N, n_angles, n_det, tab, window, add, x, st);
+        launch_back_tiled<T, 64>(b, bc, N, n_angles, n_det, tab, window, add, x, st);
     } else if (window > 0 && back_chunk == 16 && 16 * bytes_per_angle <= 40 * 1024) {
-        launch_back_tiled<T, 16>(b, N, n_angles, n_det, tab, window, add, x, st);
+        launch_back_tiled<T, 16>(b, bc, N, n_angles, n_det, tab, window, add, x, st);
     } else if (window > 0 && kBChunk * bytes_per_angle <= 40 * 1024) {
-        launch_back_tiled<T, kBChunk>(b, N, n_angles, n_det, tab, window, add, x, st);
+        launch_back_tiled<T, kBChunk>(b, bc, N, n_angles, n_det, tab, window, add, x, st);
     } else {
         dim3 grid((N + kBX - 1) / kBX, (N + kBY - 1) / kBY);
-        pixel_back_kernel<T><<<grid, dim3(kBX, kBY), 0, st>>>(b, N, n_angles, n_det, tab, add, x);
+        pixel_back_kernel<T><<<grid, dim3(kBX, kBY), 0, st>>>(b, bc, N, n_angles, n_det, tab, add, x);
     }
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_matched_tiled_t(const T *b, int N, int n_angles, int n_det, const BackAngle *tab,
-                                   int window, const MatchedAngle *mt, float thr, const float *add,
-                                   float *x, cudaStream_t st) {
+cudaError_t launch_matched_tiled_t(const T *b, ColRef bc, int N, int n_angles, int n_det,
+                                   const BackAngle *tab, int window, const MatchedAngle *mt, float thr,
+                                   const float *add, float *x, cudaStream_t st) {
     const size_t smem = sizeof(float2) * (size_t)kBChunk * window;
     const dim3 grid((N + kBT - 1) / kBT, (N + kBT - 1) / kBT, kBSplit);
     if (thr > 0.0f)
-        matched_back_tiled_kernel<T, 2><<<grid, kBThreads, smem, st>>>(b, N, n_angles, n_det, tab, window,
-                                                                       mt, thr, add, x);
+        matched_back_tiled_kernel<T, 2><<<grid, kBThreads, smem, st>>>(b, bc, N, n_angles, n_det, tab,
+                                                                       window, mt, thr, add, x);
     else
-        matched_back_tiled_kernel<T, 1><<<grid, kBThreads, smem, st>>>(b, N, n_angles, n_det, tab, window,
-                                                                       mt, thr, add, x);
+        matched_back_tiled_kernel<T, 1><<<grid, kBThreads, smem, st>>>(b, bc, N, n_angles, n_det, tab,
+                                                                       window, mt, thr, add, x);
     return cudaGetLastError();
 }
 
@@ -767,17 +854,18 @@ cudaError_t launch_matched_tiled_t(const T *b, int N, int n_angles, int n_det, c
 
 cudaError_t ctg_launch_back_matched_tiled(const void *b, int dtype, int N, int n_angles, int n_det,
                                           const BackAngle *tab, int window, const MatchedAngle *mt,
-                                          float thr, const float *add, float *x, cudaStream_t st) {
+                                          float thr, const float *add, float *x, cudaStream_t st,
+                                          ColRef bc) {
     if (window <= 0 || window > ctg_back_window_max()) return cudaErrorInvalidValue;
     switch (dtype) {
         case CTG_BASIS_FP32:
-            return launch_matched_tiled_t(static_cast<const float *>(b), N, n_angles, n_det, tab, window, mt,
-                                          thr, add, x, st);
+            return launch_matched_tiled_t(static_cast<const float *>(b), bc, N, n_angles, n_det, tab, window,
+                                          mt, thr, add, x, st);
         case CTG_BASIS_BF16:
-            return launch_matched_tiled_t(static_cast<const __nv_bfloat16 *>(b), N, n_angles, n_det, tab,
+            return launch_matched_tiled_t(static_cast<const __nv_bfloat16 *>(b), bc, N, n_angles, n_det, tab,
                                           window, mt, thr, add, x, st);
         case CTG_BASIS_FP16:
-            return launch_matched_tiled_t(static_cast<const __half *>(b), N, n_angles, n_det, tab, window,
+            return launch_matched_tiled_t(static_cast<const __half *>(b), bc, N, n_angles, n_det, tab, window,
                                           mt, thr, add, x, st);
         default: return cudaErrorInvalidValue;
     }
@@ -785,17 +873,17 @@ cudaError_t ctg_launch_back_matched_tiled(const void *b, int dtype, int N, int n
 
 cudaError_t ctg_launch_back(const void *b, int dtype, int N, int n_angles, int n_det,
                             const BackAngle *tab, int window, const float *add, float *x,
-                            cudaStream_t st, int back_chunk) {
+                            cudaStream_t st, int back_chunk, ColRef bc) {
     switch (dtype) {
         case CTG_BASIS_FP32:
-            return launch_back_t(static_cast<const float *>(b), N, n_angles, n_det, tab, window, add, x, st,
+            return launch_back_t(static_cast<const float *>(b), bc, N, n_angles, n_det, tab, window, add, x, st,
                                  back_chunk);
         case CTG_BASIS_BF16:
-            return launch_back_t(static_cast<const __nv_bfloat16 *>(b), N, n_angles, n_det, tab, window,
+            return launch_back_t(static_cast<const __nv_bfloat16 *>(b), bc, N, n_angles, n_det, tab, window,
                                  add, x, st, back_chunk);
         case CTG_BASIS_FP16:
-            return launch_back_t(static_cast<const __half *>(b), N, n_angles, n_det, tab, window, add, x, st,
-                                 back_chunk);
+            return launch_back_t(static_cast<const __half *>(b), bc, N, n_angles, n_det, tab, window, add, x,
+                                 st, back_chunk);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -137,7 +137,9 @@ __host__ __device__ inline int padded_grid(int G) { return (G + 3) & ~3; }
 // blocks' partials (fixed order, FP64) into red_out[0..nred-1].  The last
 // block's warps each take four coefficients at a time and read the partials
 // as float4, so the serial tail is a few L2 round trips.
-__device__ void block_reduce_finish(float *s_w, int nred, float *__restrict__ partials,
+// Returns true in the last block (after red_out is written and the block
+// has synchronised), false in the others.
+__device__ bool block_reduce_finish(float *s_w, int nred, float *__restrict__ partials,
                                     unsigned *__restrict__ counter,
                                     double *__restrict__ red_out, int blk, int G) {
     __shared__ bool s_last;
@@ -153,7 +155,7 @@ __device__ void block_reduce_finish(float *s_w, int nred, float *__restrict__ pa
     __syncthreads();
     if (tid == 0) s_last = (atomicAdd(counter, 1u) == (unsigned)(G - 1));
     __syncthreads();
-    if (!s_last) return;
+    if (!s_last) return false;
     __threadfence();
     const int G4 = Gp / 4;
     for (int j0 = warp * 4; j0 < nred; j0 += kWarps * 4) {
@@ -182,6 +184,8 @@ __device__ void block_reduce_finish(float *s_w, int nred, float *__restrict__ pa
         }
     }
     if (tid == 0) *counter = 0u;
+    __syncthreads();
+    return true;
 }
 
 }  // namespace
