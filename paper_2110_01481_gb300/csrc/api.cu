@@ -189,7 +189,7 @@ struct WsLayout {
     // columns R, y of the last three steps, NCP residual coefficients,
     // rho and NCP histories
     size_t off_gc, off_gs, off_gg, off_R, off_yring, off_z, off_rhoh, off_ncph;
-    bool pad2;                     // the staged image holds two interleaved images
+    size_t off_pad2;               // BA: the staging of two interleaved images
     int64_t L, n, m;
     int kmax;
     int dtype;      // basis element type
@@ -238,10 +238,10 @@ int rule_of(const ctg_opts *o) {
 }
 
 // AB / BA: the basis W ((maxit + 1) vectors of length L, the storage law k L
-// of Table 3), the Hessenberg matrix, the staged image (two interleaved
-// images for BA with a residual-based stopping rule), one n-vector, two
-// m-vectors, the iterate coefficients, the loop state (O(maxit^2) doubles
-// for the rotated Hessenberg columns) and the reduction scratch.
+// of Table 3), the Hessenberg matrix, the staged image (BA also a staging of
+// two interleaved images), one n-vector, two m-vectors, the iterate
+// coefficients, the loop state (O(maxit^2) doubles for the rotated
+// Hessenberg columns) and the reduction scratch.
 bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) {
     if (!geom_valid(g) || !opts_valid(o)) return false;
     if (variant == CTG_LSQR || variant == CTG_LSMR) return layout_lsq(g, variant, o, ly);
@@ -258,7 +258,6 @@ bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) 
     ly->dtype = o->basis_dtype;
     ly->es = ctg_basis_bytes(o->basis_dtype);
     ly->ld_w = round_up((size_t)L, 64);
-    ly->pad2 = variant == CTG_BA && rule_of(o) != kRuleMaxit;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t at = off;
@@ -267,7 +266,9 @@ bool layout_of(const ctg_geom *g, int variant, const ctg_opts *o, WsLayout *ly) 
     };
     ly->off_w = take(ly->es * ly->ld_w * (K + 1));
     ly->off_h = take(sizeof(double) * (K + 1) * K);
-    ly->off_pad = take(sizeof(float) * ctg_pad_layout(g->N, g->det_spacing).floats * (ly->pad2 ? 2 : 1));
+    const size_t pad_floats = ctg_pad_layout(g->N, g->det_spacing).floats;
+    ly->off_pad = take(sizeof(float) * pad_floats);
+    ly->off_pad2 = variant == CTG_BA ? take(sizeof(float) * 2 * pad_floats) : 0;
     ly->off_vn0 = take(sizeof(float) * round_up((size_t)n, 64));
     ly->off_vm0 = take(sizeof(float) * round_up((size_t)m, 64));
     ly->off_vm1 = take(sizeof(float) * round_up((size_t)m, 64));
@@ -670,7 +671,7 @@ struct SolveCtx {
     }
     // b = A x and b2 = A x2 in one walk (x: column xc of the basis)
     cudaError_t forward2(ColRef xc, const float *x2, float *b, float *b2) const {
-        float4 *p4 = reinterpret_cast<float4 *>(pad());
+        float4 *p4 = at<float4>(ly.off_pad2);
         const cudaError_t e = traced(ctx, 3, 1, st, [&] {
             return ctg_launch_pad2(W(), ly.dtype, xc, x2, p4, g->N, ge->pl, st);
         });
@@ -759,7 +760,9 @@ int solve_setup(ctg_ctx *ctx, const ctg_geom *g, int variant, const ctg_opts *o,
     ctg_red_scratch_carve(sc->ws + sc->ly.off_red, sc->ly.n > sc->ly.m ? sc->ly.n : sc->ly.m,
                           lsq ? 2 : o->maxit + 1, &sc->rs);
     CTG_CK(cudaMemsetAsync(sc->rs.counter, 0, 4 * sizeof(unsigned), sc->st));
-    CTG_CK(cudaMemsetAsync(sc->pad(), 0, sizeof(float) * sc->ge->pl.floats * (sc->ly.pad2 ? 2 : 1), sc->st));
+    CTG_CK(cudaMemsetAsync(sc->pad(), 0, sizeof(float) * sc->ge->pl.floats, sc->st));
+    if (sc->ly.off_pad2)
+        CTG_CK(cudaMemsetAsync(sc->ws + sc->ly.off_pad2, 0, sizeof(float) * 2 * sc->ge->pl.floats, sc->st));
     if (!lsq)
         CTG_CK(cudaMemsetAsync(sc->ws + sc->ly.off_h, 0,
                                sizeof(double) * (size_t)(o->maxit + 1) * o->maxit, sc->st));
