@@ -387,7 +387,8 @@ int ctg_set_wait_limit(ctg_ctx *ctx, int64_t polls);
  * When enabled, the solvers bracket each phase with CUDA events on the
  * solver's stream and accumulate its device time; kernel launches are
  * counted whether or not timing is enabled.  Phases: 0 forward projection
- * (the Joseph A kernel), 1 back projection (B), 2 Arnoldi CGS2 step,
+ * (the Joseph A kernel; a launch that projects two images at once counts
+ * as two executions), 1 back projection (B), 2 Arnoldi CGS2 step,
  * 3 everything else (the forward projector's image staging, residual
  * norms, iterate formation). */
 typedef struct {

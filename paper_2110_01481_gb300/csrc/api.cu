@@ -562,16 +562,17 @@ cudaEvent_t next_event(ctg_ctx *ctx) {
     return ctx->events[ctx->events_used++];
 }
 
-// Runs f() (which enqueues `nkern` kernels on st) as one execution of
-// `phase`, bracketed by events when tracing is on.
+// Runs f() (which enqueues `nkern` kernels on st) as `ncalls` executions of
+// `phase` (a projection of two images counts as two), bracketed by events
+// when tracing is on.
 template <typename F>
-cudaError_t traced(ctg_ctx *ctx, int phase, int nkern, cudaStream_t st, F f) {
+cudaError_t traced(ctg_ctx *ctx, int phase, int nkern, cudaStream_t st, F f, int ncalls = 1) {
     if (ctx->capturing) {            // counted per launch of the captured graph
         ctx->captured_kernels += nkern;
         return f();
     }
     ctx->kernels += nkern;
-    ctx->calls[phase] += 1;
+    ctx->calls[phase] += ncalls;
     if (!ctx->timing) return f();
     cudaEvent_t a = next_event(ctx), b = next_event(ctx);
     if (a) cudaEventRecord(a, st);
@@ -679,7 +680,7 @@ struct SolveCtx {
         return traced(ctx, 0, 1, st, [&] {
             return ctg_launch_forward2(p4, g->N, ge->pl, g->n_angles, g->n_det, ge->fwd, b, b2, st,
                                        ge->fwd_shape, ge->order_for(ge->fwd_shape));
-        });
+        }, 2);
     }
     cudaError_t back(const void *b, const float *add, float *x, int btype = CTG_BASIS_FP32,
                      ColRef bc = col_none()) const {

@@ -48,8 +48,11 @@ __device__ void solve_y_warp(const double *__restrict__ R, int ldr, const double
     const int lane = threadIdx.x & 31;
     const bool packed = k <= pack_cap;
     if (packed)
-        for (int j = 0; j < k; ++j)
-            for (int i = lane; i <= j; i += 32) s_pack[j * (j + 1) / 2 + i] = R[(size_t)j * ldr + i];
+        // independent loads over the k x k square (the upper triangle kept)
+        for (int e = lane; e < k * k; e += 32) {
+            const int j = e / k, i = e - j * k;
+            if (i <= j) s_pack[j * (j + 1) / 2 + i] = R[(size_t)j * ldr + i];
+        }
     // t = g; for i = k-1 .. 0: y_i = t_i / R_ii, t_j -= R_ji y_i (j < i);
     // lane l owns t_j for j = l, l + 32, ... (k <= 256)
     if (k > 256) {
@@ -103,21 +106,41 @@ __device__ void solve_y_warp(const double *__restrict__ R, int ldr, const double
 // history is the true residual).
 enum { kGivY = 1, kGivZ = 2, kGivEnd = 4 };
 
+// Column k, the rotations and the rotated column are staged through shared
+// memory (all lanes load, lane 0 runs the recurrence), so the serial part
+// does no global round trips.
+constexpr int kGivStage = 512;     // steps staged; beyond, lane 0 reads global memory
+
 __global__ void loop_givens_kernel(LoopBufs B, int mode, int pack_cap) {
     extern __shared__ double s_pack[];
     __shared__ double s_c[2];
+    __shared__ double s_h[kGivStage + 1], s_gc[kGivStage], s_gs[kGivStage];
     GmresState &S = *B.S;
     const int k = S.k, lane = threadIdx.x;
     const double *h = B.H + (size_t)(k - 1) * B.ldh;
     double *Rk = B.R + (size_t)(k - 1) * B.ldr;
-    if (lane == 0) {
-        double r_prev = h[0];
-        for (int i = 0; i < k - 1; ++i) {
-            const double a = r_prev, b = h[i + 1];
-            Rk[i] = B.gc[i] * a + B.gs[i] * b;
-            r_prev = -B.gs[i] * a + B.gc[i] * b;
+    const bool staged = k <= kGivStage;
+    if (staged) {
+        for (int i = lane; i <= k; i += 32) s_h[i] = h[i];
+        for (int i = lane; i < k - 1; i += 32) {
+            s_gc[i] = B.gc[i];
+            s_gs[i] = B.gs[i];
         }
-        const double a = r_prev, b = h[k];
+    }
+    __syncwarp();
+    const double *hh = staged ? s_h : h;
+    const double *gcc = staged ? s_gc : B.gc;
+    const double *gss = staged ? s_gs : B.gs;
+    if (lane == 0) {
+        double r_prev = hh[0];
+        for (int i = 0; i < k - 1; ++i) {
+            const double a = r_prev, b = hh[i + 1];
+            const double t = gcc[i] * a + gss[i] * b;
+            if (staged) s_h[i] = t;            // rotated column, stored below
+            else Rk[i] = t;
+            r_prev = -gss[i] * a + gcc[i] * b;
+        }
+        const double a = r_prev, b = hh[k];
         const double r = hypot(a, b);
         double c = 1.0, sn = 0.0;
         if (b != 0.0) {
@@ -126,7 +149,8 @@ __global__ void loop_givens_kernel(LoopBufs B, int mode, int pack_cap) {
         }
         B.gc[k - 1] = c;
         B.gs[k - 1] = sn;
-        Rk[k - 1] = b != 0.0 ? r : a;
+        if (staged) s_h[k - 1] = b != 0.0 ? r : a;
+        else Rk[k - 1] = b != 0.0 ? r : a;
         B.gg[k] = -sn * B.gg[k - 1];
         B.gg[k - 1] = c * B.gg[k - 1];
         const double rho = fabs(B.gg[k]);
@@ -134,8 +158,11 @@ __global__ void loop_givens_kernel(LoopBufs B, int mode, int pack_cap) {
         B.rhoh[k] = rho;
         s_c[0] = rho;
         // a NaN column marks a CGS2 step that gave up at a grid barrier
-        s_c[1] = (h[k] <= 1e-6 * sqrt(B.h1[k]) || !(h[k] == h[k])) ? 1.0 : 0.0;
+        s_c[1] = (b <= 1e-6 * sqrt(B.h1[k]) || !(b == b)) ? 1.0 : 0.0;
     }
+    __syncwarp();
+    if (staged)
+        for (int i = lane; i < k; i += 32) Rk[i] = s_h[i];
     __syncwarp();
     const double rho = s_c[0];
     const bool breakdown = s_c[1] != 0.0;
