@@ -600,28 +600,59 @@ __global__ void batch_givens_kernel(BatchInst *__restrict__ insts) {
     }
     __syncwarp();
     if (I.variant == CTG_BA && I.target > 0.0) {
-        // back substitution, one row at a time, the row sums shared by the warp
+        // y_k = R^{-1} g by back substitution, one row at a time, the row
+        // sums shared by the warp
         for (int i = k - 1; i >= 0; --i) {
             double t = 0.0;
-            for (int j = i + 1 + lane; j < k; j += 32) t += I.R[(size_t)j * ldr + i] * (-I.y[j]);
+            for (int j = i + 1 + lane; j < k; j += 32) t += I.R[(size_t)j * ldr + i] * I.y[j];
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
             if (lane == 0) {
                 const double d = I.R[(size_t)i * ldr + i];
-                I.y[i] = -(d != 0.0 ? (I.gg[i] - t) / d : 0.0);
+                I.y[i] = d != 0.0 ? (I.gg[i] - t) / d : 0.0;
             }
             __syncwarp();
         }
     }
 }
 
-// BA with the discrepancy stop: ||b - A x_k||^2 = ||(b - A x0) - T_k y_k||^2.
+// BA with the discrepancy stop: x_k = x0 + W_k y_k into the solve's x
+// (E = 1 slices; the map's local blocks cover n).
+template <typename T>
+__device__ __forceinline__ void batch_iterate_body(BatchInst &I, int blk, float *s_y) {
+    for (int j = threadIdx.x; j < I.k; j += kThreads) s_y[j] = (float)I.y[j];
+    __syncthreads();
+    const int64_t g0 = (int64_t)blk * kThreads + threadIdx.x;
+    float4 acc[1];
+    acc[0] = I.x0 ? ld4(I.x0, g0, I.n) : make_float4(0.f, 0.f, 0.f, 0.f);
+    accumulate_batched<T, 1>(static_cast<const T *>(I.W), I.ldw, I.k, s_y, g0, I.n, acc);
+    st4(I.x, g0, I.n, acc[0]);
+}
+
 __global__ void __launch_bounds__(kThreads, 2)
-batch_residual_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
+batch_iterate_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
+    extern __shared__ float s_y[];
     const int2 mp = map[blockIdx.x];
     BatchInst &I = insts[mp.x];
     if (!I.active || I.variant != CTG_BA || !(I.target > 0.0)) return;
-    gemv_norm2_body<1>(I.T, I.ldt, I.k, I.y, I.r0m, I.m, I.partials, I.counter, I.scal + 4, mp.y,
-                       vec_blocks_dev(I.m));
+    if (I.wtype == CTG_BASIS_BF16) batch_iterate_body<__nv_bfloat16>(I, mp.y, s_y);
+    else if (I.wtype == CTG_BASIS_FP16) batch_iterate_body<__half>(I, mp.y, s_y);
+    else batch_iterate_body<float>(I, mp.y, s_y);
+}
+
+// BA with the discrepancy stop: ||b - A x_k||^2 into scal[4] (A x_k in vr).
+__global__ void __launch_bounds__(kThreads, 2)
+batch_residual_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
+    __shared__ float s_w[kWarps];
+    const int2 mp = map[blockIdx.x];
+    BatchInst &I = insts[mp.x];
+    if (!I.active || I.variant != CTG_BA || !(I.target > 0.0)) return;
+    const int64_t g = (int64_t)mp.y * kThreads + threadIdx.x;
+    float4 v = ld4(I.b, g, I.m);
+    const float4 w = ld4(I.vr, g, I.m);
+    v.x -= w.x; v.y -= w.y; v.z -= w.z; v.w -= w.w;
+    float s = warp_sum(dot4(v, v));
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
+    block_reduce_finish(s_w, 1, I.partials, I.counter, I.scal + 4, mp.y, vec_blocks_dev(I.m));
 }
 
 // One thread per instance: the stopping rules (Sec. 6.4), then k -> k + 1.
@@ -1154,7 +1185,7 @@ cudaError_t ctg_batch_prepare(int max_k) {
     if ((err = prepare_batch_cgs2<float>(smem)) != cudaSuccess) return err;
     if ((err = prepare_batch_cgs2<__nv_bfloat16>(smem)) != cudaSuccess) return err;
     if ((err = prepare_batch_cgs2<__half>(smem)) != cudaSuccess) return err;
-    return ensure_smem(batch_residual_kernel, sizeof(float) * (size_t)(max_k > 0 ? max_k : 1));
+    return ensure_smem(batch_iterate_kernel, sizeof(float) * (size_t)(max_k > 0 ? max_k : 1));
 }
 
 cudaError_t ctg_batch_givens(BatchInst *insts, int n_inst, cudaStream_t st) {
@@ -1163,11 +1194,16 @@ cudaError_t ctg_batch_givens(BatchInst *insts, int n_inst, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t ctg_batch_residual(BatchInst *insts, const int2 *map_m, int nblocks, int max_k,
-                               cudaStream_t st) {
+cudaError_t ctg_batch_iterate(BatchInst *insts, const int2 *map_n, int nblocks, int max_k, cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
     const size_t smem = sizeof(float) * (size_t)(max_k > 0 ? max_k : 1);
-    batch_residual_kernel<<<nblocks, kThreads, smem, st>>>(insts, map_m);
+    batch_iterate_kernel<<<nblocks, kThreads, smem, st>>>(insts, map_n);
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_batch_residual(BatchInst *insts, const int2 *map_m, int nblocks, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    batch_residual_kernel<<<nblocks, kThreads, 0, st>>>(insts, map_m);
     return cudaGetLastError();
 }
 

@@ -74,7 +74,8 @@ size_t plan_instance(InstPlan &p, char *base) {
     const bool ba = p.variant == CTG_BA;
     const long long L = ba ? n : m;
     const PadLayout pl = ctg_pad_layout(g.N, g.det_spacing);
-    const size_t ldw = rup((size_t)L, 64), ldt = rup((size_t)m, 64);
+    const size_t ldw = rup((size_t)L, 64);
+    const bool dp = p.o.noise_norm > 0.0;
     const int Gn = ctg_vec_blocks(n), Gm = ctg_vec_blocks(m);
     const int Gp = padded4(Gn > Gm ? Gn : Gm);
     size_t off = 0;
@@ -97,12 +98,11 @@ size_t plan_instance(InstPlan &p, char *base) {
     d.L = L;
     d.maxit = maxit;
     d.ldw = (long long)ldw;
-    d.ldt = (long long)ldt;
     d.G = ctg_vec_blocks(L);
     d.target = p.o.noise_norm > 0.0 ? p.o.tau * p.o.noise_norm : 0.0;
     d.wtype = p.o.basis_dtype;
+    // the basis is the only O(maxit L) buffer: the storage law k L of Table 3
     d.W = take(ctg_basis_bytes(p.o.basis_dtype) * ldw * (size_t)(maxit + 1));
-    d.T = ba ? (float *)take(sizeof(float) * ldt * (size_t)(maxit + 1)) : nullptr;
     d.H = (double *)take(sizeof(double) * (size_t)(maxit + 1) * maxit);
     d.R = (double *)take(sizeof(double) * (size_t)maxit * maxit);
     d.gc = (double *)take(sizeof(double) * maxit);
@@ -112,8 +112,9 @@ size_t plan_instance(InstPlan &p, char *base) {
     d.hist = (double *)take(sizeof(double) * (maxit + 1));
     d.vn = (float *)take(sizeof(float) * rup((size_t)n, 64));
     d.vm = (float *)take(sizeof(float) * rup((size_t)m, 64));
-    d.r0m = ba ? (float *)take(sizeof(float) * rup((size_t)m, 64)) : nullptr;
+    d.vr = ba && dp ? (float *)take(sizeof(float) * rup((size_t)m, 64)) : nullptr;
     d.pad = (float2 *)take(sizeof(float) * pl.floats);
+    d.pad2 = ba && dp ? (float4 *)take(sizeof(float) * 2 * pl.floats) : nullptr;
     d.fwd = (const FwdAngle *)take(sizeof(FwdAngle) * g.n_angles);
     d.back = (const BackAngle *)take(sizeof(BackAngle) * g.n_angles);
     d.back_model = g.back_model;
@@ -200,12 +201,7 @@ struct ctg_batch {
     size_t ws_bytes = 0;
     BatchInst *d_insts = nullptr;
     int2 *d_maps = nullptr;
-    int map_back = 0, map_pad = 0, map_fwd = 0, map_cgs = 0, map_m = 0;   // offsets
-    int n_back = 0, n_pad = 0, n_fwd = 0, n_cgs = 0, n_m = 0;             // lengths
-    int map_b16 = 0, n_b16 = 0, map_h16 = 0, n_h16 = 0;   // AB instances with a 16-bit basis
-    int map_cgs_b16 = 0, n_cgs_b16 = 0, map_cgs_h16 = 0, n_cgs_h16 = 0;
     int max_window = 0, max_maxit = 0;
-    int fwd_shape = 0;
     int *d_active = nullptr;
     int *h_active = nullptr;     // pinned
     double *h_stage = nullptr;   // pinned: per instance scal[0..7]
@@ -232,66 +228,90 @@ void release(ctg_batch *b) {
     delete b;
 }
 
-// Everything one captured round needs: the instance array, the block maps
-// (offsets / lengths into one map array) and the launch limits.
+// The launches of a round, in order, each with its block map (offsets /
+// lengths into one map array):
+//   back: q = B w_k (AB) or B t_k (BA), FP32 launch and the AB BF16 / FP16
+//     ones; AB: stage t, q = A t; CGS2 per basis type; Givens; BA with the
+//     DP stop: x_k = x0 + W_k y_k; BA: stage w_{k+1} (and x_k), t_{k+1} =
+//     A w_{k+1} (and A x_k); BA with the DP stop: ||b - A x_k||; the
+//     stopping rules.
+enum { MB_BACK, MB_B16, MB_H16, MB_PAD_AB, MB_FWD_AB, MB_CGS, MB_CGS_B16, MB_CGS_H16,
+       MB_ITER, MB_PAD_BA, MB_FWD_BA, MB_RES, MB_COUNT };
 struct RoundSpec {
     BatchInst *insts;
     int n_inst;
     const int2 *maps;
-    int map_back, n_back, map_pad, n_pad, map_fwd, n_fwd, map_cgs, n_cgs, map_m, n_m;
-    int map_b16, n_b16, map_h16, n_h16;    // AB back phase of instances with a BF16 / FP16 basis
-    int map_cgs_b16, n_cgs_b16, map_cgs_h16, n_cgs_h16;   // CGS2 of instances with a 16-bit basis
+    int off[MB_COUNT], len[MB_COUNT];
     int max_window, max_maxit;
     int *d_active;
-    int fwd_shape;    // forward shape of the round (ctg_batch_forward)
+    int fwd_shape_ab, fwd_shape_ba;   // forward shapes of the two forward launches
 };
 
 // Build the block maps of instances `ids` (indices into the instance array).
 template <typename Plans>
 void build_maps(const Plans &plans, const std::vector<int> &ids, std::vector<int2> &maps, RoundSpec &rs) {
     maps.clear();
-    auto add = [&](int &off, int &len, auto count) {
-        off = (int)maps.size();
+    auto add = [&](int which, auto count) {
+        rs.off[which] = (int)maps.size();
         for (int i : ids) {
             const int c = count(plans[i]);
             for (int j = 0; j < c; ++j) maps.push_back(make_int2(i, j));
         }
-        len = (int)maps.size() - off;
+        rs.len[which] = (int)maps.size() - rs.off[which];
     };
-    add(rs.map_back, rs.n_back, [](const InstPlan &p) { return ctg_back_tiles(p.g.N); });
-    add(rs.map_b16, rs.n_b16, [](const InstPlan &p) {
-        return p.variant == CTG_AB && p.o.basis_dtype == CTG_BASIS_BF16 ? ctg_back_tiles(p.g.N) : 0;
+    auto is_ab = [](const InstPlan &p) { return p.variant == CTG_AB; };
+    auto ba_dp = [](const InstPlan &p) { return p.variant == CTG_BA && p.o.noise_norm > 0.0; };
+    add(MB_BACK, [&](const InstPlan &p) {
+        return (!is_ab(p) || p.o.basis_dtype == CTG_BASIS_FP32) ? ctg_back_tiles(p.g.N) : 0;
     });
-    add(rs.map_h16, rs.n_h16, [](const InstPlan &p) {
-        return p.variant == CTG_AB && p.o.basis_dtype == CTG_BASIS_FP16 ? ctg_back_tiles(p.g.N) : 0;
+    add(MB_B16, [&](const InstPlan &p) {
+        return is_ab(p) && p.o.basis_dtype == CTG_BASIS_BF16 ? ctg_back_tiles(p.g.N) : 0;
     });
-    add(rs.map_pad, rs.n_pad, [](const InstPlan &p) { return ctg_pad_tiles(p.g.N); });
-    // one forward shape for the round: several angles per warp when every
-    // instance allows it
-    bool split = !ids.empty();
-    for (int i : ids) split = split && plans[i].fwd && plans[i].fwd->split_ok;
-    rs.fwd_shape = split ? kBatchFwdSplitShape : 0;
-    const int fs = rs.fwd_shape;
-    add(rs.map_fwd, rs.n_fwd, [fs](const InstPlan &p) { return ctg_fwd_shape_blocks(fs, p.g.n_angles, p.g.n_det); });
-    // each instance's forward blocks longest first (the result is the same
-    // in any order; the launch's tail is shorter)
-    for (int t = rs.map_fwd; t < rs.map_fwd + rs.n_fwd; ++t) {
-        const InstPlan &p = plans[maps[t].x];
-        if (!p.fwd) continue;
-        const std::vector<int> &o = p.fwd->order[split ? 1 : 0];
-        if ((int)o.size() == ctg_fwd_shape_blocks(fs, p.g.n_angles, p.g.n_det)) maps[t].y = o[maps[t].y];
-    }
+    add(MB_H16, [&](const InstPlan &p) {
+        return is_ab(p) && p.o.basis_dtype == CTG_BASIS_FP16 ? ctg_back_tiles(p.g.N) : 0;
+    });
+    add(MB_PAD_AB, [&](const InstPlan &p) { return is_ab(p) ? ctg_pad_tiles(p.g.N) : 0; });
+    // one forward shape per forward launch: several angles per warp when
+    // every instance of the launch allows it
+    auto shape_for = [&](bool ab) {
+        bool split = false, any = false;
+        for (int i : ids)
+            if (is_ab(plans[i]) == ab) {
+                split = (any ? split : true) && plans[i].fwd && plans[i].fwd->split_ok;
+                any = true;
+            }
+        return any && split ? kBatchFwdSplitShape : 0;
+    };
+    rs.fwd_shape_ab = shape_for(true);
+    rs.fwd_shape_ba = shape_for(false);
+    auto add_fwd = [&](int which, bool ab) {
+        const int fs = ab ? rs.fwd_shape_ab : rs.fwd_shape_ba;
+        add(which, [&](const InstPlan &p) {
+            return is_ab(p) == ab ? ctg_fwd_shape_blocks(fs, p.g.n_angles, p.g.n_det) : 0;
+        });
+        // each instance's forward blocks longest first (the result is the
+        // same in any order; the launch's tail is shorter)
+        for (int t = rs.off[which]; t < rs.off[which] + rs.len[which]; ++t) {
+            const InstPlan &p = plans[maps[t].x];
+            if (!p.fwd) continue;
+            const std::vector<int> &o = p.fwd->order[fs == kBatchFwdSplitShape ? 1 : 0];
+            if ((int)o.size() == ctg_fwd_shape_blocks(fs, p.g.n_angles, p.g.n_det)) maps[t].y = o[maps[t].y];
+        }
+    };
+    add_fwd(MB_FWD_AB, true);
     auto cgs_blocks = [](const InstPlan &p, int wtype) {
         if (p.o.basis_dtype != wtype) return 0;
         return ctg_vec_blocks(p.variant == CTG_BA ? (long long)p.g.N * p.g.N
                                                   : (long long)p.g.n_angles * p.g.n_det);
     };
-    add(rs.map_cgs, rs.n_cgs, [&](const InstPlan &p) { return cgs_blocks(p, CTG_BASIS_FP32); });
-    add(rs.map_cgs_b16, rs.n_cgs_b16, [&](const InstPlan &p) { return cgs_blocks(p, CTG_BASIS_BF16); });
-    add(rs.map_cgs_h16, rs.n_cgs_h16, [&](const InstPlan &p) { return cgs_blocks(p, CTG_BASIS_FP16); });
-    add(rs.map_m, rs.n_m, [](const InstPlan &p) {
-        return (p.variant == CTG_BA && p.o.noise_norm > 0.0)
-                   ? ctg_vec_blocks((long long)p.g.n_angles * p.g.n_det) : 0;
+    add(MB_CGS, [&](const InstPlan &p) { return cgs_blocks(p, CTG_BASIS_FP32); });
+    add(MB_CGS_B16, [&](const InstPlan &p) { return cgs_blocks(p, CTG_BASIS_BF16); });
+    add(MB_CGS_H16, [&](const InstPlan &p) { return cgs_blocks(p, CTG_BASIS_FP16); });
+    add(MB_ITER, [&](const InstPlan &p) { return ba_dp(p) ? ctg_vec_blocks((long long)p.g.N * p.g.N) : 0; });
+    add(MB_PAD_BA, [&](const InstPlan &p) { return is_ab(p) ? 0 : ctg_pad_tiles(p.g.N); });
+    add_fwd(MB_FWD_BA, false);
+    add(MB_RES, [&](const InstPlan &p) {
+        return ba_dp(p) ? ctg_vec_blocks((long long)p.g.n_angles * p.g.n_det) : 0;
     });
 }
 
@@ -299,10 +319,9 @@ void build_maps(const Plans &plans, const std::vector<int> &ids, std::vector<int
 // two rounds with the same signature capture the same kernels in the same
 // order.
 unsigned round_signature(const RoundSpec &r) {
-    const int n[] = {r.n_back, r.n_b16, r.n_h16, r.n_pad, r.n_fwd, r.n_cgs, r.n_cgs_b16, r.n_cgs_h16, r.n_m};
     unsigned sig = 0;
-    for (int i = 0; i < (int)(sizeof(n) / sizeof(n[0])); ++i) sig |= (n[i] > 0 ? 1u : 0u) << i;
-    return sig | (unsigned)r.fwd_shape << 16;
+    for (int i = 0; i < MB_COUNT; ++i) sig |= (r.len[i] > 0 ? 1u : 0u) << i;
+    return sig | (unsigned)r.fwd_shape_ab << 16 | (unsigned)r.fwd_shape_ba << 20;
 }
 
 // Capture one round into *out.  If *out already holds an executable graph
@@ -315,21 +334,26 @@ int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out, uns
     B_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     const int2 *M = r.maps;
-    if (e == cudaSuccess) e = ctg_batch_back(r.insts, M + r.map_back, r.n_back, CTG_PH_BACK_AB, r.max_window, st);
+    auto map = [&](int w) { return M + r.off[w]; };
+    if (e == cudaSuccess) e = ctg_batch_back(r.insts, map(MB_BACK), r.len[MB_BACK], r.max_window, st);
     if (e == cudaSuccess)
-        e = ctg_batch_back(r.insts, M + r.map_b16, r.n_b16, CTG_PH_BACK_AB, r.max_window, st, CTG_BASIS_BF16);
+        e = ctg_batch_back(r.insts, map(MB_B16), r.len[MB_B16], r.max_window, st, CTG_BASIS_BF16);
     if (e == cudaSuccess)
-        e = ctg_batch_back(r.insts, M + r.map_h16, r.n_h16, CTG_PH_BACK_AB, r.max_window, st, CTG_BASIS_FP16);
-    if (e == cudaSuccess) e = ctg_batch_pad(r.insts, M + r.map_pad, r.n_pad, st);
-    if (e == cudaSuccess) e = ctg_batch_forward(r.insts, M + r.map_fwd, r.n_fwd, st, r.fwd_shape);
-    if (e == cudaSuccess) e = ctg_batch_back(r.insts, M + r.map_back, r.n_back, CTG_PH_BACK_BA, r.max_window, st);
-    if (e == cudaSuccess) e = ctg_batch_cgs2(r.insts, M + r.map_cgs, r.n_cgs, r.max_maxit, st);
+        e = ctg_batch_back(r.insts, map(MB_H16), r.len[MB_H16], r.max_window, st, CTG_BASIS_FP16);
+    if (e == cudaSuccess) e = ctg_batch_pad(r.insts, map(MB_PAD_AB), r.len[MB_PAD_AB], CTG_AB, st);
     if (e == cudaSuccess)
-        e = ctg_batch_cgs2(r.insts, M + r.map_cgs_b16, r.n_cgs_b16, r.max_maxit, st, CTG_BASIS_BF16);
+        e = ctg_batch_forward(r.insts, map(MB_FWD_AB), r.len[MB_FWD_AB], CTG_AB, st, r.fwd_shape_ab);
+    if (e == cudaSuccess) e = ctg_batch_cgs2(r.insts, map(MB_CGS), r.len[MB_CGS], r.max_maxit, st);
     if (e == cudaSuccess)
-        e = ctg_batch_cgs2(r.insts, M + r.map_cgs_h16, r.n_cgs_h16, r.max_maxit, st, CTG_BASIS_FP16);
+        e = ctg_batch_cgs2(r.insts, map(MB_CGS_B16), r.len[MB_CGS_B16], r.max_maxit, st, CTG_BASIS_BF16);
+    if (e == cudaSuccess)
+        e = ctg_batch_cgs2(r.insts, map(MB_CGS_H16), r.len[MB_CGS_H16], r.max_maxit, st, CTG_BASIS_FP16);
     if (e == cudaSuccess) e = ctg_batch_givens(r.insts, r.n_inst, st);
-    if (e == cudaSuccess) e = ctg_batch_residual(r.insts, M + r.map_m, r.n_m, r.max_maxit, st);
+    if (e == cudaSuccess) e = ctg_batch_iterate(r.insts, map(MB_ITER), r.len[MB_ITER], r.max_maxit, st);
+    if (e == cudaSuccess) e = ctg_batch_pad(r.insts, map(MB_PAD_BA), r.len[MB_PAD_BA], CTG_BA, st);
+    if (e == cudaSuccess)
+        e = ctg_batch_forward(r.insts, map(MB_FWD_BA), r.len[MB_FWD_BA], CTG_BA, st, r.fwd_shape_ba);
+    if (e == cudaSuccess) e = ctg_batch_residual(r.insts, map(MB_RES), r.len[MB_RES], st);
     if (e == cudaSuccess) e = ctg_batch_finish(r.insts, r.n_inst, r.d_active, st);
     cudaError_t e2 = cudaStreamEndCapture(st, &graph);
     if (e == cudaSuccess) e = e2;
@@ -393,16 +417,6 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
     for (int i = 0; i < n; ++i) ids[i] = i;
     RoundSpec spec{};
     build_maps(b->inst, ids, maps, spec);
-    b->map_back = spec.map_back; b->n_back = spec.n_back;
-    b->map_pad = spec.map_pad; b->n_pad = spec.n_pad;
-    b->map_fwd = spec.map_fwd; b->n_fwd = spec.n_fwd;
-    b->map_cgs = spec.map_cgs; b->n_cgs = spec.n_cgs;
-    b->map_m = spec.map_m; b->n_m = spec.n_m;
-    b->map_b16 = spec.map_b16; b->n_b16 = spec.n_b16;
-    b->map_h16 = spec.map_h16; b->n_h16 = spec.n_h16;
-    b->map_cgs_b16 = spec.map_cgs_b16; b->n_cgs_b16 = spec.n_cgs_b16;
-    b->map_cgs_h16 = spec.map_cgs_h16; b->n_cgs_h16 = spec.n_cgs_h16;
-    b->fwd_shape = spec.fwd_shape;
     if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_maps, sizeof(int2) * (maps.empty() ? 1 : maps.size())));
     if (rc == CTG_OK && !maps.empty())
         rc = ck(cudaMemcpy(b->d_maps, maps.data(), sizeof(int2) * maps.size(), cudaMemcpyHostToDevice));
@@ -419,11 +433,13 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
         rc = upload_tables(p, b->st);
     }
     if (rc == CTG_OK) {
-        RoundSpec r{b->d_insts, n, b->d_maps, b->map_back, b->n_back, b->map_pad, b->n_pad,
-                    b->map_fwd, b->n_fwd, b->map_cgs, b->n_cgs, b->map_m, b->n_m,
-                    b->map_b16, b->n_b16, b->map_h16, b->n_h16,
-                    b->map_cgs_b16, b->n_cgs_b16, b->map_cgs_h16, b->n_cgs_h16,
-                    b->max_window, b->max_maxit, b->d_active, b->fwd_shape};
+        RoundSpec r = spec;
+        r.insts = b->d_insts;
+        r.n_inst = n;
+        r.maps = b->d_maps;
+        r.max_window = b->max_window;
+        r.max_maxit = b->max_maxit;
+        r.d_active = b->d_active;
         rc = capture_round(r, b->st, &b->round);
     }
     if (rc != CTG_OK) {
@@ -440,9 +456,9 @@ extern "C" size_t ctg_batch_workspace_bytes(const ctg_batch *b) { return b ? b->
 
 namespace {
 
-// Enqueue the start of one solve: r0 (AB: b - A x0 in vm; BA: b - A x0 in
-// r0m and B r0 in vn), ||r0||^2 in scal[2] and (BA) ||b - A x0||^2 in
-// scal[4]; copies scal[0..7] to `stage` (pinned).
+// Enqueue the start of one solve: r0 (AB: b - A x0 in vm; BA: B (b - A x0)
+// in vn), ||r0||^2 in scal[2] and (BA) ||b - A x0||^2 in scal[4]; copies
+// scal[0..7] to `stage` (pinned).
 int enqueue_start(InstPlan &p, const float *b, const float *x0, double *stage, cudaStream_t st) {
     BatchInst &d = p.d;
     const RedScratch rs = scratch_of(d);
@@ -452,6 +468,7 @@ int enqueue_start(InstPlan &p, const float *b, const float *x0, double *stage, c
     B_CK(cudaMemsetAsync(d.H, 0, sizeof(double) * (size_t)(p.o.maxit + 1) * p.o.maxit, st));
     B_CK(cudaMemsetAsync(d.hist, 0, sizeof(double) * (p.o.maxit + 1), st));
     B_CK(cudaMemsetAsync(d.pad, 0, sizeof(float) * pl.floats, st));
+    if (d.pad2) B_CK(cudaMemsetAsync(d.pad2, 0, sizeof(float) * 2 * pl.floats, st));
     if (x0) {
         B_CK(ctg_launch_pad(x0, CTG_BASIS_FP32, d.pad, p.g.N, pl, st));
         B_CK(ctg_launch_forward(d.pad, p.g.N, pl, p.g.n_angles, p.g.n_det, d.fwd, d.vm, st));
@@ -459,8 +476,8 @@ int enqueue_start(InstPlan &p, const float *b, const float *x0, double *stage, c
     if (p.variant == CTG_AB) {
         B_CK(ctg_sub_norm2(b, x0 ? d.vm : nullptr, d.vm, d.m, d.scal + 2, rs, st));
     } else {
-        B_CK(ctg_sub_norm2(b, x0 ? d.vm : nullptr, d.r0m, d.m, d.scal + 4, rs, st));
-        B_CK(back_inst(p, d.r0m, nullptr, d.vn, st));
+        B_CK(ctg_sub_norm2(b, x0 ? d.vm : nullptr, d.vm, d.m, d.scal + 4, rs, st));
+        B_CK(back_inst(p, d.vm, nullptr, d.vn, st));
         B_CK(ctg_sub_norm2(d.vn, nullptr, nullptr, d.n, d.scal + 2, rs, st));
     }
     B_CK(cudaMemcpyAsync(stage, d.scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
@@ -496,6 +513,12 @@ int activate(InstPlan &p, double *stage, ctg_info *info, cudaStream_t st, int *a
     }
     d.active = 1;
     B_CK(ctg_scale(p.variant == CTG_AB ? d.vm : d.vn, d.scal + 2, d.W, d.wtype, d.L, st));
+    if (p.variant == CTG_BA) {
+        // t_1 = A w_1, which the first round back-projects
+        const PadLayout pl = ctg_pad_layout(p.g.N, p.g.det_spacing);
+        B_CK(ctg_launch_pad(d.W, d.wtype, d.pad, p.g.N, pl, st));
+        B_CK(ctg_launch_forward(d.pad, p.g.N, pl, p.g.n_angles, p.g.n_det, d.fwd, d.vm, st));
+    }
     stage[6] = beta;
     B_CK(cudaMemcpyAsync(d.gg, &stage[6], sizeof(double), cudaMemcpyHostToDevice, st));
     *active_out = 1;
@@ -560,7 +583,13 @@ extern "C" int ctg_batch_solve(ctg_batch *b, const float *const *b_dev, const fl
         active += a;
     }
     std::vector<BatchInst> hi(n);
-    for (int i = 0; i < n; ++i) hi[i] = b->inst[i].d;
+    for (int i = 0; i < n; ++i) {
+        BatchInst &d = b->inst[i].d;
+        d.b = b_dev[i];
+        d.x0 = x0_dev ? x0_dev[i] : nullptr;
+        d.x = x_dev[i];
+        hi[i] = d;
+    }
     B_CK(cudaMemcpyAsync(b->d_insts, hi.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, st));
     *b->h_active = active;
     B_CK(cudaMemcpyAsync(b->d_active, b->h_active, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -822,6 +851,9 @@ extern "C" int ctg_engine_submit(ctg_engine *e, const ctg_geom *g, int32_t varia
         return rc;
     }
     e->in_use += bytes;
+    s.plan.d.b = b_dev;
+    s.plan.d.x0 = x0_dev;
+    s.plan.d.x = x_dev;
     e->h_pinned[slot] = s.plan.d;
     B_CK(cudaMemcpyAsync(e->d_insts + slot, e->h_pinned + slot, sizeof(BatchInst), cudaMemcpyHostToDevice, e->st));
     B_CK(cudaStreamSynchronize(e->st));

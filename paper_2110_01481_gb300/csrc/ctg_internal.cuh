@@ -380,16 +380,18 @@ struct BatchInst {
     // buffers (the basis in FP32, BF16 or FP16; everything else FP32 / FP64)
     void *W;              // (maxit + 1) x ldw elements of type wtype
     long long ldw;
-    float *T;             // BA: (maxit + 1) x ldt, t_j = A w_j
-    long long ldt;
     double *H;            // (maxit + 1) x maxit, column-major, unrotated
     double *R;            // maxit x maxit, column-major: rotated H (upper triangle)
     double *gc, *gs, *gg; // Givens cosines, sines (maxit), rotated rhs (maxit + 1)
-    double *y;            // maxit: minus the least-squares solution (for r = r0 - T y)
+    double *y;            // maxit: the least-squares solution y_k (BA with the DP stop, and at exit)
     double *hist;         // maxit + 1: history as in ctg_info
-    float *vn, *vm;       // work vectors of length n and m
+    float *vn, *vm;       // work vectors of length n and m (BA: vm holds t_k = A w_k)
+    float *vr;            // BA with the DP stop: A x_k
     float2 *pad;          // staged image for the forward projector
-    float *r0m;           // BA: b - A x0
+    float4 *pad2;         // BA with the DP stop: staging of w_{k+1} and x_k, interleaved
+    const float *b;       // the solve's data b (m floats), start x0 (or NULL) and
+    const float *x0;      // iterate x (n floats; BA with the DP stop forms x_k
+    float *x;             // there every round)
     // reduction scratch of this instance (E = 1 passes, grid G)
     float *partials;
     double *h1, *h2, *scal;
@@ -402,16 +404,21 @@ struct BatchInst {
 };
 
 // Block maps: entry b of a batched launch's map is (instance, local block).
-enum { CTG_PH_BACK_AB = 0, CTG_PH_PAD = 1, CTG_PH_FWD = 2, CTG_PH_BACK_BA = 3 };
-// wtype: CTG_BASIS_FP32 launches the kernel for AB instances with an FP32
-// basis and all BA instances; BF16 / FP16 launch it for the AB instances
-// whose basis has that type.
-cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int phase,
-                           int max_window, cudaStream_t st, int wtype = CTG_BASIS_FP32);
-cudaError_t ctg_batch_pad(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st);
-// shape: 0, or kBatchFwdSplitShape when every instance of the round allows
-// it (ctg_forward_split_safe); the map's local blocks are that shape's.
-cudaError_t ctg_batch_forward(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st,
+// The back projection of a round: q = B w_k (AB) or q = B t_k (BA, t_k = A
+// w_k from the round before).  wtype: CTG_BASIS_FP32 launches the kernel
+// for AB instances with an FP32 basis and all BA instances; BF16 / FP16
+// launch it for the AB instances whose basis has that type.
+cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int max_window,
+                           cudaStream_t st, int wtype = CTG_BASIS_FP32);
+// Staging for the forward projector: AB stages t = B w_k (variant CTG_AB);
+// BA stages w_{k+1}, with x_k interleaved when it has the DP stop
+// (variant CTG_BA).
+cudaError_t ctg_batch_pad(BatchInst *insts, const int2 *map, int nblocks, int variant, cudaStream_t st);
+// The forward projection: AB q = A t; BA t_{k+1} = A w_{k+1} and, with the
+// DP stop, A x_k in the same walk.  shape: 0, or kBatchFwdSplitShape when
+// every instance of the launch allows it (ctg_forward_split_safe); the
+// map's local blocks are that shape's.
+cudaError_t ctg_batch_forward(BatchInst *insts, const int2 *map, int nblocks, int variant, cudaStream_t st,
                               int shape = 0);
 // Local block counts of one instance for the maps above.
 int ctg_back_tiles(int N);
@@ -425,8 +432,10 @@ cudaError_t ctg_batch_cgs2(BatchInst *insts, const int2 *map, int nblocks, int m
 // Set the batched kernels' shared-memory attributes (before graph capture).
 cudaError_t ctg_batch_prepare(int max_k);
 cudaError_t ctg_batch_givens(BatchInst *insts, int n_inst, cudaStream_t st);
-cudaError_t ctg_batch_residual(BatchInst *insts, const int2 *map_m, int nblocks, int max_k,
-                               cudaStream_t st);
+// BA with the DP stop: x_k = x0 + W_k y_k (map over n-blocks of those
+// instances), and ||b - A x_k||^2 (map over their m-blocks) into scal[4].
+cudaError_t ctg_batch_iterate(BatchInst *insts, const int2 *map_n, int nblocks, int max_k, cudaStream_t st);
+cudaError_t ctg_batch_residual(BatchInst *insts, const int2 *map_m, int nblocks, cudaStream_t st);
 cudaError_t ctg_batch_finish(BatchInst *insts, int n_inst, int *active_count, cudaStream_t st);
 // Exit: y = R^{-1} g for the instance's final k (stored with a + sign).
 cudaError_t ctg_batch_solve_y(BatchInst *insts, int n_inst, cudaStream_t st);

@@ -505,63 +505,76 @@ __device__ __forceinline__ void batch_back_tile(const BatchInst &I, const T *in,
 // each kernel holds the tile code of one input type only).
 template <typename T>
 __global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
-batch_back_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ map, int phase) {
+batch_back_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
     const int2 mp = map[blockIdx.x];
     const BatchInst &I = insts[mp.x];
     // the same decision in all CTAs of the cluster (they share blockIdx.x)
-    if (!I.active || ((phase == CTG_PH_BACK_AB) != (I.variant == CTG_AB))) return;
+    if (!I.active) return;
     constexpr int kType = std::is_same<T, __nv_bfloat16>::value ? CTG_BASIS_BF16
                           : std::is_same<T, __half>::value      ? CTG_BASIS_FP16
                                                                 : CTG_BASIS_FP32;
-    if (phase == CTG_PH_BACK_AB && I.wtype != kType) return;
+    if (I.variant == CTG_AB && I.wtype != kType) return;
+    if (I.variant == CTG_BA && kType != CTG_BASIS_FP32) return;
     const int tx = (I.N + kBT - 1) / kBT;
     const T *in;
     if constexpr (kType == CTG_BASIS_FP32)
-        in = phase == CTG_PH_BACK_AB ? static_cast<const float *>(I.W) + (size_t)(I.k - 1) * I.ldw
-                                     : I.T + (size_t)(I.k - 1) * I.ldt;
+        in = I.variant == CTG_AB ? static_cast<const float *>(I.W) + (size_t)(I.k - 1) * I.ldw : I.vm;
     else
         in = static_cast<const T *>(I.W) + (size_t)(I.k - 1) * I.ldw;
     batch_back_tile(I, in, mp.y % tx, mp.y / tx);
 }
 
+// AB: stage t = B w_k (in vn); BA: stage w_{k+1} (stored type), with x_k
+// interleaved for the DP stop.
+template <int kVariant>
 __global__ void batch_pad_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
     const int2 mp = map[blockIdx.x];
     const BatchInst &I = insts[mp.x];
     if (!I.active) return;
-    const int tx = (I.N + kPadTile - 1) / kPadTile;
-    // AB stages t = B w_k; BA stages w_k itself, in its stored type
-    const size_t off = (size_t)(I.k - 1) * I.ldw;
-    if (I.variant == CTG_AB)
-        pad_pairs_block<1, float>(I.vn, nullptr, I.pad, I.N, I.pad_stride, I.pad_border, mp.y % tx, mp.y / tx);
-    else if (I.wtype == CTG_BASIS_BF16)
-        pad_pairs_block<1, __nv_bfloat16>(static_cast<const __nv_bfloat16 *>(I.W) + off, nullptr, I.pad, I.N,
-                                          I.pad_stride, I.pad_border, mp.y % tx, mp.y / tx);
-    else if (I.wtype == CTG_BASIS_FP16)
-        pad_pairs_block<1, __half>(static_cast<const __half *>(I.W) + off, nullptr, I.pad, I.N, I.pad_stride,
-                                   I.pad_border, mp.y % tx, mp.y / tx);
-    else
-        pad_pairs_block<1, float>(static_cast<const float *>(I.W) + off, nullptr, I.pad, I.N, I.pad_stride,
-                                  I.pad_border, mp.y % tx, mp.y / tx);
+    const int tx = (I.N + kPadTile - 1) / kPadTile, bx = mp.y % tx, by = mp.y / tx;
+    if (kVariant == CTG_AB) {
+        pad_pairs_block<1, float>(I.vn, nullptr, I.pad, I.N, I.pad_stride, I.pad_border, bx, by);
+        return;
+    }
+    const size_t off = (size_t)I.k * I.ldw;
+    const bool two = I.target > 0.0;
+    auto stage = [&](auto *w) {
+        if (two) pad_pairs_block<2>(w + off, I.x, I.pad2, I.N, I.pad_stride, I.pad_border, bx, by);
+        else pad_pairs_block<1>(w + off, nullptr, I.pad, I.N, I.pad_stride, I.pad_border, bx, by);
+    };
+    if (I.wtype == CTG_BASIS_BF16) stage(static_cast<const __nv_bfloat16 *>(I.W));
+    else if (I.wtype == CTG_BASIS_FP16) stage(static_cast<const __half *>(I.W));
+    else stage(static_cast<const float *>(I.W));
 }
 
-// kAngles, kSplit: the forward shape of the round (one for all instances).
-template <int kAngles, int kSplit>
+// kAngles, kSplit: the forward shape of the launch (one for all instances).
+// AB: q = A t (into vm); BA: t_{k+1} = A w_{k+1} (into vm) and, with the DP
+// stop, A x_k (into vr) from the two-image staging.
+template <int kVariant, int kAngles, int kSplit>
 __global__ void __launch_bounds__(32 * kAngles / kSplit)
 batch_forward_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
     const int2 mp = map[blockIdx.x];
     const BatchInst &I = insts[mp.x];
     if (!I.active) return;
     const int bxn = (I.n_det + 32 / kSplit - 1) / (32 / kSplit);
-    // AB: q = A t; BA: t_k = A w_k, kept in T
-    float *out = I.variant == CTG_AB ? I.vm : I.T + (size_t)(I.k - 1) * I.ldt;
+    const int bx = mp.y % bxn, by = mp.y / bxn;
+    if (kVariant == CTG_BA && I.target > 0.0) {
+        if (I.pad_clamp)
+            joseph_forward_block<true, kAngles, kSplit, kBatchFwdDepth, 2>(
+                I.pad2, I.N, I.pad_stride, I.pad_border, I.n_angles, I.n_det, I.fwd, I.vm, I.vr, bx, by);
+        else
+            joseph_forward_block<false, kAngles, kSplit, kBatchFwdDepth, 2>(
+                I.pad2, I.N, I.pad_stride, I.pad_border, I.n_angles, I.n_det, I.fwd, I.vm, I.vr, bx, by);
+        return;
+    }
     if (I.pad_clamp)
         joseph_forward_block<true, kAngles, kSplit, kBatchFwdDepth>(I.pad, I.N, I.pad_stride, I.pad_border,
-                                                                    I.n_angles, I.n_det, I.fwd, out, nullptr,
-                                                                    mp.y % bxn, mp.y / bxn);
+                                                                    I.n_angles, I.n_det, I.fwd, I.vm, nullptr,
+                                                                    bx, by);
     else
         joseph_forward_block<false, kAngles, kSplit, kBatchFwdDepth>(I.pad, I.N, I.pad_stride, I.pad_border,
-                                                                     I.n_angles, I.n_det, I.fwd, out, nullptr,
-                                                                     mp.y % bxn, mp.y / bxn);
+                                                                     I.n_angles, I.n_det, I.fwd, I.vm, nullptr,
+                                                                     bx, by);
 }
 
 }  // namespace
@@ -582,34 +595,43 @@ int ctg_fwd_blocks(int n_angles, int n_det) {
 // largest window the tiled back projector can stage in shared memory
 int ctg_back_window_max() { return (40 * 1024) / (int)(sizeof(float2) * kBChunk); }
 
-cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int phase,
-                           int max_window, cudaStream_t st, int wtype) {
+cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int max_window,
+                           cudaStream_t st, int wtype) {
     if (nblocks <= 0) return cudaSuccess;
     const size_t smem = sizeof(float2) * (size_t)kBChunk * max_window;
     const dim3 grid(nblocks, 1, kBSplit);
     if (wtype == CTG_BASIS_BF16)
-        batch_back_kernel<__nv_bfloat16><<<grid, kBThreads, smem, st>>>(insts, map, phase);
+        batch_back_kernel<__nv_bfloat16><<<grid, kBThreads, smem, st>>>(insts, map);
     else if (wtype == CTG_BASIS_FP16)
-        batch_back_kernel<__half><<<grid, kBThreads, smem, st>>>(insts, map, phase);
+        batch_back_kernel<__half><<<grid, kBThreads, smem, st>>>(insts, map);
     else
-        batch_back_kernel<float><<<grid, kBThreads, smem, st>>>(insts, map, phase);
+        batch_back_kernel<float><<<grid, kBThreads, smem, st>>>(insts, map);
     return cudaGetLastError();
 }
 
-cudaError_t ctg_batch_pad(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st) {
+cudaError_t ctg_batch_pad(BatchInst *insts, const int2 *map, int nblocks, int variant, cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
-    batch_pad_kernel<<<nblocks, dim3(kPadTile, kPadRows), 0, st>>>(insts, map);
+    if (variant == CTG_AB) batch_pad_kernel<CTG_AB><<<nblocks, dim3(kPadTile, kPadRows), 0, st>>>(insts, map);
+    else batch_pad_kernel<CTG_BA><<<nblocks, dim3(kPadTile, kPadRows), 0, st>>>(insts, map);
     return cudaGetLastError();
 }
 
-cudaError_t ctg_batch_forward(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st, int shape) {
-    if (nblocks <= 0) return cudaSuccess;
+namespace {
+template <int kVariant>
+void batch_forward_t(BatchInst *insts, const int2 *map, int nblocks, cudaStream_t st, int shape) {
+    constexpr int SA = kFwdShapeAngles[kBatchFwdSplitShape], SS = kFwdShapeSplit[kBatchFwdSplitShape];
     if (shape == kBatchFwdSplitShape)
-        batch_forward_kernel<kFwdShapeAngles[kBatchFwdSplitShape], kFwdShapeSplit[kBatchFwdSplitShape]>
-            <<<nblocks, 32 * kFwdShapeAngles[kBatchFwdSplitShape] / kFwdShapeSplit[kBatchFwdSplitShape], 0, st>>>(
-                insts, map);
+        batch_forward_kernel<kVariant, SA, SS><<<nblocks, 32 * SA / SS, 0, st>>>(insts, map);
     else
-        batch_forward_kernel<kFwdAngles, 1><<<nblocks, 32 * kFwdAngles, 0, st>>>(insts, map);
+        batch_forward_kernel<kVariant, kFwdAngles, 1><<<nblocks, 32 * kFwdAngles, 0, st>>>(insts, map);
+}
+}  // namespace
+
+cudaError_t ctg_batch_forward(BatchInst *insts, const int2 *map, int nblocks, int variant, cudaStream_t st,
+                              int shape) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (variant == CTG_AB) batch_forward_t<CTG_AB>(insts, map, nblocks, st, shape);
+    else batch_forward_t<CTG_BA>(insts, map, nblocks, st, shape);
     return cudaGetLastError();
 }
 

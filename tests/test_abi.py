@@ -50,9 +50,9 @@ def _g(N, Na, Nd, S=0.0, R=180.0, ds=1.0, model=0, tau=0.0):
     return nat.CtgGeom(N, Na, Nd, model, S, R, ds, tau)
 
 
-def _o(maxit):
+def _o(maxit, basis=0):
     from paper_2110_01481_gb300 import _native as nat
-    return nat.CtgOpts(maxit, 0, 1.0, 0.0)
+    return nat.CtgOpts(maxit, basis, 1.0, 0.0)
 
 
 def test_invalid_arguments_are_rejected_on_the_host(lib):
@@ -115,11 +115,11 @@ def test_workspace_follows_the_krylov_storage_law(lib):
         assert total == ly.total_bytes
         n, m = N * N, Na * Nd
         other = total - basis_bytes
-        # BA also keeps T = A W_k (the forward projections of the basis
-        # vectors, reused by the discrepancy-principle residual)
-        t_bytes = 4 * (k + 2) * ((m + 63) // 64 * 64) if meth == "BA" else 0
-        staged = 4 * 4 * N * (N + 2 * 51)
-        assert 0 < other <= t_bytes + staged + 4 * 2 * (n + 2 * m) + 8 * (k + 1) * (k + 2) \
+        # beyond the basis: the staged image (BA also a two-image staging),
+        # one n-vector and two m-vectors, O(k^2) doubles of Hessenberg and
+        # Givens state, and the reduction scratch; no A W_k
+        staged = 4 * 4 * N * (N + 2 * 51) * (3 if meth == "BA" else 1)
+        assert 0 < other <= staged + 4 * 2 * (n + 2 * m) + 8 * (2 * k + 8) * (k + 2) \
             + 4 * (k + 4) * 1300 + 16384
 
 
@@ -149,7 +149,11 @@ def test_engine_admission_bytes_on_the_host(lib):
     rb = lambda g, v, o: lib.ctg_engine_request_bytes(ctypes.byref(g), v, ctypes.byref(o))
     ab, ba = rb(g, nat.CTG_AB, o), rb(g, nat.CTG_BA, o)
     assert 4 * 41 * 180 * 182 <= ab < 4 * 41 * 180 * 182 + (4 << 20)
-    assert 4 * 41 * (128 * 128 + 180 * 182) <= ba          # W (n) and T = A W (m)
+    # BA: the basis (n) and O(n + m) vectors, no A W: the storage law k n
+    assert 4 * 41 * 128 * 128 <= ba < 4 * 41 * 128 * 128 + (4 << 20)
+    o_dp = _o(40)
+    o_dp.noise_norm = 1.0                                 # DP: A x_k and the two-image staging too
+    assert ba <= rb(g, nat.CTG_BA, o_dp) < 4 * 41 * 128 * 128 + (4 << 20)
     # A^T and B_tau batch when two detector bins per pixel suffice (pitch >= 1)
     assert rb(_g(128, 180, 182, model=1), nat.CTG_AB, o) >= ab
     assert rb(_g(128, 180, 182, model=2, tau=0.3), nat.CTG_BA, o) >= ba
@@ -164,3 +168,22 @@ def test_engine_admission_bytes_on_the_host(lib):
     o.basis_dtype = nat.CTG_BASIS_FP32
     o.maxit = 1025
     assert rb(g, nat.CTG_AB, o) == 0
+
+
+def test_gmres_workspace_is_the_basis_at_the_benchmark_size(lib):
+    """512^2, 720 angles, 725 bins, maxit 150 (the benchmark workload): the
+    Krylov basis, (maxit + 1) vectors of length L, is the storage of both
+    methods (Table 3's k L), so BA (L = n) needs about half of AB (L = m)
+    and a 16-bit basis about half of an FP32 one."""
+    from paper_2110_01481_gb300 import _native as nat
+    g = _g(512, 720, 725)
+    n, m, k = 512 * 512, 720 * 725, 150
+    ws = lambda v, basis: lib.ctg_workspace_bytes(ctypes.byref(g), v, ctypes.byref(_o(k, basis)))
+    for v, L in ((nat.CTG_AB, m), (nat.CTG_BA, n)):
+        basis = 4 * (k + 1) * ((L + 63) // 64 * 64)
+        assert basis <= ws(v, 0) <= 1.15 * basis
+    assert ws(nat.CTG_BA, 0) < 200e6
+    assert ws(nat.CTG_BA, 0) < 0.6 * ws(nat.CTG_AB, 0)
+    for v in (nat.CTG_AB, nat.CTG_BA):
+        assert ws(v, nat.CTG_BASIS_BF16) < 0.6 * ws(v, 0)
+        assert ws(v, nat.CTG_BASIS_FP16) == ws(v, nat.CTG_BASIS_BF16)
