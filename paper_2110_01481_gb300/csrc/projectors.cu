@@ -368,9 +368,12 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
             }
         }
         __syncthreads();
-        const float2 *pw = s_pairs;
+        // shared address of an angle's window less the magic number's bits
+        // times 8, so that row r's pair is at sb + 8 t_r (32-bit wrap-around)
+        // with t_r the bits of u_r + M: one shift-add per pair address
+        unsigned sb = (unsigned)__cvta_generic_to_shared(s_pairs) - (0x4B400000u << 3);
 #pragma unroll 2
-        for (int k = 0; k < na; ++k, pw += W) {
+        for (int k = 0; k < na; ++k, sb += 8u * (unsigned)W) {
             const float4 p = s_par[k];
             const float du = 8.0f * p.y;
             float u[kBRows];
@@ -384,9 +387,9 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
             if constexpr (kModel != 0) wt = s_wt[k];
 #pragma unroll
             for (int r = 0; r < kBRows; ++r) {
-                const int idx = __float_as_int(tt[r]) - 0x4B400000;
                 const float f = ff[r];
-                const float2 pr = pw[idx];
+                const float2 pr =
+                    *static_cast<const float2 *>(__cvta_shared_to_generic(sb + (__float_as_uint(tt[r]) << 3)));
                 if constexpr (kModel == 0) {
                     acc[r] += fmaf(f, pr.y, pr.x);
                 } else {
