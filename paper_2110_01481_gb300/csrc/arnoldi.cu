@@ -956,9 +956,17 @@ cudaError_t cgs2_step_t(const T *W, int64_t ldw, int64_t L, int k, float *q, T *
     if ((err = cudaMemcpyAsync(rs.scal, rs.h1 + k, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return err;
     if (k > 0) {
-        // pass 2: q -= W h1; h2 = W^T q, ||q||^2 (h2[k])
-        if ((err = launch_pass<T, true, true, true>(W, ldw, k, nullptr, q, L, rs.h1, rs, rs.h2, st)) != cudaSuccess)
-            return err;
+        // pass 2: q -= W h1; h2 = W^T q, ||q||^2 (h2[k]), with one read of an
+        // FP32 basis where it fits the staged kernel, else two
+        if constexpr (std::is_same<T, float>::value) {
+            if (ctg_cgs_staged_ok(L, k))
+                err = ctg_cgs_pass2_staged(W, ldw, k, nullptr, q, L, rs, spin_limit, st);
+            else
+                err = launch_pass<T, true, true, true>(W, ldw, k, nullptr, q, L, rs.h1, rs, rs.h2, st);
+        } else {
+            err = launch_pass<T, true, true, true>(W, ldw, k, nullptr, q, L, rs.h1, rs, rs.h2, st);
+        }
+        if (err != cudaSuccess) return err;
         // q -= W h2 and w_out = q / ||q|| in one sweep; ||q||^2 -> scal[1]
         return launch_update_scale<T>(W, ldw, k, nullptr, nullptr, 0, q, L, rs, w_out, h_out, st);
     }
@@ -986,8 +994,15 @@ cudaError_t cgs2_loop_t(const T *W, int64_t ldw, int64_t L, float *q, const Loop
     if (nkern) *nkern = 3;
     if ((err = launch_pass<T, false, true, true>(W, ldw, ls.kmax, ls.k, q, L, nullptr, rs, rs.h1, st)) != cudaSuccess)
         return err;
-    if ((err = launch_pass<T, true, true, true>(W, ldw, ls.kmax, ls.k, q, L, rs.h1, rs, rs.h2, st)) != cudaSuccess)
-        return err;
+    bool staged = false;
+    if constexpr (std::is_same<T, float>::value) staged = ctg_cgs_staged_ok(L, ls.kmax);
+    if (staged) {
+        if constexpr (std::is_same<T, float>::value)
+            err = ctg_cgs_pass2_staged(W, ldw, ls.kmax, ls.k, q, L, rs, spin_limit, st);
+    } else {
+        err = launch_pass<T, true, true, true>(W, ldw, ls.kmax, ls.k, q, L, rs.h1, rs, rs.h2, st);
+    }
+    if (err != cudaSuccess) return err;
     return launch_update_scale<T>(W, ldw, ls.kmax, ls.k, ls.H, ls.ldh, q, L, rs, nullptr, nullptr, st);
 }
 

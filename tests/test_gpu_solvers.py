@@ -206,7 +206,10 @@ def test_workspace_modes_and_determinism(P, oracle_mod, variant):
 
 
 @pytest.mark.parametrize("L,k", [(1, 0), (3, 1), (1000, 7), (4099, 33), (522000, 64),
-                                 (262144 + 3, 150)])
+                                 (262144 + 3, 150),
+                                 # the middle pass staged through shared memory (FP32, L % 4 == 0,
+                                 # 64 < k <= 200), with a partial last slice of 104 elements
+                                 (1000, 80), (522000, 100), (262144, 150), (524288, 200)])
 def test_cgs2_entry_point(P, oracle_mod, L, k):
     """One CGS2 step against the oracle's FP64 classical Gram-Schmidt applied
     twice: h within 1e-5 of ||q||, w_out = q / ||q|| within 1e-5."""
