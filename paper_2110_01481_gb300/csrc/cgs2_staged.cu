@@ -86,16 +86,16 @@ cgs_pass2_staged_kernel(const float *__restrict__ W, int64_t ldw, int k, const i
                         float *__restrict__ q, int64_t L, const double *__restrict__ h1,
                         float *__restrict__ partials, int Gp, unsigned *__restrict__ counter,
                         double *__restrict__ red_out, int *__restrict__ err, long long spin_limit) {
-    extern __shared__ __align__(128) float s_w[];     // 2 buffers of k x kSlice, then k coefficients,
-                                                       // kSlice q values and k + 1 sums
+    extern __shared__ __align__(128) float s_w[];     // 2 buffers of k x kSlice, then kSlice q values
+                                                       // (16-byte aligned), k coefficients, k + 1 sums
     __shared__ __align__(8) unsigned long long s_bar[2];
     __shared__ bool s_last, s_fail;
     if (kdev) k = *kdev;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *buf0 = s_w, *buf1 = s_w + (size_t)k * kSlice;
-    float *s_c = buf1 + (size_t)k * kSlice;           // h1 as FP32
-    float *s_q = s_c + k;                             // the slice's updated q
-    float *s_acc = s_q + kSlice;                      // per-block sums: h2[0..k-1], ||q1||^2
+    float *s_q = buf1 + (size_t)k * kSlice;           // the slice's updated q
+    float *s_c = s_q + kSlice;                        // h1 as FP32
+    float *s_acc = s_c + k;                           // per-block sums: h2[0..k-1], ||q1||^2
     const unsigned bar0 = smem_addr(&s_bar[0]), bar1 = smem_addr(&s_bar[1]);
     const int64_t nslices = (L + kSlice - 1) / kSlice;
     if (tid == 0) {
@@ -124,31 +124,46 @@ cgs_pass2_staged_kernel(const float *__restrict__ W, int64_t ldw, int k, const i
         __syncthreads();
         if (s_fail) break;
         const int64_t i = s * kSlice + tid;
+        const int64_t rem = L - s * kSlice;               // valid elements of this slice
         const bool valid = i < L;
-        // q1 = q - W h1 for this thread's element
+        // q1 = q - W h1 for this thread's element (column tid of the slice's
+        // k x 128 buffer: consecutive threads, consecutive banks)
         float qi = valid ? q[i] : 0.0f;
         if (valid) {
-#pragma unroll 8
-            for (int j = 0; j < k; ++j) qi = fmaf(-s_c[j], buf[(size_t)j * kSlice + tid], qi);
+            float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            int j = 0;
+            for (; j + 3 < k; j += 4) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) a[e] = fmaf(s_c[j + e], buf[(size_t)(j + e) * kSlice + tid], a[e]);
+            }
+            for (; j < k; ++j) a[0] = fmaf(s_c[j], buf[(size_t)j * kSlice + tid], a[0]);
+            qi -= (a[0] + a[1]) + (a[2] + a[3]);
             q[i] = qi;
         }
-        s_q[tid] = qi;
-        const float nn = warp_sum(qi * qi);
+        s_q[tid] = qi;                                    // 0 past L
         __syncthreads();
-        // h2_j += W_j^T q1 over the slice: warp w takes j = w, w + 4, ...
-        for (int j = warp; j < k; j += kSWarps) {
-            const float *col = buf + (size_t)j * kSlice;
-            float d = 0.0f;
-#pragma unroll
-            for (int e = 0; e < kSlice / 32; ++e) {
-                const int c = lane + 32 * e;
-                const bool ok = s * kSlice + c < L;
-                d = fmaf(ok ? col[c] : 0.0f, s_q[c], d);
+        // h2_j += W_j^T q1 over the slice: thread j (< k) takes row j of the
+        // buffer, in float4 groups starting at group (lane) and wrapping, so
+        // that a warp's reads fall in distinct banks; groups past L are zero
+        // in q1 and skipped
+        for (int j = tid; j < k; j += kSlice) {
+            const float4 *row = reinterpret_cast<const float4 *>(buf + (size_t)j * kSlice);
+            const float4 *qq = reinterpret_cast<const float4 *>(s_q);
+            float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 8
+            for (int g = 0; g < kSlice / 4; ++g) {
+                const int c4 = (g + lane) & (kSlice / 4 - 1);
+                if (4 * c4 >= rem) continue;
+                const float4 w = row[c4], v = qq[c4];
+                d[0] = fmaf(w.x, v.x, d[0]);
+                d[1] = fmaf(w.y, v.y, d[1]);
+                d[2] = fmaf(w.z, v.z, d[2]);
+                d[3] = fmaf(w.w, v.w, d[3]);
             }
-            d = warp_sum(d);
-            if (lane == 0) s_acc[j] += d;
+            s_acc[j] += (d[0] + d[1]) + (d[2] + d[3]);
         }
         // ||q1||^2: the warps' sums added in warp order by thread 0
+        const float nn = warp_sum(qi * qi);
         __shared__ float s_nn[kSWarps];
         if (lane == 0) s_nn[warp] = nn;
         __syncthreads();
