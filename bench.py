@@ -299,6 +299,46 @@ def run_precision(args):
                 print(json.dumps(rows[-1]), flush=True)
             del ws
             torch.cuda.empty_cache()
+    if args.precision_oracle_k > 0:
+        precision_vs_oracle(P, torch, dev, g, args.precision_oracle_k)
+
+
+def precision_vs_oracle(P, torch, dev, g, kmax):
+    """Error of the GPU iterates against the FP64 oracle's on the 2048^2,
+    1800-angle workload: b = A x_bar + 1% noise with the oracle's FP64 A
+    (seed 4000), then for each method the oracle's iterates x_1 .. x_kmax
+    (matrix-free C projectors, MGS Arnoldi, FP64) and the GPU's x_k with the
+    basis stored in FP32, FP16 and BF16; per k, ||x_k - x_k^orc|| / ||x_k^orc||
+    and ||x_k - x_bar|| / ||x_bar||."""
+    import oracle as O
+    O.build_library()
+    og = O.Geometry(g.N, g.n_angles, g.n_det)
+    xbar = I.random_ellipses(g.N, 4000).ravel()
+    b64, enorm = I.add_noise(O.forward(og, xbar), ETA, 4000)
+    b64 = b64.astype(np.float32).astype(np.float64)
+    b = torch.tensor(b64, dtype=torch.float32, device=dev)
+    A = lambda v: O.forward(og, v)
+    B = lambda v: O.backproject(og, v)
+    ks = sorted({k for k in (1, 2, 3, 5, 8, 10, 15, 20, 25, 30, 40, 50) if k <= kmax} | {kmax})
+    xn = np.linalg.norm(xbar)
+    for variant in ("ba", "ab"):
+        t0 = time.perf_counter()
+        ref = (O.ba_gmres if variant == "ba" else O.ab_gmres)(A, B, b64, kmax, keep_iterates=True)
+        t_orc = time.perf_counter() - t0
+        fn = P.ba_gmres if variant == "ba" else P.ab_gmres
+        for basis in ("fp32", "fp16", "bf16"):
+            row = {"variant": variant, "basis": basis, "oracle_s": t_orc, "k": [], "rel_err_vs_oracle": [],
+                   "rel_err_vs_truth": [], "oracle_rel_err_vs_truth": []}
+            for k in ks:
+                r = fn(g, b, k, basis=basis)
+                torch.cuda.synchronize()
+                x = r.x.double().cpu().numpy()
+                xo = ref["iterates"][k]
+                row["k"].append(k)
+                row["rel_err_vs_oracle"].append(float(np.linalg.norm(x - xo) / np.linalg.norm(xo)))
+                row["rel_err_vs_truth"].append(float(np.linalg.norm(x - xbar) / xn))
+                row["oracle_rel_err_vs_truth"].append(float(np.linalg.norm(xo - xbar) / xn))
+            print(json.dumps({"precision_vs_fp64_oracle": row}), flush=True)
 
 
 def batch_problems(P, torch, dev, count, seed0=3000):
@@ -491,8 +531,11 @@ def serving_summary(P, torch, dev, count):
     latency and throughput of the continuous-batching engine beside the
     one-at-a-time server (the full sweep is --serve)."""
     reqs = serve_requests(P, torch, dev, count)
-    for r in reqs:
-        r.pop("xbar")
+    xbars = [r.pop("xbar") for r in reqs]
+
+    def err(outs):
+        return float(np.mean([((o - x).norm() / x.norm()).item() for o, x in zip(outs, xbars)]))
+
     serve_fifo(P, torch, reqs[:8], [0.0] * 8)
     serve_engine(P, torch, reqs[:8], [0.0] * 8, 64, 96 << 30, 4)
     _, _, _, span = serve_fifo(P, torch, reqs, [0.0] * len(reqs))
@@ -503,9 +546,10 @@ def serving_summary(P, torch, dev, count):
            "one_at_a_time_capacity_req_per_s": capacity}
     for name, fn in (("engine", lambda a: serve_engine(P, torch, reqs, a, 64, 96 << 30, 4)),
                      ("one_at_a_time", lambda a: serve_fifo(P, torch, reqs, a))):
-        done, iters, _, span = fn(arrive)
+        done, iters, outs, span = fn(arrive)
+        # both servers reach the same reconstruction error (the same solves)
         out[name] = dict(_latency_stats(arrive, done), served_req_per_s=len(reqs) / span,
-                         iterations_per_s=iters / span)
+                         iterations_per_s=iters / span, mean_rel_error_vs_truth=err(outs))
     return out
 
 
@@ -950,6 +994,8 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="basis-storage study (FP32/FP16/BF16) on the 2048^2 workload")
     ap.add_argument("--precision-k", default="25,50,100,200")
+    ap.add_argument("--precision-oracle-k", type=int, default=25,
+                    help="iterations of the FP64 oracle the 16-bit bases are compared with (0: none)")
     ap.add_argument("--batch", action="store_true",
                     help="batched engine vs one-at-a-time solves on 64 mixed instances")
     ap.add_argument("--batch-size", type=int, default=64)
