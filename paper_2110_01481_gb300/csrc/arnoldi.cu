@@ -471,39 +471,6 @@ gemv_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__restrict__
     for (int e = 0; e < E; ++e) st4(out, g0 + (int64_t)e * kThreads, L, acc[e]);
 }
 
-// res = ||base + sum_j y_j V_j||^2 (the vector itself is not stored).
-template <int E>
-__device__ __forceinline__ void gemv_norm2_body(const float *__restrict__ V, int64_t ldv, int k,
-                                                const double *__restrict__ y,
-                                                const float *__restrict__ base, int64_t L,
-                                                float *__restrict__ partials,
-                                                unsigned *__restrict__ counter,
-                                                double *__restrict__ res, int blk, int G) {
-    extern __shared__ float s_y[];
-    __shared__ float s_w[kWarps];
-    for (int j = threadIdx.x; j < k; j += kThreads) s_y[j] = (float)y[j];
-    __syncthreads();
-    const int64_t g0 = (int64_t)blk * kThreads * E + threadIdx.x;
-    float4 acc[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) acc[e] = ld4(base, g0 + (int64_t)e * kThreads, L);
-    accumulate_batched<float, E>(V, ldv, k, s_y, g0, L, acc);
-    float s = 0.f;
-#pragma unroll
-    for (int e = 0; e < E; ++e) s += dot4(acc[e], acc[e]);
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
-    block_reduce_finish(s_w, 1, partials, counter, res, blk, G);
-}
-
-template <int E>
-__global__ void __launch_bounds__(kThreads, 2)
-gemv_norm2_kernel(const float *__restrict__ V, int64_t ldv, int k, const double *__restrict__ y,
-                  const float *__restrict__ base, int64_t L, float *__restrict__ partials,
-                  unsigned *__restrict__ counter, double *__restrict__ res) {
-    gemv_norm2_body<E>(V, ldv, k, y, base, L, partials, counter, res, blockIdx.x, gridDim.x);
-}
-
 // out = a - c (or a), res = ||out||^2; out may be the same vector as a or c.
 template <int E>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -956,17 +923,9 @@ cudaError_t cgs2_step_t(const T *W, int64_t ldw, int64_t L, int k, float *q, T *
     if ((err = cudaMemcpyAsync(rs.scal, rs.h1 + k, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return err;
     if (k > 0) {
-        // pass 2: q -= W h1; h2 = W^T q, ||q||^2 (h2[k]), with one read of an
-        // FP32 basis where it fits the staged kernel, else two
-        if constexpr (std::is_same<T, float>::value) {
-            if (ctg_cgs_staged_ok(L, k))
-                err = ctg_cgs_pass2_staged(W, ldw, k, nullptr, q, L, rs, spin_limit, st);
-            else
-                err = launch_pass<T, true, true, true>(W, ldw, k, nullptr, q, L, rs.h1, rs, rs.h2, st);
-        } else {
-            err = launch_pass<T, true, true, true>(W, ldw, k, nullptr, q, L, rs.h1, rs, rs.h2, st);
-        }
-        if (err != cudaSuccess) return err;
+        // pass 2: q -= W h1; h2 = W^T q, ||q||^2 (h2[k])
+        if ((err = launch_pass<T, true, true, true>(W, ldw, k, nullptr, q, L, rs.h1, rs, rs.h2, st)) != cudaSuccess)
+            return err;
         // q -= W h2 and w_out = q / ||q|| in one sweep; ||q||^2 -> scal[1]
         return launch_update_scale<T>(W, ldw, k, nullptr, nullptr, 0, q, L, rs, w_out, h_out, st);
     }
@@ -994,15 +953,8 @@ cudaError_t cgs2_loop_t(const T *W, int64_t ldw, int64_t L, float *q, const Loop
     if (nkern) *nkern = 3;
     if ((err = launch_pass<T, false, true, true>(W, ldw, ls.kmax, ls.k, q, L, nullptr, rs, rs.h1, st)) != cudaSuccess)
         return err;
-    bool staged = false;
-    if constexpr (std::is_same<T, float>::value) staged = ctg_cgs_staged_ok(L, ls.kmax);
-    if (staged) {
-        if constexpr (std::is_same<T, float>::value)
-            err = ctg_cgs_pass2_staged(W, ldw, ls.kmax, ls.k, q, L, rs, spin_limit, st);
-    } else {
-        err = launch_pass<T, true, true, true>(W, ldw, ls.kmax, ls.k, q, L, rs.h1, rs, rs.h2, st);
-    }
-    if (err != cudaSuccess) return err;
+    if ((err = launch_pass<T, true, true, true>(W, ldw, ls.kmax, ls.k, q, L, rs.h1, rs, rs.h2, st)) != cudaSuccess)
+        return err;
     return launch_update_scale<T>(W, ldw, ls.kmax, ls.k, ls.H, ls.ldh, q, L, rs, nullptr, nullptr, st);
 }
 
@@ -1096,30 +1048,6 @@ cudaError_t ctg_gemv(const void *W, int dtype, int64_t ldw, int64_t L, int k, co
             return gemv_t(static_cast<const __half *>(W), ldw, L, k, kdev, koff, y, base, out, st);
         default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t ctg_gemv_norm2(const float *V, int64_t ldv, int64_t L, int k, const double *y,
-                           const float *base, double *res, const RedScratch &rs,
-                           cudaStream_t st) {
-    int E;
-    const int G = ctg_red_grid(L, &E);
-    const size_t smem = sizeof(float) * (size_t)(k > 0 ? k : 1);
-    cudaError_t err = cudaSuccess;
-    switch (E) {
-#define CTG_GN_CASE(EE)                                                                   \
-    case EE:                                                                              \
-        if ((err = ensure_smem(gemv_norm2_kernel<EE>, smem)) != cudaSuccess) return err;  \
-        gemv_norm2_kernel<EE><<<G, kThreads, smem, st>>>(V, ldv, k, y, base, L, rs.partials, \
-                                                         rs.counter, res);                \
-        break;
-        CTG_GN_CASE(1)
-        CTG_GN_CASE(2)
-        CTG_GN_CASE(4)
-        CTG_GN_CASE(8)
-#undef CTG_GN_CASE
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
 }
 
 cudaError_t ctg_sub_norm2(const float *a, const float *c, float *out, int64_t L,

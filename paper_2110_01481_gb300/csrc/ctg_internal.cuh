@@ -234,15 +234,6 @@ struct LoopStep {
 cudaError_t ctg_cgs2_step_loop(const void *W, int dtype, int64_t ldw, int64_t L, float *q, const LoopStep &ls,
                                const RedScratch &rs, long long spin_limit, bool cooperative, cudaStream_t st,
                                int *nkern = nullptr);
-// The middle CGS2 pass (q -= W h1; h2 = W^T q, ||q||^2 into rs.h2[0..k])
-// for an FP32 basis with one read of W, staged through shared memory by
-// bulk asynchronous copies (cgs2_staged.cu); k <= ctg_cgs_staged_max_k()
-// (k = *kdev when set, kmax bounding it).
-cudaError_t ctg_cgs_pass2_staged(const float *W, int64_t ldw, int kmax, const int *kdev, float *q, int64_t L,
-                                 const RedScratch &rs, long long spin_limit, cudaStream_t st);
-int ctg_cgs_staged_max_k();
-// Whether it serves length L (a multiple of 4) and k.
-bool ctg_cgs_staged_ok(int64_t L, int k);
 // Whether the fused step serves k <= kmax at length L with this scratch
 // (every block of its grid resident at once).
 bool ctg_cgs2_fused_ok(int dtype, int64_t L, int kmax, const RedScratch &rs);
@@ -253,10 +244,6 @@ int ctg_cgs2_fused_max();
 cudaError_t ctg_gemv(const void *W, int dtype, int64_t ldw, int64_t L, int k, const double *y,
                      const float *base, float *out, cudaStream_t st, const int *kdev = nullptr,
                      int koff = 0);
-// *res = ||base + sum_j y_j V_j||^2 (double, device); the vector is not stored.
-cudaError_t ctg_gemv_norm2(const float *V, int64_t ldv, int64_t L, int k, const double *y,
-                           const float *base, double *res, const RedScratch &rs,
-                           cudaStream_t st);
 // out = a - c (c may be NULL -> out = a) and *res = ||a - c||^2 (double, device).
 cudaError_t ctg_sub_norm2(const float *a, const float *c, float *out, int64_t L,
                           double *res, const RedScratch &rs, cudaStream_t st);
