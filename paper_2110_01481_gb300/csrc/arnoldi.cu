@@ -536,21 +536,34 @@ batch_update_scale_kernel(BatchInst *__restrict__ insts, const int2 *__restrict_
 // One warp per instance: FP64 Givens update of the Hessenberg least-squares
 // problem with the new column (rotations kept in gc/gs, rotated column in
 // R, rotated right-hand side gg), the breakdown test, and for BA with the
-// discrepancy stop, y_k = R^{-1} gg (stored negated for the residual).
-__global__ void batch_givens_kernel(BatchInst *__restrict__ insts) {
+// discrepancy stop, y_k = R^{-1} gg.  The column and the rotations are
+// staged in shared memory (all lanes load, lane 0 runs the recurrence), and
+// for y_k the packed triangle when it fits (dynamic shared memory of
+// pack_cap (pack_cap + 1) / 2 doubles).
+constexpr int kBatchGivStage = 1024;   // = the batches' largest maxit
+
+__global__ void batch_givens_kernel(BatchInst *__restrict__ insts, int pack_cap) {
+    extern __shared__ double s_pack[];
+    __shared__ double s_h[kBatchGivStage + 1], s_gc[kBatchGivStage], s_gs[kBatchGivStage];
     BatchInst &I = insts[blockIdx.x];
     if (!I.active) return;
     const int k = I.k, lane = threadIdx.x, ldr = I.maxit;
     const double *h = I.H + (size_t)(k - 1) * (I.maxit + 1);
     double *Rk = I.R + (size_t)(k - 1) * ldr;         // column k of R
+    for (int i = lane; i <= k; i += 32) s_h[i] = h[i];
+    for (int i = lane; i < k - 1; i += 32) {
+        s_gc[i] = I.gc[i];
+        s_gs[i] = I.gs[i];
+    }
+    __syncwarp();
     if (lane == 0) {
-        double r_prev = h[0];
+        double r_prev = s_h[0];
         for (int i = 0; i < k - 1; ++i) {
-            const double a = r_prev, b = h[i + 1];
-            Rk[i] = I.gc[i] * a + I.gs[i] * b;
-            r_prev = -I.gs[i] * a + I.gc[i] * b;
+            const double a = r_prev, b = s_h[i + 1];
+            s_h[i] = s_gc[i] * a + s_gs[i] * b;
+            r_prev = -s_gs[i] * a + s_gc[i] * b;
         }
-        const double a = r_prev, b = h[k];
+        const double a = r_prev, b = s_h[k];
         const double r = hypot(a, b);
         double c = 1.0, sn = 0.0;
         if (b != 0.0) {
@@ -559,27 +572,16 @@ __global__ void batch_givens_kernel(BatchInst *__restrict__ insts) {
         }
         I.gc[k - 1] = c;
         I.gs[k - 1] = sn;
-        Rk[k - 1] = b != 0.0 ? r : a;
+        s_h[k - 1] = b != 0.0 ? r : a;
         I.gg[k] = -sn * I.gg[k - 1];
         I.gg[k - 1] = c * I.gg[k - 1];
         I.rho = fabs(I.gg[k]);
-        I.breakdown = h[k] <= 1e-6 * sqrt(I.h1[k]);     // h1[k] = ||q before CGS2||^2
+        I.breakdown = b <= 1e-6 * sqrt(I.h1[k]);     // h1[k] = ||q before CGS2||^2
     }
     __syncwarp();
-    if (I.variant == CTG_BA && I.target > 0.0) {
-        // y_k = R^{-1} g by back substitution, one row at a time, the row
-        // sums shared by the warp
-        for (int i = k - 1; i >= 0; --i) {
-            double t = 0.0;
-            for (int j = i + 1 + lane; j < k; j += 32) t += I.R[(size_t)j * ldr + i] * I.y[j];
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) {
-                const double d = I.R[(size_t)i * ldr + i];
-                I.y[i] = d != 0.0 ? (I.gg[i] - t) / d : 0.0;
-            }
-            __syncwarp();
-        }
-    }
+    for (int i = lane; i < k; i += 32) Rk[i] = s_h[i];
+    __syncwarp();
+    if (I.variant == CTG_BA && I.target > 0.0) solve_y_warp(I.R, ldr, I.gg, k, I.y, s_pack, pack_cap);
 }
 
 // BA with the discrepancy stop: x_k = x0 + W_k y_k into the solve's x
@@ -646,20 +648,46 @@ __global__ void batch_finish_kernel(BatchInst *__restrict__ insts, int n, int *a
     }
 }
 
-// Exit: y = R^{-1} gg for each finished instance's k (one warp each).
-__global__ void batch_solve_y_kernel(BatchInst *__restrict__ insts) {
-    BatchInst &I = insts[blockIdx.x];
-    const int k = I.iters, lane = threadIdx.x, ldr = I.maxit;
-    for (int i = k - 1; i >= 0; --i) {
-        double t = 0.0;
-        for (int j = i + 1 + lane; j < k; j += 32) t += I.R[(size_t)j * ldr + i] * I.y[j];
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) {
-            const double d = I.R[(size_t)i * ldr + i];
-            I.y[i] = d != 0.0 ? (I.gg[i] - t) / d : 0.0;
+// The stopping rules of a round inside the batch's while-loop graph, in one
+// block (n <= 1024): as batch_finish_kernel, then thread 0 counts the round
+// (ctl[1]) and ends the loop once no instance is active (ctl[0]) or
+// max_rounds rounds have run (every instance stops by its maxit, so the
+// second condition only guards the first).
+__global__ void batch_finish_loop_kernel(BatchInst *__restrict__ insts, int n, int *ctl, int max_rounds,
+                                         cudaGraphConditionalHandle h) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        BatchInst &I = insts[i];
+        if (!I.active) continue;
+        const int k = I.k;
+        const bool dp = I.target > 0.0;
+        if (I.variant == CTG_BA && dp) I.resnorm = sqrt(I.scal[4]);
+        I.hist[k] = (I.variant == CTG_BA && dp) ? I.resnorm : I.rho;
+        int stop = -1;
+        if (I.breakdown) stop = CTG_STOP_BREAKDOWN;
+        else if (dp && (I.variant == CTG_AB ? I.rho : I.resnorm) <= I.target) stop = CTG_STOP_DP;
+        else if (k == I.maxit) stop = CTG_STOP_MAXIT;
+        if (stop >= 0) {
+            I.active = 0;
+            I.iters = k;
+            I.stop_reason = stop;
+            atomicSub(&ctl[0], 1);
+        } else {
+            I.k = k + 1;
         }
-        __syncwarp();
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int r = ++ctl[1];
+        if (atomicAdd(&ctl[0], 0) <= 0 || r >= max_rounds) cudaGraphSetConditional(h, 0u);
+    }
+}
+
+// Exit: y = R^{-1} gg for each finished instance's k (one warp each; the
+// packed triangle staged in shared memory when it fits).
+__global__ void batch_solve_y_kernel(BatchInst *__restrict__ insts, int pack_cap) {
+    extern __shared__ double s_pack[];
+    BatchInst &I = insts[blockIdx.x];
+    if (I.iters > 0) solve_y_warp(I.R, I.maxit, I.gg, I.iters, I.y, s_pack, pack_cap);
 }
 
 template <typename K>
@@ -1128,12 +1156,19 @@ cudaError_t ctg_batch_prepare(int max_k) {
     if ((err = prepare_batch_cgs2<float>(smem)) != cudaSuccess) return err;
     if ((err = prepare_batch_cgs2<__nv_bfloat16>(smem)) != cudaSuccess) return err;
     if ((err = prepare_batch_cgs2<__half>(smem)) != cudaSuccess) return err;
+    const int cap = max_k < 160 ? max_k : 160;
+    if ((err = ensure_smem(batch_givens_kernel, sizeof(double) * (size_t)cap * (cap + 1) / 2)) != cudaSuccess)
+        return err;
     return ensure_smem(batch_iterate_kernel, sizeof(float) * (size_t)(max_k > 0 ? max_k : 1));
 }
 
-cudaError_t ctg_batch_givens(BatchInst *insts, int n_inst, cudaStream_t st) {
+cudaError_t ctg_batch_givens(BatchInst *insts, int n_inst, int max_k, cudaStream_t st) {
     if (n_inst <= 0) return cudaSuccess;
-    batch_givens_kernel<<<n_inst, 32, 0, st>>>(insts);
+    const int cap = max_k < 160 ? max_k : 160;
+    const size_t smem = sizeof(double) * (size_t)cap * (cap + 1) / 2;
+    cudaError_t e = ensure_smem(batch_givens_kernel, smem);
+    if (e != cudaSuccess) return e;
+    batch_givens_kernel<<<n_inst, 32, smem, st>>>(insts, cap);
     return cudaGetLastError();
 }
 
@@ -1156,8 +1191,19 @@ cudaError_t ctg_batch_finish(BatchInst *insts, int n_inst, int *active_count, cu
     return cudaGetLastError();
 }
 
-cudaError_t ctg_batch_solve_y(BatchInst *insts, int n_inst, cudaStream_t st) {
+cudaError_t ctg_batch_finish_loop(BatchInst *insts, int n_inst, int *ctl, int max_rounds,
+                                  cudaGraphConditionalHandle h, cudaStream_t st) {
+    if (n_inst <= 0 || n_inst > 1024) return cudaErrorInvalidValue;
+    batch_finish_loop_kernel<<<1, n_inst < 128 ? 128 : 1024, 0, st>>>(insts, n_inst, ctl, max_rounds, h);
+    return cudaGetLastError();
+}
+
+cudaError_t ctg_batch_solve_y(BatchInst *insts, int n_inst, int max_k, cudaStream_t st) {
     if (n_inst <= 0) return cudaSuccess;
-    batch_solve_y_kernel<<<n_inst, 32, 0, st>>>(insts);
+    const int cap = max_k < 160 ? max_k : 160;
+    const size_t smem = sizeof(double) * (size_t)cap * (cap + 1) / 2;
+    cudaError_t e = ensure_smem(batch_solve_y_kernel, smem);
+    if (e != cudaSuccess) return e;
+    batch_solve_y_kernel<<<n_inst, 32, smem, st>>>(insts, cap);
     return cudaGetLastError();
 }

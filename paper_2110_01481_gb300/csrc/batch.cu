@@ -205,9 +205,10 @@ struct ctg_batch {
     int *d_active = nullptr;
     int *h_active = nullptr;     // pinned
     double *h_stage = nullptr;   // pinned: per instance scal[0..7]
-    cudaStream_t st = nullptr;
+    cudaStream_t st = nullptr, st_body = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t round = nullptr;
+    cudaGraphExec_t loop = nullptr;   // the whole iteration (while-loop graph), if it could be built
 };
 
 namespace {
@@ -216,6 +217,8 @@ void release(ctg_batch *b) {
     if (!b) return;
     if (b->st) cudaStreamSynchronize(b->st);
     if (b->round) cudaGraphExecDestroy(b->round);
+    if (b->loop) cudaGraphExecDestroy(b->loop);
+    if (b->st_body) cudaStreamDestroy(b->st_body);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->st) cudaStreamDestroy(b->st);
@@ -324,14 +327,11 @@ unsigned round_signature(const RoundSpec &r) {
     return sig | (unsigned)r.fwd_shape_ab << 16 | (unsigned)r.fwd_shape_ba << 20;
 }
 
-// Capture one round into *out.  If *out already holds an executable graph
-// captured with the same kernel sequence (sig_prev == this round's
-// signature), it is updated in place, which is much cheaper than
-// instantiating a new one; otherwise it is replaced.
-int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out, unsigned sig_prev = ~0u) {
-    cudaGraph_t graph = nullptr;
-    B_CK(ctg_batch_prepare(r.max_maxit));   // kernel attributes, set outside the capture
-    B_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+// Enqueue one round's launches on st (ending it with the stopping rules;
+// inside a while-loop body, loop_ctl and the loop's handle end the loop
+// when no solve is left).
+cudaError_t enqueue_round(const RoundSpec &r, cudaStream_t st, int *loop_ctl = nullptr,
+                          cudaGraphConditionalHandle h = 0) {
     cudaError_t e = cudaSuccess;
     const int2 *M = r.maps;
     auto map = [&](int w) { return M + r.off[w]; };
@@ -348,13 +348,28 @@ int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out, uns
         e = ctg_batch_cgs2(r.insts, map(MB_CGS_B16), r.len[MB_CGS_B16], r.max_maxit, st, CTG_BASIS_BF16);
     if (e == cudaSuccess)
         e = ctg_batch_cgs2(r.insts, map(MB_CGS_H16), r.len[MB_CGS_H16], r.max_maxit, st, CTG_BASIS_FP16);
-    if (e == cudaSuccess) e = ctg_batch_givens(r.insts, r.n_inst, st);
+    if (e == cudaSuccess) e = ctg_batch_givens(r.insts, r.n_inst, r.max_maxit, st);
     if (e == cudaSuccess) e = ctg_batch_iterate(r.insts, map(MB_ITER), r.len[MB_ITER], r.max_maxit, st);
     if (e == cudaSuccess) e = ctg_batch_pad(r.insts, map(MB_PAD_BA), r.len[MB_PAD_BA], CTG_BA, st);
     if (e == cudaSuccess)
         e = ctg_batch_forward(r.insts, map(MB_FWD_BA), r.len[MB_FWD_BA], CTG_BA, st, r.fwd_shape_ba);
     if (e == cudaSuccess) e = ctg_batch_residual(r.insts, map(MB_RES), r.len[MB_RES], st);
-    if (e == cudaSuccess) e = ctg_batch_finish(r.insts, r.n_inst, r.d_active, st);
+    if (e == cudaSuccess) {
+        if (loop_ctl) e = ctg_batch_finish_loop(r.insts, r.n_inst, loop_ctl, r.max_maxit, h, st);
+        else e = ctg_batch_finish(r.insts, r.n_inst, r.d_active, st);
+    }
+    return e;
+}
+
+// Capture one round into *out.  If *out already holds an executable graph
+// captured with the same kernel sequence (sig_prev == this round's
+// signature), it is updated in place, which is much cheaper than
+// instantiating a new one; otherwise it is replaced.
+int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out, unsigned sig_prev = ~0u) {
+    cudaGraph_t graph = nullptr;
+    B_CK(ctg_batch_prepare(r.max_maxit));   // kernel attributes, set outside the capture
+    B_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_round(r, st);
     cudaError_t e2 = cudaStreamEndCapture(st, &graph);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess && *out != nullptr) {
@@ -367,6 +382,53 @@ int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out, uns
     }
     if (e == cudaSuccess && *out == nullptr) e = cudaGraphInstantiate(out, graph, 0);
     if (graph) cudaGraphDestroy(graph);
+    return ck(e);
+}
+
+// Capture the whole iteration of a batch as one graph: a while-loop node
+// whose body is a round, ended on the device by the round's stopping-rule
+// kernel (loop_ctl: active solves, rounds run), so no host check runs
+// between rounds.  st captures, bs the body.
+int capture_loop(const RoundSpec &r, cudaStream_t st, cudaStream_t bs, int *loop_ctl, cudaGraphExec_t *out) {
+    if (r.n_inst > 1024) return CTG_ERR_INVALID_ARG;
+    B_CK(ctg_batch_prepare(r.max_maxit));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraphConditionalHandle h = 0;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 1u, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp);
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        e = cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            e = enqueue_round(r, bs, loop_ctl, h);
+            cudaGraph_t body = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(bs, &body);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    const cudaError_t e3 = cudaStreamEndCapture(st, &graph);
+    if (e == cudaSuccess) e = e3;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+    }
     return ck(e);
 }
 
@@ -421,10 +483,11 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
     if (rc == CTG_OK && !maps.empty())
         rc = ck(cudaMemcpy(b->d_maps, maps.data(), sizeof(int2) * maps.size(), cudaMemcpyHostToDevice));
     if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_insts, sizeof(BatchInst) * n));
-    if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_active, sizeof(int)));
+    if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_active, 2 * sizeof(int)));   // active solves, rounds run
     if (rc == CTG_OK) rc = ck(cudaMallocHost(&b->h_active, sizeof(int)));
     if (rc == CTG_OK) rc = ck(cudaMallocHost(&b->h_stage, sizeof(double) * 8 * n));
     if (rc == CTG_OK) rc = ck(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
+    if (rc == CTG_OK) rc = ck(cudaStreamCreateWithFlags(&b->st_body, cudaStreamNonBlocking));
     if (rc == CTG_OK) rc = ck(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
     if (rc == CTG_OK) rc = ck(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
     for (int i = 0; rc == CTG_OK && i < n; ++i) {
@@ -441,6 +504,9 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
         r.max_maxit = b->max_maxit;
         r.d_active = b->d_active;
         rc = capture_round(r, b->st, &b->round);
+        // the whole iteration as one graph; without it the host replays the
+        // round graph and checks the active count every few rounds
+        if (rc == CTG_OK && capture_loop(r, b->st, b->st_body, b->d_active, &b->loop) != CTG_OK) b->loop = nullptr;
     }
     if (rc != CTG_OK) {
         release(b);
@@ -593,7 +659,12 @@ extern "C" int ctg_batch_solve(ctg_batch *b, const float *const *b_dev, const fl
     B_CK(cudaMemcpyAsync(b->d_insts, hi.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, st));
     *b->h_active = active;
     B_CK(cudaMemcpyAsync(b->d_active, b->h_active, sizeof(int), cudaMemcpyHostToDevice, st));
+    B_CK(cudaMemsetAsync(b->d_active + 1, 0, sizeof(int), st));
     // ---- rounds -----------------------------------------------------------
+    if (active > 0 && b->loop) {
+        B_CK(cudaGraphLaunch(b->loop, st));
+        active = 0;
+    }
     int rounds = 0;
     while (active > 0 && rounds < b->max_maxit) {
         const int r = std::min(kRoundsPerCheck, b->max_maxit - rounds);
@@ -604,7 +675,7 @@ extern "C" int ctg_batch_solve(ctg_batch *b, const float *const *b_dev, const fl
         active = *b->h_active;
     }
     // ---- exit: y_k, x_k and its residual -----------------------------------
-    B_CK(ctg_batch_solve_y(b->d_insts, n, st));
+    B_CK(ctg_batch_solve_y(b->d_insts, n, b->max_maxit, st));
     B_CK(cudaMemcpyAsync(hi.data(), b->d_insts, sizeof(BatchInst) * n, cudaMemcpyDeviceToHost, st));
     B_CK(cudaStreamSynchronize(st));
     for (int i = 0; i < n; ++i) {
@@ -881,7 +952,7 @@ extern "C" int ctg_engine_step(ctg_engine *e, int32_t rounds, int32_t max_done, 
         *e->h_active = e->running;
         B_CK(cudaMemcpyAsync(e->d_active, e->h_active, sizeof(int), cudaMemcpyHostToDevice, st));
         for (int j = 0; j < rounds; ++j) B_CK(cudaGraphLaunch(e->round, st));
-        B_CK(ctg_batch_solve_y(e->d_insts, e->max_slots, st));   // y of solves that just finished
+        B_CK(ctg_batch_solve_y(e->d_insts, e->max_slots, 1024, st));   // y of solves that just finished
         B_CK(cudaMemcpyAsync(e->h_pinned, e->d_insts, sizeof(BatchInst) * e->max_slots,
                              cudaMemcpyDeviceToHost, st));
         B_CK(cudaMemcpyAsync(e->h_active, e->d_active, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -427,14 +427,19 @@ cudaError_t ctg_batch_cgs2(BatchInst *insts, const int2 *map, int nblocks, int m
                            cudaStream_t st, int wtype = CTG_BASIS_FP32);
 // Set the batched kernels' shared-memory attributes (before graph capture).
 cudaError_t ctg_batch_prepare(int max_k);
-cudaError_t ctg_batch_givens(BatchInst *insts, int n_inst, cudaStream_t st);
+cudaError_t ctg_batch_givens(BatchInst *insts, int n_inst, int max_k, cudaStream_t st);
 // BA with the DP stop: x_k = x0 + W_k y_k (map over n-blocks of those
 // instances), and ||b - A x_k||^2 (map over their m-blocks) into scal[4].
 cudaError_t ctg_batch_iterate(BatchInst *insts, const int2 *map_n, int nblocks, int max_k, cudaStream_t st);
 cudaError_t ctg_batch_residual(BatchInst *insts, const int2 *map_m, int nblocks, cudaStream_t st);
 cudaError_t ctg_batch_finish(BatchInst *insts, int n_inst, int *active_count, cudaStream_t st);
-// Exit: y = R^{-1} g for the instance's final k (stored with a + sign).
-cudaError_t ctg_batch_solve_y(BatchInst *insts, int n_inst, cudaStream_t st);
+// The stopping rules of a round of a batch's while-loop graph (n_inst <=
+// 1024): ctl[0] active solves, ctl[1] rounds run; ends the loop (handle h)
+// when none is active or after max_rounds rounds.
+cudaError_t ctg_batch_finish_loop(BatchInst *insts, int n_inst, int *ctl, int max_rounds,
+                                  cudaGraphConditionalHandle h, cudaStream_t st);
+// Exit: y = R^{-1} g for the instance's final k.
+cudaError_t ctg_batch_solve_y(BatchInst *insts, int n_inst, int max_k, cudaStream_t st);
 int ctg_vec_blocks(long long L);          // blocks of an E = 1 vector pass over L
 
 // ---- host helpers shared by api.cu and batch.cu --------------------------

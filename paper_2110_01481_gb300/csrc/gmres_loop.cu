@@ -39,59 +39,6 @@ __device__ void end_step(const LoopBufs &B, int stop, int iters) {
     }
 }
 
-// y = R_k^{-1} g_{1:k} by back substitution in one warp, R (upper
-// triangle, column-major with leading dimension ldr) staged in shared
-// memory in packed form when it fits (packed: column j holds j + 1 entries
-// from offset j (j + 1) / 2), else read from global memory.
-__device__ void solve_y_warp(const double *__restrict__ R, int ldr, const double *__restrict__ g, int k,
-                             double *__restrict__ y, double *s_pack, int pack_cap) {
-    const int lane = threadIdx.x & 31;
-    const bool packed = k <= pack_cap;
-    if (packed)
-        // independent loads over the k x k square (the upper triangle kept)
-        for (int e = lane; e < k * k; e += 32) {
-            const int j = e / k, i = e - j * k;
-            if (i <= j) s_pack[j * (j + 1) / 2 + i] = R[(size_t)j * ldr + i];
-        }
-    // t = g; for i = k-1 .. 0: y_i = t_i / R_ii, t_j -= R_ji y_i (j < i);
-    // lane l owns t_j for j = l, l + 32, ... (k <= 256)
-    if (k > 256) {
-        // beyond the registers: a plain loop over y (rows of R from global)
-        if (lane == 0)
-            for (int i = k - 1; i >= 0; --i) {
-                double acc = g[i];
-                for (int j = i + 1; j < k; ++j) acc -= R[(size_t)j * ldr + i] * y[j];
-                const double d = R[(size_t)i * ldr + i];
-                y[i] = d != 0.0 ? acc / d : 0.0;
-            }
-        __syncwarp();
-        return;
-    }
-    double t[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int j = lane + 32 * q;
-        t[q] = j < k ? g[j] : 0.0;
-    }
-    __syncwarp();
-    for (int i = k - 1; i >= 0; --i) {
-        const int qi = i >> 5, li = i & 31;
-        double ti = 0.0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (q == qi) ti = __shfl_sync(0xffffffffu, t[q], li);
-        const double d = packed ? s_pack[i * (i + 1) / 2 + i] : R[(size_t)i * ldr + i];
-        const double yi = d != 0.0 ? ti / d : 0.0;
-        if (lane == 0) y[i] = yi;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int j = lane + 32 * q;
-            if (j < i) t[q] -= (packed ? s_pack[i * (i + 1) / 2 + j] : R[(size_t)i * ldr + j]) * yi;
-        }
-    }
-    __syncwarp();
-}
-
 // Step k of a solve after its CGS2 step wrote Hessenberg column k: the
 // FP64 Givens update (rotations in gc, gs; rotated column into R; rotated
 // right-hand side gg), rho_k = |g_{k+1}|, the breakdown test
