@@ -686,10 +686,12 @@ struct SolveCtx {
                      ColRef bc = col_none()) const {
         return traced(ctx, 1, 1, st, [&] { return back_apply(ge, b, btype, add, x, st, bc); });
     }
-    // one CGS2 step of the loop (k on the device)
-    cudaError_t cgs2_loop(int64_t L, float *q, int kmax, bool fused, bool cooperative) const {
+    // one CGS2 step of the loop (k on the device); with the fused step, its
+    // block 0 also runs the step's Givens update in mode giv_mode (lb)
+    cudaError_t cgs2_loop(int64_t L, float *q, int kmax, bool fused, bool cooperative,
+                          const LoopBufs *lb = nullptr, int giv_mode = -1) const {
         int nk = 0;
-        const LoopStep ls{&state()->k, at<double>(ly.off_h), ly.kmax + 1, kmax, fused};
+        const LoopStep ls{&state()->k, at<double>(ly.off_h), ly.kmax + 1, kmax, fused, lb, giv_mode};
         const cudaError_t e = traced(ctx, 2, 0, st, [&] {
             return ctg_cgs2_step_loop(W(), ly.dtype, ly.ld_w, L, q, ls, rs, ctx->spin_limit, cooperative, st, &nk);
         });
@@ -886,12 +888,22 @@ int enqueue_step(SolveCtx &sc, const LoopPlan &lp, const float *b, const float *
             return ctg_loop_givens(B, need_y, need_z, end, lp.maxit, sc.st);
         });
     };
+    // the Givens update runs in the fused CGS2 step's block 0, else on its own
+    auto cgs2_givens = [&](int64_t L, float *q, bool need_y, bool need_z, bool end) -> int {
+        if (fused) {
+            const int mode = (need_y ? kGivY : 0) | (need_z ? kGivZ : 0) | (end ? kGivEnd : 0);
+            CTG_CK(sc.cgs2_loop(L, q, kmax, true, lp.cooperative, &B, mode));
+            return CTG_OK;
+        }
+        CTG_CK(sc.cgs2_loop(L, q, kmax, false, lp.cooperative));
+        CTG_CK(givens(need_y, need_z, end));
+        return CTG_OK;
+    };
     if (lp.variant == CTG_AB) {
         CTG_CK(sc.back(sc.W(), nullptr, sc.vn0(), sc.ly.dtype, col_at(kdev, -1, (long long)sc.ly.ld_w)));
         CTG_CK(sc.forward(sc.vn0(), sc.vm0()));                           // q = A B w_k
-        CTG_CK(sc.cgs2_loop(m, sc.vm0(), kmax, fused, lp.cooperative));
         const bool ncp = lp.rule == kRuleNCP;
-        CTG_CK(givens(ncp, ncp, !ncp));
+        if (const int rc = cgs2_givens(m, sc.vm0(), ncp, ncp, !ncp)) return rc;
         if (ncp) {
             // r_k = W_{k+1} z_k, its NCP distance, the stop
             CTG_CK(sc.gemv_dev(m, kdev, 1, kmax + 1, B.z, nullptr, sc.vm1()));
@@ -901,9 +913,8 @@ int enqueue_step(SolveCtx &sc, const LoopPlan &lp, const float *b, const float *
         return CTG_OK;
     }
     CTG_CK(sc.back(sc.vm0(), nullptr, sc.vn0()));                         // q = B t_k
-    CTG_CK(sc.cgs2_loop(n, sc.vn0(), kmax, fused, lp.cooperative));
     const bool resid = lp.rule != kRuleMaxit;
-    CTG_CK(givens(resid, false, false));
+    if (const int rc = cgs2_givens(n, sc.vn0(), resid, false, false)) return rc;
     const ColRef wnext = col_at(kdev, 0, (long long)sc.ly.ld_w);         // w_{k+1}
     if (!resid) {
         CTG_CK(sc.forward(sc.W(), sc.vm0(), sc.ly.dtype, wnext));         // t_{k+1}
@@ -937,6 +948,10 @@ int enqueue_exit(SolveCtx &sc, const LoopPlan &lp, const float *b, const float *
         CTG_CK(sc.back(sc.vm0(), x0, x));
     } else {
         CTG_CK(sc.gemv_dev(sc.ly.n, idev, 0, lp.maxit, B.y, x0, x));
+        // BA with the DP stop already has ||b - A x|| of this very iterate
+        // (the same y, the same sweep, projected and reduced by the same
+        // arithmetic in the step that stopped; at k = 0 the start's residual)
+        if (lp.rule == kRuleDP) return CTG_OK;
     }
     CTG_CK(sc.forward(x, sc.vm1()));
     CTG_CK(sc.sub_norm2(b, sc.vm1(), nullptr, sc.ly.m, sc.rs.scal + 5));

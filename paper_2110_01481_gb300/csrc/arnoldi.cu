@@ -15,7 +15,7 @@
 // deterministic run to run.
 #include <atomic>
 
-#include "vecops.cuh"
+#include "loop_device.cuh"
 
 namespace {
 
@@ -270,20 +270,28 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, l
 // (leading dimension ldh).  bar[0] counts barrier arrivals (zero at launch;
 // the last block to leave sets it back to zero); on a timeout h_out[0..k]
 // is set to NaN.
+// With giv_mode >= 0 (a step of the device-driven solver loop), block 0
+// then runs the step's FP64 Givens update (loop_givens_warp) on the column it
+// has just written, and, by the mode, the end of the step, so the step needs
+// no launch of its own for them; its shared memory holds kcap_giv staging
+// entries and the packed triangle for y_k beyond the step's own.
 template <typename T, int E>
 __global__ void __launch_bounds__(kThreads, 2)
 cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__restrict__ kdev,
                   float *__restrict__ q, int64_t L, T *__restrict__ w_out, double *__restrict__ h_out,
                   double *__restrict__ H, int64_t ldh, float *__restrict__ partials,
                   double *__restrict__ h1g, double *__restrict__ h2g, double *__restrict__ scal,
-                  unsigned *__restrict__ bar, int *__restrict__ err, long long spin_limit) {
+                  unsigned *__restrict__ bar, int *__restrict__ err, long long spin_limit,
+                  LoopBufs lb, int giv_mode, int kcap_giv, int pack_cap) {
     if (kdev) {
         k = *kdev;
         w_out = const_cast<T *>(W) + (size_t)k * ldw;
         h_out = H + (size_t)(k - 1) * ldh;
     }
     extern __shared__ double smem_d[];
-    double *s_h1 = smem_d;                          // k + 1: h1, then ||q_pre||^2
+    double *s_stage = smem_d;                       // 3 kcap_giv + 1: the Givens staging
+    double *s_pack = s_stage + (giv_mode >= 0 ? 3 * kcap_giv + 1 : 0);   // packed R for y_k
+    double *s_h1 = s_pack + (giv_mode >= 0 && (giv_mode & kGivY) ? pack_cap * (pack_cap + 1) / 2 : 0);
     double *s_h2 = s_h1 + (k + 1);                  // k + 1: h2, then ||q||^2
     float *s_c = reinterpret_cast<float *>(s_h2 + (k + 1));   // k coefficients
     float *s_w = s_c + k;                           // kWarps * (k + 1)
@@ -329,8 +337,15 @@ cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__rest
         }
     }
     if (!ok) {
-        // gave up at a barrier: leave q and W alone and mark the column
+        // gave up at a barrier: leave q and W alone and mark the column; the
+        // Givens update takes the NaN column for a breakdown, and the step's
+        // end reports the timeout
         for (int j = tid; j <= k; j += kThreads) h_out[j] = __longlong_as_double(0x7ff8000000000000LL);
+        if (giv_mode >= 0 && blk == 0) {
+            __syncthreads();
+            if (tid < 32) loop_givens_warp(lb, k, h_out, 0.0, giv_mode, s_pack, pack_cap,
+                                           k <= kcap_giv ? s_stage : nullptr);
+        }
         return;
     }
     // w_{k+1} = q / ||q||; q keeps the orthogonalised vector
@@ -355,7 +370,13 @@ cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__rest
         }
     }
     // the last block out resets the barrier counter for the next launch
+    // (every block has read k by now: it passed both barriers)
     if (tid == 0 && atomicAdd(bar, 1u) == (nbar + 1u) * (unsigned)G - 1u) atomicExch(bar, 0u);
+    if (giv_mode >= 0 && blk == 0) {
+        __syncthreads();                            // the column is written
+        if (tid < 32) loop_givens_warp(lb, k, h_out, s_h1[k], giv_mode, s_pack, pack_cap,
+                                       k <= kcap_giv ? s_stage : nullptr);
+    }
 }
 
 // w_out = q / sqrt(nrm2) (0 if nrm2 == 0); block 0 also assembles the
@@ -849,8 +870,15 @@ void ctg_red_scratch_carve(void *base, int64_t L, int kmax, RedScratch *rs) {
 
 namespace {
 
-size_t fused_smem_bytes(int k) {
-    return sizeof(double) * 2 * (size_t)(k + 1) + sizeof(float) * ((size_t)k + (size_t)kWarps * (k + 1));
+// giv_mode >= 0: with the Givens staging (3 k + 1 doubles) and, for y_k,
+// the packed triangle (loop_pack_cap(k) columns) in front
+size_t fused_smem_bytes(int k, int giv_mode = -1) {
+    size_t giv = 0;
+    if (giv_mode >= 0) {
+        giv = 3 * (size_t)k + 1;
+        if (giv_mode & kGivY) giv += (size_t)loop_pack_cap(k) * (loop_pack_cap(k) + 1) / 2;
+    }
+    return sizeof(double) * (giv + 2 * (size_t)(k + 1)) + sizeof(float) * ((size_t)k + (size_t)kWarps * (k + 1));
 }
 
 int scale_blocks(int64_t L) {
@@ -869,7 +897,7 @@ int fused_resident_blocks() {
     static std::atomic<int> cache[kMaxDevices];
     return per_device_cached(cache, [](int dev) {
         int per_sm = 0, sms = 0;
-        const size_t smem = fused_smem_bytes(kFusedMaxK);
+        const size_t smem = fused_smem_bytes(kFusedMaxK, kGivY);
         if (dev < 0 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cgs2_fused_kernel<T, E>, kThreads,
                                                           smem) != cudaSuccess) {
@@ -893,7 +921,15 @@ cudaError_t launch_fused(const T *W, int64_t ldw, int64_t L, int k, float *q, T 
     *done = false;
     if (G > fused_resident_blocks<T, E>()) return cudaSuccess;
     const int kcap = ls ? ls->kmax : k;
-    const size_t smem = fused_smem_bytes(kcap);
+    const int giv_mode = ls && ls->lb ? ls->giv_mode : -1;
+    const size_t smem = fused_smem_bytes(kcap, giv_mode);
+    if (smem > 48 * 1024) {
+        const cudaError_t ea = cudaFuncSetAttribute(cgs2_fused_kernel<T, E>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ea != cudaSuccess) return ea;
+    }
+    const LoopBufs lb = ls && ls->lb ? *ls->lb : LoopBufs{};
+    const int pack_cap = loop_pack_cap(kcap);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(kThreads);
@@ -910,7 +946,7 @@ cudaError_t launch_fused(const T *W, int64_t ldw, int64_t L, int k, float *q, T 
     const cudaError_t e = cudaLaunchKernelEx(&cfg, cgs2_fused_kernel<T, E>, W, ldw, k, kdev, q, L, w_out,
                                              h_out, H, ldh, rs.partials, rs.h1, rs.h2, rs.scal,
                                              rs.counter + 1, reinterpret_cast<int *>(rs.counter + 2),
-                                             spin_limit);
+                                             spin_limit, lb, giv_mode, kcap, pack_cap);
     *done = e == cudaSuccess;
     return e;
 }

@@ -224,12 +224,18 @@ cudaError_t ctg_cgs2_step(const void *W, int dtype, int64_t ldw, int64_t L, int 
 // H + (k - 1) ldh; kmax bounds k (it sizes shared memory); fused selects
 // the one-launch step (needs ctg_cgs2_fused_ok) or the three passes.
 // ||q_pre||^2 is left in rs.h1[k].
+struct LoopBufs;
 struct LoopStep {
     const int *k;
     double *H;
     long long ldh;
     int kmax;
     bool fused;
+    // with the fused step: the loop whose Givens update (and, by giv_mode's
+    // end flag, the end of the step) block 0 runs once the column is known;
+    // giv_mode < 0: none
+    const LoopBufs *lb;
+    int giv_mode;
 };
 cudaError_t ctg_cgs2_step_loop(const void *W, int dtype, int64_t ldw, int64_t L, float *q, const LoopStep &ls,
                                const RedScratch &rs, long long spin_limit, bool cooperative, cudaStream_t st,
@@ -294,6 +300,9 @@ struct LoopBufs {
     int in_graph;
     int fused_max;        // last k of the fused-CGS2 loop
 };
+// Modes of a step's Givens update: y_k every step (kGivY), AB NCP's
+// residual coefficients (kGivZ), the update ends the step (kGivEnd).
+enum { kGivY = 1, kGivZ = 2, kGivEnd = 4 };
 cudaError_t ctg_loop_init(const LoopBufs &B, int variant, int rule, int maxit, double target, cudaStream_t st);
 // need_y: y_k every step; need_z: AB NCP residual coefficients; end: the
 // Givens kernel ends the step (AB with DP or maxit)

@@ -7,137 +7,18 @@
 // so one captured sequence of launches serves every step; the kernel that
 // ends a step either advances k or stops the solve, and, inside a CUDA
 // graph, also sets the condition of the graph's while-loop nodes.
-#include "vecops.cuh"
+#include "loop_device.cuh"
 
 namespace {
 
-__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, bool in_graph, unsigned v) {
-    if (in_graph) cudaGraphSetConditional(h, v);
-}
-
-// End of step k (one thread): stop the solve with `stop` (a CTG_STOP_*
-// value + 1, 0 to go on) returning x_iters, or move to step k + 1.  A
-// timed-out grid barrier (counter[2] set) stops the solve too; the host
-// reports it.
-__device__ void end_step(const LoopBufs &B, int stop, int iters) {
-    GmresState &S = *B.S;
-    S.steps += 1;
-    if (B.counter[2] != 0u) {
-        stop = CTG_STOP_MAXIT + 1;
-        S.timed_out = 1;
-    }
-    if (stop) {
-        S.active = 0;
-        S.stop_reason = stop - 1;
-        S.iters = iters;
-        set_cond(B.c_fused, B.in_graph, 0u);
-        set_cond(B.c_pass, B.in_graph, 0u);
-    } else {
-        const int k1 = S.k + 1;
-        S.k = k1;
-        if (k1 > B.fused_max) set_cond(B.c_fused, B.in_graph, 0u);
-    }
-}
-
-// Step k of a solve after its CGS2 step wrote Hessenberg column k: the
-// FP64 Givens update (rotations in gc, gs; rotated column into R; rotated
-// right-hand side gg), rho_k = |g_{k+1}|, the breakdown test
-// h_{k+1,k} <= 1e-6 ||q_pre|| (||q_pre||^2 in h1[k]), and by `mode`:
-//   kGivY  y_k into y and yring[k % 3] (BA with a residual rule, AB NCP),
-//   kGivZ  z = beta e1 - H_k y_k, the residual's coefficients in W_{k+1}
-//          (AB NCP), by the rotations applied backwards,
-//   kGivEnd  end the step here (AB with DP / maxit): stop at breakdown, at
-//          rho_k <= target (DP) or at k = maxit, else k + 1.
-// Otherwise a breakdown or k = maxit is left in S.pending for the step's
-// last kernel.  hist[k] = rho_k unless BA with the discrepancy rule (its
-// history is the true residual).
-enum { kGivY = 1, kGivZ = 2, kGivEnd = 4 };
-
-// Column k, the rotations and the rotated column are staged through shared
-// memory (all lanes load, lane 0 runs the recurrence), so the serial part
-// does no global round trips.
-constexpr int kGivStage = 512;     // steps staged; beyond, lane 0 reads global memory
-
+// Step k's Givens update and stopping rule as a kernel of its own (where
+// the CGS2 step cannot run it: the separate passes).
 __global__ void loop_givens_kernel(LoopBufs B, int mode, int pack_cap) {
     extern __shared__ double s_pack[];
-    __shared__ double s_c[2];
-    __shared__ double s_h[kGivStage + 1], s_gc[kGivStage], s_gs[kGivStage];
-    GmresState &S = *B.S;
-    const int k = S.k, lane = threadIdx.x;
+    __shared__ double s_stage[3 * kGivStage + 1];
+    const int k = B.S->k;
     const double *h = B.H + (size_t)(k - 1) * B.ldh;
-    double *Rk = B.R + (size_t)(k - 1) * B.ldr;
-    const bool staged = k <= kGivStage;
-    if (staged) {
-        for (int i = lane; i <= k; i += 32) s_h[i] = h[i];
-        for (int i = lane; i < k - 1; i += 32) {
-            s_gc[i] = B.gc[i];
-            s_gs[i] = B.gs[i];
-        }
-    }
-    __syncwarp();
-    const double *hh = staged ? s_h : h;
-    const double *gcc = staged ? s_gc : B.gc;
-    const double *gss = staged ? s_gs : B.gs;
-    if (lane == 0) {
-        double r_prev = hh[0];
-        for (int i = 0; i < k - 1; ++i) {
-            const double a = r_prev, b = hh[i + 1];
-            const double t = gcc[i] * a + gss[i] * b;
-            if (staged) s_h[i] = t;            // rotated column, stored below
-            else Rk[i] = t;
-            r_prev = -gss[i] * a + gcc[i] * b;
-        }
-        const double a = r_prev, b = hh[k];
-        const double r = hypot(a, b);
-        double c = 1.0, sn = 0.0;
-        if (b != 0.0) {
-            c = a / r;
-            sn = b / r;
-        }
-        B.gc[k - 1] = c;
-        B.gs[k - 1] = sn;
-        if (staged) s_h[k - 1] = b != 0.0 ? r : a;
-        else Rk[k - 1] = b != 0.0 ? r : a;
-        B.gg[k] = -sn * B.gg[k - 1];
-        B.gg[k - 1] = c * B.gg[k - 1];
-        const double rho = fabs(B.gg[k]);
-        S.rho = rho;
-        B.rhoh[k] = rho;
-        s_c[0] = rho;
-        // a NaN column marks a CGS2 step that gave up at a grid barrier
-        s_c[1] = (b <= 1e-6 * sqrt(B.h1[k]) || !(b == b)) ? 1.0 : 0.0;
-    }
-    __syncwarp();
-    if (staged)
-        for (int i = lane; i < k; i += 32) Rk[i] = s_h[i];
-    __syncwarp();
-    const double rho = s_c[0];
-    const bool breakdown = s_c[1] != 0.0;
-    if (mode & kGivY) {
-        solve_y_warp(B.R, B.ldr, B.gg, k, B.y, s_pack, pack_cap);
-        double *yr = B.yring + (size_t)(k % 3) * B.ldr;
-        for (int i = lane; i < k; i += 32) yr[i] = B.y[i];
-    }
-    if ((mode & kGivZ) && lane == 0) {
-        // z = G_1^T ... G_k^T (g_{k+1} e_{k+1}), G_i acting on entries i-1, i
-        for (int i = 0; i <= k; ++i) B.z[i] = 0.0;
-        B.z[k] = B.gg[k];
-        for (int i = k - 1; i >= 0; --i) {
-            const double a = B.z[i], b = B.z[i + 1];
-            B.z[i] = B.gc[i] * a - B.gs[i] * b;
-            B.z[i + 1] = B.gs[i] * a + B.gc[i] * b;
-        }
-    }
-    if (lane != 0) return;
-    if (!(S.variant == CTG_BA && S.rule == kRuleDP)) B.hist[k] = rho;
-    const int pending = breakdown ? CTG_STOP_BREAKDOWN + 1 : (k == S.maxit ? CTG_STOP_MAXIT + 1 : 0);
-    if (mode & kGivEnd) {
-        int stop = pending;
-        if (!breakdown && S.rule == kRuleDP && rho <= S.target) stop = CTG_STOP_DP + 1;
-        end_step(B, stop, k);
-    } else {
-        S.pending = pending;
-    }
+    loop_givens_warp(B, k, h, B.h1[k], mode, s_pack, pack_cap, k <= kGivStage ? s_stage : nullptr);
 }
 
 // BA with the discrepancy principle or NCP: r = b - A x_k (Ax = A x_k from
