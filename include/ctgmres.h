@@ -96,7 +96,8 @@ typedef struct {
     int32_t maxit;            /* iteration cap, >= 1                        */
     int32_t basis_dtype;      /* CTG_BASIS_FP32, _BF16 or _FP16: element type
                                  of the stored Krylov basis W; arithmetic is
-                                 FP32 (FP64 for reductions and the
+                                 FP32 (cross-block sums as compensated FP32
+                                 pairs with FP64 results; FP64 for the
                                  Hessenberg problem) in every case         */
     double tau;               /* DP safety factor tau >= 1 (Sec. 6.4)       */
     double noise_norm;        /* ||e||; <= 0 disables the DP stop           */

@@ -11,18 +11,20 @@
 // cancels), h_{1:k,k} = h1 + h2, h_{k+1,k} = ||q||.
 // Each pass is one launch: every block reduces its slice with warp shuffles
 // into per-block partials, and the last block to finish (atomic ticket, no
-// waiting) sums the partials in a fixed order in FP64, so results are
-// deterministic run to run.
+// waiting) sums the partials in a fixed order (compensated FP32 pairs,
+// FP64 results), so results are deterministic run to run.
 #include <atomic>
 
 #include "loop_device.cuh"
 
 namespace {
 
-// Vectors per load batch: 128 bytes of basis data in flight per thread.
-template <typename T, int E>
+// Vectors per load batch: BYTES of basis data in flight per thread (128
+// where registers are short, as in the one-launch step; 256 in the separate
+// passes, measured 6-8 % faster at k = 100).
+template <typename T, int E, int BYTES = 128>
 __host__ __device__ constexpr int batch_vectors() {
-    return (int)(128 / (4 * sizeof(T) * E)) > 0 ? (int)(128 / (4 * sizeof(T) * E)) : 1;
+    return (int)(BYTES / (4 * sizeof(T) * E)) > 0 ? (int)(BYTES / (4 * sizeof(T) * E)) : 1;
 }
 
 // acc += sum_j c_j V_j over this thread's E float4 groups, loads issued in
@@ -61,11 +63,11 @@ __device__ __forceinline__ void accumulate_batched(const T *__restrict__ V, int6
 // 16-bit one).  Past the last vector the load repeats vector k-1 (a cache
 // hit) and its coefficient / dot is dropped, so every load of the batch is
 // unconditional and issued before any use.
-template <typename T, int E>
+template <typename T, int E, int BYTES = 128>
 __device__ __forceinline__ void update_slice(const T *__restrict__ W, int64_t ldw, int k,
                                              const float *s_coef, int64_t g0, int64_t L,
                                              float4 (&qv)[E]) {
-    constexpr int JB = batch_vectors<T, E>();
+    constexpr int JB = batch_vectors<T, E, BYTES>();
     for (int j0 = 0; j0 < k; j0 += JB) {
         typename RawOf<T>::type w[JB][E];
 #pragma unroll
@@ -91,16 +93,20 @@ __device__ __forceinline__ void update_slice(const T *__restrict__ W, int64_t ld
 
 // Warp sums of W_j^T qv (j < k) into s_w[warp * nred + j] and, with NORM,
 // of qv^T qv into s_w[warp * nred + k]; same load batching as update_slice.
-template <typename T, int E, bool NORM>
+// REV visits the vectors from the last to the first: after an update sweep
+// over W, the vectors it read last are the ones still in L2 (a basis larger
+// than L2 is then read from HBM about 1.6 instead of 2 times per pass).
+template <typename T, int E, bool NORM, bool REV = false, int BYTES = 128>
 __device__ __forceinline__ void dots_slice(const T *__restrict__ W, int64_t ldw, int k, int64_t g0,
                                            int64_t L, const float4 (&qv)[E], float *s_w, int nred) {
-    constexpr int JB = batch_vectors<T, E>();
+    constexpr int JB = batch_vectors<T, E, BYTES>();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int j0 = 0; j0 < k; j0 += JB) {
+    for (int t0 = 0; t0 < k; t0 += JB) {
         typename RawOf<T>::type w[JB][E];
 #pragma unroll
         for (int jj = 0; jj < JB; ++jj) {
-            const T *Wj = W + (size_t)min(j0 + jj, k - 1) * ldw;
+            const int t = min(t0 + jj, k - 1);
+            const T *Wj = W + (size_t)(REV ? k - 1 - t : t) * ldw;
 #pragma unroll
             for (int e = 0; e < E; ++e) w[jj][e] = ldraw(Wj, g0 + (int64_t)e * kThreads, L);
         }
@@ -110,7 +116,8 @@ __device__ __forceinline__ void dots_slice(const T *__restrict__ W, int64_t ldw,
 #pragma unroll
             for (int e = 0; e < E; ++e) sj += dot4(cvt4<T>(w[jj][e]), qv[e]);
             sj = warp_sum(sj);
-            if (lane == 0 && j0 + jj < k) s_w[warp * nred + j0 + jj] = sj;
+            const int t = t0 + jj;
+            if (lane == 0 && t < k) s_w[warp * nred + (REV ? k - 1 - t : t)] = sj;
         }
     }
     if (NORM) {
@@ -146,12 +153,12 @@ __device__ __forceinline__ void cgs_pass_body(const T *__restrict__ W, int64_t l
     for (int e = 0; e < E; ++e) qv[e] = ld4_rw(q, g0 + (int64_t)e * kThreads, L);
     if (UPDATE) {
         __syncthreads();
-        update_slice<T, E>(W, ldw, k, s_coef, g0, L, qv);
+        update_slice<T, E, 256>(W, ldw, k, s_coef, g0, L, qv);
 #pragma unroll
         for (int e = 0; e < E; ++e) st4(q, g0 + (int64_t)e * kThreads, L, qv[e]);
     }
     if (DOTS) {
-        dots_slice<T, E, NORM>(W, ldw, k, g0, L, qv, s_w, nred);
+        dots_slice<T, E, NORM, UPDATE, 256>(W, ldw, k, g0, L, qv, s_w, nred);
     } else if (NORM) {
         float s = 0.f;
 #pragma unroll
@@ -175,37 +182,11 @@ cgs_pass_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__restri
 }
 
 // Every block sums the partial rows [row0, row0 + nrows) of all blocks in
-// one fixed order in FP64.
+// one fixed order (compensated FP32 pairs, FP64 results), so all blocks
+// hold identical coefficients.
 __device__ __forceinline__ void reduce_rows(const float *__restrict__ partials, int row0, int nrows,
                                             int G, int Gp, double *out) {
-    // each warp takes four rows at a time and reads them as float4 (four
-    // blocks per load); the padding entries (block index >= G) are skipped
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int G4 = Gp / 4;
-    for (int j0 = warp * 4; j0 < nrows; j0 += kWarps * 4) {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int g4 = lane; g4 < G4; g4 += 32) {
-            float4 v[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                v[q] = (j0 + q < nrows)
-                           ? __ldcg(reinterpret_cast<const float4 *>(partials + (size_t)(row0 + j0 + q) * Gp) + g4)
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
-            const int b0 = 4 * g4;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                acc[q] += (double)v[q].x;
-                if (b0 + 1 < G) acc[q] += (double)v[q].y;
-                if (b0 + 2 < G) acc[q] += (double)v[q].z;
-                if (b0 + 3 < G) acc[q] += (double)v[q].w;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const double t = warp_sum_d(acc[q]);
-            if (lane == 0 && j0 + q < nrows) out[j0 + q] = t;
-        }
-    }
+    sum_partial_rows(partials, row0, nrows, G, Gp, out);
 }
 
 __device__ __forceinline__ void write_rows(const float *s_w, int nred, int row0, float *partials,
@@ -263,8 +244,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, l
 // per-block partial sums to its own rows of the partials ([0, k] pass 1,
 // [k+1, 2k] pass 2, so no block overwrites rows another block may still be
 // reading), and after the barrier every block sums the partials of all
-// blocks in the same fixed order in FP64, so all blocks hold identical
-// coefficients and the result is deterministic.
+// blocks in the same fixed order (compensated FP32 pairs), so all blocks
+// hold identical coefficients and the result is deterministic.
 // Step: k, w_out and h_out as given, or (kdev set, a step of a captured
 // solver loop) k = *kdev, w_out = column k of W and h_out = column k of H
 // (leading dimension ldh).  bar[0] counts barrier arrivals (zero at launch;
@@ -292,8 +273,8 @@ cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__rest
     double *s_stage = smem_d;                       // 3 kcap_giv + 1: the Givens staging
     double *s_pack = s_stage + (giv_mode >= 0 ? 3 * kcap_giv + 1 : 0);   // packed R for y_k
     double *s_h1 = s_pack + (giv_mode >= 0 && (giv_mode & kGivY) ? pack_cap * (pack_cap + 1) / 2 : 0);
-    double *s_h2 = s_h1 + (k + 1);                  // k + 1: h2, then ||q||^2
-    float *s_c = reinterpret_cast<float *>(s_h2 + (k + 1));   // k coefficients
+    double *s_h2 = s_h1 + (k + 1);                  // k + 2: h2, ||q1||^2, then ||q2||^2
+    float *s_c = reinterpret_cast<float *>(s_h2 + (k + 2));   // k coefficients
     float *s_w = s_c + k;                           // kWarps * (k + 1)
     const int tid = threadIdx.x, blk = blockIdx.x, G = gridDim.x, Gp = padded_grid(G);
     const unsigned nbar = k > 0 ? 2u : 1u;
@@ -329,11 +310,17 @@ cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__rest
             // first pass, so the difference loses nothing, and the step needs no
             // third grid-wide reduction.  Every block forms it in the same order.
             for (int j = tid; j < k; j += kThreads) s_c[j] = (float)s_h2[j];
+            if (tid < 32) {
+                // ||h2||^2 once per block (FP64 issues slowly): lane-strided
+                // sums, then a fixed xor tree, the same bits in every block
+                double t = 0.0;
+                for (int j = tid; j < k; j += 32) t = fma(s_h2[j], s_h2[j], t);
+                t = warp_sum_d(t);
+                if (tid == 0) s_h2[k + 1] = fmax(0.0, s_h2[k] - t);
+            }
             __syncthreads();
             update_slice<T, E>(W, ldw, k, s_c, g0, L, qv);
-            double h2sq = 0.0;
-            for (int j = 0; j < k; ++j) h2sq = fma(s_h2[j], s_h2[j], h2sq);
-            nrm2 = fmax(0.0, s_h2[k] - h2sq);
+            nrm2 = s_h2[k + 1];
         }
     }
     if (!ok) {
@@ -434,7 +421,7 @@ __device__ __forceinline__ void update_scale_body(const T *__restrict__ W, int64
     float4 qv[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) qv[e] = ld4_rw(q, g0 + (int64_t)e * kThreads, L);
-    update_slice<T, E>(W, ldw, k, s_coef, g0, L, qv);
+    update_slice<T, E, 256>(W, ldw, k, s_coef, g0, L, qv);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int64_t g = g0 + (int64_t)e * kThreads;
@@ -878,7 +865,7 @@ size_t fused_smem_bytes(int k, int giv_mode = -1) {
         giv = 3 * (size_t)k + 1;
         if (giv_mode & kGivY) giv += (size_t)loop_pack_cap(k) * (loop_pack_cap(k) + 1) / 2;
     }
-    return sizeof(double) * (giv + 2 * (size_t)(k + 1)) + sizeof(float) * ((size_t)k + (size_t)kWarps * (k + 1));
+    return sizeof(double) * (giv + 2 * (size_t)k + 3) + sizeof(float) * ((size_t)k + (size_t)kWarps * (k + 1));
 }
 
 int scale_blocks(int64_t L) {

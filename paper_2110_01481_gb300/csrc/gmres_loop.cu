@@ -22,7 +22,7 @@ __global__ void loop_givens_kernel(LoopBufs B, int mode, int pack_cap) {
 }
 
 // BA with the discrepancy principle or NCP: r = b - A x_k (Ax = A x_k from
-// the step's two-image forward projection), ||r||^2 reduced in FP64 by the
+// the step's two-image forward projection), ||r||^2 reduced across blocks by the
 // last block, which records ||b - A x_k|| and, with `decide` (DP), ends
 // the step: stop at a pending breakdown, at ||r|| <= target (DP), at a
 // pending maxit, else k + 1.  r_out: NULL, or where r is written (NCP).

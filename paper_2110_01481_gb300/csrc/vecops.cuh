@@ -48,7 +48,7 @@ __device__ __forceinline__ void st4(float *p, int64_t g, int64_t L, float4 v) {
 }
 
 // Basis vectors may be stored in FP32, BF16 or FP16; every kernel converts
-// them to FP32 on use and accumulates in FP32 (reductions in FP64).  A
+// them to FP32 on use and accumulates in FP32 (cross-block sums compensated).  A
 // float4 group of the FP32 work vector pairs with one 8-byte load of a
 // 16-bit basis vector.
 // Raw (unconverted) loads, so that a batch of loads is issued before any
@@ -129,6 +129,45 @@ __device__ __forceinline__ double warp_sum_d(double s) {
     return s;
 }
 
+// Compensated FP32 sums (Neumaier's variant of Kahan summation): s holds
+// the running FP32 sum and c the sum of the exact rounding errors of its
+// additions, so s + c (formed in FP64) carries a sum of n FP32 terms to
+// about n 2^-48 sum |x_i|, against n 2^-53 sum |x_i| for FP64 accumulation
+// and n 2^-24 sum |x_i| for plain FP32.  GB300 issues FP64 adds at about
+// 1/64 of the FP32 rate (measured: 1.6 against 100 per clock and SM), so the
+// cross-block sums of the reductions use these pairs and FP64 only for the
+// final s + c.
+struct F2 {
+    float s, c;
+};
+
+__device__ __forceinline__ F2 f2_add(F2 a, float x) {
+    const float t = a.s + x;
+    const float e = fabsf(a.s) >= fabsf(x) ? (a.s - t) + x : (x - t) + a.s;   // exact: a.s + x - t
+    return F2{t, a.c + e};
+}
+
+__device__ __forceinline__ F2 f2_merge(F2 a, F2 b) {
+    F2 r = f2_add(a, b.s);
+    r.c += b.c;
+    return r;
+}
+
+// Warp sum of F2 pairs; at each step the lane with the offset bit clear is
+// the left operand, so both partners form bit-identical results and every
+// lane ends with the same pair.
+__device__ __forceinline__ F2 warp_sum_f2(F2 v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const F2 w{__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.c, o)};
+        v = (lane & o) ? f2_merge(w, v) : f2_merge(v, w);
+    }
+    return v;
+}
+
+__device__ __forceinline__ double f2_value(F2 v) { return (double)v.s + (double)v.c; }
+
 // y = R_k^{-1} g_{1:k} by back substitution in one warp, R (upper
 // triangle, column-major with leading dimension ldr) staged in shared
 // memory in packed form when it fits (packed: column j holds j + 1 entries
@@ -186,17 +225,52 @@ __device__ void solve_y_warp(const double *__restrict__ R, int ldr, const double
 // last block can read them as float4.
 __host__ __device__ inline int padded_grid(int G) { return (G + 3) & ~3; }
 
+// Rows [row0, row0 + nrows) of the per-block partials (G blocks, row
+// stride Gp) summed over the blocks in one fixed order, as compensated
+// FP32 pairs: each warp of the block takes four rows at a time and reads
+// them as float4 (four blocks per load); out[j] (j < nrows, FP64) is written
+// by lane 0 of the warp that summed row j.  The padding entries (block index
+// >= G) are never read into a sum.
+__device__ __forceinline__ void sum_partial_rows(const float *__restrict__ partials, int row0, int nrows, int G,
+                                                 int Gp, double *out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int G4 = Gp / 4;
+    for (int j0 = warp * 4; j0 < nrows; j0 += kWarps * 4) {
+        F2 acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        for (int g4 = lane; g4 < G4; g4 += 32) {
+            float4 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                v[q] = (j0 + q < nrows)
+                           ? __ldcg(reinterpret_cast<const float4 *>(partials + (size_t)(row0 + j0 + q) * Gp) + g4)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int b0 = 4 * g4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc[q] = f2_add(acc[q], v[q].x);
+                if (b0 + 1 < G) acc[q] = f2_add(acc[q], v[q].y);
+                if (b0 + 2 < G) acc[q] = f2_add(acc[q], v[q].z);
+                if (b0 + 3 < G) acc[q] = f2_add(acc[q], v[q].w);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const F2 t = warp_sum_f2(acc[q]);
+            if (lane == 0 && j0 + q < nrows) out[j0 + q] = f2_value(t);
+        }
+    }
+}
+
 // Writes this block's nred partial sums, then lets the last block sum all
-// blocks' partials (fixed order, FP64) into red_out[0..nred-1].  The last
-// block's warps each take four coefficients at a time and read the partials
-// as float4, so the serial tail is a few L2 round trips.
-// Returns true in the last block (after red_out is written and the block
-// has synchronised), false in the others.
+// blocks' partials (fixed order, compensated FP32 pairs, sum_partial_rows)
+// into red_out[0..nred-1] in FP64, so the serial tail is a few L2 round
+// trips.  Returns true in the last block (after red_out is written and the
+// block has synchronised), false in the others.
 __device__ bool block_reduce_finish(float *s_w, int nred, float *__restrict__ partials,
                                     unsigned *__restrict__ counter,
                                     double *__restrict__ red_out, int blk, int G) {
     __shared__ bool s_last;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int Gp = padded_grid(G);
     __syncthreads();
     for (int j = tid; j < nred; j += kThreads) {
@@ -210,32 +284,7 @@ __device__ bool block_reduce_finish(float *s_w, int nred, float *__restrict__ pa
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
-    const int G4 = Gp / 4;
-    for (int j0 = warp * 4; j0 < nred; j0 += kWarps * 4) {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int g4 = lane; g4 < G4; g4 += 32) {
-            float4 v[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                v[q] = (j0 + q < nred)
-                           ? __ldcg(reinterpret_cast<const float4 *>(partials + (size_t)(j0 + q) * Gp) + g4)
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
-            const int b0 = 4 * g4;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                // the padding entries (block index >= G) were never written
-                acc[q] += (double)v[q].x;
-                if (b0 + 1 < G) acc[q] += (double)v[q].y;
-                if (b0 + 2 < G) acc[q] += (double)v[q].z;
-                if (b0 + 3 < G) acc[q] += (double)v[q].w;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const double t = warp_sum_d(acc[q]);
-            if (lane == 0 && j0 + q < nred) red_out[j0 + q] = t;
-        }
-    }
+    sum_partial_rows(partials, 0, nred, G, Gp, red_out);
     if (tid == 0) *counter = 0u;
     __syncthreads();
     return true;
