@@ -200,7 +200,10 @@ def cgs2_timing(P, torch, native, dev, k, L, steps, flush):
     """Median device time (ms) of one CGS2 step of a length-L vector against
     k stored vectors: the Arnoldi step at a large basis, where it is the
     HBM-bound kernel of the path (3 sweeps of W_k are its algorithmic
-    traffic).  L2 is flushed before every timed step."""
+    traffic).  L2 is flushed before every timed step: a write of a buffer
+    twice its size, then a read of the same buffer, so that the timed step
+    starts with L2 full of clean lines (no write-back of the flush's dirty
+    lines is charged to the step) and none of W or q in it."""
     ldw = (L + 63) // 64 * 64
     Wc = torch.randn(k + 1, ldw, device=dev, dtype=torch.float32) / math.sqrt(L)
     qc = torch.randn(L, device=dev, dtype=torch.float32)
@@ -212,6 +215,7 @@ def cgs2_timing(P, torch, native, dev, k, L, steps, flush):
     for i in range(3 + steps):
         qw.copy_(qc)
         flush.zero_()
+        flush.sum(dtype=torch.int32)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         P.cgs2(Wc, k, qw, w_out=Wc[k, :L], scratch=scratch)

@@ -303,8 +303,12 @@ joseph_forward_kernel(const void *__restrict__ pad, int N, int stride, int borde
 // order (deterministic, no atomics), each CTA finishing a quarter of the
 // tile's rows.
 constexpr int kBT = 32;          // tile side
-constexpr int kBRows = 4;        // rows per thread (threads: 32 x 8)
+constexpr int kBRows = 4;        // rows per thread (threads: 32 x 8), batched launches
 constexpr int kBThreads = 256;
+constexpr int kBRowsTiled = 4;   // rows per thread of the single launch (8 rows and 32 x 4
+                                 // threads measured 6 % slower: fewer warps to hide latency)
+template <int kRows>
+__host__ __device__ constexpr int back_threads() { return kBT * (kBT / kRows); }
 constexpr int kBChunk = 32;      // angles staged per pass
 constexpr int kBSplit = 4;       // CTAs per cluster = angle groups per tile
 
@@ -316,25 +320,32 @@ constexpr int kBSplit = 4;       // CTAs per cluster = angle groups per tile
 // scale * max(0, 1 - f inv_w) and scale * max(0, 1 - (1 - f) inv_w) (terms
 // below thr dropped for 2).  The staged pairs are (b[d], b[d+1] - b[d]) for
 // the pixel-driven B and (b[d], b[d+1]) for the others.
-template <typename T, int kModel = 0, int kChunk = kBChunk>
+// kRows: pixel rows per thread, kBT / kRows row threads per column (rows
+// di, di + kBT / kRows, ...): more rows per thread spread the per-angle
+// setup over more interpolations.
+template <typename T, int kModel = 0, int kChunk = kBChunk, int kRows = kBRows>
 __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, int n_angles,
                                                 int n_det, const BackAngle *__restrict__ tab,
                                                 int W, const float *__restrict__ add,
                                                 float *__restrict__ x, int bx, int by,
                                                 const MatchedAngle *__restrict__ mt = nullptr,
                                                 float thr = 0.0f) {
+    constexpr int kThr = back_threads<kRows>(), kRT = kBT / kRows;
+    static_assert(kChunk <= kThr && kRows % 2 == 0 && kRows <= 16, "back tile shape");
     extern __shared__ float2 s_pairs[];               // kChunk * W pairs
     __shared__ float4 s_par[kChunk];                  // cf, sf, u0' (window-relative), origin
     __shared__ float4 s_wt[kModel ? kChunk : 1];      // scale, scale inv_w, scale - scale inv_w
-    __shared__ float s_part[kBRows][kBThreads];       // this CTA's partial sums
+    __shared__ float s_part[kRows][kThr];             // this CTA's partial sums
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();       // == blockIdx.z
     const int j0 = bx * kBT, i0 = by * kBT;
-    const int dj = threadIdx.x & 31, di = threadIdx.x >> 5;   // di in [0, 8)
+    const int dj = threadIdx.x & 31, di = threadIdx.x >> 5;   // di in [0, kRT)
     const float fdj = (float)dj, fdi = (float)di;
     const int per = (n_angles + kBSplit - 1) / kBSplit;
     const int a_begin = min(n_angles, rank * per), a_end = min(n_angles, a_begin + per);
-    float acc[kBRows] = {0.f, 0.f, 0.f, 0.f};
+    float acc[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) acc[r] = 0.f;
     for (int a0 = a_begin; a0 < a_end; a0 += kChunk) {
         const int na = min(kChunk, a_end - a0);
         __syncthreads();
@@ -356,7 +367,7 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
         }
         __syncthreads();
         // one warp per staged angle, lanes along its window (no division)
-        for (int k = threadIdx.x >> 5; k < na; k += kBThreads / 32) {
+        for (int k = threadIdx.x >> 5; k < na; k += kThr / 32) {
             const int org = __float_as_int(s_par[k].w);
             const T *brow = b + (size_t)(a0 + k) * n_det;
             float2 *dst = s_pairs + k * W;
@@ -375,18 +386,18 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
 #pragma unroll 2
         for (int k = 0; k < na; ++k, sb += 8u * (unsigned)W) {
             const float4 p = s_par[k];
-            const float du = 8.0f * p.y;
-            float u[kBRows];
+            const float du = (float)kRT * p.y;
+            float u[kRows];
             u[0] = fmaf(fdi, p.y, fmaf(fdj, p.x, p.z));
 #pragma unroll
-            for (int r = 1; r < kBRows; ++r) u[r] = u[r - 1] + du;
-            float tt[kBRows], ff[kBRows];
+            for (int r = 1; r < kRows; ++r) u[r] = u[r - 1] + du;
+            float tt[kRows], ff[kRows];
 #pragma unroll
-            for (int r = 0; r < kBRows; r += 2) floor_frac2(u[r], u[r + 1], tt[r], tt[r + 1], ff[r], ff[r + 1]);
+            for (int r = 0; r < kRows; r += 2) floor_frac2(u[r], u[r + 1], tt[r], tt[r + 1], ff[r], ff[r + 1]);
             float4 wt = make_float4(0.f, 0.f, 0.f, 0.f);
             if constexpr (kModel != 0) wt = s_wt[k];
 #pragma unroll
-            for (int r = 0; r < kBRows; ++r) {
+            for (int r = 0; r < kRows; ++r) {
                 const float f = ff[r];
                 const float2 pr =
                     *static_cast<const float2 *>(__cvta_shared_to_generic(sb + (__float_as_uint(tt[r]) << 3)));
@@ -405,29 +416,33 @@ __device__ __forceinline__ void pixel_back_tile(const T *__restrict__ b, int N, 
         }
     }
 #pragma unroll
-    for (int r = 0; r < kBRows; ++r) s_part[r][threadIdx.x] = acc[r];
+    for (int r = 0; r < kRows; ++r) s_part[r][threadIdx.x] = acc[r];
     cluster.sync();
-    // this CTA finishes row group `rank` of every thread: pixel row di + 8 rank
-    float sum = 0.0f;
+    // this CTA finishes row groups rank, rank + kBSplit, ... of every
+    // thread: pixel rows di + kRT r
 #pragma unroll
-    for (int q = 0; q < kBSplit; ++q)
-        sum += cluster.map_shared_rank(&s_part[rank][0], q)[threadIdx.x];
-    const int i = i0 + di + 8 * rank, j = j0 + dj;
-    if (i < N && j < N) {
-        const size_t p = (size_t)i * N + j;
-        x[p] = add ? sum + add[p] : sum;
+    for (int r = rank; r < kRows; r += kBSplit) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kBSplit; ++q)
+            sum += cluster.map_shared_rank(&s_part[r][0], q)[threadIdx.x];
+        const int i = i0 + di + kRT * r, j = j0 + dj;
+        if (i < N && j < N) {
+            const size_t p = (size_t)i * N + j;
+            x[p] = add ? sum + add[p] : sum;
+        }
     }
     cluster.sync();   // peers' shared memory must outlive the reads above
 }
 
 // bc: the input is column bc of a basis (b + col_offset(bc)), or b itself.
 template <typename T, int kChunk>
-__global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
+__global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(back_threads<kBRowsTiled>())
 pixel_back_tiled_kernel(const T *__restrict__ b, ColRef bc, int N, int n_angles, int n_det,
                         const BackAngle *__restrict__ tab, int W, const float *__restrict__ add,
                         float *__restrict__ x) {
-    pixel_back_tile<T, 0, kChunk>(b + col_offset(bc), N, n_angles, n_det, tab, W, add, x, blockIdx.x,
-                                  blockIdx.y);
+    pixel_back_tile<T, 0, kChunk, kBRowsTiled>(b + col_offset(bc), N, n_angles, n_det, tab, W, add, x,
+                                               blockIdx.x, blockIdx.y);
 }
 
 // A^T (kModel 1) or B_tau (kModel 2) with the tiled design above.
@@ -836,7 +851,7 @@ void launch_back_tiled(const T *b, ColRef bc, int N, int n_angles, int n_det, co
                        int window, const float *add, float *x, cudaStream_t st) {
     const size_t smem = sizeof(float2) * (size_t)kChunk * window;
     const dim3 grid((N + kBT - 1) / kBT, (N + kBT - 1) / kBT, kBSplit);
-    pixel_back_tiled_kernel<T, kChunk><<<grid, kBThreads, smem, st>>>(b, bc, N, n_angles, n_det, tab,
+    pixel_back_tiled_kernel<T, kChunk><<<grid, back_threads<kBRowsTiled>(), smem, st>>>(b, bc, N, n_angles, n_det, tab,
                                                                       window, add, x);
 }
 
