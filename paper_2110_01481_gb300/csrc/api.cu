@@ -1551,3 +1551,5 @@ const char *ctg_status_string(int status) {
 }
 
 }  // extern "C"
+
+long long ctg_ctx_wait_limit(const ctg_ctx *ctx) { return ctx ? ctx->spin_limit : kCtgDefaultSpinLimit; }

@@ -550,12 +550,11 @@ batch_update_scale_kernel(BatchInst *__restrict__ insts, const int2 *__restrict_
 // pack_cap (pack_cap + 1) / 2 doubles).
 constexpr int kBatchGivStage = 1024;   // = the batches' largest maxit
 
-__global__ void batch_givens_kernel(BatchInst *__restrict__ insts, int pack_cap) {
-    extern __shared__ double s_pack[];
-    __shared__ double s_h[kBatchGivStage + 1], s_gc[kBatchGivStage], s_gs[kBatchGivStage];
-    BatchInst &I = insts[blockIdx.x];
-    if (!I.active) return;
-    const int k = I.k, lane = threadIdx.x, ldr = I.maxit;
+// The update of instance I by one warp, its column, rotations and rotated
+// column staged in s_h (k + 1), s_gc, s_gs (k - 1 each).
+__device__ void batch_givens_warp(BatchInst &I, double *s_h, double *s_gc, double *s_gs, double *s_pack,
+                                  int pack_cap) {
+    const int k = I.k, lane = threadIdx.x & 31, ldr = I.maxit;
     const double *h = I.H + (size_t)(k - 1) * (I.maxit + 1);
     double *Rk = I.R + (size_t)(k - 1) * ldr;         // column k of R
     for (int i = lane; i <= k; i += 32) s_h[i] = h[i];
@@ -590,6 +589,113 @@ __global__ void batch_givens_kernel(BatchInst *__restrict__ insts, int pack_cap)
     for (int i = lane; i < k; i += 32) Rk[i] = s_h[i];
     __syncwarp();
     if (I.variant == CTG_BA && I.target > 0.0) solve_y_warp(I.R, ldr, I.gg, k, I.y, s_pack, pack_cap);
+}
+
+__global__ void batch_givens_kernel(BatchInst *__restrict__ insts, int pack_cap) {
+    extern __shared__ double s_pack[];
+    __shared__ double s_h[kBatchGivStage + 1], s_gc[kBatchGivStage], s_gs[kBatchGivStage];
+    BatchInst &I = insts[blockIdx.x];
+    if (!I.active) return;
+    batch_givens_warp(I, s_h, s_gc, s_gs, s_pack, pack_cap);
+}
+
+// The batched one-launch CGS2 step (as cgs2_fused_kernel) for every active
+// instance of the map's launch, with each instance's Givens update in its
+// block 0: E = kBatchFusedE float4 groups per thread, batch_fused_blocks(L)
+// blocks per instance; the grid barriers span the whole launch (bar[0]:
+// arrivals, zero at launch, reset by the last block out; *err: set by a
+// wait that gave up; *spin: the polls a wait may take), and the blocks of
+// inactive instances only take part in them.  Each instance's partial rows ([0, k] pass 1, [k+1, 2k+1] pass 2)
+// are its own, and every block of an instance sums them in the same fixed
+// order.  Shared memory for k <= kcap: Givens staging (3 kcap + 1
+// doubles), the packed R for y_k (pack_cap), h1, h2, coefficients and the
+// warps' partial sums.  After a timed-out barrier the block leaves with
+// *err set; the round's stopping rules then end the batch.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2)
+batch_cgs2_fused_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ map, unsigned *__restrict__ bar,
+                        int *__restrict__ err, const long long *__restrict__ spin, int kcap, int pack_cap) {
+    constexpr int E = kBatchFusedE;
+    const long long spin_limit = *spin;
+    const int2 mp = map[blockIdx.x];
+    BatchInst &I = insts[mp.x];
+    const bool on = I.active != 0;
+    const int k = on ? I.k : 0;
+    extern __shared__ double smem_d[];
+    double *s_stage = smem_d;                                        // 3 kcap + 1
+    double *s_pack = s_stage + 3 * kcap + 1;                         // pack_cap (pack_cap + 1) / 2
+    double *s_h1 = s_pack + pack_cap * (pack_cap + 1) / 2;           // kcap + 1
+    double *s_h2 = s_h1 + kcap + 1;                                  // kcap + 2
+    float *s_c = reinterpret_cast<float *>(s_h2 + kcap + 2);         // kcap
+    float *s_w = s_c + kcap;                                         // kWarps (kcap + 1)
+    const int tid = threadIdx.x, G = gridDim.x;
+    const int Gi = batch_fused_blocks(I.L), Gpi = padded_grid(Gi);
+    const T *W = static_cast<const T *>(I.W);
+    float *q = I.variant == CTG_AB ? I.vm : I.vn;
+    const int64_t L = I.L, ldw = I.ldw;
+    const int64_t g0 = (int64_t)mp.y * kThreads * E + tid;
+    float4 qv[E];
+    if (on) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) qv[e] = ld4_rw(q, g0 + (int64_t)e * kThreads, L);
+        dots_slice<T, E, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
+        __syncthreads();
+        write_rows(s_w, k + 1, 0, I.partials, Gpi, mp.y);
+    }
+    bool ok = grid_barrier(bar, (unsigned)G, spin_limit, err);
+    if (on && ok) {
+        reduce_rows(I.partials, 0, k + 1, Gi, Gpi, s_h1);
+        __syncthreads();
+        for (int j = tid; j < k; j += kThreads) s_c[j] = (float)s_h1[j];
+        __syncthreads();
+        update_slice<T, E>(W, ldw, k, s_c, g0, L, qv);
+        dots_slice<T, E, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
+        __syncthreads();
+        write_rows(s_w, k + 1, k + 1, I.partials, Gpi, mp.y);
+    }
+    if (ok) ok = grid_barrier(bar, 2u * (unsigned)G, spin_limit, err);
+    if (!ok) return;
+    if (on) {
+        reduce_rows(I.partials, k + 1, k + 1, Gi, Gpi, s_h2);
+        __syncthreads();
+        for (int j = tid; j < k; j += kThreads) s_c[j] = (float)s_h2[j];
+        if (tid < 32) {
+            double t = 0.0;
+            for (int j = tid; j < k; j += 32) t = fma(s_h2[j], s_h2[j], t);
+            t = warp_sum_d(t);
+            if (tid == 0) s_h2[k + 1] = fmax(0.0, s_h2[k] - t);
+        }
+        __syncthreads();
+        update_slice<T, E>(W, ldw, k, s_c, g0, L, qv);
+        const double nrm2 = s_h2[k + 1];
+        const float inv = nrm2 > 0.0 ? (float)(1.0 / sqrt(nrm2)) : 0.0f;
+        T *w_out = const_cast<T *>(W) + (size_t)k * ldw;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int64_t g = g0 + (int64_t)e * kThreads;
+            st4(q, g, L, qv[e]);
+            stw4(w_out, g, L, make_float4(qv[e].x * inv, qv[e].y * inv, qv[e].z * inv, qv[e].w * inv));
+        }
+        if (mp.y == 0) {
+            double *h_out = I.H + (size_t)(k - 1) * (I.maxit + 1);
+            for (int j = tid; j < k; j += kThreads) {
+                h_out[j] = s_h1[j] + s_h2[j];
+                I.h1[j] = s_h1[j];
+                I.h2[j] = s_h2[j];
+            }
+            if (tid == 0) {
+                h_out[k] = sqrt(nrm2);
+                I.h1[k] = s_h1[k];
+                I.scal[1] = nrm2;
+            }
+        }
+    }
+    // the last block out resets the barrier counter for the next launch
+    if (tid == 0 && atomicAdd(bar, 1u) == 3u * (unsigned)G - 1u) atomicExch(bar, 0u);
+    if (on && mp.y == 0) {
+        __syncthreads();                            // the column is written
+        if (tid < 32) batch_givens_warp(I, s_stage, s_stage + kcap + 1, s_stage + 2 * kcap + 1, s_pack, pack_cap);
+    }
 }
 
 // BA with the discrepancy stop: x_k = x0 + W_k y_k into the solve's x
@@ -662,10 +768,24 @@ __global__ void batch_finish_kernel(BatchInst *__restrict__ insts, int n, int *a
 // max_rounds rounds have run (every instance stops by its maxit, so the
 // second condition only guards the first).
 __global__ void batch_finish_loop_kernel(BatchInst *__restrict__ insts, int n, int *ctl, int max_rounds,
-                                         cudaGraphConditionalHandle h) {
+                                         cudaGraphConditionalHandle h, cudaGraphConditionalHandle h_next,
+                                         int fused_max) {
+    __shared__ int s_beyond;
+    if (threadIdx.x == 0) s_beyond = 0;
+    __syncthreads();
+    const bool timed_out = atomicAdd(&ctl[3], 0) != 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         BatchInst &I = insts[i];
         if (!I.active) continue;
+        if (timed_out) {
+            // a fused step gave up at a barrier: every solve stops here (the
+            // host reports the timeout)
+            I.active = 0;
+            I.iters = I.k - 1;
+            I.stop_reason = CTG_STOP_MAXIT;
+            atomicSub(&ctl[0], 1);
+            continue;
+        }
         const int k = I.k;
         const bool dp = I.target > 0.0;
         if (I.variant == CTG_BA && dp) I.resnorm = sqrt(I.scal[4]);
@@ -681,12 +801,18 @@ __global__ void batch_finish_loop_kernel(BatchInst *__restrict__ insts, int n, i
             atomicSub(&ctl[0], 1);
         } else {
             I.k = k + 1;
+            if (fused_max > 0 && k + 1 > fused_max) s_beyond = 1;
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         const int r = ++ctl[1];
-        if (atomicAdd(&ctl[0], 0) <= 0 || r >= max_rounds) cudaGraphSetConditional(h, 0u);
+        if (atomicAdd(&ctl[0], 0) <= 0 || r >= max_rounds || timed_out) {
+            cudaGraphSetConditional(h, 0u);
+            if (h_next) cudaGraphSetConditional(h_next, 0u);
+        } else if (s_beyond) {
+            cudaGraphSetConditional(h, 0u);
+        }
     }
 }
 
@@ -700,8 +826,7 @@ __global__ void batch_solve_y_kernel(BatchInst *__restrict__ insts, int pack_cap
 
 template <typename K>
 cudaError_t ensure_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return ctg_allow_dyn_smem((const void *)kernel, bytes);
 }
 
 // k: the step's k, or (kdev set) the largest k the launch may see, which
@@ -910,11 +1035,8 @@ cudaError_t launch_fused(const T *W, int64_t ldw, int64_t L, int k, float *q, T 
     const int kcap = ls ? ls->kmax : k;
     const int giv_mode = ls && ls->lb ? ls->giv_mode : -1;
     const size_t smem = fused_smem_bytes(kcap, giv_mode);
-    if (smem > 48 * 1024) {
-        const cudaError_t ea = cudaFuncSetAttribute(cgs2_fused_kernel<T, E>,
-                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (ea != cudaSuccess) return ea;
-    }
+    const cudaError_t ea = ctg_allow_dyn_smem((const void *)cgs2_fused_kernel<T, E>, smem);
+    if (ea != cudaSuccess) return ea;
     const LoopBufs lb = ls && ls->lb ? *ls->lb : LoopBufs{};
     const int pack_cap = loop_pack_cap(kcap);
     cudaLaunchConfig_t cfg = {};
@@ -1215,10 +1337,74 @@ cudaError_t ctg_batch_finish(BatchInst *insts, int n_inst, int *active_count, cu
 }
 
 cudaError_t ctg_batch_finish_loop(BatchInst *insts, int n_inst, int *ctl, int max_rounds,
-                                  cudaGraphConditionalHandle h, cudaStream_t st) {
+                                  cudaGraphConditionalHandle h, cudaStream_t st,
+                                  cudaGraphConditionalHandle h_next, int fused_max) {
     if (n_inst <= 0 || n_inst > 1024) return cudaErrorInvalidValue;
-    batch_finish_loop_kernel<<<1, n_inst < 128 ? 128 : 1024, 0, st>>>(insts, n_inst, ctl, max_rounds, h);
+    batch_finish_loop_kernel<<<1, n_inst < 128 ? 128 : 1024, 0, st>>>(insts, n_inst, ctl, max_rounds, h,
+                                                                        h_next, fused_max);
     return cudaGetLastError();
+}
+
+namespace {
+
+size_t batch_fused_smem(int kcap) {
+    const int pc = kcap;
+    return sizeof(double) * ((size_t)3 * kcap + 1 + (size_t)pc * (pc + 1) / 2 + (size_t)2 * kcap + 3) +
+           sizeof(float) * ((size_t)kcap + (size_t)kWarps * (kcap + 1));
+}
+
+template <typename T>
+int batch_fused_resident_t(int kcap) {
+    int dev = -1, per_sm = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        ensure_smem(batch_cgs2_fused_kernel<T>, batch_fused_smem(kcap)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_cgs2_fused_kernel<T>, kThreads,
+                                                      batch_fused_smem(kcap)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * sms;
+}
+
+template <typename T>
+cudaError_t launch_batch_fused(BatchInst *insts, const int2 *map, int nblocks, int kcap, unsigned *bar, int *err,
+                               const long long *spin_limit, cudaStream_t st) {
+    const size_t smem = batch_fused_smem(kcap);
+    cudaError_t e = ensure_smem(batch_cgs2_fused_kernel<T>, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_cgs2_fused_kernel<T>, insts, map, bar, err, spin_limit, kcap, kcap);
+}
+
+}  // namespace
+
+int ctg_batch_fused_max_k() { return kFusedMaxK; }
+
+int ctg_batch_fused_resident(int kcap, int wtype) {
+    if (kcap < 1 || kcap > kFusedMaxK) return 0;
+    if (wtype == CTG_BASIS_BF16) return batch_fused_resident_t<__nv_bfloat16>(kcap);
+    if (wtype == CTG_BASIS_FP16) return batch_fused_resident_t<__half>(kcap);
+    return batch_fused_resident_t<float>(kcap);
+}
+
+cudaError_t ctg_batch_cgs2_fused(BatchInst *insts, const int2 *map, int nblocks, int kcap, unsigned *bar,
+                                 int *err, const long long *spin_limit, cudaStream_t st, int wtype) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (kcap < 1 || kcap > kFusedMaxK) return cudaErrorInvalidValue;
+    if (wtype == CTG_BASIS_BF16)
+        return launch_batch_fused<__nv_bfloat16>(insts, map, nblocks, kcap, bar, err, spin_limit, st);
+    if (wtype == CTG_BASIS_FP16) return launch_batch_fused<__half>(insts, map, nblocks, kcap, bar, err, spin_limit, st);
+    return launch_batch_fused<float>(insts, map, nblocks, kcap, bar, err, spin_limit, st);
 }
 
 cudaError_t ctg_batch_solve_y(BatchInst *insts, int n_inst, int max_k, cudaStream_t st) {

@@ -121,7 +121,12 @@ size_t plan_instance(InstPlan &p, char *base) {
     d.mt = g.back_model != CTG_BACK_PIXEL ? (const MatchedAngle *)take(sizeof(MatchedAngle) * g.n_angles)
                                           : nullptr;
     d.back_thr = 0.0f;
-    d.partials = (float *)take(sizeof(float) * (size_t)(maxit + 3) * Gp);
+    // partial rows: maxit + 3 rows of the E = 1 passes, or 2 k + 2 rows of
+    // the fused step (k <= its largest k) over its blocks
+    const int kf = maxit < ctg_batch_fused_max_k() ? maxit : ctg_batch_fused_max_k();
+    const size_t rows_pass = (size_t)(maxit + 3) * Gp;
+    const size_t rows_fused = (size_t)(2 * kf + 2) * padded4(batch_fused_blocks(L));
+    d.partials = (float *)take(sizeof(float) * (rows_pass > rows_fused ? rows_pass : rows_fused));
     d.h1 = (double *)take(sizeof(double) * (maxit + 3));
     d.h2 = (double *)take(sizeof(double) * (maxit + 3));
     d.scal = (double *)take(sizeof(double) * 8);
@@ -238,8 +243,11 @@ void release(ctg_batch *b) {
 //     DP stop: x_k = x0 + W_k y_k; BA: stage w_{k+1} (and x_k), t_{k+1} =
 //     A w_{k+1} (and A x_k); BA with the DP stop: ||b - A x_k||; the
 //     stopping rules.
+// MB_CGSF*: the blocks of the one-launch CGS2 step with the Givens update
+// (batch_fused_blocks per instance), used instead of MB_CGS* and the
+// separate Givens launch while every step is at most fused_kcap.
 enum { MB_BACK, MB_B16, MB_H16, MB_PAD_AB, MB_FWD_AB, MB_CGS, MB_CGS_B16, MB_CGS_H16,
-       MB_ITER, MB_PAD_BA, MB_FWD_BA, MB_RES, MB_COUNT };
+       MB_ITER, MB_PAD_BA, MB_FWD_BA, MB_RES, MB_CGSF, MB_CGSF_B16, MB_CGSF_H16, MB_COUNT };
 struct RoundSpec {
     BatchInst *insts;
     int n_inst;
@@ -248,6 +256,13 @@ struct RoundSpec {
     int max_window, max_maxit;
     int *d_active;
     int fwd_shape_ab, fwd_shape_ba;   // forward shapes of the two forward launches
+    // the fused step: its largest k (0: the batch takes the separate
+    // passes only), and in device memory the barrier counter, the timeout
+    // word and the wait limit
+    int fused_kcap;
+    unsigned *bar;
+    int *err;
+    const long long *spin;
 };
 
 // Build the block maps of instances `ids` (indices into the instance array).
@@ -316,6 +331,26 @@ void build_maps(const Plans &plans, const std::vector<int> &ids, std::vector<int
     add(MB_RES, [&](const InstPlan &p) {
         return ba_dp(p) ? ctg_vec_blocks((long long)p.g.n_angles * p.g.n_det) : 0;
     });
+    auto fused_blocks = [](const InstPlan &p, int wtype) {
+        if (p.o.basis_dtype != wtype) return 0;
+        return batch_fused_blocks(p.variant == CTG_BA ? (long long)p.g.N * p.g.N
+                                                      : (long long)p.g.n_angles * p.g.n_det);
+    };
+    add(MB_CGSF, [&](const InstPlan &p) { return fused_blocks(p, CTG_BASIS_FP32); });
+    add(MB_CGSF_B16, [&](const InstPlan &p) { return fused_blocks(p, CTG_BASIS_BF16); });
+    add(MB_CGSF_H16, [&](const InstPlan &p) { return fused_blocks(p, CTG_BASIS_FP16); });
+}
+
+// The largest k of the fused step for a batch whose maps are in rs (0 when
+// a fused launch's blocks would not all be resident at once: the batch
+// then takes the separate passes throughout).
+int fused_kcap_of(const RoundSpec &rs, int max_maxit) {
+    const int kcap = max_maxit < ctg_batch_fused_max_k() ? max_maxit : ctg_batch_fused_max_k();
+    const int which[3] = {MB_CGSF, MB_CGSF_B16, MB_CGSF_H16};
+    const int types[3] = {CTG_BASIS_FP32, CTG_BASIS_BF16, CTG_BASIS_FP16};
+    for (int t = 0; t < 3; ++t)
+        if (rs.len[which[t]] > 0 && rs.len[which[t]] > ctg_batch_fused_resident(kcap, types[t])) return 0;
+    return kcap;
 }
 
 // Which launches a round makes (a launcher skips a phase with no blocks):
@@ -330,8 +365,11 @@ unsigned round_signature(const RoundSpec &r) {
 // Enqueue one round's launches on st (ending it with the stopping rules;
 // inside a while-loop body, loop_ctl and the loop's handle end the loop
 // when no solve is left).
+// fused: the round's CGS2 step and Givens update by the one-launch kernel
+// (steps <= r.fused_kcap); h_next: the while loop that follows this one.
 cudaError_t enqueue_round(const RoundSpec &r, cudaStream_t st, int *loop_ctl = nullptr,
-                          cudaGraphConditionalHandle h = 0) {
+                          cudaGraphConditionalHandle h = 0, bool fused = false,
+                          cudaGraphConditionalHandle h_next = 0) {
     cudaError_t e = cudaSuccess;
     const int2 *M = r.maps;
     auto map = [&](int w) { return M + r.off[w]; };
@@ -343,19 +381,29 @@ cudaError_t enqueue_round(const RoundSpec &r, cudaStream_t st, int *loop_ctl = n
     if (e == cudaSuccess) e = ctg_batch_pad(r.insts, map(MB_PAD_AB), r.len[MB_PAD_AB], CTG_AB, st);
     if (e == cudaSuccess)
         e = ctg_batch_forward(r.insts, map(MB_FWD_AB), r.len[MB_FWD_AB], CTG_AB, st, r.fwd_shape_ab);
-    if (e == cudaSuccess) e = ctg_batch_cgs2(r.insts, map(MB_CGS), r.len[MB_CGS], r.max_maxit, st);
-    if (e == cudaSuccess)
-        e = ctg_batch_cgs2(r.insts, map(MB_CGS_B16), r.len[MB_CGS_B16], r.max_maxit, st, CTG_BASIS_BF16);
-    if (e == cudaSuccess)
-        e = ctg_batch_cgs2(r.insts, map(MB_CGS_H16), r.len[MB_CGS_H16], r.max_maxit, st, CTG_BASIS_FP16);
-    if (e == cudaSuccess) e = ctg_batch_givens(r.insts, r.n_inst, r.max_maxit, st);
+    if (fused) {
+        const int which[3] = {MB_CGSF, MB_CGSF_B16, MB_CGSF_H16};
+        const int types[3] = {CTG_BASIS_FP32, CTG_BASIS_BF16, CTG_BASIS_FP16};
+        for (int t = 0; t < 3 && e == cudaSuccess; ++t)
+            e = ctg_batch_cgs2_fused(r.insts, map(which[t]), r.len[which[t]], r.fused_kcap, r.bar, r.err, r.spin,
+                                     st, types[t]);
+    } else {
+        if (e == cudaSuccess) e = ctg_batch_cgs2(r.insts, map(MB_CGS), r.len[MB_CGS], r.max_maxit, st);
+        if (e == cudaSuccess)
+            e = ctg_batch_cgs2(r.insts, map(MB_CGS_B16), r.len[MB_CGS_B16], r.max_maxit, st, CTG_BASIS_BF16);
+        if (e == cudaSuccess)
+            e = ctg_batch_cgs2(r.insts, map(MB_CGS_H16), r.len[MB_CGS_H16], r.max_maxit, st, CTG_BASIS_FP16);
+        if (e == cudaSuccess) e = ctg_batch_givens(r.insts, r.n_inst, r.max_maxit, st);
+    }
     if (e == cudaSuccess) e = ctg_batch_iterate(r.insts, map(MB_ITER), r.len[MB_ITER], r.max_maxit, st);
     if (e == cudaSuccess) e = ctg_batch_pad(r.insts, map(MB_PAD_BA), r.len[MB_PAD_BA], CTG_BA, st);
     if (e == cudaSuccess)
         e = ctg_batch_forward(r.insts, map(MB_FWD_BA), r.len[MB_FWD_BA], CTG_BA, st, r.fwd_shape_ba);
     if (e == cudaSuccess) e = ctg_batch_residual(r.insts, map(MB_RES), r.len[MB_RES], st);
     if (e == cudaSuccess) {
-        if (loop_ctl) e = ctg_batch_finish_loop(r.insts, r.n_inst, loop_ctl, r.max_maxit, h, st);
+        if (loop_ctl)
+            e = ctg_batch_finish_loop(r.insts, r.n_inst, loop_ctl, r.max_maxit, h, st, h_next,
+                                      fused ? r.fused_kcap : 0);
         else e = ctg_batch_finish(r.insts, r.n_inst, r.d_active, st);
     }
     return e;
@@ -388,7 +436,10 @@ int capture_round(const RoundSpec &r, cudaStream_t st, cudaGraphExec_t *out, uns
 // Capture the whole iteration of a batch as one graph: a while-loop node
 // whose body is a round, ended on the device by the round's stopping-rule
 // kernel (loop_ctl: active solves, rounds run), so no host check runs
-// between rounds.  st captures, bs the body.
+// between rounds.  With the fused step (r.fused_kcap > 0) two while loops
+// follow each other: rounds with the one-launch CGS2 step until a solve's
+// next step is beyond fused_kcap, then rounds with the separate passes (the
+// first loop ends both once no solve is left).  st captures, bs the bodies.
 int capture_loop(const RoundSpec &r, cudaStream_t st, cudaStream_t bs, int *loop_ctl, cudaGraphExec_t *out) {
     if (r.n_inst > 1024) return CTG_ERR_INVALID_ARG;
     B_CK(ctg_batch_prepare(r.max_maxit));
@@ -396,29 +447,36 @@ int capture_loop(const RoundSpec &r, cudaStream_t st, cudaStream_t bs, int *loop
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t ndeps = 0;
-    cudaGraphConditionalHandle h = 0;
-    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 1u, cudaGraphCondAssignDefault);
-    cudaGraphNodeParams cp = {};
-    cudaGraphNode_t node;
-    if (e == cudaSuccess) {
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        e = cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp);
-    }
-    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-    if (e == cudaSuccess) {
-        e = cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeRelaxed);
+    const int nloops = r.fused_kcap > 0 ? 2 : 1;
+    cudaGraphConditionalHandle h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, nullptr, nullptr, nullptr);
+    for (int l = 0; l < nloops && e == cudaSuccess; ++l)
+        e = cudaGraphConditionalHandleCreate(&h[l], cg, 1u, cudaGraphCondAssignDefault);
+    for (int l = 0; l < nloops && e == cudaSuccess; ++l) {
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+        cudaGraphNodeParams cp = {};
+        cudaGraphNode_t node;
         if (e == cudaSuccess) {
-            e = enqueue_round(r, bs, loop_ctl, h);
-            cudaGraph_t body = nullptr;
-            const cudaError_t e2 = cudaStreamEndCapture(bs, &body);
-            if (e == cudaSuccess) e = e2;
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h[l];
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            e = cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp);
+        }
+        if (e == cudaSuccess)
+            e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess) {
+            e = cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                const bool fused = nloops == 2 && l == 0;
+                e = enqueue_round(r, bs, loop_ctl, h[l], fused, fused ? h[1] : 0);
+                cudaGraph_t body = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(bs, &body);
+                if (e == cudaSuccess) e = e2;
+            }
         }
     }
     const cudaError_t e3 = cudaStreamEndCapture(st, &graph);
@@ -483,7 +541,10 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
     if (rc == CTG_OK && !maps.empty())
         rc = ck(cudaMemcpy(b->d_maps, maps.data(), sizeof(int2) * maps.size(), cudaMemcpyHostToDevice));
     if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_insts, sizeof(BatchInst) * n));
-    if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_active, 2 * sizeof(int)));   // active solves, rounds run
+    // active solves, rounds run, the fused step's barrier counter and
+    // timeout word, then (8-byte aligned) the wait limit
+    if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_active, 8 * sizeof(int)));
+    if (rc == CTG_OK) rc = ck(cudaMemset(b->d_active, 0, 8 * sizeof(int)));
     if (rc == CTG_OK) rc = ck(cudaMallocHost(&b->h_active, sizeof(int)));
     if (rc == CTG_OK) rc = ck(cudaMallocHost(&b->h_stage, sizeof(double) * 8 * n));
     if (rc == CTG_OK) rc = ck(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
@@ -503,7 +564,11 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
         r.max_window = b->max_window;
         r.max_maxit = b->max_maxit;
         r.d_active = b->d_active;
-        rc = capture_round(r, b->st, &b->round);
+        r.bar = reinterpret_cast<unsigned *>(b->d_active + 2);
+        r.err = b->d_active + 3;
+        r.spin = reinterpret_cast<const long long *>(b->d_active + 4);
+        rc = capture_round(r, b->st, &b->round);   // the host-driven round: separate passes
+        r.fused_kcap = rc == CTG_OK ? fused_kcap_of(r, b->max_maxit) : 0;
         // the whole iteration as one graph; without it the host replays the
         // round graph and checks the active count every few rounds
         if (rc == CTG_OK && capture_loop(r, b->st, b->st_body, b->d_active, &b->loop) != CTG_OK) b->loop = nullptr;
@@ -659,7 +724,9 @@ extern "C" int ctg_batch_solve(ctg_batch *b, const float *const *b_dev, const fl
     B_CK(cudaMemcpyAsync(b->d_insts, hi.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, st));
     *b->h_active = active;
     B_CK(cudaMemcpyAsync(b->d_active, b->h_active, sizeof(int), cudaMemcpyHostToDevice, st));
-    B_CK(cudaMemsetAsync(b->d_active + 1, 0, sizeof(int), st));
+    B_CK(cudaMemsetAsync(b->d_active + 1, 0, 3 * sizeof(int), st));   // rounds, barrier, timeout
+    const long long wait_limit = ctg_ctx_wait_limit(b->ctx);
+    B_CK(cudaMemcpyAsync(b->d_active + 4, &wait_limit, sizeof(long long), cudaMemcpyHostToDevice, st));
     // ---- rounds -----------------------------------------------------------
     if (active > 0 && b->loop) {
         B_CK(cudaGraphLaunch(b->loop, st));
@@ -677,7 +744,11 @@ extern "C" int ctg_batch_solve(ctg_batch *b, const float *const *b_dev, const fl
     // ---- exit: y_k, x_k and its residual -----------------------------------
     B_CK(ctg_batch_solve_y(b->d_insts, n, b->max_maxit, st));
     B_CK(cudaMemcpyAsync(hi.data(), b->d_insts, sizeof(BatchInst) * n, cudaMemcpyDeviceToHost, st));
+    B_CK(cudaMemcpyAsync(b->h_active, b->d_active + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
     B_CK(cudaStreamSynchronize(st));
+    // a fused step gave up at a grid barrier: every solve stopped at its last
+    // completed step, whose iterate is still formed below
+    const bool timed_out = *b->h_active != 0;
     for (int i = 0; i < n; ++i) {
         const int rc = enqueue_finish(b->inst[i], hi[i], b_dev[i], x0_dev ? x0_dev[i] : nullptr,
                                       x_dev[i], &infos[i], b->h_stage + 8 * i, st);
@@ -688,7 +759,7 @@ extern "C" int ctg_batch_solve(ctg_batch *b, const float *const *b_dev, const fl
         if (infos[i].iters > 0) infos[i].resnorm = std::sqrt(b->h_stage[8 * i + 5]);
     B_CK(cudaEventRecord(b->ev_out, st));
     B_CK(cudaStreamWaitEvent(user, b->ev_out, 0));
-    return CTG_OK;
+    return timed_out ? CTG_ERR_TIMEOUT : CTG_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -443,13 +443,47 @@ cudaError_t ctg_batch_iterate(BatchInst *insts, const int2 *map_n, int nblocks, 
 cudaError_t ctg_batch_residual(BatchInst *insts, const int2 *map_m, int nblocks, cudaStream_t st);
 cudaError_t ctg_batch_finish(BatchInst *insts, int n_inst, int *active_count, cudaStream_t st);
 // The stopping rules of a round of a batch's while-loop graph (n_inst <=
-// 1024): ctl[0] active solves, ctl[1] rounds run; ends the loop (handle h)
-// when none is active or after max_rounds rounds.
+// 1024): ctl[0] active solves, ctl[1] rounds run, ctl[3] set when a fused
+// step's wait gave up (every solve then stops).  Ends both loops (handles
+// h and h_next) when no solve is active, after max_rounds rounds or after a
+// timeout; with fused_max > 0 (the loop of fused steps) it also ends loop h
+// alone once an active solve's next step is beyond fused_max.
 cudaError_t ctg_batch_finish_loop(BatchInst *insts, int n_inst, int *ctl, int max_rounds,
-                                  cudaGraphConditionalHandle h, cudaStream_t st);
+                                  cudaGraphConditionalHandle h, cudaStream_t st,
+                                  cudaGraphConditionalHandle h_next = 0, int fused_max = 0);
 // Exit: y = R^{-1} g for the instance's final k.
 cudaError_t ctg_batch_solve_y(BatchInst *insts, int n_inst, int max_k, cudaStream_t st);
 int ctg_vec_blocks(long long L);          // blocks of an E = 1 vector pass over L
+
+// The batched one-launch CGS2 step with each instance's Givens update
+// (steps k <= ctg_batch_fused_max_k()): kBatchFusedE float4 groups per
+// thread, batch_fused_blocks(L) blocks per instance, one cooperative launch
+// per basis type whose blocks must all be resident at once.
+constexpr int kBatchFusedE = 4;
+__host__ __device__ inline int batch_fused_blocks(long long L) {
+    return (int)(((L + 3) / 4 + 256LL * kBatchFusedE - 1) / (256LL * kBatchFusedE));
+}
+int ctg_batch_fused_max_k();
+// Blocks of one fused launch that fit at once for steps up to kcap (0 if
+// the occupancy query fails).
+int ctg_batch_fused_resident(int kcap, int wtype);
+// bar: barrier arrivals (zero at launch), err: set when a bounded wait gave
+// up, spin_limit: the polls a wait may take (device memory, read at
+// launch); kcap: the largest k of the launch (<= ctg_batch_fused_max_k()).
+cudaError_t ctg_batch_cgs2_fused(BatchInst *insts, const int2 *map, int nblocks, int kcap, unsigned *bar,
+                                 int *err, const long long *spin_limit, cudaStream_t st,
+                                 int wtype = CTG_BASIS_FP32);
+// Allow `bytes` of dynamic shared memory for a kernel: set only when its
+// static and dynamic shared memory together pass the default 48 KB.
+inline cudaError_t ctg_allow_dyn_smem(const void *kernel, size_t bytes) {
+    cudaFuncAttributes a;
+    const cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    if (a.sharedSizeBytes + bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+// The context's bounded-wait limit (ctg_set_wait_limit).
+long long ctg_ctx_wait_limit(const ctg_ctx *ctx);
 
 // ---- host helpers shared by api.cu and batch.cu --------------------------
 bool ctg_geom_valid(const ctg_geom *g);

@@ -153,10 +153,7 @@ __global__ void loop_final_kernel(LoopBufs B) {
 }
 
 int ensure_dyn_smem(const void *kern, size_t bytes) {
-    if (bytes <= 48 * 1024) return 0;
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess
-               ? 0
-               : -1;
+    return ctg_allow_dyn_smem(kern, bytes) == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace

@@ -94,7 +94,12 @@ def test_engine_matches_batch_and_single(P, oracle_mod):
         assert _submit(eng, r, bs[i], i) == i
     got = dict(eng.drain(rounds=4))
     for i, r in enumerate(reqs):
-        assert got[i].iters == batch[i].iters and torch.equal(got[i].x, batch[i].x)
+        # the batch takes the one-launch CGS2 step up to k = 64, the engine
+        # the separate passes: the same stop, the iterate to the rounding of
+        # the CGS2 sums
+        assert got[i].iters == batch[i].iters and got[i].stop_reason == batch[i].stop_reason
+        d = (got[i].x - batch[i].x).double().norm() / batch[i].x.double().norm()
+        assert d.item() <= 1e-5, (i, d.item())
         if r["noise_norm"]:
             fn = P.ab_gmres if r["variant"] == "ab" else P.ba_gmres
             ref = fn(r["geometry"], bs[i], r["maxit"], tau=1.02, noise_norm=r["noise_norm"])
