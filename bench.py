@@ -368,24 +368,21 @@ def batch_problems(P, torch, dev, count, seed0=3000):
     return probs, bs, truths
 
 
-def run_batch(args):
-    """Batched engine vs the plain one-at-a-time solves on the same
-    instances: aggregate iterations/s and the reconstruction error of each."""
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2110_01481_gb300 as P
-    dev = torch.device("cuda", 0)
-    probs, bs, truths = batch_problems(P, torch, dev, args.batch_size)
+def batched_workload(P, torch, dev, count, steps):
+    """The batched workload (`count` instances of batch_problems) through
+    ctg_batch_solve against the same solves one at a time through the
+    single-solve path: aggregate iterations/s and each result's error vs
+    x_true (wall clock around whole solves, inputs resident)."""
+    probs, bs, truths = batch_problems(P, torch, dev, count)
     batch = P.Batch(probs)
     outs = [torch.empty(p["geometry"].n, device=dev) for p in probs]
     batch.solve(bs, outs=outs)                    # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         rb = batch.solve(bs, outs=outs)
     torch.cuda.synchronize()
-    t_batch = (time.perf_counter() - t0) / args.steps
+    t_batch = (time.perf_counter() - t0) / steps
     err_b = [float(np.linalg.norm(o.double().cpu().numpy() - t) / np.linalg.norm(t))
              for o, t in zip(outs, truths)]
     # plain method: the single-solve path, one instance after another
@@ -401,16 +398,17 @@ def run_batch(args):
     plain()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         rp = plain()
     torch.cuda.synchronize()
-    t_plain = (time.perf_counter() - t0) / args.steps
+    t_plain = (time.perf_counter() - t0) / steps
     err_p = [float(np.linalg.norm(o.double().cpu().numpy() - t) / np.linalg.norm(t))
              for o, t in zip(outs, truths)]
     it_b, it_p = sum(r.iters for r in rb), sum(r.iters for r in rp)
-    print(json.dumps({
+    return {
         "workload": f"{len(probs)} instances, N in {{128,256,512,1024}}, angles in {{60,180,360,720}}, "
                     "25% limited-angle [0,120), noise 0.5-3%, AB/BA alternating, DP tau=1.02, maxit 100",
+        "steps": steps,
         "batched": {"s_per_batch": t_batch, "iterations": it_b, "iterations_per_s": it_b / t_batch},
         "plain_one_at_a_time": {"s_per_batch": t_plain, "iterations": it_p,
                                 "iterations_per_s": it_p / t_plain},
@@ -418,7 +416,17 @@ def run_batch(args):
         "same_stop_index": sum(int(a.iters == b.iters) for a, b in zip(rb, rp)),
         "mean_rel_error_vs_truth": {"batched": float(np.mean(err_b)), "plain": float(np.mean(err_p))},
         "max_abs_error_difference": float(np.max(np.abs(np.array(err_b) - np.array(err_p)))),
-        "workspace_GB": batch.workspace_bytes / 1e9}))
+        "workspace_GB": batch.workspace_bytes / 1e9}
+
+
+def run_batch(args):
+    """The batched workload alone (`--batch`)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2110_01481_gb300 as P
+    dev = torch.device("cuda", 0)
+    print(json.dumps(batched_workload(P, torch, dev, args.batch_size, args.steps)))
 
 
 def serve_requests(P, torch, dev, count, seed0=5000):
@@ -871,6 +879,9 @@ def run_gpu(args):
         "arnoldi_roofline": arnoldi_roof,
     }
     line["batched_pair"] = batched_pair(P, torch, g, b, enorm, args.steps)
+    if world == 1 and not args.no_batch64:
+        # the 64-instance batched workload, two timed solves of each server
+        line["batched_64"] = batched_workload(P, torch, dev, args.batch_size, 2)
     if world == 1 and not args.no_serve:
         line["serving"] = serving_summary(P, torch, dev, args.serve_quick)
     if world == 1 and not args.no_cpu_baseline:
@@ -1003,6 +1014,8 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="batched engine vs one-at-a-time solves on 64 mixed instances")
     ap.add_argument("--batch-size", type=int, default=64)
+    ap.add_argument("--no-batch64", action="store_true",
+                    help="skip the 64-instance batched workload in the default run")
     ap.add_argument("--methods", action="store_true",
                     help="B = A^T, B_tau, LSQR/LSMR and the NCP stop on the benchmark workload")
     ap.add_argument("--serve", action="store_true",

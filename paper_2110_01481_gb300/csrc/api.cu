@@ -370,9 +370,10 @@ int tune_geometry(GeomEntry *ge) {
     cudaError_t err = cudaMalloc(&pad, sizeof(float) * ge->pl.floats);
     if (err == cudaSuccess) err = cudaMalloc(&bv, sizeof(float) * m);
     if (err == cudaSuccess) err = cudaMalloc(&xv, sizeof(float) * n);
-    if (err == cudaSuccess) err = cudaMemset(pad, 0, sizeof(float) * ge->pl.floats);
-    if (err == cudaSuccess) err = cudaMemset(bv, 0, sizeof(float) * m);
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    // zero inputs, ordered before the timed launches on the same stream
+    if (err == cudaSuccess) err = cudaMemsetAsync(pad, 0, sizeof(float) * ge->pl.floats, st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(bv, 0, sizeof(float) * m, st);
     if (err == cudaSuccess) err = cudaEventCreate(&e0);
     if (err == cudaSuccess) err = cudaEventCreate(&e1);
     auto timed = [&](auto launch, float *us) {
@@ -1371,7 +1372,7 @@ int ctg_project(ctg_ctx *ctx, const ctg_geom *g, const float *x_dev, float *b_de
     if (!ge->pad) {
         const size_t bytes = sizeof(float) * ge->pl.floats;
         CTG_CK(cudaMalloc(&ge->pad, bytes));
-        CTG_CK(cudaMemset(ge->pad, 0, bytes));
+        CTG_CK(cudaMemsetAsync(ge->pad, 0, bytes, st));   // ordered before the staging on st
     }
     CTG_CK(traced(ctx, 3, 1, st, [&] {
         return ctg_launch_pad(x_dev, CTG_BASIS_FP32, ge->pad, g->N, ge->pl, st);
@@ -1553,3 +1554,8 @@ const char *ctg_status_string(int status) {
 }  // extern "C"
 
 long long ctg_ctx_wait_limit(const ctg_ctx *ctx) { return ctx ? ctx->spin_limit : kCtgDefaultSpinLimit; }
+
+void ctg_ctx_forced_tiles(const ctg_ctx *ctx, int *fwd_split, int *back_chunk) {
+    *fwd_split = ctx && ctx->force_fwd_angles ? ctx->force_fwd_split : 0;
+    *back_chunk = ctx ? ctx->force_back_chunk : 0;
+}

@@ -256,6 +256,7 @@ struct RoundSpec {
     int max_window, max_maxit;
     int *d_active;
     int fwd_shape_ab, fwd_shape_ba;   // forward shapes of the two forward launches
+    int back_chunk;                   // angles staged per pass by the back projections (0: 32)
     // the fused step: its largest k (0: the batch takes the separate
     // passes only), and in device memory the barrier counter, the timeout
     // word and the wait limit
@@ -266,8 +267,11 @@ struct RoundSpec {
 };
 
 // Build the block maps of instances `ids` (indices into the instance array).
+// split_ab / split_ba: the AB / BA forward launch may take the shape with
+// several angles per warp (it does when every one of its instances allows it).
 template <typename Plans>
-void build_maps(const Plans &plans, const std::vector<int> &ids, std::vector<int2> &maps, RoundSpec &rs) {
+void build_maps(const Plans &plans, const std::vector<int> &ids, std::vector<int2> &maps, RoundSpec &rs,
+                bool split_ab = true, bool split_ba = true) {
     maps.clear();
     auto add = [&](int which, auto count) {
         rs.off[which] = (int)maps.size();
@@ -298,7 +302,7 @@ void build_maps(const Plans &plans, const std::vector<int> &ids, std::vector<int
                 split = (any ? split : true) && plans[i].fwd && plans[i].fwd->split_ok;
                 any = true;
             }
-        return any && split ? kBatchFwdSplitShape : 0;
+        return any && split && (ab ? split_ab : split_ba) ? kBatchFwdSplitShape : 0;
     };
     rs.fwd_shape_ab = shape_for(true);
     rs.fwd_shape_ba = shape_for(false);
@@ -373,11 +377,12 @@ cudaError_t enqueue_round(const RoundSpec &r, cudaStream_t st, int *loop_ctl = n
     cudaError_t e = cudaSuccess;
     const int2 *M = r.maps;
     auto map = [&](int w) { return M + r.off[w]; };
-    if (e == cudaSuccess) e = ctg_batch_back(r.insts, map(MB_BACK), r.len[MB_BACK], r.max_window, st);
     if (e == cudaSuccess)
-        e = ctg_batch_back(r.insts, map(MB_B16), r.len[MB_B16], r.max_window, st, CTG_BASIS_BF16);
+        e = ctg_batch_back(r.insts, map(MB_BACK), r.len[MB_BACK], r.max_window, st, CTG_BASIS_FP32, r.back_chunk);
     if (e == cudaSuccess)
-        e = ctg_batch_back(r.insts, map(MB_H16), r.len[MB_H16], r.max_window, st, CTG_BASIS_FP16);
+        e = ctg_batch_back(r.insts, map(MB_B16), r.len[MB_B16], r.max_window, st, CTG_BASIS_BF16, r.back_chunk);
+    if (e == cudaSuccess)
+        e = ctg_batch_back(r.insts, map(MB_H16), r.len[MB_H16], r.max_window, st, CTG_BASIS_FP16, r.back_chunk);
     if (e == cudaSuccess) e = ctg_batch_pad(r.insts, map(MB_PAD_AB), r.len[MB_PAD_AB], CTG_AB, st);
     if (e == cudaSuccess)
         e = ctg_batch_forward(r.insts, map(MB_FWD_AB), r.len[MB_FWD_AB], CTG_AB, st, r.fwd_shape_ab);
@@ -490,6 +495,83 @@ int capture_loop(const RoundSpec &r, cudaStream_t st, cudaStream_t bs, int *loop
     return ck(e);
 }
 
+// The batched autotuner: times the launches whose shape the result does
+// not depend on (each ray and each pixel is summed in the same order in
+// every shape): the forward projections with four angles per warp against
+// one, and the back projection with 16, 32 and 64 angles staged per pass.
+// Each candidate runs once untimed and 3 times timed with CUDA events, on
+// the instances' zero buffers at k = 1 (their state is set up again at every
+// solve).  Writes the faster choices.
+int tune_batch(ctg_batch *b, const std::vector<int> &ids, bool tune_fwd, bool tune_back, bool *split_ab,
+               bool *split_ba, int *chunk) {
+    const int n = b->n;
+    std::vector<BatchInst> hi(n);
+    for (int i = 0; i < n; ++i) {
+        hi[i] = b->inst[i].d;
+        hi[i].active = 1;
+        hi[i].k = 1;
+    }
+    B_CK(cudaMemcpy(b->d_insts, hi.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice));
+    std::vector<int2> ms, mp;
+    RoundSpec rs{}, rp{};
+    build_maps(b->inst, ids, ms, rs, true, true);
+    build_maps(b->inst, ids, mp, rp, false, false);
+    int2 *d = nullptr;
+    B_CK(cudaMalloc(&d, sizeof(int2) * (ms.size() + mp.size() + 1)));
+    int rc = ck(cudaMemcpy(d, ms.data(), sizeof(int2) * ms.size(), cudaMemcpyHostToDevice));
+    if (rc == CTG_OK)
+        rc = ck(cudaMemcpy(d + ms.size(), mp.data(), sizeof(int2) * mp.size(), cudaMemcpyHostToDevice));
+    const int2 *ds = d, *dp = d + ms.size();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == CTG_OK) rc = ck(cudaEventCreate(&e0));
+    if (rc == CTG_OK) rc = ck(cudaEventCreate(&e1));
+    auto timed = [&](auto launch) -> float {
+        if (rc != CTG_OK) return 0.0f;
+        rc = ck(launch());
+        if (rc == CTG_OK) rc = ck(cudaEventRecord(e0, b->st));
+        for (int t = 0; t < 3 && rc == CTG_OK; ++t) rc = ck(launch());
+        if (rc == CTG_OK) rc = ck(cudaEventRecord(e1, b->st));
+        if (rc == CTG_OK) rc = ck(cudaEventSynchronize(e1));
+        float ms_ = 0.0f;
+        if (rc == CTG_OK) rc = ck(cudaEventElapsedTime(&ms_, e0, e1));
+        return ms_;
+    };
+    if (tune_fwd) {
+        const int which[2] = {MB_FWD_AB, MB_FWD_BA}, variants[2] = {CTG_AB, CTG_BA};
+        const int shapes[2] = {rs.fwd_shape_ab, rs.fwd_shape_ba};
+        bool *out[2] = {split_ab, split_ba};
+        for (int v = 0; v < 2; ++v) {
+            if (shapes[v] != kBatchFwdSplitShape || rs.len[which[v]] <= 0) continue;
+            const float t_split = timed([&] {
+                return ctg_batch_forward(b->d_insts, ds + rs.off[which[v]], rs.len[which[v]], variants[v], b->st,
+                                         kBatchFwdSplitShape);
+            });
+            const float t_one = timed([&] {
+                return ctg_batch_forward(b->d_insts, dp + rp.off[which[v]], rp.len[which[v]], variants[v], b->st, 0);
+            });
+            *out[v] = t_split <= t_one;
+        }
+    }
+    if (tune_back && rp.len[MB_BACK] > 0) {
+        float best = 0.0f;
+        for (const int c : {32, 16, 64}) {
+            if (!ctg_batch_back_chunk_ok(c, b->max_window)) continue;
+            const float t = timed([&] {
+                return ctg_batch_back(b->d_insts, dp + rp.off[MB_BACK], rp.len[MB_BACK], b->max_window, b->st,
+                                      CTG_BASIS_FP32, c);
+            });
+            if (rc == CTG_OK && (c == 32 || t < best)) {
+                best = t;
+                *chunk = c;
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d);
+    return rc;
+}
+
 }  // namespace
 
 extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
@@ -529,26 +611,22 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
         total = al256(total + p.bytes);
     }
     b->ws_bytes = total;
-    int rc = ck(cudaMalloc(&b->ws, total));
-    if (rc == CTG_OK) rc = ck(cudaMemset(b->ws, 0, total));
-    // block maps
-    std::vector<int2> maps;
+    // everything below is ordered on the batch's own (non-blocking) stream:
+    // a legacy-stream memset of the workspace would not be ordered before
+    // the table uploads on it
+    int rc = ck(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
+    if (rc == CTG_OK) rc = ck(cudaStreamCreateWithFlags(&b->st_body, cudaStreamNonBlocking));
+    if (rc == CTG_OK) rc = ck(cudaMalloc(&b->ws, total));
+    if (rc == CTG_OK) rc = ck(cudaMemsetAsync(b->ws, 0, total, b->st));
     std::vector<int> ids(n);
     for (int i = 0; i < n; ++i) ids[i] = i;
-    RoundSpec spec{};
-    build_maps(b->inst, ids, maps, spec);
-    if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_maps, sizeof(int2) * (maps.empty() ? 1 : maps.size())));
-    if (rc == CTG_OK && !maps.empty())
-        rc = ck(cudaMemcpy(b->d_maps, maps.data(), sizeof(int2) * maps.size(), cudaMemcpyHostToDevice));
     if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_insts, sizeof(BatchInst) * n));
     // active solves, rounds run, the fused step's barrier counter and
     // timeout word, then (8-byte aligned) the wait limit
     if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_active, 8 * sizeof(int)));
-    if (rc == CTG_OK) rc = ck(cudaMemset(b->d_active, 0, 8 * sizeof(int)));
+    if (rc == CTG_OK) rc = ck(cudaMemsetAsync(b->d_active, 0, 8 * sizeof(int), b->st));
     if (rc == CTG_OK) rc = ck(cudaMallocHost(&b->h_active, sizeof(int)));
     if (rc == CTG_OK) rc = ck(cudaMallocHost(&b->h_stage, sizeof(double) * 8 * n));
-    if (rc == CTG_OK) rc = ck(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
-    if (rc == CTG_OK) rc = ck(cudaStreamCreateWithFlags(&b->st_body, cudaStreamNonBlocking));
     if (rc == CTG_OK) rc = ck(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
     if (rc == CTG_OK) rc = ck(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
     for (int i = 0; rc == CTG_OK && i < n; ++i) {
@@ -556,6 +634,22 @@ extern "C" int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms,
         plan_instance(p, b->ws + p.off);
         rc = upload_tables(p, b->st);
     }
+    if (rc == CTG_OK) rc = ck(cudaStreamSynchronize(b->st));
+    // tile shapes: forced on the context, else the batched autotuner's
+    int f_split = 0, f_chunk = 0;
+    ctg_ctx_forced_tiles(ctx, &f_split, &f_chunk);
+    bool split_ab = f_split != 1, split_ba = f_split != 1;
+    int chunk = f_chunk && ctg_batch_back_chunk_ok(f_chunk, b->max_window) ? f_chunk : 32;
+    if (rc == CTG_OK && (!f_split || !f_chunk))
+        rc = tune_batch(b, ids, !f_split, !f_chunk, &split_ab, &split_ba, &chunk);
+    // block maps
+    std::vector<int2> maps;
+    RoundSpec spec{};
+    build_maps(b->inst, ids, maps, spec, split_ab, split_ba);
+    spec.back_chunk = chunk;
+    if (rc == CTG_OK) rc = ck(cudaMalloc(&b->d_maps, sizeof(int2) * (maps.empty() ? 1 : maps.size())));
+    if (rc == CTG_OK && !maps.empty())
+        rc = ck(cudaMemcpy(b->d_maps, maps.data(), sizeof(int2) * maps.size(), cudaMemcpyHostToDevice));
     if (rc == CTG_OK) {
         RoundSpec r = spec;
         r.insts = b->d_insts;
@@ -894,6 +988,9 @@ extern "C" int ctg_engine_create(ctg_ctx *ctx, int32_t max_slots, size_t hbm_bud
     e->h_insts.assign(max_slots, BatchInst{});
     int rc = ck(cudaMalloc(&e->d_insts, sizeof(BatchInst) * max_slots));
     if (rc == CTG_OK) rc = ck(cudaMemset(e->d_insts, 0, sizeof(BatchInst) * max_slots));   // all inactive
+    // the memset ran on the legacy stream; the engine's own stream is not
+    // ordered after it
+    if (rc == CTG_OK) rc = ck(cudaDeviceSynchronize());
     if (rc == CTG_OK) rc = ck(cudaMalloc(&e->d_active, sizeof(int)));
     if (rc == CTG_OK) rc = ck(cudaMallocHost(&e->h_active, sizeof(int)));
     if (rc == CTG_OK) rc = ck(cudaMallocHost(&e->h_stage, sizeof(double) * 8 * max_slots));

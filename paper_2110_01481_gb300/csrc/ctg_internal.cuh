@@ -413,8 +413,11 @@ struct BatchInst {
 // w_k from the round before).  wtype: CTG_BASIS_FP32 launches the kernel
 // for AB instances with an FP32 basis and all BA instances; BF16 / FP16
 // launch it for the AB instances whose basis has that type.
+// chunk: angles staged per pass, 16, 32 or 64 (ctg_batch_back_chunk_ok;
+// otherwise 32); the result does not depend on it.
 cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int max_window,
-                           cudaStream_t st, int wtype = CTG_BASIS_FP32);
+                           cudaStream_t st, int wtype = CTG_BASIS_FP32, int chunk = 32);
+bool ctg_batch_back_chunk_ok(int chunk, int max_window);
 // Staging for the forward projector: AB stages t = B w_k (variant CTG_AB);
 // BA stages w_{k+1}, with x_k interleaved when it has the DP stop
 // (variant CTG_BA).
@@ -484,6 +487,10 @@ inline cudaError_t ctg_allow_dyn_smem(const void *kernel, size_t bytes) {
 }
 // The context's bounded-wait limit (ctg_set_wait_limit).
 long long ctg_ctx_wait_limit(const ctg_ctx *ctx);
+// Tile shapes forced on the context (ctg_set_tiles / ctg_set_fwd_tiles):
+// *fwd_split 0 when the forward shape is not forced, else its angles per
+// warp; *back_chunk 0 when not forced.
+void ctg_ctx_forced_tiles(const ctg_ctx *ctx, int *fwd_split, int *back_chunk);
 
 // ---- host helpers shared by api.cu and batch.cu --------------------------
 bool ctg_geom_valid(const ctg_geom *g);

@@ -505,23 +505,25 @@ pixel_back_kernel(const T *__restrict__ b, ColRef bc, int N, int n_angles, int n
 // map[blockIdx.x] = (instance, local block of that instance's own grid).
 
 // One instance's tile with its back projector.
-template <typename T>
+template <typename T, int kChunk>
 __device__ __forceinline__ void batch_back_tile(const BatchInst &I, const T *in, int bx, int by) {
     if (I.back_model == CTG_BACK_MATCHED)
-        pixel_back_tile<T, 1>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn, bx, by,
-                              I.mt, 0.0f);
+        pixel_back_tile<T, 1, kChunk>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn, bx,
+                                      by, I.mt, 0.0f);
     else if (I.back_model == CTG_BACK_THRESHOLD)
-        pixel_back_tile<T, 2>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn, bx, by,
-                              I.mt, I.back_thr);
+        pixel_back_tile<T, 2, kChunk>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn, bx,
+                                      by, I.mt, I.back_thr);
     else
-        pixel_back_tile<T>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn, bx, by);
+        pixel_back_tile<T, 0, kChunk>(in, I.N, I.n_angles, I.n_det, I.back, I.back_window, nullptr, I.vn, bx,
+                                      by);
 }
 
 // T = float: AB instances with an FP32 basis (back-projecting w_k) and all
 // BA instances (back-projecting the FP32 t_k = A w_k); T = BF16 / FP16: AB
 // instances whose basis is stored in that type (their own launch, so that
 // each kernel holds the tile code of one input type only).
-template <typename T>
+// kChunk: angles staged per pass (the result does not depend on it).
+template <typename T, int kChunk>
 __global__ void __cluster_dims__(1, 1, kBSplit) __launch_bounds__(kBThreads)
 batch_back_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ map) {
     const int2 mp = map[blockIdx.x];
@@ -539,7 +541,7 @@ batch_back_kernel(const BatchInst *__restrict__ insts, const int2 *__restrict__ 
         in = I.variant == CTG_AB ? static_cast<const float *>(I.W) + (size_t)(I.k - 1) * I.ldw : I.vm;
     else
         in = static_cast<const T *>(I.W) + (size_t)(I.k - 1) * I.ldw;
-    batch_back_tile(I, in, mp.y % tx, mp.y / tx);
+    batch_back_tile<T, kChunk>(I, in, mp.y % tx, mp.y / tx);
 }
 
 // AB: stage t = B w_k (in vn); BA: stage w_{k+1} (stored type), with x_k
@@ -613,17 +615,31 @@ int ctg_fwd_blocks(int n_angles, int n_det) {
 // largest window the tiled back projector can stage in shared memory
 int ctg_back_window_max() { return (40 * 1024) / (int)(sizeof(float2) * kBChunk); }
 
-cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int max_window,
-                           cudaStream_t st, int wtype) {
-    if (nblocks <= 0) return cudaSuccess;
-    const size_t smem = sizeof(float2) * (size_t)kBChunk * max_window;
+namespace {
+template <int kChunk>
+void batch_back_t(BatchInst *insts, const int2 *map, int nblocks, int max_window, cudaStream_t st, int wtype) {
+    const size_t smem = sizeof(float2) * (size_t)kChunk * max_window;
     const dim3 grid(nblocks, 1, kBSplit);
     if (wtype == CTG_BASIS_BF16)
-        batch_back_kernel<__nv_bfloat16><<<grid, kBThreads, smem, st>>>(insts, map);
+        batch_back_kernel<__nv_bfloat16, kChunk><<<grid, kBThreads, smem, st>>>(insts, map);
     else if (wtype == CTG_BASIS_FP16)
-        batch_back_kernel<__half><<<grid, kBThreads, smem, st>>>(insts, map);
+        batch_back_kernel<__half, kChunk><<<grid, kBThreads, smem, st>>>(insts, map);
     else
-        batch_back_kernel<float><<<grid, kBThreads, smem, st>>>(insts, map);
+        batch_back_kernel<float, kChunk><<<grid, kBThreads, smem, st>>>(insts, map);
+}
+}  // namespace
+
+bool ctg_batch_back_chunk_ok(int chunk, int max_window) {
+    return (chunk == 16 || chunk == 32 || chunk == 64) && (size_t)chunk * max_window * sizeof(float2) <= 40 * 1024;
+}
+
+cudaError_t ctg_batch_back(BatchInst *insts, const int2 *map, int nblocks, int max_window,
+                           cudaStream_t st, int wtype, int chunk) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (!ctg_batch_back_chunk_ok(chunk, max_window)) chunk = kBChunk;
+    if (chunk == 16) batch_back_t<16>(insts, map, nblocks, max_window, st, wtype);
+    else if (chunk == 64) batch_back_t<64>(insts, map, nblocks, max_window, st, wtype);
+    else batch_back_t<kBChunk>(insts, map, nblocks, max_window, st, wtype);
     return cudaGetLastError();
 }
 

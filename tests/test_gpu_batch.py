@@ -272,3 +272,54 @@ def test_batch_fused_step_timeout_is_reported_and_recoverable(P, oracle_mod):
     for a, f in zip(again, fresh):
         assert a.iters == f.iters and a.stop_reason == f.stop_reason == 1
         assert torch.equal(a.x, f.x)
+
+
+def test_batch_autotuned_shapes_are_result_invariant(P, oracle_mod):
+    """The batched autotuner picks, by timing, the forward launches' shape
+    (four angles per warp or one) and the back projection's staging chunk
+    (16, 32 or 64 angles per pass).  Forcing each choice on the context gives
+    the same solves bit for bit: the tuner changes the speed only."""
+    import torch
+    cases, probs = [], []
+    for N, Na, v, seed in ((256, 360, "ab", 3301), (256, 360, "ba", 3302), (128, 180, "ba", 3303)):
+        og, xt, b, enorm = _case(oracle_mod, N, Na, 180, 0.01, seed)
+        cases.append(b)
+        probs.append({"geometry": P.Geometry(N, Na, og.n_det), "variant": v, "maxit": 40, "tau": 1.02,
+                      "noise_norm": enorm})
+    bs = [torch.tensor(b, device="cuda") for b in cases]
+    ctx = P.Context.get(bs[0].device)
+    ref = P.Batch(probs).solve(bs)
+    torch.cuda.synchronize()
+    try:
+        for angles, per_warp in ((8, 1), (16, 4)):
+            for chunk in (16, 32, 64):
+                ctx.set_tiles(angles, chunk, per_warp)
+                res = P.Batch(probs).solve(bs)
+                torch.cuda.synchronize()
+                for a, r in zip(res, ref):
+                    assert a.iters == r.iters and a.stop_reason == r.stop_reason
+                    assert torch.equal(a.x, r.x), (angles, per_warp, chunk)
+    finally:
+        ctx.set_tiles(0, 0)
+
+
+def test_batch_created_after_other_work_sees_its_tables(P, oracle_mod):
+    """A batch created while the device has just been busy (here a single
+    solve) must upload its angle tables after, not before, the zeroing of
+    its workspace (both ordered on the batch's own stream).  At 2048^2 the
+    zeroing takes long enough that a legacy-stream memset raced the table
+    uploads and left the forward table zero (t_1 = 0, a breakdown at k = 1)."""
+    import torch
+    og, xt, b, enorm = _case(oracle_mod, 2048, 180, 180, 0.01, 3401)
+    p = {"geometry": P.Geometry(2048, 180, og.n_det), "variant": "ba", "maxit": 30, "tau": 1.02,
+         "noise_norm": enorm}
+    bt = torch.tensor(b, device="cuda")
+    ref = P.ba_gmres(p["geometry"], bt, 30, tau=1.02, noise_norm=enorm)
+    for _ in range(2):
+        r = P.Batch([p]).solve([bt])[0]
+        torch.cuda.synchronize()
+        assert r.stop_reason == ref.stop_reason == 1 and abs(r.iters - ref.iters) <= 1
+        if r.iters == ref.iters:
+            d = (r.x - ref.x).double().norm() / ref.x.double().norm()
+            assert d.item() <= 1e-4
+        P.ba_gmres(p["geometry"], bt, 30, tau=1.02, noise_norm=enorm)     # busy the device again
