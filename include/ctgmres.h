@@ -284,11 +284,20 @@ int ctg_lsmr(ctg_ctx *ctx, const ctg_geom *g, const float *b_dev, const float *x
  * det_spacing >= 1); the batch owns its device workspace
  * (ctg_batch_workspace_bytes) and a stream of its own.  Invalid or
  * unsupported arguments return CTG_ERR_INVALID_ARG.
+ *   At creation the batch times its forward and back projection launches in
+ *   the tile shapes the result does not depend on and keeps the faster ones
+ *   (shapes forced with ctg_set_tiles / ctg_set_fwd_tiles are used as given).
  * ctg_batch_solve: b_dev, x_dev: host arrays of n device pointers (m and n
  * floats of each solve); x0_dev: NULL or an array whose entries may be NULL;
  * infos: n reports, filled as by ctg_ab_gmres.  Work is ordered after prior
  * work on `stream`, and `stream` waits for it; the call returns when done.
- * Each solve's result does not depend on the others in the batch. */
+ * Steps k <= 64 run every solve's CGS2 step and Givens update in one
+ * cooperative launch per basis type when its blocks fit on the device at
+ * once, later steps (or batches too large for that) the separate passes;
+ * each solve's result does not depend on the others in the batch as long as
+ * the batch takes the same form.  A wait of that launch that runs out (see
+ * ctg_set_wait_limit) stops every solve at its last completed step, whose
+ * iterate is formed and reported, and the call returns CTG_ERR_TIMEOUT. */
 typedef struct ctg_batch ctg_batch;
 int ctg_batch_create(ctg_ctx *ctx, int32_t n, const ctg_geom *geoms, const int32_t *variants,
                      const ctg_opts *opts, ctg_batch **out);
@@ -379,9 +388,11 @@ int ctg_cgs2_noalloc(const float *W_dev, int64_t ld_w, int64_t L, int32_t k,
  * at most `polls` times (about 100 ns apart; 0 restores the default of
  * 2^22, about half a second) and then gives up: the solve stops and
  * ctg_ab_gmres / ctg_ba_gmres return CTG_ERR_TIMEOUT (the context stays
- * usable; x then holds no meaningful iterate).  A limit of 1 makes a wait
- * give up unless every block has already arrived, which a test uses to
- * exercise this path.  Takes effect at the next solve. */
+ * usable; x then holds no meaningful iterate).  The batched one-launch step
+ * of ctg_batch_solve, for batches created on this context, takes the same
+ * limit.  A limit of 1 makes a wait give up unless every block has already
+ * arrived, which tests use to exercise this path.  Takes effect at the next
+ * solve. */
 int ctg_set_wait_limit(ctg_ctx *ctx, int64_t polls);
 
 /* Phase tracing (the paper has no counterpart; it reports no timings).
