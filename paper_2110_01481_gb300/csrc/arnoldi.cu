@@ -571,19 +571,15 @@ __device__ void batch_givens_warp(BatchInst &I, double *s_h, double *s_gc, doubl
             r_prev = -s_gs[i] * a + s_gc[i] * b;
         }
         const double a = r_prev, b = s_h[k];
-        const double r = hypot(a, b);
-        double c = 1.0, sn = 0.0;
-        if (b != 0.0) {
-            c = a / r;
-            sn = b / r;
-        }
+        double c, sn, rinv;
+        givens_rotation(a, b, c, sn, rinv);
         I.gc[k - 1] = c;
         I.gs[k - 1] = sn;
-        s_h[k - 1] = b != 0.0 ? r : a;
+        s_h[k - 1] = rinv;                              // R's diagonal as its reciprocal
         I.gg[k] = -sn * I.gg[k - 1];
         I.gg[k - 1] = c * I.gg[k - 1];
         I.rho = fabs(I.gg[k]);
-        I.breakdown = b <= 1e-6 * sqrt(I.h1[k]);     // h1[k] = ||q before CGS2||^2
+        I.breakdown = b * b <= 1e-12 * I.h1[k];      // b <= 1e-6 ||q before CGS2|| (h1[k] its square)
     }
     __syncwarp();
     for (int i = lane; i < k; i += 32) Rk[i] = s_h[i];

@@ -84,22 +84,19 @@ __device__ void loop_givens_warp(const LoopBufs &B, int k, const double *h, doub
             r_prev = -gss[i] * a + gcc[i] * b;
         }
         const double a = r_prev, b = hh[k];
-        const double r = hypot(a, b);
-        double c = 1.0, sn = 0.0;
-        if (b != 0.0) {
-            c = a / r;
-            sn = b / r;
-        }
+        double c, sn, rinv;
+        givens_rotation(a, b, c, sn, rinv);
         B.gc[k - 1] = c;
         B.gs[k - 1] = sn;
-        if (s_stage) s_h[k - 1] = b != 0.0 ? r : a;
-        else Rk[k - 1] = b != 0.0 ? r : a;
+        if (s_stage) s_h[k - 1] = rinv;        // R's diagonal as its reciprocal
+        else Rk[k - 1] = rinv;
         B.gg[k] = -sn * B.gg[k - 1];
         B.gg[k - 1] = c * B.gg[k - 1];
         rho = fabs(B.gg[k]);
         S.rho = rho;
         B.rhoh[k] = rho;
-        brk = (b <= 1e-6 * sqrt(qpre2) || !(b == b)) ? 1 : 0;
+        // b <= 1e-6 ||q before CGS2||, squared (b >= 0): no square root
+        brk = (!(b == b) || b * b <= 1e-12 * qpre2) ? 1 : 0;
     }
     rho = __shfl_sync(0xffffffffu, rho, 0);
     brk = __shfl_sync(0xffffffffu, brk, 0);

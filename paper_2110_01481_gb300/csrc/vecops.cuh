@@ -168,10 +168,32 @@ __device__ __forceinline__ F2 warp_sum_f2(F2 v) {
 
 __device__ __forceinline__ double f2_value(F2 v) { return (double)v.s + (double)v.c; }
 
+// The plane rotation that zeroes b below a (Sec. 2's Givens update): c =
+// a / r, s = b / r, r = (a^2 + b^2)^(1/2), or c = 1, s = 0 when b = 0; and
+// R's new diagonal entry as its reciprocal, rinv = 1 / r (1 / a when b = 0,
+// 0 for a zero entry), the form solve_y_warp takes.  On GB300 a dependent
+// FP64 division takes ~640 cycles and a square root ~675, against ~65 for an
+// FMA (measured), so the rotation takes one reciprocal square root and y_k no
+// division at all.  The entries are Hessenberg coefficients of vectors of
+// norm at most ||r0||, far from the range where a^2 + b^2 overflows.
+__device__ __forceinline__ void givens_rotation(double a, double b, double &c, double &s, double &rinv) {
+    if (b != 0.0) {
+        const double ir = rsqrt(fma(a, a, b * b));
+        c = a * ir;
+        s = b * ir;
+        rinv = ir;
+    } else {
+        c = 1.0;
+        s = 0.0;
+        rinv = a != 0.0 ? 1.0 / a : 0.0;
+    }
+}
+
 // y = R_k^{-1} g_{1:k} by back substitution in one warp, R (upper
-// triangle, column-major with leading dimension ldr) staged in shared
-// memory in packed form when it fits (packed: column j holds j + 1 entries
-// from offset j (j + 1) / 2), else read from global memory.
+// triangle, column-major with leading dimension ldr; its diagonal stored as
+// reciprocals, givens_rotation) staged in shared memory in packed form when
+// it fits (packed: column j holds j + 1 entries from offset j (j + 1) / 2),
+// else read from global memory.
 __device__ void solve_y_warp(const double *__restrict__ R, int ldr, const double *__restrict__ g, int k,
                              double *__restrict__ y, double *s_pack, int pack_cap) {
     const int lane = threadIdx.x & 31;
@@ -182,7 +204,7 @@ __device__ void solve_y_warp(const double *__restrict__ R, int ldr, const double
             const int j = e / k, i = e - j * k;
             if (i <= j) s_pack[j * (j + 1) / 2 + i] = R[(size_t)j * ldr + i];
         }
-    // t = g; for i = k-1 .. 0: y_i = t_i / R_ii, t_j -= R_ji y_i (j < i);
+    // t = g; for i = k-1 .. 0: y_i = t_i (1 / R_ii), t_j -= R_ji y_i (j < i);
     // lane l owns t_j for j = l, l + 32, ... (k <= 256)
     if (k > 256) {
         // beyond the registers: a plain loop over y (rows of R from global)
@@ -190,8 +212,7 @@ __device__ void solve_y_warp(const double *__restrict__ R, int ldr, const double
             for (int i = k - 1; i >= 0; --i) {
                 double acc = g[i];
                 for (int j = i + 1; j < k; ++j) acc -= R[(size_t)j * ldr + i] * y[j];
-                const double d = R[(size_t)i * ldr + i];
-                y[i] = d != 0.0 ? acc / d : 0.0;
+                y[i] = acc * R[(size_t)i * ldr + i];
             }
         __syncwarp();
         return;
@@ -209,8 +230,7 @@ __device__ void solve_y_warp(const double *__restrict__ R, int ldr, const double
 #pragma unroll
         for (int q = 0; q < 8; ++q)
             if (q == qi) ti = __shfl_sync(0xffffffffu, t[q], li);
-        const double d = packed ? s_pack[i * (i + 1) / 2 + i] : R[(size_t)i * ldr + i];
-        const double yi = d != 0.0 ? ti / d : 0.0;
+        const double yi = ti * (packed ? s_pack[i * (i + 1) / 2 + i] : R[(size_t)i * ldr + i]);
         if (lane == 0) y[i] = yi;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
