@@ -335,8 +335,11 @@ cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__rest
         }
         return;
     }
-    // w_{k+1} = q / ||q||; q keeps the orthogonalised vector
-    const float inv = nrm2 > 0.0 ? (float)(1.0 / sqrt(nrm2)) : 0.0f;
+    // w_{k+1} = q / ||q||; q keeps the orthogonalised vector.  One FP64
+    // reciprocal square root (a dependent division and a square root each
+    // take ~650 cycles on GB300), and ||q|| = nrm2 rnorm
+    const double rnorm = nrm2 > 0.0 ? rsqrt(nrm2) : 0.0;
+    const float inv = (float)rnorm;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int64_t g = g0 + (int64_t)e * kThreads;
@@ -350,7 +353,7 @@ cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__rest
             h2g[j] = s_h2[j];
         }
         if (tid == 0) {
-            h_out[k] = sqrt(nrm2);
+            h_out[k] = nrm2 * rnorm;
             h1g[k] = s_h1[k];
             scal[0] = s_h1[k];
             scal[1] = nrm2;
@@ -376,7 +379,8 @@ __device__ __forceinline__ void scale_body(const float *q, const double *__restr
                                            const double *__restrict__ h2,
                                            double *__restrict__ h_out, int blk, int nblk) {
     const double nn = *nrm2;
-    const float inv = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.0f;
+    const double rnorm = nn > 0.0 ? rsqrt(nn) : 0.0;
+    const float inv = (float)rnorm;
     const int64_t L4 = (L + 3) / 4;
     for (int64_t g = (int64_t)blk * blockDim.x + threadIdx.x; g < L4;
          g += (int64_t)nblk * blockDim.x) {
@@ -386,7 +390,7 @@ __device__ __forceinline__ void scale_body(const float *q, const double *__restr
     }
     if (h_out != nullptr && blk == 0) {
         for (int j = threadIdx.x; j < k; j += blockDim.x) h_out[j] = h1[j] + h2[j];
-        if (threadIdx.x == 0) h_out[k] = sqrt(nn);
+        if (threadIdx.x == 0) h_out[k] = nn * rnorm;
     }
 }
 
@@ -416,7 +420,8 @@ __device__ __forceinline__ void update_scale_body(const T *__restrict__ W, int64
     }
     __syncthreads();
     const double nn = s_nn;
-    const float inv = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.0f;
+    const double rnorm = nn > 0.0 ? rsqrt(nn) : 0.0;
+    const float inv = (float)rnorm;
     const int64_t g0 = (int64_t)blk * kThreads * E + tid;
     float4 qv[E];
 #pragma unroll
@@ -431,7 +436,7 @@ __device__ __forceinline__ void update_scale_body(const T *__restrict__ W, int64
     if (blk == 0) {
         if (h_out != nullptr) {
             for (int j = tid; j < k; j += kThreads) h_out[j] = h1[j] + h2[j];
-            if (tid == 0) h_out[k] = sqrt(nn);
+            if (tid == 0) h_out[k] = nn * rnorm;
         }
         if (tid == 0) *nrm2_out = nn;
     }
@@ -664,7 +669,9 @@ batch_cgs2_fused_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ 
         __syncthreads();
         update_slice<T, E>(W, ldw, k, s_c, g0, L, qv);
         const double nrm2 = s_h2[k + 1];
-        const float inv = nrm2 > 0.0 ? (float)(1.0 / sqrt(nrm2)) : 0.0f;
+        // as in cgs2_fused_kernel: one reciprocal square root, ||q|| = nrm2 rnorm
+        const double rnorm = nrm2 > 0.0 ? rsqrt(nrm2) : 0.0;
+        const float inv = (float)rnorm;
         T *w_out = const_cast<T *>(W) + (size_t)k * ldw;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -680,7 +687,7 @@ batch_cgs2_fused_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ 
                 I.h2[j] = s_h2[j];
             }
             if (tid == 0) {
-                h_out[k] = sqrt(nrm2);
+                h_out[k] = nrm2 * rnorm;
                 I.h1[k] = s_h1[k];
                 I.scal[1] = nrm2;
             }
