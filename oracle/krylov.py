@@ -24,7 +24,12 @@ the discrepancy principle of Sec. 6.4: stop at the smallest k >= 0 with
 Readings where the paper is silent: ``ortho='cgs2'`` replaces the MGS inner
 loop by classical Gram-Schmidt applied twice (equal in exact arithmetic); a
 breakdown is declared when h_{k+1,k} <= 1e-14 ||q_k before orthogonalisation||,
-after which the square k x k system gives x_k and the iteration stops.
+after which the iteration stops with y_k still the least-squares minimiser of
+the (k+1) x k problem, as for every other k.  The square k x k system that a
+breakdown leaves is singular when A B (or B A) is: a rank-deficient A B whose
+Krylov space from b is exhausted has h_{k+1,k} = 0 and a singular H_k, and
+the minimiser over the exhausted space is then reached by the least-squares
+solution, while a square solve blows up along the null direction.
 
 ``lsqr`` / ``lsmr`` restate Paige & Saunders (1982) and Fong & Saunders
 (2011) with damping 0 and optional full reorthogonalisation of the Lanczos
@@ -99,9 +104,9 @@ def _gmres(apply_M, r0, form_x, resid_norm, maxit, tau, noise_norm, ortho,
         e1 = np.zeros(k + 1)
         e1[0] = beta
         if H[k, k - 1] <= BREAKDOWN_RTOL * q_pre:
-            y = np.linalg.solve(H[:k, :k], e1[:k])
+            y = np.linalg.lstsq(H[:k + 1, :k], e1, rcond=None)[0]
             x = form_x(W[:k], y)
-            out["rho"].append(0.0)
+            out["rho"].append(float(np.linalg.norm(e1 - H[:k + 1, :k] @ y)))
             out["resnorm"].append(resid_norm(x))
             if keep:
                 out["iterates"].append(x)

@@ -256,3 +256,36 @@ def test_full_size_sampled_parity(P, oracle_mod, variant):
     for k in (1, 2, 4):
         _, rk = _solve(P, variant, og, b, k)
         assert _rel(rk.x.double().cpu().numpy(), ref["iterates"][k]) <= X_TOL, k
+
+
+
+@pytest.mark.parametrize("N,Na", [(4, 8), (6, 10)])
+@pytest.mark.parametrize("variant", ["ab", "ba"])
+def test_breakdown_when_the_krylov_space_is_exhausted(P, oracle_mod, variant, N, Na):
+    """On an N x N image with N^2 < m, the Krylov space of B A (square,
+    nonsingular) or of A B (rank N^2) is exhausted after about N^2 steps:
+    h_{k+1,k} falls to the rounding level and both sides stop with a
+    breakdown.  The GPU tests h_{k+1,k} <= 1e-6 ||q|| on FP32 vectors where
+    the oracle tests 1e-14 in FP64, so the GPU may stop up to two steps
+    earlier.  BA: the iterate is the unique minimiser of ||B b - B A x||, so
+    x matches the oracle's.  AB: A B is singular, the projected least-squares
+    problem becomes ill-conditioned as the space fills, and its FP32 basis
+    error (~1e-7 of ||A B||) is amplified in x (Sec. 2 minimises over the
+    space; at exhaustion the minimiser is min_z ||b - A B z||); the GPU's
+    residual stays within a factor 2 of that minimum, and the residual it
+    reports is the true ||b - A x|| of the x it returns."""
+    O = oracle_mod
+    og, _, b, _ = _problem(O, N, Na, seed=11)
+    A, B = _ops(O, og)
+    ref = (O.ab_gmres if variant == "ab" else O.ba_gmres)(A, B, b, 80)
+    _, r = _solve(P, variant, og, b, 80)
+    assert r.stop_reason == ref["stop_reason"] == 2
+    assert ref["k"] - 2 <= r.iters <= ref["k"]
+    x = r.x.double().cpu().numpy()
+    true_res = np.linalg.norm(b - A(x))
+    assert r.resnorm == pytest.approx(true_res, rel=1e-4)
+    if variant == "ba":
+        assert _rel(x, ref["x"]) <= X_TOL
+        assert r.resnorm == pytest.approx(ref["resnorm"][-1], rel=1e-4)
+    else:
+        assert (1 - 1e-9) * ref["resnorm"][-1] <= true_res <= 2.0 * ref["resnorm"][-1]

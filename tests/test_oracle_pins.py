@@ -429,6 +429,38 @@ def test_breakdown_returns_exact_solution(oracle_mod):
         np.testing.assert_allclose(r["x"], b, rtol=1e-14)
 
 
+
+@pytest.mark.parametrize("N,Na", [(4, 8), (6, 10), (5, 7)])
+def test_breakdown_of_a_singular_ab_reaches_the_least_squares_minimum(oracle_mod, N, Na):
+    """On a tiny geometry (n = N^2 < m) A B is m x m of rank n, so the Krylov
+    space K_k(A B, b) is exhausted after about n + 1 steps and the run ends in
+    a breakdown with a singular square H_k.  The returned iterate must still
+    attain min_z ||b - A B z|| (Sec. 2: AB-GMRES minimises ||b - A B u|| over
+    the Krylov space, which at exhaustion holds the minimiser), computed
+    here from the explicit matrices by a library least-squares solve; the
+    residual history is non-increasing up to rounding (GMRES minimises over
+    nested spaces).  BA-GMRES on the square nonsingular B A of the same
+    geometry ends in a breakdown at the exact minimiser of ||B b - B A x||."""
+    O = oracle_mod
+    og = O.Geometry(N, Na, I.detector_count(N))
+    n = N * N
+    m = Na * og.n_det
+    A = np.stack([O.forward(og, e) for e in np.eye(n)], 1)
+    B = np.stack([O.backproject(og, e) for e in np.eye(m)], 1)
+    assert np.linalg.matrix_rank(A @ B) == n < m
+    b = A @ I.random_ellipses(N, 11).ravel() + 0.01 * np.random.default_rng(1).standard_normal(m)
+    r = O.ab_gmres(A, B, b, 4 * n)
+    assert r["stop_reason"] == 2 and n <= r["k"] <= n + 3
+    z = np.linalg.lstsq(A @ B, b, rcond=None)[0]
+    best = np.linalg.norm(b - A @ (B @ z))
+    assert np.linalg.norm(b - A @ r["x"]) == pytest.approx(best, rel=1e-9)
+    res = np.array(r["resnorm"])
+    assert np.all(np.diff(res) <= 1e-9 * res[0])
+    rb = O.ba_gmres(A, B, b, 4 * n)
+    assert rb["stop_reason"] == 2 and rb["k"] <= n + 3
+    xb = np.linalg.solve(B @ A, B @ b)
+    np.testing.assert_allclose(rb["x"], xb, rtol=1e-8 * np.linalg.cond(B @ A), atol=0)
+
 # ------------------------------------------------------------ input pins
 def test_shepp_logan_and_noise_generators():
     x = I.shepp_logan(128)
