@@ -245,44 +245,85 @@ __device__ void solve_y_warp(const double *__restrict__ R, int ldr, const double
 // last block can read them as float4.
 __host__ __device__ inline int padded_grid(int G) { return (G + 3) & ~3; }
 
+__device__ __forceinline__ F2 shfl_xor_f2(F2 v, int o) {
+    return F2{__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.c, o)};
+}
+
 // Rows [row0, row0 + nrows) of the per-block partials (G blocks, row
 // stride Gp) summed over the blocks in one fixed order, as compensated
-// FP32 pairs: each warp of the block takes four rows at a time and reads
-// them as float4 (four blocks per load); out[j] (j < nrows, FP64) is written
-// by lane 0 of the warp that summed row j.  The padding entries (block index
+// FP32 pairs; out[j] (j < nrows, FP64).  Each warp takes R rows at a time:
+// every lane reads them as float4 (four blocks per load), two lane strides'
+// loads issued together, and adds them into one pair per row; the warp sum
+// is then a transposed butterfly: at each of the first log2(R) levels a lane
+// keeps half of its rows and merges its partner's copy of them, so a warp
+// spends log2(R) + log2(32 / R) dependent shuffle levels on R rows instead of
+// R times 5 (the serial chain of the summation tail was ~3,500 cycles for
+// four rows with one butterfly per row, measured).  Every merge takes the
+// lower lane's value first, so the order is fixed and every block that sums
+// the same partials gets the same bits.  The padding entries (block index
 // >= G) are never read into a sum.
+template <int R = 4>
 __device__ __forceinline__ void sum_partial_rows(const float *__restrict__ partials, int row0, int nrows, int G,
                                                  int Gp, double *out) {
+    static_assert(R == 2 || R == 4 || R == 8, "rows per warp");
+    constexpr int LR = R == 8 ? 3 : (R == 4 ? 2 : 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G4 = Gp / 4;
-    for (int j0 = warp * 4; j0 < nrows; j0 += kWarps * 4) {
-        F2 acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        for (int g4 = lane; g4 < G4; g4 += 32) {
-            float4 v[4];
+    for (int j0 = warp * R; j0 < nrows; j0 += kWarps * R) {
+        F2 acc[R];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                v[q] = (j0 + q < nrows)
-                           ? __ldcg(reinterpret_cast<const float4 *>(partials + (size_t)(row0 + j0 + q) * Gp) + g4)
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
-            const int b0 = 4 * g4;
+        for (int r = 0; r < R; ++r) acc[r] = F2{0.f, 0.f};
+        for (int g4 = lane; g4 < G4; g4 += 64) {
+            const bool two = g4 + 32 < G4;
+            float4 v[2][R];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                acc[q] = f2_add(acc[q], v[q].x);
-                if (b0 + 1 < G) acc[q] = f2_add(acc[q], v[q].y);
-                if (b0 + 2 < G) acc[q] = f2_add(acc[q], v[q].z);
-                if (b0 + 3 < G) acc[q] = f2_add(acc[q], v[q].w);
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    v[u][r] = (j0 + r < nrows && (u == 0 || two))
+                                  ? __ldcg(reinterpret_cast<const float4 *>(partials + (size_t)(row0 + j0 + r) * Gp) +
+                                           g4 + 32 * u)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (u == 1 && !two) break;
+                const int b0 = 4 * (g4 + 32 * u);      // < G: g4 + 32 u < G4 and Gp - G < 4
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    acc[r] = f2_add(acc[r], v[u][r].x);
+                    if (b0 + 1 < G) acc[r] = f2_add(acc[r], v[u][r].y);
+                    if (b0 + 2 < G) acc[r] = f2_add(acc[r], v[u][r].z);
+                    if (b0 + 3 < G) acc[r] = f2_add(acc[r], v[u][r].w);
+                }
             }
         }
+        int row = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const F2 t = warp_sum_f2(acc[q]);
-            if (lane == 0 && j0 + q < nrows) out[j0 + q] = f2_value(t);
+        for (int l = 0; l < LR; ++l) {
+            const int o = 16 >> l, n = R >> l;
+            const bool hi = lane & o;
+#pragma unroll
+            for (int i = 0; i < n / 2; ++i) {
+                const F2 keep = hi ? acc[i + n / 2] : acc[i];
+                const F2 recv = shfl_xor_f2(hi ? acc[i] : acc[i + n / 2], o);
+                acc[i] = f2_merge(hi ? recv : keep, hi ? keep : recv);
+            }
+            if (hi) row += n / 2;
         }
+        F2 t = acc[0];
+#pragma unroll
+        for (int o = 16 >> LR; o > 0; o >>= 1) {
+            const F2 recv = shfl_xor_f2(t, o);
+            const bool hi = lane & o;
+            t = f2_merge(hi ? recv : t, hi ? t : recv);
+        }
+        if ((lane & ((32 >> LR) - 1)) == 0 && j0 + row < nrows) out[j0 + row] = f2_value(t);
     }
 }
 
 // Writes this block's nred partial sums, then lets the last block sum all
-// blocks' partials (fixed order, compensated FP32 pairs, sum_partial_rows)
+// blocks' partials (fixed order, compensated FP32 pairs, sum_partial_rows,
+// eight rows per warp)
 // into red_out[0..nred-1] in FP64, so the serial tail is a few L2 round
 // trips.  Returns true in the last block (after red_out is written and the
 // block has synchronised), false in the others.
@@ -304,7 +345,7 @@ __device__ bool block_reduce_finish(float *s_w, int nred, float *__restrict__ pa
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
-    sum_partial_rows(partials, 0, nred, G, Gp, red_out);
+    sum_partial_rows<8>(partials, 0, nred, G, Gp, red_out);
     if (tid == 0) *counter = 0u;
     __syncthreads();
     return true;
