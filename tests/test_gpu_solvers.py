@@ -286,6 +286,7 @@ def test_breakdown_when_the_krylov_space_is_exhausted(P, oracle_mod, variant, N,
     assert r.resnorm == pytest.approx(true_res, rel=1e-4)
     if variant == "ba":
         assert _rel(x, ref["x"]) <= X_TOL
-        assert r.resnorm == pytest.approx(ref["resnorm"][-1], rel=1e-4)
+        # the residual is ~1% of ||b||, so x's 1e-4 carries into it ~100-fold
+        assert r.resnorm == pytest.approx(ref["resnorm"][-1], rel=1e-3)
     else:
         assert (1 - 1e-9) * ref["resnorm"][-1] <= true_res <= 2.0 * ref["resnorm"][-1]
