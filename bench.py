@@ -680,6 +680,21 @@ def run_methods(args):
                           "interpolations_per_s": g.n * N_ANG / (us * 1e-6)}), flush=True)
 
 
+def parse_tiles(text):
+    """--tiles A,W,C: forward angles per block A (4, 8 or 16), angles per warp W
+    (1 or 4; 4 only with A = 8 or 16), back-projection angles per pass C (16,
+    32 or 64); the projector shapes then stay fixed instead of autotuned (for
+    profiling one shape; results do not depend on the shapes)."""
+    try:
+        fa, wa, bc = (int(t) for t in text.split(","))
+    except ValueError:
+        raise SystemExit(f"--tiles wants A,W,C (three integers), got {text!r}")
+    ok = (wa == 1 and fa in (4, 8)) or (wa == 4 and fa in (8, 16))
+    if not ok or bc not in (16, 32, 64):
+        raise SystemExit(f"--tiles {text}: forward shapes 4,1 8,1 8,4 16,4; back 16, 32 or 64")
+    return fa, wa, bc
+
+
 def make_instance(P, torch, dev, seed):
     """Seeded phantom, b = A x_bar + e with the library's own A (the oracle is
     not used on the product path)."""
@@ -727,6 +742,9 @@ def run_gpu(args):
     x_ba = torch.empty(g.n, dtype=torch.float32, device=dev)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
     ctx = P.Context.get(dev)
+    if args.tiles:
+        fa, wa, bc = parse_tiles(args.tiles)
+        ctx.set_tiles(fwd_angles=fa, back_chunk=bc, fwd_warp_angles=wa)
 
     def step(bb):
         ra = P.ab_gmres(g, bb, MAXIT, tau=TAU, noise_norm=enorm, out=x_ab, workspace=ws_ab)
@@ -1003,6 +1021,9 @@ def main():
                     help="skip the short serving measurement of the default run")
     ap.add_argument("--serve-quick", type=int, default=160,
                     help="requests of the default run's serving measurement")
+    ap.add_argument("--tiles", default="",
+                    help="A,W,C: fix the projector shapes (forward angles per block, per warp; "
+                         "back angles per pass) instead of autotuning them")
     ap.add_argument("--cgs2-only", action="store_true",
                     help="time only the large-basis Arnoldi (CGS2) step")
     ap.add_argument("--cgs2-k", type=int, default=100)

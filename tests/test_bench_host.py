@@ -31,3 +31,11 @@ def test_joseph_interpolation_count_matches_oracle_matrix(oracle_mod, N, Na, Nd,
     step = np.where(row_driven[angle] == 1, A.col // N, A.col % N)
     pairs = np.unique(A.row.astype(np.int64) * N + step).size
     assert bench.joseph_interpolations(N, Na, Nd, S, R, ds) == pairs
+
+
+def test_tiles_option_accepts_the_built_shapes_only():
+    assert bench.parse_tiles("8,4,64") == (8, 4, 64)
+    assert bench.parse_tiles("4,1,16") == (4, 1, 16)
+    for bad in ("4,4,32", "16,1,32", "8,4,48", "8,4", "a,b,c"):
+        with pytest.raises(SystemExit):
+            bench.parse_tiles(bad)
