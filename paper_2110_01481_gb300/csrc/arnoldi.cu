@@ -93,9 +93,12 @@ __device__ __forceinline__ void update_slice(const T *__restrict__ W, int64_t ld
 
 // Warp sums of W_j^T qv (j < k) into s_w[warp * nred + j] and, with NORM,
 // of qv^T qv into s_w[warp * nred + k]; same load batching as update_slice.
-// REV visits the vectors from the last to the first: after an update sweep
-// over W, the vectors it read last are the ones still in L2 (a basis larger
-// than L2 is then read from HBM about 1.6 instead of 2 times per pass).
+// REV visits the vectors from the last to the first.  The separate passes
+// alternate the direction of their sweeps over W (pass 1's dots last to
+// first, pass 2's update first to last and its dots last to first, the
+// last update first to last), so each sweep starts on the vectors that the
+// one before read last, which a basis larger than L2 still finds there.
+// The order of the vectors does not change any sum.
 template <typename T, int E, bool NORM, bool REV = false, int BYTES = 128>
 __device__ __forceinline__ void dots_slice(const T *__restrict__ W, int64_t ldw, int k, int64_t g0,
                                            int64_t L, const float4 (&qv)[E], float *s_w, int nred) {
@@ -158,7 +161,7 @@ __device__ __forceinline__ void cgs_pass_body(const T *__restrict__ W, int64_t l
         for (int e = 0; e < E; ++e) st4(q, g0 + (int64_t)e * kThreads, L, qv[e]);
     }
     if (DOTS) {
-        dots_slice<T, E, NORM, UPDATE, 256>(W, ldw, k, g0, L, qv, s_w, nred);
+        dots_slice<T, E, NORM, true, 256>(W, ldw, k, g0, L, qv, s_w, nred);
     } else if (NORM) {
         float s = 0.f;
 #pragma unroll
@@ -283,7 +286,7 @@ cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__rest
 #pragma unroll
     for (int e = 0; e < E; ++e) qv[e] = ld4_rw(q, g0 + (int64_t)e * kThreads, L);
     // pass 1: h1 = W^T q, ||q||^2
-    dots_slice<T, E, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
+    dots_slice<T, E, true, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
     __syncthreads();
     write_rows(s_w, k + 1, 0, partials, Gp, blk);
     bool ok = grid_barrier(bar, (unsigned)G, spin_limit, err);
@@ -298,7 +301,7 @@ cgs2_fused_kernel(const T *__restrict__ W, int64_t ldw, int k, const int *__rest
         for (int j = tid; j < k; j += kThreads) s_c[j] = (float)s_h1[j];
         __syncthreads();
         update_slice<T, E>(W, ldw, k, s_c, g0, L, qv);
-        dots_slice<T, E, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
+        dots_slice<T, E, true, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
         __syncthreads();
         write_rows(s_w, k + 1, k + 1, partials, Gp, blk);
         ok = grid_barrier(bar, 2u * (unsigned)G, spin_limit, err);
@@ -639,7 +642,7 @@ batch_cgs2_fused_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ 
     if (on) {
 #pragma unroll
         for (int e = 0; e < E; ++e) qv[e] = ld4_rw(q, g0 + (int64_t)e * kThreads, L);
-        dots_slice<T, E, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
+        dots_slice<T, E, true, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
         __syncthreads();
         write_rows(s_w, k + 1, 0, I.partials, Gpi, mp.y);
     }
@@ -650,7 +653,7 @@ batch_cgs2_fused_kernel(BatchInst *__restrict__ insts, const int2 *__restrict__ 
         for (int j = tid; j < k; j += kThreads) s_c[j] = (float)s_h1[j];
         __syncthreads();
         update_slice<T, E>(W, ldw, k, s_c, g0, L, qv);
-        dots_slice<T, E, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
+        dots_slice<T, E, true, true>(W, ldw, k, g0, L, qv, s_w, k + 1);
         __syncthreads();
         write_rows(s_w, k + 1, k + 1, I.partials, Gpi, mp.y);
     }
