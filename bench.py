@@ -836,7 +836,8 @@ def run_gpu(args):
         arn_bytes += args.steps * (12.0 * L * it_k * (it_k + 1) / 2 + 24.0 * L * it_k)
     phases = {p: tm[p] for p in _native.PHASES}
     arnoldi_roof = {
-        "bound": "hbm", "unit": "GB/s", "kernel": "CGS2 Arnoldi step (3 passes + scale)",
+        "bound": "hbm", "unit": "GB/s",
+        "kernel": "CGS2 Arnoldi step (one cooperative launch up to k = 128 when its grid fits, else 3 passes)",
         "achieved": arn_bytes / (phases["arnoldi"]["ms"] / 1e3) / 1e9 if phases["arnoldi"]["ms"] else None,
         "peak": hbm, "peak_kind": peak_kind + " copy bandwidth",
     }

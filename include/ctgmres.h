@@ -344,11 +344,11 @@ void ctg_engine_destroy(ctg_engine *engine);
  * MGS replaced by CGS2 (equal in exact arithmetic):
  *   h = W^T q; q -= W h; h' = W^T q; q -= W h';  h_out[0..k-1] = h + h',
  *   h_out[k] = ||q||, and, if h_out[k] > 0, w_out = q / ||q||.
- * For k <= 64 (one cooperative launch) ||q|| is formed as
- * sqrt(||q1||^2 - ||h'||^2), q1 the vector after the first pass, which is
- * ||q1 - W h'|| exactly for orthonormal W and agrees with the direct norm to
- * rounding (h' is at the rounding level of ||q1||); larger k take it
- * directly.
+ * ||q|| is formed as sqrt(||q1||^2 - ||h'||^2), q1 the vector after the
+ * first pass, which is ||q1 - W h'|| exactly for orthonormal W and agrees
+ * with the direct norm to rounding (h' is at the rounding level of ||q1||).
+ * For k <= 128 the step is one cooperative launch when its grid fits on the
+ * device at once, else three launches.
  * W: k vectors of length L at stride ld_w floats (ld_w >= L, multiple of
  * 4), device, read-only; q: L floats, device, overwritten by the
  * orthogonalised vector; w_out: L floats, device (may equal q);

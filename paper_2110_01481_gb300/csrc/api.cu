@@ -1093,7 +1093,10 @@ int run_gmres(SolveCtx &sc, int variant, const float *b, const float *x0, float 
     lp.rule = rule_of(o);
     lp.maxit = o->maxit;
     lp.target = lp.rule == kRuleDP ? o->tau * o->noise_norm : 0.0;
-    lp.fused_max = std::min(o->maxit, ctg_cgs2_fused_max());
+    // steps that form y_k (BA with a residual rule, AB with NCP) take the
+    // one-launch step up to a smaller k than those that do not
+    const bool need_y = variant == CTG_AB ? lp.rule == kRuleNCP : lp.rule != kRuleMaxit;
+    lp.fused_max = std::min(o->maxit, ctg_cgs2_fused_max(need_y));
     lp.fused = ctg_cgs2_fused_ok(sc.ly.dtype, sc.ly.L, lp.fused_max, sc.rs);
     if (!lp.fused) lp.fused_max = 0;
     int rc = CTG_OK;

@@ -951,10 +951,15 @@ static int red_grid_max(int64_t L) {
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // The fused step is used for k <= kFusedMaxK: measured at L = 522,000 it
-// takes 29 / 40 / 75 / 151 us at k = 4 / 12 / 32 / 64 against 45 / 51 / 82 /
-// 153 us for the separate passes; the two meet near k = 64, where streaming
-// the basis dominates.
-constexpr int kFusedMaxK = 64;
+// takes 21 / 27 / 44 / 81 / 130 / 166 us at k = 4 / 12 / 32 / 64 / 100 / 128
+// against 137 us for the separate passes at k = 100 and 176 us at k = 129
+// (the one launch keeps q on chip and saves two launches and a summation
+// tail; at 4.19M the two are level).  A solver step that also forms y_k
+// (kGivY) stages R's packed triangle in shared memory, which beyond k = 64
+// would take the L1 capacity the step's own re-reads of its basis slice
+// use; such steps take the one launch up to kFusedMaxKY, as do batches.
+constexpr int kFusedMaxK = 128;
+constexpr int kFusedMaxKY = 64;
 
 // Partial rows: kmax + 2 for the separate passes; the fused step needs 2k + 2.
 static size_t partial_rows(int kmax) {
@@ -1015,8 +1020,9 @@ int fused_resident_blocks() {
     static std::atomic<int> cache[kMaxDevices];
     return per_device_cached(cache, [](int dev) {
         int per_sm = 0, sms = 0;
-        const size_t smem = fused_smem_bytes(kFusedMaxK, kGivY);
+        const size_t smem = std::max(fused_smem_bytes(kFusedMaxKY, kGivY), fused_smem_bytes(kFusedMaxK, kGivZ));
         if (dev < 0 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            ctg_allow_dyn_smem((const void *)cgs2_fused_kernel<T, E>, smem) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cgs2_fused_kernel<T, E>, kThreads,
                                                           smem) != cudaSuccess) {
             cudaGetLastError();
@@ -1040,6 +1046,7 @@ cudaError_t launch_fused(const T *W, int64_t ldw, int64_t L, int k, float *q, T 
     if (G > fused_resident_blocks<T, E>()) return cudaSuccess;
     const int kcap = ls ? ls->kmax : k;
     const int giv_mode = ls && ls->lb ? ls->giv_mode : -1;
+    if (giv_mode >= 0 && (giv_mode & kGivY) && kcap > kFusedMaxKY) return cudaSuccess;
     const size_t smem = fused_smem_bytes(kcap, giv_mode);
     const cudaError_t ea = ctg_allow_dyn_smem((const void *)cgs2_fused_kernel<T, E>, smem);
     if (ea != cudaSuccess) return ea;
@@ -1215,7 +1222,7 @@ bool ctg_cgs2_fused_ok(int dtype, int64_t L, int kmax, const RedScratch &rs) {
     return G <= cap;
 }
 
-int ctg_cgs2_fused_max() { return kFusedMaxK; }
+int ctg_cgs2_fused_max(bool need_y) { return need_y ? kFusedMaxKY : kFusedMaxK; }
 
 cudaError_t ctg_gemv(const void *W, int dtype, int64_t ldw, int64_t L, int k, const double *y,
                      const float *base, float *out, cudaStream_t st, const int *kdev, int koff) {
@@ -1394,10 +1401,10 @@ cudaError_t launch_batch_fused(BatchInst *insts, const int2 *map, int nblocks, i
 
 }  // namespace
 
-int ctg_batch_fused_max_k() { return kFusedMaxK; }
+int ctg_batch_fused_max_k() { return kFusedMaxKY; }
 
 int ctg_batch_fused_resident(int kcap, int wtype) {
-    if (kcap < 1 || kcap > kFusedMaxK) return 0;
+    if (kcap < 1 || kcap > kFusedMaxKY) return 0;
     if (wtype == CTG_BASIS_BF16) return batch_fused_resident_t<__nv_bfloat16>(kcap);
     if (wtype == CTG_BASIS_FP16) return batch_fused_resident_t<__half>(kcap);
     return batch_fused_resident_t<float>(kcap);
@@ -1406,7 +1413,7 @@ int ctg_batch_fused_resident(int kcap, int wtype) {
 cudaError_t ctg_batch_cgs2_fused(BatchInst *insts, const int2 *map, int nblocks, int kcap, unsigned *bar,
                                  int *err, const long long *spin_limit, cudaStream_t st, int wtype) {
     if (nblocks <= 0) return cudaSuccess;
-    if (kcap < 1 || kcap > kFusedMaxK) return cudaErrorInvalidValue;
+    if (kcap < 1 || kcap > kFusedMaxKY) return cudaErrorInvalidValue;
     if (wtype == CTG_BASIS_BF16)
         return launch_batch_fused<__nv_bfloat16>(insts, map, nblocks, kcap, bar, err, spin_limit, st);
     if (wtype == CTG_BASIS_FP16) return launch_batch_fused<__half>(insts, map, nblocks, kcap, bar, err, spin_limit, st);

@@ -243,7 +243,9 @@ cudaError_t ctg_cgs2_step_loop(const void *W, int dtype, int64_t ldw, int64_t L,
 // Whether the fused step serves k <= kmax at length L with this scratch
 // (every block of its grid resident at once).
 bool ctg_cgs2_fused_ok(int dtype, int64_t L, int kmax, const RedScratch &rs);
-int ctg_cgs2_fused_max();
+// The largest k the fused step serves: smaller for solver steps that also
+// form y_k in the step (need_y), whose packed triangle takes shared memory.
+int ctg_cgs2_fused_max(bool need_y);
 // out = base + sum_j y_j W_j (base may be NULL); y: k doubles (device); with
 // kdev set, k = *kdev + koff read on the device (k is then only the bound
 // that sizes the launch's shared memory).
