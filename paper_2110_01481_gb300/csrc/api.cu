@@ -823,7 +823,8 @@ int ensure_events(ctg_ctx *ctx);
 // 6.4 are device kernels too (gmres_loop.cu), and the kernel that ends a
 // step advances k or stops the solve.  So the whole solve is one CUDA graph:
 // the start (r0, beta, w_1), two while-loop nodes over the steps (the first
-// with the one-launch CGS2 step for k <= 64, the second with its separate
+// with the one-launch CGS2 step for k <= 128, or 64 where the step forms
+// y_k, the second with its separate
 // passes) and the exit (y_k, x_k and its true residual), launched once and
 // read back once.  With phase tracing on (or where such a graph cannot be
 // built) the host enqueues the same kernels step by step instead and reads
