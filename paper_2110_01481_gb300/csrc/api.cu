@@ -325,8 +325,8 @@ struct ctg_ctx {
         std::vector<long long> key;
         unsigned long long geom_serial;
         cudaGraphExec_t exec;
-        int n_init, n_fused, n_pass, n_exit;   // kernels per launch of each part
-        int fused_max;
+        int n_init, n_small, n_fused, n_pass, n_exit;   // kernels per launch of each part
+        int small_max, fused_max;
     };
     std::vector<LoopGraph> graphs;
     cudaStream_t cap_st[2] = {nullptr, nullptr};   // capture streams
@@ -690,9 +690,9 @@ struct SolveCtx {
     // one CGS2 step of the loop (k on the device); with the fused step, its
     // block 0 also runs the step's Givens update in mode giv_mode (lb)
     cudaError_t cgs2_loop(int64_t L, float *q, int kmax, bool fused, bool cooperative,
-                          const LoopBufs *lb = nullptr, int giv_mode = -1) const {
+                          const LoopBufs *lb = nullptr, int giv_mode = -1, bool small_grid = false) const {
         int nk = 0;
-        const LoopStep ls{&state()->k, at<double>(ly.off_h), ly.kmax + 1, kmax, fused, lb, giv_mode};
+        const LoopStep ls{&state()->k, at<double>(ly.off_h), ly.kmax + 1, kmax, fused, lb, giv_mode, small_grid};
         const cudaError_t e = traced(ctx, 2, 0, st, [&] {
             return ctg_cgs2_step_loop(W(), ly.dtype, ly.ld_w, L, q, ls, rs, ctx->spin_limit, cooperative, st, &nk);
         });
@@ -844,6 +844,7 @@ struct LoopPlan {
     double target;
     bool fused;        // the one-launch CGS2 step serves k <= fused_max
     int fused_max;
+    int small_max;     // ... on one block per SM for k <= small_max (0: none)
     bool cooperative;  // launch it cooperatively
 };
 
@@ -881,7 +882,7 @@ int enqueue_init(SolveCtx &sc, const LoopPlan &lp, const float *b, const float *
 }
 
 int enqueue_step(SolveCtx &sc, const LoopPlan &lp, const float *b, const float *x0, float *x,
-                 const LoopBufs &B, bool fused) {
+                 const LoopBufs &B, bool fused, bool small_grid = false) {
     const int64_t n = sc.ly.n, m = sc.ly.m;
     const int *kdev = &sc.state()->k;
     const int kmax = fused ? lp.fused_max : lp.maxit;
@@ -894,7 +895,7 @@ int enqueue_step(SolveCtx &sc, const LoopPlan &lp, const float *b, const float *
     auto cgs2_givens = [&](int64_t L, float *q, bool need_y, bool need_z, bool end) -> int {
         if (fused) {
             const int mode = (need_y ? kGivY : 0) | (need_z ? kGivZ : 0) | (end ? kGivEnd : 0);
-            CTG_CK(sc.cgs2_loop(L, q, kmax, true, lp.cooperative, &B, mode));
+            CTG_CK(sc.cgs2_loop(L, q, kmax, true, lp.cooperative, &B, mode, small_grid));
             return CTG_OK;
         }
         CTG_CK(sc.cgs2_loop(L, q, kmax, false, lp.cooperative));
@@ -975,7 +976,9 @@ int build_loop_graph(SolveCtx &sc, const LoopPlan &lp, const float *b, const flo
     if (rc) return rc;
     cudaStream_t user = sc.st;
     cudaStream_t cs = ctx->cap_st[0], bs = ctx->cap_st[1];
-    const bool use_fused = lp.fused, use_pass = !lp.fused || lp.maxit > lp.fused_max;
+    const bool use_small = lp.fused && lp.small_max > 0;
+    const bool use_fused = lp.fused && lp.fused_max > lp.small_max;
+    const bool use_pass = !lp.fused || lp.maxit > lp.fused_max;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     ctx->capturing = true;
@@ -998,12 +1001,16 @@ int build_loop_graph(SolveCtx &sc, const LoopPlan &lp, const float *b, const flo
     LoopBufs B = sc.loop_bufs();
     B.in_graph = 1;
     B.fused_max = lp.fused ? lp.fused_max : 0;
+    B.small_max = use_small ? lp.small_max : 0;
     // the handles belong to the graph being captured
     cudaStreamCaptureStatus cstat;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
     if ((e = cudaStreamGetCaptureInfo(cs, &cstat, nullptr, &cg, &deps, nullptr, &ndeps)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaGraphConditionalHandleCreate(&B.c_small, cg, use_small ? 1u : 0u, cudaGraphCondAssignDefault)) !=
+        cudaSuccess)
         return fail(e);
     if ((e = cudaGraphConditionalHandleCreate(&B.c_fused, cg, use_fused ? 1u : 0u, cudaGraphCondAssignDefault)) !=
         cudaSuccess)
@@ -1015,7 +1022,7 @@ int build_loop_graph(SolveCtx &sc, const LoopPlan &lp, const float *b, const flo
     if ((rc = enqueue_init(sc, lp, b, x0, B))) return fail(cudaErrorUnknown);
     out->n_init = (int)(ctx->captured_kernels - k0);
     // while-loop nodes: their bodies are captured on the second stream
-    auto add_loop = [&](cudaGraphConditionalHandle h, bool fused, int *nkern) -> cudaError_t {
+    auto add_loop = [&](cudaGraphConditionalHandle h, bool fused, bool small_grid, int *nkern) -> cudaError_t {
         cudaError_t e2 = cudaStreamGetCaptureInfo(cs, &cstat, nullptr, &cg, &deps, nullptr, &ndeps);
         if (e2 != cudaSuccess) return e2;
         cudaGraphNodeParams cp = {};
@@ -1034,7 +1041,7 @@ int build_loop_graph(SolveCtx &sc, const LoopPlan &lp, const float *b, const flo
             return e2;
         sc.st = bs;
         const long long kb = ctx->captured_kernels;
-        const int rc2 = enqueue_step(sc, lp, b, x0, x, B, fused);
+        const int rc2 = enqueue_step(sc, lp, b, x0, x, B, fused, small_grid);
         *nkern = (int)(ctx->captured_kernels - kb);
         sc.st = cs;
         cudaGraph_t body_out = nullptr;
@@ -1042,9 +1049,10 @@ int build_loop_graph(SolveCtx &sc, const LoopPlan &lp, const float *b, const flo
         if (rc2) return cudaErrorUnknown;
         return e3;
     };
-    out->n_fused = out->n_pass = 0;
-    if (use_fused && (e = add_loop(B.c_fused, true, &out->n_fused)) != cudaSuccess) return fail(e);
-    if (use_pass && (e = add_loop(B.c_pass, false, &out->n_pass)) != cudaSuccess) return fail(e);
+    out->n_small = out->n_fused = out->n_pass = 0;
+    if (use_small && (e = add_loop(B.c_small, true, true, &out->n_small)) != cudaSuccess) return fail(e);
+    if (use_fused && (e = add_loop(B.c_fused, true, false, &out->n_fused)) != cudaSuccess) return fail(e);
+    if (use_pass && (e = add_loop(B.c_pass, false, false, &out->n_pass)) != cudaSuccess) return fail(e);
     const long long ke = ctx->captured_kernels;
     if ((rc = enqueue_exit(sc, lp, b, x0, x, B))) return fail(cudaErrorUnknown);
     out->n_exit = (int)(ctx->captured_kernels - ke);
@@ -1056,6 +1064,7 @@ int build_loop_graph(SolveCtx &sc, const LoopPlan &lp, const float *b, const flo
     graph = nullptr;
     if (e != cudaSuccess) return fail(e);
     out->exec = exec;
+    out->small_max = B.small_max;
     out->fused_max = B.fused_max;
     return CTG_OK;
 }
@@ -1100,6 +1109,9 @@ int run_gmres(SolveCtx &sc, int variant, const float *b, const float *x0, float 
     lp.fused_max = std::min(o->maxit, ctg_cgs2_fused_max(need_y));
     lp.fused = ctg_cgs2_fused_ok(sc.ly.dtype, sc.ly.L, lp.fused_max, sc.rs);
     if (!lp.fused) lp.fused_max = 0;
+    lp.small_max = lp.fused && ctg_cgs2_fused_ok(sc.ly.dtype, sc.ly.L, lp.fused_max, sc.rs, true)
+                       ? std::min(lp.fused_max, ctg_cgs2_small_grid_max())
+                       : 0;
     int rc = CTG_OK;
     if (lp.rule == kRuleNCP && (rc = ensure_twiddles(sc.ge))) return rc;
     GmresState hs{};
@@ -1150,8 +1162,9 @@ int run_gmres(SolveCtx &sc, int variant, const float *b, const float *x0, float 
             CTG_CK(cudaGraphLaunch(lg.exec, sc.st));
             rc = read_outcome(sc, lp, info, &hs);
             const long long steps = hs.steps;
-            const long long sf = lg.n_fused ? std::min<long long>(steps, lg.fused_max) : 0;
-            ctx->kernels += lg.n_init + lg.n_exit + sf * lg.n_fused + (steps - sf) * lg.n_pass;
+            const long long ss = lg.n_small ? std::min<long long>(steps, lg.small_max) : 0;
+            const long long sf = lg.n_fused ? std::min<long long>(steps, lg.fused_max) - ss : 0;
+            ctx->kernels += lg.n_init + lg.n_exit + ss * lg.n_small + sf * lg.n_fused + (steps - ss - sf) * lg.n_pass;
             return rc;
         }
     }
@@ -1160,6 +1173,7 @@ int run_gmres(SolveCtx &sc, int variant, const float *b, const float *x0, float 
     LoopBufs B = sc.loop_bufs();
     B.in_graph = 0;
     B.fused_max = lp.fused ? lp.fused_max : 0;
+    B.small_max = lp.fused ? lp.small_max : 0;
     if ((rc = enqueue_init(sc, lp, b, x0, B))) return rc;
     int *flag = reinterpret_cast<int *>(sc.pinned_scratch());
     if ((rc = ensure_events(ctx))) return rc;
@@ -1171,7 +1185,9 @@ int run_gmres(SolveCtx &sc, int variant, const float *b, const float *x0, float 
             CTG_CK(cudaEventSynchronize(ctx->ev_init));
             if (!*flag) break;
         }
-        if ((rc = enqueue_step(sc, lp, b, x0, x, B, lp.fused && k <= lp.fused_max))) return rc;
+        if ((rc = enqueue_step(sc, lp, b, x0, x, B, lp.fused && k <= lp.fused_max,
+                               lp.fused && k <= lp.small_max)))
+            return rc;
         CTG_CK(cudaMemcpyAsync(flag, &sc.state()->active, sizeof(int), cudaMemcpyDeviceToHost, sc.st));
         CTG_CK(cudaEventRecord(ctx->ev_init, sc.st));
         CTG_CK(cudaEventSynchronize(ctx->ev_init));

@@ -1073,12 +1073,32 @@ cudaError_t launch_fused(const T *W, int64_t ldw, int64_t L, int k, float *q, T 
     return e;
 }
 
+// The fused step's grid: that of the separate passes (two blocks per SM),
+// or with small_grid about one block per SM.  At the solvers' small k the
+// basis is L2-resident and the step is bound by its grid barriers and
+// summation tails, which fewer blocks shorten (the 512^2 AB + BA bench
+// pair: CGS2 phase 0.72 -> 0.68 ms); at large k streaming the basis needs
+// the two blocks per SM (k = 100, L = 522,000: 130 against 175 us).
+constexpr int kSmallGridMaxK = 24;
+
+static int fused_grid(int64_t L, int *E_out, bool small_grid) {
+    if (!small_grid) return ctg_red_grid(L, E_out);
+    const int64_t L4 = (L + 3) / 4;
+    const int target = ctg_target_grid() / 2;
+    int E = 1;
+    while (E < kMaxE && (L4 + (int64_t)kThreads * E - 1) / ((int64_t)kThreads * E) > target) E *= 2;
+    int64_t G = (L4 + (int64_t)kThreads * E - 1) / ((int64_t)kThreads * E);
+    if (G < 1) G = 1;
+    *E_out = E;
+    return (int)G;
+}
+
 template <typename T>
 cudaError_t fused_dispatch(const T *W, int64_t ldw, int64_t L, int k, float *q, T *w_out, double *h_out,
                            const LoopStep *ls, const RedScratch &rs, long long spin_limit,
                            bool cooperative, cudaStream_t st, bool *done) {
     int E;
-    const int G = ctg_red_grid(L, &E);
+    const int G = fused_grid(L, &E, ls && ls->small_grid);
     switch (E) {
         case 1: return launch_fused<T, 1>(W, ldw, L, k, q, w_out, h_out, ls, rs, G, spin_limit, cooperative, st, done);
         case 2: return launch_fused<T, 2>(W, ldw, L, k, q, w_out, h_out, ls, rs, G, spin_limit, cooperative, st, done);
@@ -1202,10 +1222,12 @@ cudaError_t ctg_cgs2_step_loop(const void *W, int dtype, int64_t ldw, int64_t L,
     }
 }
 
-bool ctg_cgs2_fused_ok(int dtype, int64_t L, int kmax, const RedScratch &rs) {
+int ctg_cgs2_small_grid_max() { return kSmallGridMaxK; }
+
+bool ctg_cgs2_fused_ok(int dtype, int64_t L, int kmax, const RedScratch &rs, bool small_grid) {
     if (kmax > kFusedMaxK || rs.rows < 2 * kmax + 2) return false;
     int E;
-    const int G = ctg_red_grid(L, &E);
+    const int G = fused_grid(L, &E, small_grid);
     int cap = 0;
     switch (dtype * 16 + E) {
 #define CTG_FOK(DT, T)                                                  \

@@ -236,13 +236,18 @@ struct LoopStep {
     // giv_mode < 0: none
     const LoopBufs *lb;
     int giv_mode;
+    // the fused step on one block per SM (small k, L2-resident basis: fewer
+    // blocks make the grid barriers and the summation tails shorter)
+    bool small_grid;
 };
 cudaError_t ctg_cgs2_step_loop(const void *W, int dtype, int64_t ldw, int64_t L, float *q, const LoopStep &ls,
                                const RedScratch &rs, long long spin_limit, bool cooperative, cudaStream_t st,
                                int *nkern = nullptr);
 // Whether the fused step serves k <= kmax at length L with this scratch
 // (every block of its grid resident at once).
-bool ctg_cgs2_fused_ok(int dtype, int64_t L, int kmax, const RedScratch &rs);
+bool ctg_cgs2_fused_ok(int dtype, int64_t L, int kmax, const RedScratch &rs, bool small_grid = false);
+// The largest k a solver runs the fused step on one block per SM.
+int ctg_cgs2_small_grid_max();
 // The largest k the fused step serves: smaller for solver steps that also
 // form y_k in the step (need_y), whose packed triangle takes shared memory.
 int ctg_cgs2_fused_max(bool need_y);
@@ -298,8 +303,9 @@ struct LoopBufs {
     double *scal;         // the reduction scratch's scalars
     double *h1;           // the reduction scratch's h1 (h1[k] = ||q_pre||^2)
     unsigned *counter;    // the reduction scratch's counters ([2]: barrier timeout)
-    cudaGraphConditionalHandle c_fused, c_pass;   // while-loop conditions (in_graph)
+    cudaGraphConditionalHandle c_small, c_fused, c_pass;   // while-loop conditions (in_graph)
     int in_graph;
+    int small_max;        // last k of the loop of fused steps on one block per SM (0: none)
     int fused_max;        // last k of the fused-CGS2 loop
 };
 // Modes of a step's Givens update: y_k every step (kGivY), AB NCP's

@@ -121,6 +121,7 @@ __global__ void loop_init_kernel(LoopBufs B, int variant, int rule, int maxit, d
     if (dp0 || beta == 0.0) {
         S.active = 0;
         S.stop_reason = dp0 ? CTG_STOP_DP : CTG_STOP_BREAKDOWN;
+        set_cond(B.c_small, B.in_graph, 0u);
         set_cond(B.c_fused, B.in_graph, 0u);
         set_cond(B.c_pass, B.in_graph, 0u);
     } else {

@@ -28,11 +28,13 @@ __device__ void end_step(const LoopBufs &B, int stop, int iters) {
         S.active = 0;
         S.stop_reason = stop - 1;
         S.iters = iters;
+        set_cond(B.c_small, B.in_graph, 0u);
         set_cond(B.c_fused, B.in_graph, 0u);
         set_cond(B.c_pass, B.in_graph, 0u);
     } else {
         const int k1 = S.k + 1;
         S.k = k1;
+        if (k1 > B.small_max) set_cond(B.c_small, B.in_graph, 0u);
         if (k1 > B.fused_max) set_cond(B.c_fused, B.in_graph, 0u);
     }
 }
