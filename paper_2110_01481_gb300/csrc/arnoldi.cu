@@ -1076,8 +1076,8 @@ cudaError_t launch_fused(const T *W, int64_t ldw, int64_t L, int k, float *q, T 
 // The fused step's grid: that of the separate passes (two blocks per SM),
 // or with small_grid about one block per SM.  At the solvers' small k the
 // basis is L2-resident and the step is bound by its grid barriers and
-// summation tails, which fewer blocks shorten (the 512^2 AB + BA bench
-// pair: CGS2 phase 0.72 -> 0.68 ms); at large k streaming the basis needs
+// summation tails, which fewer blocks shorten (512^2 AB + BA pair, 720
+// angles: CGS2 phase 0.72 -> 0.69 ms per pair); at large k streaming the basis needs
 // the two blocks per SM (k = 100, L = 522,000: 130 against 175 us).
 constexpr int kSmallGridMaxK = 24;
 
